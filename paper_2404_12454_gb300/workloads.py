@@ -1,0 +1,239 @@
+"""Seeded synthetic workloads for plane-evaluation Gaussian beamlet decomposition.
+
+This module only *describes inputs*: optical prescriptions, pupil sampling, detector
+geometry, random draws and sizes.  It holds none of the method's arithmetic, so both
+the CUDA library's callers and the FP64 CPU oracle's tests build their inputs from it.
+
+The paper's experiments use a Zemax-traced Hubble-like telescope (Sec. 4.2, App. B)
+whose ray data is not public.  Paraxial GBD expressed in units of lambda*F/# is
+scale-free, so an ideal thin lens of the same focal ratio per lambda*F/# stands in
+for it: the beamlet envelope at focus is w_f = lambda*f/(pi*w0) = (2N/(pi*OF)) *
+lambda*F/#, independent of the absolute pupil size (Eq. OF, Sec. 6).
+
+Five workloads:
+
+* ``airy_small``   -- 2.4 mm pupil, lambda 1 um, F/10 lens focused on its focal
+  plane, 32 beamlets across (812 inside), OF 1.5, 128x128 pixels over +-5 lambda F/#.
+* ``airy_large``   -- same optics, 256 across (51,468 beamlets), 512x512 over
+  +-20 lambda F/#.
+* ``tilted_zernike`` -- F/5, lambda 0.633 um, Noll Z4..Z15 OPD plate drawn from
+  N(0, (0.05 lambda)^2), 128 across (12,892 beamlets), OF 2.0, waist ratio 1.2,
+  1024x1024 pixels over +-15 lambda F/#, detector tilted 10 deg about x, 5 deg about y.
+* ``sweep``        -- 1024 instances of the airy_small optics with OF ~ U[1,3],
+  waist ratio ~ U[0.8,3], beamlets across ~ U{16,32,64,128,256}, 256x256 pixels
+  over +-5 lambda F/#.
+* ``surrogate``    -- the MLP search over the sweep's parameter space.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+SEED_ZERNIKE = 240412454
+SEED_SWEEP = 240412455
+SEED_SURROGATE = 240412456
+
+# Number of beamlets across the pupil that the parameter search may use (Sec. 6).
+SWEEP_N_ACROSS = (16, 32, 64, 128, 256)
+
+
+@dataclasses.dataclass(frozen=True)
+class System:
+    """Paraxial system: optional Zernike OPD plate at the pupil, thin lens f, distance d.
+
+    ``noll`` / ``zern_coef`` are Noll indices and RMS-normalised coefficients in metres
+    of optical path over the disk of radius ``zern_radius``.
+    """
+
+    wavelength: float
+    focal_length: float
+    distance: float
+    noll: Tuple[int, ...] = ()
+    zern_coef: Tuple[float, ...] = ()
+    zern_radius: float = 1.0
+
+
+@dataclasses.dataclass(frozen=True)
+class Pupil:
+    """Uniform circular pupil of ``diameter`` sampled by ``n_across`` beamlets across."""
+
+    diameter: float
+    n_across: int
+    overlap_factor: float
+    waist_ratio: float
+
+
+@dataclasses.dataclass(frozen=True)
+class Detector:
+    """Pixel grid on a plane through (0, 0, d) rotated by R = Ry(rot_y) Rx(rot_x).
+
+    Pixel (i, j) (column i along x, row j along y) sits at detector coordinates
+    s = ((i - nx//2) * pitch_x, (j - ny//2) * pitch_y), so a pixel lies on the axis.
+    """
+
+    nx: int
+    ny: int
+    pitch_x: float
+    pitch_y: float
+    rot_x: float = 0.0
+    rot_y: float = 0.0
+
+
+@dataclasses.dataclass(frozen=True)
+class Workload:
+    name: str
+    system: System
+    pupil: Pupil
+    detector: Detector
+    # strided pixel subset on which the oracle is evaluated (None = every pixel)
+    oracle_stride: Optional[Tuple[int, int]] = None  # (offset, step) on both axes
+
+    @property
+    def f_number(self) -> float:
+        return self.system.focal_length / self.pupil.diameter
+
+
+def _span_pitch(n: int, half_span_lfd: float, wavelength: float, f_number: float) -> float:
+    """Pixel pitch for n pixels spanning +-half_span_lfd lambda*F/#."""
+    return 2.0 * half_span_lfd * wavelength * f_number / n
+
+
+def airy_small() -> Workload:
+    lam, D, f = 1.0e-6, 2.4e-3, 24.0e-3
+    p = _span_pitch(128, 5.0, lam, f / D)
+    return Workload(
+        "airy_small",
+        System(lam, f, f),
+        Pupil(D, 32, 1.5, 1.5),
+        Detector(128, 128, p, p),
+    )
+
+
+def airy_large() -> Workload:
+    lam, D, f = 1.0e-6, 2.4e-3, 24.0e-3
+    p = _span_pitch(512, 20.0, lam, f / D)
+    return Workload(
+        "airy_large",
+        System(lam, f, f),
+        Pupil(D, 256, 1.5, 1.5),
+        Detector(512, 512, p, p),
+    )
+
+
+def zernike_draw(wavelength: float, noll: Sequence[int] = tuple(range(4, 16)),
+                 sigma_waves: float = 0.05, seed: int = SEED_ZERNIKE) -> Tuple[float, ...]:
+    """Coefficients c_j ~ N(0, (sigma_waves*lambda)^2), in metres, one per Noll index."""
+    rng = np.random.default_rng(seed)
+    return tuple(float(v) for v in rng.normal(0.0, sigma_waves * wavelength, size=len(noll)))
+
+
+def tilted_zernike() -> Workload:
+    lam, D, f = 0.633e-6, 2.4e-3, 12.0e-3
+    noll = tuple(range(4, 16))
+    coef = zernike_draw(lam, noll)
+    p = _span_pitch(1024, 15.0, lam, f / D)
+    return Workload(
+        "tilted_zernike",
+        System(lam, f, f, noll, coef, D / 2.0),
+        Pupil(D, 128, 2.0, 1.2),
+        Detector(1024, 1024, p, p, math.radians(10.0), math.radians(5.0)),
+        oracle_stride=(8, 16),
+    )
+
+
+@dataclasses.dataclass(frozen=True)
+class Sweep:
+    """A batch of GBD instances sharing optics and detector, differing in (N, OF, WR)."""
+
+    system: System
+    diameter: float
+    detector: Detector
+    n_across: Tuple[int, ...]
+    overlap_factor: Tuple[float, ...]
+    waist_ratio: Tuple[float, ...]
+
+    @property
+    def n_instances(self) -> int:
+        return len(self.n_across)
+
+    def pupil(self, k: int) -> Pupil:
+        return Pupil(self.diameter, self.n_across[k], self.overlap_factor[k], self.waist_ratio[k])
+
+
+def sweep_optics() -> Tuple[System, float, Detector]:
+    lam, D, f = 1.0e-6, 2.4e-3, 24.0e-3
+    p = _span_pitch(256, 5.0, lam, f / D)
+    return System(lam, f, f), D, Detector(256, 256, p, p)
+
+
+def sweep(n_instances: int = 1024, seed: int = SEED_SWEEP) -> Sweep:
+    system, D, det = sweep_optics()
+    rng = np.random.default_rng(seed)
+    of = rng.uniform(1.0, 3.0, size=n_instances)
+    wr = rng.uniform(0.8, 3.0, size=n_instances)
+    n = rng.choice(np.asarray(SWEEP_N_ACROSS), size=n_instances)
+    return Sweep(system, D, det, tuple(int(v) for v in n), tuple(float(v) for v in of),
+                 tuple(float(v) for v in wr))
+
+
+def grid_sweep() -> Sweep:
+    """The regular reference grid of the parameter search: 21 OF x 12 WR x 5 N = 1,260."""
+    system, D, det = sweep_optics()
+    ofs = np.linspace(1.0, 3.0, 21)
+    wrs = np.linspace(0.8, 3.0, 12)
+    n, of, wr = [], [], []
+    for N in SWEEP_N_ACROSS:
+        for a in ofs:
+            for b in wrs:
+                n.append(int(N)), of.append(float(a)), wr.append(float(b))
+    return Sweep(system, D, det, tuple(n), tuple(of), tuple(wr))
+
+
+def sweep_from_params(params: Sequence[Tuple[int, float, float]]) -> Sweep:
+    system, D, det = sweep_optics()
+    return Sweep(system, D, det, tuple(int(p[0]) for p in params),
+                 tuple(float(p[1]) for p in params), tuple(float(p[2]) for p in params))
+
+
+def strided_pixels(workload: Workload) -> Tuple[np.ndarray, np.ndarray]:
+    """Column / row indices of the oracle's pixel subset (all pixels if no stride)."""
+    det = workload.detector
+    if workload.oracle_stride is None:
+        return np.arange(det.nx), np.arange(det.ny)
+    off, step = workload.oracle_stride
+    return np.arange(off, det.nx, step), np.arange(off, det.ny, step)
+
+
+WORKLOADS = {
+    "airy_small": airy_small,
+    "airy_large": airy_large,
+    "tilted_zernike": tilted_zernike,
+}
+
+
+def by_name(name: str) -> Workload:
+    return WORKLOADS[name]()
+
+
+def scaled(workload: Workload, n_across: Optional[int] = None, nx: Optional[int] = None,
+           ny: Optional[int] = None, keep_span: bool = True) -> Workload:
+    """A smaller copy of a workload (same optics) for oracle-sized parity cases."""
+    pupil = workload.pupil
+    det = workload.detector
+    if n_across is not None:
+        pupil = dataclasses.replace(pupil, n_across=n_across)
+    if nx is not None or ny is not None:
+        nx2 = nx if nx is not None else det.nx
+        ny2 = ny if ny is not None else det.ny
+        px = det.pitch_x * det.nx / nx2 if keep_span else det.pitch_x
+        py = det.pitch_y * det.ny / ny2 if keep_span else det.pitch_y
+        det = dataclasses.replace(det, nx=nx2, ny=ny2, pitch_x=px, pitch_y=py)
+    return dataclasses.replace(workload, pupil=pupil, detector=det, oracle_stride=None)
+
+
+def sweep_subset(sw: Sweep, idx: List[int]) -> Sweep:
+    return Sweep(sw.system, sw.diameter, sw.detector, tuple(sw.n_across[i] for i in idx),
+                 tuple(sw.overlap_factor[i] for i in idx), tuple(sw.waist_ratio[i] for i in idx))
