@@ -310,9 +310,10 @@ int orc_trace(double wavelength, double f, double d, int n_zern, const int* noll
 
 /* ------------------------------------------------------------------- field -- */
 
-/* Lab position of detector point s: X = (0,0,d) + Ry(rot_y) Rx(rot_x) (sx, sy, 0). */
-static void detector_point(double rot_x, double rot_y, double d, double sx, double sy,
-                           double X[3]) {
+/* Offset of detector point s from the reference point (0, 0, d) in the lab frame:
+ * X - (0, 0, d) = Ry(rot_y) Rx(rot_x) (sx, sy, 0).  Kept relative to the reference point
+ * so that the axial offset z = X_z - d carries no rounding from d itself. */
+static void detector_offset(double rot_x, double rot_y, double sx, double sy, double V[3]) {
     double ca = cos(rot_x), sa = sin(rot_x), cb = cos(rot_y), sb = sin(rot_y);
     double Rx[3][3] = {{1, 0, 0}, {0, ca, -sa}, {0, sa, ca}};
     double Ry[3][3] = {{cb, 0, sb}, {0, 1, 0}, {-sb, 0, cb}};
@@ -323,12 +324,11 @@ static void detector_point(double rot_x, double rot_y, double d, double sx, doub
             for (int k = 0; k < 3; ++k) R[i][j] += Ry[i][k] * Rx[k][j];
         }
     double v[3] = {sx, sy, 0.0};
-    for (int i = 0; i < 3; ++i) X[i] = R[i][0] * v[0] + R[i][1] * v[1] + R[i][2] * v[2];
-    X[2] += d;
+    for (int i = 0; i < 3; ++i) V[i] = R[i][0] * v[0] + R[i][1] * v[1] + R[i][2] * v[2];
 }
 
-/* Field of one beamlet at lab point X (step 5). */
-static double complex beamlet_at(const double* rec, double k, double d, const double X[3]) {
+/* Field of one beamlet at the point V (offset from the reference point) (step 5). */
+static double complex beamlet_at(const double* rec, double k, const double V[3]) {
     double complex P[2][2];
     for (int q = 0; q < 2; ++q)
         for (int c = 0; c < 2; ++c)
@@ -337,8 +337,8 @@ static double complex beamlet_at(const double* rec, double k, double d, const do
     const double* rho = rec + REC_RHO;
     const double* th = rec + REC_THETA;
     double L = rec[REC_L];
-    double z = X[2] - d;
-    double delta[2] = {X[0] - rho[0], X[1] - rho[1]};
+    double z = V[2];
+    double delta[2] = {V[0] - rho[0], V[1] - rho[1]};
     double w[2] = {delta[0] - z * th[0], delta[1] - z * th[1]};
     double th2 = th[0] * th[0] + th[1] * th[1];
     double complex quad = 0.0;
@@ -363,11 +363,11 @@ void orc_field(const double* beamlets, int n_b, double wavelength, double d, dou
     for (long p = 0; p < total; ++p) {
         int b = (int)(p / n_cols), a = (int)(p % n_cols);
         double sx = (cols[a] - nx / 2) * px, sy = (rows[b] - ny / 2) * py;
-        double X[3];
-        detector_point(rot_x, rot_y, d, sx, sy, X);
+        double V[3];
+        detector_offset(rot_x, rot_y, sx, sy, V);
         double sr = 0.0, si = 0.0, cr = 0.0, ci = 0.0;
         for (int j = 0; j < n_b; ++j) {
-            double complex e = beamlet_at(beamlets + (size_t)j * REC_SIZE, k, d, X);
+            double complex e = beamlet_at(beamlets + (size_t)j * REC_SIZE, k, V);
             double er = creal(e), ei = cimag(e);
             double t = sr + er;
             cr += (fabs(sr) >= fabs(er)) ? (sr - t) + er : (er - t) + sr;
@@ -395,7 +395,7 @@ void orc_field_exact(const double* beamlets, int n_b, double wavelength, double 
         int b = (int)(p / n_cols), a = (int)(p % n_cols);
         double sx = (cols[a] - nx / 2) * px, sy = (rows[b] - ny / 2) * py;
         double X[3];
-        detector_point(rot_x, rot_y, d, sx, sy, X);
+        detector_offset(rot_x, rot_y, sx, sy, X);
         double complex acc = 0.0;
         for (int j = 0; j < n_b; ++j) {
             const double* rec = beamlets + (size_t)j * REC_SIZE;
@@ -406,7 +406,7 @@ void orc_field_exact(const double* beamlets, int n_b, double wavelength, double 
             double complex alpha = rec[REC_ALPHA] + I * rec[REC_ALPHA + 1];
             const double* rho = rec + REC_RHO;
             const double* th = rec + REC_THETA;
-            double z = X[2] - d;
+            double z = X[2];
             cmat2 Mz;
             Mz.m[0][0] = 1.0 + z * P.m[0][0];
             Mz.m[0][1] = z * P.m[0][1];

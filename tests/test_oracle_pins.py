@@ -521,13 +521,13 @@ def test_tilted_detector_geometry_against_textbook_beam():
     sx = (np.arange(15) - 7) * p
     sy = (np.arange(13) - 6) * 1.1 * p
     SX, SY = np.meshgrid(sx, sy)
-    pts = np.stack([SX, SY, np.zeros_like(SX)], -1) @ R.T + np.array([0.0, 0.0, d])
-    z = pts[..., 2]
+    off = np.stack([SX, SY, np.zeros_like(SX)], -1) @ R.T  # X - (0, 0, d)
+    z = d + off[..., 2]
     q0 = 1j * math.pi * w0 ** 2 / lam
     a = D * D / (math.pi * w0 * w0)
     k = _k(lam)
-    Et = a * q0 / (q0 + z) * np.exp(-1j * k * (pts[..., 0] ** 2 + pts[..., 1] ** 2) / (2 * (q0 + z))) \
-        * np.exp(-1j * k * (z - d))
+    Et = a * q0 / (q0 + z) * np.exp(-1j * k * (off[..., 0] ** 2 + off[..., 1] ** 2) / (2 * (q0 + z))) \
+        * np.exp(-1j * k * off[..., 2])
     assert np.max(np.abs(E - Et)) < 1e-12 * np.abs(Et).max()
     rel = np.linalg.norm(Emid - Et) / np.linalg.norm(Et)
     assert 0 < rel < 1e-2
