@@ -1,0 +1,424 @@
+#!/usr/bin/env python
+"""Throughput of plane-evaluation Gaussian beamlet decomposition on GB300.
+
+One step = one pass of the hot path over the 512 x 512-pixel, 51,468-beamlet Airy workload
+(2.4 mm pupil, lambda 1 um, F/10, 256 beamlets across, +-20 lambda F#): gbd_trace
+(decomposition + differential trace) and gbd_field (per-beamlet projection, per-pixel
+evaluation, coherent sum) in the mixed FP32/FP64 path.  The metric is beamlet-pixel
+evaluations per second.  Also reported: the FP64 path on the same workload, the error of
+both against the FP64 CPU oracle on a pixel sample, an end-to-end number through the
+host-buffer call gbd_psf, the field kernel's fraction of the MUFU-pipe roofline and the
+oracle timed on the host cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank runs an independent replica (the workload does not need a
+collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("beamlet·pixel evals/s on 1 GB300, mixed vs FP64 path, at stated error vs FP64 "
+          "oracle")
+UNIT = "evals/s"
+# MUFU results per clock per SM for ex2 / sin / cos (CUDA C programming guide throughput
+# table), SM count and maximum SM clock of GB300.
+MUFU_PER_CLK_SM = 16
+GB300_SMS = 152
+GB300_MAX_MHZ = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0,
+                    help="target CPU time of the oracle baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(world, value: float) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64,
+                     device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def config_block(wl, nb):
+    det = wl.detector
+    return {
+        "workload": (f"{wl.name}: {nb} beamlets x {det.nx}x{det.ny} pixels, lambda "
+                     f"{wl.system.wavelength * 1e6:g} um, F/{wl.f_number:g}, "
+                     f"{wl.pupil.n_across} beamlets across, OF {wl.pupil.overlap_factor}"),
+        "n_beamlets": nb,
+        "n_pixels": det.nx * det.ny,
+        "evals_per_step": nb * det.nx * det.ny,
+        "l2": "flushed between timed steps (256 MB write); step inputs < L2",
+        "parallelism": "replicas (no data-path collective)",
+    }
+
+
+# ------------------------------------------------------------------ clocks --
+
+class ClockSampler:
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: str):
+        self.proc = None
+        self.path = None
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            self.fh = os.fdopen(fd, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "50", "-i", gpu_index], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        self.windows = []
+
+    def mark(self):
+        return time.time()
+
+    def add_window(self, t0, t1):
+        self.windows.append((t0, t1))
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.1)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        import datetime
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(parts[2]), float(parts[3]), parts[5:]))
+            except Exception:
+                continue
+        os.unlink(self.path)
+        inside = [r for r in rows if any(a - 0.06 <= r[0] <= b + 0.06 for a, b in self.windows)]
+        use = inside if inside else rows
+        if not use:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        mhz = sorted(r[1] for r in use)
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = set()
+        for r in use:
+            flags = r[3]
+            for name, flag in zip(names, flags[1:5]):
+                if flag.lower() in ("active", "0x1", "1"):
+                    reasons.add(name)
+        return {"sm_mhz": mhz[len(mhz) // 2], "sm_max_mhz": max(r[2] for r in use),
+                "reasons": sorted(reasons), "samples": len(use),
+                "samples_in_timed_region": len(inside)}
+
+
+def gpu_index_for_smi(local: int) -> str:
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(local).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        return vis.split(",")[local] if vis else str(local)
+
+
+# ------------------------------------------------------------- CPU oracle --
+
+def oracle_sample_rate(wl, seconds: float, rows_hint=None):
+    """Oracle evals/s on a strided row sample sized to about `seconds` of CPU time."""
+    import numpy as np
+
+    import oracle
+    o = oracle.trace(wl.system, wl.pupil)
+    nb = o.shape[0]
+    cols = np.arange(wl.detector.nx)
+    if rows_hint is None:
+        t0 = time.perf_counter()
+        oracle.field(o, wl.system, wl.detector, cols, [wl.detector.ny // 2])
+        t1 = time.perf_counter() - t0
+        n_rows = int(max(1, min(wl.detector.ny, seconds / max(t1, 1e-6))))
+    else:
+        n_rows = rows_hint
+    rows = np.linspace(0, wl.detector.ny - 1, n_rows).round().astype(int)
+    t0 = time.perf_counter()
+    E = oracle.field(o, wl.system, wl.detector, cols, rows)
+    dt = time.perf_counter() - t0
+    evals = nb * cols.size * rows.size
+    return {"value": evals / dt, "seconds": dt, "evals": evals, "rows": rows, "cols": cols,
+            "field": E, "cores": oracle.threads(), "nb": nb}
+
+
+# ------------------------------------------------------------------- ours --
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    from paper_2404_12454_gb300 import gbd
+    from paper_2404_12454_gb300 import workloads as W
+
+    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = W.airy_large()
+    sysm, pupil, det = wl.system, wl.pupil, wl.detector
+    nb = gbd.gbd_beamlet_count(pupil)
+    npix = det.nx * det.ny
+    evals = nb * npix
+    MIX, F64 = gbd.GBD_PREC_MIXED, gbd.GBD_PREC_F64
+
+    beam = torch.empty((nb, 36), dtype=torch.float64, device=dev)
+    ws = {p: torch.empty(max(256, gbd.gbd_field_workspace_bytes(nb, det, p)), dtype=torch.uint8,
+                         device=dev) for p in (MIX, F64)}
+    out = {MIX: torch.empty((det.ny, det.nx), dtype=torch.complex64, device=dev),
+           F64: torch.empty((det.ny, det.nx), dtype=torch.complex128, device=dev)}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(prec):
+        gbd.gbd_trace(sysm, pupil, pupil.overlap_factor, pupil.waist_ratio, beam, stream)
+        gbd.gbd_field(beam, nb, sysm.wavelength, det, prec, ws[prec], out[prec], stream)
+
+    def timed(prec, k, clocks=None):
+        times = []
+        for _ in range(k):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(prec)
+            e1.record(stream)
+            times.append((e0, e1))
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in times]
+
+    clocks = ClockSampler(gpu_index_for_smi(local))
+    for _ in range(args.warmup):
+        step(MIX)
+    gbd.gbd_sync(stream)
+
+    # ---- mixed path, K timed steps
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    gbd.gbd_timing_read()
+    gbd.gbd_timing_enable(True)
+    t0 = time.time()
+    ms = timed(MIX, args.steps)
+    t1 = time.time()
+    gbd.gbd_timing_enable(False)
+    clocks.add_window(t0, t1)
+    gbd.gbd_sync(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    kt = gbd.gbd_timing_read()
+    total_ms = allreduce_max(world, sum(ms))
+    ms_per_step = total_ms / args.steps
+    value = world * evals * args.steps / (total_ms * 1e-3)
+    E_mix = out[MIX].cpu().numpy().astype(np.complex128)
+
+    # ---- FP64 path on the same workload
+    f64 = None
+    if args.fp64_steps > 0:
+        step(F64)
+        gbd.gbd_sync(stream)
+        t0 = time.time()
+        ms64 = timed(F64, args.fp64_steps)
+        clocks.add_window(t0, time.time())
+        total64 = allreduce_max(world, sum(ms64))
+        v64 = world * evals * args.fp64_steps / (total64 * 1e-3)
+        E_64 = out[F64].cpu().numpy()
+        f64 = {"value": v64, "unit": UNIT, "ms_per_step": total64 / args.fp64_steps,
+               "steps": args.fp64_steps, "mixed_speedup": value / v64,
+               "mixed_vs_fp64_rel_l2": float(np.linalg.norm(E_mix - E_64) / np.linalg.norm(E_64))}
+
+    # ---- end to end: host-side parameters in, host field out, through gbd_psf
+    ws_psf = torch.empty(gbd.gbd_psf_workspace_bytes(pupil, det, MIX), dtype=torch.uint8, device=dev)
+    host = torch.empty((det.ny, det.nx), dtype=torch.complex64).pin_memory()
+
+    def psf_step():
+        gbd.gbd_psf(sysm, pupil, pupil.overlap_factor, pupil.waist_ratio, det, MIX, ws_psf, host,
+                    stream)
+        gbd.gbd_sync(stream)
+
+    for _ in range(2):
+        psf_step()
+    barrier(world)
+    e2e_t = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        psf_step()
+        e2e_t.append(time.perf_counter() - a)
+    e2e_total = allreduce_max(world, sum(e2e_t))
+    gbd_system_bytes = 4 * 8 + 4 + 64 * 4 + 64 * 8 + 4  # gbd_system as passed (with padding)
+    e2e = {"value": world * evals * args.steps / e2e_total, "unit": UNIT,
+           "h2d_bytes_per_step": gbd_system_bytes + 16 + 40,
+           "d2h_bytes_per_step": npix * 8,
+           "api": "gbd_psf (host parameters -> pinned host complex64 field)"}
+
+    clk = clocks.stop()
+
+    # ---- roofline of the dominant kernel (mixed field kernel, MUFU pipe)
+    kms, kn = kt["field_mixed"]
+    k_avg_s = (kms / max(kn, 1)) * 1e-3
+    probes = gbd.gbd_probe_peaks()
+    mufu_ops = 3.0 * evals
+    achieved = mufu_ops / k_avg_s / 1e9
+    derived_peak = MUFU_PER_CLK_SM * GB300_SMS * GB300_MAX_MHZ * 1e6 / 1e9
+    probe_peak_evals = 1.0 / (1.0 / probes["ex2"] + 1.0 / probes["sin"] + 1.0 / probes["cos"])
+    roofline = {
+        "bound": "alu", "pipe": "MUFU (XU): ex2 + sin + cos per beamlet-pixel",
+        "achieved": achieved, "peak": derived_peak, "unit": "GMUFU-op/s",
+        "frac": achieved / derived_peak, "traffic": None,
+        "peak_source": f"derived: {MUFU_PER_CLK_SM} MUFU results/clk/SM x {GB300_SMS} SMs x "
+                       f"{GB300_MAX_MHZ:g} MHz",
+        "kernel": "field_mixed_kernel", "kernel_ms_avg": k_avg_s * 1e3, "launches": kn,
+        "evals_per_s_kernel": evals / k_avg_s,
+        "probe_ops_per_s": probes,
+        "frac_of_probe_eval_peak": (evals / k_avg_s) / probe_peak_evals,
+    }
+
+    # ---- error and CPU baseline (rank 0, one GPU)
+    cpu = None
+    error = {}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r = oracle_sample_rate(wl, args.cpu_seconds)
+        rows, cols = r["rows"], r["cols"]
+        Eo = r["field"]
+        error["mixed_vs_oracle_rel_l2"] = float(
+            np.linalg.norm(E_mix[np.ix_(rows, cols)] - Eo) / np.linalg.norm(Eo))
+        if f64 is not None:
+            error["fp64_vs_oracle_rel_l2"] = float(
+                np.linalg.norm(E_64[np.ix_(rows, cols)] - Eo) / np.linalg.norm(Eo))
+        cpu = {"value": r["value"], "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+               "sample": f"{rows.size} of {det.ny} rows x {cols.size} columns x {r['nb']} beamlets "
+                         f"({r['evals']:.3g} evals, {r['seconds']:.1f} s, FP64 C + OpenMP)"}
+
+    launches_per_step = 4  # trace, projection, field, split reduction
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "precision": "mixed: FP64 per-beamlet trace/projection, FP32 per-pixel phase with MUFU "
+                     "ex2/sin/cos, compensated FP32 sum",
+        "data": "synthetic (ideal F/10 lens standing in for the paper's traced telescope)",
+        "config": config_block(wl, nb), "clocks": clk, "e2e": e2e, "fp64_path": f64,
+        "error": error, "roofline": roofline, "cpu_baseline": cpu,
+        "gpu_launches": launches_per_step * args.steps,
+        "kernel_ms": {k: (v[0] / max(v[1], 1)) for k, v in kt.items()},
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# -------------------------------------------------------------- reference --
+
+def run_reference(args, world, rank, local):
+    """The FP64 CPU oracle as it stands, timed on the host cores, one bounded sample of the
+    same workload per step."""
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from paper_2404_12454_gb300 import workloads as W
+    import oracle.build as ob
+    ob.build()
+    wl = W.airy_large()
+    o = oracle.trace(wl.system, wl.pupil)
+    nb = o.shape[0]
+    cols = np.arange(wl.detector.nx)
+    rows_per_step = 2
+    times = []
+    for s in range(args.warmup + args.steps):
+        rows = [(37 * s + 11 * q) % wl.detector.ny for q in range(rows_per_step)]
+        t0 = time.perf_counter()
+        oracle.field(o, wl.system, wl.detector, cols, rows)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    evals = nb * cols.size * rows_per_step
+    total = sum(times)
+    value = evals * len(times) / total
+    cpu = {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+           "sample": f"{rows_per_step} rows x {cols.size} columns x {nb} beamlets per step"}
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / len(times) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_block(wl, nb), "cpu_baseline": cpu,
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank, local)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+    run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,223 @@
+/*
+ * gbd.h -- C ABI of a GB300-native plane-evaluation Gaussian beamlet decomposition (GBD).
+ *
+ * Method (arXiv 2404.12454): a pupil wavefront is decomposed into Gaussian beamlets on a
+ * square grid (Eq. sum_gaussian, Eq. OF); each beamlet is carried through a paraxial
+ * system by a chief ray and four parabasal rays whose one-sided differences give a 4x4
+ * differential ray-transfer matrix (Sec. 2.2); the Gaussian solution of the Collins
+ * integral (Eq. gauss_prop) propagates its complex curvature and amplitude; and the
+ * beamlet is evaluated on every pixel of a common evaluation plane at once (Sec. 3,
+ * Eq. collins_factored) before the coherent sum over beamlets.
+ *
+ * Conventions shared by every call:
+ *   - SI units (metres), angles in radians, time convention exp(-ik * optical path).
+ *   - Phases are relative to the axial path: the constant exp(-ik d) is not applied.
+ *   - Calls are asynchronous on the CUDA stream passed as `stream` (a cudaStream_t; NULL
+ *     is the legacy default stream).  Pointers documented as "device" must be device
+ *     memory of the current device; the library never frees or retains caller memory.
+ *   - Argument errors are found on the host before any launch and return GBD_EINVAL;
+ *     nothing is launched then.  CUDA errors return GBD_ECUDA.  A kernel that gives up
+ *     a bounded wait records GBD_ETIMEOUT in a per-device status word read by
+ *     gbd_sync().  gbd_last_error() gives a message for the calling thread.
+ *   - No call allocates device memory except gbd_sweep_plan_create (host tables only)
+ *     and the workspace-free helpers stated below; scratch memory is a caller-provided
+ *     workspace whose size a *_workspace_bytes query returns.
+ *   - All entry points are safe to call from several host threads on different streams.
+ */
+#ifndef GBD_H
+#define GBD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GBD_OK = 0,
+    GBD_EINVAL = 1,       /* bad argument (detected on the host, nothing launched) */
+    GBD_ECUDA = 2,        /* CUDA runtime error                                    */
+    GBD_ENOMEM = 3,       /* workspace or capacity too small / host allocation     */
+    GBD_ETIMEOUT = 4,     /* a device wait gave up (see gbd_sync)                  */
+    GBD_EUNSUPPORTED = 5  /* device is not sm_103 / feature unavailable            */
+} gbd_status;
+
+enum { GBD_PREC_F64 = 0, GBD_PREC_MIXED = 1 };
+
+#define GBD_MAX_ZERN 64   /* Zernike terms in an OPD plate                       */
+#define GBD_MAX_NOLL 66   /* highest Noll index (radial order <= 10)             */
+
+/* Paraxial system: [OPD plate] -> thin lens -> free space to the reference plane.
+ * The plate is a thin phase screen at the pupil with optical path
+ * W(x, y) = sum_t zern_coef[t] * Z_{noll[t]}(x / zern_radius, y / zern_radius), Noll-ordered,
+ * RMS-normalised Zernike polynomials (Sec. 4.3 uses Noll modes).  The lens of focal
+ * length f transmits exp(+ik r^2 / 2f) (use +INFINITY for no lens, Eq. abcd_sys). */
+typedef struct {
+    double wavelength;    /* m                                         */
+    double focal_length;  /* m, +INFINITY = no lens                    */
+    double distance;      /* m, lens (pupil) to the reference plane    */
+    double zern_radius;   /* m, normalisation radius of the plate       */
+    int32_t n_zern;       /* 0 .. GBD_MAX_ZERN                          */
+    int32_t noll[GBD_MAX_ZERN];       /* 1 .. GBD_MAX_NOLL             */
+    double zern_coef[GBD_MAX_ZERN];   /* m of optical path             */
+} gbd_system;
+
+/* Uniform circular pupil of `diameter` sampled by `n_across` beamlets across: centres
+ * x_i = (i - (N-1)/2) s, s = D/N, kept when |r| <= D/2 (Eq. OF, Sec. 6). */
+typedef struct {
+    double diameter;      /* m                        */
+    int32_t n_across;     /* 1 .. 4096                */
+    int32_t reserved;
+} gbd_pupil;
+
+/* Detector plane through the reference point (0, 0, d), rotated by R = Ry(rot_y) Rx(rot_x).
+ * Pixel (i, j) (column i, row j) sits at s = ((i - nx/2) pitch_x, (j - ny/2) pitch_y)
+ * (integer division), lab point (0, 0, d) + R (s, 0).  A field is stored row-major
+ * [ny][nx].  The second-order tilted-plane rule applies (see gbd_field). */
+typedef struct {
+    double pitch_x, pitch_y;   /* m, > 0               */
+    double rot_x, rot_y;       /* rad, |.| < 1.2       */
+    int32_t nx, ny;            /* 1 .. 16384 each      */
+} gbd_detector;
+
+/* One traced beamlet (FP64, 36 doubles = 288 bytes), written by gbd_trace. */
+typedef struct {
+    double rho[2];      /* chief-ray landing point on the reference plane, m            */
+    double theta[2];    /* chief-ray slope                                             */
+    double path;        /* chief-ray optical path in excess of the axial path, m       */
+    double amp[2];      /* a_j / sqrtdet(A + B P1), complex (re, im)                    */
+    double curv[8];     /* P2 = (C + D P1)(A + B P1)^-1, 2x2 complex row-major (re, im) */
+    double abcd[16];    /* A, B, C, D 2x2 blocks, each row-major                        */
+    double center[2];   /* beamlet centre r_j in the pupil, m                           */
+    double weight;      /* a_j = s^2 / (pi w0^2)                                        */
+    double waist;       /* w0 = OF D / (2N), m                                          */
+    double reserved;    /* 0                                                            */
+} gbd_beamlet;
+
+/* Message describing the last failure on this thread ("" when none). */
+const char* gbd_last_error(void);
+
+/* Library version string. */
+const char* gbd_version(void);
+
+/* Number of beamlets gbd_trace produces for `pupil` (host only, no GPU work), or -1 for
+ * an invalid pupil.  Exact integer inside-test (2i-(N-1))^2 + (2j-(N-1))^2 <= N^2. */
+int32_t gbd_beamlet_count(const gbd_pupil* pupil);
+
+/* Synchronises `stream` and returns GBD_ETIMEOUT if any kernel of this library gave up a
+ * bounded wait on the current device since the last gbd_sync (the word is then cleared),
+ * GBD_ECUDA on a CUDA error, else GBD_OK. */
+gbd_status gbd_sync(void* stream);
+
+/* Test hook: sets the iteration limit of every device-side bounded wait on the current
+ * device (0 restores the default of about a second).  A limit of 1 makes waits that are
+ * not already satisfied give up at once, so tests can exercise GBD_ETIMEOUT. */
+gbd_status gbd_set_wait_limit(uint32_t spins);
+
+/* ---------------------------------------------------------------- gbd_trace -------
+ * Decomposes the pupil and traces every beamlet (Sec. 2.2 steps 1 and 4, Eq. gauss_prop,
+ * Eq. OF).  For each grid centre r_j inside the pupil, in row-major grid order:
+ *   w0 = overlap_factor * D / (2N),  a_j = s^2 / (pi w0^2),  P1 = -i lambda/(pi w0^2) I;
+ *   chief ray (r_j, 0); waist rays (r_j + h e_x|e_y, 0) with h = waist_ratio * w0;
+ *   divergence rays (r_j, a e_x|e_y) with a = waist_ratio * lambda / (pi w0);
+ *   each ray: plate (path += W, slope += grad W), lens (path -= r^2/2f, slope -= r/f),
+ *   distance d (r += d slope, path += d |slope|^2 / 2);
+ *   A, C columns = (waist ray - chief) / h,  B, D columns = (divergence ray - chief) / a;
+ *   P2 = (C + D P1)(A + B P1)^-1, amp = a_j / sqrtdet(A + B P1) with sqrtdet the product
+ *   of the principal square roots of the eigenvalues of A + B P1.
+ * out: device array of `capacity` records; gbd_beamlet_count(pupil) of them are written.
+ * Errors: GBD_EINVAL for non-finite / non-positive wavelength, distance or diameter,
+ * overlap_factor or waist_ratio <= 0, bad Noll indices; GBD_ENOMEM if capacity is too
+ * small.  FP64 throughout. */
+gbd_status gbd_trace(const gbd_system* system, const gbd_pupil* pupil, double overlap_factor,
+                     double waist_ratio, gbd_beamlet* out, int32_t capacity, void* stream);
+
+/* ---------------------------------------------------------------- gbd_field -------
+ * Coherent sum over beamlets of each beamlet's field on every detector pixel (Eq.
+ * sum_gaussian, Eq. collins_factored with the chief-ray slope term, Eqs. ab_prop/cd_prop):
+ *   E(s) = sum_j amp_j exp(-z tr(P)/2 - ik [path + z (1 - |theta|^2/2) + theta.delta
+ *                                            + w^T P w / 2]),
+ *   delta = X_xy(s) - rho_c,  z = X_z(s) - d,  w = delta - z theta,
+ * i.e. each beamlet propagated paraxially by the pixel's axial offset z and expanded to
+ * second order in s (exact for an untilted plane, z = 0).
+ * precision GBD_PREC_F64: FP64 throughout, field_out is complex128 [ny][nx].
+ * precision GBD_PREC_MIXED: per-beamlet projection in FP64 (constant phase reduced mod
+ *   one turn), per-pixel quadratic form, exp2/sin/cos on the MUFU pipe and the sum in
+ *   FP32 chunks combined with compensated (TwoSum) accumulation; field_out is complex64.
+ * workspace: device scratch of at least gbd_field_workspace_bytes(...) bytes, 256-byte
+ *   aligned.  Contents on entry are ignored.
+ * n_beamlets may be 0 (the field is then zero).
+ * Errors: GBD_EINVAL (bad detector, precision, null pointers, misaligned workspace),
+ * GBD_ENOMEM (workspace too small). */
+size_t gbd_field_workspace_bytes(int32_t n_beamlets, const gbd_detector* detector,
+                                 int32_t precision);
+gbd_status gbd_field(const gbd_beamlet* beamlets, int32_t n_beamlets, double wavelength,
+                     const gbd_detector* detector, int32_t precision, void* workspace,
+                     size_t workspace_bytes, void* field_out, void* stream);
+
+/* Per-beamlet projection alone (the first half of gbd_field), for inspection: writes the
+ * quadratic-form record of every beamlet to `coeffs` (device).
+ *   MIXED: 16 floats per beamlet in the tiled layout gbd_field uses
+ *          [tile = b / 64][field f = 0..3][b % 64][4 floats];
+ *          values (i0, j0, a0, p0 | a1u, p1u, a1v, p1v | auu, puu, auv, puv | avv, pvv, 0, 0)
+ *          with ln E_j(i, j) / ln 2 = a0 + a1u tu + a1v tv + auu tu^2 + auv tu tv + avv tv^2
+ *          and phase / 2 pi = p0 + ... likewise, tu = i - i0, tv = j - j0 (pixel units),
+ *          excluding the common carrier exp(-ik z(s)).
+ *   F64:   16 doubles per beamlet [tile][field f = 0..7][b % 64][2 doubles], same order.
+ * coeffs must hold gbd_project_bytes(n, precision) bytes. */
+size_t gbd_project_bytes(int32_t n_beamlets, int32_t precision);
+gbd_status gbd_project(const gbd_beamlet* beamlets, int32_t n_beamlets, double wavelength,
+                       const gbd_detector* detector, int32_t precision, void* coeffs,
+                       void* stream);
+
+/* ---------------------------------------------------------------- tuning ----------
+ * Launch shape of the field kernels: pixels per thread (rows x cols), beamlet splits.
+ * gbd_field picks a shape from a built-in heuristic unless one was set for the current
+ * device with gbd_field_set_shape; gbd_autotune_field times the candidate shapes on the
+ * given problem (synchronously, with CUDA events) and keeps the fastest. */
+typedef struct {
+    int32_t rows_per_thread;   /* mixed: 1x4, 2x2, 2x4, 4x2; F64: 1x2, 2x2    */
+    int32_t cols_per_thread;   /* (rows x cols)                               */
+    int32_t splits;            /* beamlet splits (0 = heuristic)             */
+    float   ms;                /* measured time of the shape (autotune)      */
+} gbd_shape;
+
+gbd_status gbd_field_set_shape(int32_t precision, const gbd_shape* shape);
+gbd_status gbd_field_get_shape(int32_t precision, int32_t n_beamlets,
+                               const gbd_detector* detector, gbd_shape* out);
+gbd_status gbd_autotune_field(const gbd_beamlet* beamlets, int32_t n_beamlets,
+                              double wavelength, const gbd_detector* detector,
+                              int32_t precision, void* workspace, size_t workspace_bytes,
+                              void* field_out, void* stream, gbd_shape* best);
+
+/* ---------------------------------------------------------------- host PSF --------
+ * Trace + field + copy to the host in one call, for callers that want the field in host
+ * memory: workspace (device, 256-byte aligned, >= gbd_psf_workspace_bytes) holds the
+ * beamlet table, the device field and the field scratch; host_field_out (complex64 or
+ * complex128 [ny][nx], pinned for a truly asynchronous copy) is valid after gbd_sync. */
+size_t gbd_psf_workspace_bytes(const gbd_pupil* pupil, const gbd_detector* detector,
+                               int32_t precision);
+gbd_status gbd_psf(const gbd_system* system, const gbd_pupil* pupil, double overlap_factor,
+                   double waist_ratio, const gbd_detector* detector, int32_t precision,
+                   void* workspace, size_t workspace_bytes, void* host_field_out, void* stream);
+
+/* ---------------------------------------------------------------- timing ----------
+ * Measurement hooks.  While enabled, every launch of the per-beamlet projection, the
+ * field kernels and the split reduction is bracketed by CUDA events on its stream.
+ * gbd_timing_read synchronises those events, returns per kind the summed milliseconds and
+ * launch counts (index 0 mixed field kernel, 1 FP64 field kernel, 2 projection,
+ * 3 reduction; arrays of 4) and forgets them. */
+gbd_status gbd_timing_enable(int32_t on);
+gbd_status gbd_timing_read(double* total_ms, int64_t* launches);
+
+/* ---------------------------------------------------------------- probes ----------
+ * Throughput microbenchmarks of the pipes the field kernels are bound by, on the current
+ * device (synchronous): MUFU ex2 / sin / cos results per second, FP32 FMA per second and
+ * FP64 FMA per second.  out[5] = {ex2, sin, cos, ffma, dfma} in operations/s. */
+gbd_status gbd_probe_peaks(double* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBD_H */

@@ -1,0 +1,427 @@
+// Per-(beamlet, pixel) evaluation and coherent sum (Eq. sum_gaussian evaluated with the
+// plane form of Eq. collins_factored): the hot path.
+//
+// A CTA owns a block of pixels and a contiguous range of beamlet tiles (a "split").  The
+// projected beamlet records are streamed through shared memory in 64-beamlet tiles by
+// the TMA bulk-copy engine (4-stage mbarrier pipeline, one elected producer thread); each
+// thread keeps RB x CB pixels in registers and evaluates every beamlet of the tile on
+// them.  Splits write FP64 partial fields, summed in a fixed order by a second kernel that
+// also applies the per-pixel carrier of a tilted plane.
+//
+// Mixed path, per (beamlet, pixel): 4 FFMA for the quadratic form (row terms shared across
+// the thread's columns), 3 FADD + 1 FMUL for the exact range reduction of the phase (in
+// turns) and its scaling to radians, ex2 / sin / cos on the MUFU pipe, 2 FFMA to
+// accumulate.  The sum runs in FP32 over each 64-beamlet tile and is folded into a
+// (hi, lo) pair with TwoSum between tiles.
+#include <math.h>
+
+#include "gbd_internal.cuh"
+
+namespace {
+
+__device__ unsigned int g_field_status = 0;
+
+constexpr int kStages = 4;
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+
+__device__ __forceinline__ void record_timeout() { atomicOr(&g_field_status, gbd::kStatusTimeout); }
+
+// After a failed wait: the producer waits (bounded) for the bulk copies it issued that
+// nobody consumed, so no copy lands in shared memory after the CTA has exited.
+// The drain uses at least the default limit even when the wait limit was lowered, since
+// copies complete within microseconds and must not outlive the CTA.
+__device__ void drain(uint64_t* full, int consumed, int issued, uint32_t spins) {
+    const uint32_t lim = spins > gbd::kDefaultWaitSpins ? spins : gbd::kDefaultWaitSpins;
+    for (int k = consumed; k < issued; ++k)
+        gbd::mbar_wait_bounded(&full[k % kStages], (k / kStages) & 1, lim);
+}
+
+// Warp-uniform bounded wait: every lane polls and the warp leaves together, either when
+// all lanes see the phase complete or after `spins` polls.  A completed phase stays
+// visible until this warp releases the stage, so the vote cannot flip back.
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, uint32_t spins) {
+    for (uint32_t it = 0; it < spins; ++it) {
+        const bool d = gbd::mbar_try_wait(bar, parity);
+        if (__all_sync(0xffffffffu, d)) return true;
+    }
+    return false;
+}
+
+// Stream of `nt` tiles of `bytes` bytes each from global memory through kStages shared
+// buffers.  Thread 0 is the producer; every warp consumes every tile.
+template <typename T, int kElems>
+struct TileStream {
+    T (*stage)[kElems];
+    uint64_t* full;
+    uint64_t* empty;
+    const T* src;
+    int nt;
+    int issued;
+    uint32_t bytes;
+
+    __device__ void start(int tid) {
+        if (tid == 0) {
+            for (int s = 0; s < kStages; ++s) {
+                gbd::mbar_init(&full[s], 1);
+                gbd::mbar_init(&empty[s], kWarps);
+            }
+            gbd::mbar_fence_init();
+        }
+        __syncthreads();
+        issued = 0;
+        for (; issued < kStages && issued < nt; ++issued)
+            if (tid == 0) {
+                gbd::mbar_arrive_expect_tx(&full[issued], bytes);
+                gbd::bulk_copy_g2s(stage[issued], src + (size_t)issued * kElems, bytes,
+                                   &full[issued]);
+            }
+    }
+    // Wait until tile k is in shared memory (warp-uniform result).
+    __device__ bool acquire(int k, uint32_t spins) {
+        return warp_wait(&full[k % kStages], (k / kStages) & 1, spins);
+    }
+    // This warp is done with tile k; warp 0 refills the stage with tile k + kStages once
+    // every warp has released it.  Warp-uniform result.
+    __device__ bool release(int k, int lane, int warp, uint32_t spins) {
+        const int s = k % kStages;
+        __syncwarp();
+        if (lane == 0) gbd::mbar_arrive(&empty[s]);
+        if (warp != 0 || k + kStages >= nt) return true;
+        bool good = true;
+        if (lane == 0) {
+            good = gbd::mbar_wait_bounded(&empty[s], (k / kStages) & 1, spins);
+            if (good) {
+                gbd::mbar_arrive_expect_tx(&full[s], bytes);
+                gbd::bulk_copy_g2s(stage[s], src + (size_t)(k + kStages) * kElems, bytes, &full[s]);
+            }
+        }
+        good = __shfl_sync(0xffffffffu, good, 0);
+        if (good) ++issued;
+        return good;
+    }
+};
+
+template <int RB, int CB>
+__global__ void __launch_bounds__(kThreads, 2)
+    field_mixed_kernel(const float4* __restrict__ coef, int n_tiles, int tiles_per_split, int nx,
+                       int ny, double2* __restrict__ partial, uint32_t spins) {
+    constexpr int kTileF4 = gbd::kMixedFields * gbd::kTile;
+    __shared__ __align__(128) float4 stage[kStages][kTileF4];
+    __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int t0 = blockIdx.z * tiles_per_split;
+    TileStream<float4, kTileF4> ts{stage, full, empty, coef + (size_t)t0 * kTileF4,
+                                   min(n_tiles - t0, tiles_per_split), 0, gbd::kMixedTileBytes};
+    ts.start(tid);
+
+    const int col0 = blockIdx.x * (32 * CB) + lane;
+    const int row0 = blockIdx.y * (8 * RB) + warp;
+    float colf[CB], rowf[RB];
+#pragma unroll
+    for (int c = 0; c < CB; ++c) colf[c] = (float)(col0 + 32 * c);
+#pragma unroll
+    for (int r = 0; r < RB; ++r) rowf[r] = (float)(row0 + 8 * r);
+
+    float2 acc[RB][CB], hi[RB][CB], lo[RB][CB];
+#pragma unroll
+    for (int r = 0; r < RB; ++r)
+#pragma unroll
+        for (int c = 0; c < CB; ++c) acc[r][c] = hi[r][c] = lo[r][c] = make_float2(0.f, 0.f);
+
+    const float kTwoPi = 6.28318530717958647692f;
+    int k = 0;
+    bool ok = true;
+    for (; k < ts.nt; ++k) {
+        if (!ts.acquire(k, spins)) {
+            ok = false;
+            break;
+        }
+        const float4* st = stage[k % kStages];
+#pragma unroll 1
+        for (int b = 0; b < gbd::kTile; ++b) {
+            // (i0, j0, a0, p0) (a1u, p1u, a1v, p1v) (auu, puu, auv, puv) (avv, pvv, -, -)
+            const float4 q0 = st[b];
+            const float4 q1 = st[gbd::kTile + b];
+            const float4 q2 = st[2 * gbd::kTile + b];
+            const float4 q3 = st[3 * gbd::kTile + b];
+            float tu[CB];
+#pragma unroll
+            for (int c = 0; c < CB; ++c) tu[c] = colf[c] - q0.x;
+#pragma unroll
+            for (int r = 0; r < RB; ++r) {
+                const float tv = rowf[r] - q0.y;
+                const float ra = fmaf(tv, fmaf(q3.x, tv, q1.z), q0.z);
+                const float rp = fmaf(tv, fmaf(q3.y, tv, q1.w), q0.w);
+                const float sa = fmaf(q2.z, tv, q1.x);
+                const float sp = fmaf(q2.w, tv, q1.y);
+#pragma unroll
+                for (int c = 0; c < CB; ++c) {
+                    const float ea = fmaf(tu[c], fmaf(q2.x, tu[c], sa), ra);
+                    const float ep = fmaf(tu[c], fmaf(q2.y, tu[c], sp), rp);
+                    const float amp = gbd::mufu_ex2(ea);
+                    const float x = gbd::frac_turns(ep) * kTwoPi;
+                    acc[r][c].x = fmaf(amp, gbd::mufu_cos(x), acc[r][c].x);
+                    acc[r][c].y = fmaf(amp, gbd::mufu_sin(x), acc[r][c].y);
+                }
+            }
+        }
+        // fold this tile's FP32 sums into the compensated (hi, lo) pairs
+#pragma unroll
+        for (int r = 0; r < RB; ++r)
+#pragma unroll
+            for (int c = 0; c < CB; ++c) {
+                float sx, ex, sy, ey;
+                gbd::two_sum(hi[r][c].x, acc[r][c].x, sx, ex);
+                gbd::two_sum(hi[r][c].y, acc[r][c].y, sy, ey);
+                hi[r][c] = make_float2(sx, sy);
+                lo[r][c].x += ex;
+                lo[r][c].y += ey;
+                acc[r][c] = make_float2(0.f, 0.f);
+            }
+        if (!ts.release(k, lane, warp, spins)) {
+            ok = false;
+            ++k;
+            break;
+        }
+    }
+    if (!ok) {
+        record_timeout();
+        if (tid == 0) drain(full, k, ts.issued, spins);
+        return;
+    }
+    const size_t npix = (size_t)nx * ny;
+    double2* out = partial + (size_t)blockIdx.z * npix;
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+        const int row = row0 + 8 * r;
+        if (row >= ny) continue;
+#pragma unroll
+        for (int c = 0; c < CB; ++c) {
+            const int col = col0 + 32 * c;
+            if (col >= nx) continue;
+            out[(size_t)row * nx + col] = make_double2((double)hi[r][c].x + (double)lo[r][c].x,
+                                                       (double)hi[r][c].y + (double)lo[r][c].y);
+        }
+    }
+}
+
+template <int RB, int CB>
+__global__ void __launch_bounds__(kThreads)
+    field_f64_kernel(const double2* __restrict__ coef, int n_tiles, int tiles_per_split, int nx,
+                     int ny, double2* __restrict__ partial, uint32_t spins) {
+    constexpr int kTileD2 = gbd::kF64Fields * gbd::kTile;
+    extern __shared__ __align__(128) double2 dyn[];
+    __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int t0 = blockIdx.z * tiles_per_split;
+    TileStream<double2, kTileD2> ts{reinterpret_cast<double2(*)[kTileD2]>(dyn), full, empty,
+                                    coef + (size_t)t0 * kTileD2,
+                                    min(n_tiles - t0, tiles_per_split), 0, gbd::kF64TileBytes};
+    ts.start(tid);
+
+    const int col0 = blockIdx.x * (32 * CB) + lane;
+    const int row0 = blockIdx.y * (8 * RB) + warp;
+    double acc_re[RB][CB], acc_im[RB][CB];
+#pragma unroll
+    for (int r = 0; r < RB; ++r)
+#pragma unroll
+        for (int c = 0; c < CB; ++c) acc_re[r][c] = acc_im[r][c] = 0.0;
+
+    int k = 0;
+    bool ok = true;
+    for (; k < ts.nt; ++k) {
+        if (!ts.acquire(k, spins)) {
+            ok = false;
+            break;
+        }
+        const double2* st = ts.stage[k % kStages];
+#pragma unroll 1
+        for (int b = 0; b < gbd::kTile; ++b) {
+            // (i0, j0) (a0, p0) (a1u, p1u) (a1v, p1v) (auu, puu) (auv, puv) (avv, pvv)
+            const double2 ij = st[b];
+            const double2 c0 = st[gbd::kTile + b];
+            const double2 cu = st[2 * gbd::kTile + b];
+            const double2 cv = st[3 * gbd::kTile + b];
+            const double2 cuu = st[4 * gbd::kTile + b];
+            const double2 cuv = st[5 * gbd::kTile + b];
+            const double2 cvv = st[6 * gbd::kTile + b];
+#pragma unroll
+            for (int r = 0; r < RB; ++r) {
+                const double tv = (double)(row0 + 8 * r) - ij.y;
+                const double ra = fma(tv, fma(cvv.x, tv, cv.x), c0.x);
+                const double rp = fma(tv, fma(cvv.y, tv, cv.y), c0.y);
+                const double sa = fma(cuv.x, tv, cu.x);
+                const double sp = fma(cuv.y, tv, cu.y);
+#pragma unroll
+                for (int c = 0; c < CB; ++c) {
+                    const double tu = (double)(col0 + 32 * c) - ij.x;
+                    const double ea = fma(tu, fma(cuu.x, tu, sa), ra);
+                    const double ep = fma(tu, fma(cuu.y, tu, sp), rp);
+                    const double amp = exp2(ea);
+                    double sn, cs;
+                    sincospi(2.0 * (ep - rint(ep)), &sn, &cs);
+                    acc_re[r][c] = fma(amp, cs, acc_re[r][c]);
+                    acc_im[r][c] = fma(amp, sn, acc_im[r][c]);
+                }
+            }
+        }
+        if (!ts.release(k, lane, warp, spins)) {
+            ok = false;
+            ++k;
+            break;
+        }
+    }
+    if (!ok) {
+        record_timeout();
+        if (tid == 0) drain(full, k, ts.issued, spins);
+        return;
+    }
+    const size_t npix = (size_t)nx * ny;
+    double2* out = partial + (size_t)blockIdx.z * npix;
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+        const int row = row0 + 8 * r;
+        if (row >= ny) continue;
+#pragma unroll
+        for (int c = 0; c < CB; ++c) {
+            const int col = col0 + 32 * c;
+            if (col >= nx) continue;
+            out[(size_t)row * nx + col] = make_double2(acc_re[r][c], acc_im[r][c]);
+        }
+    }
+}
+
+// Fixed-order FP64 sum of the split partials, times the carrier exp(-ik z(s)) of each
+// pixel (z = n.s is the axial offset of the tilted plane), written as complex64/128.
+template <bool F64>
+__global__ void __launch_bounds__(256) field_reduce_kernel(const double2* __restrict__ partial,
+                                                           int splits, int nx, int ny, double cx,
+                                                           double cy, void* __restrict__ out) {
+    const size_t npix = (size_t)nx * ny;
+    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npix) return;
+    double re = 0.0, im = 0.0;
+    for (int s = 0; s < splits; ++s) {
+        const double2 v = partial[(size_t)s * npix + p];
+        re += v.x;
+        im += v.y;
+    }
+    if (cx != 0.0 || cy != 0.0) {
+        const int i = (int)(p % nx), j = (int)(p / nx);
+        const double turns = cx * (i - nx / 2) + cy * (j - ny / 2);
+        double sn, cs;
+        sincospi(2.0 * (turns - rint(turns)), &sn, &cs);
+        const double r2 = re * cs - im * sn;
+        im = re * sn + im * cs;
+        re = r2;
+    }
+    if (F64)
+        static_cast<double2*>(out)[p] = make_double2(re, im);
+    else
+        static_cast<float2*>(out)[p] = make_float2((float)re, (float)im);
+}
+
+template <int RB, int CB>
+cudaError_t launch_mixed(const void* coeffs, int n_tiles, const gbd_project_params& p,
+                         const gbd_field_launch& L, double2* partial, uint32_t spins,
+                         cudaStream_t s) {
+    dim3 grid((p.nx + 32 * CB - 1) / (32 * CB), (p.ny + 8 * RB - 1) / (8 * RB), L.splits);
+    field_mixed_kernel<RB, CB><<<grid, kThreads, 0, s>>>(static_cast<const float4*>(coeffs),
+                                                         n_tiles, L.tiles_per_split, p.nx, p.ny,
+                                                         partial, spins);
+    return cudaGetLastError();
+}
+
+template <int RB, int CB>
+cudaError_t launch_f64(const void* coeffs, int n_tiles, const gbd_project_params& p,
+                       const gbd_field_launch& L, double2* partial, uint32_t spins, cudaStream_t s) {
+    const size_t smem = (size_t)kStages * gbd::kF64TileBytes;
+    cudaError_t e = cudaFuncSetAttribute(field_f64_kernel<RB, CB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((p.nx + 32 * CB - 1) / (32 * CB), (p.ny + 8 * RB - 1) / (8 * RB), L.splits);
+    field_f64_kernel<RB, CB><<<grid, kThreads, smem, s>>>(static_cast<const double2*>(coeffs),
+                                                          n_tiles, L.tiles_per_split, p.nx, p.ny,
+                                                          partial, spins);
+    return cudaGetLastError();
+}
+
+typedef cudaError_t (*launch_fn)(const void*, int, const gbd_project_params&,
+                                 const gbd_field_launch&, double2*, uint32_t, cudaStream_t);
+
+struct ShapeEntry {
+    int rb, cb;
+    launch_fn fn;
+    const void* kernel;
+};
+
+const ShapeEntry kMixedShapes[] = {
+    {1, 4, launch_mixed<1, 4>, (const void*)field_mixed_kernel<1, 4>},
+    {2, 2, launch_mixed<2, 2>, (const void*)field_mixed_kernel<2, 2>},
+    {2, 4, launch_mixed<2, 4>, (const void*)field_mixed_kernel<2, 4>},
+    {4, 2, launch_mixed<4, 2>, (const void*)field_mixed_kernel<4, 2>},
+};
+const ShapeEntry kF64Shapes[] = {
+    {1, 2, launch_f64<1, 2>, (const void*)field_f64_kernel<1, 2>},
+    {2, 2, launch_f64<2, 2>, (const void*)field_f64_kernel<2, 2>},
+};
+
+const ShapeEntry* find_shape(int precision, int rb, int cb) {
+    if (precision == GBD_PREC_MIXED) {
+        for (const auto& e : kMixedShapes)
+            if (e.rb == rb && e.cb == cb) return &e;
+    } else {
+        for (const auto& e : kF64Shapes)
+            if (e.rb == rb && e.cb == cb) return &e;
+    }
+    return nullptr;
+}
+
+}  // namespace
+
+bool gbd_field_shape_supported(int precision, int rb, int cb) {
+    return find_shape(precision, rb, cb) != nullptr;
+}
+
+int gbd_field_occupancy(int precision, int rb, int cb) {
+    const ShapeEntry* e = find_shape(precision, rb, cb);
+    if (!e) return 0;
+    int blocks = 0;
+    size_t smem = precision == GBD_PREC_MIXED ? 0 : (size_t)kStages * gbd::kF64TileBytes;
+    if (precision != GBD_PREC_MIXED)
+        cudaFuncSetAttribute(e->kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, e->kernel, kThreads, smem) !=
+        cudaSuccess)
+        return 0;
+    return blocks;
+}
+
+cudaError_t gbd_launch_field_kernel(int precision, const void* coeffs, int n_tiles,
+                                    const gbd_project_params& p, const gbd_field_launch& L,
+                                    double2* partial, uint32_t wait_spins, cudaStream_t s) {
+    const ShapeEntry* e = find_shape(precision, L.rows_per_thread, L.cols_per_thread);
+    if (!e) return cudaErrorInvalidValue;
+    return e->fn(coeffs, n_tiles, p, L, partial, wait_spins, s);
+}
+
+cudaError_t gbd_launch_field_reduce(int precision, const gbd_project_params& p, int splits,
+                                    const double2* partial, void* out, cudaStream_t s) {
+    const size_t npix = (size_t)p.nx * p.ny;
+    const double cx = -p.n[0] * p.px / p.wavelength, cy = -p.n[1] * p.py / p.wavelength;
+    const unsigned blocks = (unsigned)((npix + 255) / 256);
+    if (precision == GBD_PREC_F64)
+        field_reduce_kernel<true><<<blocks, 256, 0, s>>>(partial, splits, p.nx, p.ny, cx, cy, out);
+    else
+        field_reduce_kernel<false><<<blocks, 256, 0, s>>>(partial, splits, p.nx, p.ny, cx, cy, out);
+    return cudaGetLastError();
+}
+
+unsigned gbd_field_status_read_clear() {
+    unsigned v = 0, zero = 0;
+    if (cudaMemcpyFromSymbol(&v, g_field_status, sizeof(v)) != cudaSuccess) return 0;
+    if (v) cudaMemcpyToSymbol(g_field_status, &zero, sizeof(zero));
+    return v;
+}

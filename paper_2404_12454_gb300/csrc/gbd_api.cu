@@ -1,0 +1,604 @@
+// C ABI of the GBD library: argument validation, host-side set-up of the kernels'
+// parameters, launch-shape selection and the workspace layout.  All numerical work of
+// the method runs in the kernels of trace.cu, field.cu and sweep.cu.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "gbd.h"
+#include "gbd_internal.cuh"
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+gbd_status fail(gbd_status st, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+gbd_status cuda_fail(cudaError_t e, const char* where) {
+    return fail(GBD_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+std::mutex g_mu;
+std::map<int, uint32_t> g_wait_spins;                 // per device
+std::map<std::pair<int, int>, gbd_shape> g_shapes;     // (device, precision) -> shape
+std::map<int, int> g_sm_count;
+
+int current_device() {
+    int d = 0;
+    cudaGetDevice(&d);
+    return d;
+}
+
+uint32_t wait_spins() {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_wait_spins.find(current_device());
+    return it == g_wait_spins.end() ? gbd::kDefaultWaitSpins : it->second;
+}
+
+int sm_count() {
+    int dev = current_device();
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_sm_count.find(dev);
+    if (it != g_sm_count.end()) return it->second;
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+        n = 1;
+    g_sm_count[dev] = n;
+    return n;
+}
+
+bool finite_pos(double v) { return isfinite(v) && v > 0.0; }
+
+// ------------------------------------------------------------- kernel timing --
+// While enabled, launches of the measured kernels are bracketed by CUDA events on their
+// own stream; gbd_timing_read synchronises the events and sums the durations.
+enum { kTimeMixed = 0, kTimeF64 = 1, kTimeProject = 2, kTimeReduce = 3, kTimeKinds = 4 };
+struct TimedLaunch {
+    int kind;
+    cudaEvent_t a, b;
+};
+bool g_timing = false;
+std::vector<TimedLaunch> g_timed;
+
+struct TimingScope {
+    TimedLaunch t{-1, nullptr, nullptr};
+    cudaStream_t s;
+    TimingScope(int kind, cudaStream_t st) : s(st) {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (!g_timing) return;
+        if (cudaEventCreate(&t.a) != cudaSuccess || cudaEventCreate(&t.b) != cudaSuccess) return;
+        t.kind = kind;
+        cudaEventRecord(t.a, s);
+    }
+    ~TimingScope() {
+        if (t.kind < 0) return;
+        cudaEventRecord(t.b, s);
+        std::lock_guard<std::mutex> lk(g_mu);
+        g_timed.push_back(t);
+    }
+};
+
+// ------------------------------------------------------------------ Zernike --
+
+// Noll index -> radial order n, azimuthal order |m|, sine term?
+void noll_nm(int j, int& n, int& m, bool& is_sin) {
+    n = (int)floor((sqrt(8.0 * j - 7.0) - 1.0) / 2.0);
+    while ((n + 1) * (n + 2) / 2 < j) ++n;  // guard the floor against rounding
+    while (n > 0 && n * (n + 1) / 2 >= j) --n;
+    const int p = j - n * (n + 1) / 2;  // 1-based position inside order n
+    m = (n % 2 == 0) ? 2 * (p / 2) : 2 * ((p - 1) / 2) + 1;
+    is_sin = (m != 0) && (j % 2 == 1);
+}
+
+double binom(int a, int b) {
+    double r = 1.0;
+    for (int q = 1; q <= b; ++q) r = r * (a - b + q) / q;
+    return r;
+}
+
+double fact(int a) {
+    double r = 1.0;
+    for (int q = 2; q <= a; ++q) r *= q;
+    return r;
+}
+
+// Adds coef * Z_j(xi, eta) to the degree-ordered monomial table.
+void add_zernike(int j, double coef, double* table, int& max_deg) {
+    int n, m;
+    bool is_sin;
+    noll_nm(j, n, m, is_sin);
+    const double norm = (m == 0) ? sqrt(n + 1.0) : sqrt(2.0 * (n + 1.0));
+    for (int s = 0; s <= (n - m) / 2; ++s) {
+        const double cs = ((s & 1) ? -1.0 : 1.0) * fact(n - s) /
+                          (fact(s) * fact((n + m) / 2 - s) * fact((n - m) / 2 - s));
+        const int p = (n - m) / 2 - s;  // power of rho^2
+        for (int a = 0; a <= p; ++a) {
+            const double ca = binom(p, a);  // xi^(2a) eta^(2(p-a))
+            for (int b = 0; b <= m; ++b) {
+                // (xi + i eta)^m term: C(m,b) xi^(m-b) (i eta)^b
+                const bool odd = (b & 1) != 0;
+                if (odd != is_sin) continue;  // real part: even b; imaginary part: odd b
+                const int quarter = is_sin ? (b - 1) / 2 : b / 2;
+                const double sign = (quarter & 1) ? -1.0 : 1.0;
+                const int ex = 2 * a + (m - b), ey = 2 * (p - a) + b;
+                table[gbd::plate_index(ex, ey)] += coef * norm * cs * ca * binom(m, b) * sign;
+                max_deg = std::max(max_deg, ex + ey);
+            }
+        }
+    }
+}
+
+gbd_status check_system(const gbd_system* S) {
+    if (!S) return fail(GBD_EINVAL, "system is NULL");
+    if (!finite_pos(S->wavelength)) return fail(GBD_EINVAL, "wavelength must be finite and > 0");
+    if (!(isfinite(S->distance) && S->distance >= 0.0))
+        return fail(GBD_EINVAL, "distance must be finite and >= 0");
+    if (S->focal_length == 0.0 || isnan(S->focal_length) || S->focal_length == -INFINITY)
+        return fail(GBD_EINVAL, "focal_length must be non-zero (use +INFINITY for no lens)");
+    if (S->n_zern < 0 || S->n_zern > GBD_MAX_ZERN)
+        return fail(GBD_EINVAL, "n_zern must be in [0, %d]", GBD_MAX_ZERN);
+    if (S->n_zern > 0 && !finite_pos(S->zern_radius))
+        return fail(GBD_EINVAL, "zern_radius must be finite and > 0");
+    for (int t = 0; t < S->n_zern; ++t) {
+        if (S->noll[t] < 1 || S->noll[t] > GBD_MAX_NOLL)
+            return fail(GBD_EINVAL, "noll[%d] = %d outside [1, %d]", t, S->noll[t], GBD_MAX_NOLL);
+        if (!isfinite(S->zern_coef[t])) return fail(GBD_EINVAL, "zern_coef[%d] not finite", t);
+    }
+    return GBD_OK;
+}
+
+gbd_status check_pupil(const gbd_pupil* P) {
+    if (!P) return fail(GBD_EINVAL, "pupil is NULL");
+    if (!finite_pos(P->diameter)) return fail(GBD_EINVAL, "pupil diameter must be finite and > 0");
+    if (P->n_across < 1 || P->n_across > 4096)
+        return fail(GBD_EINVAL, "n_across must be in [1, 4096]");
+    return GBD_OK;
+}
+
+gbd_status check_detector(const gbd_detector* D) {
+    if (!D) return fail(GBD_EINVAL, "detector is NULL");
+    if (D->nx < 1 || D->ny < 1 || D->nx > 16384 || D->ny > 16384)
+        return fail(GBD_EINVAL, "detector size must be in [1, 16384] on each axis");
+    if (!finite_pos(D->pitch_x) || !finite_pos(D->pitch_y))
+        return fail(GBD_EINVAL, "pixel pitch must be finite and > 0");
+    if (!(fabs(D->rot_x) < 1.2) || !(fabs(D->rot_y) < 1.2))
+        return fail(GBD_EINVAL, "detector rotations must satisfy |rot| < 1.2 rad");
+    return GBD_OK;
+}
+
+gbd_project_params project_params(double wavelength, const gbd_detector* D) {
+    gbd_project_params p;
+    const double ca = cos(D->rot_x), sa = sin(D->rot_x), cb = cos(D->rot_y), sb = sin(D->rot_y);
+    // R = Ry(b) Rx(a); columns 0 and 1 map detector (s_x, s_y) into the lab frame
+    p.M[0] = cb;
+    p.M[1] = sb * sa;
+    p.M[2] = 0.0;
+    p.M[3] = ca;
+    p.n[0] = -sb;
+    p.n[1] = cb * sa;
+    p.wavelength = wavelength;
+    p.px = D->pitch_x;
+    p.py = D->pitch_y;
+    p.nx = D->nx;
+    p.ny = D->ny;
+    return p;
+}
+
+size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+int n_tiles_of(int n) { return (n + gbd::kTile - 1) / gbd::kTile; }
+
+size_t tile_bytes(int precision) {
+    return precision == GBD_PREC_MIXED ? gbd::kMixedTileBytes : gbd::kF64TileBytes;
+}
+
+gbd_shape default_shape(int precision) {
+    gbd_shape s;
+    s.rows_per_thread = 2;
+    s.cols_per_thread = precision == GBD_PREC_MIXED ? 4 : 2;
+    s.splits = 0;
+    s.ms = 0.f;
+    return s;
+}
+
+gbd_shape stored_shape(int precision) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_shapes.find({current_device(), precision});
+    return it == g_shapes.end() ? default_shape(precision) : it->second;
+}
+
+// Beamlet splits minimising (waves x tiles per CTA): every CTA does equal work, so the
+// time is set by how many full waves of CTAs the grid needs and how long each CTA runs.
+int heuristic_splits(int precision, int rb, int cb, int n_tiles, const gbd_detector* D) {
+    const long pix_ctas = (long)((D->nx + 32 * cb - 1) / (32 * cb)) * ((D->ny + 8 * rb - 1) / (8 * rb));
+    const int occ = std::max(1, gbd_field_occupancy(precision, rb, cb));
+    const long slots = (long)occ * sm_count();
+    int best = 1;
+    double best_cost = 1e300;
+    for (int s = 1; s <= std::min(n_tiles, 64); ++s) {
+        const int tps = (n_tiles + s - 1) / s;
+        const int s_eff = (n_tiles + tps - 1) / tps;
+        const long waves = (pix_ctas * s_eff + slots - 1) / slots;
+        const double cost = (double)waves * tps + 0.02 * s_eff;
+        if (cost < best_cost - 1e-9) {
+            best_cost = cost;
+            best = s_eff;
+        }
+    }
+    return best;
+}
+
+gbd_field_launch resolve_launch(int precision, const gbd_shape& sh, int n_tiles,
+                                const gbd_detector* D) {
+    gbd_field_launch L;
+    L.rows_per_thread = sh.rows_per_thread;
+    L.cols_per_thread = sh.cols_per_thread;
+    int s = sh.splits > 0 ? std::min(sh.splits, n_tiles)
+                          : heuristic_splits(precision, sh.rows_per_thread, sh.cols_per_thread,
+                                             n_tiles, D);
+    s = std::max(1, s);
+    L.tiles_per_split = (n_tiles + s - 1) / s;
+    L.splits = (n_tiles + L.tiles_per_split - 1) / L.tiles_per_split;
+    return L;
+}
+
+size_t workspace_for(int precision, int n, const gbd_detector* D, const gbd_field_launch& L) {
+    if (n <= 0) return 0;
+    const size_t coeff = align256((size_t)n_tiles_of(n) * tile_bytes(precision));
+    const size_t part = align256((size_t)L.splits * D->nx * D->ny * sizeof(double2));
+    return coeff + part;
+}
+
+gbd_status run_field(const gbd_beamlet* beamlets, int32_t n, double wavelength,
+                     const gbd_detector* D, int32_t precision, void* ws, size_t ws_bytes, void* out,
+                     cudaStream_t stream, const gbd_shape& sh) {
+    const gbd_project_params pp = project_params(wavelength, D);
+    const size_t npix = (size_t)D->nx * D->ny;
+    if (n == 0) {
+        const size_t elem = precision == GBD_PREC_F64 ? 16 : 8;
+        cudaError_t e = cudaMemsetAsync(out, 0, npix * elem, stream);
+        return e == cudaSuccess ? GBD_OK : cuda_fail(e, "gbd_field memset");
+    }
+    const int nt = n_tiles_of(n);
+    const gbd_field_launch L = resolve_launch(precision, sh, nt, D);
+    const size_t need = workspace_for(precision, n, D, L);
+    if (ws_bytes < need)
+        return fail(GBD_ENOMEM, "workspace of %zu bytes is smaller than the %zu needed", ws_bytes,
+                    need);
+    char* base = static_cast<char*>(ws);
+    void* coeffs = base;
+    double2* partial =
+        reinterpret_cast<double2*>(base + align256((size_t)nt * tile_bytes(precision)));
+    cudaError_t e;
+    {
+        TimingScope ts(kTimeProject, stream);
+        e = gbd_launch_project(beamlets, n, pp, precision, coeffs, stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "gbd_field projection launch");
+    {
+        TimingScope ts(precision == GBD_PREC_MIXED ? kTimeMixed : kTimeF64, stream);
+        e = gbd_launch_field_kernel(precision, coeffs, nt, pp, L, partial, wait_spins(), stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "gbd_field launch");
+    {
+        TimingScope ts(kTimeReduce, stream);
+        e = gbd_launch_field_reduce(precision, pp, L.splits, partial, out, stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "gbd_field reduce launch");
+    return GBD_OK;
+}
+
+gbd_status check_field_args(const gbd_beamlet* beamlets, int32_t n, double wavelength,
+                            const gbd_detector* D, int32_t precision, void* ws, void* out) {
+    gbd_status st = check_detector(D);
+    if (st != GBD_OK) return st;
+    if (precision != GBD_PREC_F64 && precision != GBD_PREC_MIXED)
+        return fail(GBD_EINVAL, "precision must be GBD_PREC_F64 or GBD_PREC_MIXED");
+    if (!finite_pos(wavelength)) return fail(GBD_EINVAL, "wavelength must be finite and > 0");
+    if (n < 0) return fail(GBD_EINVAL, "n_beamlets must be >= 0");
+    if (!out) return fail(GBD_EINVAL, "field_out is NULL");
+    if (n > 0 && (!beamlets || !ws)) return fail(GBD_EINVAL, "beamlets/workspace is NULL");
+    if (n > 0 && (reinterpret_cast<uintptr_t>(ws) & 255u))
+        return fail(GBD_EINVAL, "workspace must be 256-byte aligned");
+    if ((reinterpret_cast<uintptr_t>(out) & 15u) != 0)
+        return fail(GBD_EINVAL, "field_out must be 16-byte aligned");
+    return GBD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gbd_last_error(void) { return g_err; }
+
+const char* gbd_version(void) { return "gbd-gb300 0.1 (sm_103a)"; }
+
+int32_t gbd_beamlet_count(const gbd_pupil* pupil) {
+    if (check_pupil(pupil) != GBD_OK) return -1;
+    const long long N = pupil->n_across;
+    long long count = 0;
+    for (long long j = 0; j < N; ++j) {
+        const long long b = 2 * j - (N - 1);
+        const long long r2 = N * N - b * b;
+        // odd/even values a = 2i - (N-1) with a^2 <= r2
+        for (long long a = -(N - 1); a <= N - 1; a += 2)
+            if (a * a <= r2) ++count;
+    }
+    return (int32_t)count;
+}
+
+gbd_status gbd_sync(void* stream) {
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "gbd_sync");
+    unsigned st = gbd_field_status_read_clear();
+    if (st & gbd::kStatusTimeout) return fail(GBD_ETIMEOUT, "a device wait gave up (timeout)");
+    return GBD_OK;
+}
+
+gbd_status gbd_set_wait_limit(uint32_t spins) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_wait_spins[current_device()] = spins == 0 ? gbd::kDefaultWaitSpins : spins;
+    return GBD_OK;
+}
+
+gbd_status gbd_trace(const gbd_system* system, const gbd_pupil* pupil, double overlap_factor,
+                     double waist_ratio, gbd_beamlet* out, int32_t capacity, void* stream) {
+    gbd_status st = check_system(system);
+    if (st != GBD_OK) return st;
+    if ((st = check_pupil(pupil)) != GBD_OK) return st;
+    if (!finite_pos(overlap_factor)) return fail(GBD_EINVAL, "overlap_factor must be > 0");
+    if (!finite_pos(waist_ratio)) return fail(GBD_EINVAL, "waist_ratio must be > 0");
+    const int32_t n = gbd_beamlet_count(pupil);
+    if (capacity < n) return fail(GBD_ENOMEM, "capacity %d < %d beamlets", capacity, n);
+    if (n > 0 && !out) return fail(GBD_EINVAL, "out is NULL");
+    if (reinterpret_cast<uintptr_t>(out) & 15u) return fail(GBD_EINVAL, "out must be 16-byte aligned");
+    gbd_trace_params p;
+    memset(&p, 0, sizeof(p));
+    p.wavelength = system->wavelength;
+    p.inv_f = isinf(system->focal_length) ? 0.0 : 1.0 / system->focal_length;
+    p.d = system->distance;
+    p.zern_radius = system->n_zern > 0 ? system->zern_radius : 1.0;
+    p.diameter = pupil->diameter;
+    p.overlap_factor = overlap_factor;
+    p.waist_ratio = waist_ratio;
+    p.n_across = pupil->n_across;
+    p.zdeg = -1;
+    int deg = -1;
+    for (int t = 0; t < system->n_zern; ++t)
+        add_zernike(system->noll[t], system->zern_coef[t], p.zpoly, deg);
+    p.zdeg = system->n_zern > 0 ? deg : -1;
+    cudaError_t e = gbd_launch_trace(p, 1, pupil->n_across, nullptr, out,
+                                     static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "gbd_trace launch");
+    return GBD_OK;
+}
+
+size_t gbd_project_bytes(int32_t n_beamlets, int32_t precision) {
+    if (n_beamlets <= 0) return 0;
+    return (size_t)n_tiles_of(n_beamlets) *
+           (precision == GBD_PREC_MIXED ? gbd::kMixedTileBytes : gbd::kF64TileBytes);
+}
+
+gbd_status gbd_project(const gbd_beamlet* beamlets, int32_t n_beamlets, double wavelength,
+                       const gbd_detector* detector, int32_t precision, void* coeffs,
+                       void* stream) {
+    gbd_status st = check_field_args(beamlets, n_beamlets, wavelength, detector, precision,
+                                     coeffs, coeffs ? coeffs : (void*)16);
+    if (st != GBD_OK) return st;
+    if (n_beamlets == 0) return GBD_OK;
+    cudaError_t e = gbd_launch_project(beamlets, n_beamlets, project_params(wavelength, detector),
+                                       precision, coeffs, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? GBD_OK : cuda_fail(e, "gbd_project launch");
+}
+
+size_t gbd_field_workspace_bytes(int32_t n_beamlets, const gbd_detector* detector,
+                                 int32_t precision) {
+    if (check_detector(detector) != GBD_OK || n_beamlets <= 0) return 0;
+    if (precision != GBD_PREC_F64 && precision != GBD_PREC_MIXED) return 0;
+    const gbd_field_launch L =
+        resolve_launch(precision, stored_shape(precision), n_tiles_of(n_beamlets), detector);
+    return workspace_for(precision, n_beamlets, detector, L);
+}
+
+gbd_status gbd_field(const gbd_beamlet* beamlets, int32_t n_beamlets, double wavelength,
+                     const gbd_detector* detector, int32_t precision, void* workspace,
+                     size_t workspace_bytes, void* field_out, void* stream) {
+    gbd_status st = check_field_args(beamlets, n_beamlets, wavelength, detector, precision,
+                                     workspace, field_out);
+    if (st != GBD_OK) return st;
+    return run_field(beamlets, n_beamlets, wavelength, detector, precision, workspace,
+                     workspace_bytes, field_out, static_cast<cudaStream_t>(stream),
+                     stored_shape(precision));
+}
+
+gbd_status gbd_field_set_shape(int32_t precision, const gbd_shape* shape) {
+    if (precision != GBD_PREC_F64 && precision != GBD_PREC_MIXED)
+        return fail(GBD_EINVAL, "precision must be GBD_PREC_F64 or GBD_PREC_MIXED");
+    gbd_shape s = shape ? *shape : default_shape(precision);
+    if (!gbd_field_shape_supported(precision, s.rows_per_thread, s.cols_per_thread))
+        return fail(GBD_EINVAL, "unsupported shape %dx%d", s.rows_per_thread, s.cols_per_thread);
+    if (s.splits < 0 || s.splits > 1024) return fail(GBD_EINVAL, "splits must be in [0, 1024]");
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_shapes[{current_device(), precision}] = s;
+    return GBD_OK;
+}
+
+gbd_status gbd_field_get_shape(int32_t precision, int32_t n_beamlets, const gbd_detector* detector,
+                               gbd_shape* out) {
+    if (!out) return fail(GBD_EINVAL, "out is NULL");
+    gbd_status st = check_detector(detector);
+    if (st != GBD_OK) return st;
+    if (precision != GBD_PREC_F64 && precision != GBD_PREC_MIXED)
+        return fail(GBD_EINVAL, "precision must be GBD_PREC_F64 or GBD_PREC_MIXED");
+    gbd_shape s = stored_shape(precision);
+    if (n_beamlets > 0) {
+        gbd_field_launch L = resolve_launch(precision, s, n_tiles_of(n_beamlets), detector);
+        s.splits = L.splits;
+    }
+    *out = s;
+    return GBD_OK;
+}
+
+gbd_status gbd_autotune_field(const gbd_beamlet* beamlets, int32_t n_beamlets, double wavelength,
+                              const gbd_detector* detector, int32_t precision, void* workspace,
+                              size_t workspace_bytes, void* field_out, void* stream,
+                              gbd_shape* best) {
+    gbd_status st = check_field_args(beamlets, n_beamlets, wavelength, detector, precision,
+                                     workspace, field_out);
+    if (st != GBD_OK) return st;
+    if (n_beamlets == 0) return fail(GBD_EINVAL, "autotune needs at least one beamlet");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    static const int kMixed[][2] = {{1, 4}, {2, 2}, {2, 4}, {4, 2}};
+    static const int kF64[][2] = {{1, 2}, {2, 2}};
+    std::vector<std::pair<int, int>> shapes;
+    if (precision == GBD_PREC_MIXED)
+        for (auto& v : kMixed) shapes.push_back({v[0], v[1]});
+    else
+        for (auto& v : kF64) shapes.push_back({v[0], v[1]});
+    const int nt = n_tiles_of(n_beamlets);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return cuda_fail(cudaGetLastError(), "autotune events");
+    gbd_shape win{0, 0, 0, 1e30f};
+    for (auto& rc : shapes) {
+        gbd_shape cand{rc.first, rc.second, 0, 0.f};
+        const int base = resolve_launch(precision, cand, nt, detector).splits;
+        std::vector<int> splits = {base, std::max(1, base / 2), std::min(nt, base * 2)};
+        std::sort(splits.begin(), splits.end());
+        splits.erase(std::unique(splits.begin(), splits.end()), splits.end());
+        for (int sp : splits) {
+            cand.splits = sp;
+            const gbd_field_launch L = resolve_launch(precision, cand, nt, detector);
+            if (workspace_for(precision, n_beamlets, detector, L) > workspace_bytes) continue;
+            float best_ms = 1e30f;
+            for (int rep = 0; rep < 3; ++rep) {
+                cudaEventRecord(e0, s);
+                st = run_field(beamlets, n_beamlets, wavelength, detector, precision, workspace,
+                               workspace_bytes, field_out, s, cand);
+                cudaEventRecord(e1, s);
+                if (st != GBD_OK) break;
+                if (cudaEventSynchronize(e1) != cudaSuccess) break;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) best_ms = std::min(best_ms, ms);
+            }
+            if (st != GBD_OK) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return st;
+            }
+            if (best_ms < win.ms) {
+                win = cand;
+                win.ms = best_ms;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (win.rows_per_thread == 0) return fail(GBD_ENOMEM, "no candidate shape fits the workspace");
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        g_shapes[{current_device(), precision}] = win;
+    }
+    if (best) *best = win;
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GBD_OK : cuda_fail(e, "autotune");
+}
+
+gbd_status gbd_timing_enable(int32_t on) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_timing = on != 0;
+    return GBD_OK;
+}
+
+gbd_status gbd_timing_read(double* total_ms, int64_t* launches) {
+    if (!total_ms || !launches) return fail(GBD_EINVAL, "outputs are NULL");
+    std::vector<TimedLaunch> v;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        v.swap(g_timed);
+    }
+    for (int k = 0; k < kTimeKinds; ++k) {
+        total_ms[k] = 0.0;
+        launches[k] = 0;
+    }
+    cudaError_t err = cudaSuccess;
+    for (auto& t : v) {
+        cudaError_t e = cudaEventSynchronize(t.b);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t.a, t.b);
+        if (e == cudaSuccess) {
+            total_ms[t.kind] += ms;
+            launches[t.kind] += 1;
+        } else {
+            err = e;
+        }
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    return err == cudaSuccess ? GBD_OK : cuda_fail(err, "gbd_timing_read");
+}
+
+size_t gbd_psf_workspace_bytes(const gbd_pupil* pupil, const gbd_detector* detector,
+                               int32_t precision) {
+    if (check_pupil(pupil) != GBD_OK || check_detector(detector) != GBD_OK) return 0;
+    if (precision != GBD_PREC_F64 && precision != GBD_PREC_MIXED) return 0;
+    const int32_t n = gbd_beamlet_count(pupil);
+    const size_t elem = precision == GBD_PREC_F64 ? 16 : 8;
+    return align256((size_t)std::max(n, 1) * sizeof(gbd_beamlet)) +
+           align256((size_t)detector->nx * detector->ny * elem) +
+           gbd_field_workspace_bytes(n, detector, precision);
+}
+
+gbd_status gbd_psf(const gbd_system* system, const gbd_pupil* pupil, double overlap_factor,
+                   double waist_ratio, const gbd_detector* detector, int32_t precision,
+                   void* workspace, size_t workspace_bytes, void* host_field_out, void* stream) {
+    gbd_status st = check_detector(detector);
+    if (st != GBD_OK) return st;
+    if ((st = check_pupil(pupil)) != GBD_OK) return st;
+    if (precision != GBD_PREC_F64 && precision != GBD_PREC_MIXED)
+        return fail(GBD_EINVAL, "precision must be GBD_PREC_F64 or GBD_PREC_MIXED");
+    if (!host_field_out || !workspace) return fail(GBD_EINVAL, "NULL buffer");
+    if (reinterpret_cast<uintptr_t>(workspace) & 255u)
+        return fail(GBD_EINVAL, "workspace must be 256-byte aligned");
+    const size_t need = gbd_psf_workspace_bytes(pupil, detector, precision);
+    if (workspace_bytes < need)
+        return fail(GBD_ENOMEM, "workspace of %zu bytes is smaller than the %zu needed",
+                    workspace_bytes, need);
+    const int32_t n = gbd_beamlet_count(pupil);
+    const size_t elem = precision == GBD_PREC_F64 ? 16 : 8;
+    const size_t field_bytes = (size_t)detector->nx * detector->ny * elem;
+    char* base = static_cast<char*>(workspace);
+    gbd_beamlet* beamlets = reinterpret_cast<gbd_beamlet*>(base);
+    char* dfield = base + align256((size_t)std::max(n, 1) * sizeof(gbd_beamlet));
+    char* fws = dfield + align256(field_bytes);
+    st = gbd_trace(system, pupil, overlap_factor, waist_ratio, beamlets, n, stream);
+    if (st != GBD_OK) return st;
+    st = gbd_field(beamlets, n, system->wavelength, detector, precision, fws,
+                   workspace_bytes - (size_t)(fws - base), dfield, stream);
+    if (st != GBD_OK) return st;
+    cudaError_t e = cudaMemcpyAsync(host_field_out, dfield, field_bytes, cudaMemcpyDeviceToHost,
+                                    static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? GBD_OK : cuda_fail(e, "gbd_psf copy to host");
+}
+
+gbd_status gbd_probe_peaks(double* out) {
+    if (!out) return fail(GBD_EINVAL, "out is NULL");
+    cudaError_t e = gbd_run_probes(out);
+    return e == cudaSuccess ? GBD_OK : cuda_fail(e, "gbd_probe_peaks");
+}
+
+}  // extern "C"

@@ -1,0 +1,204 @@
+// Internal device helpers of the GBD library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gbd.h"
+
+namespace gbd {
+
+// Beamlets per shared-memory tile of the field kernels.  A mixed-precision tile is
+// 64 x 16 floats = 4 KB, an FP64 tile 64 x 16 doubles = 8 KB; both are one contiguous
+// bulk copy.
+constexpr int kTile = 64;
+constexpr int kMixedFields = 4;   // float4 fields per beamlet
+constexpr int kF64Fields = 8;     // double2 fields per beamlet
+constexpr uint32_t kMixedTileBytes = kTile * kMixedFields * 16;
+constexpr uint32_t kF64TileBytes = kTile * kF64Fields * 16;
+constexpr float kPadLog2Amp = -1000.0f;  // exp2 of this is 0: padding beamlets vanish
+
+// Default iteration limit of the bounded mbarrier waits (about a second of spinning).
+constexpr uint32_t kDefaultWaitSpins = 1u << 24;
+
+// Status bits recorded in a translation unit's device status word.
+constexpr unsigned kStatusTimeout = 1u;
+
+// ----------------------------------------------------------------- PTX wrappers --
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase: false after `spins` unsuccessful polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t spins) {
+    for (uint32_t it = 0; it < spins; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// 1-D bulk copy global -> shared (TMA engine), completion signalled on `bar` as
+// transaction bytes.  Both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes,
+                                              uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// MUFU (XU pipe) approximations, PTX-ISA documented forms.
+__device__ __forceinline__ float mufu_ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float mufu_sin(float x) {
+    float y;
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float mufu_cos(float x) {
+    float y;
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// x - nearest integer, exact for |x| < 2^22, on the FMA pipe: adding and removing
+// 1.5 * 2^23 rounds to an integer in the current (round-to-nearest-even) mode.
+__device__ __forceinline__ float frac_turns(float x) {
+    const float magic = 12582912.0f;
+    float n = __fsub_rn(__fadd_rn(x, magic), magic);
+    return __fsub_rn(x, n);
+}
+
+// Error-free transformation a + b = s + e (Knuth's TwoSum), FP32.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// ------------------------------------------------------------- FP64 complex --
+
+struct cd {
+    double re, im;
+};
+__host__ __device__ __forceinline__ cd mk(double r, double i = 0.0) { return cd{r, i}; }
+__host__ __device__ __forceinline__ cd operator+(cd a, cd b) { return cd{a.re + b.re, a.im + b.im}; }
+__host__ __device__ __forceinline__ cd operator-(cd a, cd b) { return cd{a.re - b.re, a.im - b.im}; }
+__host__ __device__ __forceinline__ cd operator*(cd a, cd b) {
+    return cd{a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+__host__ __device__ __forceinline__ cd operator*(double s, cd a) { return cd{s * a.re, s * a.im}; }
+__host__ __device__ __forceinline__ cd cdiv(cd a, cd b) {
+    // Smith's algorithm
+    if (fabs(b.re) >= fabs(b.im)) {
+        double r = b.im / b.re, den = b.re + b.im * r;
+        return cd{(a.re + a.im * r) / den, (a.im - a.re * r) / den};
+    } else {
+        double r = b.re / b.im, den = b.re * r + b.im;
+        return cd{(a.re * r + a.im) / den, (a.im * r - a.re) / den};
+    }
+}
+// Principal square root, branch cut on the negative real axis (sign of im kept).
+__host__ __device__ __forceinline__ cd csqrt_p(cd z) {
+    double r = hypot(z.re, z.im);
+    if (r == 0.0) return cd{0.0, z.im};
+    if (z.re >= 0.0) {
+        double t = sqrt(0.5 * (r + z.re));
+        return cd{t, z.im / (2.0 * t)};
+    }
+    double t = sqrt(0.5 * (r - z.re));
+    return cd{fabs(z.im) / (2.0 * t), copysign(t, z.im)};
+}
+
+}  // namespace gbd
+
+// ----------------------------------------------------- cross-unit host entries --
+// Implemented in the kernel translation units, called by the C ABI layer.
+
+struct gbd_trace_params {
+    double wavelength, inv_f, d, zern_radius;
+    double diameter, overlap_factor, waist_ratio;
+    int32_t n_across;
+    int32_t zdeg;                 // degree of the plate polynomial (-1 = no plate)
+    double zpoly[66];             // W(x/R, y/R) = sum zpoly[idx(a,b)] (x/R)^a (y/R)^b
+};
+
+struct gbd_project_params {
+    double wavelength;
+    double M[4];       // detector (s_x, s_y) -> lab (x, y), row-major
+    double n[2];       // detector (s_x, s_y) -> lab axial offset z
+    double px, py;
+    int32_t nx, ny;
+};
+
+struct gbd_field_launch {
+    int rows_per_thread, cols_per_thread, splits, tiles_per_split;
+};
+
+namespace gbd {
+// Index of the monomial xi^a eta^b in a degree-ordered table: degree g = a + b occupies
+// entries g(g+1)/2 .. g(g+1)/2 + g.  Degree <= 10 needs 66 entries.
+__host__ __device__ __forceinline__ int plate_index(int a, int b) {
+    int g = a + b;
+    return g * (g + 1) / 2 + b;
+}
+}  // namespace gbd
+
+// One instance of a batched trace: its own pupil sampling, written from record `offset`.
+struct gbd_instance_dev {
+    int32_t n_across;
+    int32_t reserved;
+    int64_t offset;
+    double overlap_factor, waist_ratio;
+};
+
+// Traces one pupil (d_inst == nullptr: the sampling in p) or n_instances pupils sharing
+// the optics in p, each from its own record offset.
+cudaError_t gbd_launch_trace(const gbd_trace_params& p, int n_instances, int max_n_across,
+                             const gbd_instance_dev* d_inst, gbd_beamlet* out, cudaStream_t s);
+cudaError_t gbd_launch_project(const gbd_beamlet* b, int n, const gbd_project_params& p,
+                               int precision, void* coeffs, cudaStream_t s);
+cudaError_t gbd_launch_field_kernel(int precision, const void* coeffs, int n_tiles,
+                                    const gbd_project_params& p, const gbd_field_launch& L,
+                                    double2* partial, uint32_t wait_spins, cudaStream_t s);
+cudaError_t gbd_launch_field_reduce(int precision, const gbd_project_params& p, int splits,
+                                    const double2* partial, void* out, cudaStream_t s);
+int gbd_field_occupancy(int precision, int rb, int cb);
+bool gbd_field_shape_supported(int precision, int rb, int cb);
+unsigned gbd_field_status_read_clear();
+cudaError_t gbd_run_probes(double* out);

@@ -1,0 +1,340 @@
+// Beamlet decomposition + differential ray trace (FP64), and the per-beamlet projection
+// onto the detector plane that turns each beamlet into one complex quadratic form.
+//
+// Trace: Sec. 2.2 (steps 1 and 4: chief + parabasal rays, differential ABCD), Eq. OF,
+// Eq. abcd_sys (thin lens then distance), Eq. gauss_prop (complex curvature law and the
+// 1/sqrtdet amplitude, with the eigenvalue route of App. C for the branch).
+// Projection: Eq. collins_factored with the chief-ray propagation of Eqs. ab_prop /
+// cd_prop, extended to a plane tilted about the reference point by second-order
+// expansion in the pixel position.
+#include <math.h>
+
+#include "gbd_internal.cuh"
+
+static_assert(sizeof(gbd_beamlet) == 36 * sizeof(double), "gbd_beamlet is 36 doubles");
+
+using gbd::cd;
+
+namespace {
+
+// --------------------------------------------------------------------- trace --
+
+// Number of grid centres inside the pupil in row j of an N x N cell-centred grid:
+// a = 2i - (N-1) runs over the integers of N-1's parity with a^2 <= N^2 - b^2.
+__device__ __forceinline__ int row_extent(int j, int N) {
+    long long b = 2LL * j - (N - 1);
+    long long r2 = (long long)N * N - b * b;
+    if (r2 < 0) return -1;
+    long long a = (long long)sqrt((double)r2);
+    while (a * a > r2) --a;
+    while ((a + 1) * (a + 1) <= r2) ++a;
+    if (((a - (N - 1)) & 1LL) != 0) --a;
+    return (int)a;  // -1 when the row is empty
+}
+
+struct Ray {
+    double x, y, tx, ty, path;
+};
+
+// OPD plate polynomial and its gradient at (x, y).
+__device__ void plate_eval(const gbd_trace_params& P, double x, double y, double& W, double& gx,
+                           double& gy) {
+    const double inv_r = 1.0 / P.zern_radius;
+    const double xi = x * inv_r, eta = y * inv_r;
+    double xp[11], yp[11];
+    xp[0] = yp[0] = 1.0;
+    for (int q = 1; q <= P.zdeg; ++q) {
+        xp[q] = xp[q - 1] * xi;
+        yp[q] = yp[q - 1] * eta;
+    }
+    double w = 0.0, dx = 0.0, dy = 0.0;
+    for (int g = 0; g <= P.zdeg; ++g) {
+        for (int b = 0; b <= g; ++b) {
+            const int a = g - b;
+            const double c = P.zpoly[gbd::plate_index(a, b)];
+            if (c == 0.0) continue;
+            w += c * xp[a] * yp[b];
+            if (a > 0) dx += c * a * xp[a - 1] * yp[b];
+            if (b > 0) dy += c * b * xp[a] * yp[b - 1];
+        }
+    }
+    W = w;
+    gx = dx * inv_r;
+    gy = dy * inv_r;
+}
+
+// [plate] -> thin lens -> free space d.  `path` is the optical path beyond the axis.
+__device__ void propagate(const gbd_trace_params& P, Ray& r) {
+    if (P.zdeg >= 0) {
+        double W, gx, gy;
+        plate_eval(P, r.x, r.y, W, gx, gy);
+        r.path += W;
+        r.tx += gx;
+        r.ty += gy;
+    }
+    r.path -= 0.5 * (r.x * r.x + r.y * r.y) * P.inv_f;
+    r.tx -= r.x * P.inv_f;
+    r.ty -= r.y * P.inv_f;
+    r.x += P.d * r.tx;
+    r.y += P.d * r.ty;
+    r.path += 0.5 * P.d * (r.tx * r.tx + r.ty * r.ty);
+}
+
+__device__ void trace_one(const gbd_trace_params& P, int N, double OF, double WR, int i, int j,
+                          gbd_beamlet* out) {
+    const double D = P.diameter;
+    const double s = D / N;
+    const double w0 = OF * D / (2.0 * N);
+    const double weight = s * s / (M_PI * w0 * w0);
+    const double h = WR * w0;
+    const double dth = WR * P.wavelength / (M_PI * w0);
+    const double p1 = -P.wavelength / (M_PI * w0 * w0);  // P1 = i * p1 * I
+    const double cx = (i - 0.5 * (N - 1)) * s, cy = (j - 0.5 * (N - 1)) * s;
+
+    Ray c{cx, cy, 0.0, 0.0, 0.0};
+    propagate(P, c);
+    Ray wx{cx + h, cy, 0.0, 0.0, 0.0}, wy{cx, cy + h, 0.0, 0.0, 0.0};
+    Ray dx{cx, cy, dth, 0.0, 0.0}, dy{cx, cy, 0.0, dth, 0.0};
+    propagate(P, wx);
+    propagate(P, wy);
+    propagate(P, dx);
+    propagate(P, dy);
+
+    // columns: derivative of (x, y, tx, ty) with respect to (x0, y0 | tx0, ty0)
+    double A[4] = {(wx.x - c.x) / h, (wy.x - c.x) / h, (wx.y - c.y) / h, (wy.y - c.y) / h};
+    double C[4] = {(wx.tx - c.tx) / h, (wy.tx - c.tx) / h, (wx.ty - c.ty) / h, (wy.ty - c.ty) / h};
+    double B[4] = {(dx.x - c.x) / dth, (dy.x - c.x) / dth, (dx.y - c.y) / dth, (dy.y - c.y) / dth};
+    double Dm[4] = {(dx.tx - c.tx) / dth, (dy.tx - c.tx) / dth, (dx.ty - c.ty) / dth,
+                    (dy.ty - c.ty) / dth};
+
+    // M = A + B P1, N = C + D P1 (P1 purely imaginary, isotropic)
+    cd M[4], Nn[4];
+    for (int q = 0; q < 4; ++q) {
+        M[q] = cd{A[q], B[q] * p1};
+        Nn[q] = cd{C[q], Dm[q] * p1};
+    }
+    const cd detM = M[0] * M[3] - M[1] * M[2];
+    // M^-1 = adj(M) / det
+    const cd Mi[4] = {gbd::cdiv(M[3], detM), gbd::cdiv(gbd::mk(0.0) - M[1], detM),
+                      gbd::cdiv(gbd::mk(0.0) - M[2], detM), gbd::cdiv(M[0], detM)};
+    cd Pm[4];
+    Pm[0] = Nn[0] * Mi[0] + Nn[1] * Mi[2];
+    Pm[1] = Nn[0] * Mi[1] + Nn[1] * Mi[3];
+    Pm[2] = Nn[2] * Mi[0] + Nn[3] * Mi[2];
+    Pm[3] = Nn[2] * Mi[1] + Nn[3] * Mi[3];
+    // sqrtdet(M): principal roots of the eigenvalues tr/2 +- sqrt(tr^2/4 - det)
+    const cd half_tr = 0.5 * (M[0] + M[3]);
+    const cd disc = gbd::csqrt_p(half_tr * half_tr - detM);
+    const cd sd = gbd::csqrt_p(half_tr + disc) * gbd::csqrt_p(half_tr - disc);
+    const cd amp = gbd::cdiv(gbd::mk(weight), sd);
+
+    gbd_beamlet r;
+    r.rho[0] = c.x;
+    r.rho[1] = c.y;
+    r.theta[0] = c.tx;
+    r.theta[1] = c.ty;
+    r.path = c.path;
+    r.amp[0] = amp.re;
+    r.amp[1] = amp.im;
+    for (int q = 0; q < 4; ++q) {
+        r.curv[2 * q] = Pm[q].re;
+        r.curv[2 * q + 1] = Pm[q].im;
+        r.abcd[q] = A[q];
+        r.abcd[4 + q] = B[q];
+        r.abcd[8 + q] = C[q];
+        r.abcd[12 + q] = Dm[q];
+    }
+    r.center[0] = cx;
+    r.center[1] = cy;
+    r.weight = weight;
+    r.waist = w0;
+    r.reserved = 0.0;
+    *out = r;
+}
+
+// grid: (row j, instance).  Each CTA finds its row's first record index by summing the
+// closed-form extents of the rows before it, then one thread per inside centre.
+__global__ void __launch_bounds__(128) trace_kernel(gbd_trace_params P,
+                                                    const gbd_instance_dev* __restrict__ inst,
+                                                    gbd_beamlet* __restrict__ out) {
+    int N = P.n_across;
+    double OF = P.overlap_factor, WR = P.waist_ratio;
+    long long base = 0;
+    if (inst != nullptr) {
+        const gbd_instance_dev I = inst[blockIdx.y];
+        N = I.n_across;
+        OF = I.overlap_factor;
+        WR = I.waist_ratio;
+        base = I.offset;
+    }
+    const int j = blockIdx.x;
+    if (j >= N) return;
+    __shared__ long long warp_sum[4];
+    long long acc = 0;
+    for (int q = threadIdx.x; q < j; q += blockDim.x) acc += row_extent(q, N) + 1;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    const long long row_off = warp_sum[0] + warp_sum[1] + warp_sum[2] + warp_sum[3];
+    const int a = row_extent(j, N);
+    if (a < 0) return;
+    const int i_lo = ((N - 1) - a) / 2;
+    for (int t = threadIdx.x; t <= a; t += blockDim.x)
+        trace_one(P, N, OF, WR, i_lo + t, j, out + base + row_off + t);
+}
+
+// ---------------------------------------------------------------- projection --
+
+struct Quad {
+    double a[6];  // log2 amplitude: 0, u, v, uu, uv, vv
+    double p[6];  // phase in turns
+    double i0, j0;
+    bool pad;
+};
+
+// Per-beamlet quadratic form of ln E in pixel units around the pixel (i0, j0) nearest
+// to where the chief ray meets the detector, with the carrier -ik z(s) common to all
+// beamlets left out (it is applied once per pixel after the sum).
+__device__ Quad project_one(const gbd_beamlet& b, const gbd_project_params& G) {
+    Quad q;
+    if (b.amp[0] == 0.0 && b.amp[1] == 0.0) {
+        q.pad = true;
+        return q;
+    }
+    q.pad = false;
+    const double k = 2.0 * M_PI / G.wavelength;
+    const double th0 = b.theta[0], th1 = b.theta[1];
+    const double th2 = th0 * th0 + th1 * th1;
+    const cd P00{b.curv[0], b.curv[1]}, P01{b.curv[2], b.curv[3]}, P10{b.curv[4], b.curv[5]},
+        P11{b.curv[6], b.curv[7]};
+    const cd S01 = 0.5 * (P01 + P10);  // symmetric part: w^T P w = w^T Psym w
+    const cd trP = P00 + P11;
+    // in-plane map from detector coordinates to the beamlet's transverse offset w
+    const double g00 = G.M[0] - th0 * G.n[0], g01 = G.M[1] - th0 * G.n[1];
+    const double g10 = G.M[2] - th1 * G.n[0], g11 = G.M[3] - th1 * G.n[1];
+    const double dg = g00 * g11 - g01 * g10;
+    double ic = 0.5 * G.nx, jc = 0.5 * G.ny;
+    const int hx = G.nx / 2, hy = G.ny / 2;
+    if (fabs(dg) > 1e-12) {
+        const double sx = (g11 * b.rho[0] - g01 * b.rho[1]) / dg;
+        const double sy = (-g10 * b.rho[0] + g00 * b.rho[1]) / dg;
+        ic = sx / G.px + hx;
+        jc = sy / G.py + hy;
+    }
+    double i0 = rint(ic), j0 = rint(jc);
+    if (!(i0 >= 0.0)) i0 = 0.0;
+    if (!(j0 >= 0.0)) j0 = 0.0;
+    if (i0 > G.nx - 1) i0 = G.nx - 1;
+    if (j0 > G.ny - 1) j0 = G.ny - 1;
+    q.i0 = i0;
+    q.j0 = j0;
+    const double s0x = (i0 - hx) * G.px, s0y = (j0 - hy) * G.py;
+    const double d0x = G.M[0] * s0x + G.M[1] * s0y - b.rho[0];
+    const double d0y = G.M[2] * s0x + G.M[3] * s0y - b.rho[1];
+    const double z0 = G.n[0] * s0x + G.n[1] * s0y;
+    const double wx = d0x - z0 * th0, wy = d0y - z0 * th1;
+    // columns of the maps scaled to one pixel
+    const double gu0 = g00 * G.px, gu1 = g10 * G.px, gv0 = g01 * G.py, gv1 = g11 * G.py;
+    const double mu0 = G.M[0] * G.px, mu1 = G.M[2] * G.px, mv0 = G.M[1] * G.py, mv1 = G.M[3] * G.py;
+    const double nu = G.n[0] * G.px, nv = G.n[1] * G.py;
+    // Psym w
+    const cd Pw0 = P00 * gbd::mk(wx) + S01 * gbd::mk(wy);
+    const cd Pw1 = S01 * gbd::mk(wx) + P11 * gbd::mk(wy);
+    const cd wPw = gbd::mk(wx) * Pw0 + gbd::mk(wy) * Pw1;
+    // complex "path" parts X (multiplied by -ik) and direct parts Y, per coefficient
+    cd X[6], Y[6];
+    X[0] = gbd::mk(b.path - 0.5 * z0 * th2 + th0 * d0x + th1 * d0y) + 0.5 * wPw;
+    Y[0] = -0.5 * z0 * trP;
+    X[1] = gbd::mk(-0.5 * th2 * nu + mu0 * th0 + mu1 * th1) + (gu0 * Pw0 + gu1 * Pw1);
+    Y[1] = -0.5 * nu * trP;
+    X[2] = gbd::mk(-0.5 * th2 * nv + mv0 * th0 + mv1 * th1) + (gv0 * Pw0 + gv1 * Pw1);
+    Y[2] = -0.5 * nv * trP;
+    // second order: (1/2) t^T C2 t with C2 = -ik Gp^T Psym Gp
+    const cd Gu0 = gu0 * P00 + gu1 * S01, Gu1 = gu0 * S01 + gu1 * P11;  // Psym gu
+    const cd Gv0 = gv0 * P00 + gv1 * S01, Gv1 = gv0 * S01 + gv1 * P11;  // Psym gv
+    X[3] = 0.5 * (gu0 * Gu0 + gu1 * Gu1);
+    X[4] = gv0 * Gu0 + gv1 * Gu1;
+    X[5] = 0.5 * (gv0 * Gv0 + gv1 * Gv1);
+    Y[3] = Y[4] = Y[5] = gbd::mk(0.0);
+    const double log2e = 1.4426950408889634;
+    for (int m = 0; m < 6; ++m) {
+        // c = Y - ik X:  Re c = Re Y + k Im X,  Im c = Im Y - k Re X
+        q.a[m] = (Y[m].re + k * X[m].im) * log2e;
+        q.p[m] = Y[m].im / (2.0 * M_PI) - X[m].re / G.wavelength;
+    }
+    // ln amp_j
+    const double am = hypot(b.amp[0], b.amp[1]);
+    q.a[0] += log2(am);
+    double p0 = q.p[0] + atan2(b.amp[1], b.amp[0]) / (2.0 * M_PI);
+    q.p[0] = p0 - rint(p0);
+    return q;
+}
+
+__global__ void __launch_bounds__(128) project_mixed_kernel(const gbd_beamlet* __restrict__ b, int n,
+                                                            int n_pad, gbd_project_params G,
+                                                            float4* __restrict__ out) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_pad) return;
+    float4 f0, f1, f2, f3;
+    Quad q;
+    q.pad = true;
+    if (t < n) q = project_one(b[t], G);
+    if (q.pad) {
+        f0 = make_float4(0.f, 0.f, gbd::kPadLog2Amp, 0.f);
+        f1 = f2 = f3 = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+        f0 = make_float4((float)q.i0, (float)q.j0, (float)q.a[0], (float)q.p[0]);
+        f1 = make_float4((float)q.a[1], (float)q.p[1], (float)q.a[2], (float)q.p[2]);
+        f2 = make_float4((float)q.a[3], (float)q.p[3], (float)q.a[4], (float)q.p[4]);
+        f3 = make_float4((float)q.a[5], (float)q.p[5], 0.f, 0.f);
+    }
+    float4* tile = out + (size_t)(t / gbd::kTile) * gbd::kMixedFields * gbd::kTile;
+    const int l = t % gbd::kTile;
+    tile[l] = f0;
+    tile[gbd::kTile + l] = f1;
+    tile[2 * gbd::kTile + l] = f2;
+    tile[3 * gbd::kTile + l] = f3;
+}
+
+__global__ void __launch_bounds__(128) project_f64_kernel(const gbd_beamlet* __restrict__ b, int n,
+                                                          int n_pad, gbd_project_params G,
+                                                          double2* __restrict__ out) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_pad) return;
+    double2 f[gbd::kF64Fields];
+    Quad q;
+    q.pad = true;
+    if (t < n) q = project_one(b[t], G);
+    if (q.pad) {
+        for (int m = 0; m < gbd::kF64Fields; ++m) f[m] = make_double2(0.0, 0.0);
+        f[1].x = 2.0 * gbd::kPadLog2Amp;
+    } else {
+        f[0] = make_double2(q.i0, q.j0);
+        for (int m = 0; m < 6; ++m) f[1 + m] = make_double2(q.a[m], q.p[m]);
+        f[7] = make_double2(0.0, 0.0);
+    }
+    double2* tile = out + (size_t)(t / gbd::kTile) * gbd::kF64Fields * gbd::kTile;
+    const int l = t % gbd::kTile;
+    for (int m = 0; m < gbd::kF64Fields; ++m) tile[m * gbd::kTile + l] = f[m];
+}
+
+}  // namespace
+
+cudaError_t gbd_launch_trace(const gbd_trace_params& p, int n_instances, int max_n_across,
+                             const gbd_instance_dev* d_inst, gbd_beamlet* out, cudaStream_t s) {
+    dim3 grid(max_n_across, n_instances);
+    trace_kernel<<<grid, 128, 0, s>>>(p, d_inst, out);
+    return cudaGetLastError();
+}
+
+cudaError_t gbd_launch_project(const gbd_beamlet* b, int n, const gbd_project_params& p,
+                               int precision, void* coeffs, cudaStream_t s) {
+    const int n_pad = (n + gbd::kTile - 1) / gbd::kTile * gbd::kTile;
+    if (n_pad == 0) return cudaSuccess;
+    const int blocks = (n_pad + 127) / 128;
+    if (precision == GBD_PREC_MIXED)
+        project_mixed_kernel<<<blocks, 128, 0, s>>>(b, n, n_pad, p, static_cast<float4*>(coeffs));
+    else
+        project_f64_kernel<<<blocks, 128, 0, s>>>(b, n, n_pad, p, static_cast<double2*>(coeffs));
+    return cudaGetLastError();
+}

@@ -1,0 +1,320 @@
+"""Thin ctypes binding of libgbd.so (the C ABI in include/gbd.h).
+
+Argument marshalling only: every step of the method runs in the library's CUDA kernels.
+Device buffers are torch tensors (PyTorch provides device memory and streams).  The
+binding fails loudly when the compiled library is missing; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgbd.so")
+
+GBD_OK, GBD_EINVAL, GBD_ECUDA, GBD_ENOMEM, GBD_ETIMEOUT, GBD_EUNSUPPORTED = range(6)
+GBD_PREC_F64, GBD_PREC_MIXED = 0, 1
+GBD_MAX_ZERN = 64
+BEAMLET_DOUBLES = 36
+TILE = 64
+
+STATUS_NAMES = {0: "GBD_OK", 1: "GBD_EINVAL", 2: "GBD_ECUDA", 3: "GBD_ENOMEM",
+                4: "GBD_ETIMEOUT", 5: "GBD_EUNSUPPORTED"}
+
+
+class GbdError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class gbd_system(ctypes.Structure):
+    _fields_ = [("wavelength", ctypes.c_double), ("focal_length", ctypes.c_double),
+                ("distance", ctypes.c_double), ("zern_radius", ctypes.c_double),
+                ("n_zern", ctypes.c_int32), ("noll", ctypes.c_int32 * GBD_MAX_ZERN),
+                ("zern_coef", ctypes.c_double * GBD_MAX_ZERN)]
+
+
+class gbd_pupil(ctypes.Structure):
+    _fields_ = [("diameter", ctypes.c_double), ("n_across", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class gbd_detector(ctypes.Structure):
+    _fields_ = [("pitch_x", ctypes.c_double), ("pitch_y", ctypes.c_double),
+                ("rot_x", ctypes.c_double), ("rot_y", ctypes.c_double),
+                ("nx", ctypes.c_int32), ("ny", ctypes.c_int32)]
+
+
+class gbd_shape(ctypes.Structure):
+    _fields_ = [("rows_per_thread", ctypes.c_int32), ("cols_per_thread", ctypes.c_int32),
+                ("splits", ctypes.c_int32), ("ms", ctypes.c_float)]
+
+
+# Exported symbols of libgbd.so and their ctypes signatures (name -> (restype, argtypes)).
+_P = ctypes.c_void_p
+_SIGS = {
+    "gbd_last_error": (ctypes.c_char_p, []),
+    "gbd_version": (ctypes.c_char_p, []),
+    "gbd_beamlet_count": (ctypes.c_int32, [ctypes.POINTER(gbd_pupil)]),
+    "gbd_sync": (ctypes.c_int, [_P]),
+    "gbd_set_wait_limit": (ctypes.c_int, [ctypes.c_uint32]),
+    "gbd_trace": (ctypes.c_int, [ctypes.POINTER(gbd_system), ctypes.POINTER(gbd_pupil),
+                                 ctypes.c_double, ctypes.c_double, _P, ctypes.c_int32, _P]),
+    "gbd_field_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int32, ctypes.POINTER(gbd_detector),
+                                                    ctypes.c_int32]),
+    "gbd_field": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_double, ctypes.POINTER(gbd_detector),
+                                 ctypes.c_int32, _P, ctypes.c_size_t, _P, _P]),
+    "gbd_project_bytes": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_int32]),
+    "gbd_project": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_double,
+                                   ctypes.POINTER(gbd_detector), ctypes.c_int32, _P, _P]),
+    "gbd_field_set_shape": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(gbd_shape)]),
+    "gbd_field_get_shape": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.POINTER(gbd_detector), ctypes.POINTER(gbd_shape)]),
+    "gbd_autotune_field": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_double,
+                                          ctypes.POINTER(gbd_detector), ctypes.c_int32, _P,
+                                          ctypes.c_size_t, _P, _P, ctypes.POINTER(gbd_shape)]),
+    "gbd_probe_peaks": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double)]),
+    "gbd_timing_enable": (ctypes.c_int, [ctypes.c_int32]),
+    "gbd_timing_read": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_int64)]),
+    "gbd_psf_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(gbd_pupil),
+                                                  ctypes.POINTER(gbd_detector), ctypes.c_int32]),
+    "gbd_psf": (ctypes.c_int, [ctypes.POINTER(gbd_system), ctypes.POINTER(gbd_pupil),
+                               ctypes.c_double, ctypes.c_double, ctypes.POINTER(gbd_detector),
+                               ctypes.c_int32, _P, ctypes.c_size_t, _P, _P]),
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded libgbd.so.  Raises if it has not been built (no fallback exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int) -> None:
+    if status != GBD_OK:
+        raise GbdError(status, lib().gbd_last_error().decode())
+
+
+def _stream(stream=None):
+    """cudaStream_t of a torch stream, an integer handle, or torch's current stream."""
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    import torch
+    if stream is None:
+        if not torch.cuda.is_available():
+            return ctypes.c_void_p(0)
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+# ---------------------------------------------------------------- structures --
+
+def make_system(system) -> gbd_system:
+    """gbd_system from an object with wavelength, focal_length, distance, noll, ..."""
+    s = gbd_system()
+    s.wavelength = system.wavelength
+    s.focal_length = system.focal_length
+    s.distance = system.distance
+    noll = list(getattr(system, "noll", ()))
+    coef = list(getattr(system, "zern_coef", ()))
+    if len(noll) > GBD_MAX_ZERN:
+        raise ValueError("too many Zernike terms")
+    s.n_zern = len(noll)
+    s.zern_radius = getattr(system, "zern_radius", 1.0) if noll else 1.0
+    for t, (j, c) in enumerate(zip(noll, coef)):
+        s.noll[t] = int(j)
+        s.zern_coef[t] = float(c)
+    return s
+
+
+def make_pupil(pupil) -> gbd_pupil:
+    return gbd_pupil(float(pupil.diameter), int(pupil.n_across), 0)
+
+
+def make_detector(det) -> gbd_detector:
+    return gbd_detector(float(det.pitch_x), float(det.pitch_y), float(det.rot_x), float(det.rot_y),
+                        int(det.nx), int(det.ny))
+
+
+# ------------------------------------------------------------ C ABI mirrors --
+
+def gbd_version() -> str:
+    return lib().gbd_version().decode()
+
+
+def gbd_beamlet_count(pupil) -> int:
+    return int(lib().gbd_beamlet_count(ctypes.byref(make_pupil(pupil))))
+
+
+def gbd_sync(stream=None) -> None:
+    _check(lib().gbd_sync(_stream(stream)))
+
+
+def gbd_set_wait_limit(spins: int) -> None:
+    _check(lib().gbd_set_wait_limit(int(spins)))
+
+
+def gbd_trace(system, pupil, overlap_factor: float, waist_ratio: float, out, stream=None) -> int:
+    """Traces the pupil into ``out`` (float64 CUDA tensor [capacity, 36]); returns n."""
+    n = gbd_beamlet_count(pupil)
+    cap = out.shape[0] if out is not None else 0
+    _check(lib().gbd_trace(ctypes.byref(make_system(system)), ctypes.byref(make_pupil(pupil)),
+                           float(overlap_factor), float(waist_ratio), _ptr(out), int(cap),
+                           _stream(stream)))
+    return n
+
+
+def gbd_field_workspace_bytes(n_beamlets: int, detector, precision: int) -> int:
+    return int(lib().gbd_field_workspace_bytes(int(n_beamlets),
+                                               ctypes.byref(make_detector(detector)),
+                                               int(precision)))
+
+
+def gbd_field(beamlets, n_beamlets: int, wavelength: float, detector, precision: int,
+              workspace, field_out, stream=None) -> None:
+    ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check(lib().gbd_field(_ptr(beamlets), int(n_beamlets), float(wavelength),
+                           ctypes.byref(make_detector(detector)), int(precision),
+                           _ptr(workspace), ctypes.c_size_t(ws_bytes), _ptr(field_out),
+                           _stream(stream)))
+
+
+def gbd_project_bytes(n_beamlets: int, precision: int) -> int:
+    return int(lib().gbd_project_bytes(int(n_beamlets), int(precision)))
+
+
+def gbd_project(beamlets, n_beamlets: int, wavelength: float, detector, precision: int, coeffs,
+                stream=None) -> None:
+    _check(lib().gbd_project(_ptr(beamlets), int(n_beamlets), float(wavelength),
+                             ctypes.byref(make_detector(detector)), int(precision), _ptr(coeffs),
+                             _stream(stream)))
+
+
+def gbd_field_set_shape(precision: int, rows: int, cols: int, splits: int = 0) -> None:
+    sh = gbd_shape(int(rows), int(cols), int(splits), 0.0)
+    _check(lib().gbd_field_set_shape(int(precision), ctypes.byref(sh)))
+
+
+def gbd_field_reset_shape(precision: int) -> None:
+    _check(lib().gbd_field_set_shape(int(precision), None))
+
+
+def gbd_field_get_shape(precision: int, n_beamlets: int, detector) -> Tuple[int, int, int]:
+    sh = gbd_shape()
+    _check(lib().gbd_field_get_shape(int(precision), int(n_beamlets),
+                                     ctypes.byref(make_detector(detector)), ctypes.byref(sh)))
+    return sh.rows_per_thread, sh.cols_per_thread, sh.splits
+
+
+def gbd_autotune_field(beamlets, n_beamlets: int, wavelength: float, detector, precision: int,
+                       workspace, field_out, stream=None) -> Tuple[int, int, int, float]:
+    sh = gbd_shape()
+    ws_bytes = workspace.numel() * workspace.element_size()
+    _check(lib().gbd_autotune_field(_ptr(beamlets), int(n_beamlets), float(wavelength),
+                                    ctypes.byref(make_detector(detector)), int(precision),
+                                    _ptr(workspace), ctypes.c_size_t(ws_bytes), _ptr(field_out),
+                                    _stream(stream), ctypes.byref(sh)))
+    return sh.rows_per_thread, sh.cols_per_thread, sh.splits, float(sh.ms)
+
+
+def gbd_probe_peaks() -> dict:
+    out = (ctypes.c_double * 5)()
+    _check(lib().gbd_probe_peaks(out))
+    return dict(zip(("ex2", "sin", "cos", "ffma", "dfma"), list(out)))
+
+
+TIMING_KINDS = ("field_mixed", "field_f64", "project", "reduce")
+
+
+def gbd_timing_enable(on: bool) -> None:
+    _check(lib().gbd_timing_enable(1 if on else 0))
+
+
+def gbd_timing_read() -> dict:
+    ms = (ctypes.c_double * 4)()
+    n = (ctypes.c_int64 * 4)()
+    _check(lib().gbd_timing_read(ms, n))
+    return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(TIMING_KINDS)}
+
+
+def gbd_psf_workspace_bytes(pupil, detector, precision: int) -> int:
+    return int(lib().gbd_psf_workspace_bytes(ctypes.byref(make_pupil(pupil)),
+                                             ctypes.byref(make_detector(detector)), int(precision)))
+
+
+def gbd_psf(system, pupil, overlap_factor: float, waist_ratio: float, detector, precision: int,
+            workspace, host_out, stream=None) -> None:
+    """Trace + field + copy into ``host_out`` (a CPU tensor, pinned for async copies)."""
+    ws_bytes = workspace.numel() * workspace.element_size()
+    _check(lib().gbd_psf(ctypes.byref(make_system(system)), ctypes.byref(make_pupil(pupil)),
+                         float(overlap_factor), float(waist_ratio),
+                         ctypes.byref(make_detector(detector)), int(precision), _ptr(workspace),
+                         ctypes.c_size_t(ws_bytes), _ptr(host_out), _stream(stream)))
+
+
+# ------------------------------------------------------------ conveniences --
+
+def trace(system, pupil, device="cuda", stream=None):
+    """Beamlet table as a float64 CUDA tensor [n, 36] (gbd_trace)."""
+    import torch
+    n = gbd_beamlet_count(pupil)
+    out = torch.empty((max(n, 1), BEAMLET_DOUBLES), dtype=torch.float64, device=device)
+    gbd_trace(system, pupil, pupil.overlap_factor, pupil.waist_ratio, out, stream)
+    return out[:n]
+
+
+def workspace(n_beamlets: int, detector, precision: int, device="cuda"):
+    import torch
+    nbytes = gbd_field_workspace_bytes(n_beamlets, detector, precision)
+    return torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
+
+
+def field(beamlets, wavelength: float, detector, precision: int = GBD_PREC_MIXED, ws=None,
+          out=None, stream=None):
+    """Complex field [ny, nx] (complex64 mixed / complex128 FP64) as a CUDA tensor."""
+    import torch
+    n = int(beamlets.shape[0])
+    dtype = torch.complex64 if precision == GBD_PREC_MIXED else torch.complex128
+    if out is None:
+        out = torch.empty((detector.ny, detector.nx), dtype=dtype, device=beamlets.device)
+    if ws is None:
+        ws = workspace(n, detector, precision, beamlets.device)
+    gbd_field(beamlets, n, wavelength, detector, precision, ws, out, stream)
+    return out
+
+
+def psf(system, pupil, detector, precision: int = GBD_PREC_MIXED, stream=None):
+    """Trace + field in one call; returns the complex field as a CUDA tensor."""
+    b = trace(system, pupil, stream=stream)
+    return field(b, system.wavelength, detector, precision, stream=stream)
+
+
+def unpack(rec: np.ndarray) -> dict:
+    """Named views of one gbd_beamlet record (36 doubles)."""
+    r = np.asarray(rec, dtype=np.float64)
+    return dict(rho=r[0:2], theta=r[2:4], path=r[4], amp=complex(r[5], r[6]),
+                P=(r[7:15:2] + 1j * r[8:15:2]).reshape(2, 2), A=r[15:19].reshape(2, 2),
+                B=r[19:23].reshape(2, 2), C=r[23:27].reshape(2, 2), D=r[27:31].reshape(2, 2),
+                center=r[31:33], weight=r[33], waist=r[34])

@@ -1,0 +1,134 @@
+"""The C-ABI library builds, loads and exports every symbol include/gbd.h declares; the
+host-side argument checks reject bad input before any launch (no GPU needed)."""
+import ctypes
+import math
+import os
+import re
+
+import pytest
+
+from paper_2404_12454_gb300 import build as gbuild
+from paper_2404_12454_gb300 import gbd
+from paper_2404_12454_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_]\w*[\s\*]+\**(gbd_\w+)\s*\(", text, re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    gbuild.build()
+    return gbd.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared_functions()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(lib, name), name
+    # and the binding covers every declaration under the same name
+    missing = [n for n in names if n not in gbd._SIGS]
+    assert not missing, missing
+
+
+def test_version_and_beamlet_count(lib):
+    assert "sm_103a" in gbd.gbd_version()
+    for n, expected in ((1, 1), (2, 4), (16, 208), (32, 812), (64, 3228), (128, 12892), (256, 51468)):
+        assert gbd.gbd_beamlet_count(W.Pupil(2.4e-3, n, 1.5, 1.5)) == expected
+    assert lib.gbd_beamlet_count(None) == -1
+    assert gbd.gbd_beamlet_count(W.Pupil(2.4e-3, 0, 1.5, 1.5)) == -1
+
+
+def _einval(call):
+    with pytest.raises(gbd.GbdError) as ei:
+        call()
+    assert ei.value.status in (gbd.GBD_EINVAL, gbd.GBD_ENOMEM)
+    return ei.value.status
+
+
+def test_trace_rejects_bad_arguments(lib):
+    wl = W.airy_small()
+    null = None
+
+    class T:  # stands in for a tensor; never dereferenced: validation fails first
+        shape = (10 ** 6, 36)
+
+        def data_ptr(self):
+            return 16
+
+    good_sys, good_pup = wl.system, wl.pupil
+    bad = [
+        (W.System(-1e-6, 0.024, 0.024), good_pup),
+        (W.System(float("nan"), 0.024, 0.024), good_pup),
+        (W.System(1e-6, 0.0, 0.024), good_pup),
+        (W.System(1e-6, 0.024, -1.0), good_pup),
+        (W.System(1e-6, 0.024, 0.024, (70,), (1e-7,), 1e-3), good_pup),
+        (W.System(1e-6, 0.024, 0.024, (4,), (1e-7,), 0.0), good_pup),
+        (good_sys, W.Pupil(-1.0, 32, 1.5, 1.5)),
+        (good_sys, W.Pupil(2.4e-3, 5000, 1.5, 1.5)),
+    ]
+    for s, p in bad:
+        assert _einval(lambda: gbd.gbd_trace(s, p, 1.5, 1.5, T())) == gbd.GBD_EINVAL
+    assert _einval(lambda: gbd.gbd_trace(good_sys, good_pup, 0.0, 1.5, T())) == gbd.GBD_EINVAL
+    assert _einval(lambda: gbd.gbd_trace(good_sys, good_pup, 1.5, -1.0, T())) == gbd.GBD_EINVAL
+
+    class Small(T):
+        shape = (5, 36)
+    assert _einval(lambda: gbd.gbd_trace(good_sys, good_pup, 1.5, 1.5, Small())) == gbd.GBD_ENOMEM
+    assert "capacity" in lib.gbd_last_error().decode()
+
+
+def test_field_rejects_bad_arguments(lib):
+    det = W.airy_small().detector
+
+    class T:
+        def __init__(self, addr=256, n=1 << 20):
+            self.addr, self.n = addr, n
+
+        def data_ptr(self):
+            return self.addr
+
+        def numel(self):
+            return self.n
+
+        def element_size(self):
+            return 1
+
+    cases = [
+        dict(detector=W.Detector(0, 10, 1e-6, 1e-6)),
+        dict(detector=W.Detector(10, 10, -1e-6, 1e-6)),
+        dict(detector=W.Detector(10, 10, 1e-6, 1e-6, 2.0, 0.0)),
+        dict(precision=7),
+        dict(wavelength=0.0),
+        dict(n=-1),
+        dict(ws=T(addr=300)),  # misaligned workspace
+        dict(out=T(addr=8)),   # misaligned output
+    ]
+    for c in cases:
+        args = dict(beam=T(), n=10, wavelength=1e-6, detector=det, precision=gbd.GBD_PREC_MIXED,
+                    ws=T(), out=T())
+        args.update(c)
+        st = _einval(lambda: gbd.gbd_field(args["beam"], args["n"], args["wavelength"],
+                                           args["detector"], args["precision"], args["ws"],
+                                           args["out"]))
+        assert st == gbd.GBD_EINVAL
+    with pytest.raises(gbd.GbdError):
+        gbd.gbd_field_set_shape(gbd.GBD_PREC_MIXED, 3, 3)
+
+
+def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
+    monkeypatch.setattr(gbd, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(gbd, "_lib", None)
+    with pytest.raises(RuntimeError, match="missing"):
+        gbd.lib()

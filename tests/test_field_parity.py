@@ -1,0 +1,260 @@
+"""CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Trace records field by field; fields by relative L2 over all compared pixels:
+<= 1e-11 for the FP64 path, <= 2e-5 for the mixed path (FP32 per-pixel phase and MUFU
+ex2/sin/cos, compensated sum).  Sizes span several beamlet tiles and pixel blocks with
+ragged tails; the two workloads at full size are compared on pixel subsets the oracle
+computes one by one.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2404_12454_gb300 import gbd
+from paper_2404_12454_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {gbd.GBD_PREC_F64: 1e-11, gbd.GBD_PREC_MIXED: 2e-5}
+PRECS = (gbd.GBD_PREC_F64, gbd.GBD_PREC_MIXED)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2404_12454_gb300 import build
+    build.build()
+    import torch
+    torch.cuda.init()
+    yield
+    gbd.gbd_field_reset_shape(gbd.GBD_PREC_MIXED)
+    gbd.gbd_field_reset_shape(gbd.GBD_PREC_F64)
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def gpu_trace(wl):
+    b = gbd.trace(wl.system, wl.pupil)
+    gbd.gbd_sync()
+    return b
+
+
+def gpu_field(b, wl, prec):
+    E = gbd.field(b, wl.system.wavelength, wl.detector, prec)
+    gbd.gbd_sync()
+    return E.cpu().numpy().astype(np.complex128)
+
+
+def small_cases():
+    airy = W.airy_small()
+    tz = W.tilted_zernike()
+    return {
+        "airy_small": airy,
+        "airy_ragged": W.scaled(airy, n_across=23, nx=97, ny=45),
+        "tilted_zernike_small": W.scaled(tz, n_across=24, nx=80, ny=72),
+        "defocused": W.Workload("defocused", W.System(1e-6, 0.024, 0.0246), W.Pupil(2.4e-3, 16, 1.2, 2.0),
+                                W.Detector(70, 66, 1.5e-6, 1.2e-6)),
+        "tilted_defocused": W.Workload("tilted_defocused", W.System(0.633e-6, 0.012, 0.0121),
+                                       W.Pupil(2.4e-3, 20, 2.0, 1.2),
+                                       W.Detector(64, 50, 0.4e-6, 0.5e-6, math.radians(-12),
+                                                  math.radians(7))),
+    }
+
+
+@pytest.mark.parametrize("name", list(small_cases()))
+def test_trace_records_match_oracle(name):
+    wl = small_cases()[name]
+    g = gpu_trace(wl).cpu().numpy()
+    o = oracle.trace(wl.system, wl.pupil)
+    assert g.shape[0] == o.shape[0]
+    for rg, ro in zip(g, o):
+        a, b = gbd.unpack(rg), oracle.unpack(ro)
+        assert np.allclose(a["center"], b["r"], rtol=0, atol=1e-18)
+        assert abs(a["weight"] - b["a"]) <= 1e-15 * b["a"]
+        assert abs(a["waist"] - b["w0"]) <= 1e-18
+        assert np.allclose(a["rho"], b["rho"], rtol=0, atol=1e-16)
+        assert np.allclose(a["theta"], b["theta"], rtol=0, atol=1e-14)
+        assert abs(a["path"] - b["L"]) <= 1e-17
+        for k in "ABCD":
+            scale = max(1.0, np.abs(b[k]).max())
+            assert np.allclose(a[k], b[k], rtol=0, atol=1e-10 * scale), k
+        assert np.allclose(a["P"], b["P"], rtol=0, atol=1e-10 * np.abs(b["P"]).max())
+        assert abs(a["amp"] - b["alpha"]) <= 1e-12 * abs(b["alpha"])
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("name", list(small_cases()))
+def test_field_matches_oracle(name, prec):
+    wl = small_cases()[name]
+    b = gpu_trace(wl)
+    E = gpu_field(b, wl, prec)
+    o = oracle.trace(wl.system, wl.pupil)
+    Eo = oracle.field(o, wl.system, wl.detector)
+    err = rel_l2(E, Eo)
+    assert err <= TOL[prec], err
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_full_size_airy_large_sampled(prec):
+    """512 x 512 pixels, 51,468 beamlets on the GPU; oracle on a strided 32 x 32 sample."""
+    wl = W.airy_large()
+    b = gpu_trace(wl)
+    E = gpu_field(b, wl, prec)
+    cols = np.arange(3, 512, 16)
+    rows = np.arange(5, 512, 16)
+    o = oracle.trace(wl.system, wl.pupil)
+    Eo = oracle.field(o, wl.system, wl.detector, cols, rows)
+    err = rel_l2(E[np.ix_(rows, cols)], Eo)
+    assert err <= TOL[prec], err
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_full_size_tilted_zernike_subset(prec):
+    """1024 x 1024 tilted, aberrated detector; oracle on the 64 x 64 strided subset."""
+    wl = W.tilted_zernike()
+    b = gpu_trace(wl)
+    E = gpu_field(b, wl, prec)
+    cols, rows = W.strided_pixels(wl)
+    o = oracle.trace(wl.system, wl.pupil)
+    Eo = oracle.field(o, wl.system, wl.detector, cols, rows)
+    err = rel_l2(E[np.ix_(rows, cols)], Eo)
+    assert err <= TOL[prec], err
+
+
+# ----------------------------------------------------------------- edge cases --
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_zero_beamlets_gives_zero_field(prec):
+    import torch
+    det = W.Detector(37, 11, 1e-6, 1e-6)
+    dtype = torch.complex64 if prec == gbd.GBD_PREC_MIXED else torch.complex128
+    out = torch.full((11, 37), 7.0, dtype=dtype, device="cuda")
+    empty = torch.empty((0, 36), dtype=torch.float64, device="cuda")
+    gbd.gbd_field(empty, 0, 1e-6, det, prec, None, out)
+    gbd.gbd_sync()
+    assert torch.count_nonzero(out).item() == 0
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("shape", [(1, 1), (1, 300), (300, 1), (33, 7)])
+def test_degenerate_detectors(prec, shape):
+    nx, ny = shape
+    wl = W.Workload("edge", W.System(1e-6, 0.024, 0.024), W.Pupil(2.4e-3, 9, 1.5, 1.5),
+                    W.Detector(nx, ny, 0.9e-6, 1.1e-6))
+    b = gpu_trace(wl)
+    E = gpu_field(b, wl, prec)
+    Eo = oracle.field(oracle.trace(wl.system, wl.pupil), wl.system, wl.detector)
+    assert rel_l2(E, Eo) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_single_beamlet_free_space(prec):
+    """One beamlet, no lens: the textbook Gaussian through the whole CUDA path."""
+    lam, D = 1e-6, 1e-3
+    zR = math.pi * (D / 2) ** 2 / lam
+    wl = W.Workload("one", W.System(lam, math.inf, 3 * zR), W.Pupil(D, 1, 1.0, 1.0),
+                    W.Detector(40, 40, 0.2e-3, 0.2e-3))
+    b = gpu_trace(wl)
+    E = gpu_field(b, wl, prec)
+    Eo = oracle.field(oracle.trace(wl.system, wl.pupil), wl.system, wl.detector)
+    assert rel_l2(E, Eo) <= TOL[prec]
+
+
+def test_mixed_is_deterministic():
+    wl = W.airy_small()
+    b = gpu_trace(wl)
+    E1 = gpu_field(b, wl, gbd.GBD_PREC_MIXED)
+    E2 = gpu_field(b, wl, gbd.GBD_PREC_MIXED)
+    assert np.array_equal(E1, E2)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_every_shape_and_split_matches(prec):
+    """Each compiled launch shape and several beamlet splits give the oracle's field."""
+    wl = small_cases()["tilted_zernike_small"]
+    b = gpu_trace(wl)
+    Eo = oracle.field(oracle.trace(wl.system, wl.pupil), wl.system, wl.detector)
+    shapes = [(1, 4), (2, 2), (2, 4), (4, 2)] if prec == gbd.GBD_PREC_MIXED else [(1, 2), (2, 2)]
+    try:
+        for rows, cols in shapes:
+            for splits in (1, 2, 5):
+                gbd.gbd_field_set_shape(prec, rows, cols, splits)
+                E = gpu_field(b, wl, prec)
+                assert rel_l2(E, Eo) <= TOL[prec], (rows, cols, splits)
+    finally:
+        gbd.gbd_field_reset_shape(prec)
+
+
+def test_autotune_then_parity():
+    import torch
+    wl = W.airy_small()
+    b = gpu_trace(wl)
+    prec = gbd.GBD_PREC_MIXED
+    ws = torch.empty(64 << 20, dtype=torch.uint8, device="cuda")
+    out = torch.empty((wl.detector.ny, wl.detector.nx), dtype=torch.complex64, device="cuda")
+    try:
+        r, c, s, ms = gbd.gbd_autotune_field(b, b.shape[0], wl.system.wavelength, wl.detector,
+                                             prec, ws, out)
+        assert ms > 0 and s >= 1
+        E = gpu_field(b, wl, prec)
+        Eo = oracle.field(oracle.trace(wl.system, wl.pupil), wl.system, wl.detector)
+        assert rel_l2(E, Eo) <= TOL[prec]
+    finally:
+        gbd.gbd_field_reset_shape(prec)
+
+
+def test_host_psf_matches_device_path():
+    import torch
+    wl = W.scaled(W.tilted_zernike(), n_across=16, nx=64, ny=48)
+    for prec in PRECS:
+        dtype = torch.complex64 if prec == gbd.GBD_PREC_MIXED else torch.complex128
+        ws = torch.empty(gbd.gbd_psf_workspace_bytes(wl.pupil, wl.detector, prec),
+                         dtype=torch.uint8, device="cuda")
+        host = torch.empty((48, 64), dtype=dtype).pin_memory()
+        gbd.gbd_psf(wl.system, wl.pupil, wl.pupil.overlap_factor, wl.pupil.waist_ratio,
+                    wl.detector, prec, ws, host)
+        gbd.gbd_sync()
+        E = gpu_field(gpu_trace(wl), wl, prec)
+        assert np.array_equal(host.numpy().astype(np.complex128), E)
+
+
+def test_timeout_is_reported_and_context_survives():
+    """A wait limit of one poll makes the producer's wait on busy warps give up: the
+    kernel records GBD_ETIMEOUT and exits, and the next call works normally."""
+    wl = W.airy_small()
+    b = gpu_trace(wl)
+    prec = gbd.GBD_PREC_MIXED
+    gbd.gbd_field_set_shape(prec, 2, 4, 1)  # every CTA streams all 13 tiles
+    try:
+        gbd.gbd_set_wait_limit(1)
+        gbd.field(b, wl.system.wavelength, wl.detector, prec)
+        with pytest.raises(gbd.GbdError) as ei:
+            gbd.gbd_sync()
+        assert ei.value.status == gbd.GBD_ETIMEOUT
+    finally:
+        gbd.gbd_set_wait_limit(0)
+        gbd.gbd_field_reset_shape(prec)
+    E = gpu_field(b, wl, prec)
+    Eo = oracle.field(oracle.trace(wl.system, wl.pupil), wl.system, wl.detector)
+    assert rel_l2(E, Eo) <= TOL[prec]
+
+
+def test_kernel_timing_hooks_count_launches():
+    wl = W.airy_small()
+    b = gpu_trace(wl)
+    gbd.gbd_timing_read()
+    gbd.gbd_timing_enable(True)
+    try:
+        for _ in range(3):
+            gbd.field(b, wl.system.wavelength, wl.detector, gbd.GBD_PREC_MIXED)
+        gbd.field(b, wl.system.wavelength, wl.detector, gbd.GBD_PREC_F64)
+        gbd.gbd_sync()
+        t = gbd.gbd_timing_read()
+    finally:
+        gbd.gbd_timing_enable(False)
+    assert t["field_mixed"][1] == 3 and t["field_f64"][1] == 1
+    assert t["project"][1] == 4 and t["reduce"][1] == 4
+    assert all(ms > 0 for ms, n in t.values())
