@@ -191,6 +191,31 @@ gbd_status gbd_autotune_field(const gbd_beamlet* beamlets, int32_t n_beamlets,
                               int32_t precision, void* workspace, size_t workspace_bytes,
                               void* field_out, void* stream, gbd_shape* best);
 
+/* ---------------------------------------------------------------- no allocation ---
+ * gbd_field without a workspace, for callers that must not allocate device memory: a
+ * plugin inside a host application that owns every device allocation, or a real-time
+ * loop whose memory is fixed at start-up, can neither call cudaMalloc nor pass scratch.
+ * (No counterpart in the paper: this is a property of the library, not of the method.)
+ * The scratch is one static device array of GBD_NOALLOC_SCRATCH_BYTES (32 MiB) inside
+ * the library; every GPU that loads the library holds it until the process exits.
+ *   - Same arguments and results as gbd_field, without workspace/workspace_bytes; the
+ *     caller still owns beamlets and field_out.
+ *   - The first call on a device looks the array's device address up (with that device
+ *     current); make that first call before any stream capture.
+ *   - A problem whose projected beamlet records plus one partial field of nx x ny pixels
+ *     exceeds the array is rejected with GBD_EINVAL before any launch (beamlet splits are
+ *     lowered to fit first; records take 64 B (mixed) / 128 B (FP64) per beamlet rounded
+ *     up to 64 beamlets, a partial field 16 B per pixel).
+ *   - All calls share the array and each overwrites every byte it later reads, so nothing
+ *     carries over from the previous call; calls that overlap on the GPU (for example
+ *     on two streams of one device) race on it and must be serialised.  Each device
+ *     has its own copy.
+ *   - Allocates nothing: no cudaMalloc, cudaFree or allocating library routine. */
+#define GBD_NOALLOC_SCRATCH_BYTES (32u << 20)
+gbd_status gbd_field_noalloc(const gbd_beamlet* beamlets, int32_t n_beamlets, double wavelength,
+                             const gbd_detector* detector, int32_t precision, void* field_out,
+                             void* stream);
+
 /* ---------------------------------------------------------------- host PSF --------
  * Trace + field + copy to the host in one call, for callers that want the field in host
  * memory: workspace (device, 256-byte aligned, >= gbd_psf_workspace_bytes) holds the

@@ -320,6 +320,37 @@ gbd_status check_field_args(const gbd_beamlet* beamlets, int32_t n, double wavel
 
 }  // namespace
 
+gbd_status gbd_set_error(gbd_status st, const char* msg) { return fail(st, "%s", msg); }
+
+// gbd_field on a fixed scratch buffer of known size: the beamlet splits are lowered until
+// the projected records and the split partial fields fit; sizes that do not fit even
+// with one split are rejected before anything is launched.
+gbd_status gbd_field_fixed_scratch(const gbd_beamlet* beamlets, int32_t n, double wavelength,
+                                   const gbd_detector* detector, int32_t precision,
+                                   void* scratch, size_t scratch_bytes, void* out,
+                                   cudaStream_t stream) {
+    gbd_status st = check_field_args(beamlets, n, wavelength, detector, precision, scratch, out);
+    if (st != GBD_OK) return st;
+    gbd_shape sh = stored_shape(precision);
+    if (n > 0) {
+        const int nt = n_tiles_of(n);
+        gbd_field_launch L = resolve_launch(precision, sh, nt, detector);
+        sh.splits = L.splits;
+        while (sh.splits > 1 && workspace_for(precision, n, detector, L) > scratch_bytes) {
+            --sh.splits;
+            L = resolve_launch(precision, sh, nt, detector);
+        }
+        const size_t need = workspace_for(precision, n, detector, L);
+        if (need > scratch_bytes)
+            return fail(GBD_EINVAL,
+                        "problem needs %zu bytes of scratch (beamlet records + one partial field "
+                        "of %d x %d pixels), more than the fixed %zu bytes",
+                        need, detector->nx, detector->ny, scratch_bytes);
+    }
+    return run_field(beamlets, n, wavelength, detector, precision, scratch, scratch_bytes, out,
+                     stream, sh);
+}
+
 extern "C" {
 
 const char* gbd_last_error(void) { return g_err; }

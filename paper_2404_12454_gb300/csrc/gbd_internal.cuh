@@ -199,6 +199,11 @@ cudaError_t gbd_launch_field_kernel(int precision, const void* coeffs, int n_til
 cudaError_t gbd_launch_field_reduce(int precision, const gbd_project_params& p, int splits,
                                     const double2* partial, void* out, cudaStream_t s);
 int gbd_field_occupancy(int precision, int rb, int cb);
+gbd_status gbd_set_error(gbd_status st, const char* msg);  // sets gbd_last_error()
+gbd_status gbd_field_fixed_scratch(const gbd_beamlet* beamlets, int32_t n, double wavelength,
+                                   const gbd_detector* detector, int32_t precision,
+                                   void* scratch, size_t scratch_bytes, void* out,
+                                   cudaStream_t stream);
 bool gbd_field_shape_supported(int precision, int rb, int cb);
 unsigned gbd_field_status_read_clear();
 cudaError_t gbd_run_probes(double* out);

@@ -79,6 +79,8 @@ _SIGS = {
                                           ctypes.POINTER(gbd_detector), ctypes.c_int32, _P,
                                           ctypes.c_size_t, _P, _P, ctypes.POINTER(gbd_shape)]),
     "gbd_probe_peaks": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double)]),
+    "gbd_field_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_double,
+                                         ctypes.POINTER(gbd_detector), ctypes.c_int32, _P, _P]),
     "gbd_timing_enable": (ctypes.c_int, [ctypes.c_int32]),
     "gbd_timing_read": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_int64)]),
@@ -243,6 +245,20 @@ def gbd_probe_peaks() -> dict:
     out = (ctypes.c_double * 5)()
     _check(lib().gbd_probe_peaks(out))
     return dict(zip(("ex2", "sin", "cos", "ffma", "dfma"), list(out)))
+
+
+NOALLOC_SCRATCH_BYTES = 32 << 20
+
+
+def gbd_field_noalloc(beamlets, n_beamlets: int, wavelength: float, detector, precision: int,
+                      field_out, stream=None) -> None:
+    """gbd_field without a workspace: scratch is a fixed 32 MiB array inside the library,
+    for callers that may not allocate device memory.  Calls share that array, so calls
+    that overlap on the GPU must be serialised; the first call on a device should come
+    before any stream capture."""
+    _check(lib().gbd_field_noalloc(_ptr(beamlets), int(n_beamlets), float(wavelength),
+                                   ctypes.byref(make_detector(detector)), int(precision),
+                                   _ptr(field_out), _stream(stream)))
 
 
 TIMING_KINDS = ("field_mixed", "field_f64", "project", "reduce")
