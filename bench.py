@@ -40,6 +40,9 @@ MUFU_EX2_PER_CLK_SM = 32
 MUFU_SINCOS_PER_CLK_SM = 16
 GB300_SMS = 152
 GB300_MAX_MHZ = 2070.0
+# DRAM bytes (read + write) per launch of field_mixed_kernel<2,4> on airy_large from one
+# ncu capture (profiles/field_mixed_kernel_airy_large.md); valid only for that kernel.
+FIELD_MIXED_NCU = {"kernel": "field_mixed_kernel<2, 4>", "bytes": 3.696896e6 + 48.958976e6}
 
 
 def parse():
@@ -326,7 +329,9 @@ def run_ours(args, world, rank, local):
     roofline = {
         "bound": "alu", "pipe": "MUFU (XU): ex2 + sin + cos per beamlet-pixel",
         "achieved": achieved / 1e9, "peak": peak_evals / 1e9, "unit": "Geval/s",
-        "frac": achieved / peak_evals, "traffic": None,
+        "frac": achieved / peak_evals, "traffic": FIELD_MIXED_NCU["bytes"],
+        "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one capture of "
+                          + FIELD_MIXED_NCU["kernel"],
         "peak_source": (f"derived: {GB300_SMS} SMs x {GB300_MAX_MHZ:g} MHz / (1/{MUFU_EX2_PER_CLK_SM}"
                         f" + 2/{MUFU_SINCOS_PER_CLK_SM}) clk per eval"),
         "kernel": "field_mixed_kernel", "kernel_ms_avg": k_avg_s * 1e3, "launches": kn,
