@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep-steps", type=int, default=2,
+                    help="timed runs of the 1024-instance parameter sweep (0 = skip)")
     return ap.parse_args()
 
 
@@ -166,6 +168,11 @@ class ClockSampler:
         return {"sm_mhz": mhz[len(mhz) // 2], "sm_max_mhz": max(r[2] for r in use),
                 "reasons": sorted(reasons), "samples": len(use),
                 "samples_in_timed_region": len(inside)}
+
+
+def peak_evals_const() -> float:
+    """MUFU-bound beamlet-pixel evaluations/s of a GB300 at its maximum clock."""
+    return GB300_SMS * GB300_MAX_MHZ * 1e6 / (1.0 / MUFU_EX2_PER_CLK_SM + 2.0 / MUFU_SINCOS_PER_CLK_SM)
 
 
 def gpu_index_for_smi(local: int) -> str:
@@ -315,6 +322,40 @@ def run_ours(args, world, rank, local):
            "d2h_bytes_per_step": npix * 8,
            "api": "gbd_psf (host parameters -> pinned host complex64 field)"}
 
+    # ---- batched parameter sweep: 1024 uneven instances in one persistent launch, replayed
+    # as a CUDA graph on its own stream
+    sweep = None
+    if args.sweep_steps > 0:
+        sw = W.sweep()
+        sstream = torch.cuda.Stream(device=dev)
+        with torch.cuda.stream(sstream):
+            plan = gbd.sweep_plan(sw, stream=sstream)
+            plan.run(stream=sstream, graph=True)
+            sstream.synchronize()
+            sms = []
+            t0 = time.time()
+            for _ in range(args.sweep_steps):
+                flush.zero_()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(sstream)
+                plan.run(stream=sstream, graph=True)
+                b.record(sstream)
+                sms.append((a, b))
+            sstream.synchronize()
+            clocks.add_window(t0, time.time())
+        gbd.gbd_sync(sstream)
+        sweep_ms = allreduce_max(world, sum(x.elapsed_time(y) for x, y in sms))
+        sv = world * plan.evals * args.sweep_steps / (sweep_ms * 1e-3)
+        sc = plan.scores.cpu().numpy()
+        sweep = {"value": sv, "unit": UNIT, "ms_per_sweep": sweep_ms / args.sweep_steps,
+                 "instances": plan.n, "beamlets": plan.beamlets, "evals_per_sweep": plan.evals,
+                 "work_items": plan.items, "frac_of_mufu_peak": sv / world / peak_evals_const(),
+                 "graph": True, "score_range": [float(sc.min()), float(sc.max())],
+                 "workload": "1024 instances, airy_small optics, OF~U[1,3], WR~U[0.8,3], "
+                             "N~U{16..256}, 256x256 pixels +-5 lambda F#"}
+        plan.close()
+
     clk = clocks.stop()
 
     # ---- roofline of the dominant kernel (mixed field kernel, MUFU pipe): each
@@ -366,6 +407,7 @@ def run_ours(args, world, rank, local):
                      "ex2/sin/cos, compensated FP32 sum",
         "data": "synthetic (ideal F/10 lens standing in for the paper's traced telescope)",
         "config": config_block(wl, nb), "clocks": clk, "e2e": e2e, "fp64_path": f64,
+        "sweep": sweep,
         "error": error, "roofline": roofline, "cpu_baseline": cpu,
         "gpu_launches": launches_per_step * args.steps,
         "kernel_ms": {k: (v[0] / max(v[1], 1)) for k, v in kt.items()},

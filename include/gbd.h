@@ -19,9 +19,9 @@
  *     nothing is launched then.  CUDA errors return GBD_ECUDA.  A kernel that gives up
  *     a bounded wait records GBD_ETIMEOUT in a per-device status word read by
  *     gbd_sync().  gbd_last_error() gives a message for the calling thread.
- *   - No call allocates device memory except gbd_sweep_plan_create (host tables only)
- *     and the workspace-free helpers stated below; scratch memory is a caller-provided
- *     workspace whose size a *_workspace_bytes query returns.
+ *   - No call allocates device memory (gbd_probe_peaks excepted, which is a
+ *     measurement tool); scratch memory is a caller-provided workspace whose size a
+ *     *_workspace_bytes query returns.
  *   - All entry points are safe to call from several host threads on different streams.
  */
 #ifndef GBD_H
@@ -235,6 +235,45 @@ gbd_status gbd_psf(const gbd_system* system, const gbd_pupil* pupil, double over
  * 3 reduction; arrays of 4) and forgets them. */
 gbd_status gbd_timing_enable(int32_t on);
 gbd_status gbd_timing_read(double* total_ms, int64_t* launches);
+
+/* ---------------------------------------------------------------- gbd_sweep -------
+ * Batched parameter sweep (Sec. 6, Fig. optimal_param_search): n instances that share the
+ * optics (system, pupil diameter) and an untilted detector but each have their own
+ * beamlets across, overlap factor and waist ratio, evaluated in mixed precision and scored
+ * by the RMS of |E|/|E(centre)| - |2 J1(x)/x| (x = pi r / (lambda F#), F# = f / D) over
+ * the pixels with r <= j_{1,3} lambda F# / pi (inside the third dark ring); the centre is
+ * pixel (nx/2, ny/2).
+ * gbd_sweep_plan_create: host only; validates, lays out the tables and the work list
+ *   ((instance, pixel block) items, instances with the most beamlet tiles first) and the
+ *   workspace.  shape = NULL picks 2 x 4 pixels per thread.
+ * gbd_sweep_bind: records the caller's device workspace (>= gbd_sweep_workspace_bytes,
+ *   256-byte aligned; it must outlive the plan's runs), uploads the tables and the Airy
+ *   table; synchronises `stream`.
+ * gbd_sweep_run: batched trace + projection, the persistent field + score kernel and the
+ *   finalize, asynchronous on `stream`; scores = device double[n_instances].  The score
+ *   of every instance is deterministic (fixed summation order).
+ * gbd_sweep_run_graph: the same work captured once into a CUDA graph (on the first call
+ *   for a given scores pointer and stream) and replayed; `stream` must be a created
+ *   stream, not the legacy default stream.
+ * gbd_sweep_autotune: times every supported shape on the given instances (synchronous)
+ *   and returns the fastest; the workspace must hold the largest plan.
+ * gbd_sweep_info: total beamlet-pixel evaluations, beamlets and work items of a plan. */
+typedef struct gbd_sweep_plan gbd_sweep_plan;
+gbd_status gbd_sweep_plan_create(const gbd_system* system, double diameter, const int32_t* n_across,
+                                 const double* overlap_factor, const double* waist_ratio,
+                                 int32_t n_instances, const gbd_detector* detector,
+                                 const gbd_shape* shape, gbd_sweep_plan** plan);
+size_t gbd_sweep_workspace_bytes(const gbd_sweep_plan* plan);
+gbd_status gbd_sweep_info(const gbd_sweep_plan* plan, double* evals, int64_t* beamlets,
+                          int32_t* items);
+gbd_status gbd_sweep_bind(gbd_sweep_plan* plan, void* workspace, size_t bytes, void* stream);
+gbd_status gbd_sweep_run(gbd_sweep_plan* plan, double* scores, void* stream);
+gbd_status gbd_sweep_run_graph(gbd_sweep_plan* plan, double* scores, void* stream);
+gbd_status gbd_sweep_autotune(const gbd_system* system, double diameter, const int32_t* n_across,
+                              const double* overlap_factor, const double* waist_ratio,
+                              int32_t n_instances, const gbd_detector* detector, void* workspace,
+                              size_t bytes, double* scores, void* stream, gbd_shape* best);
+void gbd_sweep_plan_destroy(gbd_sweep_plan* plan);
 
 /* ---------------------------------------------------------------- probes ----------
  * Throughput microbenchmarks of the pipes the field kernels are bound by, on the current

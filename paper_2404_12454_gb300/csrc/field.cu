@@ -15,92 +15,18 @@
 // (hi, lo) pair with TwoSum between tiles.
 #include <math.h>
 
+#include "field_core.cuh"
 #include "gbd_internal.cuh"
 
 namespace {
 
+using gbd::kStages;
+using gbd::kThreads;
+using gbd::kWarps;
+
 __device__ unsigned int g_field_status = 0;
 
-constexpr int kStages = 4;
-constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
-
 __device__ __forceinline__ void record_timeout() { atomicOr(&g_field_status, gbd::kStatusTimeout); }
-
-// After a failed wait: the producer waits (bounded) for the bulk copies it issued that
-// nobody consumed, so no copy lands in shared memory after the CTA has exited.
-// The drain uses at least the default limit even when the wait limit was lowered, since
-// copies complete within microseconds and must not outlive the CTA.
-__device__ void drain(uint64_t* full, int consumed, int issued, uint32_t spins) {
-    const uint32_t lim = spins > gbd::kDefaultWaitSpins ? spins : gbd::kDefaultWaitSpins;
-    for (int k = consumed; k < issued; ++k)
-        gbd::mbar_wait_bounded(&full[k % kStages], (k / kStages) & 1, lim);
-}
-
-// Warp-uniform bounded wait: every lane polls and the warp leaves together, either when
-// all lanes see the phase complete or after `spins` polls.  A completed phase stays
-// visible until this warp releases the stage, so the vote cannot flip back.
-__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, uint32_t spins) {
-    for (uint32_t it = 0; it < spins; ++it) {
-        const bool d = gbd::mbar_try_wait(bar, parity);
-        if (__all_sync(0xffffffffu, d)) return true;
-    }
-    return false;
-}
-
-// Stream of `nt` tiles of `bytes` bytes each from global memory through kStages shared
-// buffers.  Thread 0 is the producer; every warp consumes every tile.
-template <typename T, int kElems>
-struct TileStream {
-    T (*stage)[kElems];
-    uint64_t* full;
-    uint64_t* empty;
-    const T* src;
-    int nt;
-    int issued;
-    uint32_t bytes;
-
-    __device__ void start(int tid) {
-        if (tid == 0) {
-            for (int s = 0; s < kStages; ++s) {
-                gbd::mbar_init(&full[s], 1);
-                gbd::mbar_init(&empty[s], kWarps);
-            }
-            gbd::mbar_fence_init();
-        }
-        __syncthreads();
-        issued = 0;
-        for (; issued < kStages && issued < nt; ++issued)
-            if (tid == 0) {
-                gbd::mbar_arrive_expect_tx(&full[issued], bytes);
-                gbd::bulk_copy_g2s(stage[issued], src + (size_t)issued * kElems, bytes,
-                                   &full[issued]);
-            }
-    }
-    // Wait until tile k is in shared memory (warp-uniform result).
-    __device__ bool acquire(int k, uint32_t spins) {
-        return warp_wait(&full[k % kStages], (k / kStages) & 1, spins);
-    }
-    // This warp is done with tile k; warp 0 refills the stage with tile k + kStages once
-    // every warp has released it.  Warp-uniform result.
-    __device__ bool release(int k, int lane, int warp, uint32_t spins) {
-        const int s = k % kStages;
-        __syncwarp();
-        if (lane == 0) gbd::mbar_arrive(&empty[s]);
-        if (warp != 0 || k + kStages >= nt) return true;
-        bool good = true;
-        if (lane == 0) {
-            good = gbd::mbar_wait_bounded(&empty[s], (k / kStages) & 1, spins);
-            if (good) {
-                gbd::mbar_arrive_expect_tx(&full[s], bytes);
-                gbd::bulk_copy_g2s(stage[s], src + (size_t)(k + kStages) * kElems, bytes, &full[s]);
-            }
-        }
-        good = __shfl_sync(0xffffffffu, good, 0);
-        if (good) ++issued;
-        return good;
-    }
-};
 
 template <int RB, int CB>
 __global__ void __launch_bounds__(kThreads, 2)
@@ -109,12 +35,15 @@ __global__ void __launch_bounds__(kThreads, 2)
     constexpr int kTileF4 = gbd::kMixedFields * gbd::kTile;
     __shared__ __align__(128) float4 stage[kStages][kTileF4];
     __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
+    __shared__ int flag;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int t0 = blockIdx.z * tiles_per_split;
-    TileStream<float4, kTileF4> ts{stage, full, empty, coef + (size_t)t0 * kTileF4,
-                                   min(n_tiles - t0, tiles_per_split), 0, gbd::kMixedTileBytes};
-    ts.start(tid);
+    gbd::init_stream_barriers(full, empty, tid);
+    gbd::TileStream<float4, kTileF4> ts{stage, full, empty, coef + (size_t)t0 * kTileF4,
+                                        min(n_tiles - t0, tiles_per_split), 0,
+                                        gbd::kMixedTileBytes, 0};
+    bool ok = ts.start(tid, spins, &flag);
 
     const int col0 = blockIdx.x * (32 * CB) + lane;
     const int row0 = blockIdx.y * (8 * RB) + warp;
@@ -130,56 +59,14 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
         for (int c = 0; c < CB; ++c) acc[r][c] = hi[r][c] = lo[r][c] = make_float2(0.f, 0.f);
 
-    const float kTwoPi = 6.28318530717958647692f;
     int k = 0;
-    bool ok = true;
-    for (; k < ts.nt; ++k) {
+    for (; ok && k < ts.nt; ++k) {
         if (!ts.acquire(k, spins)) {
             ok = false;
             break;
         }
-        const float4* st = stage[k % kStages];
-#pragma unroll 1
-        for (int b = 0; b < gbd::kTile; ++b) {
-            // (i0, j0, a0, p0) (a1u, p1u, a1v, p1v) (auu, puu, auv, puv) (avv, pvv, -, -)
-            const float4 q0 = st[b];
-            const float4 q1 = st[gbd::kTile + b];
-            const float4 q2 = st[2 * gbd::kTile + b];
-            const float4 q3 = st[3 * gbd::kTile + b];
-            float tu[CB];
-#pragma unroll
-            for (int c = 0; c < CB; ++c) tu[c] = colf[c] - q0.x;
-#pragma unroll
-            for (int r = 0; r < RB; ++r) {
-                const float tv = rowf[r] - q0.y;
-                const float ra = fmaf(tv, fmaf(q3.x, tv, q1.z), q0.z);
-                const float rp = fmaf(tv, fmaf(q3.y, tv, q1.w), q0.w);
-                const float sa = fmaf(q2.z, tv, q1.x);
-                const float sp = fmaf(q2.w, tv, q1.y);
-#pragma unroll
-                for (int c = 0; c < CB; ++c) {
-                    const float ea = fmaf(tu[c], fmaf(q2.x, tu[c], sa), ra);
-                    const float ep = fmaf(tu[c], fmaf(q2.y, tu[c], sp), rp);
-                    const float amp = gbd::mufu_ex2(ea);
-                    const float x = gbd::frac_turns(ep) * kTwoPi;
-                    acc[r][c].x = fmaf(amp, gbd::mufu_cos(x), acc[r][c].x);
-                    acc[r][c].y = fmaf(amp, gbd::mufu_sin(x), acc[r][c].y);
-                }
-            }
-        }
-        // fold this tile's FP32 sums into the compensated (hi, lo) pairs
-#pragma unroll
-        for (int r = 0; r < RB; ++r)
-#pragma unroll
-            for (int c = 0; c < CB; ++c) {
-                float sx, ex, sy, ey;
-                gbd::two_sum(hi[r][c].x, acc[r][c].x, sx, ex);
-                gbd::two_sum(hi[r][c].y, acc[r][c].y, sy, ey);
-                hi[r][c] = make_float2(sx, sy);
-                lo[r][c].x += ex;
-                lo[r][c].y += ey;
-                acc[r][c] = make_float2(0.f, 0.f);
-            }
+        gbd::mixed_tile<RB, CB>(ts.tile(k), colf, rowf, acc);
+        gbd::mixed_fold<RB, CB>(acc, hi, lo);
         if (!ts.release(k, lane, warp, spins)) {
             ok = false;
             ++k;
@@ -188,7 +75,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
     if (!ok) {
         record_timeout();
-        if (tid == 0) drain(full, k, ts.issued, spins);
+        if (tid == 0) ts.drain(k, spins);
         return;
     }
     const size_t npix = (size_t)nx * ny;
@@ -214,13 +101,16 @@ __global__ void __launch_bounds__(kThreads)
     constexpr int kTileD2 = gbd::kF64Fields * gbd::kTile;
     extern __shared__ __align__(128) double2 dyn[];
     __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
+    __shared__ int flag;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int t0 = blockIdx.z * tiles_per_split;
-    TileStream<double2, kTileD2> ts{reinterpret_cast<double2(*)[kTileD2]>(dyn), full, empty,
-                                    coef + (size_t)t0 * kTileD2,
-                                    min(n_tiles - t0, tiles_per_split), 0, gbd::kF64TileBytes};
-    ts.start(tid);
+    gbd::init_stream_barriers(full, empty, tid);
+    gbd::TileStream<double2, kTileD2> ts{reinterpret_cast<double2(*)[kTileD2]>(dyn), full, empty,
+                                         coef + (size_t)t0 * kTileD2,
+                                         min(n_tiles - t0, tiles_per_split), 0,
+                                         gbd::kF64TileBytes, 0};
+    bool ok = ts.start(tid, spins, &flag);
 
     const int col0 = blockIdx.x * (32 * CB) + lane;
     const int row0 = blockIdx.y * (8 * RB) + warp;
@@ -231,13 +121,12 @@ __global__ void __launch_bounds__(kThreads)
         for (int c = 0; c < CB; ++c) acc_re[r][c] = acc_im[r][c] = 0.0;
 
     int k = 0;
-    bool ok = true;
-    for (; k < ts.nt; ++k) {
+    for (; ok && k < ts.nt; ++k) {
         if (!ts.acquire(k, spins)) {
             ok = false;
             break;
         }
-        const double2* st = ts.stage[k % kStages];
+        const double2* st = ts.tile(k);
 #pragma unroll 1
         for (int b = 0; b < gbd::kTile; ++b) {
             // (i0, j0) (a0, p0) (a1u, p1u) (a1v, p1v) (auu, puu) (auv, puv) (avv, pvv)
@@ -276,7 +165,7 @@ __global__ void __launch_bounds__(kThreads)
     }
     if (!ok) {
         record_timeout();
-        if (tid == 0) drain(full, k, ts.issued, spins);
+        if (tid == 0) ts.drain(k, spins);
         return;
     }
     const size_t npix = (size_t)nx * ny;

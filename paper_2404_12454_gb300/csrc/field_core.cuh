@@ -1,0 +1,165 @@
+// Shared building blocks of the field kernels (field.cu) and the persistent sweep kernel
+// (sweep.cu): the TMA tile stream through shared memory and the mixed-precision
+// per-(beamlet, pixel) evaluation of one 64-beamlet tile.
+#pragma once
+
+#include "gbd_internal.cuh"
+
+namespace gbd {
+
+constexpr int kStages = 4;
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+
+// Warp-uniform bounded wait: every lane polls and the warp leaves together, either when
+// all lanes see the phase complete or after `spins` polls.  A completed phase stays
+// visible until this warp releases the stage, so the vote cannot flip back.
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, uint32_t spins) {
+    for (uint32_t it = 0; it < spins; ++it) {
+        const bool d = mbar_try_wait(bar, parity);
+        if (__all_sync(0xffffffffu, d)) return true;
+    }
+    return false;
+}
+
+// Barriers of a tile stream, initialised once per CTA by all threads together.
+__device__ __forceinline__ void init_stream_barriers(uint64_t* full, uint64_t* empty, int tid) {
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kWarps);
+        }
+        mbar_fence_init();
+    }
+    __syncthreads();
+}
+
+// Stream of `nt` tiles of `bytes` bytes from global memory through kStages shared
+// buffers.  Tile k of this stream is the g0 + k-th tile the CTA has streamed (a CTA
+// that runs several streams in turn keeps counting, so barrier phases stay in step).
+// Thread 0 is the producer; every warp consumes every tile.
+template <typename T, int kElems>
+struct TileStream {
+    T (*stage)[kElems];
+    uint64_t* full;
+    uint64_t* empty;
+    const T* src;
+    int nt;
+    int g0;
+    uint32_t bytes;
+    int issued;
+
+    // Producer: once every warp has released the tile that last used the stage, copy
+    // tile k into it.  Thread 0 only.
+    __device__ bool issue(int k, uint32_t spins) {
+        const int g = g0 + k, s = g % kStages;
+        if (g >= kStages && !mbar_wait_bounded(&empty[s], ((g / kStages) - 1) & 1, spins))
+            return false;
+        mbar_arrive_expect_tx(&full[s], bytes);
+        bulk_copy_g2s(stage[s], src + (size_t)k * kElems, bytes, &full[s]);
+        return true;
+    }
+    // Prologue: thread 0 issues the first tiles; block-uniform result through `flag`.
+    __device__ bool start(int tid, uint32_t spins, int* flag) {
+        issued = 0;
+        if (tid == 0) {
+            bool ok = true;
+            const int first = nt < kStages ? nt : kStages;
+            for (; issued < first; ++issued)
+                if (!issue(issued, spins)) {
+                    ok = false;
+                    break;
+                }
+            *flag = ok ? 1 : 0;
+        }
+        __syncthreads();
+        const bool ok = *flag != 0;
+        __syncthreads();
+        return ok;
+    }
+    // Wait until tile k is in shared memory (warp-uniform result).
+    __device__ bool acquire(int k, uint32_t spins) {
+        const int g = g0 + k;
+        return warp_wait(&full[g % kStages], (g / kStages) & 1, spins);
+    }
+    __device__ const T* tile(int k) const { return stage[(g0 + k) % kStages]; }
+    // This warp is done with tile k; warp 0 then refills the stage with tile k + kStages.
+    // Warp-uniform result.
+    __device__ bool release(int k, int lane, int warp, uint32_t spins) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[(g0 + k) % kStages]);
+        if (warp != 0 || k + kStages >= nt) return true;
+        bool good = true;
+        if (lane == 0) good = issue(k + kStages, spins);
+        good = __shfl_sync(0xffffffffu, good, 0) != 0;
+        if (good) ++issued;
+        return good;
+    }
+    // After a failed wait: the producer waits for the copies it issued that nobody
+    // consumed, so none lands in shared memory after the CTA has moved on or exited.
+    // Uses at least the default limit: copies complete within microseconds.
+    __device__ void drain(int consumed, uint32_t spins) {
+        const uint32_t lim = spins > kDefaultWaitSpins ? spins : kDefaultWaitSpins;
+        for (int k = consumed; k < issued; ++k) {
+            const int g = g0 + k;
+            mbar_wait_bounded(&full[g % kStages], (g / kStages) & 1, lim);
+        }
+    }
+};
+
+// One 64-beamlet tile of mixed-precision evaluation on a thread's RB x CB pixels.
+// Record fields: (i0, j0, a0, p0) (a1u, p1u, a1v, p1v) (auu, puu, auv, puv) (avv, pvv, -, -)
+// with log2 |E| = a0 + a1u tu + a1v tv + auu tu^2 + auv tu tv + avv tv^2 and phase/2pi the
+// same in p, tu = i - i0, tv = j - j0.
+template <int RB, int CB>
+__device__ __forceinline__ void mixed_tile(const float4* __restrict__ st, const float (&colf)[CB],
+                                           const float (&rowf)[RB], float2 (&acc)[RB][CB]) {
+    const float kTwoPi = 6.28318530717958647692f;
+#pragma unroll 1
+    for (int b = 0; b < kTile; ++b) {
+        const float4 q0 = st[b];
+        const float4 q1 = st[kTile + b];
+        const float4 q2 = st[2 * kTile + b];
+        const float4 q3 = st[3 * kTile + b];
+        float tu[CB];
+#pragma unroll
+        for (int c = 0; c < CB; ++c) tu[c] = colf[c] - q0.x;
+#pragma unroll
+        for (int r = 0; r < RB; ++r) {
+            const float tv = rowf[r] - q0.y;
+            const float ra = fmaf(tv, fmaf(q3.x, tv, q1.z), q0.z);
+            const float rp = fmaf(tv, fmaf(q3.y, tv, q1.w), q0.w);
+            const float sa = fmaf(q2.z, tv, q1.x);
+            const float sp = fmaf(q2.w, tv, q1.y);
+#pragma unroll
+            for (int c = 0; c < CB; ++c) {
+                const float ea = fmaf(tu[c], fmaf(q2.x, tu[c], sa), ra);
+                const float ep = fmaf(tu[c], fmaf(q2.y, tu[c], sp), rp);
+                const float amp = mufu_ex2(ea);
+                const float x = frac_turns(ep) * kTwoPi;
+                acc[r][c].x = fmaf(amp, mufu_cos(x), acc[r][c].x);
+                acc[r][c].y = fmaf(amp, mufu_sin(x), acc[r][c].y);
+            }
+        }
+    }
+}
+
+// Fold a tile's FP32 sums into compensated (hi, lo) pairs (TwoSum) and clear them.
+template <int RB, int CB>
+__device__ __forceinline__ void mixed_fold(float2 (&acc)[RB][CB], float2 (&hi)[RB][CB],
+                                           float2 (&lo)[RB][CB]) {
+#pragma unroll
+    for (int r = 0; r < RB; ++r)
+#pragma unroll
+        for (int c = 0; c < CB; ++c) {
+            float sx, ex, sy, ey;
+            two_sum(hi[r][c].x, acc[r][c].x, sx, ex);
+            two_sum(hi[r][c].y, acc[r][c].y, sy, ey);
+            hi[r][c] = make_float2(sx, sy);
+            lo[r][c].x += ex;
+            lo[r][c].y += ey;
+            acc[r][c] = make_float2(0.f, 0.f);
+        }
+}
+
+}  // namespace gbd

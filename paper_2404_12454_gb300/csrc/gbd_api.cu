@@ -322,6 +322,31 @@ gbd_status check_field_args(const gbd_beamlet* beamlets, int32_t n, double wavel
 
 gbd_status gbd_set_error(gbd_status st, const char* msg) { return fail(st, "%s", msg); }
 
+gbd_status gbd_check_system(const gbd_system* s) { return check_system(s); }
+gbd_status gbd_check_detector(const gbd_detector* d) { return check_detector(d); }
+gbd_project_params gbd_make_project_params(double wavelength, const gbd_detector* d) {
+    return project_params(wavelength, d);
+}
+int gbd_sm_count() { return sm_count(); }
+uint32_t gbd_wait_spins() { return wait_spins(); }
+
+// Kernel parameters of the shared optics of a trace (the pupil sampling is set by the
+// caller): lens, distance and the Zernike plate expanded into monomials of x/R, y/R.
+gbd_trace_params gbd_make_trace_params(const gbd_system* system, double diameter) {
+    gbd_trace_params p;
+    memset(&p, 0, sizeof(p));
+    p.wavelength = system->wavelength;
+    p.inv_f = isinf(system->focal_length) ? 0.0 : 1.0 / system->focal_length;
+    p.d = system->distance;
+    p.zern_radius = system->n_zern > 0 ? system->zern_radius : 1.0;
+    p.diameter = diameter;
+    int deg = -1;
+    for (int t = 0; t < system->n_zern; ++t)
+        add_zernike(system->noll[t], system->zern_coef[t], p.zpoly, deg);
+    p.zdeg = system->n_zern > 0 ? deg : -1;
+    return p;
+}
+
 // gbd_field on a fixed scratch buffer of known size: the beamlet splits are lowered until
 // the projected records and the split partial fields fit; sizes that do not fit even
 // with one split are rejected before anything is launched.
@@ -374,7 +399,7 @@ int32_t gbd_beamlet_count(const gbd_pupil* pupil) {
 gbd_status gbd_sync(void* stream) {
     cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "gbd_sync");
-    unsigned st = gbd_field_status_read_clear();
+    unsigned st = gbd_field_status_read_clear() | gbd_sweep_status_read_clear();
     if (st & gbd::kStatusTimeout) return fail(GBD_ETIMEOUT, "a device wait gave up (timeout)");
     return GBD_OK;
 }
@@ -396,21 +421,10 @@ gbd_status gbd_trace(const gbd_system* system, const gbd_pupil* pupil, double ov
     if (capacity < n) return fail(GBD_ENOMEM, "capacity %d < %d beamlets", capacity, n);
     if (n > 0 && !out) return fail(GBD_EINVAL, "out is NULL");
     if (reinterpret_cast<uintptr_t>(out) & 15u) return fail(GBD_EINVAL, "out must be 16-byte aligned");
-    gbd_trace_params p;
-    memset(&p, 0, sizeof(p));
-    p.wavelength = system->wavelength;
-    p.inv_f = isinf(system->focal_length) ? 0.0 : 1.0 / system->focal_length;
-    p.d = system->distance;
-    p.zern_radius = system->n_zern > 0 ? system->zern_radius : 1.0;
-    p.diameter = pupil->diameter;
+    gbd_trace_params p = gbd_make_trace_params(system, pupil->diameter);
     p.overlap_factor = overlap_factor;
     p.waist_ratio = waist_ratio;
     p.n_across = pupil->n_across;
-    p.zdeg = -1;
-    int deg = -1;
-    for (int t = 0; t < system->n_zern; ++t)
-        add_zernike(system->noll[t], system->zern_coef[t], p.zpoly, deg);
-    p.zdeg = system->n_zern > 0 ? deg : -1;
     cudaError_t e = gbd_launch_trace(p, 1, pupil->n_across, nullptr, out,
                                      static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "gbd_trace launch");

@@ -179,7 +179,8 @@ __host__ __device__ __forceinline__ int plate_index(int a, int b) {
 }
 }  // namespace gbd
 
-// One instance of a batched trace: its own pupil sampling, written from record `offset`.
+// One instance of a batched trace: its own pupil sampling, written from record `offset`
+// (`reserved` carries the instance's beamlet count for the batched projection).
 struct gbd_instance_dev {
     int32_t n_across;
     int32_t reserved;
@@ -191,6 +192,10 @@ struct gbd_instance_dev {
 // the optics in p, each from its own record offset.
 cudaError_t gbd_launch_trace(const gbd_trace_params& p, int n_instances, int max_n_across,
                              const gbd_instance_dev* d_inst, gbd_beamlet* out, cudaStream_t s);
+// Batched trace + mixed projection straight into the tiled records (sweep set-up).
+cudaError_t gbd_launch_trace_project(const gbd_trace_params& p, int n_instances, int max_n_across,
+                                     const gbd_instance_dev* d_inst, const gbd_project_params& g,
+                                     float4* out, cudaStream_t s);
 cudaError_t gbd_launch_project(const gbd_beamlet* b, int n, const gbd_project_params& p,
                                int precision, void* coeffs, cudaStream_t s);
 cudaError_t gbd_launch_field_kernel(int precision, const void* coeffs, int n_tiles,
@@ -200,6 +205,13 @@ cudaError_t gbd_launch_field_reduce(int precision, const gbd_project_params& p, 
                                     const double2* partial, void* out, cudaStream_t s);
 int gbd_field_occupancy(int precision, int rb, int cb);
 gbd_status gbd_set_error(gbd_status st, const char* msg);  // sets gbd_last_error()
+gbd_status gbd_check_system(const gbd_system* s);
+gbd_status gbd_check_detector(const gbd_detector* d);
+gbd_project_params gbd_make_project_params(double wavelength, const gbd_detector* d);
+gbd_trace_params gbd_make_trace_params(const gbd_system* system, double diameter);
+int gbd_sm_count();
+uint32_t gbd_wait_spins();
+unsigned gbd_sweep_status_read_clear();
 gbd_status gbd_field_fixed_scratch(const gbd_beamlet* beamlets, int32_t n, double wavelength,
                                    const gbd_detector* detector, int32_t precision,
                                    void* scratch, size_t scratch_bytes, void* out,

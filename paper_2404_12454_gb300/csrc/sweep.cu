@@ -1,0 +1,498 @@
+// Batched parameter sweep (Sec. 6): many GBD instances sharing the optics and detector but
+// differing in beamlets across, overlap factor and waist ratio, each scored by the RMS
+// difference of |E|/|E(centre)| to the Airy amplitude inside the third dark ring.
+//
+// One sweep = a batched trace + projection kernel writing every instance's records at
+// tile-aligned offsets, one persistent field kernel, and a finalize kernel.  The field
+// kernel runs one CTA per resident slot; each CTA takes (instance, pixel block) work
+// items from an atomic counter in longest-first order (instances with the most beamlet
+// tiles first), evaluates the instance's beamlets on its pixels exactly as
+// field_mixed_kernel does, and folds the score's moments over its pixels
+// (S2 = sum |E|^2, S1 = sum |E| A, S0 = sum A^2, n, and |E| at the centre pixel) into a
+// per-item slot.  The finalize kernel sums each instance's items in pixel-block order,
+// so the result does not depend on which CTA ran which item:
+//     score = sqrt((S2/e0^2 - 2 S1/e0 + S0) / n).
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "field_core.cuh"
+#include "gbd_internal.cuh"
+
+namespace {
+
+using gbd::kStages;
+using gbd::kThreads;
+using gbd::kWarps;
+
+__device__ unsigned int g_sweep_status = 0;
+
+constexpr int kMoments = 5;  // S2, S1, S0, n, e0
+
+// |2 J1(x)/x| with x = pi r / (lambda F#), and whether r <= r3, per detector pixel.
+__global__ void __launch_bounds__(256) airy_table_kernel(int nx, int ny, double px, double py,
+                                                         double lam_fnum, double r3,
+                                                         double2* __restrict__ out) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nx * ny) return;
+    const int i = p % nx, j = p / nx;
+    const double sx = (i - nx / 2) * px, sy = (j - ny / 2) * py;
+    const double r = hypot(sx, sy);
+    const double x = M_PI * r / lam_fnum;
+    const double a = x == 0.0 ? 1.0 : fabs(2.0 * j1(x) / x);
+    out[p] = make_double2(a, r <= r3 ? 1.0 : 0.0);
+}
+
+template <int RB, int CB>
+__global__ void __launch_bounds__(kThreads, 2)
+    sweep_kernel(const float4* __restrict__ coef, const int2* __restrict__ inst_tiles,
+                 const int2* __restrict__ items, int n_items, int tiles_x, int n_blocks, int nx,
+                 int ny, const double2* __restrict__ airy, double* __restrict__ moments,
+                 int* __restrict__ counter, uint32_t spins) {
+    constexpr int kTileF4 = gbd::kMixedFields * gbd::kTile;
+    __shared__ __align__(128) float4 stage[kStages][kTileF4];
+    __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
+    __shared__ int flag, s_item;
+    __shared__ double red[kWarps][kMoments];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    gbd::init_stream_barriers(full, empty, tid);
+    int g = 0;  // tiles this CTA has streamed so far (keeps the barrier phases in step)
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= n_items) break;
+        const int2 it = items[item];           // (instance, pixel block)
+        const int2 tt = inst_tiles[it.x];      // (first tile, tiles)
+        gbd::TileStream<float4, kTileF4> ts{stage, full, empty, coef + (size_t)tt.x * kTileF4,
+                                            tt.y, g, gbd::kMixedTileBytes, 0};
+        bool ok = ts.start(tid, spins, &flag);
+
+        const int col0 = (it.y % tiles_x) * (32 * CB) + lane;
+        const int row0 = (it.y / tiles_x) * (8 * RB) + warp;
+        float colf[CB], rowf[RB];
+#pragma unroll
+        for (int c = 0; c < CB; ++c) colf[c] = (float)(col0 + 32 * c);
+#pragma unroll
+        for (int r = 0; r < RB; ++r) rowf[r] = (float)(row0 + 8 * r);
+        float2 acc[RB][CB], hi[RB][CB], lo[RB][CB];
+#pragma unroll
+        for (int r = 0; r < RB; ++r)
+#pragma unroll
+            for (int c = 0; c < CB; ++c) acc[r][c] = hi[r][c] = lo[r][c] = make_float2(0.f, 0.f);
+
+        int k = 0;
+        for (; ok && k < ts.nt; ++k) {
+            if (!ts.acquire(k, spins)) {
+                ok = false;
+                break;
+            }
+            gbd::mixed_tile<RB, CB>(ts.tile(k), colf, rowf, acc);
+            gbd::mixed_fold<RB, CB>(acc, hi, lo);
+            if (!ts.release(k, lane, warp, spins)) {
+                ok = false;
+                ++k;
+                break;
+            }
+        }
+        // every thread reaches this vote (failed waits end their loops), so the CTA
+        // leaves together when any warp gave up
+        if (!__syncthreads_and(ok)) {
+            atomicOr(&g_sweep_status, gbd::kStatusTimeout);
+            if (tid == 0) ts.drain(k, spins);
+            return;
+        }
+        g += ts.nt;
+
+        double m[kMoments] = {0.0, 0.0, 0.0, 0.0, -1.0};
+#pragma unroll
+        for (int r = 0; r < RB; ++r) {
+            const int row = row0 + 8 * r;
+            if (row >= ny) continue;
+#pragma unroll
+            for (int c = 0; c < CB; ++c) {
+                const int col = col0 + 32 * c;
+                if (col >= nx) continue;
+                const double re = (double)hi[r][c].x + (double)lo[r][c].x;
+                const double im = (double)hi[r][c].y + (double)lo[r][c].y;
+                const double mag = sqrt(re * re + im * im);
+                const double2 A = airy[(size_t)row * nx + col];
+                if (A.y != 0.0) {
+                    m[0] += mag * mag;
+                    m[1] += mag * A.x;
+                    m[2] += A.x * A.x;
+                    m[3] += 1.0;
+                }
+                if (row == ny / 2 && col == nx / 2) m[4] = mag;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) m[q] += __shfl_xor_sync(0xffffffffu, m[q], o);
+            m[4] = fmax(m[4], __shfl_xor_sync(0xffffffffu, m[4], o));
+        }
+        if (lane == 0)
+#pragma unroll
+            for (int q = 0; q < kMoments; ++q) red[warp][q] = m[q];
+        __syncthreads();
+        if (tid == 0) {
+            double s[kMoments] = {0.0, 0.0, 0.0, 0.0, -1.0};
+            for (int w = 0; w < kWarps; ++w) {
+                for (int q = 0; q < 4; ++q) s[q] += red[w][q];
+                s[4] = fmax(s[4], red[w][4]);
+            }
+            double* dst = moments + ((size_t)it.x * n_blocks + it.y) * kMoments;
+            for (int q = 0; q < kMoments; ++q) dst[q] = s[q];
+        }
+    }
+}
+
+// Per instance, the moments of its pixel blocks summed in block order, then the score.
+__global__ void __launch_bounds__(128) sweep_finalize_kernel(const double* __restrict__ moments,
+                                                             int n_inst, int n_blocks,
+                                                             double* __restrict__ scores) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_inst) return;
+    double s[kMoments] = {0.0, 0.0, 0.0, 0.0, -1.0};
+    for (int t = 0; t < n_blocks; ++t) {
+        const double* m = moments + ((size_t)k * n_blocks + t) * kMoments;
+        for (int q = 0; q < 4; ++q) s[q] += m[q];
+        s[4] = fmax(s[4], m[4]);
+    }
+    const double e0 = s[4];
+    double score = nan("");
+    if (e0 > 0.0 && s[3] > 0.0)
+        score = sqrt(fmax(0.0, (s[0] / (e0 * e0) - 2.0 * s[1] / e0 + s[2]) / s[3]));
+    scores[k] = score;
+}
+
+typedef cudaError_t (*sweep_launch_fn)(dim3, cudaStream_t, const float4*, const int2*, const int2*,
+                                       int, int, int, int, int, const double2*, double*, int*,
+                                       uint32_t);
+
+template <int RB, int CB>
+cudaError_t launch_sweep(dim3 grid, cudaStream_t s, const float4* coef, const int2* it_tiles,
+                         const int2* items, int n_items, int tiles_x, int n_blocks, int nx, int ny,
+                         const double2* airy, double* moments, int* counter, uint32_t spins) {
+    sweep_kernel<RB, CB><<<grid, kThreads, 0, s>>>(coef, it_tiles, items, n_items, tiles_x, n_blocks,
+                                                   nx, ny, airy, moments, counter, spins);
+    return cudaGetLastError();
+}
+
+struct SweepShape {
+    int rb, cb;
+    sweep_launch_fn fn;
+    const void* kernel;
+};
+
+const SweepShape kSweepShapes[] = {
+    {1, 4, launch_sweep<1, 4>, (const void*)sweep_kernel<1, 4>},
+    {2, 2, launch_sweep<2, 2>, (const void*)sweep_kernel<2, 2>},
+    {2, 4, launch_sweep<2, 4>, (const void*)sweep_kernel<2, 4>},
+    {4, 2, launch_sweep<4, 2>, (const void*)sweep_kernel<4, 2>},
+};
+
+const SweepShape* find_sweep_shape(int rb, int cb) {
+    for (const auto& e : kSweepShapes)
+        if (e.rb == rb && e.cb == cb) return &e;
+    return nullptr;
+}
+
+size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+}  // namespace
+
+// ------------------------------------------------------------------- plan --
+
+struct gbd_sweep_plan {
+    gbd_trace_params tp;
+    gbd_project_params pp;
+    double lam_fnum, r3;
+    int n_inst, max_n, rb, cb, tiles_x, tiles_y, n_blocks, n_items;
+    int64_t total_tiles, total_beamlets;
+    double evals;
+    std::vector<gbd_instance_dev> inst;
+    std::vector<int2> inst_tiles;
+    std::vector<int2> items;
+    size_t off_inst, off_itiles, off_items, off_airy, off_moments, off_counter, off_coef, bytes;
+    char* ws = nullptr;
+    int device = -1;
+    cudaGraphExec_t graph = nullptr;
+    double* graph_scores = nullptr;
+    cudaStream_t graph_stream = nullptr;
+};
+
+unsigned gbd_sweep_status_read_clear() {
+    unsigned v = 0, zero = 0;
+    if (cudaMemcpyFromSymbol(&v, g_sweep_status, sizeof(v)) != cudaSuccess) return 0;
+    if (v) cudaMemcpyToSymbol(g_sweep_status, &zero, sizeof(zero));
+    return v;
+}
+
+static gbd_status sweep_enqueue(gbd_sweep_plan* P, double* scores, cudaStream_t s) {
+    const SweepShape* sh = find_sweep_shape(P->rb, P->cb);
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sh->kernel, kThreads, 0) != cudaSuccess ||
+        occ < 1)
+        occ = 1;
+    char* w = P->ws;
+    int* counter = reinterpret_cast<int*>(w + P->off_counter);
+    float4* coef = reinterpret_cast<float4*>(w + P->off_coef);
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), s);
+    if (e == cudaSuccess)
+        e = gbd_launch_trace_project(P->tp, P->n_inst, P->max_n,
+                                     reinterpret_cast<const gbd_instance_dev*>(w + P->off_inst), P->pp,
+                                     coef, s);
+    if (e == cudaSuccess) {
+        const int grid = std::max(1, std::min(P->n_items, occ * gbd_sm_count()));
+        e = sh->fn(dim3(grid), s, coef, reinterpret_cast<const int2*>(w + P->off_itiles),
+                   reinterpret_cast<const int2*>(w + P->off_items), P->n_items, P->tiles_x,
+                   P->n_blocks, P->pp.nx, P->pp.ny, reinterpret_cast<const double2*>(w + P->off_airy),
+                   reinterpret_cast<double*>(w + P->off_moments), counter, gbd_wait_spins());
+    }
+    if (e == cudaSuccess) {
+        sweep_finalize_kernel<<<(P->n_inst + 127) / 128, 128, 0, s>>>(
+            reinterpret_cast<const double*>(w + P->off_moments), P->n_inst, P->n_blocks, scores);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return gbd_set_error(GBD_ECUDA, cudaGetErrorString(e));
+    return GBD_OK;
+}
+
+extern "C" {
+
+gbd_status gbd_sweep_plan_create(const gbd_system* system, double diameter, const int32_t* n_across,
+                                 const double* overlap_factor, const double* waist_ratio,
+                                 int32_t n_instances, const gbd_detector* detector,
+                                 const gbd_shape* shape, gbd_sweep_plan** plan) {
+    if (!plan) return gbd_set_error(GBD_EINVAL, "plan is NULL");
+    *plan = nullptr;
+    gbd_status st = gbd_check_system(system);
+    if (st != GBD_OK) return st;
+    if ((st = gbd_check_detector(detector)) != GBD_OK) return st;
+    if (!(isfinite(diameter) && diameter > 0.0))
+        return gbd_set_error(GBD_EINVAL, "diameter must be finite and > 0");
+    if (n_instances < 1 || n_instances > (1 << 20))
+        return gbd_set_error(GBD_EINVAL, "n_instances must be in [1, 2^20]");
+    if (!n_across || !overlap_factor || !waist_ratio)
+        return gbd_set_error(GBD_EINVAL, "instance arrays are NULL");
+    if (isinf(system->focal_length))
+        return gbd_set_error(GBD_EINVAL, "the Airy score needs a lens (finite focal length)");
+    const int rb = shape ? shape->rows_per_thread : 2, cb = shape ? shape->cols_per_thread : 4;
+    if (!find_sweep_shape(rb, cb)) return gbd_set_error(GBD_EINVAL, "unsupported sweep shape");
+    gbd_sweep_plan* P = new gbd_sweep_plan();
+    P->tp = gbd_make_trace_params(system, diameter);
+    P->pp = gbd_make_project_params(system->wavelength, detector);
+    P->lam_fnum = system->wavelength * fabs(system->focal_length) / diameter;
+    P->r3 = 10.173468135062722 * P->lam_fnum / M_PI;  // third zero of J1
+    P->n_inst = n_instances;
+    P->rb = rb;
+    P->cb = cb;
+    P->tiles_x = (detector->nx + 32 * cb - 1) / (32 * cb);
+    P->tiles_y = (detector->ny + 8 * rb - 1) / (8 * rb);
+    P->n_blocks = P->tiles_x * P->tiles_y;
+    P->max_n = 0;
+    int64_t tile = 0;
+    P->total_beamlets = 0;
+    for (int k = 0; k < n_instances; ++k) {
+        gbd_pupil pu{diameter, n_across[k], 0};
+        const int32_t nb = gbd_beamlet_count(&pu);
+        if (nb < 1 || !(overlap_factor[k] > 0.0) || !(waist_ratio[k] > 0.0) ||
+            !isfinite(overlap_factor[k]) || !isfinite(waist_ratio[k])) {
+            delete P;
+            return gbd_set_error(GBD_EINVAL, "instance with invalid n_across / OF / WR");
+        }
+        const int nt = (nb + gbd::kTile - 1) / gbd::kTile;
+        gbd_instance_dev I;
+        I.n_across = n_across[k];
+        I.reserved = nb;
+        I.offset = tile * gbd::kTile;
+        I.overlap_factor = overlap_factor[k];
+        I.waist_ratio = waist_ratio[k];
+        P->inst.push_back(I);
+        P->inst_tiles.push_back(make_int2((int)tile, nt));
+        tile += nt;
+        P->total_beamlets += nb;
+        P->max_n = std::max(P->max_n, (int)n_across[k]);
+    }
+    if (tile > INT32_MAX / 2) {
+        delete P;
+        return gbd_set_error(GBD_EINVAL, "sweep too large");
+    }
+    P->total_tiles = tile;
+    P->evals = (double)P->total_beamlets * detector->nx * detector->ny;
+    // longest first: instances with more beamlet tiles run first
+    std::vector<int> order(n_instances);
+    for (int k = 0; k < n_instances; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return P->inst_tiles[a].y > P->inst_tiles[b].y; });
+    for (int k : order)
+        for (int t = 0; t < P->n_blocks; ++t) P->items.push_back(make_int2(k, t));
+    P->n_items = (int)P->items.size();
+    size_t off = 0;
+    P->off_counter = off;
+    off += 256;
+    P->off_inst = off;
+    off = align256(off + sizeof(gbd_instance_dev) * n_instances);
+    P->off_itiles = off;
+    off = align256(off + sizeof(int2) * n_instances);
+    P->off_items = off;
+    off = align256(off + sizeof(int2) * P->items.size());
+    P->off_airy = off;
+    off = align256(off + sizeof(double2) * detector->nx * detector->ny);
+    P->off_moments = off;
+    off = align256(off + sizeof(double) * kMoments * (size_t)n_instances * P->n_blocks);
+    P->off_coef = off;
+    off = align256(off + (size_t)tile * gbd::kMixedTileBytes);
+    P->bytes = off;
+    *plan = P;
+    return GBD_OK;
+}
+
+size_t gbd_sweep_workspace_bytes(const gbd_sweep_plan* plan) { return plan ? plan->bytes : 0; }
+
+gbd_status gbd_sweep_info(const gbd_sweep_plan* plan, double* evals, int64_t* beamlets,
+                          int32_t* items) {
+    if (!plan) return gbd_set_error(GBD_EINVAL, "plan is NULL");
+    if (evals) *evals = plan->evals;
+    if (beamlets) *beamlets = plan->total_beamlets;
+    if (items) *items = plan->n_items;
+    return GBD_OK;
+}
+
+gbd_status gbd_sweep_bind(gbd_sweep_plan* P, void* workspace, size_t bytes, void* stream) {
+    if (!P) return gbd_set_error(GBD_EINVAL, "plan is NULL");
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255u))
+        return gbd_set_error(GBD_EINVAL, "workspace must be non-NULL and 256-byte aligned");
+    if (bytes < P->bytes) return gbd_set_error(GBD_ENOMEM, "sweep workspace too small");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (P->graph) {
+        cudaGraphExecDestroy(P->graph);
+        P->graph = nullptr;
+    }
+    P->ws = static_cast<char*>(workspace);
+    cudaGetDevice(&P->device);
+    char* w = P->ws;
+    cudaError_t e = cudaMemcpyAsync(w + P->off_inst, P->inst.data(),
+                                    sizeof(gbd_instance_dev) * P->inst.size(),
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(w + P->off_itiles, P->inst_tiles.data(),
+                            sizeof(int2) * P->inst_tiles.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(w + P->off_items, P->items.data(), sizeof(int2) * P->items.size(),
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        const int npix = P->pp.nx * P->pp.ny;
+        airy_table_kernel<<<(npix + 255) / 256, 256, 0, s>>>(
+            P->pp.nx, P->pp.ny, P->pp.px, P->pp.py, P->lam_fnum, P->r3,
+            reinterpret_cast<double2*>(w + P->off_airy));
+        e = cudaGetLastError();
+    }
+    // the host tables are read by the copies above: finish before returning
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return gbd_set_error(GBD_ECUDA, cudaGetErrorString(e));
+    return GBD_OK;
+}
+
+gbd_status gbd_sweep_run(gbd_sweep_plan* P, double* scores, void* stream) {
+    if (!P || !P->ws) return gbd_set_error(GBD_EINVAL, "plan is NULL or not bound");
+    if (!scores) return gbd_set_error(GBD_EINVAL, "scores is NULL");
+    return sweep_enqueue(P, scores, static_cast<cudaStream_t>(stream));
+}
+
+gbd_status gbd_sweep_run_graph(gbd_sweep_plan* P, double* scores, void* stream) {
+    if (!P || !P->ws) return gbd_set_error(GBD_EINVAL, "plan is NULL or not bound");
+    if (!scores) return gbd_set_error(GBD_EINVAL, "scores is NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (s == nullptr || s == cudaStreamLegacy || s == cudaStreamPerThread)
+        return gbd_set_error(GBD_EINVAL, "graph capture needs a created (non-default) stream");
+    if (!P->graph || P->graph_scores != scores || P->graph_stream != s) {
+        if (P->graph) {
+            cudaGraphExecDestroy(P->graph);
+            P->graph = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return gbd_set_error(GBD_ECUDA, cudaGetErrorString(e));
+        gbd_status st = sweep_enqueue(P, scores, s);
+        e = cudaStreamEndCapture(s, &g);
+        if (st != GBD_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (e != cudaSuccess) return gbd_set_error(GBD_ECUDA, cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&P->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            P->graph = nullptr;
+            return gbd_set_error(GBD_ECUDA, cudaGetErrorString(e));
+        }
+        P->graph_scores = scores;
+        P->graph_stream = s;
+    }
+    cudaError_t e = cudaGraphLaunch(P->graph, s);
+    if (e != cudaSuccess) return gbd_set_error(GBD_ECUDA, cudaGetErrorString(e));
+    return GBD_OK;
+}
+
+void gbd_sweep_plan_destroy(gbd_sweep_plan* P) {
+    if (!P) return;
+    if (P->graph) cudaGraphExecDestroy(P->graph);
+    delete P;
+}
+
+}  // extern "C"
+
+extern "C" gbd_status gbd_sweep_autotune(const gbd_system* system, double diameter,
+                                         const int32_t* n_across, const double* overlap_factor,
+                                         const double* waist_ratio, int32_t n_instances,
+                                         const gbd_detector* detector, void* workspace,
+                                         size_t bytes, double* scores, void* stream,
+                                         gbd_shape* best) {
+    if (!best) return gbd_set_error(GBD_EINVAL, "best is NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return gbd_set_error(GBD_ECUDA, "autotune events");
+    gbd_shape win{0, 0, 1, 1e30f};
+    gbd_status st = GBD_OK;
+    for (const auto& sh : kSweepShapes) {
+        gbd_shape cand{sh.rb, sh.cb, 1, 0.f};
+        gbd_sweep_plan* P = nullptr;
+        st = gbd_sweep_plan_create(system, diameter, n_across, overlap_factor, waist_ratio,
+                                   n_instances, detector, &cand, &P);
+        if (st != GBD_OK) break;
+        if (P->bytes > bytes) {
+            gbd_sweep_plan_destroy(P);
+            continue;
+        }
+        st = gbd_sweep_bind(P, workspace, bytes, stream);
+        float ms = 1e30f;
+        for (int rep = 0; st == GBD_OK && rep < 2; ++rep) {
+            cudaEventRecord(e0, s);
+            st = gbd_sweep_run(P, scores, stream);
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) st = gbd_set_error(GBD_ECUDA, "autotune");
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (rep > 0) ms = t;
+        }
+        gbd_sweep_plan_destroy(P);
+        if (st != GBD_OK) break;
+        if (ms < win.ms) {
+            win = cand;
+            win.ms = ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != GBD_OK) return st;
+    if (win.rows_per_thread == 0) return gbd_set_error(GBD_ENOMEM, "no shape fits the workspace");
+    *best = win;
+    return GBD_OK;
+}

@@ -270,15 +270,9 @@ __device__ Quad project_one(const gbd_beamlet& b, const gbd_project_params& G) {
     return q;
 }
 
-__global__ void __launch_bounds__(128) project_mixed_kernel(const gbd_beamlet* __restrict__ b, int n,
-                                                            int n_pad, gbd_project_params G,
-                                                            float4* __restrict__ out) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n_pad) return;
+// Mixed-precision record of beamlet `t` in the tiled layout (4 float4 fields per beamlet).
+__device__ __forceinline__ void write_mixed(float4* __restrict__ out, long long t, const Quad& q) {
     float4 f0, f1, f2, f3;
-    Quad q;
-    q.pad = true;
-    if (t < n) q = project_one(b[t], G);
     if (q.pad) {
         f0 = make_float4(0.f, 0.f, gbd::kPadLog2Amp, 0.f);
         f1 = f2 = f3 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -289,11 +283,22 @@ __global__ void __launch_bounds__(128) project_mixed_kernel(const gbd_beamlet* _
         f3 = make_float4((float)q.a[5], (float)q.p[5], 0.f, 0.f);
     }
     float4* tile = out + (size_t)(t / gbd::kTile) * gbd::kMixedFields * gbd::kTile;
-    const int l = t % gbd::kTile;
+    const int l = (int)(t % gbd::kTile);
     tile[l] = f0;
     tile[gbd::kTile + l] = f1;
     tile[2 * gbd::kTile + l] = f2;
     tile[3 * gbd::kTile + l] = f3;
+}
+
+__global__ void __launch_bounds__(128) project_mixed_kernel(const gbd_beamlet* __restrict__ b, int n,
+                                                            int n_pad, gbd_project_params G,
+                                                            float4* __restrict__ out) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_pad) return;
+    Quad q;
+    q.pad = true;
+    if (t < n) q = project_one(b[t], G);
+    write_mixed(out, t, q);
 }
 
 __global__ void __launch_bounds__(128) project_f64_kernel(const gbd_beamlet* __restrict__ b, int n,
@@ -318,7 +323,49 @@ __global__ void __launch_bounds__(128) project_f64_kernel(const gbd_beamlet* __r
     for (int m = 0; m < gbd::kF64Fields; ++m) tile[m * gbd::kTile + l] = f[m];
 }
 
+// Batched trace + projection for a parameter sweep: instance blockIdx.y (its own N, OF,
+// WR) writes its mixed-precision records from record `offset` (a tile boundary), and the
+// CTA of its first row also writes the padding records up to the next tile boundary.
+__global__ void __launch_bounds__(128)
+    trace_project_kernel(gbd_trace_params P, const gbd_instance_dev* __restrict__ inst,
+                         gbd_project_params G, float4* __restrict__ out) {
+    const gbd_instance_dev I = inst[blockIdx.y];
+    const int N = I.n_across;
+    const int j = blockIdx.x;
+    if (j >= N) return;
+    __shared__ long long warp_sum[4];
+    long long acc = 0;
+    for (int q = threadIdx.x; q < j; q += blockDim.x) acc += row_extent(q, N) + 1;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    const long long row_off = warp_sum[0] + warp_sum[1] + warp_sum[2] + warp_sum[3];
+    if (j == 0) {
+        const long long nb = I.reserved;  // beamlets of this instance
+        const long long pad_end = (nb + gbd::kTile - 1) / gbd::kTile * gbd::kTile;
+        Quad q;
+        q.pad = true;
+        for (long long t = nb + threadIdx.x; t < pad_end; t += blockDim.x) write_mixed(out, I.offset + t, q);
+    }
+    const int a = row_extent(j, N);
+    if (a < 0) return;
+    const int i_lo = ((N - 1) - a) / 2;
+    for (int t = threadIdx.x; t <= a; t += blockDim.x) {
+        gbd_beamlet b;
+        trace_one(P, N, I.overlap_factor, I.waist_ratio, i_lo + t, j, &b);
+        write_mixed(out, I.offset + row_off + t, project_one(b, G));
+    }
+}
+
 }  // namespace
+
+cudaError_t gbd_launch_trace_project(const gbd_trace_params& p, int n_instances, int max_n_across,
+                                     const gbd_instance_dev* d_inst, const gbd_project_params& g,
+                                     float4* out, cudaStream_t s) {
+    dim3 grid(max_n_across, n_instances);
+    trace_project_kernel<<<grid, 128, 0, s>>>(p, d_inst, g, out);
+    return cudaGetLastError();
+}
 
 cudaError_t gbd_launch_trace(const gbd_trace_params& p, int n_instances, int max_n_across,
                              const gbd_instance_dev* d_inst, gbd_beamlet* out, cudaStream_t s) {

@@ -79,6 +79,25 @@ _SIGS = {
                                           ctypes.POINTER(gbd_detector), ctypes.c_int32, _P,
                                           ctypes.c_size_t, _P, _P, ctypes.POINTER(gbd_shape)]),
     "gbd_probe_peaks": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double)]),
+    "gbd_sweep_plan_create": (ctypes.c_int, [ctypes.POINTER(gbd_system), ctypes.c_double,
+                                             ctypes.POINTER(ctypes.c_int32),
+                                             ctypes.POINTER(ctypes.c_double),
+                                             ctypes.POINTER(ctypes.c_double), ctypes.c_int32,
+                                             ctypes.POINTER(gbd_detector), ctypes.POINTER(gbd_shape),
+                                             ctypes.POINTER(ctypes.c_void_p)]),
+    "gbd_sweep_workspace_bytes": (ctypes.c_size_t, [_P]),
+    "gbd_sweep_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]),
+    "gbd_sweep_bind": (ctypes.c_int, [_P, _P, ctypes.c_size_t, _P]),
+    "gbd_sweep_run": (ctypes.c_int, [_P, _P, _P]),
+    "gbd_sweep_run_graph": (ctypes.c_int, [_P, _P, _P]),
+    "gbd_sweep_autotune": (ctypes.c_int, [ctypes.POINTER(gbd_system), ctypes.c_double,
+                                          ctypes.POINTER(ctypes.c_int32),
+                                          ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_double), ctypes.c_int32,
+                                          ctypes.POINTER(gbd_detector), _P, ctypes.c_size_t, _P, _P,
+                                          ctypes.POINTER(gbd_shape)]),
+    "gbd_sweep_plan_destroy": (None, [_P]),
     "gbd_field_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_double,
                                          ctypes.POINTER(gbd_detector), ctypes.c_int32, _P, _P]),
     "gbd_timing_enable": (ctypes.c_int, [ctypes.c_int32]),
@@ -259,6 +278,76 @@ def gbd_field_noalloc(beamlets, n_beamlets: int, wavelength: float, detector, pr
     _check(lib().gbd_field_noalloc(_ptr(beamlets), int(n_beamlets), float(wavelength),
                                    ctypes.byref(make_detector(detector)), int(precision),
                                    _ptr(field_out), _stream(stream)))
+
+
+def _instance_arrays(n_across, overlap_factor, waist_ratio):
+    n = len(n_across)
+    if not (len(overlap_factor) == n and len(waist_ratio) == n):
+        raise ValueError("instance arrays differ in length")
+    a = (ctypes.c_int32 * n)(*[int(v) for v in n_across])
+    b = (ctypes.c_double * n)(*[float(v) for v in overlap_factor])
+    c = (ctypes.c_double * n)(*[float(v) for v in waist_ratio])
+    return n, a, b, c
+
+
+class SweepPlan:
+    """A bound batched sweep (gbd_sweep_plan_* / gbd_sweep_bind): n instances sharing
+    the optics and detector, each with its own (n_across, overlap_factor, waist_ratio);
+    run() returns the Airy scores as a float64 CUDA tensor."""
+
+    def __init__(self, system, diameter, n_across, overlap_factor, waist_ratio, detector,
+                 shape: Optional[Tuple[int, int]] = None, stream=None, device="cuda"):
+        import torch
+        n, a, b, c = _instance_arrays(n_across, overlap_factor, waist_ratio)
+        self.n = n
+        self._plan = ctypes.c_void_p()
+        sh = gbd_shape(shape[0], shape[1], 1, 0.0) if shape else None
+        _check(lib().gbd_sweep_plan_create(ctypes.byref(make_system(system)), float(diameter), a, b,
+                                           c, n, ctypes.byref(make_detector(detector)),
+                                           ctypes.byref(sh) if sh else None,
+                                           ctypes.byref(self._plan)))
+        self.bytes = int(lib().gbd_sweep_workspace_bytes(self._plan))
+        self.ws = torch.empty(self.bytes, dtype=torch.uint8, device=device)
+        self.scores = torch.empty(n, dtype=torch.float64, device=device)
+        _check(lib().gbd_sweep_bind(self._plan, _ptr(self.ws), ctypes.c_size_t(self.bytes),
+                                    _stream(stream)))
+        ev, nb, items = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int32()
+        _check(lib().gbd_sweep_info(self._plan, ctypes.byref(ev), ctypes.byref(nb),
+                                    ctypes.byref(items)))
+        self.evals, self.beamlets, self.items = float(ev.value), int(nb.value), int(items.value)
+
+    def run(self, stream=None, graph: bool = False):
+        fn = lib().gbd_sweep_run_graph if graph else lib().gbd_sweep_run
+        _check(fn(self._plan, _ptr(self.scores), _stream(stream)))
+        return self.scores
+
+    def close(self):
+        if getattr(self, "_plan", None) is not None and self._plan.value:
+            lib().gbd_sweep_plan_destroy(self._plan)
+            self._plan = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sweep_plan(sw, shape=None, stream=None) -> SweepPlan:
+    """SweepPlan for a workloads.Sweep description."""
+    return SweepPlan(sw.system, sw.diameter, sw.n_across, sw.overlap_factor, sw.waist_ratio,
+                     sw.detector, shape, stream)
+
+
+def gbd_sweep_autotune(system, diameter, n_across, overlap_factor, waist_ratio, detector,
+                       workspace, scores, stream=None) -> Tuple[int, int, float]:
+    n, a, b, c = _instance_arrays(n_across, overlap_factor, waist_ratio)
+    sh = gbd_shape()
+    _check(lib().gbd_sweep_autotune(ctypes.byref(make_system(system)), float(diameter), a, b, c, n,
+                                    ctypes.byref(make_detector(detector)), _ptr(workspace),
+                                    ctypes.c_size_t(workspace.numel()), _ptr(scores),
+                                    _stream(stream), ctypes.byref(sh)))
+    return sh.rows_per_thread, sh.cols_per_thread, float(sh.ms)
 
 
 TIMING_KINDS = ("field_mixed", "field_f64", "project", "reduce")

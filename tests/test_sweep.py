@@ -1,0 +1,138 @@
+"""Batched parameter sweep (persistent kernel with fused Airy score) against the oracle.
+
+The oracle scores an instance by tracing it, summing its field on every pixel in FP64 and
+applying the score's definition directly.  The sweep computes the mixed-precision field and
+the score from moments.  A field error of relative L2 eps moves the score by at most about
+2 eps (the score is an RMS over fewer pixels than the field's norm), so the
+bound here is 2 x the mixed-path tolerance, 4e-5.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2404_12454_gb300 import gbd
+from paper_2404_12454_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+SCORE_TOL = 4e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2404_12454_gb300 import build
+    build.build()
+    import torch
+    torch.cuda.init()
+
+
+def oracle_scores(sw, idx):
+    out = []
+    for k in idx:
+        pupil = sw.pupil(k)
+        b = oracle.trace(sw.system, pupil)
+        E = oracle.field(b, sw.system, sw.detector)
+        out.append(oracle.airy_score(E, sw.detector, sw.system.wavelength,
+                                     sw.system.focal_length / sw.diameter))
+    return np.array(out)
+
+
+def small_sweep():
+    rng = np.random.default_rng(7)
+    n = [16, 32, 64, 16, 32, 128, 64, 32, 16, 64]
+    of = rng.uniform(1.0, 3.0, size=len(n))
+    wr = rng.uniform(0.8, 3.0, size=len(n))
+    return W.sweep_from_params(list(zip(n, of, wr)))
+
+
+def test_small_sweep_scores_match_oracle():
+    sw = small_sweep()
+    plan = gbd.sweep_plan(sw)
+    got = plan.run().cpu().numpy()
+    gbd.gbd_sync()
+    want = oracle_scores(sw, range(sw.n_instances))
+    assert np.all(np.isfinite(got))
+    assert np.max(np.abs(got - want)) <= SCORE_TOL, (got, want)
+    # the scores are distinct numbers, not a constant
+    assert np.ptp(want) > 1e-3
+
+
+def test_sweep_deterministic_graph_and_shapes():
+    import torch
+    sw = small_sweep()
+    plan = gbd.sweep_plan(sw)
+    a = plan.run().clone()
+    b = plan.run().clone()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        c = plan.run(stream=s, graph=True).clone()
+        d = plan.run(stream=s, graph=True).clone()
+    s.synchronize()
+    gbd.gbd_sync()
+    assert torch.equal(a, b) and torch.equal(a, c) and torch.equal(c, d)
+    for shape in ((1, 4), (2, 2), (4, 2)):
+        p2 = gbd.sweep_plan(sw, shape=shape)
+        e = p2.run().clone()
+        gbd.gbd_sync()
+        assert torch.max(torch.abs(e - a)).item() < 1e-6, shape
+
+
+def test_full_sweep_seeded_subset_matches_oracle():
+    """The 1024-instance sweep in one persistent launch; 16 seeded instances re-scored by
+    the oracle (chosen across every beamlet count, at most one of 256 across)."""
+    sw = W.sweep()
+    plan = gbd.sweep_plan(sw)
+    assert plan.n == 1024 and plan.items == 1024 * 32
+    got = plan.run().cpu().numpy()
+    gbd.gbd_sync()
+    assert np.all(np.isfinite(got))
+    n = np.asarray(sw.n_across)
+    rng = np.random.default_rng(240412455)
+    idx = []
+    for N, count in ((16, 4), (32, 4), (64, 4), (128, 3), (256, 1)):
+        cand = np.flatnonzero(n == N)
+        idx += list(rng.choice(cand, size=count, replace=False))
+    want = oracle_scores(sw, idx)
+    assert np.max(np.abs(got[idx] - want)) <= SCORE_TOL, (got[idx], want)
+
+
+def test_sweep_autotune_picks_a_supported_shape():
+    import torch
+    sw = W.sweep_subset(W.sweep(), list(range(24)))
+    probe = gbd.sweep_plan(sw, shape=(1, 4))
+    ws = torch.empty(probe.bytes * 2, dtype=torch.uint8, device="cuda")
+    scores = torch.empty(sw.n_instances, dtype=torch.float64, device="cuda")
+    r, c, ms = gbd.gbd_sweep_autotune(sw.system, sw.diameter, sw.n_across, sw.overlap_factor,
+                                      sw.waist_ratio, sw.detector, ws, scores)
+    assert (r, c) in ((1, 4), (2, 2), (2, 4), (4, 2)) and ms > 0
+
+
+def test_sweep_rejects_bad_instances():
+    sw = small_sweep()
+    with pytest.raises(gbd.GbdError):
+        gbd.SweepPlan(sw.system, sw.diameter, [16, 0], [1.5, 1.5], [1.0, 1.0], sw.detector)
+    with pytest.raises(gbd.GbdError):
+        gbd.SweepPlan(sw.system, sw.diameter, [16], [-1.0], [1.0], sw.detector)
+    with pytest.raises(gbd.GbdError):
+        gbd.SweepPlan(W.System(1e-6, math.inf, 0.02), sw.diameter, [16], [1.5], [1.0],
+                      sw.detector)
+
+
+def test_sweep_timeout_reported_then_recovers():
+    sw = small_sweep()
+    plan = gbd.sweep_plan(sw)
+    ref = plan.run().clone()
+    gbd.gbd_sync()
+    try:
+        gbd.gbd_set_wait_limit(1)
+        plan.run()
+        with pytest.raises(gbd.GbdError) as ei:
+            gbd.gbd_sync()
+        assert ei.value.status == gbd.GBD_ETIMEOUT
+    finally:
+        gbd.gbd_set_wait_limit(0)
+    again = plan.run().clone()
+    gbd.gbd_sync()
+    assert bool((again == ref).all())
