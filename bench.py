@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweep-steps", type=int, default=2,
                     help="timed runs of the 1024-instance parameter sweep (0 = skip)")
+    ap.add_argument("--no-surrogate", action="store_true",
+                    help="skip the surrogate-guided search versus grid and random search")
     return ap.parse_args()
 
 
@@ -356,6 +358,34 @@ def run_ours(args, world, rank, local):
                              "N~U{16..256}, 256x256 pixels +-5 lambda F#"}
         plan.close()
 
+    # ---- surrogate-guided search versus the reference grid and random search
+    surrogate = None
+    if not args.no_surrogate:
+        from paper_2404_12454_gb300 import surrogate as S
+        t0 = time.perf_counter()
+        grid = S.grid_search()
+        t_grid = time.perf_counter() - t0
+        target = 1.01 * grid.best[1]
+        t0 = time.perf_counter()
+        sur = S.surrogate_search(rounds=12, target=target)
+        t_sur = time.perf_counter() - t0
+        n_sur = sur.evals_to_reach(target)
+        rnd = S.random_search(budget=n_sur if n_sur else len(sur.scores))
+        net = S.MLP()
+        xs = np.random.default_rng(0).normal(size=(1024, 3)).astype(np.float32)
+        net.fit(xs, xs[:, 0], steps=5)
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        net.fit(xs, xs[:, 0], steps=100)
+        torch.cuda.synchronize()
+        step_us = (time.perf_counter() - a) / 100 * 1e6
+        surrogate = {"grid_evals": len(grid.scores), "grid_best": grid.best[1],
+                     "grid_best_params": list(grid.best[0]), "grid_seconds": t_grid,
+                     "surrogate_evals_to_1pct": n_sur, "surrogate_best": sur.best[1],
+                     "surrogate_best_params": list(sur.best[0]), "surrogate_seconds": t_sur,
+                     "random_best_same_budget": rnd.best[1],
+                     "mlp_train_step_us_batch1024": step_us}
+
     clk = clocks.stop()
 
     # ---- roofline of the dominant kernel (mixed field kernel, MUFU pipe): each
@@ -407,7 +437,7 @@ def run_ours(args, world, rank, local):
                      "ex2/sin/cos, compensated FP32 sum",
         "data": "synthetic (ideal F/10 lens standing in for the paper's traced telescope)",
         "config": config_block(wl, nb), "clocks": clk, "e2e": e2e, "fp64_path": f64,
-        "sweep": sweep,
+        "sweep": sweep, "surrogate": surrogate,
         "error": error, "roofline": roofline, "cpu_baseline": cpu,
         "gpu_launches": launches_per_step * args.steps,
         "kernel_ms": {k: (v[0] / max(v[1], 1)) for k, v in kt.items()},

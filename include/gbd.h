@@ -275,6 +275,38 @@ gbd_status gbd_sweep_autotune(const gbd_system* system, double diameter, const i
                               size_t bytes, double* scores, void* stream, gbd_shape* best);
 void gbd_sweep_plan_destroy(gbd_sweep_plan* plan);
 
+/* ---------------------------------------------------------------- MLP surrogate ---
+ * Not in the paper: a small network that learns log10 of the sweep's Airy score from
+ * (overlap factor, waist ratio, log2 beamlets across), standardised by the caller, so
+ * that a search verifies only the parameter sets it predicts to be best.
+ * Architecture: 3 -> 128 -> 128 -> 128 -> 128 -> 1, exact GELU 0.5 x (1 + erf(x / sqrt 2))
+ * after each hidden layer, linear output.  GBD_MLP_PARAMS floats in the order
+ * W1[128][3] b1[128] W2[128][128] b2[128] W3 b3 W4 b4 W5[1][128] b5[1] (W[out][in]).
+ * Compute: BF16 weights (round to nearest even from the FP32 master copy), FP32
+ * activations and accumulation; loss = mean over the batch of (y - target)^2; Adam with
+ * bias correction on the FP32 master weights.  All reductions have a fixed order, so
+ * results are deterministic.  x is float[batch][3], target/y float[batch], all device.
+ * gbd_mlp_pack:       weights (uint16 BF16 bits) = round(master).
+ * gbd_mlp_forward:    y = MLP(x); no workspace.
+ * gbd_mlp_grad:       grad = dLoss/dparams (float[GBD_MLP_PARAMS]) and *loss (device float,
+ *                     may be NULL) at the BF16 weights; workspace >= gbd_mlp_workspace_bytes.
+ * gbd_mlp_adam:       one Adam step (step counts from 1) on master/m/v, then repacks.
+ * gbd_mlp_train_step: gbd_mlp_grad then gbd_mlp_adam (the gradient lives in the workspace). */
+#define GBD_MLP_PARAMS 50177
+size_t gbd_mlp_workspace_bytes(int32_t batch);
+gbd_status gbd_mlp_pack(const float* master, uint16_t* weights, void* stream);
+gbd_status gbd_mlp_forward(const uint16_t* weights, const float* x, int32_t batch, float* y,
+                           void* stream);
+gbd_status gbd_mlp_grad(const uint16_t* weights, const float* x, const float* target,
+                        int32_t batch, float* grad, float* loss, void* workspace, size_t bytes,
+                        void* stream);
+gbd_status gbd_mlp_adam(float* master, uint16_t* weights, float* m, float* v, const float* grad,
+                        float lr, float beta1, float beta2, float eps, int32_t step, void* stream);
+gbd_status gbd_mlp_train_step(float* master, uint16_t* weights, float* m, float* v,
+                              const float* x, const float* target, int32_t batch, float lr,
+                              float beta1, float beta2, float eps, int32_t step, float* loss,
+                              void* workspace, size_t bytes, void* stream);
+
 /* ---------------------------------------------------------------- probes ----------
  * Throughput microbenchmarks of the pipes the field kernels are bound by, on the current
  * device (synchronous): MUFU ex2 / sin / cos results per second, FP32 FMA per second and

@@ -98,6 +98,15 @@ _SIGS = {
                                           ctypes.POINTER(gbd_detector), _P, ctypes.c_size_t, _P, _P,
                                           ctypes.POINTER(gbd_shape)]),
     "gbd_sweep_plan_destroy": (None, [_P]),
+    "gbd_mlp_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int32]),
+    "gbd_mlp_pack": (ctypes.c_int, [_P, _P, _P]),
+    "gbd_mlp_forward": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, _P]),
+    "gbd_mlp_grad": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, _P, _P, _P, ctypes.c_size_t, _P]),
+    "gbd_mlp_adam": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_float, ctypes.c_float,
+                                    ctypes.c_float, ctypes.c_float, ctypes.c_int32, _P]),
+    "gbd_mlp_train_step": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, ctypes.c_int32, ctypes.c_float,
+                                          ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                          ctypes.c_int32, _P, _P, ctypes.c_size_t, _P]),
     "gbd_field_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_double,
                                          ctypes.POINTER(gbd_detector), ctypes.c_int32, _P, _P]),
     "gbd_timing_enable": (ctypes.c_int, [ctypes.c_int32]),
@@ -348,6 +357,42 @@ def gbd_sweep_autotune(system, diameter, n_across, overlap_factor, waist_ratio, 
                                     ctypes.c_size_t(workspace.numel()), _ptr(scores),
                                     _stream(stream), ctypes.byref(sh)))
     return sh.rows_per_thread, sh.cols_per_thread, float(sh.ms)
+
+
+MLP_PARAMS = 50177
+
+
+def gbd_mlp_workspace_bytes(batch: int) -> int:
+    return int(lib().gbd_mlp_workspace_bytes(int(batch)))
+
+
+def gbd_mlp_pack(master, weights, stream=None) -> None:
+    _check(lib().gbd_mlp_pack(_ptr(master), _ptr(weights), _stream(stream)))
+
+
+def gbd_mlp_forward(weights, x, y, stream=None) -> None:
+    _check(lib().gbd_mlp_forward(_ptr(weights), _ptr(x), int(x.shape[0]), _ptr(y), _stream(stream)))
+
+
+def gbd_mlp_grad(weights, x, target, grad, loss, workspace, stream=None) -> None:
+    _check(lib().gbd_mlp_grad(_ptr(weights), _ptr(x), _ptr(target), int(x.shape[0]), _ptr(grad),
+                              _ptr(loss), _ptr(workspace), ctypes.c_size_t(workspace.numel()),
+                              _stream(stream)))
+
+
+def gbd_mlp_adam(master, weights, m, v, grad, lr, beta1, beta2, eps, step, stream=None) -> None:
+    _check(lib().gbd_mlp_adam(_ptr(master), _ptr(weights), _ptr(m), _ptr(v), _ptr(grad),
+                              float(lr), float(beta1), float(beta2), float(eps), int(step),
+                              _stream(stream)))
+
+
+def gbd_mlp_train_step(master, weights, m, v, x, target, lr, beta1, beta2, eps, step, loss,
+                       workspace, stream=None) -> None:
+    _check(lib().gbd_mlp_train_step(_ptr(master), _ptr(weights), _ptr(m), _ptr(v), _ptr(x),
+                                    _ptr(target), int(x.shape[0]), float(lr), float(beta1),
+                                    float(beta2), float(eps), int(step), _ptr(loss),
+                                    _ptr(workspace), ctypes.c_size_t(workspace.numel()),
+                                    _stream(stream)))
 
 
 TIMING_KINDS = ("field_mixed", "field_f64", "project", "reduce")

@@ -1,0 +1,107 @@
+"""MLP surrogate kernels (through the C ABI) against the FP64 reference in oracle/mlp.py.
+
+The GPU keeps BF16 weights and FP32 activations; the reference uses the same BF16 weights
+and float64 arithmetic, so forward values agree to FP32 rounding (1e-5 relative) and the
+gradient, an FP32 sum over the batch, to 1e-4 relative L2.  BF16 rounding decides bits, so
+it is compared bit for bit.
+"""
+import numpy as np
+import pytest
+
+from oracle import mlp as M
+from paper_2404_12454_gb300 import gbd
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2404_12454_gb300 import build
+    build.build()
+    import torch
+    torch.cuda.init()
+
+
+def _setup(seed=0, B=300):
+    import torch
+    rng = np.random.default_rng(seed)
+    p = rng.normal(0.0, 0.15, size=M.N_PARAMS).astype(np.float32)
+    x = rng.normal(size=(B, 3)).astype(np.float32)
+    t = rng.normal(size=B).astype(np.float32)
+    P = torch.tensor(p, device="cuda")
+    Wb = torch.empty(M.N_PARAMS, dtype=torch.int16, device="cuda")
+    gbd.gbd_mlp_pack(P, Wb)
+    return p, x, t, P, Wb, torch.tensor(x, device="cuda"), torch.tensor(t, device="cuda")
+
+
+def test_pack_rounds_like_the_reference():
+    p, *_ , Wb, _, _ = _setup()
+    bits = Wb.cpu().numpy().view(np.uint16)
+    assert np.array_equal(bits, M.bf16_bits(p))
+
+
+@pytest.mark.parametrize("B", [1, 31, 300, 1024])
+def test_forward_matches_reference(B):
+    import torch
+    p, x, t, P, Wb, X, T = _setup(1, B)
+    y = torch.empty(B, dtype=torch.float32, device="cuda")
+    gbd.gbd_mlp_forward(Wb, X, y)
+    gbd.gbd_sync()
+    want, _ = M.forward(p, x)
+    got = y.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(got - want)) <= 1e-5 * np.max(np.abs(want)) + 1e-6
+
+
+@pytest.mark.parametrize("B", [1, 257, 1024])
+def test_gradient_matches_reference(B):
+    import torch
+    p, x, t, P, Wb, X, T = _setup(2, B)
+    grad = torch.empty(M.N_PARAMS, dtype=torch.float32, device="cuda")
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    ws = torch.empty(gbd.gbd_mlp_workspace_bytes(B), dtype=torch.uint8, device="cuda")
+    gbd.gbd_mlp_grad(Wb, X, T, grad, loss, ws)
+    gbd.gbd_sync()
+    L, g = M.loss_grad(p, x, t)
+    gg = grad.cpu().numpy().astype(np.float64)
+    assert abs(loss.item() - L) <= 1e-5 * L
+    assert np.linalg.norm(gg - g) <= 1e-4 * np.linalg.norm(g)
+    # every layer separately (the first layer's gradient is the smallest)
+    k = 0
+    for o, i in M.SHAPES:
+        for n in (o * i, o):
+            seg = slice(k, k + n)
+            assert np.linalg.norm(gg[seg] - g[seg]) <= 1e-3 * np.linalg.norm(g[seg]) + 1e-9
+            k += n
+
+
+def test_adam_matches_reference():
+    import torch
+    rng = np.random.default_rng(4)
+    p = rng.normal(size=M.N_PARAMS).astype(np.float32)
+    m = rng.normal(0, 0.01, size=M.N_PARAMS).astype(np.float32)
+    v = rng.uniform(0, 1e-4, size=M.N_PARAMS).astype(np.float32)
+    g = rng.normal(0, 0.01, size=M.N_PARAMS).astype(np.float32)
+    P, Mm, V, G = (torch.tensor(a, device="cuda") for a in (p, m, v, g))
+    Wb = torch.empty(M.N_PARAMS, dtype=torch.int16, device="cuda")
+    gbd.gbd_mlp_adam(P, Wb, Mm, V, G, 1e-3, 0.9, 0.999, 1e-8, 7)
+    gbd.gbd_sync()
+    p2, m2, v2 = M.adam(p.astype(np.float64), m.astype(np.float64), v.astype(np.float64),
+                        g.astype(np.float64), 1e-3, 0.9, 0.999, 1e-8, 7)
+    assert np.max(np.abs(P.cpu().numpy() - p2)) <= 1e-6 * np.max(np.abs(p2))
+    assert np.max(np.abs(Mm.cpu().numpy() - m2)) <= 1e-6 * np.max(np.abs(m2))
+    assert np.max(np.abs(V.cpu().numpy() - v2)) <= 1e-6 * np.max(np.abs(v2))
+    assert np.array_equal(Wb.cpu().numpy().view(np.uint16), M.bf16_bits(P.cpu().numpy()))
+
+
+def test_training_learns_and_is_deterministic():
+    from paper_2404_12454_gb300.surrogate import MLP
+    rng = np.random.default_rng(5)
+    x = rng.uniform(-1.5, 1.5, size=(512, 3)).astype(np.float32)
+    y = (np.sin(1.5 * x[:, 0]) + 0.5 * x[:, 1] ** 2 - 0.3 * x[:, 2]).astype(np.float32)
+    a, b = MLP(11), MLP(11)
+    first = float(np.mean((a.predict(x) - y) ** 2))
+    la = a.fit(x, y, steps=300)
+    lb = b.fit(x, y, steps=300)
+    assert la == lb
+    assert np.array_equal(a.master.cpu().numpy(), b.master.cpu().numpy())
+    assert la < 0.05 * first, (first, la)
