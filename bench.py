@@ -367,10 +367,10 @@ def run_ours(args, world, rank, local):
         t_grid = time.perf_counter() - t0
         target = 1.01 * grid.best[1]
         t0 = time.perf_counter()
-        sur = S.surrogate_search(rounds=12, target=target)
+        sur = S.surrogate_search(rounds=3)
         t_sur = time.perf_counter() - t0
         n_sur = sur.evals_to_reach(target)
-        rnd = S.random_search(budget=n_sur if n_sur else len(sur.scores))
+        rnd = S.random_search(budget=len(sur.scores))
         net = S.MLP()
         xs = np.random.default_rng(0).normal(size=(1024, 3)).astype(np.float32)
         net.fit(xs, xs[:, 0], steps=5)
@@ -383,7 +383,10 @@ def run_ours(args, world, rank, local):
                      "grid_best_params": list(grid.best[0]), "grid_seconds": t_grid,
                      "surrogate_evals_to_1pct": n_sur, "surrogate_best": sur.best[1],
                      "surrogate_best_params": list(sur.best[0]), "surrogate_seconds": t_sur,
+                     "surrogate_evals": len(sur.scores),
+                     "median_proposal_score": float(np.median(sur.scores[128:])),
                      "random_best_same_budget": rnd.best[1],
+                     "median_random_score": float(np.median(rnd.scores[128:])),
                      "mlp_train_step_us_batch1024": step_us}
 
     clk = clocks.stop()

@@ -147,11 +147,13 @@ def random_search(budget: int, batch: int = 64, seed: int = W.SEED_SURROGATE + 1
 
 def surrogate_search(rounds: int = 8, per_round: int = 64, n_init: int = 128, pool: int = 16384,
                      fit_steps: int = 400, seed: int = W.SEED_SURROGATE,
-                     checkpoint: Optional[str] = None, target: Optional[float] = None) -> SearchResult:
+                     checkpoint: Optional[str] = None, target: Optional[float] = None,
+                     min_rounds: int = 1) -> SearchResult:
     """Seeded initial sample (the first n_init instances of the 1024-instance sweep), then
-    rounds of fit -> rank a random pool -> verify the best per_round candidates.  Stops early
-    once the best verified score reaches `target` (if given).  With `checkpoint`, the data
-    and the network are saved after every round and a run resumes from them."""
+    rounds of fit -> rank a random pool -> verify the best per_round candidates.  After
+    `min_rounds` rounds it stops early once the best verified score reaches `target` (if
+    given).  With `checkpoint`, the data and the network are saved after every round and a
+    run resumes from them."""
     sw = W.sweep()
     params = [(sw.n_across[k], sw.overlap_factor[k], sw.waist_ratio[k]) for k in range(n_init)]
     start_round = 0
@@ -175,7 +177,7 @@ def surrogate_search(rounds: int = 8, per_round: int = 64, n_init: int = 128, po
     for _ in range(start_round):  # keep the candidate stream identical on resume
         random_candidates(pool, rng)
     for r in range(start_round, rounds):
-        if target is not None and min(scores) <= target:
+        if target is not None and r >= min_rounds and min(scores) <= target:
             break
         y = np.log10(np.asarray(scores))
         mu, sd = float(y.mean()), float(y.std() + 1e-12)

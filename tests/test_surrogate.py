@@ -21,15 +21,24 @@ def grid():
 
 
 def test_surrogate_reaches_grid_optimum_with_fewer_evaluations(grid):
+    """On these optics the grid optimum lies on the box boundary (256 across, OF = 1; the
+    waist ratio does not act on an ideal lens), so the seeded initial sample alone comes
+    within 1 %.  What the network adds shows in what it proposes: after three rounds its
+    verified proposals are far better than random draws, and its best is at least as good
+    as random search with the same number of evaluations."""
     g_params, g_best = grid.best
     target = 1.01 * g_best
-    sur = S.surrogate_search(rounds=12, target=target)
+    sur = S.surrogate_search(rounds=3)
     n_sur = sur.evals_to_reach(target)
-    rnd = S.random_search(budget=n_sur if n_sur else len(sur.scores))
-    print(f"grid best {g_best:.4e} at {g_params} (1260 evals); surrogate best {sur.best[1]:.4e} "
-          f"at {sur.best[0]} after {n_sur} evals; random best {rnd.best[1]:.4e} at the same budget")
-    assert n_sur is not None and n_sur < 1260
-    # what the network gains: at the surrogate's budget, random search does no better
+    rnd = S.random_search(budget=len(sur.scores))
+    prop = np.asarray(sur.scores[128:])
+    rprop = np.asarray(rnd.scores[128:])
+    print(f"grid best {g_best:.6e} at {g_params} ({len(grid.scores)} evals); surrogate best "
+          f"{sur.best[1]:.6e} at {sur.best[0]}, within 1 % after {n_sur} evals; random best "
+          f"{rnd.best[1]:.6e} with {len(rnd.scores)} evals; median proposal {np.median(prop):.3e} "
+          f"vs median random draw {np.median(rprop):.3e}")
+    assert n_sur is not None and n_sur < len(grid.scores)
+    assert np.median(prop) <= 0.5 * np.median(rprop)
     assert sur.best[1] <= rnd.best[1]
 
 
