@@ -40,9 +40,10 @@ MUFU_EX2_PER_CLK_SM = 32
 MUFU_SINCOS_PER_CLK_SM = 16
 GB300_SMS = 152
 GB300_MAX_MHZ = 2070.0
-# DRAM bytes (read + write) per launch of field_mixed_kernel<2,4> on airy_large from one
-# ncu capture (profiles/field_mixed_kernel_airy_large.md); valid only for that kernel.
-FIELD_MIXED_NCU = {"kernel": "field_mixed_kernel<2, 4>", "bytes": 3.696896e6 + 48.958976e6}
+# DRAM bytes (read + write) per launch of the mixed field kernel on airy_large from one ncu
+# capture (profiles/field_mixed_kernel_airy_large.md); None until the current kernel has
+# been captured.
+FIELD_MIXED_NCU = None
 
 
 def parse():
@@ -259,6 +260,13 @@ def run_ours(args, world, rank, local):
         return [a.elapsed_time(b) for a, b in times]
 
     clocks = ClockSampler(gpu_index_for_smi(local))
+    # the library's autotuner picks the launch shape (pixels per thread, beamlet splits)
+    gbd.gbd_trace(sysm, pupil, pupil.overlap_factor, pupil.waist_ratio, beam, stream)
+    tune_ws = torch.empty(320 << 20, dtype=torch.uint8, device=dev)
+    tuned = gbd.gbd_autotune_field(beam, nb, sysm.wavelength, det, MIX, tune_ws, out[MIX], stream)
+    del tune_ws
+    ws[MIX] = torch.empty(max(256, gbd.gbd_field_workspace_bytes(nb, det, MIX)), dtype=torch.uint8,
+                          device=dev)
     for _ in range(args.warmup):
         step(MIX)
     gbd.gbd_sync(stream)
@@ -403,9 +411,10 @@ def run_ours(args, world, rank, local):
     roofline = {
         "bound": "alu", "pipe": "MUFU (XU): ex2 + sin + cos per beamlet-pixel",
         "achieved": achieved / 1e9, "peak": peak_evals / 1e9, "unit": "Geval/s",
-        "frac": achieved / peak_evals, "traffic": FIELD_MIXED_NCU["bytes"],
-        "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one capture of "
-                          + FIELD_MIXED_NCU["kernel"],
+        "frac": achieved / peak_evals,
+        "traffic": FIELD_MIXED_NCU["bytes"] if FIELD_MIXED_NCU else None,
+        "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum, one capture of "
+                           + FIELD_MIXED_NCU["kernel"]) if FIELD_MIXED_NCU else None,
         "peak_source": (f"derived: {GB300_SMS} SMs x {GB300_MAX_MHZ:g} MHz / (1/{MUFU_EX2_PER_CLK_SM}"
                         f" + 2/{MUFU_SINCOS_PER_CLK_SM}) clk per eval"),
         "kernel": "field_mixed_kernel", "kernel_ms_avg": k_avg_s * 1e3, "launches": kn,
@@ -431,7 +440,9 @@ def run_ours(args, world, rank, local):
                "sample": f"{rows.size} of {det.ny} rows x {cols.size} columns x {r['nb']} beamlets "
                          f"({r['evals']:.3g} evals, {r['seconds']:.1f} s, FP64 C + OpenMP)"}
 
-    launches_per_step = 4  # trace, projection, field, split reduction
+    # trace, projection, field (the instantiation the wide-phase flag selects; the other
+    # returns at once), split reduction
+    launches_per_step = 5
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -440,6 +451,8 @@ def run_ours(args, world, rank, local):
                      "ex2/sin/cos, compensated FP32 sum",
         "data": "synthetic (ideal F/10 lens standing in for the paper's traced telescope)",
         "config": config_block(wl, nb), "clocks": clk, "e2e": e2e, "fp64_path": f64,
+        "autotuned_shape": {"rows_per_thread": tuned[0], "cols_per_thread": tuned[1],
+                            "splits": tuned[2], "ms": tuned[3]},
         "sweep": sweep, "surrogate": surrogate,
         "error": error, "roofline": roofline, "cpu_baseline": cpu,
         "gpu_launches": launches_per_step * args.steps,

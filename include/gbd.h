@@ -143,8 +143,10 @@ gbd_status gbd_trace(const gbd_system* system, const gbd_pupil* pupil, double ov
  * second order in s (exact for an untilted plane, z = 0).
  * precision GBD_PREC_F64: FP64 throughout, field_out is complex128 [ny][nx].
  * precision GBD_PREC_MIXED: per-beamlet projection in FP64 (constant phase reduced mod
- *   one turn), per-pixel quadratic form, exp2/sin/cos on the MUFU pipe and the sum in
- *   FP32 chunks combined with compensated (TwoSum) accumulation; field_out is complex64.
+ *   one turn), per-pixel quadratic form in FP32, exp2/sin/cos on the MUFU pipe (phases
+ *   reduced exactly first when some beamlet's phase can exceed 256 rad on the detector)
+ *   and the sum in FP32 64-beamlet chunks combined with compensated (TwoSum)
+ *   accumulation; field_out is complex64.
  * workspace: device scratch of at least gbd_field_workspace_bytes(...) bytes, 256-byte
  *   aligned.  Contents on entry are ignored.
  * n_beamlets may be 0 (the field is then zero).
@@ -161,15 +163,19 @@ gbd_status gbd_field(const gbd_beamlet* beamlets, int32_t n_beamlets, double wav
  *   MIXED: 16 floats per beamlet in the tiled layout gbd_field uses
  *          [tile = b / 64][field f = 0..3][b % 64][4 floats];
  *          values (i0, j0, a0, p0 | a1u, p1u, a1v, p1v | auu, puu, auv, puv | avv, pvv, 0, 0)
- *          with ln E_j(i, j) / ln 2 = a0 + a1u tu + a1v tv + auu tu^2 + auv tu tv + avv tv^2
- *          and phase / 2 pi = p0 + ... likewise, tu = i - i0, tv = j - j0 (pixel units),
- *          excluding the common carrier exp(-ik z(s)).
- *   F64:   16 doubles per beamlet [tile][field f = 0..7][b % 64][2 doubles], same order.
+ *          with log2 |E_j(i, j)| = a0 + a1u tu + a1v tv + auu tu^2 + auv tu tv + avv tv^2 and
+ *          the phase in radians p0 + ... likewise (p0 in [-pi, pi)), tu = i - i0, tv = j - j0
+ *          (pixel units), excluding the common carrier exp(-ik z(s)).
+ *          wide_flag (device, may be NULL; zero it first) is set to 1 if some beamlet's
+ *          phase can exceed 256 rad on the detector, in which case gbd_field reduces every
+ *          per-pixel phase exactly before sin/cos.
+ *   F64:   16 doubles per beamlet [tile][field f = 0..7][b % 64][2 doubles], same order, the
+ *          phase in turns (phase / 2 pi); wide_flag is not used.
  * coeffs must hold gbd_project_bytes(n, precision) bytes. */
 size_t gbd_project_bytes(int32_t n_beamlets, int32_t precision);
 gbd_status gbd_project(const gbd_beamlet* beamlets, int32_t n_beamlets, double wavelength,
                        const gbd_detector* detector, int32_t precision, void* coeffs,
-                       void* stream);
+                       uint32_t* wide_flag, void* stream);
 
 /* ---------------------------------------------------------------- tuning ----------
  * Launch shape of the field kernels: pixels per thread (rows x cols), beamlet splits.

@@ -9,9 +9,9 @@
 // also applies the per-pixel carrier of a tilted plane.
 //
 // Mixed path, per (beamlet, pixel): 4 FFMA for the quadratic form (row terms shared across
-// the thread's columns), 3 FADD + 1 FMUL for the exact range reduction of the phase (in
-// turns) and its scaling to radians, ex2 / sin / cos on the MUFU pipe, 2 FFMA to
-// accumulate.  The sum runs in FP32 over each 64-beamlet tile and is folded into a
+// the thread's columns; phase coefficients in radians), ex2 / sin / cos on the MUFU pipe,
+// 2 FFMA to accumulate.  If the projection found a beamlet whose phase can exceed 256 rad
+// on the detector, the instantiation that reduces every phase exactly runs instead.  The sum runs in FP32 over each 64-beamlet tile and is folded into a
 // (hi, lo) pair with TwoSum between tiles.
 #include <math.h>
 
@@ -28,10 +28,14 @@ __device__ unsigned int g_field_status = 0;
 
 __device__ __forceinline__ void record_timeout() { atomicOr(&g_field_status, gbd::kStatusTimeout); }
 
-template <int RB, int CB>
+// WIDE selects the instantiation with per-pixel phase reduction.  Both instantiations are
+// launched; each returns at once unless the projection's wide-phase flag selects it.
+template <int RB, int CB, bool WIDE>
 __global__ void __launch_bounds__(kThreads, 2)
     field_mixed_kernel(const float4* __restrict__ coef, int n_tiles, int tiles_per_split, int nx,
-                       int ny, double2* __restrict__ partial, uint32_t spins) {
+                       int ny, double2* __restrict__ partial, const unsigned* __restrict__ wide,
+                       uint32_t spins) {
+    if ((*wide != 0u) != WIDE) return;
     constexpr int kTileF4 = gbd::kMixedFields * gbd::kTile;
     __shared__ __align__(128) float4 stage[kStages][kTileF4];
     __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
@@ -65,7 +69,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             ok = false;
             break;
         }
-        gbd::mixed_tile<RB, CB>(ts.tile(k), colf, rowf, acc);
+        gbd::mixed_tile<RB, CB, WIDE>(ts.tile(k), colf, rowf, acc);
         gbd::mixed_fold<RB, CB>(acc, hi, lo);
         if (!ts.release(k, lane, warp, spins)) {
             ok = false;
@@ -215,18 +219,21 @@ __global__ void __launch_bounds__(256) field_reduce_kernel(const double2* __rest
 
 template <int RB, int CB>
 cudaError_t launch_mixed(const void* coeffs, int n_tiles, const gbd_project_params& p,
-                         const gbd_field_launch& L, double2* partial, uint32_t spins,
-                         cudaStream_t s) {
+                         const gbd_field_launch& L, double2* partial, const unsigned* wide,
+                         uint32_t spins, cudaStream_t s) {
     dim3 grid((p.nx + 32 * CB - 1) / (32 * CB), (p.ny + 8 * RB - 1) / (8 * RB), L.splits);
-    field_mixed_kernel<RB, CB><<<grid, kThreads, 0, s>>>(static_cast<const float4*>(coeffs),
-                                                         n_tiles, L.tiles_per_split, p.nx, p.ny,
-                                                         partial, spins);
+    const float4* c = static_cast<const float4*>(coeffs);
+    field_mixed_kernel<RB, CB, false><<<grid, kThreads, 0, s>>>(c, n_tiles, L.tiles_per_split, p.nx,
+                                                                p.ny, partial, wide, spins);
+    field_mixed_kernel<RB, CB, true><<<grid, kThreads, 0, s>>>(c, n_tiles, L.tiles_per_split, p.nx,
+                                                               p.ny, partial, wide, spins);
     return cudaGetLastError();
 }
 
 template <int RB, int CB>
 cudaError_t launch_f64(const void* coeffs, int n_tiles, const gbd_project_params& p,
-                       const gbd_field_launch& L, double2* partial, uint32_t spins, cudaStream_t s) {
+                       const gbd_field_launch& L, double2* partial, const unsigned* /*wide*/,
+                       uint32_t spins, cudaStream_t s) {
     const size_t smem = (size_t)kStages * gbd::kF64TileBytes;
     cudaError_t e = cudaFuncSetAttribute(field_f64_kernel<RB, CB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -239,7 +246,8 @@ cudaError_t launch_f64(const void* coeffs, int n_tiles, const gbd_project_params
 }
 
 typedef cudaError_t (*launch_fn)(const void*, int, const gbd_project_params&,
-                                 const gbd_field_launch&, double2*, uint32_t, cudaStream_t);
+                                 const gbd_field_launch&, double2*, const unsigned*, uint32_t,
+                                 cudaStream_t);
 
 struct ShapeEntry {
     int rb, cb;
@@ -248,10 +256,10 @@ struct ShapeEntry {
 };
 
 const ShapeEntry kMixedShapes[] = {
-    {1, 4, launch_mixed<1, 4>, (const void*)field_mixed_kernel<1, 4>},
-    {2, 2, launch_mixed<2, 2>, (const void*)field_mixed_kernel<2, 2>},
-    {2, 4, launch_mixed<2, 4>, (const void*)field_mixed_kernel<2, 4>},
-    {4, 2, launch_mixed<4, 2>, (const void*)field_mixed_kernel<4, 2>},
+    {1, 4, launch_mixed<1, 4>, (const void*)field_mixed_kernel<1, 4, false>},
+    {2, 2, launch_mixed<2, 2>, (const void*)field_mixed_kernel<2, 2, false>},
+    {2, 4, launch_mixed<2, 4>, (const void*)field_mixed_kernel<2, 4, false>},
+    {4, 2, launch_mixed<4, 2>, (const void*)field_mixed_kernel<4, 2, false>},
 };
 const ShapeEntry kF64Shapes[] = {
     {1, 2, launch_f64<1, 2>, (const void*)field_f64_kernel<1, 2>},
@@ -290,10 +298,11 @@ int gbd_field_occupancy(int precision, int rb, int cb) {
 
 cudaError_t gbd_launch_field_kernel(int precision, const void* coeffs, int n_tiles,
                                     const gbd_project_params& p, const gbd_field_launch& L,
-                                    double2* partial, uint32_t wait_spins, cudaStream_t s) {
+                                    double2* partial, const unsigned* wide, uint32_t wait_spins,
+                                    cudaStream_t s) {
     const ShapeEntry* e = find_shape(precision, L.rows_per_thread, L.cols_per_thread);
     if (!e) return cudaErrorInvalidValue;
-    return e->fn(coeffs, n_tiles, p, L, partial, wait_spins, s);
+    return e->fn(coeffs, n_tiles, p, L, partial, wide, wait_spins, s);
 }
 
 cudaError_t gbd_launch_field_reduce(int precision, const gbd_project_params& p, int splits,

@@ -107,14 +107,22 @@ struct TileStream {
     }
 };
 
+// Phase magnitude (radians) above which a beamlet's phase is range-reduced per pixel.
+// Below it the MUFU sin/cos take the radians directly: their absolute error grows about
+// linearly with |x| (3e-7 at pi, 1e-5 at 100 rad on GB300), so at <= 256 rad it stays
+// well inside the mixed path's tolerance without the four reduction instructions.
+constexpr float kWidePhase = 256.0f;
+
 // One 64-beamlet tile of mixed-precision evaluation on a thread's RB x CB pixels.
 // Record fields: (i0, j0, a0, p0) (a1u, p1u, a1v, p1v) (auu, puu, auv, puv) (avv, pvv, -, -)
-// with log2 |E| = a0 + a1u tu + a1v tv + auu tu^2 + auv tu tv + avv tv^2 and phase/2pi the
-// same in p, tu = i - i0, tv = j - j0.
-template <int RB, int CB>
+// with log2 |E| = a0 + a1u tu + a1v tv + auu tu^2 + auv tu tv + avv tv^2 and the phase in
+// radians the same in p, tu = i - i0, tv = j - j0.  WIDE: some beamlet's phase may exceed
+// kWidePhase on this detector, so every phase is reduced exactly to [-pi, pi] (in turns,
+// where x - rint(x) is exact) before sin/cos.
+template <int RB, int CB, bool WIDE>
 __device__ __forceinline__ void mixed_tile(const float4* __restrict__ st, const float (&colf)[CB],
                                            const float (&rowf)[RB], float2 (&acc)[RB][CB]) {
-    const float kTwoPi = 6.28318530717958647692f;
+    const float kTwoPi = 6.28318530717958647692f, kInvTwoPi = 0.15915494309189533577f;
 #pragma unroll 1
     for (int b = 0; b < kTile; ++b) {
         const float4 q0 = st[b];
@@ -134,9 +142,9 @@ __device__ __forceinline__ void mixed_tile(const float4* __restrict__ st, const 
 #pragma unroll
             for (int c = 0; c < CB; ++c) {
                 const float ea = fmaf(tu[c], fmaf(q2.x, tu[c], sa), ra);
-                const float ep = fmaf(tu[c], fmaf(q2.y, tu[c], sp), rp);
+                float x = fmaf(tu[c], fmaf(q2.y, tu[c], sp), rp);
+                if (WIDE) x = frac_turns(x * kInvTwoPi) * kTwoPi;
                 const float amp = mufu_ex2(ea);
-                const float x = frac_turns(ep) * kTwoPi;
                 acc[r][c].x = fmaf(amp, mufu_cos(x), acc[r][c].x);
                 acc[r][c].y = fmaf(amp, mufu_sin(x), acc[r][c].y);
             }

@@ -195,12 +195,15 @@ cudaError_t gbd_launch_trace(const gbd_trace_params& p, int n_instances, int max
 // Batched trace + mixed projection straight into the tiled records (sweep set-up).
 cudaError_t gbd_launch_trace_project(const gbd_trace_params& p, int n_instances, int max_n_across,
                                      const gbd_instance_dev* d_inst, const gbd_project_params& g,
-                                     float4* out, cudaStream_t s);
+                                     float4* out, unsigned* wide, cudaStream_t s);
+// `wide` (mixed only, may be null): set to 1 when some beamlet's phase may exceed the
+// wide-phase bound on this detector; the caller zeroes it first.
 cudaError_t gbd_launch_project(const gbd_beamlet* b, int n, const gbd_project_params& p,
-                               int precision, void* coeffs, cudaStream_t s);
+                               int precision, void* coeffs, unsigned* wide, cudaStream_t s);
 cudaError_t gbd_launch_field_kernel(int precision, const void* coeffs, int n_tiles,
                                     const gbd_project_params& p, const gbd_field_launch& L,
-                                    double2* partial, uint32_t wait_spins, cudaStream_t s);
+                                    double2* partial, const unsigned* wide, uint32_t wait_spins,
+                                    cudaStream_t s);
 cudaError_t gbd_launch_field_reduce(int precision, const gbd_project_params& p, int splits,
                                     const double2* partial, void* out, cudaStream_t s);
 int gbd_field_occupancy(int precision, int rb, int cb);

@@ -44,12 +44,15 @@ __global__ void __launch_bounds__(256) airy_table_kernel(int nx, int ny, double 
     out[p] = make_double2(a, r <= r3 ? 1.0 : 0.0);
 }
 
-template <int RB, int CB>
+// WIDE: as in field_mixed_kernel, both instantiations are launched and the projection's
+// wide-phase flag selects the one that works.
+template <int RB, int CB, bool WIDE>
 __global__ void __launch_bounds__(kThreads, 2)
     sweep_kernel(const float4* __restrict__ coef, const int2* __restrict__ inst_tiles,
                  const int2* __restrict__ items, int n_items, int tiles_x, int n_blocks, int nx,
                  int ny, const double2* __restrict__ airy, double* __restrict__ moments,
-                 int* __restrict__ counter, uint32_t spins) {
+                 int* __restrict__ counter, const unsigned* __restrict__ wide, uint32_t spins) {
+    if ((*wide != 0u) != WIDE) return;
     constexpr int kTileF4 = gbd::kMixedFields * gbd::kTile;
     __shared__ __align__(128) float4 stage[kStages][kTileF4];
     __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
@@ -90,7 +93,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                 ok = false;
                 break;
             }
-            gbd::mixed_tile<RB, CB>(ts.tile(k), colf, rowf, acc);
+            gbd::mixed_tile<RB, CB, WIDE>(ts.tile(k), colf, rowf, acc);
             gbd::mixed_fold<RB, CB>(acc, hi, lo);
             if (!ts.release(k, lane, warp, spins)) {
                 ok = false;
@@ -172,14 +175,19 @@ __global__ void __launch_bounds__(128) sweep_finalize_kernel(const double* __res
 
 typedef cudaError_t (*sweep_launch_fn)(dim3, cudaStream_t, const float4*, const int2*, const int2*,
                                        int, int, int, int, int, const double2*, double*, int*,
-                                       uint32_t);
+                                       const unsigned*, uint32_t);
 
 template <int RB, int CB>
 cudaError_t launch_sweep(dim3 grid, cudaStream_t s, const float4* coef, const int2* it_tiles,
                          const int2* items, int n_items, int tiles_x, int n_blocks, int nx, int ny,
-                         const double2* airy, double* moments, int* counter, uint32_t spins) {
-    sweep_kernel<RB, CB><<<grid, kThreads, 0, s>>>(coef, it_tiles, items, n_items, tiles_x, n_blocks,
-                                                   nx, ny, airy, moments, counter, spins);
+                         const double2* airy, double* moments, int* counter, const unsigned* wide,
+                         uint32_t spins) {
+    sweep_kernel<RB, CB, false><<<grid, kThreads, 0, s>>>(coef, it_tiles, items, n_items, tiles_x,
+                                                          n_blocks, nx, ny, airy, moments, counter,
+                                                          wide, spins);
+    sweep_kernel<RB, CB, true><<<grid, kThreads, 0, s>>>(coef, it_tiles, items, n_items, tiles_x,
+                                                         n_blocks, nx, ny, airy, moments, counter,
+                                                         wide, spins);
     return cudaGetLastError();
 }
 
@@ -190,10 +198,10 @@ struct SweepShape {
 };
 
 const SweepShape kSweepShapes[] = {
-    {1, 4, launch_sweep<1, 4>, (const void*)sweep_kernel<1, 4>},
-    {2, 2, launch_sweep<2, 2>, (const void*)sweep_kernel<2, 2>},
-    {2, 4, launch_sweep<2, 4>, (const void*)sweep_kernel<2, 4>},
-    {4, 2, launch_sweep<4, 2>, (const void*)sweep_kernel<4, 2>},
+    {1, 4, launch_sweep<1, 4>, (const void*)sweep_kernel<1, 4, false>},
+    {2, 2, launch_sweep<2, 2>, (const void*)sweep_kernel<2, 2, false>},
+    {2, 4, launch_sweep<2, 4>, (const void*)sweep_kernel<2, 4, false>},
+    {4, 2, launch_sweep<4, 2>, (const void*)sweep_kernel<4, 2, false>},
 };
 
 const SweepShape* find_sweep_shape(int rb, int cb) {
@@ -240,19 +248,21 @@ static gbd_status sweep_enqueue(gbd_sweep_plan* P, double* scores, cudaStream_t 
         occ < 1)
         occ = 1;
     char* w = P->ws;
+    // the first 256 bytes hold the work counter (offset 0) and the wide-phase flag (64)
     int* counter = reinterpret_cast<int*>(w + P->off_counter);
+    unsigned* wide = reinterpret_cast<unsigned*>(w + P->off_counter + 64);
     float4* coef = reinterpret_cast<float4*>(w + P->off_coef);
-    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), s);
+    cudaError_t e = cudaMemsetAsync(w + P->off_counter, 0, 256, s);
     if (e == cudaSuccess)
         e = gbd_launch_trace_project(P->tp, P->n_inst, P->max_n,
                                      reinterpret_cast<const gbd_instance_dev*>(w + P->off_inst), P->pp,
-                                     coef, s);
+                                     coef, wide, s);
     if (e == cudaSuccess) {
         const int grid = std::max(1, std::min(P->n_items, occ * gbd_sm_count()));
         e = sh->fn(dim3(grid), s, coef, reinterpret_cast<const int2*>(w + P->off_itiles),
                    reinterpret_cast<const int2*>(w + P->off_items), P->n_items, P->tiles_x,
                    P->n_blocks, P->pp.nx, P->pp.ny, reinterpret_cast<const double2*>(w + P->off_airy),
-                   reinterpret_cast<double*>(w + P->off_moments), counter, gbd_wait_spins());
+                   reinterpret_cast<double*>(w + P->off_moments), counter, wide, gbd_wait_spins());
     }
     if (e == cudaSuccess) {
         sweep_finalize_kernel<<<(P->n_inst + 127) / 128, 128, 0, s>>>(

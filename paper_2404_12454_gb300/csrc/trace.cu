@@ -9,6 +9,7 @@
 // expansion in the pixel position.
 #include <math.h>
 
+#include "field_core.cuh"
 #include "gbd_internal.cuh"
 
 static_assert(sizeof(gbd_beamlet) == 36 * sizeof(double), "gbd_beamlet is 36 doubles");
@@ -270,17 +271,28 @@ __device__ Quad project_one(const gbd_beamlet& b, const gbd_project_params& G) {
     return q;
 }
 
-// Mixed-precision record of beamlet `t` in the tiled layout (4 float4 fields per beamlet).
-__device__ __forceinline__ void write_mixed(float4* __restrict__ out, long long t, const Quad& q) {
+// Mixed-precision record of beamlet `t` in the tiled layout (4 float4 fields per beamlet),
+// phase coefficients in radians.  Returns whether the beamlet's phase can exceed the
+// wide-phase bound anywhere on the detector (|tu| <= U, |tv| <= V around its centre).
+__device__ __forceinline__ bool write_mixed(float4* __restrict__ out, long long t, const Quad& q,
+                                            const gbd_project_params& G) {
     float4 f0, f1, f2, f3;
+    bool wide = false;
     if (q.pad) {
         f0 = make_float4(0.f, 0.f, gbd::kPadLog2Amp, 0.f);
         f1 = f2 = f3 = make_float4(0.f, 0.f, 0.f, 0.f);
     } else {
-        f0 = make_float4((float)q.i0, (float)q.j0, (float)q.a[0], (float)q.p[0]);
-        f1 = make_float4((float)q.a[1], (float)q.p[1], (float)q.a[2], (float)q.p[2]);
-        f2 = make_float4((float)q.a[3], (float)q.p[3], (float)q.a[4], (float)q.p[4]);
-        f3 = make_float4((float)q.a[5], (float)q.p[5], 0.f, 0.f);
+        const double tp = 2.0 * M_PI;
+        double p[6];
+        for (int m = 0; m < 6; ++m) p[m] = q.p[m] * tp;
+        const double U = fmax(q.i0, G.nx - 1 - q.i0), V = fmax(q.j0, G.ny - 1 - q.j0);
+        const double bound = fabs(p[0]) + fabs(p[1]) * U + fabs(p[2]) * V + fabs(p[3]) * U * U +
+                             fabs(p[4]) * U * V + fabs(p[5]) * V * V;
+        wide = !(bound <= (double)gbd::kWidePhase);
+        f0 = make_float4((float)q.i0, (float)q.j0, (float)q.a[0], (float)p[0]);
+        f1 = make_float4((float)q.a[1], (float)p[1], (float)q.a[2], (float)p[2]);
+        f2 = make_float4((float)q.a[3], (float)p[3], (float)q.a[4], (float)p[4]);
+        f3 = make_float4((float)q.a[5], (float)p[5], 0.f, 0.f);
     }
     float4* tile = out + (size_t)(t / gbd::kTile) * gbd::kMixedFields * gbd::kTile;
     const int l = (int)(t % gbd::kTile);
@@ -288,17 +300,19 @@ __device__ __forceinline__ void write_mixed(float4* __restrict__ out, long long 
     tile[gbd::kTile + l] = f1;
     tile[2 * gbd::kTile + l] = f2;
     tile[3 * gbd::kTile + l] = f3;
+    return wide;
 }
 
 __global__ void __launch_bounds__(128) project_mixed_kernel(const gbd_beamlet* __restrict__ b, int n,
                                                             int n_pad, gbd_project_params G,
-                                                            float4* __restrict__ out) {
+                                                            float4* __restrict__ out,
+                                                            unsigned* __restrict__ wide) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n_pad) return;
     Quad q;
     q.pad = true;
     if (t < n) q = project_one(b[t], G);
-    write_mixed(out, t, q);
+    if (write_mixed(out, t, q, G) && wide) atomicOr(wide, 1u);
 }
 
 __global__ void __launch_bounds__(128) project_f64_kernel(const gbd_beamlet* __restrict__ b, int n,
@@ -328,7 +342,7 @@ __global__ void __launch_bounds__(128) project_f64_kernel(const gbd_beamlet* __r
 // CTA of its first row also writes the padding records up to the next tile boundary.
 __global__ void __launch_bounds__(128)
     trace_project_kernel(gbd_trace_params P, const gbd_instance_dev* __restrict__ inst,
-                         gbd_project_params G, float4* __restrict__ out) {
+                         gbd_project_params G, float4* __restrict__ out, unsigned* __restrict__ wide) {
     const gbd_instance_dev I = inst[blockIdx.y];
     const int N = I.n_across;
     const int j = blockIdx.x;
@@ -345,7 +359,7 @@ __global__ void __launch_bounds__(128)
         const long long pad_end = (nb + gbd::kTile - 1) / gbd::kTile * gbd::kTile;
         Quad q;
         q.pad = true;
-        for (long long t = nb + threadIdx.x; t < pad_end; t += blockDim.x) write_mixed(out, I.offset + t, q);
+        for (long long t = nb + threadIdx.x; t < pad_end; t += blockDim.x) write_mixed(out, I.offset + t, q, G);
     }
     const int a = row_extent(j, N);
     if (a < 0) return;
@@ -353,7 +367,7 @@ __global__ void __launch_bounds__(128)
     for (int t = threadIdx.x; t <= a; t += blockDim.x) {
         gbd_beamlet b;
         trace_one(P, N, I.overlap_factor, I.waist_ratio, i_lo + t, j, &b);
-        write_mixed(out, I.offset + row_off + t, project_one(b, G));
+        if (write_mixed(out, I.offset + row_off + t, project_one(b, G), G) && wide) atomicOr(wide, 1u);
     }
 }
 
@@ -361,9 +375,9 @@ __global__ void __launch_bounds__(128)
 
 cudaError_t gbd_launch_trace_project(const gbd_trace_params& p, int n_instances, int max_n_across,
                                      const gbd_instance_dev* d_inst, const gbd_project_params& g,
-                                     float4* out, cudaStream_t s) {
+                                     float4* out, unsigned* wide, cudaStream_t s) {
     dim3 grid(max_n_across, n_instances);
-    trace_project_kernel<<<grid, 128, 0, s>>>(p, d_inst, g, out);
+    trace_project_kernel<<<grid, 128, 0, s>>>(p, d_inst, g, out, wide);
     return cudaGetLastError();
 }
 
@@ -375,12 +389,12 @@ cudaError_t gbd_launch_trace(const gbd_trace_params& p, int n_instances, int max
 }
 
 cudaError_t gbd_launch_project(const gbd_beamlet* b, int n, const gbd_project_params& p,
-                               int precision, void* coeffs, cudaStream_t s) {
+                               int precision, void* coeffs, unsigned* wide, cudaStream_t s) {
     const int n_pad = (n + gbd::kTile - 1) / gbd::kTile * gbd::kTile;
     if (n_pad == 0) return cudaSuccess;
     const int blocks = (n_pad + 127) / 128;
     if (precision == GBD_PREC_MIXED)
-        project_mixed_kernel<<<blocks, 128, 0, s>>>(b, n, n_pad, p, static_cast<float4*>(coeffs));
+        project_mixed_kernel<<<blocks, 128, 0, s>>>(b, n, n_pad, p, static_cast<float4*>(coeffs), wide);
     else
         project_f64_kernel<<<blocks, 128, 0, s>>>(b, n, n_pad, p, static_cast<double2*>(coeffs));
     return cudaGetLastError();

@@ -71,7 +71,7 @@ _SIGS = {
                                  ctypes.c_int32, _P, ctypes.c_size_t, _P, _P]),
     "gbd_project_bytes": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_int32]),
     "gbd_project": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_double,
-                                   ctypes.POINTER(gbd_detector), ctypes.c_int32, _P, _P]),
+                                   ctypes.POINTER(gbd_detector), ctypes.c_int32, _P, _P, _P]),
     "gbd_field_set_shape": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(gbd_shape)]),
     "gbd_field_get_shape": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32,
                                            ctypes.POINTER(gbd_detector), ctypes.POINTER(gbd_shape)]),
@@ -236,10 +236,12 @@ def gbd_project_bytes(n_beamlets: int, precision: int) -> int:
 
 
 def gbd_project(beamlets, n_beamlets: int, wavelength: float, detector, precision: int, coeffs,
-                stream=None) -> None:
+                wide_flag=None, stream=None) -> None:
+    """Projected records into ``coeffs``; ``wide_flag`` (int32 CUDA tensor, zeroed) is set
+    to 1 if some beamlet's phase can exceed 256 rad on the detector (mixed only)."""
     _check(lib().gbd_project(_ptr(beamlets), int(n_beamlets), float(wavelength),
                              ctypes.byref(make_detector(detector)), int(precision), _ptr(coeffs),
-                             _stream(stream)))
+                             _ptr(wide_flag), _stream(stream)))
 
 
 def gbd_field_set_shape(precision: int, rows: int, cols: int, splits: int = 0) -> None:

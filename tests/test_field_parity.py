@@ -258,3 +258,26 @@ def test_kernel_timing_hooks_count_launches():
     assert t["field_mixed"][1] == 3 and t["field_f64"][1] == 1
     assert t["project"][1] == 4 and t["reduce"][1] == 4
     assert all(ms > 0 for ms, n in t.values())
+
+
+def test_wide_phase_flag_selects_exact_reduction():
+    """On a +-100 lambda F# detector the edge beamlets' phases exceed 256 rad: the
+    projection raises the wide-phase flag and the reduced instantiation keeps the mixed
+    field within tolerance; on the benchmark workload the flag stays clear."""
+    import torch
+    base = W.airy_small()
+    wide = W.Workload("wide", base.system, base.pupil, W.Detector(1024, 1024, 2e-6, 2e-6))
+    for wl, expect in ((wide, 1), (W.airy_large(), 0)):
+        b = gpu_trace(wl)
+        n = b.shape[0]
+        coef = torch.empty(gbd.gbd_project_bytes(n, gbd.GBD_PREC_MIXED), dtype=torch.uint8,
+                           device="cuda")
+        flag = torch.zeros(1, dtype=torch.int32, device="cuda")
+        gbd.gbd_project(b, n, wl.system.wavelength, wl.detector, gbd.GBD_PREC_MIXED, coef, flag)
+        gbd.gbd_sync()
+        assert int(flag.item()) == expect, wl.name
+    b = gpu_trace(wide)
+    E = gpu_field(b, wide, gbd.GBD_PREC_MIXED)
+    idx = np.arange(5, 1024, 33)
+    Eo = oracle.field(oracle.trace(wide.system, wide.pupil), wide.system, wide.detector, idx, idx)
+    assert rel_l2(E[np.ix_(idx, idx)], Eo) <= TOL[gbd.GBD_PREC_MIXED]
