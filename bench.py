@@ -40,10 +40,11 @@ MUFU_EX2_PER_CLK_SM = 32
 MUFU_SINCOS_PER_CLK_SM = 16
 GB300_SMS = 152
 GB300_MAX_MHZ = 2070.0
-# DRAM bytes (read + write) per launch of the mixed field kernel on airy_large from one ncu
-# capture (profiles/field_mixed_kernel_airy_large.md); None until the current kernel has
-# been captured.
-FIELD_MIXED_NCU = None
+# DRAM bytes per launch of field_mixed_kernel<2,4,false> on airy_large from one ncu capture
+# (profiles/field_mixed_kernel_airy_large.md) at 26 beamlet splits.  The reads are the
+# record tiles; the writes are the split partial fields, which scale with the split count.
+FIELD_MIXED_NCU = {"kernel": "field_mixed_kernel<2, 4, false>", "read": 3.599616e6,
+                   "write": 48.867072e6, "splits": 26, "rows": 2, "cols": 4}
 
 
 def parse():
@@ -171,6 +172,14 @@ class ClockSampler:
         return {"sm_mhz": mhz[len(mhz) // 2], "sm_max_mhz": max(r[2] for r in use),
                 "reasons": sorted(reasons), "samples": len(use),
                 "samples_in_timed_region": len(inside)}
+
+
+def traffic_bytes(tuned):
+    """Per-launch DRAM bytes of the captured kernel, writes scaled to the split count used."""
+    n = FIELD_MIXED_NCU
+    if tuned[0] != n["rows"] or tuned[1] != n["cols"]:
+        return None
+    return n["read"] + n["write"] * tuned[2] / n["splits"]
 
 
 def peak_evals_const() -> float:
@@ -412,9 +421,10 @@ def run_ours(args, world, rank, local):
         "bound": "alu", "pipe": "MUFU (XU): ex2 + sin + cos per beamlet-pixel",
         "achieved": achieved / 1e9, "peak": peak_evals / 1e9, "unit": "Geval/s",
         "frac": achieved / peak_evals,
-        "traffic": FIELD_MIXED_NCU["bytes"] if FIELD_MIXED_NCU else None,
-        "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum, one capture of "
-                           + FIELD_MIXED_NCU["kernel"]) if FIELD_MIXED_NCU else None,
+        "traffic": traffic_bytes(tuned),
+        "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one capture of "
+                           f"{FIELD_MIXED_NCU['kernel']} at {FIELD_MIXED_NCU['splits']} splits; "
+                           "writes scaled to this launch's split count"),
         "peak_source": (f"derived: {GB300_SMS} SMs x {GB300_MAX_MHZ:g} MHz / (1/{MUFU_EX2_PER_CLK_SM}"
                         f" + 2/{MUFU_SINCOS_PER_CLK_SM}) clk per eval"),
         "kernel": "field_mixed_kernel", "kernel_ms_avg": k_avg_s * 1e3, "launches": kn,
