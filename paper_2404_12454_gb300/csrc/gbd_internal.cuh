@@ -193,9 +193,13 @@ struct gbd_instance_dev {
 cudaError_t gbd_launch_trace(const gbd_trace_params& p, int n_instances, int max_n_across,
                              const gbd_instance_dev* d_inst, gbd_beamlet* out, cudaStream_t s);
 // Batched trace + mixed projection straight into the tiled records (sweep set-up).
-cudaError_t gbd_launch_trace_project(const gbd_trace_params& p, int n_instances, int max_n_across,
-                                     const gbd_instance_dev* d_inst, const gbd_project_params& g,
-                                     float4* out, unsigned* wide, cudaStream_t s);
+// One thread per record; d_rows[d_rbase[k] + j] = first beamlet index of row j of
+// instance k (inside the instance).
+cudaError_t gbd_launch_trace_project(const gbd_trace_params& p, int n_instances,
+                                     const gbd_instance_dev* d_inst, const int* d_rbase,
+                                     const int* d_rows, long long n_records,
+                                     const gbd_project_params& g, float4* out, unsigned* wide,
+                                     cudaStream_t s);
 // `wide` (mixed only, may be null): set to 1 when some beamlet's phase may exceed the
 // wide-phase bound on this detector; the caller zeroes it first.
 cudaError_t gbd_launch_project(const gbd_beamlet* b, int n, const gbd_project_params& p,

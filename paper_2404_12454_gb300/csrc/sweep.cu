@@ -224,9 +224,11 @@ struct gbd_sweep_plan {
     int64_t total_tiles, total_beamlets;
     double evals;
     std::vector<gbd_instance_dev> inst;
+    std::vector<int> rbase, rows;  // per-instance row tables of the batched trace
     std::vector<int2> inst_tiles;
     std::vector<int2> items;
     size_t off_inst, off_itiles, off_items, off_airy, off_moments, off_counter, off_coef, bytes;
+    size_t off_rbase, off_rows;
     char* ws = nullptr;
     int device = -1;
     cudaGraphExec_t graph = nullptr;
@@ -254,9 +256,11 @@ static gbd_status sweep_enqueue(gbd_sweep_plan* P, double* scores, cudaStream_t 
     float4* coef = reinterpret_cast<float4*>(w + P->off_coef);
     cudaError_t e = cudaMemsetAsync(w + P->off_counter, 0, 256, s);
     if (e == cudaSuccess)
-        e = gbd_launch_trace_project(P->tp, P->n_inst, P->max_n,
-                                     reinterpret_cast<const gbd_instance_dev*>(w + P->off_inst), P->pp,
-                                     coef, wide, s);
+        e = gbd_launch_trace_project(P->tp, P->n_inst,
+                                     reinterpret_cast<const gbd_instance_dev*>(w + P->off_inst),
+                                     reinterpret_cast<const int*>(w + P->off_rbase),
+                                     reinterpret_cast<const int*>(w + P->off_rows),
+                                     P->total_tiles * gbd::kTile, P->pp, coef, wide, s);
     if (e == cudaSuccess) {
         const int grid = std::max(1, std::min(P->n_items, occ * gbd_sm_count()));
         e = sh->fn(dim3(grid), s, coef, reinterpret_cast<const int2*>(w + P->off_itiles),
@@ -317,6 +321,23 @@ gbd_status gbd_sweep_plan_create(const gbd_system* system, double diameter, cons
             return gbd_set_error(GBD_EINVAL, "instance with invalid n_across / OF / WR");
         }
         const int nt = (nb + gbd::kTile - 1) / gbd::kTile;
+        // first beamlet of each grid row: rows are contiguous runs of centres with
+        // (2i-(N-1))^2 + (2j-(N-1))^2 <= N^2
+        {
+            const long long N = n_across[k];
+            P->rbase.push_back((int)P->rows.size());
+            int acc = 0;
+            for (long long j = 0; j < N; ++j) {
+                P->rows.push_back(acc);
+                const long long b = 2 * j - (N - 1), r2 = N * N - b * b;
+                for (long long a = -(N - 1); a <= N - 1; a += 2)
+                    if (a * a <= r2) ++acc;
+            }
+            if (acc != nb) {
+                delete P;
+                return gbd_set_error(GBD_EINVAL, "internal: row table disagrees with the count");
+            }
+        }
         gbd_instance_dev I;
         I.n_across = n_across[k];
         I.reserved = nb;
@@ -350,6 +371,10 @@ gbd_status gbd_sweep_plan_create(const gbd_system* system, double diameter, cons
     off = align256(off + sizeof(gbd_instance_dev) * n_instances);
     P->off_itiles = off;
     off = align256(off + sizeof(int2) * n_instances);
+    P->off_rbase = off;
+    off = align256(off + sizeof(int) * P->rbase.size());
+    P->off_rows = off;
+    off = align256(off + sizeof(int) * P->rows.size());
     P->off_items = off;
     off = align256(off + sizeof(int2) * P->items.size());
     P->off_airy = off;
@@ -395,6 +420,12 @@ gbd_status gbd_sweep_bind(gbd_sweep_plan* P, void* workspace, size_t bytes, void
                             sizeof(int2) * P->inst_tiles.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(w + P->off_items, P->items.data(), sizeof(int2) * P->items.size(),
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(w + P->off_rbase, P->rbase.data(), sizeof(int) * P->rbase.size(),
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(w + P->off_rows, P->rows.data(), sizeof(int) * P->rows.size(),
                             cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) {
         const int npix = P->pp.nx * P->pp.ny;

@@ -116,8 +116,9 @@ __device__ void trace_one(const gbd_trace_params& P, int N, double OF, double WR
     }
     const cd detM = M[0] * M[3] - M[1] * M[2];
     // M^-1 = adj(M) / det
-    const cd Mi[4] = {gbd::cdiv(M[3], detM), gbd::cdiv(gbd::mk(0.0) - M[1], detM),
-                      gbd::cdiv(gbd::mk(0.0) - M[2], detM), gbd::cdiv(M[0], detM)};
+    const cd rdet = gbd::cdiv(gbd::mk(1.0), detM);
+    const cd Mi[4] = {M[3] * rdet, gbd::mk(0.0) - M[1] * rdet, gbd::mk(0.0) - M[2] * rdet,
+                      M[0] * rdet};
     cd Pm[4];
     Pm[0] = Nn[0] * Mi[0] + Nn[1] * Mi[2];
     Pm[1] = Nn[0] * Mi[1] + Nn[1] * Mi[3];
@@ -337,47 +338,55 @@ __global__ void __launch_bounds__(128) project_f64_kernel(const gbd_beamlet* __r
     for (int m = 0; m < gbd::kF64Fields; ++m) tile[m * gbd::kTile + l] = f[m];
 }
 
-// Batched trace + projection for a parameter sweep: instance blockIdx.y (its own N, OF,
-// WR) writes its mixed-precision records from record `offset` (a tile boundary), and the
-// CTA of its first row also writes the padding records up to the next tile boundary.
-__global__ void __launch_bounds__(128)
-    trace_project_kernel(gbd_trace_params P, const gbd_instance_dev* __restrict__ inst,
-                         gbd_project_params G, float4* __restrict__ out, unsigned* __restrict__ wide) {
-    const gbd_instance_dev I = inst[blockIdx.y];
-    const int N = I.n_across;
-    const int j = blockIdx.x;
-    if (j >= N) return;
-    __shared__ long long warp_sum[4];
-    long long acc = 0;
-    for (int q = threadIdx.x; q < j; q += blockDim.x) acc += row_extent(q, N) + 1;
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    const long long row_off = warp_sum[0] + warp_sum[1] + warp_sum[2] + warp_sum[3];
-    if (j == 0) {
-        const long long nb = I.reserved;  // beamlets of this instance
-        const long long pad_end = (nb + gbd::kTile - 1) / gbd::kTile * gbd::kTile;
-        Quad q;
-        q.pad = true;
-        for (long long t = nb + threadIdx.x; t < pad_end; t += blockDim.x) write_mixed(out, I.offset + t, q, G);
+// Batched trace + projection for a parameter sweep, one thread per record.  Records of
+// instance k start at inst[k].offset (a tile boundary); rows[rbase[k] + j] is the index,
+// inside the instance, of the first beamlet of grid row j.  Records between an instance's
+// last beamlet and the next tile boundary are written as padding.
+__global__ void __launch_bounds__(256)
+    trace_project_kernel(gbd_trace_params P, const gbd_instance_dev* __restrict__ inst, int n_inst,
+                         const int* __restrict__ rbase, const int* __restrict__ rows,
+                         long long n_records, gbd_project_params G, float4* __restrict__ out,
+                         unsigned* __restrict__ wide) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_records) return;
+    int lo = 0, hi = n_inst - 1;  // last instance starting at or before t
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        if (inst[mid].offset <= t) lo = mid;
+        else hi = mid - 1;
     }
-    const int a = row_extent(j, N);
-    if (a < 0) return;
-    const int i_lo = ((N - 1) - a) / 2;
-    for (int t = threadIdx.x; t <= a; t += blockDim.x) {
-        gbd_beamlet b;
-        trace_one(P, N, I.overlap_factor, I.waist_ratio, i_lo + t, j, &b);
-        if (write_mixed(out, I.offset + row_off + t, project_one(b, G), G) && wide) atomicOr(wide, 1u);
+    const gbd_instance_dev I = inst[lo];
+    const long long u = t - I.offset;
+    Quad q;
+    q.pad = true;
+    if (u < I.reserved) {
+        const int N = I.n_across;
+        const int* R = rows + rbase[lo];
+        int a = 0, b = N - 1;  // last row whose first beamlet is at or before u
+        while (a < b) {
+            const int m = (a + b + 1) / 2;
+            if (R[m] <= u) a = m;
+            else b = m - 1;
+        }
+        const int i = ((N - 1) - row_extent(a, N)) / 2 + (int)(u - R[a]);
+        gbd_beamlet bm;
+        trace_one(P, N, I.overlap_factor, I.waist_ratio, i, a, &bm);
+        q = project_one(bm, G);
     }
+    if (write_mixed(out, t, q, G) && wide) atomicOr(wide, 1u);
 }
 
 }  // namespace
 
-cudaError_t gbd_launch_trace_project(const gbd_trace_params& p, int n_instances, int max_n_across,
-                                     const gbd_instance_dev* d_inst, const gbd_project_params& g,
-                                     float4* out, unsigned* wide, cudaStream_t s) {
-    dim3 grid(max_n_across, n_instances);
-    trace_project_kernel<<<grid, 128, 0, s>>>(p, d_inst, g, out, wide);
+cudaError_t gbd_launch_trace_project(const gbd_trace_params& p, int n_instances,
+                                     const gbd_instance_dev* d_inst, const int* d_rbase,
+                                     const int* d_rows, long long n_records,
+                                     const gbd_project_params& g, float4* out, unsigned* wide,
+                                     cudaStream_t s) {
+    if (n_records <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((n_records + 255) / 256);
+    trace_project_kernel<<<blocks, 256, 0, s>>>(p, d_inst, n_instances, d_rbase, d_rows, n_records, g,
+                                                out, wide);
     return cudaGetLastError();
 }
 
