@@ -170,7 +170,9 @@ gbd_status gbd_field(const gbd_beamlet* beamlets, int32_t n_beamlets, double wav
  *          phase can exceed 256 rad on the detector, in which case gbd_field reduces every
  *          per-pixel phase exactly before sin/cos.
  *   F64:   16 doubles per beamlet [tile][field f = 0..7][b % 64][2 doubles], same order, the
- *          phase in turns (phase / 2 pi); wide_flag is not used.
+ *          phase in turns (phase / 2 pi), field 7 = S = exp of twice the uu coefficient as
+ *          a complex number (re, im), the second ratio of a row recurrence; wide_flag is
+ *          not used.
  * coeffs must hold gbd_project_bytes(n, precision) bytes. */
 size_t gbd_project_bytes(int32_t n_beamlets, int32_t precision);
 gbd_status gbd_project(const gbd_beamlet* beamlets, int32_t n_beamlets, double wavelength,
@@ -183,8 +185,9 @@ gbd_status gbd_project(const gbd_beamlet* beamlets, int32_t n_beamlets, double w
  * device with gbd_field_set_shape; gbd_autotune_field times the candidate shapes on the
  * given problem (synchronously, with CUDA events) and keeps the fastest. */
 typedef struct {
-    int32_t rows_per_thread;   /* mixed: 1x4, 2x2, 2x4, 4x2; F64: 1x2, 2x2    */
-    int32_t cols_per_thread;   /* (rows x cols)                               */
+    int32_t rows_per_thread;   /* mixed: 1x4, 2x2, 2x4, 4x2 (columns 32 apart);   */
+    int32_t cols_per_thread;   /* F64: 1x2, 2x2 (direct), 1x8, 2x8, 1x16, 1x32   */
+                               /* (contiguous row segments, complex recurrence)   */
     int32_t splits;            /* beamlet splits (0 = heuristic)             */
     float   ms;                /* measured time of the shape (autotune)      */
 } gbd_shape;

@@ -187,6 +187,126 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
+// FP64 path on contiguous row segments.  Along a row the exponent is quadratic in the
+// column, so E(u+1) = E(u) R(u) and R(u+1) = R(u) S with S = exp(2 c_uu) fixed per beamlet
+// (record field 7): per (beamlet, row segment) the thread evaluates E and R once with
+// exp2 + sincospi and then advances with two complex multiplies per pixel.  The products
+// keep FP64 relative precision; a beamlet whose amplitude at the segment's first pixel
+// is below 2^-1000 contributes zero to that segment (it cannot rise by 2^900 within the
+// CB pixels of a segment sampled by the detector).
+template <int RB, int CB>
+__global__ void __launch_bounds__(kThreads)
+    field_f64_row_kernel(const double2* __restrict__ coef, int n_tiles, int tiles_per_split,
+                         int nx, int ny, double2* __restrict__ partial, uint32_t spins) {
+    constexpr int kTileD2 = gbd::kF64Fields * gbd::kTile;
+    extern __shared__ __align__(128) double2 dyn[];
+    __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
+    __shared__ int flag;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int t0 = blockIdx.z * tiles_per_split;
+    gbd::init_stream_barriers(full, empty, tid);
+    gbd::TileStream<double2, kTileD2> ts{reinterpret_cast<double2(*)[kTileD2]>(dyn), full, empty,
+                                         coef + (size_t)t0 * kTileD2,
+                                         min(n_tiles - t0, tiles_per_split), 0,
+                                         gbd::kF64TileBytes, 0};
+    bool ok = ts.start(tid, spins, &flag);
+
+    // thread -> segment of CB columns x RB rows, segments numbered row-band by row-band
+    const int segs_x = (nx + CB - 1) / CB;
+    const long long seg = (long long)blockIdx.x * kThreads + tid;
+    const int col0 = (int)(seg % segs_x) * CB;
+    const int row0 = (int)(seg / segs_x) * RB;  // rows row0 .. row0 + RB - 1
+    double acc_re[RB][CB], acc_im[RB][CB];
+#pragma unroll
+    for (int r = 0; r < RB; ++r)
+#pragma unroll
+        for (int c = 0; c < CB; ++c) acc_re[r][c] = acc_im[r][c] = 0.0;
+
+    int k = 0;
+    for (; ok && k < ts.nt; ++k) {
+        if (!ts.acquire(k, spins)) {
+            ok = false;
+            break;
+        }
+        const double2* st = ts.tile(k);
+#pragma unroll 1
+        for (int b = 0; b < gbd::kTile; ++b) {
+            const double2 ij = st[b];
+            const double2 c0 = st[gbd::kTile + b];
+            const double2 cu = st[2 * gbd::kTile + b];
+            const double2 cv = st[3 * gbd::kTile + b];
+            const double2 cuu = st[4 * gbd::kTile + b];
+            const double2 cuv = st[5 * gbd::kTile + b];
+            const double2 cvv = st[6 * gbd::kTile + b];
+            const double2 S = st[7 * gbd::kTile + b];
+            const double tu = (double)col0 - ij.x;
+#pragma unroll
+            for (int r = 0; r < RB; ++r) {
+                const double tv = (double)(row0 + r) - ij.y;
+                const double ra = fma(tv, fma(cvv.x, tv, cv.x), c0.x);
+                const double rp = fma(tv, fma(cvv.y, tv, cv.y), c0.y);
+                const double sa = fma(cuv.x, tv, cu.x);
+                const double sp = fma(cuv.y, tv, cu.y);
+                // exponent at the first pixel and its step to the next
+                const double ea = fma(tu, fma(cuu.x, tu, sa), ra);
+                const double ep = fma(tu, fma(cuu.y, tu, sp), rp);
+                const double da = fma(cuu.x, 2.0 * tu + 1.0, sa);
+                const double dp = fma(cuu.y, 2.0 * tu + 1.0, sp);
+                double er = 0.0, ei = 0.0, rr, ri;
+                if (ea > -1000.0) {
+                    const double amp = exp2(ea);
+                    double sn, cs;
+                    sincospi(2.0 * (ep - rint(ep)), &sn, &cs);
+                    er = amp * cs;
+                    ei = amp * sn;
+                }
+                {
+                    const double amp = exp2(da);
+                    double sn, cs;
+                    sincospi(2.0 * (dp - rint(dp)), &sn, &cs);
+                    rr = amp * cs;
+                    ri = amp * sn;
+                }
+#pragma unroll
+                for (int c = 0; c < CB; ++c) {
+                    acc_re[r][c] += er;
+                    acc_im[r][c] += ei;
+                    const double nr = fma(er, rr, -ei * ri), ni = fma(er, ri, ei * rr);
+                    er = nr;
+                    ei = ni;
+                    const double mr = fma(rr, S.x, -ri * S.y), mi = fma(rr, S.y, ri * S.x);
+                    rr = mr;
+                    ri = mi;
+                }
+            }
+        }
+        if (!ts.release(k, lane, warp, spins)) {
+            ok = false;
+            ++k;
+            break;
+        }
+    }
+    if (!ok) {
+        record_timeout();
+        if (tid == 0) ts.drain(k, spins);
+        return;
+    }
+    const size_t npix = (size_t)nx * ny;
+    double2* out = partial + (size_t)blockIdx.z * npix;
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+        const int row = row0 + r;
+        if (row >= ny) continue;
+#pragma unroll
+        for (int c = 0; c < CB; ++c) {
+            const int col = col0 + c;
+            if (col >= nx) continue;
+            out[(size_t)row * nx + col] = make_double2(acc_re[r][c], acc_im[r][c]);
+        }
+    }
+}
+
 // Fixed-order FP64 sum of the split partials, times the carrier exp(-ik z(s)) of each
 // pixel (z = n.s is the axial offset of the tilted plane), written as complex64/128.
 template <bool F64>
@@ -245,6 +365,22 @@ cudaError_t launch_f64(const void* coeffs, int n_tiles, const gbd_project_params
     return cudaGetLastError();
 }
 
+template <int RB, int CB>
+cudaError_t launch_f64_row(const void* coeffs, int n_tiles, const gbd_project_params& p,
+                           const gbd_field_launch& L, double2* partial, const unsigned* /*wide*/,
+                           uint32_t spins, cudaStream_t s) {
+    const size_t smem = (size_t)kStages * gbd::kF64TileBytes;
+    cudaError_t e = cudaFuncSetAttribute(field_f64_row_kernel<RB, CB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const long long segs = (long long)((p.nx + CB - 1) / CB) * ((p.ny + RB - 1) / RB);
+    dim3 grid((unsigned)((segs + kThreads - 1) / kThreads), 1, L.splits);
+    field_f64_row_kernel<RB, CB><<<grid, kThreads, smem, s>>>(static_cast<const double2*>(coeffs),
+                                                              n_tiles, L.tiles_per_split, p.nx,
+                                                              p.ny, partial, spins);
+    return cudaGetLastError();
+}
+
 typedef cudaError_t (*launch_fn)(const void*, int, const gbd_project_params&,
                                  const gbd_field_launch&, double2*, const unsigned*, uint32_t,
                                  cudaStream_t);
@@ -261,9 +397,15 @@ const ShapeEntry kMixedShapes[] = {
     {2, 4, launch_mixed<2, 4>, (const void*)field_mixed_kernel<2, 4, false>},
     {4, 2, launch_mixed<4, 2>, (const void*)field_mixed_kernel<4, 2, false>},
 };
+// (1,2), (2,2): every pixel evaluated directly (columns 32 apart); (1,8), (1,16), (2,8),
+// (1,32): contiguous row segments advanced by complex multiplies.
 const ShapeEntry kF64Shapes[] = {
     {1, 2, launch_f64<1, 2>, (const void*)field_f64_kernel<1, 2>},
     {2, 2, launch_f64<2, 2>, (const void*)field_f64_kernel<2, 2>},
+    {1, 8, launch_f64_row<1, 8>, (const void*)field_f64_row_kernel<1, 8>},
+    {2, 8, launch_f64_row<2, 8>, (const void*)field_f64_row_kernel<2, 8>},
+    {1, 16, launch_f64_row<1, 16>, (const void*)field_f64_row_kernel<1, 16>},
+    {1, 32, launch_f64_row<1, 32>, (const void*)field_f64_row_kernel<1, 32>},
 };
 
 const ShapeEntry* find_shape(int precision, int rb, int cb) {

@@ -207,8 +207,8 @@ size_t tile_bytes(int precision) {
 
 gbd_shape default_shape(int precision) {
     gbd_shape s;
-    s.rows_per_thread = 2;
-    s.cols_per_thread = precision == GBD_PREC_MIXED ? 4 : 2;
+    s.rows_per_thread = precision == GBD_PREC_MIXED ? 2 : 1;
+    s.cols_per_thread = precision == GBD_PREC_MIXED ? 4 : 16;
     s.splits = 0;
     s.ms = 0.f;
     return s;
@@ -223,8 +223,18 @@ gbd_shape stored_shape(int precision) {
 // Beamlet splits: enough CTAs for about 16 waves of resident CTAs, so that the last,
 // partly filled wave costs little (measured on GB300: 16 waves beat 4 by ~5 % on the
 // 512^2-pixel, 51k-beamlet field), without splitting a beamlet range below 8 tiles.
+// CTAs per beamlet split: pixel blocks of 32 cb x 8 rb (columns 32 apart), or for the FP64
+// row-segment shapes (cb >= 8) 256 segments of cb x rb pixels.
+long pixel_ctas(int precision, int rb, int cb, const gbd_detector* D) {
+    if (precision == GBD_PREC_F64 && cb >= 8) {
+        const long segs = (long)((D->nx + cb - 1) / cb) * ((D->ny + rb - 1) / rb);
+        return (segs + 255) / 256;
+    }
+    return (long)((D->nx + 32 * cb - 1) / (32 * cb)) * ((D->ny + 8 * rb - 1) / (8 * rb));
+}
+
 int heuristic_splits(int precision, int rb, int cb, int n_tiles, const gbd_detector* D) {
-    const long pix_ctas = (long)((D->nx + 32 * cb - 1) / (32 * cb)) * ((D->ny + 8 * rb - 1) / (8 * rb));
+    const long pix_ctas = pixel_ctas(precision, rb, cb, D);
     const int occ = std::max(1, gbd_field_occupancy(precision, rb, cb));
     const long slots = (long)occ * sm_count();
     long s = (16 * slots + pix_ctas - 1) / pix_ctas;
@@ -506,7 +516,7 @@ gbd_status gbd_autotune_field(const gbd_beamlet* beamlets, int32_t n_beamlets, d
     if (n_beamlets == 0) return fail(GBD_EINVAL, "autotune needs at least one beamlet");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     static const int kMixed[][2] = {{1, 4}, {2, 2}, {2, 4}, {4, 2}};
-    static const int kF64[][2] = {{1, 2}, {2, 2}};
+    static const int kF64[][2] = {{1, 2}, {2, 2}, {1, 8}, {2, 8}, {1, 16}, {1, 32}};
     std::vector<std::pair<int, int>> shapes;
     if (precision == GBD_PREC_MIXED)
         for (auto& v : kMixed) shapes.push_back({v[0], v[1]});

@@ -331,7 +331,12 @@ __global__ void __launch_bounds__(128) project_f64_kernel(const gbd_beamlet* __r
     } else {
         f[0] = make_double2(q.i0, q.j0);
         for (int m = 0; m < 6; ++m) f[1 + m] = make_double2(q.a[m], q.p[m]);
-        f[7] = make_double2(0.0, 0.0);
+        // S = E(u+2)E(u)/E(u+1)^2 = exp of twice the uu coefficient, for row recurrences
+        const double sa = exp2(2.0 * q.a[3]);
+        const double sp = 2.0 * q.p[3];
+        double sn, cs;
+        sincospi(2.0 * (sp - rint(sp)), &sn, &cs);
+        f[7] = make_double2(sa * cs, sa * sn);
     }
     double2* tile = out + (size_t)(t / gbd::kTile) * gbd::kF64Fields * gbd::kTile;
     const int l = t % gbd::kTile;

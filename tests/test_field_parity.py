@@ -177,7 +177,8 @@ def test_every_shape_and_split_matches(prec):
     wl = small_cases()["tilted_zernike_small"]
     b = gpu_trace(wl)
     Eo = oracle.field(oracle.trace(wl.system, wl.pupil), wl.system, wl.detector)
-    shapes = [(1, 4), (2, 2), (2, 4), (4, 2)] if prec == gbd.GBD_PREC_MIXED else [(1, 2), (2, 2)]
+    shapes = ([(1, 4), (2, 2), (2, 4), (4, 2)] if prec == gbd.GBD_PREC_MIXED
+              else [(1, 2), (2, 2), (1, 8), (2, 8), (1, 16), (1, 32)])
     try:
         for rows, cols in shapes:
             for splits in (1, 2, 5):
