@@ -266,6 +266,10 @@ gbd_status gbd_timing_read(double* total_ms, int64_t* launches);
  *   stream, not the legacy default stream.
  * gbd_sweep_autotune: times every supported shape on the given instances (synchronous)
  *   and returns the fastest; the workspace must hold the largest plan.
+ * gbd_sweep_set_zones: optional annular zones lo[z] <= r / (lambda F#) < hi[z] (Sec. 6 uses
+ *   0-5, 5-10, 10-15 lambda/D), at most 7, before gbd_sweep_bind; the scores array then
+ *   holds 1 + n_zones doubles per instance: the score above, then the same RMS over
+ *   each zone (same |E(centre)| normalisation).
  * gbd_sweep_info: total beamlet-pixel evaluations, beamlets and work items of a plan. */
 typedef struct gbd_sweep_plan gbd_sweep_plan;
 gbd_status gbd_sweep_plan_create(const gbd_system* system, double diameter, const int32_t* n_across,
@@ -273,6 +277,8 @@ gbd_status gbd_sweep_plan_create(const gbd_system* system, double diameter, cons
                                  int32_t n_instances, const gbd_detector* detector,
                                  const gbd_shape* shape, gbd_sweep_plan** plan);
 size_t gbd_sweep_workspace_bytes(const gbd_sweep_plan* plan);
+gbd_status gbd_sweep_set_zones(gbd_sweep_plan* plan, int32_t n_zones, const double* lo,
+                               const double* hi);
 gbd_status gbd_sweep_info(const gbd_sweep_plan* plan, double* evals, int64_t* beamlets,
                           int32_t* items);
 gbd_status gbd_sweep_bind(gbd_sweep_plan* plan, void* workspace, size_t bytes, void* stream);

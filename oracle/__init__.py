@@ -55,6 +55,8 @@ def lib():
         L.orc_airy_amp.restype = _D
         L.orc_airy_score.argtypes = [_PD, _I, _I, _D, _D, _D, _D]
         L.orc_airy_score.restype = _D
+        L.orc_zone_score.argtypes = [_PD, _I, _I, _D, _D, _D, _D, _D, _D]
+        L.orc_zone_score.restype = _D
         _lib = L
     return _lib
 
@@ -154,6 +156,14 @@ def airy_score(field_: np.ndarray, detector, wavelength: float, f_number: float)
     f = np.ascontiguousarray(np.stack([field_.real, field_.imag], axis=-1), dtype=np.float64)
     return lib().orc_airy_score(_pd(f), detector.nx, detector.ny, detector.pitch_x,
                                 detector.pitch_y, wavelength, f_number)
+
+
+def zone_score(field_: np.ndarray, detector, wavelength: float, f_number: float, lo: float,
+               hi: float) -> float:
+    """RMS of |E|/|E(centre)| - |2 J1(x)/x| over lo <= r/(lambda F#) < hi (Sec. 6 zones)."""
+    f = np.ascontiguousarray(np.stack([field_.real, field_.imag], axis=-1), dtype=np.float64)
+    return lib().orc_zone_score(_pd(f), detector.nx, detector.ny, detector.pitch_x,
+                                detector.pitch_y, wavelength, f_number, lo, hi)
 
 
 def unpack(rec: np.ndarray) -> dict:

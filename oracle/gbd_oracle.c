@@ -436,6 +436,27 @@ double orc_airy_amp(double r, double wavelength, double fnum) {
     return fabs(2.0 * j1(x) / x);
 }
 
+/* RMS of |E|/|E(centre)| - A over the pixels with lo <= r / (lambda F#) < hi (an annular
+ * zone, Sec. 6).  Same layout and normalisation as orc_airy_score. */
+double orc_zone_score(const double* field, int nx, int ny, double px, double py,
+                      double wavelength, double fnum, double lo, double hi) {
+    const double* ec = field + 2 * ((size_t)(ny / 2) * nx + nx / 2);
+    double e0 = hypot(ec[0], ec[1]);
+    double acc = 0.0;
+    long n = 0;
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            double sx = (i - nx / 2) * px, sy = (j - ny / 2) * py;
+            double r = hypot(sx, sy), u = r / (wavelength * fnum);
+            if (u < lo || u >= hi) continue;
+            const double* e = field + 2 * ((size_t)j * nx + i);
+            double diff = hypot(e[0], e[1]) / e0 - orc_airy_amp(r, wavelength, fnum);
+            acc += diff * diff;
+            ++n;
+        }
+    return sqrt(acc / (double)n);
+}
+
 /* RMS of |E|/|E(centre)| - A over the pixels with r <= r3, r3 = j_{1,3} lambda F# / pi
  * (inside the third dark ring).  field: ny x nx complex (re, im interleaved); the
  * centre pixel is (nx/2, ny/2).  Untilted detector. */

@@ -28,11 +28,20 @@ using gbd::kWarps;
 
 __device__ unsigned int g_sweep_status = 0;
 
-constexpr int kMoments = 5;  // S2, S1, S0, n, e0
+// Score regions: region 0 is the disc inside the third dark ring (r <= j_{1,3} lambda F#/pi),
+// regions 1.. are optional annular zones lo <= r/(lambda F#) < hi.  Per region the
+// moments S2 = sum |E|^2, S1 = sum |E| A, S0 = sum A^2 and the pixel count n.
+constexpr int kMaxRegions = 8;
 
-// |2 J1(x)/x| with x = pi r / (lambda F#), and whether r <= r3, per detector pixel.
+struct Regions {
+    int n;
+    double lo[kMaxRegions], hi[kMaxRegions];  // in lambda F# (region 0: [0, r3] closed)
+};
+
+// Per pixel: |2 J1(x)/x| with x = pi r / (lambda F#), and the bit mask of the regions the
+// pixel belongs to.
 __global__ void __launch_bounds__(256) airy_table_kernel(int nx, int ny, double px, double py,
-                                                         double lam_fnum, double r3,
+                                                         double lam_fnum, Regions R,
                                                          double2* __restrict__ out) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= nx * ny) return;
@@ -41,7 +50,11 @@ __global__ void __launch_bounds__(256) airy_table_kernel(int nx, int ny, double 
     const double r = hypot(sx, sy);
     const double x = M_PI * r / lam_fnum;
     const double a = x == 0.0 ? 1.0 : fabs(2.0 * j1(x) / x);
-    out[p] = make_double2(a, r <= r3 ? 1.0 : 0.0);
+    const double u = r / lam_fnum;
+    unsigned mask = u <= R.hi[0] ? 1u : 0u;
+    for (int z = 1; z < R.n; ++z)
+        if (u >= R.lo[z] && u < R.hi[z]) mask |= 1u << z;
+    out[p] = make_double2(a, (double)mask);
 }
 
 // WIDE: as in field_mixed_kernel, both instantiations are launched and the projection's
@@ -50,14 +63,16 @@ template <int RB, int CB, bool WIDE>
 __global__ void __launch_bounds__(kThreads, 2)
     sweep_kernel(const float4* __restrict__ coef, const int2* __restrict__ inst_tiles,
                  const int2* __restrict__ items, int n_items, int tiles_x, int n_blocks, int nx,
-                 int ny, const double2* __restrict__ airy, double* __restrict__ moments,
-                 int* __restrict__ counter, const unsigned* __restrict__ wide, uint32_t spins) {
+                 int ny, const double2* __restrict__ airy, int n_regions,
+                 double* __restrict__ moments, int* __restrict__ counter,
+                 const unsigned* __restrict__ wide, uint32_t spins) {
     if ((*wide != 0u) != WIDE) return;
     constexpr int kTileF4 = gbd::kMixedFields * gbd::kTile;
     __shared__ __align__(128) float4 stage[kStages][kTileF4];
     __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
     __shared__ int flag, s_item;
-    __shared__ double red[kWarps][kMoments];
+    __shared__ double red[kWarps][kMaxRegions][4];
+    __shared__ double red_e0[kWarps];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     gbd::init_stream_barriers(full, empty, tid);
@@ -110,84 +125,111 @@ __global__ void __launch_bounds__(kThreads, 2)
         }
         g += ts.nt;
 
-        double m[kMoments] = {0.0, 0.0, 0.0, 0.0, -1.0};
+        // epilogue: |E| per pixel, then per region the moments of this item's pixels
+        double mag[RB][CB], amp[RB][CB];
+        unsigned msk[RB][CB];
+        double e0 = -1.0;
 #pragma unroll
-        for (int r = 0; r < RB; ++r) {
-            const int row = row0 + 8 * r;
-            if (row >= ny) continue;
+        for (int r = 0; r < RB; ++r)
 #pragma unroll
             for (int c = 0; c < CB; ++c) {
-                const int col = col0 + 32 * c;
-                if (col >= nx) continue;
+                const int row = row0 + 8 * r, col = col0 + 32 * c;
                 const double re = (double)hi[r][c].x + (double)lo[r][c].x;
                 const double im = (double)hi[r][c].y + (double)lo[r][c].y;
-                const double mag = sqrt(re * re + im * im);
-                const double2 A = airy[(size_t)row * nx + col];
-                if (A.y != 0.0) {
-                    m[0] += mag * mag;
-                    m[1] += mag * A.x;
-                    m[2] += A.x * A.x;
-                    m[3] += 1.0;
+                mag[r][c] = sqrt(re * re + im * im);
+                amp[r][c] = 0.0;
+                msk[r][c] = 0u;
+                if (row < ny && col < nx) {
+                    const double2 A = airy[(size_t)row * nx + col];
+                    amp[r][c] = A.x;
+                    msk[r][c] = (unsigned)A.y;
+                    if (row == ny / 2 && col == nx / 2) e0 = mag[r][c];
                 }
-                if (row == ny / 2 && col == nx / 2) m[4] = mag;
+            }
+        for (int o = 16; o > 0; o >>= 1) e0 = fmax(e0, __shfl_xor_sync(0xffffffffu, e0, o));
+        if (lane == 0) red_e0[warp] = e0;
+        for (int z = 0; z < n_regions; ++z) {
+            double m0 = 0.0, m1 = 0.0, m2 = 0.0, m3 = 0.0;
+#pragma unroll
+            for (int r = 0; r < RB; ++r)
+#pragma unroll
+                for (int c = 0; c < CB; ++c)
+                    if (msk[r][c] & (1u << z)) {
+                        m0 += mag[r][c] * mag[r][c];
+                        m1 += mag[r][c] * amp[r][c];
+                        m2 += amp[r][c] * amp[r][c];
+                        m3 += 1.0;
+                    }
+            for (int o = 16; o > 0; o >>= 1) {
+                m0 += __shfl_xor_sync(0xffffffffu, m0, o);
+                m1 += __shfl_xor_sync(0xffffffffu, m1, o);
+                m2 += __shfl_xor_sync(0xffffffffu, m2, o);
+                m3 += __shfl_xor_sync(0xffffffffu, m3, o);
+            }
+            if (lane == 0) {
+                red[warp][z][0] = m0;
+                red[warp][z][1] = m1;
+                red[warp][z][2] = m2;
+                red[warp][z][3] = m3;
             }
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) m[q] += __shfl_xor_sync(0xffffffffu, m[q], o);
-            m[4] = fmax(m[4], __shfl_xor_sync(0xffffffffu, m[4], o));
-        }
-        if (lane == 0)
-#pragma unroll
-            for (int q = 0; q < kMoments; ++q) red[warp][q] = m[q];
         __syncthreads();
+        // one slot per item: e0, then 4 moments per region, summed over warps in order
+        const int stride = 1 + 4 * n_regions;
+        double* dst = moments + ((size_t)it.x * n_blocks + it.y) * stride;
         if (tid == 0) {
-            double s[kMoments] = {0.0, 0.0, 0.0, 0.0, -1.0};
-            for (int w = 0; w < kWarps; ++w) {
-                for (int q = 0; q < 4; ++q) s[q] += red[w][q];
-                s[4] = fmax(s[4], red[w][4]);
-            }
-            double* dst = moments + ((size_t)it.x * n_blocks + it.y) * kMoments;
-            for (int q = 0; q < kMoments; ++q) dst[q] = s[q];
+            double s = -1.0;
+            for (int w = 0; w < kWarps; ++w) s = fmax(s, red_e0[w]);
+            dst[0] = s;
+        }
+        if (tid < 4 * n_regions) {
+            const int z = tid / 4, q = tid % 4;
+            double s = 0.0;
+            for (int w = 0; w < kWarps; ++w) s += red[w][z][q];
+            dst[1 + tid] = s;
         }
     }
 }
 
-// Per instance, the moments of its pixel blocks summed in block order, then the score.
+// Per instance, the moments of its pixel blocks summed in block order, then one score per
+// region: scores[k * n_regions + z].
 __global__ void __launch_bounds__(128) sweep_finalize_kernel(const double* __restrict__ moments,
                                                              int n_inst, int n_blocks,
+                                                             int n_regions,
                                                              double* __restrict__ scores) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n_inst) return;
-    double s[kMoments] = {0.0, 0.0, 0.0, 0.0, -1.0};
-    for (int t = 0; t < n_blocks; ++t) {
-        const double* m = moments + ((size_t)k * n_blocks + t) * kMoments;
-        for (int q = 0; q < 4; ++q) s[q] += m[q];
-        s[4] = fmax(s[4], m[4]);
+    const int stride = 1 + 4 * n_regions;
+    double e0 = -1.0;
+    for (int t = 0; t < n_blocks; ++t) e0 = fmax(e0, moments[((size_t)k * n_blocks + t) * stride]);
+    for (int z = 0; z < n_regions; ++z) {
+        double s[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int t = 0; t < n_blocks; ++t) {
+            const double* m = moments + ((size_t)k * n_blocks + t) * stride + 1 + 4 * z;
+            for (int q = 0; q < 4; ++q) s[q] += m[q];
+        }
+        double score = nan("");
+        if (e0 > 0.0 && s[3] > 0.0)
+            score = sqrt(fmax(0.0, (s[0] / (e0 * e0) - 2.0 * s[1] / e0 + s[2]) / s[3]));
+        scores[(size_t)k * n_regions + z] = score;
     }
-    const double e0 = s[4];
-    double score = nan("");
-    if (e0 > 0.0 && s[3] > 0.0)
-        score = sqrt(fmax(0.0, (s[0] / (e0 * e0) - 2.0 * s[1] / e0 + s[2]) / s[3]));
-    scores[k] = score;
 }
 
 typedef cudaError_t (*sweep_launch_fn)(dim3, cudaStream_t, const float4*, const int2*, const int2*,
-                                       int, int, int, int, int, const double2*, double*, int*,
+                                       int, int, int, int, int, const double2*, int, double*, int*,
                                        const unsigned*, uint32_t);
 
 template <int RB, int CB>
 cudaError_t launch_sweep(dim3 grid, cudaStream_t s, const float4* coef, const int2* it_tiles,
                          const int2* items, int n_items, int tiles_x, int n_blocks, int nx, int ny,
-                         const double2* airy, double* moments, int* counter, const unsigned* wide,
-                         uint32_t spins) {
+                         const double2* airy, int n_regions, double* moments, int* counter,
+                         const unsigned* wide, uint32_t spins) {
     sweep_kernel<RB, CB, false><<<grid, kThreads, 0, s>>>(coef, it_tiles, items, n_items, tiles_x,
-                                                          n_blocks, nx, ny, airy, moments, counter,
-                                                          wide, spins);
+                                                          n_blocks, nx, ny, airy, n_regions,
+                                                          moments, counter, wide, spins);
     sweep_kernel<RB, CB, true><<<grid, kThreads, 0, s>>>(coef, it_tiles, items, n_items, tiles_x,
-                                                         n_blocks, nx, ny, airy, moments, counter,
-                                                         wide, spins);
+                                                         n_blocks, nx, ny, airy, n_regions,
+                                                         moments, counter, wide, spins);
     return cudaGetLastError();
 }
 
@@ -220,6 +262,7 @@ struct gbd_sweep_plan {
     gbd_trace_params tp;
     gbd_project_params pp;
     double lam_fnum, r3;
+    Regions regions;
     int n_inst, max_n, rb, cb, tiles_x, tiles_y, n_blocks, n_items;
     int64_t total_tiles, total_beamlets;
     double evals;
@@ -266,15 +309,40 @@ static gbd_status sweep_enqueue(gbd_sweep_plan* P, double* scores, cudaStream_t 
         e = sh->fn(dim3(grid), s, coef, reinterpret_cast<const int2*>(w + P->off_itiles),
                    reinterpret_cast<const int2*>(w + P->off_items), P->n_items, P->tiles_x,
                    P->n_blocks, P->pp.nx, P->pp.ny, reinterpret_cast<const double2*>(w + P->off_airy),
-                   reinterpret_cast<double*>(w + P->off_moments), counter, wide, gbd_wait_spins());
+                   P->regions.n, reinterpret_cast<double*>(w + P->off_moments), counter, wide,
+                   gbd_wait_spins());
     }
     if (e == cudaSuccess) {
         sweep_finalize_kernel<<<(P->n_inst + 127) / 128, 128, 0, s>>>(
-            reinterpret_cast<const double*>(w + P->off_moments), P->n_inst, P->n_blocks, scores);
+            reinterpret_cast<const double*>(w + P->off_moments), P->n_inst, P->n_blocks,
+            P->regions.n, scores);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return gbd_set_error(GBD_ECUDA, cudaGetErrorString(e));
     return GBD_OK;
+}
+
+static void sweep_layout(gbd_sweep_plan* P, int nx, int ny) {
+    size_t off = 0;
+    P->off_counter = off;
+    off += 256;
+    P->off_inst = off;
+    off = align256(off + sizeof(gbd_instance_dev) * P->n_inst);
+    P->off_itiles = off;
+    off = align256(off + sizeof(int2) * P->n_inst);
+    P->off_rbase = off;
+    off = align256(off + sizeof(int) * P->rbase.size());
+    P->off_rows = off;
+    off = align256(off + sizeof(int) * P->rows.size());
+    P->off_items = off;
+    off = align256(off + sizeof(int2) * P->items.size());
+    P->off_airy = off;
+    off = align256(off + sizeof(double2) * (size_t)nx * ny);
+    P->off_moments = off;
+    off = align256(off + sizeof(double) * (1 + 4 * P->regions.n) * (size_t)P->n_inst * P->n_blocks);
+    P->off_coef = off;
+    off = align256(off + (size_t)P->total_tiles * gbd::kMixedTileBytes);
+    P->bytes = off;
 }
 
 extern "C" {
@@ -303,6 +371,9 @@ gbd_status gbd_sweep_plan_create(const gbd_system* system, double diameter, cons
     P->pp = gbd_make_project_params(system->wavelength, detector);
     P->lam_fnum = system->wavelength * fabs(system->focal_length) / diameter;
     P->r3 = 10.173468135062722 * P->lam_fnum / M_PI;  // third zero of J1
+    P->regions.n = 1;
+    P->regions.lo[0] = 0.0;
+    P->regions.hi[0] = 10.173468135062722 / M_PI;
     P->n_inst = n_instances;
     P->rb = rb;
     P->cb = cb;
@@ -364,31 +435,31 @@ gbd_status gbd_sweep_plan_create(const gbd_system* system, double diameter, cons
     for (int k : order)
         for (int t = 0; t < P->n_blocks; ++t) P->items.push_back(make_int2(k, t));
     P->n_items = (int)P->items.size();
-    size_t off = 0;
-    P->off_counter = off;
-    off += 256;
-    P->off_inst = off;
-    off = align256(off + sizeof(gbd_instance_dev) * n_instances);
-    P->off_itiles = off;
-    off = align256(off + sizeof(int2) * n_instances);
-    P->off_rbase = off;
-    off = align256(off + sizeof(int) * P->rbase.size());
-    P->off_rows = off;
-    off = align256(off + sizeof(int) * P->rows.size());
-    P->off_items = off;
-    off = align256(off + sizeof(int2) * P->items.size());
-    P->off_airy = off;
-    off = align256(off + sizeof(double2) * detector->nx * detector->ny);
-    P->off_moments = off;
-    off = align256(off + sizeof(double) * kMoments * (size_t)n_instances * P->n_blocks);
-    P->off_coef = off;
-    off = align256(off + (size_t)tile * gbd::kMixedTileBytes);
-    P->bytes = off;
+    sweep_layout(P, detector->nx, detector->ny);
     *plan = P;
     return GBD_OK;
 }
 
 size_t gbd_sweep_workspace_bytes(const gbd_sweep_plan* plan) { return plan ? plan->bytes : 0; }
+
+gbd_status gbd_sweep_set_zones(gbd_sweep_plan* P, int32_t n_zones, const double* lo,
+                               const double* hi) {
+    if (!P) return gbd_set_error(GBD_EINVAL, "plan is NULL");
+    if (P->ws) return gbd_set_error(GBD_EINVAL, "set zones before gbd_sweep_bind");
+    if (n_zones < 0 || n_zones > kMaxRegions - 1)
+        return gbd_set_error(GBD_EINVAL, "n_zones must be in [0, 7]");
+    if (n_zones > 0 && (!lo || !hi)) return gbd_set_error(GBD_EINVAL, "zone bounds are NULL");
+    for (int z = 0; z < n_zones; ++z)
+        if (!(lo[z] >= 0.0) || !(hi[z] > lo[z]) || !isfinite(hi[z]))
+            return gbd_set_error(GBD_EINVAL, "zone bounds must satisfy 0 <= lo < hi < inf");
+    P->regions.n = 1 + n_zones;
+    for (int z = 0; z < n_zones; ++z) {
+        P->regions.lo[1 + z] = lo[z];
+        P->regions.hi[1 + z] = hi[z];
+    }
+    sweep_layout(P, P->pp.nx, P->pp.ny);
+    return GBD_OK;
+}
 
 gbd_status gbd_sweep_info(const gbd_sweep_plan* plan, double* evals, int64_t* beamlets,
                           int32_t* items) {
@@ -430,7 +501,7 @@ gbd_status gbd_sweep_bind(gbd_sweep_plan* P, void* workspace, size_t bytes, void
     if (e == cudaSuccess) {
         const int npix = P->pp.nx * P->pp.ny;
         airy_table_kernel<<<(npix + 255) / 256, 256, 0, s>>>(
-            P->pp.nx, P->pp.ny, P->pp.px, P->pp.py, P->lam_fnum, P->r3,
+            P->pp.nx, P->pp.ny, P->pp.px, P->pp.py, P->lam_fnum, P->regions,
             reinterpret_cast<double2*>(w + P->off_airy));
         e = cudaGetLastError();
     }

@@ -86,6 +86,8 @@ _SIGS = {
                                              ctypes.POINTER(gbd_detector), ctypes.POINTER(gbd_shape),
                                              ctypes.POINTER(ctypes.c_void_p)]),
     "gbd_sweep_workspace_bytes": (ctypes.c_size_t, [_P]),
+    "gbd_sweep_set_zones": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_double)]),
     "gbd_sweep_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]),
     "gbd_sweep_bind": (ctypes.c_int, [_P, _P, ctypes.c_size_t, _P]),
@@ -307,7 +309,8 @@ class SweepPlan:
     run() returns the Airy scores as a float64 CUDA tensor."""
 
     def __init__(self, system, diameter, n_across, overlap_factor, waist_ratio, detector,
-                 shape: Optional[Tuple[int, int]] = None, stream=None, device="cuda"):
+                 shape: Optional[Tuple[int, int]] = None, stream=None, device="cuda",
+                 zones: Optional[Sequence[Tuple[float, float]]] = None):
         import torch
         n, a, b, c = _instance_arrays(n_across, overlap_factor, waist_ratio)
         self.n = n
@@ -317,9 +320,15 @@ class SweepPlan:
                                            c, n, ctypes.byref(make_detector(detector)),
                                            ctypes.byref(sh) if sh else None,
                                            ctypes.byref(self._plan)))
+        self.n_regions = 1
+        if zones:
+            lo = (ctypes.c_double * len(zones))(*[float(z[0]) for z in zones])
+            hi = (ctypes.c_double * len(zones))(*[float(z[1]) for z in zones])
+            _check(lib().gbd_sweep_set_zones(self._plan, len(zones), lo, hi))
+            self.n_regions = 1 + len(zones)
         self.bytes = int(lib().gbd_sweep_workspace_bytes(self._plan))
         self.ws = torch.empty(self.bytes, dtype=torch.uint8, device=device)
-        self.scores = torch.empty(n, dtype=torch.float64, device=device)
+        self.scores = torch.empty(n * self.n_regions, dtype=torch.float64, device=device)
         _check(lib().gbd_sweep_bind(self._plan, _ptr(self.ws), ctypes.c_size_t(self.bytes),
                                     _stream(stream)))
         ev, nb, items = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int32()
@@ -328,9 +337,10 @@ class SweepPlan:
         self.evals, self.beamlets, self.items = float(ev.value), int(nb.value), int(items.value)
 
     def run(self, stream=None, graph: bool = False):
+        """Scores as a float64 CUDA tensor: [n] without zones, [n, 1 + zones] with."""
         fn = lib().gbd_sweep_run_graph if graph else lib().gbd_sweep_run
         _check(fn(self._plan, _ptr(self.scores), _stream(stream)))
-        return self.scores
+        return self.scores if self.n_regions == 1 else self.scores.view(self.n, self.n_regions)
 
     def close(self):
         if getattr(self, "_plan", None) is not None and self._plan.value:
@@ -344,10 +354,10 @@ class SweepPlan:
             pass
 
 
-def sweep_plan(sw, shape=None, stream=None) -> SweepPlan:
+def sweep_plan(sw, shape=None, stream=None, zones=None) -> SweepPlan:
     """SweepPlan for a workloads.Sweep description."""
     return SweepPlan(sw.system, sw.diameter, sw.n_across, sw.overlap_factor, sw.waist_ratio,
-                     sw.detector, shape, stream)
+                     sw.detector, shape, stream, zones=zones)
 
 
 def gbd_sweep_autotune(system, diameter, n_across, overlap_factor, waist_ratio, detector,

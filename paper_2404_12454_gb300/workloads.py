@@ -192,6 +192,25 @@ def grid_sweep() -> Sweep:
     return Sweep(system, D, det, tuple(n), tuple(of), tuple(wr))
 
 
+# Annular zones of Sec. 6, in lambda/D (= lambda F# on the focal plane).
+PAPER_ZONES = ((0.0, 5.0), (5.0, 10.0), (10.0, 15.0))
+
+
+def zone_sweep(of_values: Sequence[float] = tuple(np.linspace(1.0, 2.0, 11)),
+               n_across: Sequence[int] = (32, 64, 128, 256), waist_ratio: float = 1.0) -> Sweep:
+    """OF x N grid on the airy optics with a 512x512 detector over +-15.2 lambda F#: the
+    paper's parameter-search sampling (App. D: 512^2 pixels of 2.8 mas, i.e. 0.059 lambda/D
+    at lambda 551 nm, D 2.4 m) scaled to these optics, wide enough for the 10-15 lambda/D zone."""
+    lam, D, f = 1.0e-6, 2.4e-3, 24.0e-3
+    p = 0.0592 * lam * f / D
+    det = Detector(512, 512, p, p)
+    n, of, wr = [], [], []
+    for N in n_across:
+        for a in of_values:
+            n.append(int(N)), of.append(float(a)), wr.append(float(waist_ratio))
+    return Sweep(System(lam, f, f), D, det, tuple(n), tuple(of), tuple(wr))
+
+
 def sweep_from_params(params: Sequence[Tuple[int, float, float]]) -> Sweep:
     system, D, det = sweep_optics()
     return Sweep(system, D, det, tuple(int(p[0]) for p in params),

@@ -531,3 +531,24 @@ def test_tilted_detector_geometry_against_textbook_beam():
     assert np.max(np.abs(E - Et)) < 1e-12 * np.abs(Et).max()
     rel = np.linalg.norm(Emid - Et) / np.linalg.norm(Et)
     assert 0 < rel < 1e-2
+
+
+def test_zone_score_definition():
+    """A zone covering the whole third-ring disc reproduces the region score; a uniform
+    relative error eps inside one zone gives eps * RMS(A) over that zone only."""
+    lam, F = 1e-6, 10.0
+    det = W.Detector(96, 96, 0.9e-6, 0.9e-6)
+    xs = (np.arange(96) - 48) * det.pitch_x
+    X, Y = np.meshgrid(xs, xs)
+    R = np.hypot(X, Y)
+    A = np.vectorize(lambda r: oracle.airy_amp(r, lam, F))(R)
+    E = A * (1 + 0.003 * np.cos(X / 2e-6)) * np.exp(0.7j * Y / 1e-6)
+    j13 = 10.173468135062722
+    assert abs(oracle.zone_score(E, det, lam, F, 0.0, j13 / math.pi) -
+               oracle.airy_score(E, det, lam, F)) < 1e-15
+    u = R / (lam * F)
+    zone = (u >= 2.0) & (u < 4.0)
+    E2 = A * (1 + 0.01 * zone)
+    want = 0.01 * math.sqrt(np.mean(A[zone] ** 2))
+    assert abs(oracle.zone_score(E2, det, lam, F, 2.0, 4.0) - want) < 1e-15
+    assert oracle.zone_score(E2, det, lam, F, 4.0, 6.0) < 1e-15

@@ -136,3 +136,24 @@ def test_sweep_timeout_reported_then_recovers():
     again = plan.run().clone()
     gbd.gbd_sync()
     assert bool((again == ref).all())
+
+
+def test_zone_scores_match_oracle():
+    """Annular zones of Sec. 6 (0-5, 5-10, 10-15 lambda/D) fused into the sweep epilogue,
+    on a 512x512 detector over +-15.2 lambda F#."""
+    full = W.zone_sweep()
+    sw = W.sweep_subset(full, [0, 5, 10, 13, 18])
+    plan = gbd.sweep_plan(sw, zones=W.PAPER_ZONES)
+    got = plan.run().cpu().numpy()
+    gbd.gbd_sync()
+    assert got.shape == (5, 4)
+    lam, F = sw.system.wavelength, sw.system.focal_length / sw.diameter
+    for k in range(sw.n_instances):
+        b = oracle.trace(sw.system, sw.pupil(k))
+        E = oracle.field(b, sw.system, sw.detector)
+        want = [oracle.airy_score(E, sw.detector, lam, F)]
+        want += [oracle.zone_score(E, sw.detector, lam, F, lo, hi) for lo, hi in W.PAPER_ZONES]
+        assert np.max(np.abs(got[k] - np.asarray(want))) <= SCORE_TOL, (k, got[k], want)
+    # the plain score column equals a plan without zones
+    plain = gbd.sweep_plan(sw).run().cpu().numpy()
+    assert np.array_equal(plain, got[:, 0])
