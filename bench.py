@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweep-steps", type=int, default=2,
                     help="timed runs of the 1024-instance parameter sweep (0 = skip)")
+    ap.add_argument("--no-point", action="store_true",
+                    help="skip the plane- versus point-evaluation comparison")
     ap.add_argument("--no-surrogate", action="store_true",
                     help="skip the surrogate-guided search versus grid and random search")
     return ap.parse_args()
@@ -375,6 +377,44 @@ def run_ours(args, world, rank, local):
                              "N~U{16..256}, 256x256 pixels +-5 lambda F#"}
         plan.close()
 
+    # ---- plane evaluation versus point evaluation (Sec. 2.2's method) on the tilted,
+    # aberrated workload at 256^2 pixels over the same span, both FP64
+    point = None
+    if not args.no_point:
+        tz = W.scaled(W.tilted_zernike(), nx=256, ny=256)
+        bt = gbd.trace(tz.system, tz.pupil, stream=stream)
+        nbt = bt.shape[0]
+        ev = nbt * 256 * 256
+        Ep = gbd.field(bt, tz.system.wavelength, tz.detector, F64, stream=stream)
+        Eq = gbd.field_point(bt, tz.system.wavelength, tz.detector, stream=stream)
+        gbd.gbd_sync(stream)
+        wsq = torch.empty(max(256, gbd.gbd_field_point_workspace_bytes(nbt, tz.detector)),
+                          dtype=torch.uint8, device=dev)
+        wsp = torch.empty(max(256, gbd.gbd_field_workspace_bytes(nbt, tz.detector, F64)),
+                          dtype=torch.uint8, device=dev)
+        t = {}
+        for name, fn in (("plane", lambda: gbd.gbd_field(bt, nbt, tz.system.wavelength, tz.detector,
+                                                          F64, wsp, Ep, stream)),
+                         ("point", lambda: gbd.gbd_field_point(bt, nbt, tz.system.wavelength,
+                                                               tz.detector, wsq, Eq, stream))):
+            fn()
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b2 = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(2):
+                fn()
+            b2.record(stream)
+            torch.cuda.synchronize()
+            t[name] = a.elapsed_time(b2) / 2
+        gbd.gbd_sync(stream)
+        Epn, Eqn = Ep.cpu().numpy(), Eq.cpu().numpy()
+        point = {"workload": f"tilted_zernike optics, {nbt} beamlets x 256x256 pixels (same span), FP64",
+                 "plane_evals_per_s": ev / (t["plane"] * 1e-3),
+                 "point_evals_per_s": ev / (t["point"] * 1e-3),
+                 "plane_over_point_speedup": t["point"] / t["plane"],
+                 "plane_vs_point_rel_l2": float(np.linalg.norm(Epn - Eqn) / np.linalg.norm(Eqn))}
+
     # ---- surrogate-guided search versus the reference grid and random search
     surrogate = None
     if not args.no_surrogate:
@@ -463,7 +503,7 @@ def run_ours(args, world, rank, local):
         "config": config_block(wl, nb), "clocks": clk, "e2e": e2e, "fp64_path": f64,
         "autotuned_shape": {"rows_per_thread": tuned[0], "cols_per_thread": tuned[1],
                             "splits": tuned[2], "ms": tuned[3]},
-        "sweep": sweep, "surrogate": surrogate,
+        "sweep": sweep, "surrogate": surrogate, "point_evaluation": point,
         "error": error, "roofline": roofline, "cpu_baseline": cpu,
         "gpu_launches": launches_per_step * args.steps,
         "kernel_ms": {k: (v[0] / max(v[1], 1)) for k, v in kt.items()},

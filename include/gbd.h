@@ -179,6 +179,19 @@ gbd_status gbd_project(const gbd_beamlet* beamlets, int32_t n_beamlets, double w
                        const gbd_detector* detector, int32_t precision, void* coeffs,
                        uint32_t* wide_flag, void* stream);
 
+/* ---------------------------------------------------------------- point evaluation --
+ * The prior method the plane rule accelerates (Sec. 2.2): each beamlet propagated to each
+ * pixel on its own.  Here the beamlet is carried paraxially from the reference plane to
+ * the pixel's axial offset z: P(z) = P (I + z P)^-1, amplitude amp / sqrtdet(I + z P)
+ * (eigenvalue branch), centroid rho + z theta, path + z (1 + |theta|^2 / 2), and evaluated
+ * at the pixel; FP64, complex128 [ny][nx] output.  On an untilted plane it equals
+ * gbd_field; on a tilted plane their difference is the plane rule's method error.
+ * workspace >= gbd_field_point_workspace_bytes, 256-byte aligned. */
+size_t gbd_field_point_workspace_bytes(int32_t n_beamlets, const gbd_detector* detector);
+gbd_status gbd_field_point(const gbd_beamlet* beamlets, int32_t n_beamlets, double wavelength,
+                           const gbd_detector* detector, void* workspace, size_t workspace_bytes,
+                           void* field_out, void* stream);
+
 /* ---------------------------------------------------------------- tuning ----------
  * Launch shape of the field kernels: pixels per thread (rows x cols), beamlet splits.
  * gbd_field picks a shape from a built-in heuristic unless one was set for the current
@@ -241,7 +254,7 @@ gbd_status gbd_psf(const gbd_system* system, const gbd_pupil* pupil, double over
  * field kernels and the split reduction is bracketed by CUDA events on its stream.
  * gbd_timing_read synchronises those events, returns per kind the summed milliseconds and
  * launch counts (index 0 mixed field kernel, 1 FP64 field kernel, 2 projection,
- * 3 reduction; arrays of 4) and forgets them. */
+ * 3 reduction, 4 point evaluation; arrays of 5) and forgets them. */
 gbd_status gbd_timing_enable(int32_t on);
 gbd_status gbd_timing_read(double* total_ms, int64_t* launches);
 

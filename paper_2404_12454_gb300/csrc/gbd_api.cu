@@ -65,7 +65,7 @@ bool finite_pos(double v) { return isfinite(v) && v > 0.0; }
 // ------------------------------------------------------------- kernel timing --
 // While enabled, launches of the measured kernels are bracketed by CUDA events on their
 // own stream; gbd_timing_read synchronises the events and sums the durations.
-enum { kTimeMixed = 0, kTimeF64 = 1, kTimeProject = 2, kTimeReduce = 3, kTimeKinds = 4 };
+enum { kTimeMixed = 0, kTimeF64 = 1, kTimeProject = 2, kTimeReduce = 3, kTimePoint = 4, kTimeKinds = 5 };
 struct TimedLaunch {
     int kind;
     cudaEvent_t a, b;
@@ -408,7 +408,8 @@ int32_t gbd_beamlet_count(const gbd_pupil* pupil) {
 gbd_status gbd_sync(void* stream) {
     cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "gbd_sync");
-    unsigned st = gbd_field_status_read_clear() | gbd_sweep_status_read_clear();
+    unsigned st = gbd_field_status_read_clear() | gbd_sweep_status_read_clear() |
+                  gbd_point_status_read_clear();
     if (st & gbd::kStatusTimeout) return fail(GBD_ETIMEOUT, "a device wait gave up (timeout)");
     return GBD_OK;
 }
@@ -648,6 +649,56 @@ gbd_status gbd_psf(const gbd_system* system, const gbd_pupil* pupil, double over
     cudaError_t e = cudaMemcpyAsync(host_field_out, dfield, field_bytes, cudaMemcpyDeviceToHost,
                                     static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? GBD_OK : cuda_fail(e, "gbd_psf copy to host");
+}
+
+// Point evaluation: workspace [packed beamlet tiles | split partial fields].
+static int point_splits(int n_tiles, const gbd_detector* D) {
+    const long pix = gbd_point_pixel_ctas(D->nx, D->ny);
+    const long slots = (long)gbd_point_occupancy() * sm_count();
+    long s = (16 * slots + pix - 1) / pix;
+    s = std::min<long>(s, std::max(1, n_tiles / 4));
+    s = std::max<long>(1, std::min<long>(s, 64));
+    const int tps = (n_tiles + (int)s - 1) / (int)s;
+    return (n_tiles + tps - 1) / tps;
+}
+
+size_t gbd_field_point_workspace_bytes(int32_t n_beamlets, const gbd_detector* detector) {
+    if (check_detector(detector) != GBD_OK || n_beamlets <= 0) return 0;
+    const int nt = n_tiles_of(n_beamlets);
+    const int sp = point_splits(nt, detector);
+    return align256((size_t)nt * gbd::kF64TileBytes) +
+           align256((size_t)sp * detector->nx * detector->ny * sizeof(double2));
+}
+
+gbd_status gbd_field_point(const gbd_beamlet* beamlets, int32_t n_beamlets, double wavelength,
+                           const gbd_detector* detector, void* workspace, size_t workspace_bytes,
+                           void* field_out, void* stream) {
+    gbd_status st = check_field_args(beamlets, n_beamlets, wavelength, detector, GBD_PREC_F64,
+                                     workspace, field_out);
+    if (st != GBD_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const gbd_project_params pp = project_params(wavelength, detector);
+    if (n_beamlets == 0) {
+        cudaError_t e = cudaMemsetAsync(field_out, 0, (size_t)detector->nx * detector->ny * 16, s);
+        return e == cudaSuccess ? GBD_OK : cuda_fail(e, "gbd_field_point memset");
+    }
+    const int nt = n_tiles_of(n_beamlets);
+    const int sp = point_splits(nt, detector);
+    const int tps = (nt + sp - 1) / sp;
+    const size_t need = gbd_field_point_workspace_bytes(n_beamlets, detector);
+    if (workspace_bytes < need)
+        return fail(GBD_ENOMEM, "workspace of %zu bytes is smaller than the %zu needed",
+                    workspace_bytes, need);
+    char* base = static_cast<char*>(workspace);
+    double2* partial = reinterpret_cast<double2*>(base + align256((size_t)nt * gbd::kF64TileBytes));
+    cudaError_t e;
+    {
+        TimingScope ts(kTimePoint, s);
+        e = gbd_launch_point(beamlets, n_beamlets, pp, base, sp, tps, partial, wait_spins(), s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "gbd_field_point launch");
+    e = gbd_launch_field_reduce(GBD_PREC_F64, pp, sp, partial, field_out, s);
+    return e == cudaSuccess ? GBD_OK : cuda_fail(e, "gbd_field_point reduce");
 }
 
 gbd_status gbd_probe_peaks(double* out) {

@@ -219,6 +219,14 @@ gbd_trace_params gbd_make_trace_params(const gbd_system* system, double diameter
 int gbd_sm_count();
 uint32_t gbd_wait_spins();
 unsigned gbd_sweep_status_read_clear();
+unsigned gbd_point_status_read_clear();
+long gbd_point_pixel_ctas(int nx, int ny);
+int gbd_point_occupancy();
+// Point evaluation: packs the beamlets into `coeffs` (FP64 tiles) and launches the
+// per-(beamlet, pixel) propagation kernel writing split partial fields.
+cudaError_t gbd_launch_point(const gbd_beamlet* b, int n, const gbd_project_params& p, void* coeffs,
+                             int splits, int tiles_per_split, double2* partial, uint32_t spins,
+                             cudaStream_t s);
 gbd_status gbd_field_fixed_scratch(const gbd_beamlet* beamlets, int32_t n, double wavelength,
                                    const gbd_detector* detector, int32_t precision,
                                    void* scratch, size_t scratch_bytes, void* out,

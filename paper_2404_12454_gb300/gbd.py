@@ -109,6 +109,10 @@ _SIGS = {
     "gbd_mlp_train_step": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, ctypes.c_int32, ctypes.c_float,
                                           ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                           ctypes.c_int32, _P, _P, ctypes.c_size_t, _P]),
+    "gbd_field_point_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int32,
+                                                          ctypes.POINTER(gbd_detector)]),
+    "gbd_field_point": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_double,
+                                       ctypes.POINTER(gbd_detector), _P, ctypes.c_size_t, _P, _P]),
     "gbd_field_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_double,
                                          ctypes.POINTER(gbd_detector), ctypes.c_int32, _P, _P]),
     "gbd_timing_enable": (ctypes.c_int, [ctypes.c_int32]),
@@ -371,6 +375,30 @@ def gbd_sweep_autotune(system, diameter, n_across, overlap_factor, waist_ratio, 
     return sh.rows_per_thread, sh.cols_per_thread, float(sh.ms)
 
 
+def gbd_field_point_workspace_bytes(n_beamlets: int, detector) -> int:
+    return int(lib().gbd_field_point_workspace_bytes(int(n_beamlets),
+                                                     ctypes.byref(make_detector(detector))))
+
+
+def gbd_field_point(beamlets, n_beamlets: int, wavelength: float, detector, workspace, field_out,
+                    stream=None) -> None:
+    ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check(lib().gbd_field_point(_ptr(beamlets), int(n_beamlets), float(wavelength),
+                                 ctypes.byref(make_detector(detector)), _ptr(workspace),
+                                 ctypes.c_size_t(ws_bytes), _ptr(field_out), _stream(stream)))
+
+
+def field_point(beamlets, wavelength: float, detector, stream=None):
+    """Point-evaluation field (complex128 CUDA tensor [ny, nx])."""
+    import torch
+    n = int(beamlets.shape[0])
+    out = torch.empty((detector.ny, detector.nx), dtype=torch.complex128, device=beamlets.device)
+    ws = torch.empty(max(256, gbd_field_point_workspace_bytes(n, detector)), dtype=torch.uint8,
+                     device=beamlets.device)
+    gbd_field_point(beamlets, n, wavelength, detector, ws, out, stream)
+    return out
+
+
 MLP_PARAMS = 50177
 
 
@@ -407,7 +435,7 @@ def gbd_mlp_train_step(master, weights, m, v, x, target, lr, beta1, beta2, eps, 
                                     _stream(stream)))
 
 
-TIMING_KINDS = ("field_mixed", "field_f64", "project", "reduce")
+TIMING_KINDS = ("field_mixed", "field_f64", "project", "reduce", "point")
 
 
 def gbd_timing_enable(on: bool) -> None:
@@ -415,8 +443,8 @@ def gbd_timing_enable(on: bool) -> None:
 
 
 def gbd_timing_read() -> dict:
-    ms = (ctypes.c_double * 4)()
-    n = (ctypes.c_int64 * 4)()
+    ms = (ctypes.c_double * 5)()
+    n = (ctypes.c_int64 * 5)()
     _check(lib().gbd_timing_read(ms, n))
     return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(TIMING_KINDS)}
 

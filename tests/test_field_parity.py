@@ -257,8 +257,8 @@ def test_kernel_timing_hooks_count_launches():
     finally:
         gbd.gbd_timing_enable(False)
     assert t["field_mixed"][1] == 3 and t["field_f64"][1] == 1
-    assert t["project"][1] == 4 and t["reduce"][1] == 4
-    assert all(ms > 0 for ms, n in t.values())
+    assert t["project"][1] == 4 and t["reduce"][1] == 4 and t["point"][1] == 0
+    assert all(t[k][0] > 0 for k in ("field_mixed", "field_f64", "project", "reduce"))
 
 
 def test_wide_phase_flag_selects_exact_reduction():
@@ -282,3 +282,38 @@ def test_wide_phase_flag_selects_exact_reduction():
     idx = np.arange(5, 1024, 33)
     Eo = oracle.field(oracle.trace(wide.system, wide.pupil), wide.system, wide.detector, idx, idx)
     assert rel_l2(E[np.ix_(idx, idx)], Eo) <= TOL[gbd.GBD_PREC_MIXED]
+
+
+# ------------------------------------------------------------ point evaluation --
+
+def test_point_evaluation_matches_exact_oracle_on_tilted_planes():
+    """Every beamlet propagated to every pixel (Sec. 2.2's method) against the oracle's
+    exact paraxial propagation; the plane rule differs from it by its method error."""
+    for wl in (small_cases()["tilted_zernike_small"], small_cases()["tilted_defocused"]):
+        b = gpu_trace(wl)
+        E = gbd.field_point(b, wl.system.wavelength, wl.detector)
+        gbd.gbd_sync()
+        E = E.cpu().numpy()
+        o = oracle.trace(wl.system, wl.pupil)
+        Ex = oracle.field(o, wl.system, wl.detector, exact=True)
+        assert rel_l2(E, Ex) <= 1e-11
+        Ep = gpu_field(b, wl, gbd.GBD_PREC_F64)
+        assert 0 < rel_l2(Ep, E) < 1e-3
+
+
+def test_point_equals_plane_on_untilted_plane_and_full_size_subset():
+    wl = small_cases()["defocused"]
+    b = gpu_trace(wl)
+    E = gbd.field_point(b, wl.system.wavelength, wl.detector).cpu().numpy()
+    Ep = gpu_field(b, wl, gbd.GBD_PREC_F64)
+    assert rel_l2(E, Ep) <= 1e-12
+    full = W.tilted_zernike()
+    b = gpu_trace(full)
+    E = gbd.field_point(b, full.system.wavelength, full.detector)
+    gbd.gbd_sync()
+    E = E.cpu().numpy()
+    cols, rows = W.strided_pixels(full)
+    cols, rows = cols[::4], rows[::4]
+    Ex = oracle.field(oracle.trace(full.system, full.pupil), full.system, full.detector, cols,
+                      rows, exact=True)
+    assert rel_l2(E[np.ix_(rows, cols)], Ex) <= 1e-11
