@@ -57,6 +57,9 @@ def lib():
         L.orc_airy_score.restype = _D
         L.orc_zone_score.argtypes = [_PD, _I, _I, _D, _D, _D, _D, _D, _D]
         L.orc_zone_score.restype = _D
+        L.orc_mirror_ray.argtypes = [_I, _PD, _PD, _PD, _D, _D, _D, _D, _D, _PD]
+        L.orc_trace_mirrors.argtypes = [_D, _I, _PD, _PD, _PD, _D, _D, _I, _D, _D, _PD, _I]
+        L.orc_trace_mirrors.restype = _I
         _lib = L
     return _lib
 
@@ -119,7 +122,8 @@ def field(beamlets: np.ndarray, system, detector, cols: Optional[Sequence[int]] 
     fn = lib().orc_field_exact if exact else lib().orc_field
     if b.shape[0] == 0:
         return np.zeros((r.size, c.size), dtype=np.complex128)
-    fn(_pd(b), b.shape[0], system.wavelength, system.distance, detector.rot_x, detector.rot_y,
+    fn(_pd(b), b.shape[0], system.wavelength, getattr(system, "distance", 0.0), detector.rot_x,
+       detector.rot_y,
        detector.nx, detector.ny, detector.pitch_x, detector.pitch_y, _pi(c), c.size, _pi(r),
        r.size, _pd(out))
     return out[..., 0] + 1j * out[..., 1]
@@ -164,6 +168,34 @@ def zone_score(field_: np.ndarray, detector, wavelength: float, f_number: float,
     f = np.ascontiguousarray(np.stack([field_.real, field_.imag], axis=-1), dtype=np.float64)
     return lib().orc_zone_score(_pd(f), detector.nx, detector.ny, detector.pitch_x,
                                 detector.pitch_y, wavelength, f_number, lo, hi)
+
+
+def _mirror_arrays(msys):
+    n = len(msys.radius)
+    return (n, np.ascontiguousarray(msys.radius, dtype=np.float64),
+            np.ascontiguousarray(msys.conic, dtype=np.float64),
+            np.ascontiguousarray(msys.spacing, dtype=np.float64))
+
+
+def mirror_ray(msys, x0: float, y0: float, ax: float = 0.0, ay: float = 0.0) -> np.ndarray:
+    """Real ray through the mirrors: (x, y, theta_x, theta_y, path) at the image plane."""
+    n, R, K, T = _mirror_arrays(msys)
+    out = np.zeros(5)
+    lib().orc_mirror_ray(n, _pd(R), _pd(K), _pd(T), msys.pupil_offset, x0, y0, ax, ay, _pd(out))
+    return out
+
+
+def trace_mirrors(msys, pupil) -> np.ndarray:
+    """Beamlet table of a pupil in front of a sequence of conic mirrors."""
+    nb = count(pupil.n_across)
+    out = np.zeros((max(nb, 1), REC_SIZE), dtype=np.float64)
+    n, R, K, T = _mirror_arrays(msys)
+    got = lib().orc_trace_mirrors(msys.wavelength, n, _pd(R), _pd(K), _pd(T), msys.pupil_offset,
+                                  pupil.diameter, pupil.n_across, pupil.overlap_factor,
+                                  pupil.waist_ratio, _pd(out), out.shape[0])
+    if got != nb:
+        raise RuntimeError(f"oracle mirror trace produced {got} beamlets, expected {nb}")
+    return out[:nb]
 
 
 def unpack(rec: np.ndarray) -> dict:

@@ -480,3 +480,173 @@ double orc_airy_score(const double* field, int nx, int ny, double px, double py,
         }
     return sqrt(acc / (double)n);
 }
+
+/* ----------------------------------------------------- two-mirror telescope -- */
+/* Real-ray trace through reflective conic surfaces (the Ritchey-Chretien prescription of
+ * App. B), for beamlets decomposed on an entrance-pupil plane in front of the first
+ * mirror.  Light enters travelling +z.  Mirror k: vertex z_k (z_1 = 0, z_{k+1} = z_k + t_k
+ * with t_k the signed distance listed after surface k), radius R_k with App. B's sign
+ * (negative = concave, positive = convex towards the arriving light), conic K_k.  With
+ * s_k = +-1 the direction of travel before mirror k, the lab-frame curvature is
+ * c_k = s_k / R_k and the surface is the conic
+ *     z - z_k = c r^2 / (1 + sqrt(1 - (1 + K) c^2 r^2)),   r^2 = x^2 + y^2.
+ * Intersections: Newton's method on the sag (starting from the vertex plane).  Normals
+ * from the sag's gradient.  Reflection u' = u - 2 (u.n) n.  Optical path = geometric
+ * length (air).  The image plane is t_last after the last vertex. */
+
+typedef struct {
+    int n;
+    double z[8], c[8], K[8];
+    double z_ep, z_img;
+} orc_mirrors;
+
+static void mirrors_setup(int n, const double* radius, const double* conic, const double* dist,
+                          double pupil_offset, orc_mirrors* M) {
+    M->n = n;
+    double z = 0.0, s = 1.0;
+    for (int k = 0; k < n; ++k) {
+        M->z[k] = z;
+        M->c[k] = s / radius[k];
+        M->K[k] = conic[k];
+        z += dist[k];
+        s = -s;
+    }
+    M->z_img = z;
+    M->z_ep = -pupil_offset;
+}
+
+static double sag(double c, double K, double r2) {
+    return c * r2 / (1.0 + sqrt(1.0 - (1.0 + K) * c * c * r2));
+}
+
+/* d(sag)/d(r2) */
+static double dsag_dr2(double c, double K, double r2) {
+    double q = sqrt(1.0 - (1.0 + K) * c * c * r2);
+    double den = 1.0 + q;
+    /* sag = c r2 / den;  dq/dr2 = -(1+K) c^2 / (2 q) */
+    double dq = -(1.0 + K) * c * c / (2.0 * q);
+    return c / den - c * r2 * dq / (den * den);
+}
+
+/* Traces one ray from (x0, y0, z_ep) with direction slopes (ax, ay) to the image plane:
+ * position, slopes and geometric path length. */
+static void mirror_ray(const orc_mirrors* M, double x0, double y0, double ax, double ay,
+                       double out_xy[2], double out_th[2], double* path) {
+    double p[3] = {x0, y0, M->z_ep};
+    double nu = sqrt(1.0 + ax * ax + ay * ay);
+    double u[3] = {ax / nu, ay / nu, 1.0 / nu};
+    double L = 0.0;
+    for (int k = 0; k < M->n; ++k) {
+        /* Newton on g(t) = z(t) - z_k - sag(r2(t)), starting at the vertex plane */
+        double t = (M->z[k] - p[2]) / u[2];
+        for (int it = 0; it < 60; ++it) {
+            double x = p[0] + t * u[0], y = p[1] + t * u[1], zz = p[2] + t * u[2];
+            double r2 = x * x + y * y;
+            double g = zz - M->z[k] - sag(M->c[k], M->K[k], r2);
+            double dg = u[2] - dsag_dr2(M->c[k], M->K[k], r2) * 2.0 * (x * u[0] + y * u[1]);
+            double step = g / dg;
+            t -= step;
+            if (fabs(step) < 1e-16 * (1.0 + fabs(t))) break;
+        }
+        for (int q = 0; q < 3; ++q) p[q] += t * u[q];
+        L += t;
+        /* surface normal from the gradient of z - sag(r2) */
+        double r2 = p[0] * p[0] + p[1] * p[1];
+        double ds = dsag_dr2(M->c[k], M->K[k], r2);
+        double n[3] = {-2.0 * ds * p[0], -2.0 * ds * p[1], 1.0};
+        double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        for (int q = 0; q < 3; ++q) n[q] /= nn;
+        double un = u[0] * n[0] + u[1] * n[1] + u[2] * n[2];
+        for (int q = 0; q < 3; ++q) u[q] -= 2.0 * un * n[q];
+    }
+    double t = (M->z_img - p[2]) / u[2];
+    for (int q = 0; q < 3; ++q) p[q] += t * u[q];
+    L += t;
+    out_xy[0] = p[0];
+    out_xy[1] = p[1];
+    out_th[0] = u[0] / u[2];
+    out_th[1] = u[1] / u[2];
+    *path = L;
+}
+
+/* exported for tests: one ray (x0, y0, slopes ax, ay) -> (x, y, theta_x, theta_y, path) */
+void orc_mirror_ray(int n, const double* radius, const double* conic, const double* dist,
+                    double pupil_offset, double x0, double y0, double ax, double ay, double* out) {
+    orc_mirrors M;
+    mirrors_setup(n, radius, conic, dist, pupil_offset, &M);
+    mirror_ray(&M, x0, y0, ax, ay, out, out + 2, out + 4);
+}
+
+/* Beamlet table for a pupil of `diameter` in front of the mirrors (same record layout and
+ * steps as orc_trace; the path is relative to the axial ray). */
+int orc_trace_mirrors(double wavelength, int n, const double* radius, const double* conic,
+                      const double* dist, double pupil_offset, double diameter, int n_across,
+                      double overlap_factor, double waist_ratio, double* out, int capacity) {
+    orc_mirrors Msys;
+    mirrors_setup(n, radius, conic, dist, pupil_offset, &Msys);
+    const int N = n_across;
+    const double s = diameter / N;
+    const double w0 = overlap_factor * diameter / (2.0 * N);
+    const double a = s * s / (M_PI * w0 * w0);
+    const double h = waist_ratio * w0;
+    const double dth = waist_ratio * wavelength / (M_PI * w0);
+    const double complex p1 = -I * wavelength / (M_PI * w0 * w0);
+    double axy[2], ath[2], apath;
+    mirror_ray(&Msys, 0.0, 0.0, 0.0, 0.0, axy, ath, &apath);
+    int nb = 0;
+    for (int j = 0; j < N; ++j) {
+        for (int i = 0; i < N; ++i) {
+            if (!inside(i, j, N)) continue;
+            if (nb >= capacity) return -1;
+            double* rec = out + (size_t)nb * REC_SIZE;
+            memset(rec, 0, sizeof(double) * REC_SIZE);
+            double rx = (i - (N - 1) / 2.0) * s, ry = (j - (N - 1) / 2.0) * s;
+            double rc[2], tc[2], Lc;
+            mirror_ray(&Msys, rx, ry, 0.0, 0.0, rc, tc, &Lc);
+            double A[2][2], B[2][2], C[2][2], D[2][2];
+            for (int k = 0; k < 2; ++k) {
+                double r[2], t[2], o;
+                mirror_ray(&Msys, rx + (k == 0 ? h : 0.0), ry + (k == 1 ? h : 0.0), 0.0, 0.0, r, t, &o);
+                for (int q = 0; q < 2; ++q) {
+                    A[q][k] = (r[q] - rc[q]) / h;
+                    C[q][k] = (t[q] - tc[q]) / h;
+                }
+                mirror_ray(&Msys, rx, ry, k == 0 ? dth : 0.0, k == 1 ? dth : 0.0, r, t, &o);
+                for (int q = 0; q < 2; ++q) {
+                    B[q][k] = (r[q] - rc[q]) / dth;
+                    D[q][k] = (t[q] - tc[q]) / dth;
+                }
+            }
+            cmat2 Mm, Nn;
+            for (int q = 0; q < 2; ++q)
+                for (int k = 0; k < 2; ++k) {
+                    Mm.m[q][k] = A[q][k] + B[q][k] * p1;
+                    Nn.m[q][k] = C[q][k] + D[q][k] * p1;
+                }
+            cmat2 P = cmul(Nn, cinv(Mm));
+            double complex alpha = a / orc_sqrtdet(Mm.m[0][0], Mm.m[0][1], Mm.m[1][0], Mm.m[1][1]);
+            rec[REC_RJ] = rx;
+            rec[REC_RJ + 1] = ry;
+            rec[REC_A] = a;
+            rec[REC_W0] = w0;
+            for (int q = 0; q < 2; ++q)
+                for (int k = 0; k < 2; ++k) {
+                    rec[REC_ABCD + 0 + 2 * q + k] = A[q][k];
+                    rec[REC_ABCD + 4 + 2 * q + k] = B[q][k];
+                    rec[REC_ABCD + 8 + 2 * q + k] = C[q][k];
+                    rec[REC_ABCD + 12 + 2 * q + k] = D[q][k];
+                    rec[REC_P + 2 * (2 * q + k)] = creal(P.m[q][k]);
+                    rec[REC_P + 2 * (2 * q + k) + 1] = cimag(P.m[q][k]);
+                }
+            rec[REC_ALPHA] = creal(alpha);
+            rec[REC_ALPHA + 1] = cimag(alpha);
+            rec[REC_L] = Lc - apath;
+            rec[REC_RHO] = rc[0];
+            rec[REC_RHO + 1] = rc[1];
+            rec[REC_THETA] = tc[0];
+            rec[REC_THETA + 1] = tc[1];
+            ++nb;
+        }
+    }
+    return nb;
+}

@@ -211,6 +211,38 @@ def zone_sweep(of_values: Sequence[float] = tuple(np.linspace(1.0, 2.0, 11)),
     return Sweep(System(lam, f, f), D, det, tuple(n), tuple(of), tuple(wr))
 
 
+@dataclasses.dataclass(frozen=True)
+class MirrorSystem:
+    """Sequence of reflective conic surfaces, light entering along +z, with App. B's sign
+    for the radii (negative = concave, positive = convex towards the arriving light) and
+    the signed axial distance from each vertex to the next surface (the last one: to the
+    image plane).  The entrance pupil is a plane `pupil_offset` before the first vertex."""
+
+    wavelength: float
+    radius: Tuple[float, ...]
+    conic: Tuple[float, ...]
+    spacing: Tuple[float, ...]
+    diameter: Tuple[float, ...]
+    pupil_offset: float = 0.1
+
+
+# App. B: Hubble-like Ritchey-Chretien telescope without the central obscuration.
+HST_RADIUS = (-11.0400, 1.35800)
+HST_CONIC = (-1.00230, -1.49686)
+HST_SPACING = (-4.90607, 6.40620)
+HST_DIAMETER = (2.40000, 0.28112)
+HST_EFL = 57.6          # App. D
+MAS = math.pi / (180.0 * 3600.0 * 1000.0)
+
+
+def hst_rc(n_across: int = 64, overlap_factor: float = 1.5, waist_ratio: float = 1.0,
+           npix: int = 256, pixel_mas: float = 2.8, wavelength: float = 0.551e-6):
+    """The App. B telescope at lambda = 551 nm (App. D), 2.8 mas pixels on its focal plane."""
+    msys = MirrorSystem(wavelength, HST_RADIUS, HST_CONIC, HST_SPACING, HST_DIAMETER)
+    p = HST_EFL * pixel_mas * MAS
+    return msys, Pupil(HST_DIAMETER[0], n_across, overlap_factor, waist_ratio), Detector(npix, npix, p, p)
+
+
 def sweep_from_params(params: Sequence[Tuple[int, float, float]]) -> Sweep:
     system, D, det = sweep_optics()
     return Sweep(system, D, det, tuple(int(p[0]) for p in params),

@@ -552,3 +552,49 @@ def test_zone_score_definition():
     want = 0.01 * math.sqrt(np.mean(A[zone] ** 2))
     assert abs(oracle.zone_score(E2, det, lam, F, 2.0, 4.0) - want) < 1e-15
     assert oracle.zone_score(E2, det, lam, F, 4.0, 6.0) < 1e-15
+
+
+# ------------------------------------------------ conic mirrors (App. B) --
+
+def test_paraboloid_focuses_every_ray_with_equal_path():
+    """K = -1: every ray parallel to the axis meets the focus |R|/2 with the same optical
+    path (Fermat), so landing points are 0 and excess paths vanish."""
+    m = W.MirrorSystem(1e-6, (-2.0,), (-1.0,), (-1.0,), (1.0,), pupil_offset=0.5)
+    ref = oracle.mirror_ray(m, 0.0, 0.0)
+    for x, y in ((0.0, 0.1), (0.2, -0.3), (-0.35, 0.35), (0.49, 0.0)):
+        r = oracle.mirror_ray(m, x, y)
+        assert abs(r[0]) < 1e-13 and abs(r[1]) < 1e-13
+        assert abs(r[4] - ref[4]) < 1e-13
+
+
+def test_sphere_marginal_crossing_closed_form():
+    """K = 0, radius 2 concave: a ray at height h crosses the axis 1/cos(a) - 2 from the
+    vertex (a = asin(h/2)), the classic spherical aberration of a mirror."""
+    m = W.MirrorSystem(1e-6, (-2.0,), (0.0,), (-1.0,), (1.0,), pupil_offset=0.5)
+    for h in (0.05, 0.2, 0.45):
+        r = oracle.mirror_ray(m, 0.0, h)
+        # image plane at z = -1; the ray continues towards -z with slope theta = dy/dz
+        z_cross = -1.0 - r[1] / r[3]
+        a = math.asin(h / 2.0)
+        assert abs(z_cross - (-2.0 + 1.0 / math.cos(a))) < 1e-12
+
+
+def test_rc_paraxial_limit_and_focal_length():
+    """Tiny pupil: the one-sided differences of real rays give the unfolded paraxial
+    matrix T(t2) L(f2) T(|t1|) L(f1) T(offset) with f = -R/2 (App. B signs), and the
+    focal length is App. D's 57.6 m."""
+    msys, _, _ = W.hst_rc()
+    b = oracle.trace_mirrors(msys, W.Pupil(2e-3, 4, 1.5, 0.05))
+
+    def T(d):
+        return np.array([[1.0, d], [0.0, 1.0]])
+
+    def Lf(f):
+        return np.array([[1.0, 0.0], [-1.0 / f, 1.0]])
+    R, t = msys.radius, msys.spacing
+    M = T(t[1]) @ Lf(-R[1] / 2) @ T(abs(t[0])) @ Lf(-R[0] / 2) @ T(msys.pupil_offset)
+    for rec in b:
+        u = oracle.unpack(rec)
+        for blk, (q, k) in (("A", (0, 0)), ("B", (0, 1)), ("C", (1, 0)), ("D", (1, 1))):
+            assert np.max(np.abs(u[blk] - M[q, k] * np.eye(2))) <= 1e-6 * max(1.0, abs(M[q, k]))
+    assert abs(-1.0 / M[1, 0] - W.HST_EFL) < 1e-3 * W.HST_EFL
