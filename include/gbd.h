@@ -133,6 +133,35 @@ gbd_status gbd_set_wait_limit(uint32_t spins);
 gbd_status gbd_trace(const gbd_system* system, const gbd_pupil* pupil, double overlap_factor,
                      double waist_ratio, gbd_beamlet* out, int32_t capacity, void* stream);
 
+/* ---------------------------------------------------------------- mirrors ---------
+ * Real-ray trace through reflective conic surfaces (the Ritchey-Chretien telescope of
+ * App. B), for the same decomposition as gbd_trace.  Light enters travelling +z; the
+ * entrance pupil (where beamlets are decomposed and rays start, slopes 0 or the
+ * divergence rays' a) is a plane pupil_offset before the first vertex.  Surface k has
+ * vertex z_k (z_1 = 0, z_{k+1} = z_k + spacing[k]; the image / reference plane is
+ * spacing[n-1] after the last vertex), radius with App. B's sign (negative = concave,
+ * positive = convex towards the arriving light) and conic constant; its lab-frame
+ * curvature is s_k / radius[k] with s_k = +-1 the direction of travel before it.  Rays are
+ * traced exactly (intersection, reflection about the surface normal, geometric path);
+ * path is the excess over the axial ray from the pupil plane to the reference plane.
+ * No obscuration or vignetting is modelled (the paper removes the secondary's).
+ * Errors: GBD_EINVAL for n_mirrors outside [1, GBD_MAX_MIRRORS], zero or non-finite
+ * radius/spacing, non-finite conic, pupil_offset <= 0. */
+#define GBD_MAX_MIRRORS 4
+typedef struct {
+    double wavelength;                 /* m                                        */
+    double pupil_offset;               /* m, > 0                                   */
+    int32_t n_mirrors;
+    int32_t reserved;
+    double radius[GBD_MAX_MIRRORS];    /* m, App. B sign convention                */
+    double conic[GBD_MAX_MIRRORS];
+    double spacing[GBD_MAX_MIRRORS];   /* m, signed axial distance to the next one */
+} gbd_mirror_system;
+
+gbd_status gbd_trace_mirrors(const gbd_mirror_system* system, const gbd_pupil* pupil,
+                             double overlap_factor, double waist_ratio, gbd_beamlet* out,
+                             int32_t capacity, void* stream);
+
 /* ---------------------------------------------------------------- gbd_field -------
  * Coherent sum over beamlets of each beamlet's field on every detector pixel (Eq.
  * sum_gaussian, Eq. collins_factored with the chief-ray slope term, Eqs. ab_prop/cd_prop):

@@ -441,6 +441,52 @@ gbd_status gbd_trace(const gbd_system* system, const gbd_pupil* pupil, double ov
     return GBD_OK;
 }
 
+gbd_status gbd_trace_mirrors(const gbd_mirror_system* system, const gbd_pupil* pupil,
+                             double overlap_factor, double waist_ratio, gbd_beamlet* out,
+                             int32_t capacity, void* stream) {
+    if (!system) return fail(GBD_EINVAL, "system is NULL");
+    gbd_status st = check_pupil(pupil);
+    if (st != GBD_OK) return st;
+    if (!finite_pos(system->wavelength)) return fail(GBD_EINVAL, "wavelength must be finite and > 0");
+    if (!finite_pos(system->pupil_offset)) return fail(GBD_EINVAL, "pupil_offset must be > 0");
+    const int n = system->n_mirrors;
+    if (n < 1 || n > GBD_MAX_MIRRORS)
+        return fail(GBD_EINVAL, "n_mirrors must be in [1, %d]", GBD_MAX_MIRRORS);
+    for (int k = 0; k < n; ++k)
+        if (!isfinite(system->radius[k]) || system->radius[k] == 0.0 ||
+            !isfinite(system->spacing[k]) || system->spacing[k] == 0.0 ||
+            !isfinite(system->conic[k]))
+            return fail(GBD_EINVAL, "mirror %d: radius and spacing must be finite and non-zero", k);
+    if (!finite_pos(overlap_factor)) return fail(GBD_EINVAL, "overlap_factor must be > 0");
+    if (!finite_pos(waist_ratio)) return fail(GBD_EINVAL, "waist_ratio must be > 0");
+    const int32_t nb = gbd_beamlet_count(pupil);
+    if (capacity < nb) return fail(GBD_ENOMEM, "capacity %d < %d beamlets", capacity, nb);
+    if (nb > 0 && !out) return fail(GBD_EINVAL, "out is NULL");
+    if (reinterpret_cast<uintptr_t>(out) & 15u) return fail(GBD_EINVAL, "out must be 16-byte aligned");
+    gbd_mirror_params m;
+    memset(&m, 0, sizeof(m));
+    m.n = n;
+    m.n_across = pupil->n_across;
+    double z = 0.0, dir = 1.0, axial = system->pupil_offset;
+    for (int k = 0; k < n; ++k) {
+        m.z[k] = z;
+        m.c[k] = dir / system->radius[k];
+        m.K[k] = system->conic[k];
+        z += system->spacing[k];
+        axial += fabs(system->spacing[k]);
+        dir = -dir;
+    }
+    m.z_img = z;
+    m.z_ep = -system->pupil_offset;
+    m.axial_path = axial;
+    m.wavelength = system->wavelength;
+    m.diameter = pupil->diameter;
+    m.overlap_factor = overlap_factor;
+    m.waist_ratio = waist_ratio;
+    cudaError_t e = gbd_launch_trace_mirrors(m, out, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? GBD_OK : cuda_fail(e, "gbd_trace_mirrors launch");
+}
+
 size_t gbd_project_bytes(int32_t n_beamlets, int32_t precision) {
     if (n_beamlets <= 0) return 0;
     return (size_t)n_tiles_of(n_beamlets) *

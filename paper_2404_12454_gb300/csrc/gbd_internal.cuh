@@ -158,6 +158,15 @@ struct gbd_trace_params {
     double zpoly[66];             // W(x/R, y/R) = sum zpoly[idx(a,b)] (x/R)^a (y/R)^b
 };
 
+// Sequence of reflective conics (lab-frame curvatures, vertices) for real-ray traces.
+struct gbd_mirror_params {
+    int32_t n;
+    int32_t n_across;
+    double z[GBD_MAX_MIRRORS], c[GBD_MAX_MIRRORS], K[GBD_MAX_MIRRORS];
+    double z_ep, z_img, axial_path;
+    double wavelength, diameter, overlap_factor, waist_ratio;
+};
+
 struct gbd_project_params {
     double wavelength;
     double M[4];       // detector (s_x, s_y) -> lab (x, y), row-major
@@ -204,6 +213,7 @@ cudaError_t gbd_launch_trace_project(const gbd_trace_params& p, int n_instances,
 // wide-phase bound on this detector; the caller zeroes it first.
 cudaError_t gbd_launch_project(const gbd_beamlet* b, int n, const gbd_project_params& p,
                                int precision, void* coeffs, unsigned* wide, cudaStream_t s);
+cudaError_t gbd_launch_trace_mirrors(const gbd_mirror_params& m, gbd_beamlet* out, cudaStream_t s);
 cudaError_t gbd_launch_field_kernel(int precision, const void* coeffs, int n_tiles,
                                     const gbd_project_params& p, const gbd_field_launch& L,
                                     double2* partial, const unsigned* wide, uint32_t wait_spins,

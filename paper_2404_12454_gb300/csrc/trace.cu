@@ -81,26 +81,76 @@ __device__ void propagate(const gbd_trace_params& P, Ray& r) {
     r.path += 0.5 * P.d * (r.tx * r.tx + r.ty * r.ty);
 }
 
-__device__ void trace_one(const gbd_trace_params& P, int N, double OF, double WR, int i, int j,
-                          gbd_beamlet* out) {
-    const double D = P.diameter;
+// Ray propagators: map a ray leaving the pupil plane at (x, y) with slopes (tx, ty) to its
+// position, slopes and optical path (in excess of the axial ray's) on the reference plane.
+struct LensTracer {
+    const gbd_trace_params& P;
+    __device__ void operator()(Ray& r) const { propagate(P, r); }
+};
+
+// Real rays through reflective conic surfaces.  Along the ray q(t) = q + t u (q from the
+// vertex) the implicit surface F = c (x^2 + y^2) - 2 z + (1 + K) c z^2 is the quadratic
+// a t^2 + b t + c0, and dF/dt = 2 a t + b = +-sqrt(b^2 - 4 a c0) at its two roots.  The
+// sheet through the vertex has grad F ~ (0, 0, -2) there, so the wanted root is the one with
+// dF/dt of sign s = -sign(u_z).  It is evaluated without cancellation: (-b + s r) / 2a when
+// -b and s r agree in sign, else 2 c0 / (-b - s r), which stays finite as a -> 0 (nearly
+// flat or parabolic surfaces).  Normals come from the implicit gradient.
+struct MirrorTracer {
+    const gbd_mirror_params& M;
+    __device__ void operator()(Ray& r) const {
+        const double nrm = rsqrt(1.0 + r.tx * r.tx + r.ty * r.ty);
+        double ux = r.tx * nrm, uy = r.ty * nrm, uz = nrm;
+        double px = r.x, py = r.y, pz = M.z_ep, path = 0.0;
+        for (int k = 0; k < M.n; ++k) {
+            const double c = M.c[k], e = (1.0 + M.K[k]) * c;
+            const double qz = pz - M.z[k];
+            const double a = c * (ux * ux + uy * uy) + e * uz * uz;
+            const double b = 2.0 * (c * (px * ux + py * uy) - uz + e * qz * uz);
+            const double c0 = c * (px * px + py * py) - 2.0 * qz + e * qz * qz;
+            const double sr = copysign(sqrt(fmax(b * b - 4.0 * a * c0, 0.0)), -uz);
+            const double t = (b * sr < 0.0) ? (sr - b) / (2.0 * a) : 2.0 * c0 / (-b - sr);
+            px += t * ux;
+            py += t * uy;
+            pz += t * uz;
+            path += t;
+            double nx = 2.0 * c * px, ny = 2.0 * c * py, nz = -2.0 + 2.0 * e * (pz - M.z[k]);
+            const double inv = rsqrt(nx * nx + ny * ny + nz * nz);
+            nx *= inv;
+            ny *= inv;
+            nz *= inv;
+            const double un = ux * nx + uy * ny + uz * nz;
+            ux -= 2.0 * un * nx;
+            uy -= 2.0 * un * ny;
+            uz -= 2.0 * un * nz;
+        }
+        const double t = (M.z_img - pz) / uz;
+        r.x = px + t * ux;
+        r.y = py + t * uy;
+        r.tx = ux / uz;
+        r.ty = uy / uz;
+        r.path = path + t - M.axial_path;
+    }
+};
+
+template <class Tracer>
+__device__ void trace_one(const Tracer& T, double D, double lambda, int N, double OF, double WR,
+                          int i, int j, gbd_beamlet* out) {
     const double s = D / N;
     const double w0 = OF * D / (2.0 * N);
     const double weight = s * s / (M_PI * w0 * w0);
     const double h = WR * w0;
-    const double dth = WR * P.wavelength / (M_PI * w0);
-    const double p1 = -P.wavelength / (M_PI * w0 * w0);  // P1 = i * p1 * I
+    const double dth = WR * lambda / (M_PI * w0);
+    const double p1 = -lambda / (M_PI * w0 * w0);  // P1 = i * p1 * I
     const double cx = (i - 0.5 * (N - 1)) * s, cy = (j - 0.5 * (N - 1)) * s;
 
     Ray c{cx, cy, 0.0, 0.0, 0.0};
-    propagate(P, c);
+    T(c);
     Ray wx{cx + h, cy, 0.0, 0.0, 0.0}, wy{cx, cy + h, 0.0, 0.0, 0.0};
     Ray dx{cx, cy, dth, 0.0, 0.0}, dy{cx, cy, 0.0, dth, 0.0};
-    propagate(P, wx);
-    propagate(P, wy);
-    propagate(P, dx);
-    propagate(P, dy);
-
+    T(wx);
+    T(wy);
+    T(dx);
+    T(dy);
     // columns: derivative of (x, y, tx, ty) with respect to (x0, y0 | tx0, ty0)
     double A[4] = {(wx.x - c.x) / h, (wy.x - c.x) / h, (wx.y - c.y) / h, (wy.y - c.y) / h};
     double C[4] = {(wx.tx - c.tx) / h, (wy.tx - c.tx) / h, (wx.ty - c.ty) / h, (wy.ty - c.ty) / h};
@@ -182,7 +232,29 @@ __global__ void __launch_bounds__(128) trace_kernel(gbd_trace_params P,
     if (a < 0) return;
     const int i_lo = ((N - 1) - a) / 2;
     for (int t = threadIdx.x; t <= a; t += blockDim.x)
-        trace_one(P, N, OF, WR, i_lo + t, j, out + base + row_off + t);
+        trace_one(LensTracer{P}, P.diameter, P.wavelength, N, OF, WR, i_lo + t, j,
+                  out + base + row_off + t);
+}
+
+// Pupil in front of a sequence of conic mirrors, one CTA per grid row (as trace_kernel).
+__global__ void __launch_bounds__(128) trace_mirrors_kernel(gbd_mirror_params M,
+                                                            gbd_beamlet* __restrict__ out) {
+    const int N = M.n_across;
+    const int j = blockIdx.x;
+    if (j >= N) return;
+    __shared__ long long warp_sum[4];
+    long long acc = 0;
+    for (int q = threadIdx.x; q < j; q += blockDim.x) acc += row_extent(q, N) + 1;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    const long long row_off = warp_sum[0] + warp_sum[1] + warp_sum[2] + warp_sum[3];
+    const int a = row_extent(j, N);
+    if (a < 0) return;
+    const int i_lo = ((N - 1) - a) / 2;
+    for (int t = threadIdx.x; t <= a; t += blockDim.x)
+        trace_one(MirrorTracer{M}, M.diameter, M.wavelength, N, M.overlap_factor, M.waist_ratio,
+                  i_lo + t, j, out + row_off + t);
 }
 
 // ---------------------------------------------------------------- projection --
@@ -375,7 +447,8 @@ __global__ void __launch_bounds__(256)
         }
         const int i = ((N - 1) - row_extent(a, N)) / 2 + (int)(u - R[a]);
         gbd_beamlet bm;
-        trace_one(P, N, I.overlap_factor, I.waist_ratio, i, a, &bm);
+        trace_one(LensTracer{P}, P.diameter, P.wavelength, N, I.overlap_factor, I.waist_ratio, i, a,
+                  &bm);
         q = project_one(bm, G);
     }
     if (write_mixed(out, t, q, G) && wide) atomicOr(wide, 1u);
@@ -399,6 +472,11 @@ cudaError_t gbd_launch_trace(const gbd_trace_params& p, int n_instances, int max
                              const gbd_instance_dev* d_inst, gbd_beamlet* out, cudaStream_t s) {
     dim3 grid(max_n_across, n_instances);
     trace_kernel<<<grid, 128, 0, s>>>(p, d_inst, out);
+    return cudaGetLastError();
+}
+
+cudaError_t gbd_launch_trace_mirrors(const gbd_mirror_params& m, gbd_beamlet* out, cudaStream_t s) {
+    trace_mirrors_kernel<<<m.n_across, 128, 0, s>>>(m, out);
     return cudaGetLastError();
 }
 

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(HERE, "libgbd.so")
 GBD_OK, GBD_EINVAL, GBD_ECUDA, GBD_ENOMEM, GBD_ETIMEOUT, GBD_EUNSUPPORTED = range(6)
 GBD_PREC_F64, GBD_PREC_MIXED = 0, 1
 GBD_MAX_ZERN = 64
+GBD_MAX_MIRRORS = 4
 BEAMLET_DOUBLES = 36
 TILE = 64
 
@@ -44,6 +45,14 @@ class gbd_pupil(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
+class gbd_mirror_system(ctypes.Structure):
+    _fields_ = [("wavelength", ctypes.c_double), ("pupil_offset", ctypes.c_double),
+                ("n_mirrors", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("radius", ctypes.c_double * GBD_MAX_MIRRORS),
+                ("conic", ctypes.c_double * GBD_MAX_MIRRORS),
+                ("spacing", ctypes.c_double * GBD_MAX_MIRRORS)]
+
+
 class gbd_detector(ctypes.Structure):
     _fields_ = [("pitch_x", ctypes.c_double), ("pitch_y", ctypes.c_double),
                 ("rot_x", ctypes.c_double), ("rot_y", ctypes.c_double),
@@ -65,6 +74,9 @@ _SIGS = {
     "gbd_set_wait_limit": (ctypes.c_int, [ctypes.c_uint32]),
     "gbd_trace": (ctypes.c_int, [ctypes.POINTER(gbd_system), ctypes.POINTER(gbd_pupil),
                                  ctypes.c_double, ctypes.c_double, _P, ctypes.c_int32, _P]),
+    "gbd_trace_mirrors": (ctypes.c_int, [ctypes.POINTER(gbd_mirror_system),
+                                         ctypes.POINTER(gbd_pupil), ctypes.c_double,
+                                         ctypes.c_double, _P, ctypes.c_int32, _P]),
     "gbd_field_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int32, ctypes.POINTER(gbd_detector),
                                                     ctypes.c_int32]),
     "gbd_field": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_double, ctypes.POINTER(gbd_detector),
@@ -185,6 +197,24 @@ def make_system(system) -> gbd_system:
     return s
 
 
+def make_mirror_system(msys) -> gbd_mirror_system:
+    """gbd_mirror_system from an object with wavelength, pupil_offset, radius, conic, spacing."""
+    n = len(msys.radius)
+    if not (len(msys.conic) == n and len(msys.spacing) == n):
+        raise ValueError("radius, conic and spacing must have one entry per mirror")
+    if n > GBD_MAX_MIRRORS:
+        raise ValueError("too many mirrors")
+    s = gbd_mirror_system()
+    s.wavelength = msys.wavelength
+    s.pupil_offset = msys.pupil_offset
+    s.n_mirrors = n
+    for k in range(n):
+        s.radius[k] = float(msys.radius[k])
+        s.conic[k] = float(msys.conic[k])
+        s.spacing[k] = float(msys.spacing[k])
+    return s
+
+
 def make_pupil(pupil) -> gbd_pupil:
     return gbd_pupil(float(pupil.diameter), int(pupil.n_across), 0)
 
@@ -219,6 +249,17 @@ def gbd_trace(system, pupil, overlap_factor: float, waist_ratio: float, out, str
     _check(lib().gbd_trace(ctypes.byref(make_system(system)), ctypes.byref(make_pupil(pupil)),
                            float(overlap_factor), float(waist_ratio), _ptr(out), int(cap),
                            _stream(stream)))
+    return n
+
+
+def gbd_trace_mirrors(msys, pupil, overlap_factor: float, waist_ratio: float, out,
+                      stream=None) -> int:
+    """Traces the pupil through conic mirrors into ``out`` (float64 [capacity, 36])."""
+    n = gbd_beamlet_count(pupil)
+    cap = out.shape[0] if out is not None else 0
+    _check(lib().gbd_trace_mirrors(ctypes.byref(make_mirror_system(msys)),
+                                   ctypes.byref(make_pupil(pupil)), float(overlap_factor),
+                                   float(waist_ratio), _ptr(out), int(cap), _stream(stream)))
     return n
 
 
@@ -472,6 +513,15 @@ def trace(system, pupil, device="cuda", stream=None):
     n = gbd_beamlet_count(pupil)
     out = torch.empty((max(n, 1), BEAMLET_DOUBLES), dtype=torch.float64, device=device)
     gbd_trace(system, pupil, pupil.overlap_factor, pupil.waist_ratio, out, stream)
+    return out[:n]
+
+
+def trace_mirrors(msys, pupil, device="cuda", stream=None):
+    """Beamlet table of a pupil in front of conic mirrors (gbd_trace_mirrors)."""
+    import torch
+    n = gbd_beamlet_count(pupil)
+    out = torch.empty((max(n, 1), BEAMLET_DOUBLES), dtype=torch.float64, device=device)
+    gbd_trace_mirrors(msys, pupil, pupil.overlap_factor, pupil.waist_ratio, out, stream)
     return out[:n]
 
 

@@ -89,6 +89,43 @@ def test_trace_rejects_bad_arguments(lib):
     assert "capacity" in lib.gbd_last_error().decode()
 
 
+def test_trace_mirrors_rejects_bad_arguments(lib):
+    msys, pupil, _ = W.hst_rc(n_across=16)
+
+    class T:
+        shape = (10 ** 6, 36)
+
+        def data_ptr(self):
+            return 16
+
+    def with_(**kw):
+        d = dict(wavelength=msys.wavelength, radius=msys.radius, conic=msys.conic,
+                 spacing=msys.spacing, diameter=msys.diameter, pupil_offset=msys.pupil_offset)
+        d.update(kw)
+        return W.MirrorSystem(**d)
+
+    bad = [
+        with_(wavelength=0.0),
+        with_(pupil_offset=0.0),
+        with_(radius=(), conic=(), spacing=(), diameter=()),
+        with_(radius=(0.0, 1.358)),
+        with_(radius=(float("inf"), 1.358)),
+        with_(spacing=(-4.9, 0.0)),
+        with_(conic=(float("nan"), -1.5)),
+    ]
+    for m in bad:
+        assert _einval(lambda: gbd.gbd_trace_mirrors(m, pupil, 1.5, 1.0, T())) == gbd.GBD_EINVAL
+    assert _einval(lambda: gbd.gbd_trace_mirrors(msys, pupil, 0.0, 1.0, T())) == gbd.GBD_EINVAL
+    assert _einval(lambda: gbd.gbd_trace_mirrors(msys, W.Pupil(-1.0, 16, 1.5, 1.0), 1.5, 1.0,
+                                                 T())) == gbd.GBD_EINVAL
+
+    class Small(T):
+        shape = (5, 36)
+    assert _einval(lambda: gbd.gbd_trace_mirrors(msys, pupil, 1.5, 1.0, Small())) == gbd.GBD_ENOMEM
+    with pytest.raises(ValueError):
+        gbd.make_mirror_system(with_(radius=(-1.0,) * 5, conic=(0.0,) * 5, spacing=(1.0,) * 5))
+
+
 def test_field_rejects_bad_arguments(lib):
     det = W.airy_small().detector
 

@@ -598,3 +598,16 @@ def test_rc_paraxial_limit_and_focal_length():
         for blk, (q, k) in (("A", (0, 0)), ("B", (0, 1)), ("C", (1, 0)), ("D", (1, 1))):
             assert np.max(np.abs(u[blk] - M[q, k] * np.eye(2))) <= 1e-6 * max(1.0, abs(M[q, k]))
     assert abs(-1.0 / M[1, 0] - W.HST_EFL) < 1e-3 * W.HST_EFL
+
+
+def test_rc_point_image_is_the_airy_pattern():
+    """The corrected telescope (App. B) is diffraction-limited on axis: its beamlet sum
+    reaches the Airy peak pi D^2 / (4 lambda f) of a 2.4 m, f = 57.6 m pupil and follows
+    |2 J1(x)/x| inside the third dark ring.  A wrong conic, curvature sign or reflection
+    leaves waves of aberration and fails both."""
+    msys, pupil, det = W.hst_rc(n_across=64, npix=256)
+    E = oracle.field(oracle.trace_mirrors(msys, pupil), msys, det)
+    D, f = W.HST_DIAMETER[0], W.HST_EFL
+    peak = math.pi * D * D / (4.0 * msys.wavelength * f)
+    assert abs(abs(E[det.ny // 2, det.nx // 2]) / peak - 1.0) < 3e-3
+    assert oracle.airy_score(E, det, msys.wavelength, f / D) < 5e-3
