@@ -43,8 +43,9 @@ GB300_MAX_MHZ = 2070.0
 # DRAM bytes per launch of field_mixed_kernel<2,4,false> on airy_large from one ncu capture
 # (profiles/field_mixed_kernel_airy_large.md) at 26 beamlet splits.  The reads are the
 # record tiles; the writes are the split partial fields, which scale with the split count.
-FIELD_MIXED_NCU = {"kernel": "field_mixed_kernel<2, 4, false>", "read": 3.599616e6,
-                   "write": 48.867072e6, "splits": 26, "rows": 2, "cols": 4}
+FIELD_MIXED_NCU = {"kernel": "field_mixed_kernel<2, 4, false, true> (row pairs)",
+                   "read": 3.337472e6, "write": 181.91232e6, "splits": 58, "rows": 2, "cols": 4,
+                   "scheme": 1}
 
 
 def parse():
@@ -61,6 +62,11 @@ def parse():
                     help="timed runs of the 1024-instance parameter sweep (0 = skip)")
     ap.add_argument("--no-point", action="store_true",
                     help="skip the plane- versus point-evaluation comparison")
+    ap.add_argument("--shape", default="",
+                    help="fixed mixed launch shape 'rows,cols,splits[,scheme]' instead of the "
+                         "autotuner's pick (scheme 1 = row pairs)")
+    ap.add_argument("--no-telescope", action="store_true",
+                    help="skip the App. B telescope (conic-mirror trace + field) line")
     ap.add_argument("--no-surrogate", action="store_true",
                     help="skip the surrogate-guided search versus grid and random search")
     return ap.parse_args()
@@ -179,7 +185,7 @@ class ClockSampler:
 def traffic_bytes(tuned):
     """Per-launch DRAM bytes of the captured kernel, writes scaled to the split count used."""
     n = FIELD_MIXED_NCU
-    if tuned[0] != n["rows"] or tuned[1] != n["cols"]:
+    if tuned[0] != n["rows"] or tuned[1] != n["cols"] or tuned[4] != n["scheme"]:
         return None
     return n["read"] + n["write"] * tuned[2] / n["splits"]
 
@@ -271,11 +277,19 @@ def run_ours(args, world, rank, local):
         return [a.elapsed_time(b) for a, b in times]
 
     clocks = ClockSampler(gpu_index_for_smi(local))
-    # the library's autotuner picks the launch shape (pixels per thread, beamlet splits)
+    # the library's autotuner picks the launch shape (pixels per thread, beamlet splits,
+    # scheme) unless --shape fixes it
     gbd.gbd_trace(sysm, pupil, pupil.overlap_factor, pupil.waist_ratio, beam, stream)
-    tune_ws = torch.empty(320 << 20, dtype=torch.uint8, device=dev)
-    tuned = gbd.gbd_autotune_field(beam, nb, sysm.wavelength, det, MIX, tune_ws, out[MIX], stream)
-    del tune_ws
+    if args.shape:
+        v = [int(x) for x in args.shape.split(",")]
+        gbd.gbd_field_set_shape(MIX, v[0], v[1], v[2], v[3] if len(v) > 3 else 0)
+        r_, c_, s_, k_ = gbd.gbd_field_get_shape(MIX, nb, det)
+        tuned = (r_, c_, s_, 0.0, k_)
+    else:
+        tune_ws = torch.empty(320 << 20, dtype=torch.uint8, device=dev)
+        tuned = gbd.gbd_autotune_field(beam, nb, sysm.wavelength, det, MIX, tune_ws, out[MIX],
+                                       stream)
+        del tune_ws
     ws[MIX] = torch.empty(max(256, gbd.gbd_field_workspace_bytes(nb, det, MIX)), dtype=torch.uint8,
                           device=dev)
     for _ in range(args.warmup):
@@ -415,6 +429,39 @@ def run_ours(args, world, rank, local):
                  "plane_over_point_speedup": t["point"] / t["plane"],
                  "plane_vs_point_rel_l2": float(np.linalg.norm(Epn - Eqn) / np.linalg.norm(Eqn))}
 
+    # ---- the App. B telescope: real-ray trace through its two conic mirrors, then the
+    # mixed-precision plane evaluation, 256 beamlets across on 512^2 pixels of 2.8 mas
+    telescope = None
+    if not args.no_telescope:
+        msys, tpup, tdet = W.hst_rc(n_across=256, npix=512)
+        nbr = gbd.gbd_beamlet_count(tpup)
+        br = torch.empty((nbr, gbd.BEAMLET_DOUBLES), dtype=torch.float64, device=dev)
+        wsr = gbd.workspace(nbr, tdet, MIX, dev)
+        Er = torch.empty((tdet.ny, tdet.nx), dtype=torch.complex64, device=dev)
+
+        def rc_step():
+            gbd.gbd_trace_mirrors(msys, tpup, tpup.overlap_factor, tpup.waist_ratio, br, stream)
+            gbd.gbd_field(br, nbr, msys.wavelength, tdet, MIX, wsr, Er, stream)
+        for _ in range(3):
+            rc_step()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b2 = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(3):
+            rc_step()
+        b2.record(stream)
+        torch.cuda.synchronize()
+        gbd.gbd_sync(stream)
+        rc_ms = a.elapsed_time(b2) / 3
+        airy_peak = math.pi * W.HST_DIAMETER[0] ** 2 / (4.0 * msys.wavelength * W.HST_EFL)
+        telescope = {"workload": f"App. B Ritchey-Chretien telescope, {nbr} beamlets x "
+                                 f"{tdet.nx}x{tdet.ny} pixels of 2.8 mas, real-ray trace + mixed field",
+                     "ms_per_psf": rc_ms, "value": nbr * tdet.nx * tdet.ny / (rc_ms * 1e-3),
+                     "unit": UNIT,
+                     "centre_over_airy_peak": float(abs(Er[tdet.ny // 2, tdet.nx // 2].item())
+                                                    / airy_peak)}
+
     # ---- surrogate-guided search versus the reference grid and random search
     surrogate = None
     if not args.no_surrogate:
@@ -448,30 +495,41 @@ def run_ours(args, world, rank, local):
 
     clk = clocks.stop()
 
-    # ---- roofline of the dominant kernel (mixed field kernel, MUFU pipe): each
-    # beamlet-pixel evaluation issues one ex2, one sin and one cos
+    # ---- roofline of the dominant kernel (mixed field kernel, MUFU pipe).  The direct
+    # scheme issues one ex2, one sin and one cos per beamlet-pixel evaluation; the row-pair
+    # scheme evaluates the first row and one row-step factor per column block exactly
+    # (cols + 1 exact evaluations per 2 x cols pixels) and the second row by complex
+    # multiplies on the FMA pipe.
     kms, kn = kt["field_mixed"]
     k_avg_s = (kms / max(kn, 1)) * 1e-3
     probes = gbd.gbd_probe_peaks()
-    clk_per_eval = 1.0 / MUFU_EX2_PER_CLK_SM + 2.0 / MUFU_SINCOS_PER_CLK_SM
-    peak_evals = GB300_SMS * GB300_MAX_MHZ * 1e6 / clk_per_eval
-    probe_peak_evals = 1.0 / (1.0 / probes["ex2"] + 1.0 / probes["sin"] + 1.0 / probes["cos"])
+    clk_per_exact = 1.0 / MUFU_EX2_PER_CLK_SM + 2.0 / MUFU_SINCOS_PER_CLK_SM
+    exact_per_eval = (tuned[1] + 1) / (2.0 * tuned[1]) if tuned[4] else 1.0
+    peak_direct = GB300_SMS * GB300_MAX_MHZ * 1e6 / clk_per_exact
+    peak_evals = peak_direct / exact_per_eval
+    probe_peak_direct = 1.0 / (1.0 / probes["ex2"] + 1.0 / probes["sin"] + 1.0 / probes["cos"])
     achieved = evals / k_avg_s
     roofline = {
-        "bound": "alu", "pipe": "MUFU (XU): ex2 + sin + cos per beamlet-pixel",
+        "bound": "alu",
+        "pipe": (f"MUFU (XU): ex2 + sin + cos per exact evaluation, {exact_per_eval:.4g} exact "
+                 "evaluations per beamlet-pixel (scheme "
+                 + ("row_pair" if tuned[4] else "direct") + ")"),
         "achieved": achieved / 1e9, "peak": peak_evals / 1e9, "unit": "Geval/s",
         "frac": achieved / peak_evals,
         "traffic": traffic_bytes(tuned),
         "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one capture of "
                            f"{FIELD_MIXED_NCU['kernel']} at {FIELD_MIXED_NCU['splits']} splits; "
                            "writes scaled to this launch's split count"),
-        "peak_source": (f"derived: {GB300_SMS} SMs x {GB300_MAX_MHZ:g} MHz / (1/{MUFU_EX2_PER_CLK_SM}"
-                        f" + 2/{MUFU_SINCOS_PER_CLK_SM}) clk per eval"),
+        "peak_source": (f"derived: {GB300_SMS} SMs x {GB300_MAX_MHZ:g} MHz / ((1/{MUFU_EX2_PER_CLK_SM}"
+                        f" + 2/{MUFU_SINCOS_PER_CLK_SM}) clk per exact evaluation x "
+                        f"{exact_per_eval:.4g})"),
         "kernel": "field_mixed_kernel", "kernel_ms_avg": k_avg_s * 1e3, "launches": kn,
-        "mufu_gops": 3.0 * achieved / 1e9,
+        "mufu_gops": 3.0 * exact_per_eval * achieved / 1e9,
+        "direct_scheme_peak": peak_direct / 1e9,
+        "frac_of_direct_scheme_peak": achieved / peak_direct,
         "probe_ops_per_s": probes,
-        "probe_peak_evals_per_s": probe_peak_evals,
-        "frac_of_probe_peak": achieved / probe_peak_evals,
+        "probe_peak_evals_per_s": probe_peak_direct / exact_per_eval,
+        "frac_of_probe_peak": achieved * exact_per_eval / probe_peak_direct,
     }
 
     # ---- error and CPU baseline (rank 0, one GPU)
@@ -497,13 +555,17 @@ def run_ours(args, world, rank, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "precision": "mixed: FP64 per-beamlet trace/projection, FP32 per-pixel phase with MUFU "
-                     "ex2/sin/cos, compensated FP32 sum",
+        "precision": ("mixed: FP64 per-beamlet trace/projection, FP32 per-pixel phase with MUFU "
+                      "ex2/sin/cos" + (" (second row of each pair by an FP32 complex row-step "
+                                       "factor)" if tuned[4] else "") + ", compensated FP32 sum"),
         "data": "synthetic (ideal F/10 lens standing in for the paper's traced telescope)",
         "config": config_block(wl, nb), "clocks": clk, "e2e": e2e, "fp64_path": f64,
         "autotuned_shape": {"rows_per_thread": tuned[0], "cols_per_thread": tuned[1],
-                            "splits": tuned[2], "ms": tuned[3]},
+                            "splits": tuned[2], "ms": tuned[3],
+                            "scheme": "row_pair" if tuned[4] else "direct",
+                            "fixed_by_flag": bool(args.shape)},
         "sweep": sweep, "surrogate": surrogate, "point_evaluation": point,
+        "telescope": telescope,
         "error": error, "roofline": roofline, "cpu_baseline": cpu,
         "gpu_launches": launches_per_step * args.steps,
         "kernel_ms": {k: (v[0] / max(v[1], 1)) for k, v in kt.items()},

@@ -191,13 +191,16 @@ gbd_status gbd_field(const gbd_beamlet* beamlets, int32_t n_beamlets, double wav
  * quadratic-form record of every beamlet to `coeffs` (device).
  *   MIXED: 16 floats per beamlet in the tiled layout gbd_field uses
  *          [tile = b / 64][field f = 0..3][b % 64][4 floats];
- *          values (i0, j0, a0, p0 | a1u, p1u, a1v, p1v | auu, puu, auv, puv | avv, pvv, 0, 0)
+ *          values (i0, j0, a0, p0 | a1u, p1u, a1v, p1v | auu, puu, auv, puv | avv, pvv, Tr, Ti)
  *          with log2 |E_j(i, j)| = a0 + a1u tu + a1v tv + auu tu^2 + auv tu tv + avv tv^2 and
  *          the phase in radians p0 + ... likewise (p0 in [-pi, pi)), tu = i - i0, tv = j - j0
- *          (pixel units), excluding the common carrier exp(-ik z(s)).
- *          wide_flag (device, may be NULL; zero it first) is set to 1 if some beamlet's
- *          phase can exceed 256 rad on the detector, in which case gbd_field reduces every
- *          per-pixel phase exactly before sin/cos.
+ *          (pixel units), excluding the common carrier exp(-ik z(s)); T = Tr + i Ti =
+ *          exp(256 (auv ln 2 + i puv)), the row-pair scheme's column factor.
+ *          wide_flag (device, may be NULL; zero it first) is OR-ed with bit 0 if some
+ *          beamlet's phase can exceed 256 rad on the detector (gbd_field then reduces every
+ *          per-pixel phase exactly before sin/cos) and bit 1 if some beamlet's log2
+ *          amplitude can change by more than 64 over 8 rows (the row-pair scheme then falls
+ *          back to direct evaluation).
  *   F64:   16 doubles per beamlet [tile][field f = 0..7][b % 64][2 doubles], same order, the
  *          phase in turns (phase / 2 pi), field 7 = S = exp of twice the uu coefficient as
  *          a complex number (re, im), the second ratio of a row recurrence; wide_flag is
@@ -232,8 +235,13 @@ typedef struct {
                                /* (contiguous row segments, complex recurrence)   */
     int32_t splits;            /* beamlet splits (0 = heuristic)             */
     float   ms;                /* measured time of the shape (autotune)      */
+    int32_t scheme;            /* mixed only: GBD_SCHEME_DIRECT, or           */
+                               /* GBD_SCHEME_ROW_PAIR (2x2, 2x4: the second   */
+                               /* row from the first by a complex factor)     */
 } gbd_shape;
 
+#define GBD_SCHEME_DIRECT 0
+#define GBD_SCHEME_ROW_PAIR 1
 gbd_status gbd_field_set_shape(int32_t precision, const gbd_shape* shape);
 gbd_status gbd_field_get_shape(int32_t precision, int32_t n_beamlets,
                                const gbd_detector* detector, gbd_shape* out);

@@ -28,14 +28,16 @@ __device__ unsigned int g_field_status = 0;
 
 __device__ __forceinline__ void record_timeout() { atomicOr(&g_field_status, gbd::kStatusTimeout); }
 
-// WIDE selects the instantiation with per-pixel phase reduction.  Both instantiations are
-// launched; each returns at once unless the projection's wide-phase flag selects it.
-template <int RB, int CB, bool WIDE>
+// WIDE selects the instantiation with per-pixel phase reduction, PAIR (RB = 2) the row-pair
+// evaluation.  Several instantiations are launched for one field; each returns at once
+// unless the projection's flag word, masked by `mask`, equals `want`.
+template <int RB, int CB, bool WIDE, bool PAIR>
 __global__ void __launch_bounds__(kThreads, 2)
     field_mixed_kernel(const float4* __restrict__ coef, int n_tiles, int tiles_per_split, int nx,
-                       int ny, double2* __restrict__ partial, const unsigned* __restrict__ wide,
-                       uint32_t spins) {
-    if ((*wide != 0u) != WIDE) return;
+                       int ny, double2* __restrict__ partial, const unsigned* __restrict__ flags,
+                       unsigned mask, unsigned want, uint32_t spins) {
+    static_assert(!PAIR || RB == 2, "row pairs need two rows per thread");
+    if ((*flags & mask) != want) return;
     constexpr int kTileF4 = gbd::kMixedFields * gbd::kTile;
     __shared__ __align__(128) float4 stage[kStages][kTileF4];
     __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
@@ -69,7 +71,10 @@ __global__ void __launch_bounds__(kThreads, 2)
             ok = false;
             break;
         }
-        gbd::mixed_tile<RB, CB, WIDE>(ts.tile(k), colf, rowf, acc);
+        if constexpr (PAIR)
+            gbd::mixed_tile_pair<CB, WIDE>(ts.tile(k), colf, rowf[0], acc);
+        else
+            gbd::mixed_tile<RB, CB, WIDE>(ts.tile(k), colf, rowf, acc);
         gbd::mixed_fold<RB, CB>(acc, hi, lo);
         if (!ts.release(k, lane, warp, spins)) {
             ok = false;
@@ -339,14 +344,39 @@ __global__ void __launch_bounds__(256) field_reduce_kernel(const double2* __rest
 
 template <int RB, int CB>
 cudaError_t launch_mixed(const void* coeffs, int n_tiles, const gbd_project_params& p,
-                         const gbd_field_launch& L, double2* partial, const unsigned* wide,
+                         const gbd_field_launch& L, double2* partial, const unsigned* flags,
                          uint32_t spins, cudaStream_t s) {
+    using gbd::kFlagWide;
     dim3 grid((p.nx + 32 * CB - 1) / (32 * CB), (p.ny + 8 * RB - 1) / (8 * RB), L.splits);
     const float4* c = static_cast<const float4*>(coeffs);
-    field_mixed_kernel<RB, CB, false><<<grid, kThreads, 0, s>>>(c, n_tiles, L.tiles_per_split, p.nx,
-                                                                p.ny, partial, wide, spins);
-    field_mixed_kernel<RB, CB, true><<<grid, kThreads, 0, s>>>(c, n_tiles, L.tiles_per_split, p.nx,
-                                                               p.ny, partial, wide, spins);
+    const int tps = L.tiles_per_split;
+    field_mixed_kernel<RB, CB, false, false><<<grid, kThreads, 0, s>>>(
+        c, n_tiles, tps, p.nx, p.ny, partial, flags, kFlagWide, 0u, spins);
+    field_mixed_kernel<RB, CB, true, false><<<grid, kThreads, 0, s>>>(
+        c, n_tiles, tps, p.nx, p.ny, partial, flags, kFlagWide, kFlagWide, spins);
+    return cudaGetLastError();
+}
+
+// Row pairs, with the direct 2 x CB kernels as the fallback when the projection flags a
+// beamlet too steep for the recurrence.
+template <int CB>
+cudaError_t launch_mixed_pair(const void* coeffs, int n_tiles, const gbd_project_params& p,
+                              const gbd_field_launch& L, double2* partial, const unsigned* flags,
+                              uint32_t spins, cudaStream_t s) {
+    using gbd::kFlagSteep;
+    using gbd::kFlagWide;
+    constexpr unsigned kBoth = kFlagWide | kFlagSteep;
+    dim3 grid((p.nx + 32 * CB - 1) / (32 * CB), (p.ny + 15) / 16, L.splits);
+    const float4* c = static_cast<const float4*>(coeffs);
+    const int tps = L.tiles_per_split;
+    field_mixed_kernel<2, CB, false, true><<<grid, kThreads, 0, s>>>(
+        c, n_tiles, tps, p.nx, p.ny, partial, flags, kBoth, 0u, spins);
+    field_mixed_kernel<2, CB, true, true><<<grid, kThreads, 0, s>>>(
+        c, n_tiles, tps, p.nx, p.ny, partial, flags, kBoth, kFlagWide, spins);
+    field_mixed_kernel<2, CB, false, false><<<grid, kThreads, 0, s>>>(
+        c, n_tiles, tps, p.nx, p.ny, partial, flags, kBoth, kFlagSteep, spins);
+    field_mixed_kernel<2, CB, true, false><<<grid, kThreads, 0, s>>>(
+        c, n_tiles, tps, p.nx, p.ny, partial, flags, kBoth, kBoth, spins);
     return cudaGetLastError();
 }
 
@@ -386,33 +416,35 @@ typedef cudaError_t (*launch_fn)(const void*, int, const gbd_project_params&,
                                  cudaStream_t);
 
 struct ShapeEntry {
-    int rb, cb;
+    int rb, cb, scheme;
     launch_fn fn;
     const void* kernel;
 };
 
 const ShapeEntry kMixedShapes[] = {
-    {1, 4, launch_mixed<1, 4>, (const void*)field_mixed_kernel<1, 4, false>},
-    {2, 2, launch_mixed<2, 2>, (const void*)field_mixed_kernel<2, 2, false>},
-    {2, 4, launch_mixed<2, 4>, (const void*)field_mixed_kernel<2, 4, false>},
-    {4, 2, launch_mixed<4, 2>, (const void*)field_mixed_kernel<4, 2, false>},
+    {1, 4, GBD_SCHEME_DIRECT, launch_mixed<1, 4>, (const void*)field_mixed_kernel<1, 4, false, false>},
+    {2, 2, GBD_SCHEME_DIRECT, launch_mixed<2, 2>, (const void*)field_mixed_kernel<2, 2, false, false>},
+    {2, 4, GBD_SCHEME_DIRECT, launch_mixed<2, 4>, (const void*)field_mixed_kernel<2, 4, false, false>},
+    {4, 2, GBD_SCHEME_DIRECT, launch_mixed<4, 2>, (const void*)field_mixed_kernel<4, 2, false, false>},
+    {2, 2, GBD_SCHEME_ROW_PAIR, launch_mixed_pair<2>, (const void*)field_mixed_kernel<2, 2, false, true>},
+    {2, 4, GBD_SCHEME_ROW_PAIR, launch_mixed_pair<4>, (const void*)field_mixed_kernel<2, 4, false, true>},
 };
 // (1,2), (2,2): every pixel evaluated directly (columns 32 apart); (1,8), (1,16), (2,8),
 // (1,32): contiguous row segments advanced by complex multiplies.
 const ShapeEntry kF64Shapes[] = {
-    {1, 2, launch_f64<1, 2>, (const void*)field_f64_kernel<1, 2>},
-    {2, 2, launch_f64<2, 2>, (const void*)field_f64_kernel<2, 2>},
-    {1, 8, launch_f64_row<1, 8>, (const void*)field_f64_row_kernel<1, 8>},
-    {2, 8, launch_f64_row<2, 8>, (const void*)field_f64_row_kernel<2, 8>},
-    {1, 16, launch_f64_row<1, 16>, (const void*)field_f64_row_kernel<1, 16>},
-    {1, 32, launch_f64_row<1, 32>, (const void*)field_f64_row_kernel<1, 32>},
+    {1, 2, 0, launch_f64<1, 2>, (const void*)field_f64_kernel<1, 2>},
+    {2, 2, 0, launch_f64<2, 2>, (const void*)field_f64_kernel<2, 2>},
+    {1, 8, 0, launch_f64_row<1, 8>, (const void*)field_f64_row_kernel<1, 8>},
+    {2, 8, 0, launch_f64_row<2, 8>, (const void*)field_f64_row_kernel<2, 8>},
+    {1, 16, 0, launch_f64_row<1, 16>, (const void*)field_f64_row_kernel<1, 16>},
+    {1, 32, 0, launch_f64_row<1, 32>, (const void*)field_f64_row_kernel<1, 32>},
 };
 
-const ShapeEntry* find_shape(int precision, int rb, int cb) {
+const ShapeEntry* find_shape(int precision, int rb, int cb, int scheme) {
     if (precision == GBD_PREC_MIXED) {
         for (const auto& e : kMixedShapes)
-            if (e.rb == rb && e.cb == cb) return &e;
-    } else {
+            if (e.rb == rb && e.cb == cb && e.scheme == scheme) return &e;
+    } else if (scheme == GBD_SCHEME_DIRECT) {
         for (const auto& e : kF64Shapes)
             if (e.rb == rb && e.cb == cb) return &e;
     }
@@ -421,12 +453,12 @@ const ShapeEntry* find_shape(int precision, int rb, int cb) {
 
 }  // namespace
 
-bool gbd_field_shape_supported(int precision, int rb, int cb) {
-    return find_shape(precision, rb, cb) != nullptr;
+bool gbd_field_shape_supported(int precision, int rb, int cb, int scheme) {
+    return find_shape(precision, rb, cb, scheme) != nullptr;
 }
 
-int gbd_field_occupancy(int precision, int rb, int cb) {
-    const ShapeEntry* e = find_shape(precision, rb, cb);
+int gbd_field_occupancy(int precision, int rb, int cb, int scheme) {
+    const ShapeEntry* e = find_shape(precision, rb, cb, scheme);
     if (!e) return 0;
     int blocks = 0;
     size_t smem = precision == GBD_PREC_MIXED ? 0 : (size_t)kStages * gbd::kF64TileBytes;
@@ -442,7 +474,7 @@ cudaError_t gbd_launch_field_kernel(int precision, const void* coeffs, int n_til
                                     const gbd_project_params& p, const gbd_field_launch& L,
                                     double2* partial, const unsigned* wide, uint32_t wait_spins,
                                     cudaStream_t s) {
-    const ShapeEntry* e = find_shape(precision, L.rows_per_thread, L.cols_per_thread);
+    const ShapeEntry* e = find_shape(precision, L.rows_per_thread, L.cols_per_thread, L.scheme);
     if (!e) return cudaErrorInvalidValue;
     return e->fn(coeffs, n_tiles, p, L, partial, wide, wait_spins, s);
 }

@@ -152,6 +152,58 @@ __device__ __forceinline__ void mixed_tile(const float4* __restrict__ st, const 
     }
 }
 
+// Row-pair variant of mixed_tile on rows v (evaluated directly) and v + 8 (derived): with
+// ln E quadratic in the pixel, E(u, v + 8) = E(u, v) R(u) where the 8-row step factor
+// R(u) = exp(8 (c_v + c_uv tu + c_vv (2 tv + 8))) is itself geometric along the thread's
+// columns, R(u + 32) = R(u) T with T = exp(256 c_uv) from the record.  One exact R per
+// beamlet (reduced to [-pi, pi] always) replaces CB - 1 of the 2 CB exact evaluations'
+// three MUFU operations each; the second row costs 2 FMUL + 4 FFMA (+ 4 for the next R).
+// Requires the projection's steep flag to be clear (every R within 2^+-64).
+template <int CB, bool WIDE>
+__device__ __forceinline__ void mixed_tile_pair(const float4* __restrict__ st,
+                                                const float (&colf)[CB], float rowf,
+                                                float2 (&acc)[2][CB]) {
+    const float kTwoPi = 6.28318530717958647692f, kInvTwoPi = 0.15915494309189533577f;
+#pragma unroll 1
+    for (int b = 0; b < kTile; ++b) {
+        const float4 q0 = st[b];
+        const float4 q1 = st[kTile + b];
+        const float4 q2 = st[2 * kTile + b];
+        const float4 q3 = st[3 * kTile + b];
+        float tu[CB];
+#pragma unroll
+        for (int c = 0; c < CB; ++c) tu[c] = colf[c] - q0.x;
+        const float tv = rowf - q0.y;
+        const float ra = fmaf(tv, fmaf(q3.x, tv, q1.z), q0.z);
+        const float rp = fmaf(tv, fmaf(q3.y, tv, q1.w), q0.w);
+        const float sa = fmaf(q2.z, tv, q1.x);
+        const float sp = fmaf(q2.w, tv, q1.y);
+        const float w = fmaf(2.0f, tv, 8.0f);
+        const float ga = 8.0f * fmaf(q3.x, w, fmaf(q2.z, tu[0], q1.z));
+        const float gp = frac_turns(8.0f * kInvTwoPi * fmaf(q3.y, w, fmaf(q2.w, tu[0], q1.w))) * kTwoPi;
+        const float gm = mufu_ex2(ga);
+        float rx = gm * mufu_cos(gp), ry = gm * mufu_sin(gp);
+#pragma unroll
+        for (int c = 0; c < CB; ++c) {
+            const float ea = fmaf(tu[c], fmaf(q2.x, tu[c], sa), ra);
+            float x = fmaf(tu[c], fmaf(q2.y, tu[c], sp), rp);
+            if (WIDE) x = frac_turns(x * kInvTwoPi) * kTwoPi;
+            const float amp = mufu_ex2(ea);
+            const float cs = mufu_cos(x), sn = mufu_sin(x);
+            acc[0][c].x = fmaf(amp, cs, acc[0][c].x);
+            acc[0][c].y = fmaf(amp, sn, acc[0][c].y);
+            const float wx = amp * rx, wy = amp * ry;
+            acc[1][c].x = fmaf(cs, wx, fmaf(-sn, wy, acc[1][c].x));
+            acc[1][c].y = fmaf(cs, wy, fmaf(sn, wx, acc[1][c].y));
+            if (c + 1 < CB) {
+                const float nx = fmaf(rx, q3.z, -ry * q3.w);
+                ry = fmaf(rx, q3.w, ry * q3.z);
+                rx = nx;
+            }
+        }
+    }
+}
+
 // Fold a tile's FP32 sums into compensated (hi, lo) pairs (TwoSum) and clear them.
 template <int RB, int CB>
 __device__ __forceinline__ void mixed_fold(float2 (&acc)[RB][CB], float2 (&hi)[RB][CB],

@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
 #include <map>
 #include <mutex>
 #include <vector>
@@ -211,6 +212,7 @@ gbd_shape default_shape(int precision) {
     s.cols_per_thread = precision == GBD_PREC_MIXED ? 4 : 16;
     s.splits = 0;
     s.ms = 0.f;
+    s.scheme = GBD_SCHEME_DIRECT;
     return s;
 }
 
@@ -233,9 +235,10 @@ long pixel_ctas(int precision, int rb, int cb, const gbd_detector* D) {
     return (long)((D->nx + 32 * cb - 1) / (32 * cb)) * ((D->ny + 8 * rb - 1) / (8 * rb));
 }
 
-int heuristic_splits(int precision, int rb, int cb, int n_tiles, const gbd_detector* D) {
+int heuristic_splits(int precision, int rb, int cb, int scheme, int n_tiles,
+                     const gbd_detector* D) {
     const long pix_ctas = pixel_ctas(precision, rb, cb, D);
-    const int occ = std::max(1, gbd_field_occupancy(precision, rb, cb));
+    const int occ = std::max(1, gbd_field_occupancy(precision, rb, cb, scheme));
     const long slots = (long)occ * sm_count();
     long s = (16 * slots + pix_ctas - 1) / pix_ctas;
     s = std::min<long>(s, std::max(1, n_tiles / 8));
@@ -249,9 +252,10 @@ gbd_field_launch resolve_launch(int precision, const gbd_shape& sh, int n_tiles,
     gbd_field_launch L;
     L.rows_per_thread = sh.rows_per_thread;
     L.cols_per_thread = sh.cols_per_thread;
+    L.scheme = sh.scheme;
     int s = sh.splits > 0 ? std::min(sh.splits, n_tiles)
                           : heuristic_splits(precision, sh.rows_per_thread, sh.cols_per_thread,
-                                             n_tiles, D);
+                                             sh.scheme, n_tiles, D);
     s = std::max(1, s);
     L.tiles_per_split = (n_tiles + s - 1) / s;
     L.splits = (n_tiles + L.tiles_per_split - 1) / L.tiles_per_split;
@@ -529,8 +533,9 @@ gbd_status gbd_field_set_shape(int32_t precision, const gbd_shape* shape) {
     if (precision != GBD_PREC_F64 && precision != GBD_PREC_MIXED)
         return fail(GBD_EINVAL, "precision must be GBD_PREC_F64 or GBD_PREC_MIXED");
     gbd_shape s = shape ? *shape : default_shape(precision);
-    if (!gbd_field_shape_supported(precision, s.rows_per_thread, s.cols_per_thread))
-        return fail(GBD_EINVAL, "unsupported shape %dx%d", s.rows_per_thread, s.cols_per_thread);
+    if (!gbd_field_shape_supported(precision, s.rows_per_thread, s.cols_per_thread, s.scheme))
+        return fail(GBD_EINVAL, "unsupported shape %dx%d (scheme %d)", s.rows_per_thread,
+                    s.cols_per_thread, s.scheme);
     if (s.splits < 0 || s.splits > 1024) return fail(GBD_EINVAL, "splits must be in [0, 1024]");
     std::lock_guard<std::mutex> lk(g_mu);
     g_shapes[{current_device(), precision}] = s;
@@ -562,20 +567,22 @@ gbd_status gbd_autotune_field(const gbd_beamlet* beamlets, int32_t n_beamlets, d
     if (st != GBD_OK) return st;
     if (n_beamlets == 0) return fail(GBD_EINVAL, "autotune needs at least one beamlet");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    static const int kMixed[][2] = {{1, 4}, {2, 2}, {2, 4}, {4, 2}};
-    static const int kF64[][2] = {{1, 2}, {2, 2}, {1, 8}, {2, 8}, {1, 16}, {1, 32}};
-    std::vector<std::pair<int, int>> shapes;
+    static const int kMixed[][3] = {{1, 4, GBD_SCHEME_DIRECT},   {2, 2, GBD_SCHEME_DIRECT},
+                                    {2, 4, GBD_SCHEME_DIRECT},   {4, 2, GBD_SCHEME_DIRECT},
+                                    {2, 2, GBD_SCHEME_ROW_PAIR}, {2, 4, GBD_SCHEME_ROW_PAIR}};
+    static const int kF64[][3] = {{1, 2, 0}, {2, 2, 0}, {1, 8, 0}, {2, 8, 0}, {1, 16, 0}, {1, 32, 0}};
+    std::vector<std::array<int, 3>> shapes;
     if (precision == GBD_PREC_MIXED)
-        for (auto& v : kMixed) shapes.push_back({v[0], v[1]});
+        for (auto& v : kMixed) shapes.push_back({v[0], v[1], v[2]});
     else
-        for (auto& v : kF64) shapes.push_back({v[0], v[1]});
+        for (auto& v : kF64) shapes.push_back({v[0], v[1], v[2]});
     const int nt = n_tiles_of(n_beamlets);
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return cuda_fail(cudaGetLastError(), "autotune events");
-    gbd_shape win{0, 0, 0, 1e30f};
+    gbd_shape win{0, 0, 0, 1e30f, 0};
     for (auto& rc : shapes) {
-        gbd_shape cand{rc.first, rc.second, 0, 0.f};
+        gbd_shape cand{rc[0], rc[1], 0, 0.f, rc[2]};
         const int base = resolve_launch(precision, cand, nt, detector).splits;
         std::vector<int> splits = {std::max(1, base / 2), base, std::min(nt, base * 3 / 2),
                                    std::min(nt, base * 2), std::min(nt, base * 5 / 2)};

@@ -23,6 +23,9 @@ constexpr uint32_t kDefaultWaitSpins = 1u << 24;
 
 // Status bits recorded in a translation unit's device status word.
 constexpr unsigned kStatusTimeout = 1u;
+// Bits of the projection's flag word (mixed records).
+constexpr unsigned kFlagWide = 1u;   // some phase may exceed kWidePhase on the detector
+constexpr unsigned kFlagSteep = 2u;  // the row-pair recurrence could leave FP32 range
 
 // ----------------------------------------------------------------- PTX wrappers --
 
@@ -176,7 +179,7 @@ struct gbd_project_params {
 };
 
 struct gbd_field_launch {
-    int rows_per_thread, cols_per_thread, splits, tiles_per_split;
+    int rows_per_thread, cols_per_thread, splits, tiles_per_split, scheme;
 };
 
 namespace gbd {
@@ -220,7 +223,7 @@ cudaError_t gbd_launch_field_kernel(int precision, const void* coeffs, int n_til
                                     cudaStream_t s);
 cudaError_t gbd_launch_field_reduce(int precision, const gbd_project_params& p, int splits,
                                     const double2* partial, void* out, cudaStream_t s);
-int gbd_field_occupancy(int precision, int rb, int cb);
+int gbd_field_occupancy(int precision, int rb, int cb, int scheme);
 gbd_status gbd_set_error(gbd_status st, const char* msg);  // sets gbd_last_error()
 gbd_status gbd_check_system(const gbd_system* s);
 gbd_status gbd_check_detector(const gbd_detector* d);
@@ -241,6 +244,6 @@ gbd_status gbd_field_fixed_scratch(const gbd_beamlet* beamlets, int32_t n, doubl
                                    const gbd_detector* detector, int32_t precision,
                                    void* scratch, size_t scratch_bytes, void* out,
                                    cudaStream_t stream);
-bool gbd_field_shape_supported(int precision, int rb, int cb);
+bool gbd_field_shape_supported(int precision, int rb, int cb, int scheme);
 unsigned gbd_field_status_read_clear();
 cudaError_t gbd_run_probes(double* out);

@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                  int ny, const double2* __restrict__ airy, int n_regions,
                  double* __restrict__ moments, int* __restrict__ counter,
                  const unsigned* __restrict__ wide, uint32_t spins) {
-    if ((*wide != 0u) != WIDE) return;
+    if (((*wide & gbd::kFlagWide) != 0u) != WIDE) return;
     constexpr int kTileF4 = gbd::kMixedFields * gbd::kTile;
     __shared__ __align__(128) float4 stage[kStages][kTileF4];
     __shared__ __align__(8) uint64_t full[kStages], empty[kStages];

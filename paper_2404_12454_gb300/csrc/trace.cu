@@ -345,12 +345,16 @@ __device__ Quad project_one(const gbd_beamlet& b, const gbd_project_params& G) {
 }
 
 // Mixed-precision record of beamlet `t` in the tiled layout (4 float4 fields per beamlet),
-// phase coefficients in radians.  Returns whether the beamlet's phase can exceed the
-// wide-phase bound anywhere on the detector (|tu| <= U, |tv| <= V around its centre).
-__device__ __forceinline__ bool write_mixed(float4* __restrict__ out, long long t, const Quad& q,
-                                            const gbd_project_params& G) {
+// phase coefficients in radians; the last field's spare pair holds T = exp(256 c_uv), the
+// factor between the 8-row steps of columns 32 apart (row-pair kernels).  Returns the flag
+// bits: kFlagWide if the beamlet's phase can exceed the wide-phase bound anywhere on the
+// detector (|tu| <= U, |tv| <= V around its centre), kFlagSteep if its log2 amplitude can
+// change by more than 64 over an 8-row step there (with T^3 included), where the row-pair
+// recurrence could under- or overflow FP32.
+__device__ __forceinline__ unsigned write_mixed(float4* __restrict__ out, long long t, const Quad& q,
+                                                const gbd_project_params& G) {
     float4 f0, f1, f2, f3;
-    bool wide = false;
+    unsigned flags = 0;
     if (q.pad) {
         f0 = make_float4(0.f, 0.f, gbd::kPadLog2Amp, 0.f);
         f1 = f2 = f3 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -361,11 +365,19 @@ __device__ __forceinline__ bool write_mixed(float4* __restrict__ out, long long 
         const double U = fmax(q.i0, G.nx - 1 - q.i0), V = fmax(q.j0, G.ny - 1 - q.j0);
         const double bound = fabs(p[0]) + fabs(p[1]) * U + fabs(p[2]) * V + fabs(p[3]) * U * U +
                              fabs(p[4]) * U * V + fabs(p[5]) * V * V;
-        wide = !(bound <= (double)gbd::kWidePhase);
+        if (!(bound <= (double)gbd::kWidePhase)) flags |= gbd::kFlagWide;
+        // log2 amplitude change over 8 rows: 8 (a_v + a_uv tu + a_vv (2 tv + 8))
+        const double step = 8.0 * (fabs(q.a[2]) + fabs(q.a[4]) * (U + 96.0) +
+                                    fabs(q.a[5]) * (2.0 * V + 8.0)) + 768.0 * fabs(q.a[4]);
+        if (!(step <= 64.0)) flags |= gbd::kFlagSteep;
+        const double tm = exp2(256.0 * q.a[4]);
+        const double tt = 256.0 * q.p[4];
+        double sn, cs;
+        sincospi(2.0 * (tt - rint(tt)), &sn, &cs);
         f0 = make_float4((float)q.i0, (float)q.j0, (float)q.a[0], (float)p[0]);
         f1 = make_float4((float)q.a[1], (float)p[1], (float)q.a[2], (float)p[2]);
         f2 = make_float4((float)q.a[3], (float)p[3], (float)q.a[4], (float)p[4]);
-        f3 = make_float4((float)q.a[5], (float)p[5], 0.f, 0.f);
+        f3 = make_float4((float)q.a[5], (float)p[5], (float)(tm * cs), (float)(tm * sn));
     }
     float4* tile = out + (size_t)(t / gbd::kTile) * gbd::kMixedFields * gbd::kTile;
     const int l = (int)(t % gbd::kTile);
@@ -373,7 +385,7 @@ __device__ __forceinline__ bool write_mixed(float4* __restrict__ out, long long 
     tile[gbd::kTile + l] = f1;
     tile[2 * gbd::kTile + l] = f2;
     tile[3 * gbd::kTile + l] = f3;
-    return wide;
+    return flags;
 }
 
 __global__ void __launch_bounds__(128) project_mixed_kernel(const gbd_beamlet* __restrict__ b, int n,
@@ -385,7 +397,8 @@ __global__ void __launch_bounds__(128) project_mixed_kernel(const gbd_beamlet* _
     Quad q;
     q.pad = true;
     if (t < n) q = project_one(b[t], G);
-    if (write_mixed(out, t, q, G) && wide) atomicOr(wide, 1u);
+    const unsigned f = write_mixed(out, t, q, G);
+    if (f && wide) atomicOr(wide, f);
 }
 
 __global__ void __launch_bounds__(128) project_f64_kernel(const gbd_beamlet* __restrict__ b, int n,
@@ -451,7 +464,8 @@ __global__ void __launch_bounds__(256)
                   &bm);
         q = project_one(bm, G);
     }
-    if (write_mixed(out, t, q, G) && wide) atomicOr(wide, 1u);
+    const unsigned f = write_mixed(out, t, q, G);
+    if (f && wide) atomicOr(wide, f);
 }
 
 }  // namespace

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "libgbd.so")
 
 GBD_OK, GBD_EINVAL, GBD_ECUDA, GBD_ENOMEM, GBD_ETIMEOUT, GBD_EUNSUPPORTED = range(6)
 GBD_PREC_F64, GBD_PREC_MIXED = 0, 1
+GBD_SCHEME_DIRECT, GBD_SCHEME_ROW_PAIR = 0, 1
 GBD_MAX_ZERN = 64
 GBD_MAX_MIRRORS = 4
 BEAMLET_DOUBLES = 36
@@ -61,7 +62,7 @@ class gbd_detector(ctypes.Structure):
 
 class gbd_shape(ctypes.Structure):
     _fields_ = [("rows_per_thread", ctypes.c_int32), ("cols_per_thread", ctypes.c_int32),
-                ("splits", ctypes.c_int32), ("ms", ctypes.c_float)]
+                ("splits", ctypes.c_int32), ("ms", ctypes.c_float), ("scheme", ctypes.c_int32)]
 
 
 # Exported symbols of libgbd.so and their ctypes signatures (name -> (restype, argtypes)).
@@ -284,15 +285,17 @@ def gbd_project_bytes(n_beamlets: int, precision: int) -> int:
 
 def gbd_project(beamlets, n_beamlets: int, wavelength: float, detector, precision: int, coeffs,
                 wide_flag=None, stream=None) -> None:
-    """Projected records into ``coeffs``; ``wide_flag`` (int32 CUDA tensor, zeroed) is set
-    to 1 if some beamlet's phase can exceed 256 rad on the detector (mixed only)."""
+    """Projected records into ``coeffs``; ``wide_flag`` (int32 CUDA tensor, zeroed) gets
+    bit 0 if some beamlet's phase can exceed 256 rad on the detector and bit 1 if the
+    row-pair scheme must fall back to direct evaluation (mixed only)."""
     _check(lib().gbd_project(_ptr(beamlets), int(n_beamlets), float(wavelength),
                              ctypes.byref(make_detector(detector)), int(precision), _ptr(coeffs),
                              _ptr(wide_flag), _stream(stream)))
 
 
-def gbd_field_set_shape(precision: int, rows: int, cols: int, splits: int = 0) -> None:
-    sh = gbd_shape(int(rows), int(cols), int(splits), 0.0)
+def gbd_field_set_shape(precision: int, rows: int, cols: int, splits: int = 0,
+                        scheme: int = GBD_SCHEME_DIRECT) -> None:
+    sh = gbd_shape(int(rows), int(cols), int(splits), 0.0, int(scheme))
     _check(lib().gbd_field_set_shape(int(precision), ctypes.byref(sh)))
 
 
@@ -300,22 +303,22 @@ def gbd_field_reset_shape(precision: int) -> None:
     _check(lib().gbd_field_set_shape(int(precision), None))
 
 
-def gbd_field_get_shape(precision: int, n_beamlets: int, detector) -> Tuple[int, int, int]:
+def gbd_field_get_shape(precision: int, n_beamlets: int, detector) -> Tuple[int, int, int, int]:
     sh = gbd_shape()
     _check(lib().gbd_field_get_shape(int(precision), int(n_beamlets),
                                      ctypes.byref(make_detector(detector)), ctypes.byref(sh)))
-    return sh.rows_per_thread, sh.cols_per_thread, sh.splits
+    return sh.rows_per_thread, sh.cols_per_thread, sh.splits, sh.scheme
 
 
 def gbd_autotune_field(beamlets, n_beamlets: int, wavelength: float, detector, precision: int,
-                       workspace, field_out, stream=None) -> Tuple[int, int, int, float]:
+                       workspace, field_out, stream=None) -> Tuple[int, int, int, float, int]:
     sh = gbd_shape()
     ws_bytes = workspace.numel() * workspace.element_size()
     _check(lib().gbd_autotune_field(_ptr(beamlets), int(n_beamlets), float(wavelength),
                                     ctypes.byref(make_detector(detector)), int(precision),
                                     _ptr(workspace), ctypes.c_size_t(ws_bytes), _ptr(field_out),
                                     _stream(stream), ctypes.byref(sh)))
-    return sh.rows_per_thread, sh.cols_per_thread, sh.splits, float(sh.ms)
+    return sh.rows_per_thread, sh.cols_per_thread, sh.splits, float(sh.ms), sh.scheme
 
 
 def gbd_probe_peaks() -> dict:
@@ -360,7 +363,7 @@ class SweepPlan:
         n, a, b, c = _instance_arrays(n_across, overlap_factor, waist_ratio)
         self.n = n
         self._plan = ctypes.c_void_p()
-        sh = gbd_shape(shape[0], shape[1], 1, 0.0) if shape else None
+        sh = gbd_shape(shape[0], shape[1], 1, 0.0, 0) if shape else None
         _check(lib().gbd_sweep_plan_create(ctypes.byref(make_system(system)), float(diameter), a, b,
                                            c, n, ctypes.byref(make_detector(detector)),
                                            ctypes.byref(sh) if sh else None,

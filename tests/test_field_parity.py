@@ -177,14 +177,53 @@ def test_every_shape_and_split_matches(prec):
     wl = small_cases()["tilted_zernike_small"]
     b = gpu_trace(wl)
     Eo = oracle.field(oracle.trace(wl.system, wl.pupil), wl.system, wl.detector)
-    shapes = ([(1, 4), (2, 2), (2, 4), (4, 2)] if prec == gbd.GBD_PREC_MIXED
-              else [(1, 2), (2, 2), (1, 8), (2, 8), (1, 16), (1, 32)])
+    D, P = gbd.GBD_SCHEME_DIRECT, gbd.GBD_SCHEME_ROW_PAIR
+    shapes = ([(1, 4, D), (2, 2, D), (2, 4, D), (4, 2, D), (2, 2, P), (2, 4, P)]
+              if prec == gbd.GBD_PREC_MIXED
+              else [(1, 2, D), (2, 2, D), (1, 8, D), (2, 8, D), (1, 16, D), (1, 32, D)])
     try:
-        for rows, cols in shapes:
+        for rows, cols, scheme in shapes:
             for splits in (1, 2, 5):
-                gbd.gbd_field_set_shape(prec, rows, cols, splits)
+                gbd.gbd_field_set_shape(prec, rows, cols, splits, scheme)
                 E = gpu_field(b, wl, prec)
-                assert rel_l2(E, Eo) <= TOL[prec], (rows, cols, splits)
+                assert rel_l2(E, Eo) <= TOL[prec], (rows, cols, splits, scheme)
+    finally:
+        gbd.gbd_field_reset_shape(prec)
+
+
+def projection_flags(b, wl):
+    import torch
+    n = b.shape[0]
+    coef = torch.empty(gbd.gbd_project_bytes(n, gbd.GBD_PREC_MIXED), dtype=torch.uint8,
+                       device="cuda")
+    flag = torch.zeros(1, dtype=torch.int32, device="cuda")
+    gbd.gbd_project(b, n, wl.system.wavelength, wl.detector, gbd.GBD_PREC_MIXED, coef, flag)
+    gbd.gbd_sync()
+    return int(flag.item())
+
+
+@pytest.mark.parametrize("name", list(small_cases()) + ["airy_large", "tilted_zernike"])
+def test_row_pair_scheme_is_not_flagged_on_the_workloads(name):
+    """The row-pair recurrence applies to every workload (no fallback to direct)."""
+    wl = small_cases()[name] if name in small_cases() else W.by_name(name)
+    assert projection_flags(gpu_trace(wl), wl) & 2 == 0
+
+
+@pytest.mark.parametrize("splits", (1, 3))
+def test_row_pair_scheme_falls_back_on_steep_beamlets(splits):
+    """Beamlets 2.5 pixels wide on a 96-pixel detector: the amplitude changes by more than
+    2^64 over 8 rows near the edges, the projection flags it, and the row-pair shape
+    evaluates directly instead; the field still matches the oracle."""
+    wl = W.Workload("steep", W.System(1e-6, 0.024, 0.024), W.Pupil(2.4e-3, 4, 1.0, 1.0),
+                    W.Detector(96, 96, 1e-5, 1e-5))
+    b = gpu_trace(wl)
+    assert projection_flags(b, wl) & 2
+    Eo = oracle.field(oracle.trace(wl.system, wl.pupil), wl.system, wl.detector)
+    prec = gbd.GBD_PREC_MIXED
+    try:
+        gbd.gbd_field_set_shape(prec, 2, 4, splits, gbd.GBD_SCHEME_ROW_PAIR)
+        E = gpu_field(b, wl, prec)
+        assert rel_l2(E, Eo) <= TOL[prec]
     finally:
         gbd.gbd_field_reset_shape(prec)
 
@@ -197,8 +236,8 @@ def test_autotune_then_parity():
     ws = torch.empty(64 << 20, dtype=torch.uint8, device="cuda")
     out = torch.empty((wl.detector.ny, wl.detector.nx), dtype=torch.complex64, device="cuda")
     try:
-        r, c, s, ms = gbd.gbd_autotune_field(b, b.shape[0], wl.system.wavelength, wl.detector,
-                                             prec, ws, out)
+        r, c, s, ms, scheme = gbd.gbd_autotune_field(b, b.shape[0], wl.system.wavelength,
+                                                     wl.detector, prec, ws, out)
         assert ms > 0 and s >= 1
         E = gpu_field(b, wl, prec)
         Eo = oracle.field(oracle.trace(wl.system, wl.pupil), wl.system, wl.detector)
