@@ -236,8 +236,9 @@ typedef struct {
     int32_t splits;            /* beamlet splits (0 = heuristic)             */
     float   ms;                /* measured time of the shape (autotune)      */
     int32_t scheme;            /* mixed only: GBD_SCHEME_DIRECT, or           */
-                               /* GBD_SCHEME_ROW_PAIR (2x2, 2x4: the second   */
-                               /* row from the first by a complex factor)     */
+                               /* GBD_SCHEME_ROW_PAIR (2x2, 2x4, 2x8: the     */
+                               /* second row from the first by a complex      */
+                               /* factor)                                     */
 } gbd_shape;
 
 #define GBD_SCHEME_DIRECT 0

@@ -103,6 +103,87 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
 }
 
+// Row pairs on 2 x CB pixels per thread with the compensation pairs in shared memory
+// (wider blocks amortise the per-beamlet row terms over more columns).  Dynamic shared
+// memory: the kStages record stages, then 2 CB x kThreads float4 (hi, lo) slots.
+template <int CB, bool WIDE>
+__global__ void __launch_bounds__(kThreads, 2)
+    field_mixed_pair_smem_kernel(const float4* __restrict__ coef, int n_tiles, int tiles_per_split,
+                                 int nx, int ny, double2* __restrict__ partial,
+                                 const unsigned* __restrict__ flags, unsigned mask, unsigned want,
+                                 uint32_t spins) {
+    if ((*flags & mask) != want) return;
+    constexpr int kTileF4 = gbd::kMixedFields * gbd::kTile;
+    extern __shared__ __align__(128) float4 dyn4[];
+    float4(*stage)[kTileF4] = reinterpret_cast<float4(*)[kTileF4]>(dyn4);
+    float4* comp = dyn4 + kStages * kTileF4;
+    __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
+    __shared__ int flag;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+    for (int m = 0; m < 2 * CB; ++m) comp[m * kThreads + tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int t0 = blockIdx.z * tiles_per_split;
+    gbd::init_stream_barriers(full, empty, tid);
+    gbd::TileStream<float4, kTileF4> ts{stage, full, empty, coef + (size_t)t0 * kTileF4,
+                                        min(n_tiles - t0, tiles_per_split), 0,
+                                        gbd::kMixedTileBytes, 0};
+    bool ok = ts.start(tid, spins, &flag);
+
+    const int col0 = blockIdx.x * (32 * CB) + lane;
+    const int row0 = blockIdx.y * 16 + warp;
+    float colf[CB];
+#pragma unroll
+    for (int c = 0; c < CB; ++c) colf[c] = (float)(col0 + 32 * c);
+    const float rowf = (float)row0;
+
+    float2 acc[2][CB];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int c = 0; c < CB; ++c) acc[r][c] = make_float2(0.f, 0.f);
+
+    int k = 0;
+    for (; ok && k < ts.nt; ++k) {
+        if (!ts.acquire(k, spins)) {
+            ok = false;
+            break;
+        }
+        gbd::mixed_tile_pair<CB, WIDE>(ts.tile(k), colf, rowf, acc);
+        gbd::mixed_fold_smem<2, CB>(acc, comp, tid);
+        if (!ts.release(k, lane, warp, spins)) {
+            ok = false;
+            ++k;
+            break;
+        }
+    }
+    if (!ok) {
+        record_timeout();
+        if (tid == 0) ts.drain(k, spins);
+        return;
+    }
+    const size_t npix = (size_t)nx * ny;
+    double2* out = partial + (size_t)blockIdx.z * npix;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int row = row0 + 8 * r;
+        if (row >= ny) continue;
+#pragma unroll
+        for (int c = 0; c < CB; ++c) {
+            const int col = col0 + 32 * c;
+            if (col >= nx) continue;
+            const float4 v = comp[(r * CB + c) * kThreads + tid];
+            out[(size_t)row * nx + col] = make_double2((double)v.x + (double)v.z,
+                                                       (double)v.y + (double)v.w);
+        }
+    }
+}
+
+template <int CB>
+constexpr size_t pair_smem_bytes() {
+    return (size_t)kStages * gbd::kMixedTileBytes + (size_t)2 * CB * kThreads * sizeof(float4);
+}
+
 template <int RB, int CB>
 __global__ void __launch_bounds__(kThreads)
     field_f64_kernel(const double2* __restrict__ coef, int n_tiles, int tiles_per_split, int nx,
@@ -411,6 +492,37 @@ cudaError_t launch_f64_row(const void* coeffs, int n_tiles, const gbd_project_pa
     return cudaGetLastError();
 }
 
+// Row pairs on 2 x CB pixels with shared-memory compensation; the direct 2 x 4 kernels (on
+// their own pixel grid, same splits) are the steep-beamlet fallback.
+template <int CB>
+cudaError_t launch_mixed_pair_smem(const void* coeffs, int n_tiles, const gbd_project_params& p,
+                                   const gbd_field_launch& L, double2* partial,
+                                   const unsigned* flags, uint32_t spins, cudaStream_t s) {
+    using gbd::kFlagSteep;
+    using gbd::kFlagWide;
+    constexpr unsigned kBoth = kFlagWide | kFlagSteep;
+    constexpr size_t smem = pair_smem_bytes<CB>();
+    cudaError_t e = cudaFuncSetAttribute(field_mixed_pair_smem_kernel<CB, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(field_mixed_pair_smem_kernel<CB, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((p.nx + 32 * CB - 1) / (32 * CB), (p.ny + 15) / 16, L.splits);
+    dim3 grid24((p.nx + 127) / 128, (p.ny + 15) / 16, L.splits);
+    const float4* c = static_cast<const float4*>(coeffs);
+    const int tps = L.tiles_per_split;
+    field_mixed_pair_smem_kernel<CB, false><<<grid, kThreads, smem, s>>>(
+        c, n_tiles, tps, p.nx, p.ny, partial, flags, kBoth, 0u, spins);
+    field_mixed_pair_smem_kernel<CB, true><<<grid, kThreads, smem, s>>>(
+        c, n_tiles, tps, p.nx, p.ny, partial, flags, kBoth, kFlagWide, spins);
+    field_mixed_kernel<2, 4, false, false><<<grid24, kThreads, 0, s>>>(
+        c, n_tiles, tps, p.nx, p.ny, partial, flags, kBoth, kFlagSteep, spins);
+    field_mixed_kernel<2, 4, true, false><<<grid24, kThreads, 0, s>>>(
+        c, n_tiles, tps, p.nx, p.ny, partial, flags, kBoth, kBoth, spins);
+    return cudaGetLastError();
+}
+
 typedef cudaError_t (*launch_fn)(const void*, int, const gbd_project_params&,
                                  const gbd_field_launch&, double2*, const unsigned*, uint32_t,
                                  cudaStream_t);
@@ -419,6 +531,7 @@ struct ShapeEntry {
     int rb, cb, scheme;
     launch_fn fn;
     const void* kernel;
+    size_t smem;  // dynamic shared memory of `kernel` (0: static only)
 };
 
 const ShapeEntry kMixedShapes[] = {
@@ -428,16 +541,19 @@ const ShapeEntry kMixedShapes[] = {
     {4, 2, GBD_SCHEME_DIRECT, launch_mixed<4, 2>, (const void*)field_mixed_kernel<4, 2, false, false>},
     {2, 2, GBD_SCHEME_ROW_PAIR, launch_mixed_pair<2>, (const void*)field_mixed_kernel<2, 2, false, true>},
     {2, 4, GBD_SCHEME_ROW_PAIR, launch_mixed_pair<4>, (const void*)field_mixed_kernel<2, 4, false, true>},
+    {2, 8, GBD_SCHEME_ROW_PAIR, launch_mixed_pair_smem<8>,
+     (const void*)field_mixed_pair_smem_kernel<8, false>, pair_smem_bytes<8>()},
 };
 // (1,2), (2,2): every pixel evaluated directly (columns 32 apart); (1,8), (1,16), (2,8),
 // (1,32): contiguous row segments advanced by complex multiplies.
+constexpr size_t kF64Smem = (size_t)kStages * gbd::kF64TileBytes;
 const ShapeEntry kF64Shapes[] = {
-    {1, 2, 0, launch_f64<1, 2>, (const void*)field_f64_kernel<1, 2>},
-    {2, 2, 0, launch_f64<2, 2>, (const void*)field_f64_kernel<2, 2>},
-    {1, 8, 0, launch_f64_row<1, 8>, (const void*)field_f64_row_kernel<1, 8>},
-    {2, 8, 0, launch_f64_row<2, 8>, (const void*)field_f64_row_kernel<2, 8>},
-    {1, 16, 0, launch_f64_row<1, 16>, (const void*)field_f64_row_kernel<1, 16>},
-    {1, 32, 0, launch_f64_row<1, 32>, (const void*)field_f64_row_kernel<1, 32>},
+    {1, 2, 0, launch_f64<1, 2>, (const void*)field_f64_kernel<1, 2>, kF64Smem},
+    {2, 2, 0, launch_f64<2, 2>, (const void*)field_f64_kernel<2, 2>, kF64Smem},
+    {1, 8, 0, launch_f64_row<1, 8>, (const void*)field_f64_row_kernel<1, 8>, kF64Smem},
+    {2, 8, 0, launch_f64_row<2, 8>, (const void*)field_f64_row_kernel<2, 8>, kF64Smem},
+    {1, 16, 0, launch_f64_row<1, 16>, (const void*)field_f64_row_kernel<1, 16>, kF64Smem},
+    {1, 32, 0, launch_f64_row<1, 32>, (const void*)field_f64_row_kernel<1, 32>, kF64Smem},
 };
 
 const ShapeEntry* find_shape(int precision, int rb, int cb, int scheme) {
@@ -461,8 +577,8 @@ int gbd_field_occupancy(int precision, int rb, int cb, int scheme) {
     const ShapeEntry* e = find_shape(precision, rb, cb, scheme);
     if (!e) return 0;
     int blocks = 0;
-    size_t smem = precision == GBD_PREC_MIXED ? 0 : (size_t)kStages * gbd::kF64TileBytes;
-    if (precision != GBD_PREC_MIXED)
+    const size_t smem = e->smem;
+    if (smem > 0)
         cudaFuncSetAttribute(e->kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, e->kernel, kThreads, smem) !=
         cudaSuccess)

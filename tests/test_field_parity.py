@@ -178,7 +178,7 @@ def test_every_shape_and_split_matches(prec):
     b = gpu_trace(wl)
     Eo = oracle.field(oracle.trace(wl.system, wl.pupil), wl.system, wl.detector)
     D, P = gbd.GBD_SCHEME_DIRECT, gbd.GBD_SCHEME_ROW_PAIR
-    shapes = ([(1, 4, D), (2, 2, D), (2, 4, D), (4, 2, D), (2, 2, P), (2, 4, P)]
+    shapes = ([(1, 4, D), (2, 2, D), (2, 4, D), (4, 2, D), (2, 2, P), (2, 4, P), (2, 8, P)]
               if prec == gbd.GBD_PREC_MIXED
               else [(1, 2, D), (2, 2, D), (1, 8, D), (2, 8, D), (1, 16, D), (1, 32, D)])
     try:
@@ -221,9 +221,10 @@ def test_row_pair_scheme_falls_back_on_steep_beamlets(splits):
     Eo = oracle.field(oracle.trace(wl.system, wl.pupil), wl.system, wl.detector)
     prec = gbd.GBD_PREC_MIXED
     try:
-        gbd.gbd_field_set_shape(prec, 2, 4, splits, gbd.GBD_SCHEME_ROW_PAIR)
-        E = gpu_field(b, wl, prec)
-        assert rel_l2(E, Eo) <= TOL[prec]
+        for cols in (4, 8):
+            gbd.gbd_field_set_shape(prec, 2, cols, splits, gbd.GBD_SCHEME_ROW_PAIR)
+            E = gpu_field(b, wl, prec)
+            assert rel_l2(E, Eo) <= TOL[prec], cols
     finally:
         gbd.gbd_field_reset_shape(prec)
 
