@@ -43,8 +43,8 @@ GB300_MAX_MHZ = 2070.0
 # DRAM bytes per launch of field_mixed_kernel<2,4,false> on airy_large from one ncu capture
 # (profiles/field_mixed_kernel_airy_large.md) at 26 beamlet splits.  The reads are the
 # record tiles; the writes are the split partial fields, which scale with the split count.
-FIELD_MIXED_NCU = {"kernel": "field_mixed_kernel<2, 4, false, true> (row pairs)",
-                   "read": 3.337472e6, "write": 181.91232e6, "splits": 58, "rows": 2, "cols": 4,
+FIELD_MIXED_NCU = {"kernel": "field_mixed_pair_smem_kernel<8, false> (2x8 row pairs)",
+                   "read": 3.415296e6, "write": 182.765824e6, "splits": 58, "rows": 2, "cols": 8,
                    "scheme": 1}
 
 
@@ -385,7 +385,10 @@ def run_ours(args, world, rank, local):
         sc = plan.scores.cpu().numpy()
         sweep = {"value": sv, "unit": UNIT, "ms_per_sweep": sweep_ms / args.sweep_steps,
                  "instances": plan.n, "beamlets": plan.beamlets, "evals_per_sweep": plan.evals,
-                 "work_items": plan.items, "frac_of_mufu_peak": sv / world / peak_evals_const(),
+                 "work_items": plan.items,
+                 "shape": "2x8 row pairs (library default)",
+                 "frac_of_mufu_peak": sv / world / (peak_evals_const() * 16.0 / 9.0),
+                 "frac_of_direct_scheme_mufu_peak": sv / world / peak_evals_const(),
                  "graph": True, "score_range": [float(sc.min()), float(sc.max())],
                  "workload": "1024 instances, airy_small optics, OF~U[1,3], WR~U[0.8,3], "
                              "N~U{16..256}, 256x256 pixels +-5 lambda F#"}
@@ -548,9 +551,9 @@ def run_ours(args, world, rank, local):
                "sample": f"{rows.size} of {det.ny} rows x {cols.size} columns x {r['nb']} beamlets "
                          f"({r['evals']:.3g} evals, {r['seconds']:.1f} s, FP64 C + OpenMP)"}
 
-    # trace, projection, field (the instantiation the wide-phase flag selects; the other
-    # returns at once), split reduction
-    launches_per_step = 5
+    # trace, projection, field (the instantiation the flag word selects; the others return
+    # at once: one for the direct scheme, three for row pairs), split reduction
+    launches_per_step = 3 + (4 if tuned[4] else 2)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,

@@ -57,18 +57,22 @@ __global__ void __launch_bounds__(256) airy_table_kernel(int nx, int ny, double 
     out[p] = make_double2(a, (double)mask);
 }
 
-// WIDE: as in field_mixed_kernel, both instantiations are launched and the projection's
-// wide-phase flag selects the one that works.
-template <int RB, int CB, bool WIDE>
+// WIDE, PAIR: as in field_mixed_kernel (several instantiations are launched; each returns
+// at once unless the projection's flag word masked by `mask` equals `want`).  SMEM keeps
+// the compensation pairs in dynamic shared memory after the record stages (2 x 8 blocks).
+template <int RB, int CB, bool WIDE, bool PAIR, bool SMEM>
 __global__ void __launch_bounds__(kThreads, 2)
     sweep_kernel(const float4* __restrict__ coef, const int2* __restrict__ inst_tiles,
                  const int2* __restrict__ items, int n_items, int tiles_x, int n_blocks, int nx,
                  int ny, const double2* __restrict__ airy, int n_regions,
                  double* __restrict__ moments, int* __restrict__ counter,
-                 const unsigned* __restrict__ wide, uint32_t spins) {
-    if (((*wide & gbd::kFlagWide) != 0u) != WIDE) return;
+                 const unsigned* __restrict__ flags, unsigned mask, unsigned want, uint32_t spins) {
+    static_assert(!PAIR || RB == 2, "row pairs need two rows per thread");
+    if ((*flags & mask) != want) return;
     constexpr int kTileF4 = gbd::kMixedFields * gbd::kTile;
-    __shared__ __align__(128) float4 stage[kStages][kTileF4];
+    extern __shared__ __align__(128) float4 sweep_dyn[];
+    float4(*stage)[kTileF4] = reinterpret_cast<float4(*)[kTileF4]>(sweep_dyn);
+    float4* comp = sweep_dyn + kStages * kTileF4;  // SMEM: [RB * CB][kThreads]
     __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
     __shared__ int flag, s_item;
     __shared__ double red[kWarps][kMaxRegions][4];
@@ -100,7 +104,10 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
         for (int r = 0; r < RB; ++r)
 #pragma unroll
-            for (int c = 0; c < CB; ++c) acc[r][c] = hi[r][c] = lo[r][c] = make_float2(0.f, 0.f);
+            for (int c = 0; c < CB; ++c) {
+                acc[r][c] = hi[r][c] = lo[r][c] = make_float2(0.f, 0.f);
+                if constexpr (SMEM) comp[(r * CB + c) * kThreads + tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
 
         int k = 0;
         for (; ok && k < ts.nt; ++k) {
@@ -108,8 +115,14 @@ __global__ void __launch_bounds__(kThreads, 2)
                 ok = false;
                 break;
             }
-            gbd::mixed_tile<RB, CB, WIDE>(ts.tile(k), colf, rowf, acc);
-            gbd::mixed_fold<RB, CB>(acc, hi, lo);
+            if constexpr (PAIR)
+                gbd::mixed_tile_pair<CB, WIDE>(ts.tile(k), colf, rowf[0], acc);
+            else
+                gbd::mixed_tile<RB, CB, WIDE>(ts.tile(k), colf, rowf, acc);
+            if constexpr (SMEM)
+                gbd::mixed_fold_smem<RB, CB>(acc, comp, tid);
+            else
+                gbd::mixed_fold<RB, CB>(acc, hi, lo);
             if (!ts.release(k, lane, warp, spins)) {
                 ok = false;
                 ++k;
@@ -125,27 +138,26 @@ __global__ void __launch_bounds__(kThreads, 2)
         }
         g += ts.nt;
 
-        // epilogue: |E| per pixel, then per region the moments of this item's pixels
-        double mag[RB][CB], amp[RB][CB];
-        unsigned msk[RB][CB];
+        // epilogue: per region the moments of this item's pixels; |E| is recomputed per
+        // region rather than kept, which holds the wide blocks' register use down
+        auto mag_of = [&](int r, int c) -> double {
+            double re, im;
+            if constexpr (SMEM) {
+                const float4 v = comp[(r * CB + c) * kThreads + tid];
+                re = (double)v.x + (double)v.z;
+                im = (double)v.y + (double)v.w;
+            } else {
+                re = (double)hi[r][c].x + (double)lo[r][c].x;
+                im = (double)hi[r][c].y + (double)lo[r][c].y;
+            }
+            return sqrt(re * re + im * im);
+        };
         double e0 = -1.0;
 #pragma unroll
         for (int r = 0; r < RB; ++r)
 #pragma unroll
-            for (int c = 0; c < CB; ++c) {
-                const int row = row0 + 8 * r, col = col0 + 32 * c;
-                const double re = (double)hi[r][c].x + (double)lo[r][c].x;
-                const double im = (double)hi[r][c].y + (double)lo[r][c].y;
-                mag[r][c] = sqrt(re * re + im * im);
-                amp[r][c] = 0.0;
-                msk[r][c] = 0u;
-                if (row < ny && col < nx) {
-                    const double2 A = airy[(size_t)row * nx + col];
-                    amp[r][c] = A.x;
-                    msk[r][c] = (unsigned)A.y;
-                    if (row == ny / 2 && col == nx / 2) e0 = mag[r][c];
-                }
-            }
+            for (int c = 0; c < CB; ++c)
+                if (row0 + 8 * r == ny / 2 && col0 + 32 * c == nx / 2) e0 = mag_of(r, c);
         for (int o = 16; o > 0; o >>= 1) e0 = fmax(e0, __shfl_xor_sync(0xffffffffu, e0, o));
         if (lane == 0) red_e0[warp] = e0;
         for (int z = 0; z < n_regions; ++z) {
@@ -153,13 +165,17 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
             for (int r = 0; r < RB; ++r)
 #pragma unroll
-                for (int c = 0; c < CB; ++c)
-                    if (msk[r][c] & (1u << z)) {
-                        m0 += mag[r][c] * mag[r][c];
-                        m1 += mag[r][c] * amp[r][c];
-                        m2 += amp[r][c] * amp[r][c];
-                        m3 += 1.0;
-                    }
+                for (int c = 0; c < CB; ++c) {
+                    const int row = row0 + 8 * r, col = col0 + 32 * c;
+                    if (row >= ny || col >= nx) continue;
+                    const double2 A = airy[(size_t)row * nx + col];
+                    if (!((unsigned)A.y & (1u << z))) continue;
+                    const double mg = mag_of(r, c);
+                    m0 += mg * mg;
+                    m1 += mg * A.x;
+                    m2 += A.x * A.x;
+                    m3 += 1.0;
+                }
             for (int o = 16; o > 0; o >>= 1) {
                 m0 += __shfl_xor_sync(0xffffffffu, m0, o);
                 m1 += __shfl_xor_sync(0xffffffffu, m1, o);
@@ -219,36 +235,98 @@ typedef cudaError_t (*sweep_launch_fn)(dim3, cudaStream_t, const float4*, const 
                                        int, int, int, int, int, const double2*, int, double*, int*,
                                        const unsigned*, uint32_t);
 
+constexpr size_t sweep_smem(int rb, int cb, bool smem) {
+    return (size_t)kStages * gbd::kMixedTileBytes +
+           (smem ? (size_t)rb * cb * kThreads * sizeof(float4) : 0);
+}
+
+template <int RB, int CB, bool WIDE, bool PAIR, bool SMEM>
+cudaError_t launch_one(dim3 grid, cudaStream_t s, const float4* coef, const int2* it_tiles,
+                       const int2* items, int n_items, int tiles_x, int n_blocks, int nx, int ny,
+                       const double2* airy, int n_regions, double* moments, int* counter,
+                       const unsigned* flags, unsigned mask, unsigned want, uint32_t spins) {
+    constexpr size_t smem = sweep_smem(RB, CB, SMEM);
+    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<RB, CB, WIDE, PAIR, SMEM>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    sweep_kernel<RB, CB, WIDE, PAIR, SMEM><<<grid, kThreads, smem, s>>>(
+        coef, it_tiles, items, n_items, tiles_x, n_blocks, nx, ny, airy, n_regions, moments,
+        counter, flags, mask, want, spins);
+    return cudaGetLastError();
+}
+
+// Direct evaluation: the narrow- and wide-phase instantiations.
 template <int RB, int CB>
 cudaError_t launch_sweep(dim3 grid, cudaStream_t s, const float4* coef, const int2* it_tiles,
                          const int2* items, int n_items, int tiles_x, int n_blocks, int nx, int ny,
                          const double2* airy, int n_regions, double* moments, int* counter,
-                         const unsigned* wide, uint32_t spins) {
-    sweep_kernel<RB, CB, false><<<grid, kThreads, 0, s>>>(coef, it_tiles, items, n_items, tiles_x,
-                                                          n_blocks, nx, ny, airy, n_regions,
-                                                          moments, counter, wide, spins);
-    sweep_kernel<RB, CB, true><<<grid, kThreads, 0, s>>>(coef, it_tiles, items, n_items, tiles_x,
-                                                         n_blocks, nx, ny, airy, n_regions,
-                                                         moments, counter, wide, spins);
-    return cudaGetLastError();
+                         const unsigned* flags, uint32_t spins) {
+    using gbd::kFlagWide;
+    cudaError_t e = launch_one<RB, CB, false, false, false>(
+        grid, s, coef, it_tiles, items, n_items, tiles_x, n_blocks, nx, ny, airy, n_regions,
+        moments, counter, flags, kFlagWide, 0u, spins);
+    if (e == cudaSuccess)
+        e = launch_one<RB, CB, true, false, false>(grid, s, coef, it_tiles, items, n_items, tiles_x,
+                                                   n_blocks, nx, ny, airy, n_regions, moments,
+                                                   counter, flags, kFlagWide, kFlagWide, spins);
+    return e;
+}
+
+// Row pairs on 2 x CB pixels, with direct evaluation on the same pixel blocks as the
+// fallback for steep beamlets; SMEM for the 2 x 8 blocks.
+template <int CB>
+cudaError_t launch_sweep_pair(dim3 grid, cudaStream_t s, const float4* coef, const int2* it_tiles,
+                              const int2* items, int n_items, int tiles_x, int n_blocks, int nx,
+                              int ny, const double2* airy, int n_regions, double* moments,
+                              int* counter, const unsigned* flags, uint32_t spins) {
+    using gbd::kFlagSteep;
+    using gbd::kFlagWide;
+    constexpr unsigned kBoth = kFlagWide | kFlagSteep;
+    constexpr bool kSmem = CB >= 8;
+    cudaError_t e = launch_one<2, CB, false, true, kSmem>(
+        grid, s, coef, it_tiles, items, n_items, tiles_x, n_blocks, nx, ny, airy, n_regions,
+        moments, counter, flags, kBoth, 0u, spins);
+    if (e == cudaSuccess)
+        e = launch_one<2, CB, true, true, kSmem>(grid, s, coef, it_tiles, items, n_items, tiles_x,
+                                                 n_blocks, nx, ny, airy, n_regions, moments,
+                                                 counter, flags, kBoth, kFlagWide, spins);
+    if (e == cudaSuccess)
+        e = launch_one<2, CB, false, false, kSmem>(grid, s, coef, it_tiles, items, n_items,
+                                                   tiles_x, n_blocks, nx, ny, airy, n_regions,
+                                                   moments, counter, flags, kBoth, kFlagSteep,
+                                                   spins);
+    if (e == cudaSuccess)
+        e = launch_one<2, CB, true, false, kSmem>(grid, s, coef, it_tiles, items, n_items, tiles_x,
+                                                  n_blocks, nx, ny, airy, n_regions, moments,
+                                                  counter, flags, kBoth, kBoth, spins);
+    return e;
 }
 
 struct SweepShape {
-    int rb, cb;
+    int rb, cb, scheme;
     sweep_launch_fn fn;
     const void* kernel;
+    size_t smem;
 };
 
 const SweepShape kSweepShapes[] = {
-    {1, 4, launch_sweep<1, 4>, (const void*)sweep_kernel<1, 4, false>},
-    {2, 2, launch_sweep<2, 2>, (const void*)sweep_kernel<2, 2, false>},
-    {2, 4, launch_sweep<2, 4>, (const void*)sweep_kernel<2, 4, false>},
-    {4, 2, launch_sweep<4, 2>, (const void*)sweep_kernel<4, 2, false>},
+    {1, 4, GBD_SCHEME_DIRECT, launch_sweep<1, 4>, (const void*)sweep_kernel<1, 4, false, false, false>,
+     sweep_smem(1, 4, false)},
+    {2, 2, GBD_SCHEME_DIRECT, launch_sweep<2, 2>, (const void*)sweep_kernel<2, 2, false, false, false>,
+     sweep_smem(2, 2, false)},
+    {2, 4, GBD_SCHEME_DIRECT, launch_sweep<2, 4>, (const void*)sweep_kernel<2, 4, false, false, false>,
+     sweep_smem(2, 4, false)},
+    {4, 2, GBD_SCHEME_DIRECT, launch_sweep<4, 2>, (const void*)sweep_kernel<4, 2, false, false, false>,
+     sweep_smem(4, 2, false)},
+    {2, 4, GBD_SCHEME_ROW_PAIR, launch_sweep_pair<4>,
+     (const void*)sweep_kernel<2, 4, false, true, false>, sweep_smem(2, 4, false)},
+    {2, 8, GBD_SCHEME_ROW_PAIR, launch_sweep_pair<8>,
+     (const void*)sweep_kernel<2, 8, false, true, true>, sweep_smem(2, 8, true)},
 };
 
-const SweepShape* find_sweep_shape(int rb, int cb) {
+const SweepShape* find_sweep_shape(int rb, int cb, int scheme) {
     for (const auto& e : kSweepShapes)
-        if (e.rb == rb && e.cb == cb) return &e;
+        if (e.rb == rb && e.cb == cb && e.scheme == scheme) return &e;
     return nullptr;
 }
 
@@ -263,7 +341,7 @@ struct gbd_sweep_plan {
     gbd_project_params pp;
     double lam_fnum, r3;
     Regions regions;
-    int n_inst, max_n, rb, cb, tiles_x, tiles_y, n_blocks, n_items;
+    int n_inst, max_n, rb, cb, scheme, tiles_x, tiles_y, n_blocks, n_items;
     int64_t total_tiles, total_beamlets;
     double evals;
     std::vector<gbd_instance_dev> inst;
@@ -287,9 +365,11 @@ unsigned gbd_sweep_status_read_clear() {
 }
 
 static gbd_status sweep_enqueue(gbd_sweep_plan* P, double* scores, cudaStream_t s) {
-    const SweepShape* sh = find_sweep_shape(P->rb, P->cb);
+    const SweepShape* sh = find_sweep_shape(P->rb, P->cb, P->scheme);
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sh->kernel, kThreads, 0) != cudaSuccess ||
+    cudaFuncSetAttribute(sh->kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh->smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sh->kernel, kThreads, sh->smem) !=
+            cudaSuccess ||
         occ < 1)
         occ = 1;
     char* w = P->ws;
@@ -364,8 +444,10 @@ gbd_status gbd_sweep_plan_create(const gbd_system* system, double diameter, cons
         return gbd_set_error(GBD_EINVAL, "instance arrays are NULL");
     if (isinf(system->focal_length))
         return gbd_set_error(GBD_EINVAL, "the Airy score needs a lens (finite focal length)");
-    const int rb = shape ? shape->rows_per_thread : 2, cb = shape ? shape->cols_per_thread : 4;
-    if (!find_sweep_shape(rb, cb)) return gbd_set_error(GBD_EINVAL, "unsupported sweep shape");
+    const int rb = shape ? shape->rows_per_thread : 2, cb = shape ? shape->cols_per_thread : 8;
+    const int scheme = shape ? shape->scheme : GBD_SCHEME_ROW_PAIR;
+    if (!find_sweep_shape(rb, cb, scheme))
+        return gbd_set_error(GBD_EINVAL, "unsupported sweep shape");
     gbd_sweep_plan* P = new gbd_sweep_plan();
     P->tp = gbd_make_trace_params(system, diameter);
     P->pp = gbd_make_project_params(system->wavelength, detector);
@@ -377,6 +459,7 @@ gbd_status gbd_sweep_plan_create(const gbd_system* system, double diameter, cons
     P->n_inst = n_instances;
     P->rb = rb;
     P->cb = cb;
+    P->scheme = scheme;
     P->tiles_x = (detector->nx + 32 * cb - 1) / (32 * cb);
     P->tiles_y = (detector->ny + 8 * rb - 1) / (8 * rb);
     P->n_blocks = P->tiles_x * P->tiles_y;
@@ -571,10 +654,10 @@ extern "C" gbd_status gbd_sweep_autotune(const gbd_system* system, double diamet
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return gbd_set_error(GBD_ECUDA, "autotune events");
-    gbd_shape win{0, 0, 1, 1e30f};
+    gbd_shape win{0, 0, 1, 1e30f, 0};
     gbd_status st = GBD_OK;
     for (const auto& sh : kSweepShapes) {
-        gbd_shape cand{sh.rb, sh.cb, 1, 0.f};
+        gbd_shape cand{sh.rb, sh.cb, 1, 0.f, sh.scheme};
         gbd_sweep_plan* P = nullptr;
         st = gbd_sweep_plan_create(system, diameter, n_across, overlap_factor, waist_ratio,
                                    n_instances, detector, &cand, &P);

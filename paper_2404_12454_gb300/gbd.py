@@ -357,13 +357,16 @@ class SweepPlan:
     run() returns the Airy scores as a float64 CUDA tensor."""
 
     def __init__(self, system, diameter, n_across, overlap_factor, waist_ratio, detector,
-                 shape: Optional[Tuple[int, int]] = None, stream=None, device="cuda",
+                 shape: Optional[Tuple[int, ...]] = None, stream=None, device="cuda",
                  zones: Optional[Sequence[Tuple[float, float]]] = None):
+        """shape: (rows, cols[, scheme]) per thread; None = the library's default
+        (2 x 8 row pairs)."""
         import torch
         n, a, b, c = _instance_arrays(n_across, overlap_factor, waist_ratio)
         self.n = n
         self._plan = ctypes.c_void_p()
-        sh = gbd_shape(shape[0], shape[1], 1, 0.0, 0) if shape else None
+        sh = (gbd_shape(shape[0], shape[1], 1, 0.0, shape[2] if len(shape) > 2 else 0)
+              if shape else None)
         _check(lib().gbd_sweep_plan_create(ctypes.byref(make_system(system)), float(diameter), a, b,
                                            c, n, ctypes.byref(make_detector(detector)),
                                            ctypes.byref(sh) if sh else None,
@@ -409,14 +412,14 @@ def sweep_plan(sw, shape=None, stream=None, zones=None) -> SweepPlan:
 
 
 def gbd_sweep_autotune(system, diameter, n_across, overlap_factor, waist_ratio, detector,
-                       workspace, scores, stream=None) -> Tuple[int, int, float]:
+                       workspace, scores, stream=None) -> Tuple[int, int, float, int]:
     n, a, b, c = _instance_arrays(n_across, overlap_factor, waist_ratio)
     sh = gbd_shape()
     _check(lib().gbd_sweep_autotune(ctypes.byref(make_system(system)), float(diameter), a, b, c, n,
                                     ctypes.byref(make_detector(detector)), _ptr(workspace),
                                     ctypes.c_size_t(workspace.numel()), _ptr(scores),
                                     _stream(stream), ctypes.byref(sh)))
-    return sh.rows_per_thread, sh.cols_per_thread, float(sh.ms)
+    return sh.rows_per_thread, sh.cols_per_thread, float(sh.ms), sh.scheme
 
 
 def gbd_field_point_workspace_bytes(n_beamlets: int, detector) -> int:

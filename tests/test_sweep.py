@@ -72,7 +72,8 @@ def test_sweep_deterministic_graph_and_shapes():
     s.synchronize()
     gbd.gbd_sync()
     assert torch.equal(a, b) and torch.equal(a, c) and torch.equal(c, d)
-    for shape in ((1, 4), (2, 2), (4, 2)):
+    for shape in ((1, 4), (2, 2), (2, 4), (4, 2), (2, 4, gbd.GBD_SCHEME_ROW_PAIR),
+                  (2, 8, gbd.GBD_SCHEME_ROW_PAIR)):
         p2 = gbd.sweep_plan(sw, shape=shape)
         e = p2.run().clone()
         gbd.gbd_sync()
@@ -80,11 +81,12 @@ def test_sweep_deterministic_graph_and_shapes():
 
 
 def test_full_sweep_seeded_subset_matches_oracle():
-    """The 1024-instance sweep in one persistent launch; 16 seeded instances re-scored by
-    the oracle (chosen across every beamlet count, at most one of 256 across)."""
+    """The 1024-instance sweep in one persistent launch (default shape: 2 x 8 row pairs);
+    16 seeded instances re-scored by the oracle (chosen across every beamlet count, at
+    most one of 256 across)."""
     sw = W.sweep()
     plan = gbd.sweep_plan(sw)
-    assert plan.n == 1024 and plan.items == 1024 * 32
+    assert plan.n == 1024 and plan.items == 1024 * 16  # default blocks: 256 x 16 pixels
     got = plan.run().cpu().numpy()
     gbd.gbd_sync()
     assert np.all(np.isfinite(got))
@@ -101,12 +103,14 @@ def test_full_sweep_seeded_subset_matches_oracle():
 def test_sweep_autotune_picks_a_supported_shape():
     import torch
     sw = W.sweep_subset(W.sweep(), list(range(24)))
-    probe = gbd.sweep_plan(sw, shape=(1, 4))
+    probe = gbd.sweep_plan(sw, shape=(2, 8, gbd.GBD_SCHEME_ROW_PAIR))
     ws = torch.empty(probe.bytes * 2, dtype=torch.uint8, device="cuda")
     scores = torch.empty(sw.n_instances, dtype=torch.float64, device="cuda")
-    r, c, ms = gbd.gbd_sweep_autotune(sw.system, sw.diameter, sw.n_across, sw.overlap_factor,
-                                      sw.waist_ratio, sw.detector, ws, scores)
-    assert (r, c) in ((1, 4), (2, 2), (2, 4), (4, 2)) and ms > 0
+    r, c, ms, scheme = gbd.gbd_sweep_autotune(sw.system, sw.diameter, sw.n_across,
+                                              sw.overlap_factor, sw.waist_ratio, sw.detector,
+                                              ws, scores)
+    assert (r, c, scheme) in ((1, 4, 0), (2, 2, 0), (2, 4, 0), (4, 2, 0), (2, 4, 1),
+                              (2, 8, 1)) and ms > 0
 
 
 def test_sweep_rejects_bad_instances():
@@ -157,3 +161,16 @@ def test_zone_scores_match_oracle():
     # the plain score column equals a plan without zones
     plain = gbd.sweep_plan(sw).run().cpu().numpy()
     assert np.array_equal(plain, got[:, 0])
+
+
+def test_sweep_row_pairs_fall_back_on_steep_beamlets():
+    """Beamlets 2.5 pixels wide on a coarse 96-pixel detector: the projection flags them as
+    too steep for the row-pair recurrence and the default (row-pair) plan evaluates them
+    directly; scores match the oracle's."""
+    system, D, _ = W.sweep_optics()
+    det = W.Detector(96, 96, 1e-5, 1e-5)
+    sw = W.Sweep(system, D, det, (4, 6), (1.0, 1.2), (1.0, 1.5))
+    got = gbd.sweep_plan(sw).run().cpu().numpy()
+    gbd.gbd_sync()
+    want = oracle_scores(sw, range(sw.n_instances))
+    assert np.max(np.abs(got - want)) <= SCORE_TOL, (got, want)
