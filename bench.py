@@ -526,7 +526,9 @@ def run_ours(args, world, rank, local):
         "peak_source": (f"derived: {GB300_SMS} SMs x {GB300_MAX_MHZ:g} MHz / ((1/{MUFU_EX2_PER_CLK_SM}"
                         f" + 2/{MUFU_SINCOS_PER_CLK_SM}) clk per exact evaluation x "
                         f"{exact_per_eval:.4g})"),
-        "kernel": "field_mixed_kernel", "kernel_ms_avg": k_avg_s * 1e3, "launches": kn,
+        "kernel": ("field_mixed_pair_smem_kernel" if tuned[4] and tuned[1] >= 8
+                   else "field_mixed_kernel") + f" ({tuned[0]}x{tuned[1]}, {tuned[2]} splits)",
+        "kernel_ms_avg": k_avg_s * 1e3, "launches": kn,
         "mufu_gops": 3.0 * exact_per_eval * achieved / 1e9,
         "direct_scheme_peak": peak_direct / 1e9,
         "frac_of_direct_scheme_peak": achieved / peak_direct,

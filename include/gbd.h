@@ -225,10 +225,11 @@ gbd_status gbd_field_point(const gbd_beamlet* beamlets, int32_t n_beamlets, doub
                            void* field_out, void* stream);
 
 /* ---------------------------------------------------------------- tuning ----------
- * Launch shape of the field kernels: pixels per thread (rows x cols), beamlet splits.
- * gbd_field picks a shape from a built-in heuristic unless one was set for the current
- * device with gbd_field_set_shape; gbd_autotune_field times the candidate shapes on the
- * given problem (synchronously, with CUDA events) and keeps the fastest. */
+ * Launch shape of the field kernels: pixels per thread (rows x cols), beamlet splits and
+ * (mixed) evaluation scheme.  Unless a shape was set for the current device with
+ * gbd_field_set_shape, gbd_field uses 2x8 row pairs (mixed) or 1x16 row segments (F64)
+ * with splits from a built-in heuristic; gbd_autotune_field times the candidate shapes
+ * on the given problem (synchronously, with CUDA events) and keeps the fastest. */
 typedef struct {
     int32_t rows_per_thread;   /* mixed: 1x4, 2x2, 2x4, 4x2 (columns 32 apart);   */
     int32_t cols_per_thread;   /* F64: 1x2, 2x2 (direct), 1x8, 2x8, 1x16, 1x32   */
@@ -288,11 +289,12 @@ gbd_status gbd_psf(const gbd_system* system, const gbd_pupil* pupil, double over
                    void* workspace, size_t workspace_bytes, void* host_field_out, void* stream);
 
 /* ---------------------------------------------------------------- timing ----------
- * Measurement hooks.  While enabled, every launch of the per-beamlet projection, the
- * field kernels and the split reduction is bracketed by CUDA events on its stream.
- * gbd_timing_read synchronises those events, returns per kind the summed milliseconds and
- * launch counts (index 0 mixed field kernel, 1 FP64 field kernel, 2 projection,
- * 3 reduction, 4 point evaluation; arrays of 5) and forgets them. */
+ * Measurement hooks.  While enabled, every launch of the traces, the per-beamlet
+ * projection, the field kernels and the split reduction is bracketed by CUDA events on its
+ * stream.  gbd_timing_read synchronises those events, returns per kind the summed
+ * milliseconds and launch counts (index 0 mixed field kernel, 1 FP64 field kernel,
+ * 2 projection, 3 reduction, 4 point evaluation, 5 trace (gbd_trace, gbd_trace_mirrors);
+ * arrays of 6) and forgets them. */
 gbd_status gbd_timing_enable(int32_t on);
 gbd_status gbd_timing_read(double* total_ms, int64_t* launches);
 

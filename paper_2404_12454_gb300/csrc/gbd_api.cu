@@ -66,7 +66,15 @@ bool finite_pos(double v) { return isfinite(v) && v > 0.0; }
 // ------------------------------------------------------------- kernel timing --
 // While enabled, launches of the measured kernels are bracketed by CUDA events on their
 // own stream; gbd_timing_read synchronises the events and sums the durations.
-enum { kTimeMixed = 0, kTimeF64 = 1, kTimeProject = 2, kTimeReduce = 3, kTimePoint = 4, kTimeKinds = 5 };
+enum {
+    kTimeMixed = 0,
+    kTimeF64 = 1,
+    kTimeProject = 2,
+    kTimeReduce = 3,
+    kTimePoint = 4,
+    kTimeTrace = 5,
+    kTimeKinds = 6
+};
 struct TimedLaunch {
     int kind;
     cudaEvent_t a, b;
@@ -195,6 +203,9 @@ gbd_project_params project_params(double wavelength, const gbd_detector* D) {
     p.py = D->pitch_y;
     p.nx = D->nx;
     p.ny = D->ny;
+    p.inv_wavelength = 1.0 / wavelength;
+    p.inv_px = 1.0 / D->pitch_x;
+    p.inv_py = 1.0 / D->pitch_y;
     return p;
 }
 
@@ -209,10 +220,10 @@ size_t tile_bytes(int precision) {
 gbd_shape default_shape(int precision) {
     gbd_shape s;
     s.rows_per_thread = precision == GBD_PREC_MIXED ? 2 : 1;
-    s.cols_per_thread = precision == GBD_PREC_MIXED ? 4 : 16;
+    s.cols_per_thread = precision == GBD_PREC_MIXED ? 8 : 16;
     s.splits = 0;
     s.ms = 0.f;
-    s.scheme = GBD_SCHEME_DIRECT;
+    s.scheme = precision == GBD_PREC_MIXED ? GBD_SCHEME_ROW_PAIR : GBD_SCHEME_DIRECT;
     return s;
 }
 
@@ -439,8 +450,11 @@ gbd_status gbd_trace(const gbd_system* system, const gbd_pupil* pupil, double ov
     p.overlap_factor = overlap_factor;
     p.waist_ratio = waist_ratio;
     p.n_across = pupil->n_across;
-    cudaError_t e = gbd_launch_trace(p, 1, pupil->n_across, nullptr, out,
-                                     static_cast<cudaStream_t>(stream));
+    cudaError_t e;
+    {
+        TimingScope ts(kTimeTrace, static_cast<cudaStream_t>(stream));
+        e = gbd_launch_trace(p, 1, pupil->n_across, nullptr, out, static_cast<cudaStream_t>(stream));
+    }
     if (e != cudaSuccess) return cuda_fail(e, "gbd_trace launch");
     return GBD_OK;
 }
@@ -487,7 +501,11 @@ gbd_status gbd_trace_mirrors(const gbd_mirror_system* system, const gbd_pupil* p
     m.diameter = pupil->diameter;
     m.overlap_factor = overlap_factor;
     m.waist_ratio = waist_ratio;
-    cudaError_t e = gbd_launch_trace_mirrors(m, out, static_cast<cudaStream_t>(stream));
+    cudaError_t e;
+    {
+        TimingScope ts(kTimeTrace, static_cast<cudaStream_t>(stream));
+        e = gbd_launch_trace_mirrors(m, out, static_cast<cudaStream_t>(stream));
+    }
     return e == cudaSuccess ? GBD_OK : cuda_fail(e, "gbd_trace_mirrors launch");
 }
 

@@ -176,6 +176,7 @@ struct gbd_project_params {
     double n[2];       // detector (s_x, s_y) -> lab axial offset z
     double px, py;
     int32_t nx, ny;
+    double inv_wavelength, inv_px, inv_py;  // reciprocals (FP64 division is slow here)
 };
 
 struct gbd_field_launch {

@@ -137,10 +137,11 @@ __device__ void trace_one(const Tracer& T, double D, double lambda, int N, doubl
                           int i, int j, gbd_beamlet* out) {
     const double s = D / N;
     const double w0 = OF * D / (2.0 * N);
-    const double weight = s * s / (M_PI * w0 * w0);
+    const double ipw = 1.0 / (M_PI * w0);  // shared by the three quotients below
+    const double weight = s * s * ipw / w0;
     const double h = WR * w0;
-    const double dth = WR * lambda / (M_PI * w0);
-    const double p1 = -lambda / (M_PI * w0 * w0);  // P1 = i * p1 * I
+    const double dth = WR * lambda * ipw;
+    const double p1 = -lambda * ipw / w0;  // P1 = i * p1 * I
     const double cx = (i - 0.5 * (N - 1)) * s, cy = (j - 0.5 * (N - 1)) * s;
 
     Ray c{cx, cy, 0.0, 0.0, 0.0};
@@ -151,12 +152,15 @@ __device__ void trace_one(const Tracer& T, double D, double lambda, int N, doubl
     T(wy);
     T(dx);
     T(dy);
-    // columns: derivative of (x, y, tx, ty) with respect to (x0, y0 | tx0, ty0)
-    double A[4] = {(wx.x - c.x) / h, (wy.x - c.x) / h, (wx.y - c.y) / h, (wy.y - c.y) / h};
-    double C[4] = {(wx.tx - c.tx) / h, (wy.tx - c.tx) / h, (wx.ty - c.ty) / h, (wy.ty - c.ty) / h};
-    double B[4] = {(dx.x - c.x) / dth, (dy.x - c.x) / dth, (dx.y - c.y) / dth, (dy.y - c.y) / dth};
-    double Dm[4] = {(dx.tx - c.tx) / dth, (dy.tx - c.tx) / dth, (dx.ty - c.ty) / dth,
-                    (dy.ty - c.ty) / dth};
+    // columns: derivative of (x, y, tx, ty) with respect to (x0, y0 | tx0, ty0); one
+    // reciprocal per step instead of 16 FP64 divisions (the difference is within an ulp)
+    const double ih = 1.0 / h, idt = 1.0 / dth;
+    double A[4] = {(wx.x - c.x) * ih, (wy.x - c.x) * ih, (wx.y - c.y) * ih, (wy.y - c.y) * ih};
+    double C[4] = {(wx.tx - c.tx) * ih, (wy.tx - c.tx) * ih, (wx.ty - c.ty) * ih,
+                   (wy.ty - c.ty) * ih};
+    double B[4] = {(dx.x - c.x) * idt, (dy.x - c.x) * idt, (dx.y - c.y) * idt, (dy.y - c.y) * idt};
+    double Dm[4] = {(dx.tx - c.tx) * idt, (dy.tx - c.tx) * idt, (dx.ty - c.ty) * idt,
+                    (dy.ty - c.ty) * idt};
 
     // M = A + B P1, N = C + D P1 (P1 purely imaginary, isotropic)
     cd M[4], Nn[4];
@@ -290,10 +294,11 @@ __device__ Quad project_one(const gbd_beamlet& b, const gbd_project_params& G) {
     double ic = 0.5 * G.nx, jc = 0.5 * G.ny;
     const int hx = G.nx / 2, hy = G.ny / 2;
     if (fabs(dg) > 1e-12) {
-        const double sx = (g11 * b.rho[0] - g01 * b.rho[1]) / dg;
-        const double sy = (-g10 * b.rho[0] + g00 * b.rho[1]) / dg;
-        ic = sx / G.px + hx;
-        jc = sy / G.py + hy;
+        const double idg = 1.0 / dg;
+        const double sx = (g11 * b.rho[0] - g01 * b.rho[1]) * idg;
+        const double sy = (-g10 * b.rho[0] + g00 * b.rho[1]) * idg;
+        ic = sx * G.inv_px + hx;
+        jc = sy * G.inv_py + hy;
     }
     double i0 = rint(ic), j0 = rint(jc);
     if (!(i0 >= 0.0)) i0 = 0.0;
@@ -330,16 +335,16 @@ __device__ Quad project_one(const gbd_beamlet& b, const gbd_project_params& G) {
     X[4] = gv0 * Gu0 + gv1 * Gu1;
     X[5] = 0.5 * (gv0 * Gv0 + gv1 * Gv1);
     Y[3] = Y[4] = Y[5] = gbd::mk(0.0);
-    const double log2e = 1.4426950408889634;
+    const double log2e = 1.4426950408889634, inv_two_pi = 0.15915494309189533577;
     for (int m = 0; m < 6; ++m) {
         // c = Y - ik X:  Re c = Re Y + k Im X,  Im c = Im Y - k Re X
         q.a[m] = (Y[m].re + k * X[m].im) * log2e;
-        q.p[m] = Y[m].im / (2.0 * M_PI) - X[m].re / G.wavelength;
+        q.p[m] = Y[m].im * inv_two_pi - X[m].re * G.inv_wavelength;
     }
     // ln amp_j
     const double am = hypot(b.amp[0], b.amp[1]);
     q.a[0] += log2(am);
-    double p0 = q.p[0] + atan2(b.amp[1], b.amp[0]) / (2.0 * M_PI);
+    double p0 = q.p[0] + atan2(b.amp[1], b.amp[0]) * inv_two_pi;
     q.p[0] = p0 - rint(p0);
     return q;
 }

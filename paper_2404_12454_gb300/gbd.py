@@ -482,7 +482,7 @@ def gbd_mlp_train_step(master, weights, m, v, x, target, lr, beta1, beta2, eps, 
                                     _stream(stream)))
 
 
-TIMING_KINDS = ("field_mixed", "field_f64", "project", "reduce", "point")
+TIMING_KINDS = ("field_mixed", "field_f64", "project", "reduce", "point", "trace")
 
 
 def gbd_timing_enable(on: bool) -> None:
@@ -490,8 +490,8 @@ def gbd_timing_enable(on: bool) -> None:
 
 
 def gbd_timing_read() -> dict:
-    ms = (ctypes.c_double * 5)()
-    n = (ctypes.c_int64 * 5)()
+    ms = (ctypes.c_double * len(TIMING_KINDS))()
+    n = (ctypes.c_int64 * len(TIMING_KINDS))()
     _check(lib().gbd_timing_read(ms, n))
     return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(TIMING_KINDS)}
 

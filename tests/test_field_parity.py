@@ -111,6 +111,30 @@ def test_full_size_airy_large_sampled(prec):
     assert err <= TOL[prec], err
 
 
+@pytest.mark.parametrize("name", ["airy_large", "tilted_zernike"])
+def test_full_size_in_the_autotuned_launch_configuration(name):
+    """The configuration bench.py times: the autotuner's pick (shape, splits, scheme) on
+    the full-size workload, checked on the oracle's strided pixel sample."""
+    import torch
+    wl = W.by_name(name)
+    b = gpu_trace(wl)
+    prec = gbd.GBD_PREC_MIXED
+    ws = torch.empty(640 << 20, dtype=torch.uint8, device="cuda")
+    out = torch.empty((wl.detector.ny, wl.detector.nx), dtype=torch.complex64, device="cuda")
+    try:
+        gbd.gbd_autotune_field(b, b.shape[0], wl.system.wavelength, wl.detector, prec, ws, out)
+        del ws
+        E = gpu_field(b, wl, prec)
+    finally:
+        gbd.gbd_field_reset_shape(prec)
+    if name == "airy_large":
+        cols, rows = np.arange(3, 512, 16), np.arange(5, 512, 16)
+    else:
+        cols, rows = W.strided_pixels(wl)
+    Eo = oracle.field(oracle.trace(wl.system, wl.pupil), wl.system, wl.detector, cols, rows)
+    assert rel_l2(E[np.ix_(rows, cols)], Eo) <= TOL[prec]
+
+
 @pytest.mark.parametrize("prec", PRECS)
 def test_full_size_tilted_zernike_subset(prec):
     """1024 x 1024 tilted, aberrated detector; oracle on the 64 x 64 strided subset."""
@@ -289,6 +313,7 @@ def test_kernel_timing_hooks_count_launches():
     gbd.gbd_timing_read()
     gbd.gbd_timing_enable(True)
     try:
+        gbd.trace(wl.system, wl.pupil)
         for _ in range(3):
             gbd.field(b, wl.system.wavelength, wl.detector, gbd.GBD_PREC_MIXED)
         gbd.field(b, wl.system.wavelength, wl.detector, gbd.GBD_PREC_F64)
@@ -298,7 +323,8 @@ def test_kernel_timing_hooks_count_launches():
         gbd.gbd_timing_enable(False)
     assert t["field_mixed"][1] == 3 and t["field_f64"][1] == 1
     assert t["project"][1] == 4 and t["reduce"][1] == 4 and t["point"][1] == 0
-    assert all(t[k][0] > 0 for k in ("field_mixed", "field_f64", "project", "reduce"))
+    assert t["trace"][1] == 1
+    assert all(t[k][0] > 0 for k in ("field_mixed", "field_f64", "project", "reduce", "trace"))
 
 
 def test_wide_phase_flag_selects_exact_reduction():
