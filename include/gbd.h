@@ -266,7 +266,7 @@ gbd_status gbd_autotune_field(const gbd_beamlet* beamlets, int32_t n_beamlets,
  *   - A problem whose projected beamlet records plus one partial field of nx x ny pixels
  *     exceeds the array is rejected with GBD_EINVAL before any launch (beamlet splits are
  *     lowered to fit first; records take 64 B (mixed) / 128 B (FP64) per beamlet rounded
- *     up to 64 beamlets, a partial field 16 B per pixel).
+ *     up to 64 beamlets, a partial field 8 B (mixed) / 16 B (FP64) per pixel).
  *   - All calls share the array and each overwrites every byte it later reads, so nothing
  *     carries over from the previous call; calls that overlap on the GPU (for example
  *     on two streams of one device) race on it and must be serialised.  Each device

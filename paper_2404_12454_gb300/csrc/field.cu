@@ -5,7 +5,9 @@
 // projected beamlet records are streamed through shared memory in 64-beamlet tiles by
 // the TMA bulk-copy engine (4-stage mbarrier pipeline, one elected producer thread); each
 // thread keeps RB x CB pixels in registers and evaluates every beamlet of the tile on
-// them.  Splits write FP64 partial fields, summed in a fixed order by a second kernel that
+// them.  Splits write partial fields (the mixed kernels round their compensated (hi, lo)
+// sums to FP32 pairs, the FP64 kernels write FP64), summed in a fixed order in FP64 by a
+// second kernel that
 // also applies the per-pixel carrier of a tilted plane.
 //
 // Mixed path, per (beamlet, pixel): 4 FFMA for the quadratic form (row terms shared across
@@ -34,7 +36,7 @@ __device__ __forceinline__ void record_timeout() { atomicOr(&g_field_status, gbd
 template <int RB, int CB, bool WIDE, bool PAIR>
 __global__ void __launch_bounds__(kThreads, 2)
     field_mixed_kernel(const float4* __restrict__ coef, int n_tiles, int tiles_per_split, int nx,
-                       int ny, double2* __restrict__ partial, const unsigned* __restrict__ flags,
+                       int ny, float2* __restrict__ partial, const unsigned* __restrict__ flags,
                        unsigned mask, unsigned want, uint32_t spins) {
     static_assert(!PAIR || RB == 2, "row pairs need two rows per thread");
     if ((*flags & mask) != want) return;
@@ -88,7 +90,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         return;
     }
     const size_t npix = (size_t)nx * ny;
-    double2* out = partial + (size_t)blockIdx.z * npix;
+    float2* out = partial + (size_t)blockIdx.z * npix;
 #pragma unroll
     for (int r = 0; r < RB; ++r) {
         const int row = row0 + 8 * r;
@@ -97,8 +99,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         for (int c = 0; c < CB; ++c) {
             const int col = col0 + 32 * c;
             if (col >= nx) continue;
-            out[(size_t)row * nx + col] = make_double2((double)hi[r][c].x + (double)lo[r][c].x,
-                                                       (double)hi[r][c].y + (double)lo[r][c].y);
+            out[(size_t)row * nx + col] = gbd::round_pair(hi[r][c], lo[r][c]);
         }
     }
 }
@@ -109,7 +110,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 template <int CB, bool WIDE>
 __global__ void __launch_bounds__(kThreads, 2)
     field_mixed_pair_smem_kernel(const float4* __restrict__ coef, int n_tiles, int tiles_per_split,
-                                 int nx, int ny, double2* __restrict__ partial,
+                                 int nx, int ny, float2* __restrict__ partial,
                                  const unsigned* __restrict__ flags, unsigned mask, unsigned want,
                                  uint32_t spins) {
     if ((*flags & mask) != want) return;
@@ -163,7 +164,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         return;
     }
     const size_t npix = (size_t)nx * ny;
-    double2* out = partial + (size_t)blockIdx.z * npix;
+    float2* out = partial + (size_t)blockIdx.z * npix;
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
         const int row = row0 + 8 * r;
@@ -173,8 +174,8 @@ __global__ void __launch_bounds__(kThreads, 2)
             const int col = col0 + 32 * c;
             if (col >= nx) continue;
             const float4 v = comp[(r * CB + c) * kThreads + tid];
-            out[(size_t)row * nx + col] = make_double2((double)v.x + (double)v.z,
-                                                       (double)v.y + (double)v.w);
+            out[(size_t)row * nx + col] =
+                gbd::round_pair(make_float2(v.x, v.y), make_float2(v.z, v.w));
         }
     }
 }
@@ -393,20 +394,33 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
-// Fixed-order FP64 sum of the split partials, times the carrier exp(-ik z(s)) of each
-// pixel (z = n.s is the axial offset of the tilted plane), written as complex64/128.
-template <bool F64>
-__global__ void __launch_bounds__(256) field_reduce_kernel(const double2* __restrict__ partial,
+// Fixed-order FP64 sum of the split partials (float2 from the mixed kernels, double2 from
+// the FP64 ones), times the carrier exp(-ik z(s)) of each pixel (z = n.s is the axial
+// offset of the tilted plane), written as complex64/128.
+template <bool F64, typename P>
+__global__ void __launch_bounds__(256) field_reduce_kernel(const P* __restrict__ partial,
                                                            int splits, int nx, int ny, double cx,
                                                            double cy, void* __restrict__ out) {
     const size_t npix = (size_t)nx * ny;
     const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= npix) return;
+    // split order, eight loads in flight per thread (the loop is latency-bound otherwise)
     double re = 0.0, im = 0.0;
-    for (int s = 0; s < splits; ++s) {
-        const double2 v = partial[(size_t)s * npix + p];
-        re += v.x;
-        im += v.y;
+    int s = 0;
+    for (; s + 8 <= splits; s += 8) {
+        P v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = __ldg(partial + (size_t)(s + u) * npix + p);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            re += (double)v[u].x;
+            im += (double)v[u].y;
+        }
+    }
+    for (; s < splits; ++s) {
+        const P v = __ldg(partial + (size_t)s * npix + p);
+        re += (double)v.x;
+        im += (double)v.y;
     }
     if (cx != 0.0 || cy != 0.0) {
         const int i = (int)(p % nx), j = (int)(p / nx);
@@ -423,11 +437,59 @@ __global__ void __launch_bounds__(256) field_reduce_kernel(const double2* __rest
         static_cast<float2*>(out)[p] = make_float2((float)re, (float)im);
 }
 
+// The mixed path's reduction: GB300's FP64 pipe is too slow for an FP64 add per split and
+// pixel (it made this kernel FP64-bound at ~1 TB/s), so the float2 partials are summed in
+// FP32 with Neumaier's compensation, in split order; the carrier's phase in turns is
+// reduced in FP64 (one multiply-add and a rounding) and rotated in FP32.
+__global__ void __launch_bounds__(256) field_reduce_mixed_kernel(const float2* __restrict__ partial,
+                                                                 int splits, int nx, int ny,
+                                                                 double cx, double cy,
+                                                                 float2* __restrict__ out) {
+    const size_t npix = (size_t)nx * ny;
+    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npix) return;
+    float sr = 0.f, si = 0.f, cr = 0.f, ci = 0.f;
+    auto add = [](float& sum, float& comp, float x) {
+        const float t = __fadd_rn(sum, x);
+        comp = __fadd_rn(comp, fabsf(sum) >= fabsf(x) ? __fadd_rn(__fsub_rn(sum, t), x)
+                                                       : __fadd_rn(__fsub_rn(x, t), sum));
+        sum = t;
+    };
+    int s = 0;
+    for (; s + 8 <= splits; s += 8) {
+        float2 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = __ldg(partial + (size_t)(s + u) * npix + p);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            add(sr, cr, v[u].x);
+            add(si, ci, v[u].y);
+        }
+    }
+    for (; s < splits; ++s) {
+        const float2 v = __ldg(partial + (size_t)s * npix + p);
+        add(sr, cr, v.x);
+        add(si, ci, v.y);
+    }
+    float re = __fadd_rn(sr, cr), im = __fadd_rn(si, ci);
+    if (cx != 0.0 || cy != 0.0) {
+        const int i = (int)(p % nx), j = (int)(p / nx);
+        const double turns = cx * (i - nx / 2) + cy * (j - ny / 2);
+        float sn, cs;
+        sincospif(2.0f * (float)(turns - rint(turns)), &sn, &cs);
+        const float r2 = re * cs - im * sn;
+        im = re * sn + im * cs;
+        re = r2;
+    }
+    out[p] = make_float2(re, im);
+}
+
 template <int RB, int CB>
 cudaError_t launch_mixed(const void* coeffs, int n_tiles, const gbd_project_params& p,
-                         const gbd_field_launch& L, double2* partial, const unsigned* flags,
+                         const gbd_field_launch& L, void* partial_v, const unsigned* flags,
                          uint32_t spins, cudaStream_t s) {
     using gbd::kFlagWide;
+    float2* partial = static_cast<float2*>(partial_v);
     dim3 grid((p.nx + 32 * CB - 1) / (32 * CB), (p.ny + 8 * RB - 1) / (8 * RB), L.splits);
     const float4* c = static_cast<const float4*>(coeffs);
     const int tps = L.tiles_per_split;
@@ -442,8 +504,9 @@ cudaError_t launch_mixed(const void* coeffs, int n_tiles, const gbd_project_para
 // beamlet too steep for the recurrence.
 template <int CB>
 cudaError_t launch_mixed_pair(const void* coeffs, int n_tiles, const gbd_project_params& p,
-                              const gbd_field_launch& L, double2* partial, const unsigned* flags,
+                              const gbd_field_launch& L, void* partial_v, const unsigned* flags,
                               uint32_t spins, cudaStream_t s) {
+    float2* partial = static_cast<float2*>(partial_v);
     using gbd::kFlagSteep;
     using gbd::kFlagWide;
     constexpr unsigned kBoth = kFlagWide | kFlagSteep;
@@ -463,8 +526,9 @@ cudaError_t launch_mixed_pair(const void* coeffs, int n_tiles, const gbd_project
 
 template <int RB, int CB>
 cudaError_t launch_f64(const void* coeffs, int n_tiles, const gbd_project_params& p,
-                       const gbd_field_launch& L, double2* partial, const unsigned* /*wide*/,
+                       const gbd_field_launch& L, void* partial_v, const unsigned* /*wide*/,
                        uint32_t spins, cudaStream_t s) {
+    double2* partial = static_cast<double2*>(partial_v);
     const size_t smem = (size_t)kStages * gbd::kF64TileBytes;
     cudaError_t e = cudaFuncSetAttribute(field_f64_kernel<RB, CB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -478,8 +542,9 @@ cudaError_t launch_f64(const void* coeffs, int n_tiles, const gbd_project_params
 
 template <int RB, int CB>
 cudaError_t launch_f64_row(const void* coeffs, int n_tiles, const gbd_project_params& p,
-                           const gbd_field_launch& L, double2* partial, const unsigned* /*wide*/,
+                           const gbd_field_launch& L, void* partial_v, const unsigned* /*wide*/,
                            uint32_t spins, cudaStream_t s) {
+    double2* partial = static_cast<double2*>(partial_v);
     const size_t smem = (size_t)kStages * gbd::kF64TileBytes;
     cudaError_t e = cudaFuncSetAttribute(field_f64_row_kernel<RB, CB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -496,8 +561,9 @@ cudaError_t launch_f64_row(const void* coeffs, int n_tiles, const gbd_project_pa
 // their own pixel grid, same splits) are the steep-beamlet fallback.
 template <int CB>
 cudaError_t launch_mixed_pair_smem(const void* coeffs, int n_tiles, const gbd_project_params& p,
-                                   const gbd_field_launch& L, double2* partial,
+                                   const gbd_field_launch& L, void* partial_v,
                                    const unsigned* flags, uint32_t spins, cudaStream_t s) {
+    float2* partial = static_cast<float2*>(partial_v);
     using gbd::kFlagSteep;
     using gbd::kFlagWide;
     constexpr unsigned kBoth = kFlagWide | kFlagSteep;
@@ -524,7 +590,7 @@ cudaError_t launch_mixed_pair_smem(const void* coeffs, int n_tiles, const gbd_pr
 }
 
 typedef cudaError_t (*launch_fn)(const void*, int, const gbd_project_params&,
-                                 const gbd_field_launch&, double2*, const unsigned*, uint32_t,
+                                 const gbd_field_launch&, void*, const unsigned*, uint32_t,
                                  cudaStream_t);
 
 struct ShapeEntry {
@@ -588,7 +654,7 @@ int gbd_field_occupancy(int precision, int rb, int cb, int scheme) {
 
 cudaError_t gbd_launch_field_kernel(int precision, const void* coeffs, int n_tiles,
                                     const gbd_project_params& p, const gbd_field_launch& L,
-                                    double2* partial, const unsigned* wide, uint32_t wait_spins,
+                                    void* partial, const unsigned* wide, uint32_t wait_spins,
                                     cudaStream_t s) {
     const ShapeEntry* e = find_shape(precision, L.rows_per_thread, L.cols_per_thread, L.scheme);
     if (!e) return cudaErrorInvalidValue;
@@ -596,14 +662,17 @@ cudaError_t gbd_launch_field_kernel(int precision, const void* coeffs, int n_til
 }
 
 cudaError_t gbd_launch_field_reduce(int precision, const gbd_project_params& p, int splits,
-                                    const double2* partial, void* out, cudaStream_t s) {
+                                    const void* partial, void* out, cudaStream_t s) {
     const size_t npix = (size_t)p.nx * p.ny;
     const double cx = -p.n[0] * p.px / p.wavelength, cy = -p.n[1] * p.py / p.wavelength;
     const unsigned blocks = (unsigned)((npix + 255) / 256);
     if (precision == GBD_PREC_F64)
-        field_reduce_kernel<true><<<blocks, 256, 0, s>>>(partial, splits, p.nx, p.ny, cx, cy, out);
+        field_reduce_kernel<true, double2><<<blocks, 256, 0, s>>>(
+            static_cast<const double2*>(partial), splits, p.nx, p.ny, cx, cy, out);
     else
-        field_reduce_kernel<false><<<blocks, 256, 0, s>>>(partial, splits, p.nx, p.ny, cx, cy, out);
+        field_reduce_mixed_kernel<<<blocks, 256, 0, s>>>(static_cast<const float2*>(partial), splits,
+                                                         p.nx, p.ny, cx, cy,
+                                                         static_cast<float2*>(out));
     return cudaGetLastError();
 }
 

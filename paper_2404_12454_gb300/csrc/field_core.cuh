@@ -204,6 +204,11 @@ __device__ __forceinline__ void mixed_tile_pair(const float4* __restrict__ st,
     }
 }
 
+// A compensated (hi, lo) sum rounded once to FP32 (the split partial written to memory).
+__device__ __forceinline__ float2 round_pair(float2 hi, float2 lo) {
+    return make_float2((float)((double)hi.x + (double)lo.x), (float)((double)hi.y + (double)lo.y));
+}
+
 // Fold a tile's FP32 sums into compensated (hi, lo) pairs (TwoSum) and clear them.
 template <int RB, int CB>
 __device__ __forceinline__ void mixed_fold(float2 (&acc)[RB][CB], float2 (&hi)[RB][CB],

@@ -279,7 +279,8 @@ constexpr size_t kFlagBytes = 256;
 size_t workspace_for(int precision, int n, const gbd_detector* D, const gbd_field_launch& L) {
     if (n <= 0) return 0;
     const size_t coeff = align256((size_t)n_tiles_of(n) * tile_bytes(precision));
-    const size_t part = align256((size_t)L.splits * D->nx * D->ny * sizeof(double2));
+    const size_t elem = precision == GBD_PREC_MIXED ? sizeof(float2) : sizeof(double2);
+    const size_t part = align256((size_t)L.splits * D->nx * D->ny * elem);
     return kFlagBytes + coeff + part;
 }
 
@@ -302,8 +303,7 @@ gbd_status run_field(const gbd_beamlet* beamlets, int32_t n, double wavelength,
     char* base = static_cast<char*>(ws);
     unsigned* wide = reinterpret_cast<unsigned*>(base);
     void* coeffs = base + kFlagBytes;
-    double2* partial = reinterpret_cast<double2*>(base + kFlagBytes +
-                                                  align256((size_t)nt * tile_bytes(precision)));
+    void* partial = base + kFlagBytes + align256((size_t)nt * tile_bytes(precision));
     cudaError_t e = cudaMemsetAsync(wide, 0, sizeof(unsigned), stream);
     if (e != cudaSuccess) return cuda_fail(e, "gbd_field flag reset");
     {

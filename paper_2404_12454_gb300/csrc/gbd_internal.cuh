@@ -220,10 +220,11 @@ cudaError_t gbd_launch_project(const gbd_beamlet* b, int n, const gbd_project_pa
 cudaError_t gbd_launch_trace_mirrors(const gbd_mirror_params& m, gbd_beamlet* out, cudaStream_t s);
 cudaError_t gbd_launch_field_kernel(int precision, const void* coeffs, int n_tiles,
                                     const gbd_project_params& p, const gbd_field_launch& L,
-                                    double2* partial, const unsigned* wide, uint32_t wait_spins,
+                                    void* partial, const unsigned* wide, uint32_t wait_spins,
                                     cudaStream_t s);
+// partial: float2 per pixel and split for GBD_PREC_MIXED, double2 for GBD_PREC_F64
 cudaError_t gbd_launch_field_reduce(int precision, const gbd_project_params& p, int splits,
-                                    const double2* partial, void* out, cudaStream_t s);
+                                    const void* partial, void* out, cudaStream_t s);
 int gbd_field_occupancy(int precision, int rb, int cb, int scheme);
 gbd_status gbd_set_error(gbd_status st, const char* msg);  // sets gbd_last_error()
 gbd_status gbd_check_system(const gbd_system* s);
