@@ -383,3 +383,42 @@ def test_point_equals_plane_on_untilted_plane_and_full_size_subset():
     Ex = oracle.field(oracle.trace(full.system, full.pupil), full.system, full.detector, cols,
                       rows, exact=True)
     assert rel_l2(E[np.ix_(rows, cols)], Ex) <= 1e-11
+
+
+# ------------------------------------------------------------ maximum sizes --
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_maximum_pupil_grid(prec):
+    """4096 beamlets across (13,176,792 beamlets, the largest pupil the ABI accepts) on a
+    ragged 72 x 40 detector; the oracle sums every beamlet at a strided 9 x 5 sample."""
+    wl = W.Workload("max_pupil", W.System(1e-6, 0.024, 0.024), W.Pupil(2.4e-3, 4096, 1.5, 1.5),
+                    W.Detector(72, 40, 0.8e-6, 0.8e-6))
+    b = gpu_trace(wl)
+    assert b.shape[0] == oracle.count(4096)
+    E = gpu_field(b, wl, prec)
+    cols, rows = np.arange(3, 72, 8), np.arange(1, 40, 8)
+    o = oracle.trace(wl.system, wl.pupil)
+    Eo = oracle.field(o, wl.system, wl.detector, cols, rows)
+    assert rel_l2(E[np.ix_(rows, cols)], Eo) <= TOL[prec]
+
+
+def test_maximum_detector():
+    """A 16384 x 16384 detector (the largest the ABI accepts, 2^28 pixels) over +-82 lambda
+    F#, so the wide-phase instantiation runs; 52 beamlets; the oracle checks an 11 x 11
+    sample across the central +-12 lambda F# that includes the first and last row and
+    column."""
+    import torch
+    n = 16384
+    wl = W.Workload("max_det", W.System(1e-6, 0.024, 0.024), W.Pupil(2.4e-3, 8, 1.5, 1.5),
+                    W.Detector(n, n, 1e-7, 1e-7))
+    b = gpu_trace(wl)
+    assert projection_flags(b, wl) & 1
+    E = gbd.field(b, wl.system.wavelength, wl.detector, gbd.GBD_PREC_MIXED)
+    gbd.gbd_sync()
+    idx = np.array([0, 7000, 7600, 7900, 8150, 8192, 8250, 8500, 8800, 9400, n - 1])
+    sub = E[torch.as_tensor(idx, device=E.device)][:, torch.as_tensor(idx, device=E.device)]
+    sub = sub.cpu().numpy().astype(np.complex128)
+    del E
+    Eo = oracle.field(oracle.trace(wl.system, wl.pupil), wl.system, wl.detector, idx, idx)
+    assert rel_l2(sub, Eo) <= TOL[gbd.GBD_PREC_MIXED]
+    assert np.count_nonzero(np.abs(Eo) > 1e-3 * np.abs(Eo).max()) >= 30
