@@ -127,18 +127,20 @@ __host__ __device__ __forceinline__ cd operator*(cd a, cd b) {
 }
 __host__ __device__ __forceinline__ cd operator*(double s, cd a) { return cd{s * a.re, s * a.im}; }
 __host__ __device__ __forceinline__ cd cdiv(cd a, cd b) {
-    // Smith's algorithm
+    // Smith's algorithm, one reciprocal of the denominator (FP64 division is slow on GB300)
     if (fabs(b.re) >= fabs(b.im)) {
-        double r = b.im / b.re, den = b.re + b.im * r;
-        return cd{(a.re + a.im * r) / den, (a.im - a.re * r) / den};
+        const double r = b.im / b.re, inv = 1.0 / (b.re + b.im * r);
+        return cd{(a.re + a.im * r) * inv, (a.im - a.re * r) * inv};
     } else {
-        double r = b.re / b.im, den = b.re * r + b.im;
-        return cd{(a.re * r + a.im) / den, (a.im * r - a.re) / den};
+        const double r = b.re / b.im, inv = 1.0 / (b.re * r + b.im);
+        return cd{(a.re * r + a.im) * inv, (a.im * r - a.re) * inv};
     }
 }
-// Principal square root, branch cut on the negative real axis (sign of im kept).
+// Principal square root, branch cut on the negative real axis (sign of im kept).  The
+// modulus is formed directly: the arguments here (entries of A + B P1 and their
+// determinants) stay far from FP64 overflow and underflow, so hypot's scaling is not needed.
 __host__ __device__ __forceinline__ cd csqrt_p(cd z) {
-    double r = hypot(z.re, z.im);
+    double r = sqrt(fma(z.re, z.re, z.im * z.im));
     if (r == 0.0) return cd{0.0, z.im};
     if (z.re >= 0.0) {
         double t = sqrt(0.5 * (r + z.re));

@@ -280,7 +280,7 @@ __device__ Quad project_one(const gbd_beamlet& b, const gbd_project_params& G) {
         return q;
     }
     q.pad = false;
-    const double k = 2.0 * M_PI / G.wavelength;
+    const double k = 2.0 * M_PI * G.inv_wavelength;
     const double th0 = b.theta[0], th1 = b.theta[1];
     const double th2 = th0 * th0 + th1 * th1;
     const cd P00{b.curv[0], b.curv[1]}, P01{b.curv[2], b.curv[3]}, P10{b.curv[4], b.curv[5]},
@@ -342,7 +342,7 @@ __device__ Quad project_one(const gbd_beamlet& b, const gbd_project_params& G) {
         q.p[m] = Y[m].im * inv_two_pi - X[m].re * G.inv_wavelength;
     }
     // ln amp_j
-    const double am = hypot(b.amp[0], b.amp[1]);
+    const double am = sqrt(fma(b.amp[0], b.amp[0], b.amp[1] * b.amp[1]));
     q.a[0] += log2(am);
     double p0 = q.p[0] + atan2(b.amp[1], b.amp[0]) * inv_two_pi;
     q.p[0] = p0 - rint(p0);
