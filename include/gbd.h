@@ -81,7 +81,8 @@ typedef struct {
     int32_t nx, ny;            /* 1 .. 16384 each      */
 } gbd_detector;
 
-/* One traced beamlet (FP64, 36 doubles = 288 bytes), written by gbd_trace. */
+/* One traced beamlet (FP64, 36 doubles = 288 bytes), written by gbd_trace and
+ * gbd_trace_mirrors. */
 typedef struct {
     double rho[2];      /* chief-ray landing point on the reference plane, m            */
     double theta[2];    /* chief-ray slope                                             */
@@ -173,9 +174,12 @@ gbd_status gbd_trace_mirrors(const gbd_mirror_system* system, const gbd_pupil* p
  * precision GBD_PREC_F64: FP64 throughout, field_out is complex128 [ny][nx].
  * precision GBD_PREC_MIXED: per-beamlet projection in FP64 (constant phase reduced mod
  *   one turn), per-pixel quadratic form in FP32, exp2/sin/cos on the MUFU pipe (phases
- *   reduced exactly first when some beamlet's phase can exceed 256 rad on the detector)
- *   and the sum in FP32 64-beamlet chunks combined with compensated (TwoSum)
- *   accumulation; field_out is complex64.
+ *   reduced exactly first when some beamlet's phase can exceed 256 rad on the detector).
+ *   With the default row-pair scheme (see gbd_shape) only every other row of 8 is
+ *   evaluated so; the row 8 below is that value times the beamlet's exact 8-row step
+ *   factor (an FP32 complex multiply).  The sum runs in FP32 64-beamlet chunks combined
+ *   with compensated (TwoSum) accumulation; beamlet splits are rounded once to FP32 and
+ *   summed in split order with Neumaier's compensation; field_out is complex64.
  * workspace: device scratch of at least gbd_field_workspace_bytes(...) bytes, 256-byte
  *   aligned.  Contents on entry are ignored.
  * n_beamlets may be 0 (the field is then zero).
