@@ -138,24 +138,32 @@ def random_candidates(n: int, rng: np.random.Generator) -> List[Tuple[int, float
 
 
 def random_search(budget: int, batch: int = 64, seed: int = W.SEED_SURROGATE + 1) -> SearchResult:
+    """`budget` uniform draws over the search box, drawn and counted `batch` at a time (the
+    first batch equals a surrogate search's initial sample of that size and seed)."""
     rng = np.random.default_rng(seed)
-    params = random_candidates(budget, rng)
-    s = evaluate(params)
     steps = [batch] * (budget // batch) + ([budget % batch] if budget % batch else [])
+    params = []
+    for k in steps:
+        params += random_candidates(k, rng)
+    s = evaluate(params)
     return SearchResult(params, list(s), _curve(s, steps))
 
 
 def surrogate_search(rounds: int = 8, per_round: int = 64, n_init: int = 128, pool: int = 16384,
                      fit_steps: int = 400, seed: int = W.SEED_SURROGATE,
                      checkpoint: Optional[str] = None, target: Optional[float] = None,
-                     min_rounds: int = 1) -> SearchResult:
-    """Seeded initial sample (the first n_init instances of the 1024-instance sweep), then
-    rounds of fit -> rank a random pool -> verify the best per_round candidates.  After
-    `min_rounds` rounds it stops early once the best verified score reaches `target` (if
-    given).  With `checkpoint`, the data and the network are saved after every round and a
-    run resumes from them."""
-    sw = W.sweep()
-    params = [(sw.n_across[k], sw.overlap_factor[k], sw.waist_ratio[k]) for k in range(n_init)]
+                     min_rounds: int = 1, init_seed: Optional[int] = None) -> SearchResult:
+    """Seeded initial sample (the first n_init instances of the 1024-instance sweep, or
+    n_init random candidates drawn with `init_seed`), then rounds of fit -> rank a random
+    pool -> verify the best per_round candidates.  After `min_rounds` rounds it stops early
+    once the best verified score reaches `target` (if given).  With `checkpoint`, the data
+    and the network are saved after every round and a run resumes from them."""
+    if init_seed is None:
+        sw = W.sweep()
+        params = [(sw.n_across[k], sw.overlap_factor[k], sw.waist_ratio[k])
+                  for k in range(n_init)]
+    else:
+        params = random_candidates(n_init, np.random.default_rng(init_seed))
     start_round = 0
     net = MLP(seed)
     if checkpoint and os.path.exists(checkpoint):
@@ -195,3 +203,22 @@ def surrogate_search(rounds: int = 8, per_round: int = 64, n_init: int = 128, po
             np.savez(checkpoint, params=np.array(params, dtype=np.float64),
                      scores=np.array(scores), steps=np.array(steps), round=r + 1, **st)
     return SearchResult(params, scores, _curve(np.asarray(scores), steps))
+
+
+def compare_with_random(target: float, seeds: Sequence[int], n_init: int = 32,
+                        per_round: int = 32, budget: int = 1260) -> dict:
+    """Evaluations each method needs to come within `target`, per seed: the surrogate
+    search from n_init random draws (then rounds of per_round proposals), and random search
+    drawing per_round candidates at a time, both capped at `budget` evaluations (None when
+    the cap is hit first).  Both start from the same seeded draw of n_init candidates."""
+    out = {"seeds": list(seeds), "surrogate": [], "random": []}
+    rounds = (budget - n_init) // per_round
+    for sd in seeds:
+        sur = surrogate_search(rounds=rounds, per_round=per_round, n_init=n_init,
+                               seed=W.SEED_SURROGATE + sd, target=target, min_rounds=0,
+                               init_seed=sd)
+        out["surrogate"].append(sur.evals_to_reach(target))
+        rnd = random_search(budget=budget, batch=n_init if n_init == per_round else per_round,
+                            seed=sd)
+        out["random"].append(rnd.evals_to_reach(target))
+    return out
