@@ -3,8 +3,8 @@
 The oracle scores an instance by tracing it, summing its field on every pixel in FP64 and
 applying the score's definition directly.  The sweep computes the mixed-precision field and
 the score from moments.  A field error of relative L2 eps moves the score by at most about
-2 eps (the score is an RMS over fewer pixels than the field's norm), so the
-bound here is 2 x the mixed-path tolerance, 4e-5.
+2 eps (the score is an RMS over fewer pixels than the field's norm), so the bound here is
+2 x the mixed-path tolerance, 4e-5.
 """
 import math
 
