@@ -193,7 +193,7 @@ def grid_sweep() -> Sweep:
 
 
 # Annular zones of Sec. 6, in lambda/D (= lambda F# on the focal plane).
-PAPER_ZONES = ((0.0, 5.0), (5.0, 10.0), (10.0, 15.0))
+ANNULAR_ZONES = ((0.0, 5.0), (5.0, 10.0), (10.0, 15.0))
 
 
 def zone_sweep(of_values: Sequence[float] = tuple(np.linspace(1.0, 2.0, 11)),

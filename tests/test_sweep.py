@@ -147,7 +147,7 @@ def test_zone_scores_match_oracle():
     on a 512x512 detector over +-15.2 lambda F#."""
     full = W.zone_sweep()
     sw = W.sweep_subset(full, [0, 5, 10, 13, 18])
-    plan = gbd.sweep_plan(sw, zones=W.PAPER_ZONES)
+    plan = gbd.sweep_plan(sw, zones=W.ANNULAR_ZONES)
     got = plan.run().cpu().numpy()
     gbd.gbd_sync()
     assert got.shape == (5, 4)
@@ -156,7 +156,7 @@ def test_zone_scores_match_oracle():
         b = oracle.trace(sw.system, sw.pupil(k))
         E = oracle.field(b, sw.system, sw.detector)
         want = [oracle.airy_score(E, sw.detector, lam, F)]
-        want += [oracle.zone_score(E, sw.detector, lam, F, lo, hi) for lo, hi in W.PAPER_ZONES]
+        want += [oracle.zone_score(E, sw.detector, lam, F, lo, hi) for lo, hi in W.ANNULAR_ZONES]
         assert np.max(np.abs(got[k] - np.asarray(want))) <= SCORE_TOL, (k, got[k], want)
     # the plain score column equals a plan without zones
     plain = gbd.sweep_plan(sw).run().cpu().numpy()
