@@ -422,3 +422,75 @@ def test_maximum_detector():
     Eo = oracle.field(oracle.trace(wl.system, wl.pupil), wl.system, wl.detector, idx, idx)
     assert rel_l2(sub, Eo) <= TOL[gbd.GBD_PREC_MIXED]
     assert np.count_nonzero(np.abs(Eo) > 1e-3 * np.abs(Eo).max()) >= 30
+
+
+# ------------------------------------------------------- streams, threads, graphs --
+
+def test_concurrent_host_threads_on_separate_streams():
+    """Two host threads, each with its own stream and workspace, run trace + field at the
+    same time on different workloads; each result equals the same call made alone."""
+    import threading
+    import torch
+    cases = [W.airy_small(), W.scaled(W.tilted_zernike(), n_across=24, nx=80, ny=72)]
+    alone = []
+    for wl in cases:
+        b = gpu_trace(wl)
+        alone.append(gpu_field(b, wl, gbd.GBD_PREC_MIXED))
+    results = [None, None]
+    errors = []
+
+    def work(k):
+        try:
+            wl = cases[k]
+            s = torch.cuda.Stream()
+            with torch.cuda.stream(s):
+                for _ in range(5):
+                    b = gbd.trace(wl.system, wl.pupil, stream=s)
+                    E = gbd.field(b, wl.system.wavelength, wl.detector, gbd.GBD_PREC_MIXED,
+                                  stream=s)
+                gbd.gbd_sync(s)
+                results[k] = E.cpu().numpy().astype(np.complex128)
+        except Exception as e:  # reported below, on the main thread
+            errors.append(e)
+
+    threads = [threading.Thread(target=work, args=(k,)) for k in range(2)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    for k in range(2):
+        assert np.array_equal(results[k], alone[k])
+
+
+def test_trace_and_field_replay_from_a_cuda_graph():
+    """trace + field captured once into a CUDA graph (torch.cuda.CUDAGraph): with the
+    beamlet table and the field zeroed after capture, a replay rebuilds both and equals
+    the eager result bit for bit."""
+    import torch
+    wl = W.airy_small()
+    prec = gbd.GBD_PREC_MIXED
+    n = gbd.gbd_beamlet_count(wl.pupil)
+    beam = torch.empty((n, gbd.BEAMLET_DOUBLES), dtype=torch.float64, device="cuda")
+    ws = gbd.workspace(n, wl.detector, prec)
+    out = torch.empty((wl.detector.ny, wl.detector.nx), dtype=torch.complex64, device="cuda")
+    eager_b = gpu_trace(wl)
+    eager = gpu_field(eager_b, wl, prec)
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        # one eager pass on the capture stream first (library state, kernel attributes)
+        gbd.gbd_trace(wl.system, wl.pupil, wl.pupil.overlap_factor, wl.pupil.waist_ratio,
+                      beam, s)
+        gbd.gbd_field(beam, n, wl.system.wavelength, wl.detector, prec, ws, out, s)
+        s.synchronize()
+        with torch.cuda.graph(g, stream=s):
+            gbd.gbd_trace(wl.system, wl.pupil, wl.pupil.overlap_factor, wl.pupil.waist_ratio,
+                          beam, s)
+            gbd.gbd_field(beam, n, wl.system.wavelength, wl.detector, prec, ws, out, s)
+    out.zero_()
+    beam.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    gbd.gbd_sync()
+    assert np.array_equal(out.cpu().numpy().astype(np.complex128), eager)
