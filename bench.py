@@ -241,7 +241,12 @@ def run_ours(args, world, rank, local):
     from paper_2404_12454_gb300 import gbd
     from paper_2404_12454_gb300 import workloads as W
 
-    __graft_entry__.build()
+    # one build per node (the in-tree objects are shared), then every rank loads it
+    if local == 0:
+        __graft_entry__.build()
+    barrier(world)
+    if local != 0:
+        __graft_entry__.build()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     wl = W.airy_large()
