@@ -190,9 +190,16 @@ def traffic_bytes(tuned):
     return n["read"] + n["write"] * tuned[2] / n["splits"]
 
 
-def peak_evals_const() -> float:
-    """MUFU-bound beamlet-pixel evaluations/s of a GB300 at its maximum clock."""
-    return GB300_SMS * GB300_MAX_MHZ * 1e6 / (1.0 / MUFU_EX2_PER_CLK_SM + 2.0 / MUFU_SINCOS_PER_CLK_SM)
+def peak_evals_const(cols: int = 0) -> float:
+    """MUFU-bound beamlet-pixel evaluations/s of a GB300 at its maximum clock: the direct
+    scheme (cols = 0), or row pairs on 2 x cols pixels (4 ex2 and cols + 1 sin/cos pairs
+    per beamlet and block)."""
+    if cols:
+        n_ex2, n_sc = 4.0 / (2 * cols), (cols + 1) / (2.0 * cols)
+    else:
+        n_ex2, n_sc = 1.0, 1.0
+    return GB300_SMS * GB300_MAX_MHZ * 1e6 / (n_ex2 / MUFU_EX2_PER_CLK_SM +
+                                              2.0 * n_sc / MUFU_SINCOS_PER_CLK_SM)
 
 
 def gpu_index_for_smi(local: int) -> str:
@@ -406,7 +413,7 @@ def run_ours(args, world, rank, local):
                  "instances": plan.n, "beamlets": plan.beamlets, "evals_per_sweep": plan.evals,
                  "work_items": plan.items,
                  "shape": "2x8 row pairs (library default)",
-                 "frac_of_mufu_peak": sv / world / (peak_evals_const() * 16.0 / 9.0),
+                 "frac_of_mufu_peak": sv / world / peak_evals_const(8),
                  "frac_of_direct_scheme_mufu_peak": sv / world / peak_evals_const(),
                  "graph": True, "score_range": [float(sc.min()), float(sc.max())],
                  "workload": "1024 instances, airy_small optics, OF~U[1,3], WR~U[0.8,3], "
@@ -532,42 +539,43 @@ def run_ours(args, world, rank, local):
     clk = clocks.stop()
 
     # ---- roofline of the dominant kernel (mixed field kernel, MUFU pipe).  The direct
-    # scheme issues one ex2, one sin and one cos per beamlet-pixel evaluation; the row-pair
-    # scheme evaluates the first row and one row-step factor per column block exactly
-    # (cols + 1 exact evaluations per 2 x cols pixels) and the second row by complex
-    # multiplies on the FMA pipe.
+    # scheme issues one ex2, one sin and one cos per beamlet-pixel evaluation.  Per beamlet
+    # and 2 x cols pixel block the row-pair scheme issues cols + 1 sin/cos pairs (the first
+    # row and the exact row-step factor) and 4 ex2 (that factor, and the first row's
+    # amplitude, its column ratio and the ratio's ratio); the second row and the first
+    # row's amplitude come from multiplies on the FMA pipe.
     kms, kn = kt["field_mixed"]
     k_avg_s = (kms / max(kn, 1)) * 1e-3
     probes = gbd.gbd_probe_peaks()
-    clk_per_exact = 1.0 / MUFU_EX2_PER_CLK_SM + 2.0 / MUFU_SINCOS_PER_CLK_SM
-    exact_per_eval = (tuned[1] + 1) / (2.0 * tuned[1]) if tuned[4] else 1.0
-    peak_direct = GB300_SMS * GB300_MAX_MHZ * 1e6 / clk_per_exact
-    peak_evals = peak_direct / exact_per_eval
-    probe_peak_direct = 1.0 / (1.0 / probes["ex2"] + 1.0 / probes["sin"] + 1.0 / probes["cos"])
+    n_ex2, n_sc = (4.0 / (2 * tuned[1]), (tuned[1] + 1) / (2.0 * tuned[1])) if tuned[4] else (1.0, 1.0)
+    clk_per_eval = n_ex2 / MUFU_EX2_PER_CLK_SM + 2.0 * n_sc / MUFU_SINCOS_PER_CLK_SM
+    peak_direct = GB300_SMS * GB300_MAX_MHZ * 1e6 / (1.0 / MUFU_EX2_PER_CLK_SM +
+                                                    2.0 / MUFU_SINCOS_PER_CLK_SM)
+    peak_evals = GB300_SMS * GB300_MAX_MHZ * 1e6 / clk_per_eval
+    probe_peak = 1.0 / (n_ex2 / probes["ex2"] + n_sc / probes["sin"] + n_sc / probes["cos"])
     achieved = evals / k_avg_s
     roofline = {
         "bound": "alu",
-        "pipe": (f"MUFU (XU): ex2 + sin + cos per exact evaluation, {exact_per_eval:.4g} exact "
-                 "evaluations per beamlet-pixel (scheme "
-                 + ("row_pair" if tuned[4] else "direct") + ")"),
+        "pipe": (f"MUFU (XU): {n_ex2:.4g} ex2 + {n_sc:.4g} sin + {n_sc:.4g} cos per "
+                 "beamlet-pixel (scheme " + ("row_pair" if tuned[4] else "direct") + ")"),
         "achieved": achieved / 1e9, "peak": peak_evals / 1e9, "unit": "Geval/s",
         "frac": achieved / peak_evals,
         "traffic": traffic_bytes(tuned),
         "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one capture of "
                            f"{FIELD_MIXED_NCU['kernel']} at {FIELD_MIXED_NCU['splits']} splits; "
                            "writes scaled to this launch's split count"),
-        "peak_source": (f"derived: {GB300_SMS} SMs x {GB300_MAX_MHZ:g} MHz / ((1/{MUFU_EX2_PER_CLK_SM}"
-                        f" + 2/{MUFU_SINCOS_PER_CLK_SM}) clk per exact evaluation x "
-                        f"{exact_per_eval:.4g})"),
+        "peak_source": (f"derived: {GB300_SMS} SMs x {GB300_MAX_MHZ:g} MHz / ({n_ex2:.4g}/"
+                        f"{MUFU_EX2_PER_CLK_SM} + {2 * n_sc:.4g}/{MUFU_SINCOS_PER_CLK_SM}) clk "
+                        "per evaluation"),
         "kernel": ("field_mixed_pair_smem_kernel" if tuned[4] and tuned[1] >= 8
                    else "field_mixed_kernel") + f" ({tuned[0]}x{tuned[1]}, {tuned[2]} splits)",
         "kernel_ms_avg": k_avg_s * 1e3, "launches": kn,
-        "mufu_gops": 3.0 * exact_per_eval * achieved / 1e9,
+        "mufu_gops": (n_ex2 + 2.0 * n_sc) * achieved / 1e9,
         "direct_scheme_peak": peak_direct / 1e9,
         "frac_of_direct_scheme_peak": achieved / peak_direct,
         "probe_ops_per_s": probes,
-        "probe_peak_evals_per_s": probe_peak_direct / exact_per_eval,
-        "frac_of_probe_peak": achieved * exact_per_eval / probe_peak_direct,
+        "probe_peak_evals_per_s": probe_peak,
+        "frac_of_probe_peak": achieved / probe_peak,
     }
 
     # ---- error and CPU baseline (rank 0, one GPU)

@@ -202,9 +202,11 @@ gbd_status gbd_field(const gbd_beamlet* beamlets, int32_t n_beamlets, double wav
  *          exp(256 (auv ln 2 + i puv)), the row-pair scheme's column factor.
  *          wide_flag (device, may be NULL; zero it first) is OR-ed with bit 0 if some
  *          beamlet's phase can exceed 256 rad on the detector (gbd_field then reduces every
- *          per-pixel phase exactly before sin/cos) and bit 1 if some beamlet's log2
+ *          per-pixel phase exactly before sin/cos), bit 1 if some beamlet's log2
  *          amplitude can change by more than 64 over 8 rows (the row-pair scheme then falls
- *          back to direct evaluation).
+ *          back to direct evaluation) and bit 2 if it can change by more than 64 over 8
+ *          columns 32 apart (the row-pair scheme then evaluates each amplitude instead of
+ *          carrying it along the row).
  *   F64:   16 doubles per beamlet [tile][field f = 0..7][b % 64][2 doubles], same order, the
  *          phase in turns (phase / 2 pi), field 7 = S = exp of twice the uu coefficient as
  *          a complex number (re, im), the second ratio of a row recurrence; wide_flag is

@@ -32,14 +32,16 @@ __device__ __forceinline__ void record_timeout() { atomicOr(&g_field_status, gbd
 
 // WIDE selects the instantiation with per-pixel phase reduction, PAIR (RB = 2) the row-pair
 // evaluation.  Several instantiations are launched for one field; each returns at once
-// unless the projection's flag word, masked by `mask`, equals `want`.
+// unless the projection's flag word, masked by `mask`, equals `want` and (if `anyof` is
+// not 0) shares a bit with `anyof`.
 template <int RB, int CB, bool WIDE, bool PAIR>
 __global__ void __launch_bounds__(kThreads, 2)
     field_mixed_kernel(const float4* __restrict__ coef, int n_tiles, int tiles_per_split, int nx,
                        int ny, float2* __restrict__ partial, const unsigned* __restrict__ flags,
-                       unsigned mask, unsigned want, uint32_t spins) {
+                       unsigned mask, unsigned want, unsigned anyof, uint32_t spins) {
     static_assert(!PAIR || RB == 2, "row pairs need two rows per thread");
-    if ((*flags & mask) != want) return;
+    const unsigned fw = *flags;
+    if ((fw & mask) != want || (anyof != 0u && (fw & anyof) == 0u)) return;
     constexpr int kTileF4 = gbd::kMixedFields * gbd::kTile;
     __shared__ __align__(128) float4 stage[kStages][kTileF4];
     __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
@@ -112,8 +114,9 @@ __global__ void __launch_bounds__(kThreads, 2)
     field_mixed_pair_smem_kernel(const float4* __restrict__ coef, int n_tiles, int tiles_per_split,
                                  int nx, int ny, float2* __restrict__ partial,
                                  const unsigned* __restrict__ flags, unsigned mask, unsigned want,
-                                 uint32_t spins) {
-    if ((*flags & mask) != want) return;
+                                 unsigned anyof, uint32_t spins) {
+    const unsigned fw = *flags;
+    if ((fw & mask) != want || (anyof != 0u && (fw & anyof) == 0u)) return;
     constexpr int kTileF4 = gbd::kMixedFields * gbd::kTile;
     extern __shared__ __align__(128) float4 dyn4[];
     float4(*stage)[kTileF4] = reinterpret_cast<float4(*)[kTileF4]>(dyn4);
@@ -494,9 +497,9 @@ cudaError_t launch_mixed(const void* coeffs, int n_tiles, const gbd_project_para
     const float4* c = static_cast<const float4*>(coeffs);
     const int tps = L.tiles_per_split;
     field_mixed_kernel<RB, CB, false, false><<<grid, kThreads, 0, s>>>(
-        c, n_tiles, tps, p.nx, p.ny, partial, flags, kFlagWide, 0u, spins);
+        c, n_tiles, tps, p.nx, p.ny, partial, flags, kFlagWide, 0u, 0u, spins);
     field_mixed_kernel<RB, CB, true, false><<<grid, kThreads, 0, s>>>(
-        c, n_tiles, tps, p.nx, p.ny, partial, flags, kFlagWide, kFlagWide, spins);
+        c, n_tiles, tps, p.nx, p.ny, partial, flags, kFlagWide, kFlagWide, 0u, spins);
     return cudaGetLastError();
 }
 
@@ -507,20 +510,23 @@ cudaError_t launch_mixed_pair(const void* coeffs, int n_tiles, const gbd_project
                               const gbd_field_launch& L, void* partial_v, const unsigned* flags,
                               uint32_t spins, cudaStream_t s) {
     float2* partial = static_cast<float2*>(partial_v);
+    using gbd::kFlagColSteep;
     using gbd::kFlagSteep;
     using gbd::kFlagWide;
-    constexpr unsigned kBoth = kFlagWide | kFlagSteep;
+    constexpr unsigned kBoth = kFlagWide | kFlagSteep, kAll = kBoth | kFlagColSteep;
     dim3 grid((p.nx + 32 * CB - 1) / (32 * CB), (p.ny + 15) / 16, L.splits);
     const float4* c = static_cast<const float4*>(coeffs);
     const int tps = L.tiles_per_split;
+    // exactly one runs: narrow, then wide (or column-steep), then the steep fallbacks
     field_mixed_kernel<2, CB, false, true><<<grid, kThreads, 0, s>>>(
-        c, n_tiles, tps, p.nx, p.ny, partial, flags, kBoth, 0u, spins);
+        c, n_tiles, tps, p.nx, p.ny, partial, flags, kAll, 0u, 0u, spins);
     field_mixed_kernel<2, CB, true, true><<<grid, kThreads, 0, s>>>(
-        c, n_tiles, tps, p.nx, p.ny, partial, flags, kBoth, kFlagWide, spins);
+        c, n_tiles, tps, p.nx, p.ny, partial, flags, kFlagSteep, 0u, kFlagWide | kFlagColSteep,
+        spins);
     field_mixed_kernel<2, CB, false, false><<<grid, kThreads, 0, s>>>(
-        c, n_tiles, tps, p.nx, p.ny, partial, flags, kBoth, kFlagSteep, spins);
+        c, n_tiles, tps, p.nx, p.ny, partial, flags, kBoth, kFlagSteep, 0u, spins);
     field_mixed_kernel<2, CB, true, false><<<grid, kThreads, 0, s>>>(
-        c, n_tiles, tps, p.nx, p.ny, partial, flags, kBoth, kBoth, spins);
+        c, n_tiles, tps, p.nx, p.ny, partial, flags, kBoth, kBoth, 0u, spins);
     return cudaGetLastError();
 }
 
@@ -564,9 +570,10 @@ cudaError_t launch_mixed_pair_smem(const void* coeffs, int n_tiles, const gbd_pr
                                    const gbd_field_launch& L, void* partial_v,
                                    const unsigned* flags, uint32_t spins, cudaStream_t s) {
     float2* partial = static_cast<float2*>(partial_v);
+    using gbd::kFlagColSteep;
     using gbd::kFlagSteep;
     using gbd::kFlagWide;
-    constexpr unsigned kBoth = kFlagWide | kFlagSteep;
+    constexpr unsigned kBoth = kFlagWide | kFlagSteep, kAll = kBoth | kFlagColSteep;
     constexpr size_t smem = pair_smem_bytes<CB>();
     cudaError_t e = cudaFuncSetAttribute(field_mixed_pair_smem_kernel<CB, false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -578,14 +585,16 @@ cudaError_t launch_mixed_pair_smem(const void* coeffs, int n_tiles, const gbd_pr
     dim3 grid24((p.nx + 127) / 128, (p.ny + 15) / 16, L.splits);
     const float4* c = static_cast<const float4*>(coeffs);
     const int tps = L.tiles_per_split;
+    // exactly one runs: narrow, then wide (or column-steep), then the steep fallbacks
     field_mixed_pair_smem_kernel<CB, false><<<grid, kThreads, smem, s>>>(
-        c, n_tiles, tps, p.nx, p.ny, partial, flags, kBoth, 0u, spins);
+        c, n_tiles, tps, p.nx, p.ny, partial, flags, kAll, 0u, 0u, spins);
     field_mixed_pair_smem_kernel<CB, true><<<grid, kThreads, smem, s>>>(
-        c, n_tiles, tps, p.nx, p.ny, partial, flags, kBoth, kFlagWide, spins);
+        c, n_tiles, tps, p.nx, p.ny, partial, flags, kFlagSteep, 0u, kFlagWide | kFlagColSteep,
+        spins);
     field_mixed_kernel<2, 4, false, false><<<grid24, kThreads, 0, s>>>(
-        c, n_tiles, tps, p.nx, p.ny, partial, flags, kBoth, kFlagSteep, spins);
+        c, n_tiles, tps, p.nx, p.ny, partial, flags, kBoth, kFlagSteep, 0u, spins);
     field_mixed_kernel<2, 4, true, false><<<grid24, kThreads, 0, s>>>(
-        c, n_tiles, tps, p.nx, p.ny, partial, flags, kBoth, kBoth, spins);
+        c, n_tiles, tps, p.nx, p.ny, partial, flags, kBoth, kBoth, 0u, spins);
     return cudaGetLastError();
 }
 

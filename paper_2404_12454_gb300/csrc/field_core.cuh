@@ -183,12 +183,24 @@ __device__ __forceinline__ void mixed_tile_pair(const float4* __restrict__ st,
         const float gp = frac_turns(8.0f * kInvTwoPi * fmaf(q3.y, w, fmaf(q2.w, tu[0], q1.w))) * kTwoPi;
         const float gm = mufu_ex2(ga);
         float rx = gm * mufu_cos(gp), ry = gm * mufu_sin(gp);
+        // narrow phases: the first row's amplitude along the thread's columns by a real
+        // recurrence, amp(c + 1) = amp(c) rho(c), rho(c + 1) = rho(c) sig with
+        // log2 rho(0) = 32 (sa + a_uu (2 tu0 + 32)) and log2 sig = 2048 a_uu: three ex2
+        // instead of CB (the launch requires the projection's column-steep flag clear).
+        // The WIDE instantiation, which also serves column-steep fields, evaluates each.
+        float amp = 0.f, rho = 0.f, sig = 0.f;
+        if (!WIDE) {
+            amp = mufu_ex2(fmaf(tu[0], fmaf(q2.x, tu[0], sa), ra));
+            rho = mufu_ex2(32.0f * fmaf(q2.x, fmaf(2.0f, tu[0], 32.0f), sa));
+            sig = mufu_ex2(2048.0f * q2.x);
+        }
 #pragma unroll
         for (int c = 0; c < CB; ++c) {
-            const float ea = fmaf(tu[c], fmaf(q2.x, tu[c], sa), ra);
             float x = fmaf(tu[c], fmaf(q2.y, tu[c], sp), rp);
-            if (WIDE) x = frac_turns(x * kInvTwoPi) * kTwoPi;
-            const float amp = mufu_ex2(ea);
+            if (WIDE) {
+                x = frac_turns(x * kInvTwoPi) * kTwoPi;
+                amp = mufu_ex2(fmaf(tu[c], fmaf(q2.x, tu[c], sa), ra));
+            }
             const float cs = mufu_cos(x), sn = mufu_sin(x);
             acc[0][c].x = fmaf(amp, cs, acc[0][c].x);
             acc[0][c].y = fmaf(amp, sn, acc[0][c].y);
@@ -199,6 +211,10 @@ __device__ __forceinline__ void mixed_tile_pair(const float4* __restrict__ st,
                 const float nx = fmaf(rx, q3.z, -ry * q3.w);
                 ry = fmaf(rx, q3.w, ry * q3.z);
                 rx = nx;
+                if (!WIDE) {
+                    amp *= rho;
+                    rho *= sig;
+                }
             }
         }
     }

@@ -26,6 +26,7 @@ constexpr unsigned kStatusTimeout = 1u;
 // Bits of the projection's flag word (mixed records).
 constexpr unsigned kFlagWide = 1u;   // some phase may exceed kWidePhase on the detector
 constexpr unsigned kFlagSteep = 2u;  // the row-pair recurrence could leave FP32 range
+constexpr unsigned kFlagColSteep = 4u;  // so could an amplitude recurrence along a row
 
 // ----------------------------------------------------------------- PTX wrappers --
 

@@ -66,9 +66,11 @@ __global__ void __launch_bounds__(kThreads, 2)
                  const int2* __restrict__ items, int n_items, int tiles_x, int n_blocks, int nx,
                  int ny, const double2* __restrict__ airy, int n_regions,
                  double* __restrict__ moments, int* __restrict__ counter,
-                 const unsigned* __restrict__ flags, unsigned mask, unsigned want, uint32_t spins) {
+                 const unsigned* __restrict__ flags, unsigned mask, unsigned want, unsigned anyof,
+                 uint32_t spins) {
     static_assert(!PAIR || RB == 2, "row pairs need two rows per thread");
-    if ((*flags & mask) != want) return;
+    const unsigned fw = *flags;
+    if ((fw & mask) != want || (anyof != 0u && (fw & anyof) == 0u)) return;
     constexpr int kTileF4 = gbd::kMixedFields * gbd::kTile;
     extern __shared__ __align__(128) float4 sweep_dyn[];
     float4(*stage)[kTileF4] = reinterpret_cast<float4(*)[kTileF4]>(sweep_dyn);
@@ -244,14 +246,15 @@ template <int RB, int CB, bool WIDE, bool PAIR, bool SMEM>
 cudaError_t launch_one(dim3 grid, cudaStream_t s, const float4* coef, const int2* it_tiles,
                        const int2* items, int n_items, int tiles_x, int n_blocks, int nx, int ny,
                        const double2* airy, int n_regions, double* moments, int* counter,
-                       const unsigned* flags, unsigned mask, unsigned want, uint32_t spins) {
+                       const unsigned* flags, unsigned mask, unsigned want, unsigned anyof,
+                       uint32_t spins) {
     constexpr size_t smem = sweep_smem(RB, CB, SMEM);
     cudaError_t e = cudaFuncSetAttribute(sweep_kernel<RB, CB, WIDE, PAIR, SMEM>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     sweep_kernel<RB, CB, WIDE, PAIR, SMEM><<<grid, kThreads, smem, s>>>(
         coef, it_tiles, items, n_items, tiles_x, n_blocks, nx, ny, airy, n_regions, moments,
-        counter, flags, mask, want, spins);
+        counter, flags, mask, want, anyof, spins);
     return cudaGetLastError();
 }
 
@@ -264,41 +267,44 @@ cudaError_t launch_sweep(dim3 grid, cudaStream_t s, const float4* coef, const in
     using gbd::kFlagWide;
     cudaError_t e = launch_one<RB, CB, false, false, false>(
         grid, s, coef, it_tiles, items, n_items, tiles_x, n_blocks, nx, ny, airy, n_regions,
-        moments, counter, flags, kFlagWide, 0u, spins);
+        moments, counter, flags, kFlagWide, 0u, 0u, spins);
     if (e == cudaSuccess)
         e = launch_one<RB, CB, true, false, false>(grid, s, coef, it_tiles, items, n_items, tiles_x,
                                                    n_blocks, nx, ny, airy, n_regions, moments,
-                                                   counter, flags, kFlagWide, kFlagWide, spins);
+                                                   counter, flags, kFlagWide, kFlagWide, 0u, spins);
     return e;
 }
 
 // Row pairs on 2 x CB pixels, with direct evaluation on the same pixel blocks as the
-// fallback for steep beamlets; SMEM for the 2 x 8 blocks.
+// fallback for steep beamlets; SMEM for the 2 x 8 blocks.  Exactly one instantiation
+// runs: narrow phase, then wide phase or column-steep, then the steep fallbacks.
 template <int CB>
 cudaError_t launch_sweep_pair(dim3 grid, cudaStream_t s, const float4* coef, const int2* it_tiles,
                               const int2* items, int n_items, int tiles_x, int n_blocks, int nx,
                               int ny, const double2* airy, int n_regions, double* moments,
                               int* counter, const unsigned* flags, uint32_t spins) {
+    using gbd::kFlagColSteep;
     using gbd::kFlagSteep;
     using gbd::kFlagWide;
-    constexpr unsigned kBoth = kFlagWide | kFlagSteep;
+    constexpr unsigned kBoth = kFlagWide | kFlagSteep, kAll = kBoth | kFlagColSteep;
     constexpr bool kSmem = CB >= 8;
     cudaError_t e = launch_one<2, CB, false, true, kSmem>(
         grid, s, coef, it_tiles, items, n_items, tiles_x, n_blocks, nx, ny, airy, n_regions,
-        moments, counter, flags, kBoth, 0u, spins);
+        moments, counter, flags, kAll, 0u, 0u, spins);
     if (e == cudaSuccess)
         e = launch_one<2, CB, true, true, kSmem>(grid, s, coef, it_tiles, items, n_items, tiles_x,
                                                  n_blocks, nx, ny, airy, n_regions, moments,
-                                                 counter, flags, kBoth, kFlagWide, spins);
+                                                 counter, flags, kFlagSteep, 0u,
+                                                 kFlagWide | kFlagColSteep, spins);
     if (e == cudaSuccess)
         e = launch_one<2, CB, false, false, kSmem>(grid, s, coef, it_tiles, items, n_items,
                                                    tiles_x, n_blocks, nx, ny, airy, n_regions,
                                                    moments, counter, flags, kBoth, kFlagSteep,
-                                                   spins);
+                                                   0u, spins);
     if (e == cudaSuccess)
         e = launch_one<2, CB, true, false, kSmem>(grid, s, coef, it_tiles, items, n_items, tiles_x,
                                                   n_blocks, nx, ny, airy, n_regions, moments,
-                                                  counter, flags, kBoth, kBoth, spins);
+                                                  counter, flags, kBoth, kBoth, 0u, spins);
     return e;
 }
 

@@ -355,7 +355,8 @@ __device__ Quad project_one(const gbd_beamlet& b, const gbd_project_params& G) {
 // bits: kFlagWide if the beamlet's phase can exceed the wide-phase bound anywhere on the
 // detector (|tu| <= U, |tv| <= V around its centre), kFlagSteep if its log2 amplitude can
 // change by more than 64 over an 8-row step there (with T^3 included), where the row-pair
-// recurrence could under- or overflow FP32.
+// recurrence could under- or overflow FP32, and kFlagColSteep if it can change by more
+// than 64 along a thread's 8 columns (the amplitude recurrence's limit).
 __device__ __forceinline__ unsigned write_mixed(float4* __restrict__ out, long long t, const Quad& q,
                                                 const gbd_project_params& G) {
     float4 f0, f1, f2, f3;
@@ -375,6 +376,12 @@ __device__ __forceinline__ unsigned write_mixed(float4* __restrict__ out, long l
         const double step = 8.0 * (fabs(q.a[2]) + fabs(q.a[4]) * (U + 96.0) +
                                     fabs(q.a[5]) * (2.0 * V + 8.0)) + 768.0 * fabs(q.a[4]);
         if (!(step <= 64.0)) flags |= gbd::kFlagSteep;
+        // log2 amplitude change over one 32-column step: the narrow-phase row-pair kernels
+        // carry the first row's amplitude along a thread's (up to 8) columns by a
+        // recurrence, which needs the whole 224-pixel span within 2^64
+        const double colstep = 32.0 * (fabs(q.a[1]) + fabs(q.a[4]) * V +
+                                       fabs(q.a[3]) * (2.0 * U + 32.0));
+        if (!(8.0 * colstep <= 64.0)) flags |= gbd::kFlagColSteep;
         const double tm = exp2(256.0 * q.a[4]);
         const double tt = 256.0 * q.p[4];
         double sn, cs;

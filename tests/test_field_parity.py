@@ -228,9 +228,33 @@ def projection_flags(b, wl):
 
 @pytest.mark.parametrize("name", list(small_cases()) + ["airy_large", "tilted_zernike"])
 def test_row_pair_scheme_is_not_flagged_on_the_workloads(name):
-    """The row-pair recurrence applies to every workload (no fallback to direct)."""
+    """The row-pair recurrence applies to every workload (no fallback to direct); on the
+    full-size workloads the amplitude recurrence along rows applies too (the narrow-phase
+    instantiation runs)."""
     wl = small_cases()[name] if name in small_cases() else W.by_name(name)
-    assert projection_flags(gpu_trace(wl), wl) & 2 == 0
+    f = projection_flags(gpu_trace(wl), wl)
+    assert f & 2 == 0
+    if name in ("airy_large", "tilted_zernike"):
+        assert f == 0
+
+
+def test_column_steep_fields_use_the_general_row_pair_instantiation():
+    """Beamlets ~20 pixels wide against a thread's 224-pixel column span: the projection
+    flags the amplitude recurrence along rows as unsafe (bit 2) but not the row pairs
+    (bit 1); the general instantiation then evaluates each amplitude and the field
+    matches the oracle."""
+    wl = small_cases()["tilted_zernike_small"]
+    b = gpu_trace(wl)
+    f = projection_flags(b, wl)
+    assert f & 4 and not f & 2
+    Eo = oracle.field(oracle.trace(wl.system, wl.pupil), wl.system, wl.detector)
+    for cols in (4, 8):
+        try:
+            gbd.gbd_field_set_shape(gbd.GBD_PREC_MIXED, 2, cols, 3, gbd.GBD_SCHEME_ROW_PAIR)
+            E = gpu_field(b, wl, gbd.GBD_PREC_MIXED)
+        finally:
+            gbd.gbd_field_reset_shape(gbd.GBD_PREC_MIXED)
+        assert rel_l2(E, Eo) <= TOL[gbd.GBD_PREC_MIXED], cols
 
 
 @pytest.mark.parametrize("splits", (1, 3))
@@ -342,7 +366,7 @@ def test_wide_phase_flag_selects_exact_reduction():
         flag = torch.zeros(1, dtype=torch.int32, device="cuda")
         gbd.gbd_project(b, n, wl.system.wavelength, wl.detector, gbd.GBD_PREC_MIXED, coef, flag)
         gbd.gbd_sync()
-        assert int(flag.item()) == expect, wl.name
+        assert int(flag.item()) & 1 == expect, wl.name
     b = gpu_trace(wide)
     E = gpu_field(b, wide, gbd.GBD_PREC_MIXED)
     idx = np.arange(5, 1024, 33)
