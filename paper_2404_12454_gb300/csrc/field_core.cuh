@@ -155,10 +155,12 @@ __device__ __forceinline__ void mixed_tile(const float4* __restrict__ st, const 
 // Row-pair variant of mixed_tile on rows v (evaluated directly) and v + 8 (derived): with
 // ln E quadratic in the pixel, E(u, v + 8) = E(u, v) R(u) where the 8-row step factor
 // R(u) = exp(8 (c_v + c_uv tu + c_vv (2 tv + 8))) is itself geometric along the thread's
-// columns, R(u + 32) = R(u) T with T = exp(256 c_uv) from the record.  One exact R per
-// beamlet (reduced to [-pi, pi] always) replaces CB - 1 of the 2 CB exact evaluations'
-// three MUFU operations each; the second row costs 2 FMUL + 4 FFMA (+ 4 for the next R).
-// Requires the projection's steep flag to be clear (every R within 2^+-64).
+// columns, R(u + 32) = R(u) T with T = exp(256 c_uv) from the record.  Per beamlet and
+// thread: one exact R (ex2 + sin + cos, its phase always reduced to [-pi, pi]), sin + cos
+// for each first-row pixel, and (narrow phases) the first row's amplitude by a real
+// recurrence: 4 ex2 + 2 (CB + 1) sin/cos for 2 CB pixels instead of 6 CB MUFU operations.
+// The second row costs 2 FMUL + 4 FFMA per pixel (+ 4 for the next R, + 2 for the next
+// amplitude).  Requires the projection's steep flag to be clear (every R within 2^+-64).
 template <int CB, bool WIDE>
 __device__ __forceinline__ void mixed_tile_pair(const float4* __restrict__ st,
                                                 const float (&colf)[CB], float rowf,
