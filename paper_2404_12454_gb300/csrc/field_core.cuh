@@ -156,7 +156,8 @@ __device__ __forceinline__ void mixed_tile(const float4* __restrict__ st, const 
 // ln E quadratic in the pixel, E(u, v + 8) = E(u, v) R(u) where the 8-row step factor
 // R(u) = exp(8 (c_v + c_uv tu + c_vv (2 tv + 8))) is itself geometric along the thread's
 // columns, R(u + 32) = R(u) T with T = exp(256 c_uv) from the record.  Per beamlet and
-// thread: one exact R (ex2 + sin + cos, its phase always reduced to [-pi, pi]), sin + cos
+// thread: one exact R (ex2 + sin + cos; its phase, at most 64 rad unless the field is
+// wide, reduced to [-pi, pi] in the WIDE instantiation), sin + cos
 // for each first-row pixel, and (narrow phases) the first row's amplitude by a real
 // recurrence: 4 ex2 + 2 (CB + 1) sin/cos for 2 CB pixels instead of 6 CB MUFU operations.
 // The second row costs 2 FMUL + 4 FFMA per pixel (+ 4 for the next R, + 2 for the next
@@ -182,7 +183,9 @@ __device__ __forceinline__ void mixed_tile_pair(const float4* __restrict__ st,
         const float sp = fmaf(q2.w, tv, q1.y);
         const float w = fmaf(2.0f, tv, 8.0f);
         const float ga = 8.0f * fmaf(q3.x, w, fmaf(q2.z, tu[0], q1.z));
-        const float gp = frac_turns(8.0f * kInvTwoPi * fmaf(q3.y, w, fmaf(q2.w, tu[0], q1.w))) * kTwoPi;
+        float gp = 8.0f * fmaf(q3.y, w, fmaf(q2.w, tu[0], q1.w));
+        // the projection holds |gp| to 64 rad unless the wide flag is set
+        if (WIDE) gp = frac_turns(gp * kInvTwoPi) * kTwoPi;
         const float gm = mufu_ex2(ga);
         float rx = gm * mufu_cos(gp), ry = gm * mufu_sin(gp);
         // narrow phases: the first row's amplitude along the thread's columns by a real

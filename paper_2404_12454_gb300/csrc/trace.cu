@@ -371,7 +371,10 @@ __device__ __forceinline__ unsigned write_mixed(float4* __restrict__ out, long l
         const double U = fmax(q.i0, G.nx - 1 - q.i0), V = fmax(q.j0, G.ny - 1 - q.j0);
         const double bound = fabs(p[0]) + fabs(p[1]) * U + fabs(p[2]) * V + fabs(p[3]) * U * U +
                              fabs(p[4]) * U * V + fabs(p[5]) * V * V;
-        if (!(bound <= (double)gbd::kWidePhase)) flags |= gbd::kFlagWide;
+        // the row-pair kernels' 8-row step phase 8 (p_v + p_uv tu + p_vv (2 tv + 8)) is
+        // taken unreduced by the narrow instantiations, so it is held to 64 rad as well
+        const double rowstep = 8.0 * (fabs(p[2]) + fabs(p[4]) * U + fabs(p[5]) * (2.0 * V + 8.0));
+        if (!(bound <= (double)gbd::kWidePhase) || !(rowstep <= 64.0)) flags |= gbd::kFlagWide;
         // log2 amplitude change over 8 rows: 8 (a_v + a_uv tu + a_vv (2 tv + 8))
         const double step = 8.0 * (fabs(q.a[2]) + fabs(q.a[4]) * (U + 96.0) +
                                     fabs(q.a[5]) * (2.0 * V + 8.0)) + 768.0 * fabs(q.a[4]);
