@@ -175,7 +175,7 @@ __device__ __forceinline__ void mixed_tile_pair(const float4* __restrict__ st,
         const float4 q3 = st[3 * kTile + b];
         float tu[CB];
 #pragma unroll
-        for (int c = 0; c < CB; ++c) tu[c] = colf[c] - q0.x;
+        for (int c = 0; c < CB; ++c) tu[c] = WIDE || c == 0 ? colf[c] - q0.x : 0.f;
         const float tv = rowf - q0.y;
         const float ra = fmaf(tv, fmaf(q3.x, tv, q1.z), q0.z);
         const float rp = fmaf(tv, fmaf(q3.y, tv, q1.w), q0.w);
@@ -184,6 +184,10 @@ __device__ __forceinline__ void mixed_tile_pair(const float4* __restrict__ st,
         const float w = fmaf(2.0f, tv, 8.0f);
         const float ga = 8.0f * fmaf(q3.x, w, fmaf(q2.z, tu[0], q1.z));
         float gp = 8.0f * fmaf(q3.y, w, fmaf(q2.w, tu[0], q1.w));
+        // narrow phases: the first row's phase at column c as x0 + c (d1 + c d2), the
+        // quadratic in tu = tu0 + 32 c expanded about the thread's first column
+        const float x0 = fmaf(tu[0], fmaf(q2.y, tu[0], sp), rp);
+        const float d1 = 32.0f * fmaf(q2.y, tu[0] + tu[0], sp), d2 = 1024.0f * q2.y;
         // the projection holds |gp| to 64 rad unless the wide flag is set
         if (WIDE) gp = frac_turns(gp * kInvTwoPi) * kTwoPi;
         const float gm = mufu_ex2(ga);
@@ -201,10 +205,13 @@ __device__ __forceinline__ void mixed_tile_pair(const float4* __restrict__ st,
         }
 #pragma unroll
         for (int c = 0; c < CB; ++c) {
-            float x = fmaf(tu[c], fmaf(q2.y, tu[c], sp), rp);
+            float x;
             if (WIDE) {
+                x = fmaf(tu[c], fmaf(q2.y, tu[c], sp), rp);
                 x = frac_turns(x * kInvTwoPi) * kTwoPi;
                 amp = mufu_ex2(fmaf(tu[c], fmaf(q2.x, tu[c], sa), ra));
+            } else {
+                x = c == 0 ? x0 : fmaf((float)(c * c), d2, fmaf((float)c, d1, x0));
             }
             const float cs = mufu_cos(x), sn = mufu_sin(x);
             acc[0][c].x = fmaf(amp, cs, acc[0][c].x);
