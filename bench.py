@@ -44,7 +44,7 @@ GB300_MAX_MHZ = 2070.0
 # (profiles/field_mixed_kernel_airy_large.md) at 26 beamlet splits.  The reads are the
 # record tiles; the writes are the split partial fields, which scale with the split count.
 FIELD_MIXED_NCU = {"kernel": "field_mixed_pair_smem_kernel<8, false> (2x8 row pairs)",
-                   "read": 3.394048e6, "write": 128.067584e6, "splits": 90, "rows": 2, "cols": 8,
+                   "read": 3.343104e6, "write": 128.155392e6, "splits": 90, "rows": 2, "cols": 8,
                    "scheme": 1}
 
 
