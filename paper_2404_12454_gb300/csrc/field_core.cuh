@@ -114,7 +114,7 @@ struct TileStream {
 constexpr float kWidePhase = 256.0f;
 
 // One 64-beamlet tile of mixed-precision evaluation on a thread's RB x CB pixels.
-// Record fields: (i0, j0, a0, p0) (a1u, p1u, a1v, p1v) (auu, puu, auv, puv) (avv, pvv, -, -)
+// Record fields: (i0, j0, a0, p0) (a1u, p1u, a1v, p1v) (auu, puu, auv, puv) (avv, pvv, T)
 // with log2 |E| = a0 + a1u tu + a1v tv + auu tu^2 + auv tu tv + avv tv^2 and the phase in
 // radians the same in p, tu = i - i0, tv = j - j0.  WIDE: some beamlet's phase may exceed
 // kWidePhase on this detector, so every phase is reduced exactly to [-pi, pi] (in turns,
