@@ -30,6 +30,10 @@
  *                   - ik [L + z (1 - |theta|^2/2) + theta.delta + w^T P w / 2],
  *          delta = X_xy - rho_c,  w = delta - z theta
  *   6. Coherent sum over beamlets                                    Eq. sum_gaussian
+ *   7. Airy score (RMS of |E|/|E(0)| - |2 J1(x)/x| inside the third dark ring) and the
+ *      annular-zone scores                                                        Sec. 6
+ *   8. Real rays through reflective conics (the Ritchey-Chretien telescope), the same
+ *      steps 3-4 on their differences                                             App. B
  *
  * The global axial phase exp(-ik d) is dropped: phases are relative to the axial path.
  */
