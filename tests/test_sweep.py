@@ -174,3 +174,29 @@ def test_sweep_row_pairs_fall_back_on_steep_beamlets():
     gbd.gbd_sync()
     want = oracle_scores(sw, range(sw.n_instances))
     assert np.max(np.abs(got - want)) <= SCORE_TOL, (got, want)
+
+
+def test_sweep_general_row_pair_instantiation():
+    """A coarse detector (4 um pixels, +-25 lambda F#) where the beamlets are narrower than
+    a thread's column span: the projection flags the amplitude recurrence (bit 2) but not
+    the row pairs (bit 1), so the sweep's general row-pair instantiation runs; scores
+    match the oracle's."""
+    import torch
+    system, D, _ = W.sweep_optics()
+    det = W.Detector(128, 128, 4e-6, 4e-6)
+    sw = W.Sweep(system, D, det, (16, 32, 64), (2.0, 3.0, 1.5), (1.0, 1.0, 1.2))
+    flags = 0
+    for k in range(sw.n_instances):
+        b = gbd.trace(sw.system, sw.pupil(k))
+        n = b.shape[0]
+        coef = torch.empty(gbd.gbd_project_bytes(n, gbd.GBD_PREC_MIXED), dtype=torch.uint8,
+                           device="cuda")
+        flag = torch.zeros(1, dtype=torch.int32, device="cuda")
+        gbd.gbd_project(b, n, sw.system.wavelength, det, gbd.GBD_PREC_MIXED, coef, flag)
+        gbd.gbd_sync()
+        flags |= int(flag.item())
+    assert flags & 4 and not flags & 2, flags
+    got = gbd.sweep_plan(sw).run().cpu().numpy()
+    gbd.gbd_sync()
+    want = oracle_scores(sw, range(sw.n_instances))
+    assert np.max(np.abs(got - want)) <= SCORE_TOL, (got, want)
