@@ -341,12 +341,28 @@ __device__ Quad project_one(const gbd_beamlet& b, const gbd_project_params& G) {
         q.a[m] = (Y[m].re + k * X[m].im) * log2e;
         q.p[m] = Y[m].im * inv_two_pi - X[m].re * G.inv_wavelength;
     }
-    // ln amp_j
+    return q;
+}
+
+// The beamlet amplitude's log2 modulus and argument (turns) added to the constant term,
+// then the constant phase reduced to [-1/2, 1/2) turns.  FP64 for the FP64 records.
+__device__ __forceinline__ void add_amplitude_f64(Quad& q, const gbd_beamlet& b) {
     const double am = sqrt(fma(b.amp[0], b.amp[0], b.amp[1] * b.amp[1]));
     q.a[0] += log2(am);
-    double p0 = q.p[0] + atan2(b.amp[1], b.amp[0]) * inv_two_pi;
+    const double p0 = q.p[0] + atan2(b.amp[1], b.amp[0]) * 0.15915494309189533577;
     q.p[0] = p0 - rint(p0);
-    return q;
+}
+
+// The same for the mixed records, whose coefficients are FP32: the amplitude is scaled by
+// its binary exponent (exact) and the mantissa's log2 and argument taken in FP32, which
+// saves two FP64 library calls per beamlet; the sum and the reduction stay FP64.
+__device__ __forceinline__ void add_amplitude_f32(Quad& q, const gbd_beamlet& b) {
+    int e;
+    frexp(fmax(fabs(b.amp[0]), fabs(b.amp[1])), &e);
+    const float re = (float)ldexp(b.amp[0], -e), im = (float)ldexp(b.amp[1], -e);
+    q.a[0] += (double)e + 0.5 * (double)log2f(fmaf(re, re, im * im));
+    const double p0 = q.p[0] + (double)atan2f(im, re) * 0.15915494309189533577;
+    q.p[0] = p0 - rint(p0);
 }
 
 // Mixed-precision record of beamlet `t` in the tiled layout (4 float4 fields per beamlet),
@@ -385,14 +401,15 @@ __device__ __forceinline__ unsigned write_mixed(float4* __restrict__ out, long l
         const double colstep = 32.0 * (fabs(q.a[1]) + fabs(q.a[4]) * V +
                                        fabs(q.a[3]) * (2.0 * U + 32.0));
         if (!(8.0 * colstep <= 64.0)) flags |= gbd::kFlagColSteep;
-        const double tm = exp2(256.0 * q.a[4]);
+        // T in FP32 (it is stored as FP32), its phase reduced in FP64 first
+        const float tm = exp2f((float)(256.0 * q.a[4]));
         const double tt = 256.0 * q.p[4];
-        double sn, cs;
-        sincospi(2.0 * (tt - rint(tt)), &sn, &cs);
+        float sn, cs;
+        sincospif((float)(2.0 * (tt - rint(tt))), &sn, &cs);
         f0 = make_float4((float)q.i0, (float)q.j0, (float)q.a[0], (float)p[0]);
         f1 = make_float4((float)q.a[1], (float)p[1], (float)q.a[2], (float)p[2]);
         f2 = make_float4((float)q.a[3], (float)p[3], (float)q.a[4], (float)p[4]);
-        f3 = make_float4((float)q.a[5], (float)p[5], (float)(tm * cs), (float)(tm * sn));
+        f3 = make_float4((float)q.a[5], (float)p[5], tm * cs, tm * sn);
     }
     float4* tile = out + (size_t)(t / gbd::kTile) * gbd::kMixedFields * gbd::kTile;
     const int l = (int)(t % gbd::kTile);
@@ -411,7 +428,10 @@ __global__ void __launch_bounds__(128) project_mixed_kernel(const gbd_beamlet* _
     if (t >= n_pad) return;
     Quad q;
     q.pad = true;
-    if (t < n) q = project_one(b[t], G);
+    if (t < n) {
+        q = project_one(b[t], G);
+        if (!q.pad) add_amplitude_f32(q, b[t]);
+    }
     const unsigned f = write_mixed(out, t, q, G);
     if (f && wide) atomicOr(wide, f);
 }
@@ -424,7 +444,10 @@ __global__ void __launch_bounds__(128) project_f64_kernel(const gbd_beamlet* __r
     double2 f[gbd::kF64Fields];
     Quad q;
     q.pad = true;
-    if (t < n) q = project_one(b[t], G);
+    if (t < n) {
+        q = project_one(b[t], G);
+        if (!q.pad) add_amplitude_f64(q, b[t]);
+    }
     if (q.pad) {
         for (int m = 0; m < gbd::kF64Fields; ++m) f[m] = make_double2(0.0, 0.0);
         f[1].x = 2.0 * gbd::kPadLog2Amp;
@@ -478,6 +501,7 @@ __global__ void __launch_bounds__(256)
         trace_one(LensTracer{P}, P.diameter, P.wavelength, N, I.overlap_factor, I.waist_ratio, i, a,
                   &bm);
         q = project_one(bm, G);
+        if (!q.pad) add_amplitude_f32(q, bm);
     }
     const unsigned f = write_mixed(out, t, q, G);
     if (f && wide) atomicOr(wide, f);
