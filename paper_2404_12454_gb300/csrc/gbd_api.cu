@@ -450,6 +450,8 @@ gbd_status gbd_trace(const gbd_system* system, const gbd_pupil* pupil, double ov
     p.overlap_factor = overlap_factor;
     p.waist_ratio = waist_ratio;
     p.n_across = pupil->n_across;
+    p.grid = gbd_make_grid(pupil->diameter, system->wavelength, pupil->n_across, overlap_factor,
+                           waist_ratio);
     cudaError_t e;
     {
         TimingScope ts(kTimeTrace, static_cast<cudaStream_t>(stream));
@@ -501,6 +503,8 @@ gbd_status gbd_trace_mirrors(const gbd_mirror_system* system, const gbd_pupil* p
     m.diameter = pupil->diameter;
     m.overlap_factor = overlap_factor;
     m.waist_ratio = waist_ratio;
+    m.grid = gbd_make_grid(pupil->diameter, system->wavelength, pupil->n_across, overlap_factor,
+                           waist_ratio);
     cudaError_t e;
     {
         TimingScope ts(kTimeTrace, static_cast<cudaStream_t>(stream));

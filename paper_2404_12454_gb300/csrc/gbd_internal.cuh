@@ -156,12 +156,34 @@ __host__ __device__ __forceinline__ cd csqrt_p(cd z) {
 // ----------------------------------------------------- cross-unit host entries --
 // Implemented in the kernel translation units, called by the C ABI layer.
 
+// Decomposition constants of one pupil sampling (Eq. OF): spacing s = D/N, waist
+// w0 = OF D/(2N), weight s^2/(pi w0^2), parabasal steps h = WR w0 and
+// dth = WR lambda/(pi w0) with their reciprocals, P1 = i p1 I with p1 = -lambda/(pi w0^2).
+// Computed once per pupil on the host (IEEE FP64, as on the device).
+struct gbd_grid {
+    double s, w0, weight, h, dth, p1, ih, idt;
+};
+inline gbd_grid gbd_make_grid(double D, double lambda, int N, double OF, double WR) {
+    gbd_grid g;
+    g.s = D / N;
+    g.w0 = OF * D / (2.0 * N);
+    const double ipw = 1.0 / (M_PI * g.w0);
+    g.weight = g.s * g.s * ipw / g.w0;
+    g.h = WR * g.w0;
+    g.dth = WR * lambda * ipw;
+    g.p1 = -lambda * ipw / g.w0;
+    g.ih = 1.0 / g.h;
+    g.idt = 1.0 / g.dth;
+    return g;
+}
+
 struct gbd_trace_params {
     double wavelength, inv_f, d, zern_radius;
     double diameter, overlap_factor, waist_ratio;
     int32_t n_across;
     int32_t zdeg;                 // degree of the plate polynomial (-1 = no plate)
     double zpoly[66];             // W(x/R, y/R) = sum zpoly[idx(a,b)] (x/R)^a (y/R)^b
+    gbd_grid grid;                // of the single pupil traced without an instance table
 };
 
 // Sequence of reflective conics (lab-frame curvatures, vertices) for real-ray traces.
@@ -171,6 +193,7 @@ struct gbd_mirror_params {
     double z[GBD_MAX_MIRRORS], c[GBD_MAX_MIRRORS], K[GBD_MAX_MIRRORS];
     double z_ep, z_img, axial_path;
     double wavelength, diameter, overlap_factor, waist_ratio;
+    gbd_grid grid;
 };
 
 struct gbd_project_params {
@@ -202,6 +225,7 @@ struct gbd_instance_dev {
     int32_t reserved;
     int64_t offset;
     double overlap_factor, waist_ratio;
+    gbd_grid grid;
 };
 
 // Traces one pupil (d_inst == nullptr: the sampling in p) or n_instances pupils sharing

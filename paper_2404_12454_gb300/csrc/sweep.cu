@@ -504,6 +504,8 @@ gbd_status gbd_sweep_plan_create(const gbd_system* system, double diameter, cons
         I.offset = tile * gbd::kTile;
         I.overlap_factor = overlap_factor[k];
         I.waist_ratio = waist_ratio[k];
+        I.grid = gbd_make_grid(diameter, system->wavelength, n_across[k], overlap_factor[k],
+                               waist_ratio[k]);
         P->inst.push_back(I);
         P->inst_tiles.push_back(make_int2((int)tile, nt));
         tile += nt;

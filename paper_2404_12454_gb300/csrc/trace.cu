@@ -133,15 +133,10 @@ struct MirrorTracer {
 };
 
 template <class Tracer>
-__device__ void trace_one(const Tracer& T, double D, double lambda, int N, double OF, double WR,
-                          int i, int j, gbd_beamlet* out) {
-    const double s = D / N;
-    const double w0 = OF * D / (2.0 * N);
-    const double ipw = 1.0 / (M_PI * w0);  // shared by the three quotients below
-    const double weight = s * s * ipw / w0;
-    const double h = WR * w0;
-    const double dth = WR * lambda * ipw;
-    const double p1 = -lambda * ipw / w0;  // P1 = i * p1 * I
+__device__ void trace_one(const Tracer& T, const gbd_grid& g, int N, int i, int j,
+                          gbd_beamlet* out) {
+    const double s = g.s, w0 = g.w0, weight = g.weight, h = g.h, dth = g.dth;
+    const double p1 = g.p1;  // P1 = i * p1 * I
     const double cx = (i - 0.5 * (N - 1)) * s, cy = (j - 0.5 * (N - 1)) * s;
 
     Ray c{cx, cy, 0.0, 0.0, 0.0};
@@ -153,8 +148,8 @@ __device__ void trace_one(const Tracer& T, double D, double lambda, int N, doubl
     T(dx);
     T(dy);
     // columns: derivative of (x, y, tx, ty) with respect to (x0, y0 | tx0, ty0); one
-    // reciprocal per step instead of 16 FP64 divisions (the difference is within an ulp)
-    const double ih = 1.0 / h, idt = 1.0 / dth;
+    // reciprocal per step (from the grid) instead of 16 FP64 divisions (within an ulp)
+    const double ih = g.ih, idt = g.idt;
     double A[4] = {(wx.x - c.x) * ih, (wy.x - c.x) * ih, (wx.y - c.y) * ih, (wy.y - c.y) * ih};
     double C[4] = {(wx.tx - c.tx) * ih, (wy.tx - c.tx) * ih, (wx.ty - c.ty) * ih,
                    (wy.ty - c.ty) * ih};
@@ -214,13 +209,12 @@ __global__ void __launch_bounds__(128) trace_kernel(gbd_trace_params P,
                                                     const gbd_instance_dev* __restrict__ inst,
                                                     gbd_beamlet* __restrict__ out) {
     int N = P.n_across;
-    double OF = P.overlap_factor, WR = P.waist_ratio;
+    const gbd_grid* g = &P.grid;
     long long base = 0;
     if (inst != nullptr) {
-        const gbd_instance_dev I = inst[blockIdx.y];
+        const gbd_instance_dev& I = inst[blockIdx.y];
         N = I.n_across;
-        OF = I.overlap_factor;
-        WR = I.waist_ratio;
+        g = &I.grid;
         base = I.offset;
     }
     const int j = blockIdx.x;
@@ -236,8 +230,7 @@ __global__ void __launch_bounds__(128) trace_kernel(gbd_trace_params P,
     if (a < 0) return;
     const int i_lo = ((N - 1) - a) / 2;
     for (int t = threadIdx.x; t <= a; t += blockDim.x)
-        trace_one(LensTracer{P}, P.diameter, P.wavelength, N, OF, WR, i_lo + t, j,
-                  out + base + row_off + t);
+        trace_one(LensTracer{P}, *g, N, i_lo + t, j, out + base + row_off + t);
 }
 
 // Pupil in front of a sequence of conic mirrors, one CTA per grid row (as trace_kernel).
@@ -257,8 +250,7 @@ __global__ void __launch_bounds__(128) trace_mirrors_kernel(gbd_mirror_params M,
     if (a < 0) return;
     const int i_lo = ((N - 1) - a) / 2;
     for (int t = threadIdx.x; t <= a; t += blockDim.x)
-        trace_one(MirrorTracer{M}, M.diameter, M.wavelength, N, M.overlap_factor, M.waist_ratio,
-                  i_lo + t, j, out + row_off + t);
+        trace_one(MirrorTracer{M}, M.grid, N, i_lo + t, j, out + row_off + t);
 }
 
 // ---------------------------------------------------------------- projection --
@@ -498,8 +490,7 @@ __global__ void __launch_bounds__(256)
         }
         const int i = ((N - 1) - row_extent(a, N)) / 2 + (int)(u - R[a]);
         gbd_beamlet bm;
-        trace_one(LensTracer{P}, P.diameter, P.wavelength, N, I.overlap_factor, I.waist_ratio, i, a,
-                  &bm);
+        trace_one(LensTracer{P}, I.grid, N, i, a, &bm);
         q = project_one(bm, G);
         if (!q.pad) add_amplitude_f32(q, bm);
     }
