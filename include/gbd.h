@@ -233,9 +233,11 @@ gbd_status gbd_field_point(const gbd_beamlet* beamlets, int32_t n_beamlets, doub
 /* ---------------------------------------------------------------- tuning ----------
  * Launch shape of the field kernels: pixels per thread (rows x cols), beamlet splits and
  * (mixed) evaluation scheme.  Unless a shape was set for the current device with
- * gbd_field_set_shape, gbd_field uses 2x8 row pairs (mixed) or 1x16 row segments (F64)
- * with splits from a built-in heuristic; gbd_autotune_field times the candidate shapes
- * on the given problem (synchronously, with CUDA events) and keeps the fastest. */
+ * gbd_field_set_shape (NULL restores this default), gbd_field uses row pairs with 8, 4 or
+ * 2 columns per thread, whichever covers the detector's width at the least estimated
+ * cost (8 for widths that are multiples of 256), or 1x16 row segments (F64), with splits
+ * from a built-in heuristic; gbd_autotune_field times the candidate shapes on the given
+ * problem (synchronously, with CUDA events) and keeps the fastest. */
 typedef struct {
     int32_t rows_per_thread;   /* mixed: 1x4, 2x2, 2x4, 4x2 (columns 32 apart);   */
     int32_t cols_per_thread;   /* F64: 1x2, 2x2 (direct), 1x8, 2x8, 1x16, 1x32   */
@@ -313,7 +315,9 @@ gbd_status gbd_timing_read(double* total_ms, int64_t* launches);
  * pixel (nx/2, ny/2).
  * gbd_sweep_plan_create: host only; validates, lays out the tables and the work list
  *   ((instance, pixel block) items, instances with the most beamlet tiles first) and the
- *   workspace.  shape = NULL picks 2 x 4 pixels per thread.
+ *   workspace.  shape = NULL picks row pairs with 8 or 4 columns per thread, whichever
+ *   covers the detector's width at the lower estimated cost (8 for widths that are
+ *   multiples of 256); a shape's scheme field selects direct or row-pair evaluation.
  * gbd_sweep_bind: records the caller's device workspace (>= gbd_sweep_workspace_bytes,
  *   256-byte aligned; it must outlive the plan's runs), uploads the tables and the Airy
  *   table; synchronises `stream`.

@@ -227,10 +227,37 @@ gbd_shape default_shape(int precision) {
     return s;
 }
 
-gbd_shape stored_shape(int precision) {
-    std::lock_guard<std::mutex> lk(g_mu);
-    auto it = g_shapes.find({current_device(), precision});
-    return it == g_shapes.end() ? default_shape(precision) : it->second;
+// Columns per thread of the default mixed shape for a detector nx pixels wide: a thread
+// block covers 32 cb columns, so narrow or ragged detectors waste part of a 2 x 8 block;
+// the pick minimises (columns covered / nx) x the shape's relative cost per pixel
+// (measured on GB300: 2 x 8 row pairs 1, 2 x 4 about 1.2, 2 x 2 about 1.45).
+int auto_cols(int nx, int min_cols = 2) {
+    static const int kCols[3] = {8, 4, 2};
+    static const double kCost[3] = {1.0, 1.2, 1.45};
+    int best = 8;
+    double best_cost = 1e300;
+    for (int k = 0; k < 3 && kCols[k] >= min_cols; ++k) {
+        const long span = 32L * kCols[k];
+        const double cover = (double)((nx + span - 1) / span * span) / nx;
+        if (cover * kCost[k] < best_cost) {
+            best_cost = cover * kCost[k];
+            best = kCols[k];
+        }
+    }
+    return best;
+}
+
+// The shape set for this device and precision, else the default (for the mixed path with
+// its columns per thread fitted to the detector's width).
+gbd_shape stored_shape(int precision, const gbd_detector* D) {
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        auto it = g_shapes.find({current_device(), precision});
+        if (it != g_shapes.end()) return it->second;
+    }
+    gbd_shape s = default_shape(precision);
+    if (precision == GBD_PREC_MIXED && D) s.cols_per_thread = auto_cols(D->nx);
+    return s;
 }
 
 // Beamlet splits: enough CTAs for about 16 waves of resident CTAs, so that the last,
@@ -352,6 +379,7 @@ gbd_project_params gbd_make_project_params(double wavelength, const gbd_detector
     return project_params(wavelength, d);
 }
 int gbd_sm_count() { return sm_count(); }
+int gbd_auto_cols(int nx, int min_cols) { return auto_cols(nx, min_cols); }
 uint32_t gbd_wait_spins() { return wait_spins(); }
 
 // Kernel parameters of the shared optics of a trace (the pupil sampling is set by the
@@ -380,7 +408,7 @@ gbd_status gbd_field_fixed_scratch(const gbd_beamlet* beamlets, int32_t n, doubl
                                    cudaStream_t stream) {
     gbd_status st = check_field_args(beamlets, n, wavelength, detector, precision, scratch, out);
     if (st != GBD_OK) return st;
-    gbd_shape sh = stored_shape(precision);
+    gbd_shape sh = stored_shape(precision, detector);
     if (n > 0) {
         const int nt = n_tiles_of(n);
         gbd_field_launch L = resolve_launch(precision, sh, nt, detector);
@@ -536,7 +564,8 @@ size_t gbd_field_workspace_bytes(int32_t n_beamlets, const gbd_detector* detecto
     if (check_detector(detector) != GBD_OK || n_beamlets <= 0) return 0;
     if (precision != GBD_PREC_F64 && precision != GBD_PREC_MIXED) return 0;
     const gbd_field_launch L =
-        resolve_launch(precision, stored_shape(precision), n_tiles_of(n_beamlets), detector);
+        resolve_launch(precision, stored_shape(precision, detector), n_tiles_of(n_beamlets),
+                       detector);
     return workspace_for(precision, n_beamlets, detector, L);
 }
 
@@ -548,13 +577,18 @@ gbd_status gbd_field(const gbd_beamlet* beamlets, int32_t n_beamlets, double wav
     if (st != GBD_OK) return st;
     return run_field(beamlets, n_beamlets, wavelength, detector, precision, workspace,
                      workspace_bytes, field_out, static_cast<cudaStream_t>(stream),
-                     stored_shape(precision));
+                     stored_shape(precision, detector));
 }
 
 gbd_status gbd_field_set_shape(int32_t precision, const gbd_shape* shape) {
     if (precision != GBD_PREC_F64 && precision != GBD_PREC_MIXED)
         return fail(GBD_EINVAL, "precision must be GBD_PREC_F64 or GBD_PREC_MIXED");
-    gbd_shape s = shape ? *shape : default_shape(precision);
+    if (!shape) {  // back to the default (fitted to each detector)
+        std::lock_guard<std::mutex> lk(g_mu);
+        g_shapes.erase({current_device(), precision});
+        return GBD_OK;
+    }
+    gbd_shape s = *shape;
     if (!gbd_field_shape_supported(precision, s.rows_per_thread, s.cols_per_thread, s.scheme))
         return fail(GBD_EINVAL, "unsupported shape %dx%d (scheme %d)", s.rows_per_thread,
                     s.cols_per_thread, s.scheme);
@@ -571,7 +605,7 @@ gbd_status gbd_field_get_shape(int32_t precision, int32_t n_beamlets, const gbd_
     if (st != GBD_OK) return st;
     if (precision != GBD_PREC_F64 && precision != GBD_PREC_MIXED)
         return fail(GBD_EINVAL, "precision must be GBD_PREC_F64 or GBD_PREC_MIXED");
-    gbd_shape s = stored_shape(precision);
+    gbd_shape s = stored_shape(precision, detector);
     if (n_beamlets > 0) {
         gbd_field_launch L = resolve_launch(precision, s, n_tiles_of(n_beamlets), detector);
         s.splits = L.splits;

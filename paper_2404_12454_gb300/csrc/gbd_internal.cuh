@@ -253,6 +253,9 @@ cudaError_t gbd_launch_field_kernel(int precision, const void* coeffs, int n_til
 cudaError_t gbd_launch_field_reduce(int precision, const gbd_project_params& p, int splits,
                                     const void* partial, void* out, cudaStream_t s);
 int gbd_field_occupancy(int precision, int rb, int cb, int scheme);
+// Columns per thread (8, 4 or 2, at least min_cols) of the row-pair shape that covers a
+// detector nx pixels wide at the least estimated cost.
+int gbd_auto_cols(int nx, int min_cols);
 gbd_status gbd_set_error(gbd_status st, const char* msg);  // sets gbd_last_error()
 gbd_status gbd_check_system(const gbd_system* s);
 gbd_status gbd_check_detector(const gbd_detector* d);

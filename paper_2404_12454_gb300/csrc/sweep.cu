@@ -450,7 +450,8 @@ gbd_status gbd_sweep_plan_create(const gbd_system* system, double diameter, cons
         return gbd_set_error(GBD_EINVAL, "instance arrays are NULL");
     if (isinf(system->focal_length))
         return gbd_set_error(GBD_EINVAL, "the Airy score needs a lens (finite focal length)");
-    const int rb = shape ? shape->rows_per_thread : 2, cb = shape ? shape->cols_per_thread : 8;
+    const int rb = shape ? shape->rows_per_thread : 2;
+    const int cb = shape ? shape->cols_per_thread : gbd_auto_cols(detector->nx, 4);
     const int scheme = shape ? shape->scheme : GBD_SCHEME_ROW_PAIR;
     if (!find_sweep_shape(rb, cb, scheme))
         return gbd_set_error(GBD_EINVAL, "unsupported sweep shape");

@@ -359,8 +359,8 @@ class SweepPlan:
     def __init__(self, system, diameter, n_across, overlap_factor, waist_ratio, detector,
                  shape: Optional[Tuple[int, ...]] = None, stream=None, device="cuda",
                  zones: Optional[Sequence[Tuple[float, float]]] = None):
-        """shape: (rows, cols[, scheme]) per thread; None = the library's default
-        (2 x 8 row pairs)."""
+        """shape: (rows, cols[, scheme]) per thread; None = the library's default (row
+        pairs, 8 or 4 columns per thread fitted to the detector's width)."""
         import torch
         n, a, b, c = _instance_arrays(n_across, overlap_factor, waist_ratio)
         self.n = n
