@@ -273,10 +273,25 @@ long pixel_ctas(int precision, int rb, int cb, const gbd_detector* D) {
     return (long)((D->nx + 32 * cb - 1) / (32 * cb)) * ((D->ny + 8 * rb - 1) / (8 * rb));
 }
 
+// Resident CTAs per SM of a field kernel shape, queried once per device and shape.
+int cached_occupancy(int precision, int rb, int cb, int scheme) {
+    static std::map<std::array<int, 5>, int> cache;
+    const std::array<int, 5> key = {current_device(), precision, rb, cb, scheme};
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) return it->second;
+    }
+    const int occ = std::max(1, gbd_field_occupancy(precision, rb, cb, scheme));
+    std::lock_guard<std::mutex> lk(g_mu);
+    cache[key] = occ;
+    return occ;
+}
+
 int heuristic_splits(int precision, int rb, int cb, int scheme, int n_tiles,
                      const gbd_detector* D) {
     const long pix_ctas = pixel_ctas(precision, rb, cb, D);
-    const int occ = std::max(1, gbd_field_occupancy(precision, rb, cb, scheme));
+    const int occ = cached_occupancy(precision, rb, cb, scheme);
     const long slots = (long)occ * sm_count();
     long s = (16 * slots + pix_ctas - 1) / pix_ctas;
     s = std::min<long>(s, std::max(1, n_tiles / 8));
