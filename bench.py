@@ -328,6 +328,29 @@ def run_ours(args, world, rank, local):
     value = world * evals * args.steps / (total_ms * 1e-3)
     E_mix = out[MIX].cpu().numpy().astype(np.complex128)
 
+    # ---- the direct scheme (every pixel by ex2 + sin + cos) on the same step, for
+    # comparison with the scheme the autotuner picked; then the picked shape is restored
+    direct = None
+    if tuned[4]:
+        gbd.gbd_field_set_shape(MIX, 2, 4, 0, gbd.GBD_SCHEME_DIRECT)
+        ws_d = torch.empty(max(256, gbd.gbd_field_workspace_bytes(nb, det, MIX)),
+                           dtype=torch.uint8, device=dev)
+        ws_keep, ws[MIX] = ws[MIX], ws_d
+        timed(MIX, 2)
+        gbd.gbd_timing_read()
+        gbd.gbd_timing_enable(True)
+        md = timed(MIX, 3)
+        gbd.gbd_timing_enable(False)
+        gbd.gbd_sync(stream)
+        kd = gbd.gbd_timing_read()["field_mixed"]
+        kd_s = kd[0] / max(kd[1], 1) * 1e-3
+        direct = {"shape": "2x4 direct", "value": evals * len(md) / (sum(md) * 1e-3),
+                  "unit": UNIT, "kernel_ms": kd_s * 1e3,
+                  "frac_of_mufu_peak": evals / kd_s / peak_evals_const()}
+        ws[MIX] = ws_keep
+        del ws_d
+        gbd.gbd_field_set_shape(MIX, tuned[0], tuned[1], tuned[2], tuned[4])
+
     # ---- FP64 path on the same workload
     f64 = None
     if args.fp64_steps > 0:
@@ -606,6 +629,7 @@ def run_ours(args, world, rank, local):
                                        "factor)" if tuned[4] else "") + ", compensated FP32 sum"),
         "data": "synthetic (ideal F/10 lens standing in for the paper's traced telescope)",
         "config": config_block(wl, nb), "clocks": clk, "e2e": e2e, "fp64_path": f64,
+        "direct_scheme": direct,
         "autotuned_shape": {"rows_per_thread": tuned[0], "cols_per_thread": tuned[1],
                             "splits": tuned[2], "ms": tuned[3],
                             "scheme": "row_pair" if tuned[4] else "direct",
