@@ -363,13 +363,22 @@ void gbd_sweep_plan_destroy(gbd_sweep_plan* plan);
  * Compute: BF16 weights (round to nearest even from the FP32 master copy), FP32
  * activations and accumulation; loss = mean over the batch of (y - target)^2; Adam with
  * bias correction on the FP32 master weights.  All reductions have a fixed order, so
- * results are deterministic.  x is float[batch][3], target/y float[batch], all device.
+ * results are deterministic.  x is float[batch][3], target/y float[batch], all device;
+ * weights 16-byte aligned, workspaces 256-byte aligned (EINVAL otherwise); batch 1 .. 2^20
+ * for training, 1 .. 2^24 for the forward pass.
  * gbd_mlp_pack:       weights (uint16 BF16 bits) = round(master).
  * gbd_mlp_forward:    y = MLP(x); no workspace.
  * gbd_mlp_grad:       grad = dLoss/dparams (float[GBD_MLP_PARAMS]) and *loss (device float,
- *                     may be NULL) at the BF16 weights; workspace >= gbd_mlp_workspace_bytes.
+ *                     may be NULL) at the BF16 weights; workspace >= gbd_mlp_workspace_bytes
+ *                     (the four hidden layers' activations, GELU derivatives and errors,
+ *                     3 x 4 x batch x 128 floats, and per-chunk gradient partials).
  * gbd_mlp_adam:       one Adam step (step counts from 1) on master/m/v, then repacks.
- * gbd_mlp_train_step: gbd_mlp_grad then gbd_mlp_adam (the gradient lives in the workspace). */
+ * gbd_mlp_train:      `steps` full-batch steps (gradient, then Adam), step numbers
+ *                     first_step, first_step + 1, ...; *loss (may be NULL) = the loss of
+ *                     the last step, at the weights before its update.  The launches are
+ *                     queued on `stream` from this call, without returning to the caller
+ *                     between steps; nothing is synchronised.
+ * gbd_mlp_train_step: gbd_mlp_train with steps = 1. */
 #define GBD_MLP_PARAMS 50177
 size_t gbd_mlp_workspace_bytes(int32_t batch);
 gbd_status gbd_mlp_pack(const float* master, uint16_t* weights, void* stream);
@@ -380,6 +389,10 @@ gbd_status gbd_mlp_grad(const uint16_t* weights, const float* x, const float* ta
                         void* stream);
 gbd_status gbd_mlp_adam(float* master, uint16_t* weights, float* m, float* v, const float* grad,
                         float lr, float beta1, float beta2, float eps, int32_t step, void* stream);
+gbd_status gbd_mlp_train(float* master, uint16_t* weights, float* m, float* v, const float* x,
+                         const float* target, int32_t batch, float lr, float beta1, float beta2,
+                         float eps, int32_t first_step, int32_t steps, float* loss,
+                         void* workspace, size_t bytes, void* stream);
 gbd_status gbd_mlp_train_step(float* master, uint16_t* weights, float* m, float* v,
                               const float* x, const float* target, int32_t batch, float lr,
                               float beta1, float beta2, float eps, int32_t step, float* loss,

@@ -119,6 +119,9 @@ _SIGS = {
     "gbd_mlp_grad": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, _P, _P, _P, ctypes.c_size_t, _P]),
     "gbd_mlp_adam": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_float, ctypes.c_float,
                                     ctypes.c_float, ctypes.c_float, ctypes.c_int32, _P]),
+    "gbd_mlp_train": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, ctypes.c_int32, ctypes.c_float,
+                                     ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                     ctypes.c_int32, ctypes.c_int32, _P, _P, ctypes.c_size_t, _P]),
     "gbd_mlp_train_step": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, ctypes.c_int32, ctypes.c_float,
                                           ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                           ctypes.c_int32, _P, _P, ctypes.c_size_t, _P]),
@@ -471,6 +474,15 @@ def gbd_mlp_adam(master, weights, m, v, grad, lr, beta1, beta2, eps, step, strea
     _check(lib().gbd_mlp_adam(_ptr(master), _ptr(weights), _ptr(m), _ptr(v), _ptr(grad),
                               float(lr), float(beta1), float(beta2), float(eps), int(step),
                               _stream(stream)))
+
+
+def gbd_mlp_train(master, weights, m, v, x, target, lr, beta1, beta2, eps, first_step, steps,
+                  loss, workspace, stream=None) -> None:
+    _check(lib().gbd_mlp_train(_ptr(master), _ptr(weights), _ptr(m), _ptr(v), _ptr(x),
+                               _ptr(target), int(x.shape[0]), float(lr), float(beta1),
+                               float(beta2), float(eps), int(first_step), int(steps), _ptr(loss),
+                               _ptr(workspace), ctypes.c_size_t(workspace.numel()),
+                               _stream(stream)))
 
 
 def gbd_mlp_train_step(master, weights, m, v, x, target, lr, beta1, beta2, eps, step, loss,

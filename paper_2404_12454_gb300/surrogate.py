@@ -77,10 +77,10 @@ class MLP:
         ws = torch.empty(gbd.gbd_mlp_workspace_bytes(xt.shape[0]), dtype=torch.uint8,
                          device=self.device)
         loss = torch.zeros(1, dtype=torch.float32, device=self.device)
-        for _ in range(steps):
-            self.step += 1
-            gbd.gbd_mlp_train_step(self.master, self.weights, self.m, self.v, xt, yt, lr, 0.9,
-                                   0.999, 1e-8, self.step, loss, ws)
+        if steps > 0:
+            gbd.gbd_mlp_train(self.master, self.weights, self.m, self.v, xt, yt, lr, 0.9, 0.999,
+                              1e-8, self.step + 1, steps, loss, ws)
+            self.step += steps
         return float(loss.item())
 
     def predict(self, x: np.ndarray) -> np.ndarray:

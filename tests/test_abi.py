@@ -164,6 +164,53 @@ def test_field_rejects_bad_arguments(lib):
         gbd.gbd_field_set_shape(gbd.GBD_PREC_MIXED, 3, 3)
 
 
+def test_mlp_rejects_bad_arguments(lib):
+    class T:
+        def __init__(self, addr=256, n=1 << 26, rows=64):
+            self.addr, self.n, self.shape = addr, n, (rows, 3)
+
+        def data_ptr(self):
+            return self.addr
+
+        def numel(self):
+            return self.n
+
+    B = 64
+    need = gbd.gbd_mlp_workspace_bytes(B)
+    assert need >= 3 * 4 * B * 128 * 4 + 2 * B * 4
+    assert gbd.gbd_mlp_workspace_bytes(0) == 0
+    base = dict(master=T(), weights=T(), m=T(), v=T(), x=T(), target=T(), lr=1e-3, b1=0.9,
+                b2=0.999, eps=1e-8, first=1, steps=3, loss=T(), ws=T(n=need))
+    cases = [
+        (dict(master=None), gbd.GBD_EINVAL),
+        (dict(weights=T(addr=264)), gbd.GBD_EINVAL),   # weights not 16-byte aligned
+        (dict(ws=T(addr=272, n=need)), gbd.GBD_EINVAL),  # workspace not 256-byte aligned
+        (dict(ws=T(n=need - 1)), gbd.GBD_ENOMEM),
+        (dict(x=T(rows=0)), gbd.GBD_EINVAL),
+        (dict(x=T(rows=(1 << 20) + 1)), gbd.GBD_EINVAL),
+        (dict(steps=-1), gbd.GBD_EINVAL),
+        (dict(first=0), gbd.GBD_EINVAL),
+        (dict(first=2 ** 31 - 2, steps=5), gbd.GBD_EINVAL),
+        (dict(lr=0.0), gbd.GBD_EINVAL),
+        (dict(b1=1.0), gbd.GBD_EINVAL),
+        (dict(eps=-1.0), gbd.GBD_EINVAL),
+    ]
+    for c, want in cases:
+        a = dict(base)
+        a.update(c)
+        if a["x"].shape[0] != B and "ws" not in c:
+            a["ws"] = T(n=max(256, gbd.gbd_mlp_workspace_bytes(a["x"].shape[0])))
+        with pytest.raises(gbd.GbdError) as ei:
+            gbd.gbd_mlp_train(a["master"], a["weights"], a["m"], a["v"], a["x"], a["target"],
+                              a["lr"], a["b1"], a["b2"], a["eps"], a["first"], a["steps"],
+                              a["loss"], a["ws"])
+        assert ei.value.status == want, (c, ei.value.status)
+    with pytest.raises(gbd.GbdError):
+        gbd.gbd_mlp_forward(T(addr=258), T(), T())
+    with pytest.raises(gbd.GbdError):
+        gbd.gbd_mlp_adam(T(), T(), T(), T(), T(), 1e-3, 0.9, 0.999, 1e-8, 0)
+
+
 def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(gbd, "LIB_PATH", str(tmp_path / "missing.so"))
     monkeypatch.setattr(gbd, "_lib", None)

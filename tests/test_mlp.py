@@ -40,7 +40,8 @@ def test_pack_rounds_like_the_reference():
     assert np.array_equal(bits, M.bf16_bits(p))
 
 
-@pytest.mark.parametrize("B", [1, 31, 300, 1024])
+# 5000 samples take the 32-samples-per-CTA kernels and leave ragged gradient chunks
+@pytest.mark.parametrize("B", [1, 31, 300, 1024, 5000])
 def test_forward_matches_reference(B):
     import torch
     p, x, t, P, Wb, X, T = _setup(1, B)
@@ -52,7 +53,7 @@ def test_forward_matches_reference(B):
     assert np.max(np.abs(got - want)) <= 1e-5 * np.max(np.abs(want)) + 1e-6
 
 
-@pytest.mark.parametrize("B", [1, 257, 1024])
+@pytest.mark.parametrize("B", [1, 257, 1024, 5000])
 def test_gradient_matches_reference(B):
     import torch
     p, x, t, P, Wb, X, T = _setup(2, B)
@@ -96,6 +97,35 @@ def test_adam_matches_reference():
     same = P.cpu().numpy() == p2f
     assert same.mean() > 0.9
     assert np.array_equal(Wb.cpu().numpy().view(np.uint16)[same], M.bf16_bits(p2f)[same])
+
+
+@pytest.mark.parametrize("B", [200, 1024])
+def test_multi_step_training_equals_separate_steps(B):
+    """gbd_mlp_train over k steps (gradient partials summed inside Adam) gives the same bits
+    as k rounds of gbd_mlp_grad + gbd_mlp_adam, and its loss is the last step's."""
+    import torch
+    p, x, t, P, Wb, X, T = _setup(6, B)
+    ws = torch.empty(gbd.gbd_mlp_workspace_bytes(B), dtype=torch.uint8, device="cuda")
+    state = [(P.clone(), Wb.clone(), torch.zeros_like(P), torch.zeros_like(P)) for _ in range(2)]
+    loss_a = torch.zeros(1, dtype=torch.float32, device="cuda")
+    Pa, Wa, Ma, Va = state[0]
+    gbd.gbd_mlp_train(Pa, Wa, Ma, Va, X, T, 1e-3, 0.9, 0.999, 1e-8, 1, 4, loss_a, ws)
+    Pb, Wb2, Mb, Vb = state[1]
+    grad = torch.empty(M.N_PARAMS, dtype=torch.float32, device="cuda")
+    loss_b = torch.zeros(1, dtype=torch.float32, device="cuda")
+    for step in range(1, 5):
+        gbd.gbd_mlp_grad(Wb2, X, T, grad, loss_b, ws)
+        gbd.gbd_mlp_adam(Pb, Wb2, Mb, Vb, grad, 1e-3, 0.9, 0.999, 1e-8, step)
+    gbd.gbd_sync()
+    for a, b in zip(state[0], state[1]):
+        assert torch.equal(a, b)
+    assert loss_a.item() == loss_b.item()
+    # zero steps leave everything untouched
+    before = [a.clone() for a in state[0]]
+    gbd.gbd_mlp_train(Pa, Wa, Ma, Va, X, T, 1e-3, 0.9, 0.999, 1e-8, 5, 0, loss_a, ws)
+    gbd.gbd_sync()
+    for a, b in zip(state[0], before):
+        assert torch.equal(a, b)
 
 
 def test_training_learns_and_is_deterministic():
