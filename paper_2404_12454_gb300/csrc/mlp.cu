@@ -88,27 +88,31 @@ __device__ __forceinline__ void stage_hidden_weights(const uint16_t* __restrict_
     }
 }
 
-// Forward pass of TB samples per CTA; thread o owns hidden unit o.  When abuf is non-null
-// (training) the activations gelu(z_l) and derivatives gelu'(z_l) of the four hidden
-// layers are stored, [layer][sample][unit].
-template <int TB>
-__global__ void __launch_bounds__(H) mlp_fwd_kernel(const uint16_t* __restrict__ W,
-                                                    const float* __restrict__ x, int B,
-                                                    float* __restrict__ abuf,
-                                                    float* __restrict__ gbuf,
-                                                    float* __restrict__ y) {
+// Forward pass of TB samples per CTA in G = TB / SPT groups of 128 threads: thread (g, o)
+// owns hidden unit o of samples g SPT .. g SPT + SPT - 1 (the groups share the staged
+// weights; more warps per SM hide the latency of the short per-sample chains).  When abuf
+// is non-null (training) the activations gelu(z_l) and derivatives gelu'(z_l) of the four
+// hidden layers are stored, [layer][sample][unit].
+template <int TB, int SPT>
+__global__ void __launch_bounds__(H * (TB / SPT)) mlp_fwd_kernel(const uint16_t* __restrict__ W,
+                                                                 const float* __restrict__ x, int B,
+                                                                 float* __restrict__ abuf,
+                                                                 float* __restrict__ gbuf,
+                                                                 float* __restrict__ y) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint16_t* ws = reinterpret_cast<uint16_t*>(smem);
     float(*act)[TB][H] =
         reinterpret_cast<float(*)[TB][H]>(smem + sizeof(uint16_t) * 3 * H * WPAD);
-    const int o = threadIdx.x, b0 = blockIdx.x * TB;
+    const int o = threadIdx.x & (H - 1), bs = (threadIdx.x >> 7) * SPT;
+    const int b0 = blockIdx.x * TB;
     const int nb = min(TB, B - b0);
     stage_hidden_weights(W, ws, WPAD);
     {
         const float w0 = bf(W[off_w(0) + o * 3]), w1 = bf(W[off_w(0) + o * 3 + 1]),
                     w2 = bf(W[off_w(0) + o * 3 + 2]), bias = bf(W[off_b(0) + o]);
 #pragma unroll
-        for (int b = 0; b < TB; ++b) {
+        for (int k = 0; k < SPT; ++k) {
+            const int b = bs + k;
             float a = 0.f;
             if (b < nb) {
                 const float* xb = x + (size_t)(b0 + b) * 3;
@@ -128,51 +132,52 @@ __global__ void __launch_bounds__(H) mlp_fwd_kernel(const uint16_t* __restrict__
         const float(*cur)[H] = act[(l - 1) & 1];
         float(*nxt)[H] = act[l & 1];
         const uint16_t* wrow = ws + (size_t)((l - 1) * H + o) * WPAD;
-        float acc[TB];
+        float acc[SPT];
         const float bias = bf(W[off_b(l) + o]);
 #pragma unroll
-        for (int b = 0; b < TB; ++b) acc[b] = bias;
-#pragma unroll 2
+        for (int k = 0; k < SPT; ++k) acc[k] = bias;
+#pragma unroll 4
         for (int i = 0; i < H; i += 8) {
             const uint4 wv = *reinterpret_cast<const uint4*>(wrow + i);
             const float w0 = bf_lo(wv.x), w1 = bf_hi(wv.x), w2 = bf_lo(wv.y), w3 = bf_hi(wv.y),
                         w4 = bf_lo(wv.z), w5 = bf_hi(wv.z), w6 = bf_lo(wv.w), w7 = bf_hi(wv.w);
 #pragma unroll
-            for (int b = 0; b < TB; ++b) {
-                const float4 a = *reinterpret_cast<const float4*>(&cur[b][i]);
-                const float4 c = *reinterpret_cast<const float4*>(&cur[b][i + 4]);
-                float s = fmaf(a.x, w0, acc[b]);
+            for (int k = 0; k < SPT; ++k) {
+                const float4 a = *reinterpret_cast<const float4*>(&cur[bs + k][i]);
+                const float4 c = *reinterpret_cast<const float4*>(&cur[bs + k][i + 4]);
+                float s = fmaf(a.x, w0, acc[k]);
                 s = fmaf(a.y, w1, s);
                 s = fmaf(a.z, w2, s);
                 s = fmaf(a.w, w3, s);
                 s = fmaf(c.x, w4, s);
                 s = fmaf(c.y, w5, s);
                 s = fmaf(c.z, w6, s);
-                acc[b] = fmaf(c.w, w7, s);
+                acc[k] = fmaf(c.w, w7, s);
             }
         }
         float* al = abuf ? abuf + (size_t)l * B * H : nullptr;
         float* gl = gbuf ? gbuf + (size_t)l * B * H : nullptr;
 #pragma unroll
-        for (int b = 0; b < TB; ++b) {
+        for (int k = 0; k < SPT; ++k) {
+            const int b = bs + k;
             float a = 0.f;
             if (b < nb) {
-                a = gelu(acc[b]);
+                a = gelu(acc[k]);
                 if (al) {
                     al[(size_t)(b0 + b) * H + o] = a;
-                    gl[(size_t)(b0 + b) * H + o] = gelu_grad(acc[b]);
+                    gl[(size_t)(b0 + b) * H + o] = gelu_grad(acc[k]);
                 }
             }
             nxt[b][o] = a;
         }
         __syncthreads();
     }
-    // output unit: warp w takes samples w, w + 4, ...; lane k the inputs 4k .. 4k + 3
-    const int warp = o >> 5, lane = o & 31;
+    // output unit: warp w takes samples w, w + warps, ...; lane k the inputs 4k .. 4k + 3
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint2 w5 = *reinterpret_cast<const uint2*>(W + off_w(4) + lane * 4);
     const float v0 = bf_lo(w5.x), v1 = bf_hi(w5.x), v2 = bf_lo(w5.y), v3 = bf_hi(w5.y);
     const float bias5 = bf(W[off_b(4)]);
-    for (int b = warp; b < nb; b += H / 32) {
+    for (int b = warp; b < nb; b += (int)(blockDim.x >> 5)) {
         const float4 a = *reinterpret_cast<const float4*>(&act[1][b][lane * 4]);
         float s = fmaf(a.w, v3, fmaf(a.z, v2, fmaf(a.y, v1, a.x * v0)));
         for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
@@ -180,30 +185,33 @@ __global__ void __launch_bounds__(H) mlp_fwd_kernel(const uint16_t* __restrict__
     }
 }
 
-// Backward pass of TB samples per CTA: output error of the mean squared loss, then the
-// error of every hidden layer (thread i owns unit i).  dbuf[l] = dL/dz_l, dout = dL/dy.
-template <int TB>
-__global__ void __launch_bounds__(H) mlp_bwd_kernel(const uint16_t* __restrict__ W,
-                                                    const float* __restrict__ gbuf,
-                                                    const float* __restrict__ y,
-                                                    const float* __restrict__ target, int B,
-                                                    float* __restrict__ dbuf,
-                                                    float* __restrict__ dout) {
+// Backward pass of TB samples per CTA, grouped like the forward pass (thread (g, i) owns
+// unit i of its group's samples): output error of the mean squared loss, then the error
+// of every hidden layer.  dbuf[l] = dL/dz_l, dout = dL/dy.
+template <int TB, int SPT>
+__global__ void __launch_bounds__(H * (TB / SPT)) mlp_bwd_kernel(const uint16_t* __restrict__ W,
+                                                                 const float* __restrict__ gbuf,
+                                                                 const float* __restrict__ y,
+                                                                 const float* __restrict__ target,
+                                                                 int B, float* __restrict__ dbuf,
+                                                                 float* __restrict__ dout) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint16_t* ws = reinterpret_cast<uint16_t*>(smem);  // [3][o][i], W2..W4
     float(*dn)[TB][H] = reinterpret_cast<float(*)[TB][H]>(smem + sizeof(uint16_t) * 3 * H * H);
     float* dy = reinterpret_cast<float*>(smem + sizeof(uint16_t) * 3 * H * H +
                                          sizeof(float) * 2 * TB * H);
-    const int i = threadIdx.x, b0 = blockIdx.x * TB;
+    const int i = threadIdx.x & (H - 1), bs = (threadIdx.x >> 7) * SPT;
+    const int b0 = blockIdx.x * TB;
     const int nb = min(TB, B - b0);
     stage_hidden_weights(W, ws, H);
-    if (i < TB) {
+    if (threadIdx.x < TB) {
+        const int b = threadIdx.x;
         float d = 0.f;
-        if (i < nb) {
-            d = 2.0f * (y[b0 + i] - target[b0 + i]) / (float)B;
-            dout[b0 + i] = d;
+        if (b < nb) {
+            d = 2.0f * (y[b0 + b] - target[b0 + b]) / (float)B;
+            dout[b0 + b] = d;
         }
-        dy[i] = d;
+        dy[b] = d;
     }
     cp_async_wait_all();
     __syncthreads();
@@ -211,7 +219,8 @@ __global__ void __launch_bounds__(H) mlp_bwd_kernel(const uint16_t* __restrict__
         const float w = bf(W[off_w(4) + i]);
         const float* g = gbuf + (size_t)3 * B * H;
 #pragma unroll
-        for (int b = 0; b < TB; ++b) {
+        for (int k = 0; k < SPT; ++k) {
+            const int b = bs + k;
             float d = 0.f;
             if (b < nb) {
                 d = dy[b] * w * g[(size_t)(b0 + b) * H + i];
@@ -226,27 +235,28 @@ __global__ void __launch_bounds__(H) mlp_bwd_kernel(const uint16_t* __restrict__
         float(*nxt)[H] = dn[(3 - l) & 1];
         const uint16_t* Wn = ws + (size_t)l * H * H;  // W_{l+1}[o][i]: layer l -> l + 1
         const float* g = gbuf + (size_t)l * B * H;
-        float acc[TB], gv[TB];
+        float acc[SPT], gv[SPT];
 #pragma unroll
-        for (int b = 0; b < TB; ++b) {
-            acc[b] = 0.f;
-            gv[b] = b < nb ? g[(size_t)(b0 + b) * H + i] : 0.f;  // in flight during the sum
+        for (int k = 0; k < SPT; ++k) {
+            acc[k] = 0.f;
+            gv[k] = bs + k < nb ? g[(size_t)(b0 + bs + k) * H + i] : 0.f;  // in flight during the sum
         }
-#pragma unroll 2
+#pragma unroll 4
         for (int o = 0; o < H; o += 4) {
             const float w0 = bf(Wn[o * H + i]), w1 = bf(Wn[(o + 1) * H + i]),
                         w2 = bf(Wn[(o + 2) * H + i]), w3 = bf(Wn[(o + 3) * H + i]);
 #pragma unroll
-            for (int b = 0; b < TB; ++b) {
-                const float4 d = *reinterpret_cast<const float4*>(&cur[b][o]);
-                acc[b] = fmaf(d.w, w3, fmaf(d.z, w2, fmaf(d.y, w1, fmaf(d.x, w0, acc[b]))));
+            for (int k = 0; k < SPT; ++k) {
+                const float4 d = *reinterpret_cast<const float4*>(&cur[bs + k][o]);
+                acc[k] = fmaf(d.w, w3, fmaf(d.z, w2, fmaf(d.y, w1, fmaf(d.x, w0, acc[k]))));
             }
         }
 #pragma unroll
-        for (int b = 0; b < TB; ++b) {
+        for (int k = 0; k < SPT; ++k) {
+            const int b = bs + k;
             float d = 0.f;
             if (b < nb) {
-                d = acc[b] * gv[b];
+                d = acc[k] * gv[k];
                 dbuf[(size_t)l * B * H + (size_t)(b0 + b) * H + i] = d;
             }
             nxt[b][i] = d;
@@ -439,8 +449,9 @@ __global__ void __launch_bounds__(256) mlp_pack_kernel(const float* __restrict__
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
 // Samples per forward/backward CTA: 8 while that leaves SMs idle, else 32 (fewer
-// re-stagings of the weights per sample).
-constexpr int kSmallTB = 8, kLargeTB = 32;
+// re-stagings of the weights per sample); either way four groups of 128 threads.
+constexpr int kSmallTB = 8, kLargeTB = 32, kGroups = 4;
+constexpr int kSmallSPT = kSmallTB / kGroups, kLargeSPT = kLargeTB / kGroups;
 bool use_large_tb(int B) { return B >= 152 * kLargeTB; }
 
 cudaError_t set_smem_attrs() {
@@ -449,10 +460,10 @@ cudaError_t set_smem_attrs() {
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     };
-    set((const void*)mlp_fwd_kernel<kSmallTB>, fwd_smem<kSmallTB>());
-    set((const void*)mlp_fwd_kernel<kLargeTB>, fwd_smem<kLargeTB>());
-    set((const void*)mlp_bwd_kernel<kSmallTB>, bwd_smem<kSmallTB>());
-    set((const void*)mlp_bwd_kernel<kLargeTB>, bwd_smem<kLargeTB>());
+    set((const void*)mlp_fwd_kernel<kSmallTB, kSmallSPT>, fwd_smem<kSmallTB>());
+    set((const void*)mlp_fwd_kernel<kLargeTB, kLargeSPT>, fwd_smem<kLargeTB>());
+    set((const void*)mlp_bwd_kernel<kSmallTB, kSmallSPT>, bwd_smem<kSmallTB>());
+    set((const void*)mlp_bwd_kernel<kLargeTB, kLargeSPT>, bwd_smem<kLargeTB>());
     set((const void*)mlp_wgrad_kernel, kWgradSmem);
     return e;
 }
@@ -460,11 +471,11 @@ cudaError_t set_smem_attrs() {
 void launch_forward(const uint16_t* W, const float* x, int B, float* abuf, float* gbuf, float* y,
                     cudaStream_t s) {
     if (use_large_tb(B))
-        mlp_fwd_kernel<kLargeTB><<<(B + kLargeTB - 1) / kLargeTB, H, fwd_smem<kLargeTB>(), s>>>(
-            W, x, B, abuf, gbuf, y);
+        mlp_fwd_kernel<kLargeTB, kLargeSPT><<<(B + kLargeTB - 1) / kLargeTB, H * kGroups,
+                                              fwd_smem<kLargeTB>(), s>>>(W, x, B, abuf, gbuf, y);
     else
-        mlp_fwd_kernel<kSmallTB><<<(B + kSmallTB - 1) / kSmallTB, H, fwd_smem<kSmallTB>(), s>>>(
-            W, x, B, abuf, gbuf, y);
+        mlp_fwd_kernel<kSmallTB, kSmallSPT><<<(B + kSmallTB - 1) / kSmallTB, H * kGroups,
+                                              fwd_smem<kSmallTB>(), s>>>(W, x, B, abuf, gbuf, y);
 }
 
 struct TrainBuffers {
@@ -491,11 +502,13 @@ void launch_gradient(const uint16_t* W, const float* x, const float* target, int
                      const TrainBuffers& t, cudaStream_t s) {
     launch_forward(W, x, B, t.abuf, t.gbuf, t.y, s);
     if (use_large_tb(B))
-        mlp_bwd_kernel<kLargeTB><<<(B + kLargeTB - 1) / kLargeTB, H, bwd_smem<kLargeTB>(), s>>>(
-            W, t.gbuf, t.y, target, B, t.dbuf, t.dout);
+        mlp_bwd_kernel<kLargeTB, kLargeSPT><<<(B + kLargeTB - 1) / kLargeTB, H * kGroups,
+                                              bwd_smem<kLargeTB>(), s>>>(W, t.gbuf, t.y, target, B,
+                                                                         t.dbuf, t.dout);
     else
-        mlp_bwd_kernel<kSmallTB><<<(B + kSmallTB - 1) / kSmallTB, H, bwd_smem<kSmallTB>(), s>>>(
-            W, t.gbuf, t.y, target, B, t.dbuf, t.dout);
+        mlp_bwd_kernel<kSmallTB, kSmallSPT><<<(B + kSmallTB - 1) / kSmallTB, H * kGroups,
+                                              bwd_smem<kSmallTB>(), s>>>(W, t.gbuf, t.y, target, B,
+                                                                         t.dbuf, t.dout);
     mlp_wgrad_kernel<<<dim3(WG_TASKS, n_chunks(B)), WG_THREADS, kWgradSmem, s>>>(
         x, t.abuf, t.dbuf, t.dout, t.y, target, B, t.part);
 }
