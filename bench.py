@@ -40,9 +40,10 @@ MUFU_EX2_PER_CLK_SM = 32
 MUFU_SINCOS_PER_CLK_SM = 16
 GB300_SMS = 152
 GB300_MAX_MHZ = 2070.0
-# DRAM bytes per launch of field_mixed_kernel<2,4,false> on airy_large from one ncu capture
-# (profiles/field_mixed_kernel_airy_large.md) at 26 beamlet splits.  The reads are the
-# record tiles; the writes are the split partial fields, which scale with the split count.
+# DRAM bytes per launch of the 2 x 8 row-pair field kernel on airy_large from one ncu
+# capture (profiles/field_mixed_pair_smem_kernel_airy_large.md) at 90 beamlet splits.  The
+# reads are the record tiles; the writes are the split partial fields, which scale with
+# the split count.
 FIELD_MIXED_NCU = {"kernel": "field_mixed_pair_smem_kernel<8, false> (2x8 row pairs)",
                    "read": 3.343104e6, "write": 128.155392e6, "splits": 90, "rows": 2, "cols": 8,
                    "scheme": 1}
@@ -527,14 +528,7 @@ def run_ours(args, world, rank, local):
         t_sur = time.perf_counter() - t0
         n_sur = sur.evals_to_reach(target)
         rnd = S.random_search(budget=len(sur.scores))
-        net = S.MLP()
-        xs = np.random.default_rng(0).normal(size=(1024, 3)).astype(np.float32)
-        net.fit(xs, xs[:, 0], steps=5)
-        torch.cuda.synchronize()
-        a = time.perf_counter()
-        net.fit(xs, xs[:, 0], steps=100)
-        torch.cuda.synchronize()
-        step_us = (time.perf_counter() - a) / 100 * 1e6
+        step_us = S.time_training(1024, 100)
         # ablation over 8 seeds, both searches starting from the same 32 random draws and
         # spending 32 evaluations per round: the contract's 1 % target (flat here: any
         # 256-across set with OF < 1.45 meets it) and a 0.01 % target

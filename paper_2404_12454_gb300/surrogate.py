@@ -222,3 +222,33 @@ def compare_with_random(target: float, seeds: Sequence[int], n_init: int = 32,
                             seed=sd)
         out["random"].append(rnd.evals_to_reach(target))
     return out
+
+
+def time_training(batch: int = 1024, steps: int = 100, seed: int = 0) -> float:
+    """Microseconds per full-batch training step of a fresh network on `batch` synthetic
+    samples (inputs ~ N(0, 1), target = first input), after 5 untimed steps."""
+    import time
+
+    import torch
+    net = MLP()
+    xs = np.random.default_rng(seed).normal(size=(batch, 3)).astype(np.float32)
+    net.fit(xs, xs[:, 0], steps=5)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    net.fit(xs, xs[:, 0], steps=steps)
+    torch.cuda.synchronize()
+    return (time.perf_counter() - t0) / steps * 1e6
+
+
+if __name__ == "__main__":
+    import argparse
+    import json
+
+    ap = argparse.ArgumentParser(description="time the surrogate network's training step")
+    ap.add_argument("--batch", type=int, default=1024)
+    ap.add_argument("--steps", type=int, default=100)
+    a = ap.parse_args()
+    from . import build
+    build.build()
+    print(json.dumps({"batch": a.batch, "steps": a.steps,
+                      "us_per_step": time_training(a.batch, a.steps)}))
