@@ -421,6 +421,7 @@ gbd_status gbd_field_fixed_scratch(const gbd_beamlet* beamlets, int32_t n, doubl
                                    const gbd_detector* detector, int32_t precision,
                                    void* scratch, size_t scratch_bytes, void* out,
                                    cudaStream_t stream) {
+    GBD_NVTX_RANGE("gbd_field_fixed_scratch");
     gbd_status st = check_field_args(beamlets, n, wavelength, detector, precision, scratch, out);
     if (st != GBD_OK) return st;
     gbd_shape sh = stored_shape(precision, detector);
@@ -480,6 +481,7 @@ gbd_status gbd_set_wait_limit(uint32_t spins) {
 
 gbd_status gbd_trace(const gbd_system* system, const gbd_pupil* pupil, double overlap_factor,
                      double waist_ratio, gbd_beamlet* out, int32_t capacity, void* stream) {
+    GBD_NVTX_RANGE("gbd_trace");
     gbd_status st = check_system(system);
     if (st != GBD_OK) return st;
     if ((st = check_pupil(pupil)) != GBD_OK) return st;
@@ -507,6 +509,7 @@ gbd_status gbd_trace(const gbd_system* system, const gbd_pupil* pupil, double ov
 gbd_status gbd_trace_mirrors(const gbd_mirror_system* system, const gbd_pupil* pupil,
                              double overlap_factor, double waist_ratio, gbd_beamlet* out,
                              int32_t capacity, void* stream) {
+    GBD_NVTX_RANGE("gbd_trace_mirrors");
     if (!system) return fail(GBD_EINVAL, "system is NULL");
     gbd_status st = check_pupil(pupil);
     if (st != GBD_OK) return st;
@@ -565,6 +568,7 @@ size_t gbd_project_bytes(int32_t n_beamlets, int32_t precision) {
 gbd_status gbd_project(const gbd_beamlet* beamlets, int32_t n_beamlets, double wavelength,
                        const gbd_detector* detector, int32_t precision, void* coeffs,
                        uint32_t* wide_flag, void* stream) {
+    GBD_NVTX_RANGE("gbd_project");
     gbd_status st = check_field_args(beamlets, n_beamlets, wavelength, detector, precision,
                                      coeffs, coeffs ? coeffs : (void*)16);
     if (st != GBD_OK) return st;
@@ -587,6 +591,7 @@ size_t gbd_field_workspace_bytes(int32_t n_beamlets, const gbd_detector* detecto
 gbd_status gbd_field(const gbd_beamlet* beamlets, int32_t n_beamlets, double wavelength,
                      const gbd_detector* detector, int32_t precision, void* workspace,
                      size_t workspace_bytes, void* field_out, void* stream) {
+    GBD_NVTX_RANGE("gbd_field");
     gbd_status st = check_field_args(beamlets, n_beamlets, wavelength, detector, precision,
                                      workspace, field_out);
     if (st != GBD_OK) return st;
@@ -633,6 +638,7 @@ gbd_status gbd_autotune_field(const gbd_beamlet* beamlets, int32_t n_beamlets, d
                               const gbd_detector* detector, int32_t precision, void* workspace,
                               size_t workspace_bytes, void* field_out, void* stream,
                               gbd_shape* best) {
+    GBD_NVTX_RANGE("gbd_autotune_field");
     gbd_status st = check_field_args(beamlets, n_beamlets, wavelength, detector, precision,
                                      workspace, field_out);
     if (st != GBD_OK) return st;
@@ -747,6 +753,7 @@ size_t gbd_psf_workspace_bytes(const gbd_pupil* pupil, const gbd_detector* detec
 gbd_status gbd_psf(const gbd_system* system, const gbd_pupil* pupil, double overlap_factor,
                    double waist_ratio, const gbd_detector* detector, int32_t precision,
                    void* workspace, size_t workspace_bytes, void* host_field_out, void* stream) {
+    GBD_NVTX_RANGE("gbd_psf");
     gbd_status st = check_detector(detector);
     if (st != GBD_OK) return st;
     if ((st = check_pupil(pupil)) != GBD_OK) return st;
@@ -798,6 +805,7 @@ size_t gbd_field_point_workspace_bytes(int32_t n_beamlets, const gbd_detector* d
 gbd_status gbd_field_point(const gbd_beamlet* beamlets, int32_t n_beamlets, double wavelength,
                            const gbd_detector* detector, void* workspace, size_t workspace_bytes,
                            void* field_out, void* stream) {
+    GBD_NVTX_RANGE("gbd_field_point");
     gbd_status st = check_field_args(beamlets, n_beamlets, wavelength, detector, GBD_PREC_F64,
                                      workspace, field_out);
     if (st != GBD_OK) return st;

@@ -2,11 +2,23 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "gbd.h"
 
 namespace gbd {
+
+// Named NVTX range over the host side of an API call, so that profiler timelines group
+// each call's launches under its name (header-only NVTX v3: without an attached tool a
+// push/pop pair costs a few nanoseconds).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define GBD_NVTX_RANGE(name) ::gbd::NvtxRange gbd_nvtx_range_(name)
 
 // Beamlets per shared-memory tile of the field kernels.  A mixed-precision tile is
 // 64 x 16 floats = 4 KB, an FP64 tile 64 x 16 doubles = 8 KB; both are one contiguous

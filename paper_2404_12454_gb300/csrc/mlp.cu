@@ -567,6 +567,7 @@ gbd_status gbd_mlp_pack(const float* master, uint16_t* weights, void* stream) {
 
 gbd_status gbd_mlp_forward(const uint16_t* weights, const float* x, int32_t batch, float* y,
                            void* stream) {
+    GBD_NVTX_RANGE("gbd_mlp_forward");
     if (!weights || !x || !y) return gbd_set_error(GBD_EINVAL, "NULL buffer");
     if (batch < 1 || batch > (1 << 24)) return gbd_set_error(GBD_EINVAL, "batch out of range");
     if (reinterpret_cast<uintptr_t>(weights) & 15u)
@@ -580,6 +581,7 @@ gbd_status gbd_mlp_forward(const uint16_t* weights, const float* x, int32_t batc
 gbd_status gbd_mlp_grad(const uint16_t* weights, const float* x, const float* target,
                         int32_t batch, float* grad, float* loss, void* workspace, size_t bytes,
                         void* stream) {
+    GBD_NVTX_RANGE("gbd_mlp_grad");
     if (!grad) return gbd_set_error(GBD_EINVAL, "NULL buffer");
     gbd_status st = check_train(weights, x, target, batch, workspace, bytes);
     if (st != GBD_OK) return st;
@@ -595,6 +597,7 @@ gbd_status gbd_mlp_grad(const uint16_t* weights, const float* x, const float* ta
 
 gbd_status gbd_mlp_adam(float* master, uint16_t* weights, float* m, float* v, const float* grad,
                         float lr, float beta1, float beta2, float eps, int32_t step, void* stream) {
+    GBD_NVTX_RANGE("gbd_mlp_adam");
     if (!master || !weights || !m || !v || !grad) return gbd_set_error(GBD_EINVAL, "NULL buffer");
     gbd_status st = check_adam(lr, beta1, beta2, eps, step);
     if (st != GBD_OK) return st;
@@ -607,6 +610,7 @@ gbd_status gbd_mlp_train(float* master, uint16_t* weights, float* m, float* v, c
                          const float* target, int32_t batch, float lr, float beta1, float beta2,
                          float eps, int32_t first_step, int32_t steps, float* loss,
                          void* workspace, size_t bytes, void* stream) {
+    GBD_NVTX_RANGE("gbd_mlp_train");
     if (!master || !m || !v) return gbd_set_error(GBD_EINVAL, "NULL buffer");
     if (steps < 0 || first_step > INT32_MAX - steps)
         return gbd_set_error(GBD_EINVAL, "step count out of range");

@@ -437,6 +437,7 @@ gbd_status gbd_sweep_plan_create(const gbd_system* system, double diameter, cons
                                  const double* overlap_factor, const double* waist_ratio,
                                  int32_t n_instances, const gbd_detector* detector,
                                  const gbd_shape* shape, gbd_sweep_plan** plan) {
+    GBD_NVTX_RANGE("gbd_sweep_plan_create");
     if (!plan) return gbd_set_error(GBD_EINVAL, "plan is NULL");
     *plan = nullptr;
     gbd_status st = gbd_check_system(system);
@@ -563,6 +564,7 @@ gbd_status gbd_sweep_info(const gbd_sweep_plan* plan, double* evals, int64_t* be
 }
 
 gbd_status gbd_sweep_bind(gbd_sweep_plan* P, void* workspace, size_t bytes, void* stream) {
+    GBD_NVTX_RANGE("gbd_sweep_bind");
     if (!P) return gbd_set_error(GBD_EINVAL, "plan is NULL");
     if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255u))
         return gbd_set_error(GBD_EINVAL, "workspace must be non-NULL and 256-byte aligned");
@@ -604,12 +606,14 @@ gbd_status gbd_sweep_bind(gbd_sweep_plan* P, void* workspace, size_t bytes, void
 }
 
 gbd_status gbd_sweep_run(gbd_sweep_plan* P, double* scores, void* stream) {
+    GBD_NVTX_RANGE("gbd_sweep_run");
     if (!P || !P->ws) return gbd_set_error(GBD_EINVAL, "plan is NULL or not bound");
     if (!scores) return gbd_set_error(GBD_EINVAL, "scores is NULL");
     return sweep_enqueue(P, scores, static_cast<cudaStream_t>(stream));
 }
 
 gbd_status gbd_sweep_run_graph(gbd_sweep_plan* P, double* scores, void* stream) {
+    GBD_NVTX_RANGE("gbd_sweep_run_graph");
     if (!P || !P->ws) return gbd_set_error(GBD_EINVAL, "plan is NULL or not bound");
     if (!scores) return gbd_set_error(GBD_EINVAL, "scores is NULL");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
