@@ -108,7 +108,9 @@ __global__ void __launch_bounds__(kThreads, 2)
 
 // Row pairs on 2 x CB pixels per thread with the compensation pairs in shared memory
 // (wider blocks amortise the per-beamlet row terms over more columns).  Dynamic shared
-// memory: the kStages record stages, then 2 CB x kThreads float4 (hi, lo) slots.
+// memory: the kStages record stages, then 2 CB x kThreads float4 (hi, lo) slots, then
+// (narrow instantiation) each warp's row terms of the current tile, kPairRowF4 x kTile
+// float4 per warp.
 template <int CB, bool WIDE>
 __global__ void __launch_bounds__(kThreads, 2)
     field_mixed_pair_smem_kernel(const float4* __restrict__ coef, int n_tiles, int tiles_per_split,
@@ -125,6 +127,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     __shared__ int flag;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float4* ent = comp + 2 * CB * kThreads + warp * (gbd::kPairRowF4 * gbd::kTile);
 #pragma unroll
     for (int m = 0; m < 2 * CB; ++m) comp[m * kThreads + tid] = make_float4(0.f, 0.f, 0.f, 0.f);
     const int t0 = blockIdx.z * tiles_per_split;
@@ -153,7 +156,14 @@ __global__ void __launch_bounds__(kThreads, 2)
             ok = false;
             break;
         }
-        gbd::mixed_tile_pair<CB, WIDE>(ts.tile(k), colf, rowf, acc);
+        if constexpr (WIDE) {
+            gbd::mixed_tile_pair<CB, WIDE>(ts.tile(k), colf, rowf, acc);
+        } else {
+            __syncwarp();  // every lane is done with the previous tile's row terms
+            gbd::mixed_pair_rows(ts.tile(k), rowf, ent, lane);
+            __syncwarp();
+            gbd::mixed_tile_pair_rows<CB>(ts.tile(k), ent, colf, acc);
+        }
         gbd::mixed_fold_smem<2, CB>(acc, comp, tid);
         if (!ts.release(k, lane, warp, spins)) {
             ok = false;
@@ -185,7 +195,8 @@ __global__ void __launch_bounds__(kThreads, 2)
 
 template <int CB>
 constexpr size_t pair_smem_bytes() {
-    return (size_t)kStages * gbd::kMixedTileBytes + (size_t)2 * CB * kThreads * sizeof(float4);
+    return (size_t)kStages * gbd::kMixedTileBytes + (size_t)2 * CB * kThreads * sizeof(float4) +
+           (size_t)kWarps * gbd::kPairRowF4 * gbd::kTile * sizeof(float4);
 }
 
 template <int RB, int CB>

@@ -232,6 +232,88 @@ __device__ __forceinline__ void mixed_tile_pair(const float4* __restrict__ st,
     }
 }
 
+// Row terms of a tile for the narrow row-pair evaluation.  Within a warp every lane shares
+// the first row v (the lanes differ only in their columns), so the parts of the
+// per-beamlet setup that do not depend on the column are computed once per warp and tile:
+// lane l takes beamlets l and l + 32 and stores, SoA over the tile's 64 beamlets,
+//   ent[0][b] = (ra, rp, sa, sp): log2-amplitude / phase of the row at tu = 0 and their
+//               tu-slopes (the quadratic form with tv = v - v_c substituted),
+//   ent[1][b] = (32 sa + 1024 a_uu, 32 sp, 8 (a_v + a_vv (2 tv + 8)), 8 (p_v + p_vv (2 tv + 8))),
+//   ent[2][b] = (64 a_uu, 64 p_uu, 8 a_uv, 8 p_uv),
+// so that mixed_tile_pair_rows forms the first-row amplitude and phase, the amplitude's
+// first ratio rho, the phase step d1 and the 8-row step factor's exponent with one or two
+// FFMA each in the thread's first column tu0.  kPairRowF4 float4 per beamlet and warp.
+constexpr int kPairRowF4 = 3;
+__device__ __forceinline__ void mixed_pair_rows(const float4* __restrict__ st, float rowf,
+                                                float4* __restrict__ ent, int lane) {
+#pragma unroll
+    for (int h = 0; h < kTile / 32; ++h) {
+        const int b = lane + 32 * h;
+        const float4 q0 = st[b];
+        const float4 q1 = st[kTile + b];
+        const float4 q2 = st[2 * kTile + b];
+        const float4 q3 = st[3 * kTile + b];
+        const float tv = rowf - q0.y;
+        const float ra = fmaf(tv, fmaf(q3.x, tv, q1.z), q0.z);
+        const float rp = fmaf(tv, fmaf(q3.y, tv, q1.w), q0.w);
+        const float sa = fmaf(q2.z, tv, q1.x);
+        const float sp = fmaf(q2.w, tv, q1.y);
+        const float w = fmaf(2.0f, tv, 8.0f);
+        ent[b] = make_float4(ra, rp, sa, sp);
+        ent[kTile + b] = make_float4(fmaf(1024.0f, q2.x, 32.0f * sa), 32.0f * sp,
+                                     8.0f * fmaf(q3.x, w, q1.z), 8.0f * fmaf(q3.y, w, q1.w));
+        ent[2 * kTile + b] = make_float4(64.0f * q2.x, 64.0f * q2.y, 8.0f * q2.z, 8.0f * q2.w);
+    }
+}
+
+// The narrow instantiation of mixed_tile_pair (same arithmetic, regrouped) on the row
+// terms of mixed_pair_rows: per beamlet and thread only the column-dependent setup is
+// left (about 27 instructions instead of 43 for the 2 x CB pixels).
+template <int CB>
+__device__ __forceinline__ void mixed_tile_pair_rows(const float4* __restrict__ st,
+                                                     const float4* __restrict__ ent,
+                                                     const float (&colf)[CB],
+                                                     float2 (&acc)[2][CB]) {
+    const float* stf = reinterpret_cast<const float*>(st);
+#pragma unroll 1
+    for (int b = 0; b < kTile; ++b) {
+        const float uc = stf[4 * b];                                               // q0.x
+        const float2 quu = reinterpret_cast<const float2*>(st + 2 * kTile + b)[0];  // q2.xy
+        const float2 T = reinterpret_cast<const float2*>(st + 3 * kTile + b)[1];    // q3.zw
+        const float4 e0 = ent[b];
+        const float4 e1 = ent[kTile + b];
+        const float4 e2 = ent[2 * kTile + b];
+        const float tu0 = colf[0] - uc;
+        const float ga = fmaf(e2.z, tu0, e1.z);
+        const float gp = fmaf(e2.w, tu0, e1.w);  // within 64 rad: the field is not wide
+        const float x0 = fmaf(tu0, fmaf(quu.y, tu0, e0.w), e0.y);
+        const float d1 = fmaf(e2.y, tu0, e1.y);
+        const float gm = mufu_ex2(ga);
+        float rx = gm * mufu_cos(gp), ry = gm * mufu_sin(gp);
+        float amp = mufu_ex2(fmaf(tu0, fmaf(quu.x, tu0, e0.z), e0.x));
+        float rho = mufu_ex2(fmaf(e2.x, tu0, e1.x));
+        const float sig = mufu_ex2(2048.0f * quu.x);
+#pragma unroll
+        for (int c = 0; c < CB; ++c) {
+            // first-row phase x0 + c d1 + 1024 c^2 p_uu about the thread's first column
+            const float x = c == 0 ? x0 : fmaf((float)(1024 * c * c), quu.y, fmaf((float)c, d1, x0));
+            const float cs = mufu_cos(x), sn = mufu_sin(x);
+            acc[0][c].x = fmaf(amp, cs, acc[0][c].x);
+            acc[0][c].y = fmaf(amp, sn, acc[0][c].y);
+            const float wx = amp * rx, wy = amp * ry;
+            acc[1][c].x = fmaf(cs, wx, fmaf(-sn, wy, acc[1][c].x));
+            acc[1][c].y = fmaf(cs, wy, fmaf(sn, wx, acc[1][c].y));
+            if (c + 1 < CB) {
+                const float nx = fmaf(rx, T.x, -ry * T.y);
+                ry = fmaf(rx, T.y, ry * T.x);
+                rx = nx;
+                amp *= rho;
+                rho *= sig;
+            }
+        }
+    }
+}
+
 // A compensated (hi, lo) sum rounded once to FP32 (the split partial written to memory).
 __device__ __forceinline__ float2 round_pair(float2 hi, float2 lo) {
     return make_float2((float)((double)hi.x + (double)lo.x), (float)((double)hi.y + (double)lo.y));

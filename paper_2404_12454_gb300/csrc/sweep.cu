@@ -75,6 +75,8 @@ __global__ void __launch_bounds__(kThreads, 2)
     extern __shared__ __align__(128) float4 sweep_dyn[];
     float4(*stage)[kTileF4] = reinterpret_cast<float4(*)[kTileF4]>(sweep_dyn);
     float4* comp = sweep_dyn + kStages * kTileF4;  // SMEM: [RB * CB][kThreads]
+    // SMEM: then each warp's row terms of the current tile (narrow row pairs)
+    float4* ent = comp + RB * CB * kThreads + (threadIdx.x >> 5) * (gbd::kPairRowF4 * gbd::kTile);
     __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
     __shared__ int flag, s_item;
     __shared__ double red[kWarps][kMaxRegions][4];
@@ -117,7 +119,12 @@ __global__ void __launch_bounds__(kThreads, 2)
                 ok = false;
                 break;
             }
-            if constexpr (PAIR)
+            if constexpr (PAIR && SMEM && !WIDE) {
+                __syncwarp();  // every lane is done with the previous tile's row terms
+                gbd::mixed_pair_rows(ts.tile(k), rowf[0], ent, lane);
+                __syncwarp();
+                gbd::mixed_tile_pair_rows<CB>(ts.tile(k), ent, colf, acc);
+            } else if constexpr (PAIR)
                 gbd::mixed_tile_pair<CB, WIDE>(ts.tile(k), colf, rowf[0], acc);
             else
                 gbd::mixed_tile<RB, CB, WIDE>(ts.tile(k), colf, rowf, acc);
@@ -239,7 +246,9 @@ typedef cudaError_t (*sweep_launch_fn)(dim3, cudaStream_t, const float4*, const 
 
 constexpr size_t sweep_smem(int rb, int cb, bool smem) {
     return (size_t)kStages * gbd::kMixedTileBytes +
-           (smem ? (size_t)rb * cb * kThreads * sizeof(float4) : 0);
+           (smem ? (size_t)rb * cb * kThreads * sizeof(float4) +
+                       (size_t)kWarps * gbd::kPairRowF4 * gbd::kTile * sizeof(float4)
+                 : 0);
 }
 
 template <int RB, int CB, bool WIDE, bool PAIR, bool SMEM>
