@@ -45,7 +45,7 @@ GB300_MAX_MHZ = 2070.0
 # reads are the record tiles; the writes are the split partial fields, which scale with
 # the split count.
 FIELD_MIXED_NCU = {"kernel": "field_mixed_pair_smem_kernel<8, false> (2x8 row pairs)",
-                   "read": 3.343104e6, "write": 128.155392e6, "splits": 90, "rows": 2, "cols": 8,
+                   "read": 3.38944e6, "write": 127.755776e6, "splits": 90, "rows": 2, "cols": 8,
                    "scheme": 1}
 
 
