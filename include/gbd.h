@@ -204,9 +204,10 @@ gbd_status gbd_field(const gbd_beamlet* beamlets, int32_t n_beamlets, double wav
  *          beamlet's phase can exceed 256 rad on the detector (gbd_field then reduces every
  *          per-pixel phase exactly before sin/cos), bit 1 if some beamlet's log2
  *          amplitude can change by more than 64 over 8 rows (the row-pair scheme then falls
- *          back to direct evaluation) and bit 2 if it can change by more than 64 over 8
+ *          back to direct evaluation), bit 2 if it can change by more than 64 over 8
  *          columns 32 apart (the row-pair scheme then evaluates each amplitude instead of
- *          carrying it along the row).
+ *          carrying it along the row) and bit 3 if some beamlet's T is not exactly 1 (the
+ *          field has a uv term; without one the row-pair kernels leave out T's update).
  *   F64:   16 doubles per beamlet [tile][field f = 0..7][b % 64][2 doubles], same order, the
  *          phase in turns (phase / 2 pi), field 7 = S = exp of twice the uu coefficient as
  *          a complex number (re, im), the second ratio of a row recurrence; wide_flag is

@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 // memory: the kStages record stages, then 2 CB x kThreads float4 (hi, lo) slots, then
 // (narrow instantiation) each warp's row terms of the current tile, kPairRowF4 x kTile
 // float4 per warp.
-template <int CB, bool WIDE>
+template <int CB, bool WIDE, bool CROSS = true>
 __global__ void __launch_bounds__(kThreads, 2)
     field_mixed_pair_smem_kernel(const float4* __restrict__ coef, int n_tiles, int tiles_per_split,
                                  int nx, int ny, float2* __restrict__ partial,
@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             __syncwarp();  // every lane is done with the previous tile's row terms
             gbd::mixed_pair_rows(ts.tile(k), rowf, ent, lane);
             __syncwarp();
-            gbd::mixed_tile_pair_rows<CB>(ts.tile(k), ent, colf, acc);
+            gbd::mixed_tile_pair_rows<CB, CROSS>(ts.tile(k), ent, colf, acc);
         }
         gbd::mixed_fold_smem<2, CB>(acc, comp, tid);
         if (!ts.release(k, lane, warp, spins)) {
@@ -582,23 +582,28 @@ cudaError_t launch_mixed_pair_smem(const void* coeffs, int n_tiles, const gbd_pr
                                    const unsigned* flags, uint32_t spins, cudaStream_t s) {
     float2* partial = static_cast<float2*>(partial_v);
     using gbd::kFlagColSteep;
+    using gbd::kFlagCross;
     using gbd::kFlagSteep;
     using gbd::kFlagWide;
     constexpr unsigned kBoth = kFlagWide | kFlagSteep, kAll = kBoth | kFlagColSteep;
     constexpr size_t smem = pair_smem_bytes<CB>();
-    cudaError_t e = cudaFuncSetAttribute(field_mixed_pair_smem_kernel<CB, false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(field_mixed_pair_smem_kernel<CB, true>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaSuccess;
+    for (const void* fn : {(const void*)field_mixed_pair_smem_kernel<CB, false, false>,
+                           (const void*)field_mixed_pair_smem_kernel<CB, false, true>,
+                           (const void*)field_mixed_pair_smem_kernel<CB, true, true>})
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((p.nx + 32 * CB - 1) / (32 * CB), (p.ny + 15) / 16, L.splits);
     dim3 grid24((p.nx + 127) / 128, (p.ny + 15) / 16, L.splits);
     const float4* c = static_cast<const float4*>(coeffs);
     const int tps = L.tiles_per_split;
-    // exactly one runs: narrow, then wide (or column-steep), then the steep fallbacks
-    field_mixed_pair_smem_kernel<CB, false><<<grid, kThreads, smem, s>>>(
-        c, n_tiles, tps, p.nx, p.ny, partial, flags, kAll, 0u, 0u, spins);
+    // exactly one runs: narrow without and with a uv term, then wide (or column-steep),
+    // then the steep fallbacks
+    field_mixed_pair_smem_kernel<CB, false, false><<<grid, kThreads, smem, s>>>(
+        c, n_tiles, tps, p.nx, p.ny, partial, flags, kAll | kFlagCross, 0u, 0u, spins);
+    field_mixed_pair_smem_kernel<CB, false, true><<<grid, kThreads, smem, s>>>(
+        c, n_tiles, tps, p.nx, p.ny, partial, flags, kAll, 0u, kFlagCross, spins);
     field_mixed_pair_smem_kernel<CB, true><<<grid, kThreads, smem, s>>>(
         c, n_tiles, tps, p.nx, p.ny, partial, flags, kFlagSteep, 0u, kFlagWide | kFlagColSteep,
         spins);
@@ -628,7 +633,7 @@ const ShapeEntry kMixedShapes[] = {
     {2, 2, GBD_SCHEME_ROW_PAIR, launch_mixed_pair<2>, (const void*)field_mixed_kernel<2, 2, false, true>},
     {2, 4, GBD_SCHEME_ROW_PAIR, launch_mixed_pair<4>, (const void*)field_mixed_kernel<2, 4, false, true>},
     {2, 8, GBD_SCHEME_ROW_PAIR, launch_mixed_pair_smem<8>,
-     (const void*)field_mixed_pair_smem_kernel<8, false>, pair_smem_bytes<8>()},
+     (const void*)field_mixed_pair_smem_kernel<8, false, false>, pair_smem_bytes<8>()},
 };
 // (1,2), (2,2): every pixel evaluated directly (columns 32 apart); (1,8), (1,16), (2,8),
 // (1,32): contiguous row segments advanced by complex multiplies.

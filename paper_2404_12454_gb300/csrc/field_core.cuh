@@ -268,8 +268,10 @@ __device__ __forceinline__ void mixed_pair_rows(const float4* __restrict__ st, f
 
 // The narrow instantiation of mixed_tile_pair (same arithmetic, regrouped) on the row
 // terms of mixed_pair_rows: per beamlet and thread only the column-dependent setup is
-// left (about 27 instructions instead of 43 for the 2 x CB pixels).
-template <int CB>
+// left (about 27 instructions instead of 43 for the 2 x CB pixels).  CROSS = false is
+// for fields without a uv term (the projection's cross flag clear): there every T is
+// exactly 1, R(u + 32) = R(u) T is the identity, and its update is left out.
+template <int CB, bool CROSS>
 __device__ __forceinline__ void mixed_tile_pair_rows(const float4* __restrict__ st,
                                                      const float4* __restrict__ ent,
                                                      const float (&colf)[CB],
@@ -304,9 +306,11 @@ __device__ __forceinline__ void mixed_tile_pair_rows(const float4* __restrict__ 
             acc[1][c].x = fmaf(cs, wx, fmaf(-sn, wy, acc[1][c].x));
             acc[1][c].y = fmaf(cs, wy, fmaf(sn, wx, acc[1][c].y));
             if (c + 1 < CB) {
-                const float nx = fmaf(rx, T.x, -ry * T.y);
-                ry = fmaf(rx, T.y, ry * T.x);
-                rx = nx;
+                if (CROSS) {
+                    const float nx = fmaf(rx, T.x, -ry * T.y);
+                    ry = fmaf(rx, T.y, ry * T.x);
+                    rx = nx;
+                }
                 amp *= rho;
                 rho *= sig;
             }

@@ -39,6 +39,7 @@ constexpr unsigned kStatusTimeout = 1u;
 constexpr unsigned kFlagWide = 1u;   // some phase may exceed kWidePhase on the detector
 constexpr unsigned kFlagSteep = 2u;  // the row-pair recurrence could leave FP32 range
 constexpr unsigned kFlagColSteep = 4u;  // so could an amplitude recurrence along a row
+constexpr unsigned kFlagCross = 8u;     // some beamlet has a uv term (column factor T != 1)
 
 // ----------------------------------------------------------------- PTX wrappers --
 

@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(256) airy_table_kernel(int nx, int ny, double 
 // WIDE, PAIR: as in field_mixed_kernel (several instantiations are launched; each returns
 // at once unless the projection's flag word masked by `mask` equals `want`).  SMEM keeps
 // the compensation pairs in dynamic shared memory after the record stages (2 x 8 blocks).
-template <int RB, int CB, bool WIDE, bool PAIR, bool SMEM>
+template <int RB, int CB, bool WIDE, bool PAIR, bool SMEM, bool CROSS = true>
 __global__ void __launch_bounds__(kThreads, 2)
     sweep_kernel(const float4* __restrict__ coef, const int2* __restrict__ inst_tiles,
                  const int2* __restrict__ items, int n_items, int tiles_x, int n_blocks, int nx,
@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                 __syncwarp();  // every lane is done with the previous tile's row terms
                 gbd::mixed_pair_rows(ts.tile(k), rowf[0], ent, lane);
                 __syncwarp();
-                gbd::mixed_tile_pair_rows<CB>(ts.tile(k), ent, colf, acc);
+                gbd::mixed_tile_pair_rows<CB, CROSS>(ts.tile(k), ent, colf, acc);
             } else if constexpr (PAIR)
                 gbd::mixed_tile_pair<CB, WIDE>(ts.tile(k), colf, rowf[0], acc);
             else
@@ -251,17 +251,17 @@ constexpr size_t sweep_smem(int rb, int cb, bool smem) {
                  : 0);
 }
 
-template <int RB, int CB, bool WIDE, bool PAIR, bool SMEM>
+template <int RB, int CB, bool WIDE, bool PAIR, bool SMEM, bool CROSS = true>
 cudaError_t launch_one(dim3 grid, cudaStream_t s, const float4* coef, const int2* it_tiles,
                        const int2* items, int n_items, int tiles_x, int n_blocks, int nx, int ny,
                        const double2* airy, int n_regions, double* moments, int* counter,
                        const unsigned* flags, unsigned mask, unsigned want, unsigned anyof,
                        uint32_t spins) {
     constexpr size_t smem = sweep_smem(RB, CB, SMEM);
-    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<RB, CB, WIDE, PAIR, SMEM>,
+    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<RB, CB, WIDE, PAIR, SMEM, CROSS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    sweep_kernel<RB, CB, WIDE, PAIR, SMEM><<<grid, kThreads, smem, s>>>(
+    sweep_kernel<RB, CB, WIDE, PAIR, SMEM, CROSS><<<grid, kThreads, smem, s>>>(
         coef, it_tiles, items, n_items, tiles_x, n_blocks, nx, ny, airy, n_regions, moments,
         counter, flags, mask, want, anyof, spins);
     return cudaGetLastError();
@@ -293,13 +293,25 @@ cudaError_t launch_sweep_pair(dim3 grid, cudaStream_t s, const float4* coef, con
                               int ny, const double2* airy, int n_regions, double* moments,
                               int* counter, const unsigned* flags, uint32_t spins) {
     using gbd::kFlagColSteep;
+    using gbd::kFlagCross;
     using gbd::kFlagSteep;
     using gbd::kFlagWide;
     constexpr unsigned kBoth = kFlagWide | kFlagSteep, kAll = kBoth | kFlagColSteep;
     constexpr bool kSmem = CB >= 8;
-    cudaError_t e = launch_one<2, CB, false, true, kSmem>(
-        grid, s, coef, it_tiles, items, n_items, tiles_x, n_blocks, nx, ny, airy, n_regions,
-        moments, counter, flags, kAll, 0u, 0u, spins);
+    cudaError_t e = cudaSuccess;
+    if constexpr (kSmem) {  // the shared-memory form has a no-uv-term instantiation
+        e = launch_one<2, CB, false, true, kSmem, false>(
+            grid, s, coef, it_tiles, items, n_items, tiles_x, n_blocks, nx, ny, airy, n_regions,
+            moments, counter, flags, kAll | kFlagCross, 0u, 0u, spins);
+        if (e == cudaSuccess)
+            e = launch_one<2, CB, false, true, kSmem>(
+                grid, s, coef, it_tiles, items, n_items, tiles_x, n_blocks, nx, ny, airy,
+                n_regions, moments, counter, flags, kAll, 0u, kFlagCross, spins);
+    } else {
+        e = launch_one<2, CB, false, true, kSmem>(
+            grid, s, coef, it_tiles, items, n_items, tiles_x, n_blocks, nx, ny, airy, n_regions,
+            moments, counter, flags, kAll, 0u, 0u, spins);
+    }
     if (e == cudaSuccess)
         e = launch_one<2, CB, true, true, kSmem>(grid, s, coef, it_tiles, items, n_items, tiles_x,
                                                  n_blocks, nx, ny, airy, n_regions, moments,
@@ -336,7 +348,7 @@ const SweepShape kSweepShapes[] = {
     {2, 4, GBD_SCHEME_ROW_PAIR, launch_sweep_pair<4>,
      (const void*)sweep_kernel<2, 4, false, true, false>, sweep_smem(2, 4, false)},
     {2, 8, GBD_SCHEME_ROW_PAIR, launch_sweep_pair<8>,
-     (const void*)sweep_kernel<2, 8, false, true, true>, sweep_smem(2, 8, true)},
+     (const void*)sweep_kernel<2, 8, false, true, true, false>, sweep_smem(2, 8, true)},
 };
 
 const SweepShape* find_sweep_shape(int rb, int cb, int scheme) {
