@@ -191,14 +191,26 @@ def traffic_bytes(tuned):
     return n["read"] + n["write"] * tuned[2] / n["splits"]
 
 
-def peak_evals_const(cols: int = 0) -> float:
+def mufu_mix(rows: int = 1, cols: int = 0, scheme: int = 0):
+    """MUFU operations per beamlet-pixel evaluation (ex2, and sin = cos) of a launch shape.
+    Direct scheme: one ex2, sin and cos per evaluation.  Row pairs on 2 x cols pixels, per
+    beamlet and block: cols + 1 sin/cos pairs (the first row and the exact row-step
+    factor) and 4 ex2 (that factor, and the first row's amplitude, its column ratio and the
+    ratio's ratio); the second row comes from multiplies on the FMA pipe.  Row triples on
+    3 x cols pixels (no uv term): cols + 1 sin/cos pairs and 3 ex2 per block, plus per
+    beamlet and warp of 32 blocks the shared 2 ex2 and one sin/cos pair of the row terms."""
+    if not scheme or not cols:
+        return 1.0, 1.0
+    if rows == 3:
+        px = 3.0 * cols
+        return 3.0 / px + 2.0 / (32 * px), (cols + 1) / px + 1.0 / (32 * px)
+    return 4.0 / (2 * cols), (cols + 1) / (2.0 * cols)
+
+
+def peak_evals_const(cols: int = 0, rows: int = 2) -> float:
     """MUFU-bound beamlet-pixel evaluations/s of a GB300 at its maximum clock: the direct
-    scheme (cols = 0), or row pairs on 2 x cols pixels (4 ex2 and cols + 1 sin/cos pairs
-    per beamlet and block)."""
-    if cols:
-        n_ex2, n_sc = 4.0 / (2 * cols), (cols + 1) / (2.0 * cols)
-    else:
-        n_ex2, n_sc = 1.0, 1.0
+    scheme (cols = 0), or the row-pair / row-triple scheme on rows x cols pixels."""
+    n_ex2, n_sc = mufu_mix(rows, cols, 1 if cols else 0)
     return GB300_SMS * GB300_MAX_MHZ * 1e6 / (n_ex2 / MUFU_EX2_PER_CLK_SM +
                                               2.0 * n_sc / MUFU_SINCOS_PER_CLK_SM)
 
@@ -555,16 +567,12 @@ def run_ours(args, world, rank, local):
 
     clk = clocks.stop()
 
-    # ---- roofline of the dominant kernel (mixed field kernel, MUFU pipe).  The direct
-    # scheme issues one ex2, one sin and one cos per beamlet-pixel evaluation.  Per beamlet
-    # and 2 x cols pixel block the row-pair scheme issues cols + 1 sin/cos pairs (the first
-    # row and the exact row-step factor) and 4 ex2 (that factor, and the first row's
-    # amplitude, its column ratio and the ratio's ratio); the second row and the first
-    # row's amplitude come from multiplies on the FMA pipe.
+    # ---- roofline of the dominant kernel (mixed field kernel, MUFU pipe), with the MUFU
+    # operations per evaluation of the scheme that ran (mufu_mix)
     kms, kn = kt["field_mixed"]
     k_avg_s = (kms / max(kn, 1)) * 1e-3
     probes = gbd.gbd_probe_peaks()
-    n_ex2, n_sc = (4.0 / (2 * tuned[1]), (tuned[1] + 1) / (2.0 * tuned[1])) if tuned[4] else (1.0, 1.0)
+    n_ex2, n_sc = mufu_mix(tuned[0], tuned[1], tuned[4])
     clk_per_eval = n_ex2 / MUFU_EX2_PER_CLK_SM + 2.0 * n_sc / MUFU_SINCOS_PER_CLK_SM
     peak_direct = GB300_SMS * GB300_MAX_MHZ * 1e6 / (1.0 / MUFU_EX2_PER_CLK_SM +
                                                     2.0 / MUFU_SINCOS_PER_CLK_SM)
@@ -584,7 +592,8 @@ def run_ours(args, world, rank, local):
         "peak_source": (f"derived: {GB300_SMS} SMs x {GB300_MAX_MHZ:g} MHz / ({n_ex2:.4g}/"
                         f"{MUFU_EX2_PER_CLK_SM} + {2 * n_sc:.4g}/{MUFU_SINCOS_PER_CLK_SM}) clk "
                         "per evaluation"),
-        "kernel": ("field_mixed_pair_smem_kernel" if tuned[4] and tuned[1] >= 8
+        "kernel": ("field_mixed_triple_kernel" if tuned[4] and tuned[0] == 3
+                   else "field_mixed_pair_smem_kernel" if tuned[4] and tuned[1] >= 8
                    else "field_mixed_kernel") + f" ({tuned[0]}x{tuned[1]}, {tuned[2]} splits)",
         "kernel_ms_avg": k_avg_s * 1e3, "launches": kn,
         "mufu_gops": (n_ex2 + 2.0 * n_sc) * achieved / 1e9,

@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             gbd::mixed_tile_pair<CB, WIDE>(ts.tile(k), colf, rowf, acc);
         } else {
             __syncwarp();  // every lane is done with the previous tile's row terms
-            gbd::mixed_pair_rows(ts.tile(k), rowf, ent, lane);
+            gbd::mixed_pair_rows<gbd::kPairRowF4>(ts.tile(k), rowf, ent, lane);
             __syncwarp();
             gbd::mixed_tile_pair_rows<CB, CROSS>(ts.tile(k), ent, colf, acc);
         }
@@ -191,6 +191,89 @@ __global__ void __launch_bounds__(kThreads, 2)
                 gbd::round_pair(make_float2(v.x, v.y), make_float2(v.z, v.w));
         }
     }
+}
+
+// Row triples on 3 x CB pixels per thread (rows 8 apart, columns 32 apart) for fields
+// without a uv term (mixed_tile_triple_rows).  The sums stay in FP32 registers over the
+// whole split, so the launch requires short splits (at most kTripleMaxTiles tiles = 1,024
+// beamlets); the reduction sums the splits with compensation.  Dynamic shared memory: the
+// kStages record stages, then each warp's row terms of the current tile.
+constexpr int kTripleMaxTiles = 16;
+template <int CB>
+__global__ void __launch_bounds__(kThreads, 2)
+    field_mixed_triple_kernel(const float4* __restrict__ coef, int n_tiles, int tiles_per_split,
+                              int nx, int ny, float2* __restrict__ partial,
+                              const unsigned* __restrict__ flags, unsigned mask, unsigned want,
+                              uint32_t spins) {
+    const unsigned fw = *flags;
+    if ((fw & mask) != want) return;
+    constexpr int kTileF4 = gbd::kMixedFields * gbd::kTile;
+    extern __shared__ __align__(128) float4 dyn4[];
+    float4(*stage)[kTileF4] = reinterpret_cast<float4(*)[kTileF4]>(dyn4);
+    __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
+    __shared__ int flag;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float4* ent = dyn4 + kStages * kTileF4 + warp * (gbd::kTripleRowF4 * gbd::kTile);
+    const int t0 = blockIdx.z * tiles_per_split;
+    gbd::init_stream_barriers(full, empty, tid);
+    gbd::TileStream<float4, kTileF4> ts{stage, full, empty, coef + (size_t)t0 * kTileF4,
+                                        min(n_tiles - t0, tiles_per_split), 0,
+                                        gbd::kMixedTileBytes, 0};
+    bool ok = ts.start(tid, spins, &flag);
+
+    const int col0 = blockIdx.x * (32 * CB) + lane;
+    const int row0 = blockIdx.y * 24 + warp;
+    float colf[CB];
+#pragma unroll
+    for (int c = 0; c < CB; ++c) colf[c] = (float)(col0 + 32 * c);
+    const float rowf = (float)row0;
+
+    float2 acc[3][CB];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < CB; ++c) acc[r][c] = make_float2(0.f, 0.f);
+
+    int k = 0;
+    for (; ok && k < ts.nt; ++k) {
+        if (!ts.acquire(k, spins)) {
+            ok = false;
+            break;
+        }
+        __syncwarp();  // every lane is done with the previous tile's row terms
+        gbd::mixed_pair_rows<gbd::kTripleRowF4>(ts.tile(k), rowf, ent, lane);
+        __syncwarp();
+        gbd::mixed_tile_triple_rows<CB>(ts.tile(k), ent, colf, acc);
+        if (!ts.release(k, lane, warp, spins)) {
+            ok = false;
+            ++k;
+            break;
+        }
+    }
+    if (!ok) {
+        record_timeout();
+        if (tid == 0) ts.drain(k, spins);
+        return;
+    }
+    const size_t npix = (size_t)nx * ny;
+    float2* out = partial + (size_t)blockIdx.z * npix;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const int row = row0 + 8 * r;
+        if (row >= ny) continue;
+#pragma unroll
+        for (int c = 0; c < CB; ++c) {
+            const int col = col0 + 32 * c;
+            if (col >= nx) continue;
+            out[(size_t)row * nx + col] = acc[r][c];
+        }
+    }
+}
+
+constexpr size_t triple_smem_bytes() {
+    return (size_t)kStages * gbd::kMixedTileBytes +
+           (size_t)kWarps * gbd::kTripleRowF4 * gbd::kTile * sizeof(float4);
 }
 
 template <int CB>
@@ -576,10 +659,13 @@ cudaError_t launch_f64_row(const void* coeffs, int n_tiles, const gbd_project_pa
 
 // Row pairs on 2 x CB pixels with shared-memory compensation; the direct 2 x 4 kernels (on
 // their own pixel grid, same splits) are the steep-beamlet fallback.
+// With `after_triple` the row-triple kernel has been launched first and takes the fields
+// with neither a uv term nor 16-row steepness; the narrow no-uv-term row pairs then take
+// only the 16-row-steep ones.
 template <int CB>
-cudaError_t launch_mixed_pair_smem(const void* coeffs, int n_tiles, const gbd_project_params& p,
-                                   const gbd_field_launch& L, void* partial_v,
-                                   const unsigned* flags, uint32_t spins, cudaStream_t s) {
+cudaError_t launch_pair_set(const void* coeffs, int n_tiles, const gbd_project_params& p,
+                            const gbd_field_launch& L, void* partial_v, const unsigned* flags,
+                            uint32_t spins, cudaStream_t s, bool after_triple) {
     float2* partial = static_cast<float2*>(partial_v);
     using gbd::kFlagColSteep;
     using gbd::kFlagCross;
@@ -601,7 +687,8 @@ cudaError_t launch_mixed_pair_smem(const void* coeffs, int n_tiles, const gbd_pr
     // exactly one runs: narrow without and with a uv term, then wide (or column-steep),
     // then the steep fallbacks
     field_mixed_pair_smem_kernel<CB, false, false><<<grid, kThreads, smem, s>>>(
-        c, n_tiles, tps, p.nx, p.ny, partial, flags, kAll | kFlagCross, 0u, 0u, spins);
+        c, n_tiles, tps, p.nx, p.ny, partial, flags, kAll | kFlagCross, 0u,
+        after_triple ? gbd::kFlagSteep16 : 0u, spins);
     field_mixed_pair_smem_kernel<CB, false, true><<<grid, kThreads, smem, s>>>(
         c, n_tiles, tps, p.nx, p.ny, partial, flags, kAll, 0u, kFlagCross, spins);
     field_mixed_pair_smem_kernel<CB, true><<<grid, kThreads, smem, s>>>(
@@ -612,6 +699,35 @@ cudaError_t launch_mixed_pair_smem(const void* coeffs, int n_tiles, const gbd_pr
     field_mixed_kernel<2, 4, true, false><<<grid24, kThreads, 0, s>>>(
         c, n_tiles, tps, p.nx, p.ny, partial, flags, kBoth, kBoth, 0u, spins);
     return cudaGetLastError();
+}
+
+template <int CB>
+cudaError_t launch_mixed_pair_smem(const void* coeffs, int n_tiles, const gbd_project_params& p,
+                                   const gbd_field_launch& L, void* partial, const unsigned* flags,
+                                   uint32_t spins, cudaStream_t s) {
+    return launch_pair_set<CB>(coeffs, n_tiles, p, L, partial, flags, spins, s, false);
+}
+
+// Row triples (3 x CB) when the splits are short enough for FP32 sums, with the 2 x CB
+// row-pair set behind them for fields the triples cannot take; longer splits run the
+// row-pair set alone.
+template <int CB>
+cudaError_t launch_mixed_triple(const void* coeffs, int n_tiles, const gbd_project_params& p,
+                                const gbd_field_launch& L, void* partial, const unsigned* flags,
+                                uint32_t spins, cudaStream_t s) {
+    if (L.tiles_per_split > kTripleMaxTiles)
+        return launch_pair_set<CB>(coeffs, n_tiles, p, L, partial, flags, spins, s, false);
+    constexpr size_t smem = triple_smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(field_mixed_triple_kernel<CB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    constexpr unsigned kNarrow = gbd::kFlagWide | gbd::kFlagSteep | gbd::kFlagColSteep |
+                                 gbd::kFlagCross | gbd::kFlagSteep16;
+    dim3 grid((p.nx + 32 * CB - 1) / (32 * CB), (p.ny + 23) / 24, L.splits);
+    field_mixed_triple_kernel<CB><<<grid, kThreads, smem, s>>>(
+        static_cast<const float4*>(coeffs), n_tiles, L.tiles_per_split, p.nx, p.ny,
+        static_cast<float2*>(partial), flags, kNarrow, 0u, spins);
+    return launch_pair_set<CB>(coeffs, n_tiles, p, L, partial, flags, spins, s, true);
 }
 
 typedef cudaError_t (*launch_fn)(const void*, int, const gbd_project_params&,
@@ -634,6 +750,8 @@ const ShapeEntry kMixedShapes[] = {
     {2, 4, GBD_SCHEME_ROW_PAIR, launch_mixed_pair<4>, (const void*)field_mixed_kernel<2, 4, false, true>},
     {2, 8, GBD_SCHEME_ROW_PAIR, launch_mixed_pair_smem<8>,
      (const void*)field_mixed_pair_smem_kernel<8, false, false>, pair_smem_bytes<8>()},
+    {3, 8, GBD_SCHEME_ROW_PAIR, launch_mixed_triple<8>, (const void*)field_mixed_triple_kernel<8>,
+     triple_smem_bytes()},
 };
 // (1,2), (2,2): every pixel evaluated directly (columns 32 apart); (1,8), (1,16), (2,8),
 // (1,32): contiguous row segments advanced by complex multiplies.

@@ -240,10 +240,15 @@ __device__ __forceinline__ void mixed_tile_pair(const float4* __restrict__ st,
 //               tu-slopes (the quadratic form with tv = v - v_c substituted),
 //   ent[1][b] = (32 sa + 1024 a_uu, 32 sp, 8 (a_v + a_vv (2 tv + 8)), 8 (p_v + p_vv (2 tv + 8))),
 //   ent[2][b] = (64 a_uu, 64 p_uu, 8 a_uv, 8 p_uv),
-// so that mixed_tile_pair_rows forms the first-row amplitude and phase, the amplitude's
-// first ratio rho, the phase step d1 and the 8-row step factor's exponent with one or two
-// FFMA each in the thread's first column tu0.  kPairRowF4 float4 per beamlet and warp.
+//   ent[3][b] = (sig = 2^(2048 a_uu), K = 2^(128 a_vv) e^(i 128 p_vv), 0)  (row triples),
+// so that the tile loops form the first-row amplitude and phase, the amplitude's first
+// ratio rho, the phase step d1 and the 8-row step factor's exponent with one or two FFMA
+// each in the thread's first column tu0.  sig is the amplitude ratio's own ratio along a
+// row; K the ratio of consecutive 8-row step factors.  NF4 (kPairRowF4 or kTripleRowF4)
+// float4 per beamlet and warp.
 constexpr int kPairRowF4 = 3;
+constexpr int kTripleRowF4 = 4;
+template <int NF4>
 __device__ __forceinline__ void mixed_pair_rows(const float4* __restrict__ st, float rowf,
                                                 float4* __restrict__ ent, int lane) {
 #pragma unroll
@@ -263,6 +268,14 @@ __device__ __forceinline__ void mixed_pair_rows(const float4* __restrict__ st, f
         ent[kTile + b] = make_float4(fmaf(1024.0f, q2.x, 32.0f * sa), 32.0f * sp,
                                      8.0f * fmaf(q3.x, w, q1.z), 8.0f * fmaf(q3.y, w, q1.w));
         ent[2 * kTile + b] = make_float4(64.0f * q2.x, 64.0f * q2.y, 8.0f * q2.z, 8.0f * q2.w);
+        if (NF4 > 3) {
+            // K's phase reduced exactly (once per warp and beamlet, so the cost is small)
+            const float km = mufu_ex2(128.0f * q3.x);
+            const float kp =
+                frac_turns(128.0f * q3.y * 0.15915494309189533577f) * 6.28318530717958647692f;
+            ent[3 * kTile + b] = make_float4(mufu_ex2(2048.0f * q2.x), km * mufu_cos(kp),
+                                             km * mufu_sin(kp), 0.0f);
+        }
     }
 }
 
@@ -311,6 +324,60 @@ __device__ __forceinline__ void mixed_tile_pair_rows(const float4* __restrict__ 
                     ry = fmaf(rx, T.y, ry * T.x);
                     rx = nx;
                 }
+                amp *= rho;
+                rho *= sig;
+            }
+        }
+    }
+}
+
+// Row triples v, v + 8, v + 16 for fields without a uv term (every T exactly 1): the
+// 8-row step factor R is then constant along the thread's row, the next one is R K
+// (K from mixed_pair_rows), so the third row is the first times R R K.  Per beamlet and
+// thread the setup of mixed_tile_pair_rows plus two complex products, per column 21
+// instructions for 3 pixels and no MUFU operation beyond the first row's sin + cos:
+// 22 MUFU operations per 24 pixels.  Requires the steep and 16-row steep flags clear
+// (|log2 R| and |log2 R R K| within 64).
+template <int CB>
+__device__ __forceinline__ void mixed_tile_triple_rows(const float4* __restrict__ st,
+                                                       const float4* __restrict__ ent,
+                                                       const float (&colf)[CB],
+                                                       float2 (&acc)[3][CB]) {
+    const float* stf = reinterpret_cast<const float*>(st);
+#pragma unroll 1
+    for (int b = 0; b < kTile; ++b) {
+        const float uc = stf[4 * b];                                               // q0.x
+        const float2 quu = reinterpret_cast<const float2*>(st + 2 * kTile + b)[0];  // q2.xy
+        const float4 e0 = ent[b];
+        const float4 e1 = ent[kTile + b];
+        const float4 e2 = ent[2 * kTile + b];
+        const float4 e3 = ent[3 * kTile + b];
+        const float tu0 = colf[0] - uc;
+        const float ga = fmaf(e2.z, tu0, e1.z);
+        const float gp = fmaf(e2.w, tu0, e1.w);  // within 64 rad: the field is not wide
+        const float x0 = fmaf(tu0, fmaf(quu.y, tu0, e0.w), e0.y);
+        const float d1 = fmaf(e2.y, tu0, e1.y);
+        const float gm = mufu_ex2(ga);
+        const float rx = gm * mufu_cos(gp), ry = gm * mufu_sin(gp);
+        // R2 = R K, then R R2
+        const float kx = fmaf(rx, e3.y, -ry * e3.z), ky = fmaf(rx, e3.z, ry * e3.y);
+        const float sx = fmaf(rx, kx, -ry * ky), sy = fmaf(rx, ky, ry * kx);
+        float amp = mufu_ex2(fmaf(tu0, fmaf(quu.x, tu0, e0.z), e0.x));
+        float rho = mufu_ex2(fmaf(e2.x, tu0, e1.x));
+        const float sig = e3.x;
+#pragma unroll
+        for (int c = 0; c < CB; ++c) {
+            const float x = c == 0 ? x0 : fmaf((float)(1024 * c * c), quu.y, fmaf((float)c, d1, x0));
+            const float cs = mufu_cos(x), sn = mufu_sin(x);
+            acc[0][c].x = fmaf(amp, cs, acc[0][c].x);
+            acc[0][c].y = fmaf(amp, sn, acc[0][c].y);
+            const float wx = amp * rx, wy = amp * ry;
+            acc[1][c].x = fmaf(cs, wx, fmaf(-sn, wy, acc[1][c].x));
+            acc[1][c].y = fmaf(cs, wy, fmaf(sn, wx, acc[1][c].y));
+            const float vx = amp * sx, vy = amp * sy;
+            acc[2][c].x = fmaf(cs, vx, fmaf(-sn, vy, acc[2][c].x));
+            acc[2][c].y = fmaf(cs, vy, fmaf(sn, vx, acc[2][c].y));
+            if (c + 1 < CB) {
                 amp *= rho;
                 rho *= sig;
             }
