@@ -40,12 +40,12 @@ MUFU_EX2_PER_CLK_SM = 32
 MUFU_SINCOS_PER_CLK_SM = 16
 GB300_SMS = 152
 GB300_MAX_MHZ = 2070.0
-# DRAM bytes per launch of the 2 x 8 row-pair field kernel on airy_large from one ncu
-# capture (profiles/field_mixed_pair_smem_kernel_airy_large.md) at 90 beamlet splits.  The
+# DRAM bytes per launch of the 3 x 8 row-triple field kernel on airy_large from one ncu
+# capture (profiles/field_mixed_triple_kernel_airy_large.md) at 62 beamlet splits.  The
 # reads are the record tiles; the writes are the split partial fields, which scale with
 # the split count.
-FIELD_MIXED_NCU = {"kernel": "field_mixed_pair_smem_kernel<8, false> (2x8 row pairs)",
-                   "read": 3.38944e6, "write": 127.755776e6, "splits": 90, "rows": 2, "cols": 8,
+FIELD_MIXED_NCU = {"kernel": "field_mixed_triple_kernel<8> (3x8 row triples)",
+                   "read": 3.531776e6, "write": 69.199616e6, "splits": 62, "rows": 3, "cols": 8,
                    "scheme": 1}
 
 
