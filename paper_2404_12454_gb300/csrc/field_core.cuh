@@ -334,7 +334,8 @@ __device__ __forceinline__ void mixed_tile_pair_rows(const float4* __restrict__ 
 // Row triples v, v + 8, v + 16 for fields without a uv term (every T exactly 1): the
 // 8-row step factor R is then constant along the thread's row, the next one is R K
 // (K from mixed_pair_rows), so the third row is the first times R R K.  Per beamlet and
-// thread the setup of mixed_tile_pair_rows plus two complex products, per column 21
+// thread the setup of mixed_tile_pair_rows plus two complex products; per column the
+// first row's value E0 = amp (cos, sin) and its products with R and R R K, 19
 // instructions for 3 pixels and no MUFU operation beyond the first row's sin + cos:
 // 22 MUFU operations per 24 pixels.  Requires the steep and 16-row steep flags clear
 // (|log2 R| and |log2 R R K| within 64).
@@ -368,15 +369,14 @@ __device__ __forceinline__ void mixed_tile_triple_rows(const float4* __restrict_
 #pragma unroll
         for (int c = 0; c < CB; ++c) {
             const float x = c == 0 ? x0 : fmaf((float)(1024 * c * c), quu.y, fmaf((float)c, d1, x0));
-            const float cs = mufu_cos(x), sn = mufu_sin(x);
-            acc[0][c].x = fmaf(amp, cs, acc[0][c].x);
-            acc[0][c].y = fmaf(amp, sn, acc[0][c].y);
-            const float wx = amp * rx, wy = amp * ry;
-            acc[1][c].x = fmaf(cs, wx, fmaf(-sn, wy, acc[1][c].x));
-            acc[1][c].y = fmaf(cs, wy, fmaf(sn, wx, acc[1][c].y));
-            const float vx = amp * sx, vy = amp * sy;
-            acc[2][c].x = fmaf(cs, vx, fmaf(-sn, vy, acc[2][c].x));
-            acc[2][c].y = fmaf(cs, vy, fmaf(sn, vx, acc[2][c].y));
+            // the first row's value E0 once, then E0, E0 R and E0 R R K into the three rows
+            const float ex = amp * mufu_cos(x), ey = amp * mufu_sin(x);
+            acc[0][c].x += ex;
+            acc[0][c].y += ey;
+            acc[1][c].x = fmaf(ex, rx, fmaf(-ey, ry, acc[1][c].x));
+            acc[1][c].y = fmaf(ex, ry, fmaf(ey, rx, acc[1][c].y));
+            acc[2][c].x = fmaf(ex, sx, fmaf(-ey, sy, acc[2][c].x));
+            acc[2][c].y = fmaf(ex, sy, fmaf(ey, sx, acc[2][c].y));
             if (c + 1 < CB) {
                 amp *= rho;
                 rho *= sig;
