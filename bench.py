@@ -196,13 +196,14 @@ def mufu_mix(rows: int = 1, cols: int = 0, scheme: int = 0):
     Direct scheme: one ex2, sin and cos per evaluation.  Row pairs on 2 x cols pixels, per
     beamlet and block: cols + 1 sin/cos pairs (the first row and the exact row-step
     factor) and 4 ex2 (that factor, and the first row's amplitude, its column ratio and the
-    ratio's ratio); the second row comes from multiplies on the FMA pipe.  Row triples on
-    3 x cols pixels (no uv term): cols + 1 sin/cos pairs and 3 ex2 per block, plus per
-    beamlet and warp of 32 blocks the shared 2 ex2 and one sin/cos pair of the row terms."""
+    ratio's ratio); the second row comes from multiplies on the FMA pipe.  Row triples or
+    quadruples on rows x cols pixels (no uv term): cols + 1 sin/cos pairs and 3 ex2 per
+    block, plus per beamlet and warp of 32 blocks the shared 2 ex2 and one sin/cos pair of
+    the row terms."""
     if not scheme or not cols:
         return 1.0, 1.0
-    if rows == 3:
-        px = 3.0 * cols
+    if rows in (3, 4):
+        px = float(rows * cols)
         return 3.0 / px + 2.0 / (32 * px), (cols + 1) / px + 1.0 / (32 * px)
     return 4.0 / (2 * cols), (cols + 1) / (2.0 * cols)
 
@@ -592,7 +593,7 @@ def run_ours(args, world, rank, local):
         "peak_source": (f"derived: {GB300_SMS} SMs x {GB300_MAX_MHZ:g} MHz / ({n_ex2:.4g}/"
                         f"{MUFU_EX2_PER_CLK_SM} + {2 * n_sc:.4g}/{MUFU_SINCOS_PER_CLK_SM}) clk "
                         "per evaluation"),
-        "kernel": ("field_mixed_triple_kernel" if tuned[4] and tuned[0] == 3
+        "kernel": ("field_mixed_rows_kernel" if tuned[4] and tuned[0] in (3, 4)
                    else "field_mixed_pair_smem_kernel" if tuned[4] and tuned[1] >= 8
                    else "field_mixed_kernel") + f" ({tuned[0]}x{tuned[1]}, {tuned[2]} splits)",
         "kernel_ms_avg": k_avg_s * 1e3, "launches": kn,

@@ -193,18 +193,18 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
 }
 
-// Row triples on 3 x CB pixels per thread (rows 8 apart, columns 32 apart) for fields
-// without a uv term (mixed_tile_triple_rows).  The sums stay in FP32 registers over the
-// whole split, so the launch requires short splits (at most kTripleMaxTiles tiles = 1,024
-// beamlets); the reduction sums the splits with compensation.  Dynamic shared memory: the
-// kStages record stages, then each warp's row terms of the current tile.
-constexpr int kTripleMaxTiles = 16;
-template <int CB>
+// Row triples or quadruples on RB x CB pixels per thread (rows 8 apart, columns 32
+// apart) for fields without a uv term (mixed_tile_rows).  The sums stay in FP32 registers
+// over the whole split, so the launch requires short splits (at most kRowsMaxTiles tiles
+// = 1,024 beamlets); the reduction sums the splits with compensation.  Dynamic shared
+// memory: the kStages record stages, then each warp's row terms of the current tile.
+constexpr int kRowsMaxTiles = 16;
+template <int RB, int CB>
 __global__ void __launch_bounds__(kThreads, 2)
-    field_mixed_triple_kernel(const float4* __restrict__ coef, int n_tiles, int tiles_per_split,
-                              int nx, int ny, float2* __restrict__ partial,
-                              const unsigned* __restrict__ flags, unsigned mask, unsigned want,
-                              uint32_t spins) {
+    field_mixed_rows_kernel(const float4* __restrict__ coef, int n_tiles, int tiles_per_split,
+                            int nx, int ny, float2* __restrict__ partial,
+                            const unsigned* __restrict__ flags, unsigned mask, unsigned want,
+                            uint32_t spins) {
     const unsigned fw = *flags;
     if ((fw & mask) != want) return;
     constexpr int kTileF4 = gbd::kMixedFields * gbd::kTile;
@@ -223,15 +223,15 @@ __global__ void __launch_bounds__(kThreads, 2)
     bool ok = ts.start(tid, spins, &flag);
 
     const int col0 = blockIdx.x * (32 * CB) + lane;
-    const int row0 = blockIdx.y * 24 + warp;
+    const int row0 = blockIdx.y * (8 * RB) + warp;
     float colf[CB];
 #pragma unroll
     for (int c = 0; c < CB; ++c) colf[c] = (float)(col0 + 32 * c);
     const float rowf = (float)row0;
 
-    float2 acc[3][CB];
+    float2 acc[RB][CB];
 #pragma unroll
-    for (int r = 0; r < 3; ++r)
+    for (int r = 0; r < RB; ++r)
 #pragma unroll
         for (int c = 0; c < CB; ++c) acc[r][c] = make_float2(0.f, 0.f);
 
@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         __syncwarp();  // every lane is done with the previous tile's row terms
         gbd::mixed_pair_rows<gbd::kTripleRowF4>(ts.tile(k), rowf, ent, lane);
         __syncwarp();
-        gbd::mixed_tile_triple_rows<CB>(ts.tile(k), ent, colf, acc);
+        gbd::mixed_tile_rows<RB, CB>(ts.tile(k), ent, colf, acc);
         if (!ts.release(k, lane, warp, spins)) {
             ok = false;
             ++k;
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     const size_t npix = (size_t)nx * ny;
     float2* out = partial + (size_t)blockIdx.z * npix;
 #pragma unroll
-    for (int r = 0; r < 3; ++r) {
+    for (int r = 0; r < RB; ++r) {
         const int row = row0 + 8 * r;
         if (row >= ny) continue;
 #pragma unroll
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
 }
 
-constexpr size_t triple_smem_bytes() {
+constexpr size_t rows_smem_bytes() {
     return (size_t)kStages * gbd::kMixedTileBytes +
            (size_t)kWarps * gbd::kTripleRowF4 * gbd::kTile * sizeof(float4);
 }
@@ -659,9 +659,9 @@ cudaError_t launch_f64_row(const void* coeffs, int n_tiles, const gbd_project_pa
 
 // Row pairs on 2 x CB pixels with shared-memory compensation; the direct 2 x 4 kernels (on
 // their own pixel grid, same splits) are the steep-beamlet fallback.
-// With `after_triple` the row-triple kernel has been launched first and takes the fields
-// with neither a uv term nor 16-row steepness; the narrow no-uv-term row pairs then take
-// only the 16-row-steep ones.
+// With `after_triple` the row-triple (or quadruple) kernel has been launched first and
+// takes the fields with neither a uv term nor multi-row steepness; the narrow no-uv-term
+// row pairs then take only the multi-row-steep ones.
 template <int CB>
 cudaError_t launch_pair_set(const void* coeffs, int n_tiles, const gbd_project_params& p,
                             const gbd_field_launch& L, void* partial_v, const unsigned* flags,
@@ -688,7 +688,7 @@ cudaError_t launch_pair_set(const void* coeffs, int n_tiles, const gbd_project_p
     // then the steep fallbacks
     field_mixed_pair_smem_kernel<CB, false, false><<<grid, kThreads, smem, s>>>(
         c, n_tiles, tps, p.nx, p.ny, partial, flags, kAll | kFlagCross, 0u,
-        after_triple ? gbd::kFlagSteep16 : 0u, spins);
+        after_triple ? gbd::kFlagSteepRows : 0u, spins);
     field_mixed_pair_smem_kernel<CB, false, true><<<grid, kThreads, smem, s>>>(
         c, n_tiles, tps, p.nx, p.ny, partial, flags, kAll, 0u, kFlagCross, spins);
     field_mixed_pair_smem_kernel<CB, true><<<grid, kThreads, smem, s>>>(
@@ -708,23 +708,23 @@ cudaError_t launch_mixed_pair_smem(const void* coeffs, int n_tiles, const gbd_pr
     return launch_pair_set<CB>(coeffs, n_tiles, p, L, partial, flags, spins, s, false);
 }
 
-// Row triples (3 x CB) when the splits are short enough for FP32 sums, with the 2 x CB
-// row-pair set behind them for fields the triples cannot take; longer splits run the
-// row-pair set alone.
-template <int CB>
-cudaError_t launch_mixed_triple(const void* coeffs, int n_tiles, const gbd_project_params& p,
-                                const gbd_field_launch& L, void* partial, const unsigned* flags,
-                                uint32_t spins, cudaStream_t s) {
-    if (L.tiles_per_split > kTripleMaxTiles)
+// Row triples or quadruples (RB x CB) when the splits are short enough for FP32 sums,
+// with the 2 x CB row-pair set behind them for fields they cannot take; longer splits run
+// the row-pair set alone.
+template <int RB, int CB>
+cudaError_t launch_mixed_rows(const void* coeffs, int n_tiles, const gbd_project_params& p,
+                              const gbd_field_launch& L, void* partial, const unsigned* flags,
+                              uint32_t spins, cudaStream_t s) {
+    if (L.tiles_per_split > kRowsMaxTiles)
         return launch_pair_set<CB>(coeffs, n_tiles, p, L, partial, flags, spins, s, false);
-    constexpr size_t smem = triple_smem_bytes();
-    cudaError_t e = cudaFuncSetAttribute(field_mixed_triple_kernel<CB>,
+    constexpr size_t smem = rows_smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(field_mixed_rows_kernel<RB, CB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     constexpr unsigned kNarrow = gbd::kFlagWide | gbd::kFlagSteep | gbd::kFlagColSteep |
-                                 gbd::kFlagCross | gbd::kFlagSteep16;
-    dim3 grid((p.nx + 32 * CB - 1) / (32 * CB), (p.ny + 23) / 24, L.splits);
-    field_mixed_triple_kernel<CB><<<grid, kThreads, smem, s>>>(
+                                 gbd::kFlagCross | gbd::kFlagSteepRows;
+    dim3 grid((p.nx + 32 * CB - 1) / (32 * CB), (p.ny + 8 * RB - 1) / (8 * RB), L.splits);
+    field_mixed_rows_kernel<RB, CB><<<grid, kThreads, smem, s>>>(
         static_cast<const float4*>(coeffs), n_tiles, L.tiles_per_split, p.nx, p.ny,
         static_cast<float2*>(partial), flags, kNarrow, 0u, spins);
     return launch_pair_set<CB>(coeffs, n_tiles, p, L, partial, flags, spins, s, true);
@@ -750,8 +750,10 @@ const ShapeEntry kMixedShapes[] = {
     {2, 4, GBD_SCHEME_ROW_PAIR, launch_mixed_pair<4>, (const void*)field_mixed_kernel<2, 4, false, true>},
     {2, 8, GBD_SCHEME_ROW_PAIR, launch_mixed_pair_smem<8>,
      (const void*)field_mixed_pair_smem_kernel<8, false, false>, pair_smem_bytes<8>()},
-    {3, 8, GBD_SCHEME_ROW_PAIR, launch_mixed_triple<8>, (const void*)field_mixed_triple_kernel<8>,
-     triple_smem_bytes()},
+    {3, 8, GBD_SCHEME_ROW_PAIR, launch_mixed_rows<3, 8>, (const void*)field_mixed_rows_kernel<3, 8>,
+     rows_smem_bytes()},
+    {4, 8, GBD_SCHEME_ROW_PAIR, launch_mixed_rows<4, 8>, (const void*)field_mixed_rows_kernel<4, 8>,
+     rows_smem_bytes()},
 };
 // (1,2), (2,2): every pixel evaluated directly (columns 32 apart); (1,8), (1,16), (2,8),
 // (1,32): contiguous row segments advanced by complex multiplies.

@@ -331,19 +331,21 @@ __device__ __forceinline__ void mixed_tile_pair_rows(const float4* __restrict__ 
     }
 }
 
-// Row triples v, v + 8, v + 16 for fields without a uv term (every T exactly 1): the
-// 8-row step factor R is then constant along the thread's row, the next one is R K
-// (K from mixed_pair_rows), so the third row is the first times R R K.  Per beamlet and
-// thread the setup of mixed_tile_pair_rows plus two complex products; per column the
-// first row's value E0 = amp (cos, sin) and its products with R and R R K, 19
-// instructions for 3 pixels and no MUFU operation beyond the first row's sin + cos:
-// 22 MUFU operations per 24 pixels.  Requires the steep and 16-row steep flags clear
-// (|log2 R| and |log2 R R K| within 64).
-template <int CB>
-__device__ __forceinline__ void mixed_tile_triple_rows(const float4* __restrict__ st,
-                                                       const float4* __restrict__ ent,
-                                                       const float (&colf)[CB],
-                                                       float2 (&acc)[3][CB]) {
+// Row triples (RB = 3: rows v, v + 8, v + 16) and quadruples (RB = 4: also v + 24) for
+// fields without a uv term (every T exactly 1): the 8-row step factor R is then constant
+// along the thread's row, the next ones are R K and R K^2 (K from mixed_pair_rows), so row
+// 8 r below the first is the first times S_r = R (R K) ... (R K^(r-1)).  Per beamlet and
+// thread the setup of mixed_tile_pair_rows plus two complex products per extra row; per
+// column the first row's value E0 = amp (cos, sin) and its products with every S_r
+// (4 FFMA each): 19 instructions for 3 pixels, 23 for 4, and no MUFU operation beyond the
+// first row's sin + cos: 22 MUFU operations per 8 RB pixels.  Requires the steep and
+// multi-row steep flags clear (every |log2 S_r| within 64).
+template <int RB, int CB>
+__device__ __forceinline__ void mixed_tile_rows(const float4* __restrict__ st,
+                                                const float4* __restrict__ ent,
+                                                const float (&colf)[CB],
+                                                float2 (&acc)[RB][CB]) {
+    static_assert(RB == 3 || RB == 4, "row triples or quadruples");
     const float* stf = reinterpret_cast<const float*>(st);
 #pragma unroll 1
     for (int b = 0; b < kTile; ++b) {
@@ -359,24 +361,31 @@ __device__ __forceinline__ void mixed_tile_triple_rows(const float4* __restrict_
         const float x0 = fmaf(tu0, fmaf(quu.y, tu0, e0.w), e0.y);
         const float d1 = fmaf(e2.y, tu0, e1.y);
         const float gm = mufu_ex2(ga);
-        const float rx = gm * mufu_cos(gp), ry = gm * mufu_sin(gp);
-        // R2 = R K, then R R2
-        const float kx = fmaf(rx, e3.y, -ry * e3.z), ky = fmaf(rx, e3.z, ry * e3.y);
-        const float sx = fmaf(rx, kx, -ry * ky), sy = fmaf(rx, ky, ry * kx);
+        // S_1 = R, then step factor f_r = f_(r-1) K and S_r = S_(r-1) f_r
+        float2 S[RB - 1];
+        S[0] = make_float2(gm * mufu_cos(gp), gm * mufu_sin(gp));
+        float2 f = S[0];
+#pragma unroll
+        for (int r = 1; r < RB - 1; ++r) {
+            f = make_float2(fmaf(f.x, e3.y, -f.y * e3.z), fmaf(f.x, e3.z, f.y * e3.y));
+            S[r] = make_float2(fmaf(S[r - 1].x, f.x, -S[r - 1].y * f.y),
+                               fmaf(S[r - 1].x, f.y, S[r - 1].y * f.x));
+        }
         float amp = mufu_ex2(fmaf(tu0, fmaf(quu.x, tu0, e0.z), e0.x));
         float rho = mufu_ex2(fmaf(e2.x, tu0, e1.x));
         const float sig = e3.x;
 #pragma unroll
         for (int c = 0; c < CB; ++c) {
             const float x = c == 0 ? x0 : fmaf((float)(1024 * c * c), quu.y, fmaf((float)c, d1, x0));
-            // the first row's value E0 once, then E0, E0 R and E0 R R K into the three rows
+            // the first row's value E0 once, then E0 S_r into the later rows
             const float ex = amp * mufu_cos(x), ey = amp * mufu_sin(x);
             acc[0][c].x += ex;
             acc[0][c].y += ey;
-            acc[1][c].x = fmaf(ex, rx, fmaf(-ey, ry, acc[1][c].x));
-            acc[1][c].y = fmaf(ex, ry, fmaf(ey, rx, acc[1][c].y));
-            acc[2][c].x = fmaf(ex, sx, fmaf(-ey, sy, acc[2][c].x));
-            acc[2][c].y = fmaf(ex, sy, fmaf(ey, sx, acc[2][c].y));
+#pragma unroll
+            for (int r = 1; r < RB; ++r) {
+                acc[r][c].x = fmaf(ex, S[r - 1].x, fmaf(-ey, S[r - 1].y, acc[r][c].x));
+                acc[r][c].y = fmaf(ex, S[r - 1].y, fmaf(ey, S[r - 1].x, acc[r][c].y));
+            }
             if (c + 1 < CB) {
                 amp *= rho;
                 rho *= sig;

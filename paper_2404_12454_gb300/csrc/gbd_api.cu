@@ -219,7 +219,7 @@ size_t tile_bytes(int precision) {
 
 gbd_shape default_shape(int precision) {
     gbd_shape s;
-    s.rows_per_thread = precision == GBD_PREC_MIXED ? 3 : 1;
+    s.rows_per_thread = precision == GBD_PREC_MIXED ? 4 : 1;
     s.cols_per_thread = precision == GBD_PREC_MIXED ? 8 : 16;
     s.splits = 0;
     s.ms = 0.f;
@@ -248,8 +248,9 @@ int auto_cols(int nx, int min_cols = 2) {
 }
 
 // The shape set for this device and precision, else the default (for the mixed path with
-// its columns per thread fitted to the detector's width: row triples on 8 columns, which
-// run the 2 x 8 row pairs themselves for the fields they cannot take, else row pairs).
+// its columns per thread fitted to the detector's width: row quadruples on 8 columns,
+// which run the 2 x 8 row pairs themselves for the fields they cannot take, else row
+// pairs).
 gbd_shape stored_shape(int precision, const gbd_detector* D) {
     {
         std::lock_guard<std::mutex> lk(g_mu);
@@ -259,7 +260,7 @@ gbd_shape stored_shape(int precision, const gbd_detector* D) {
     gbd_shape s = default_shape(precision);
     if (precision == GBD_PREC_MIXED && D) {
         s.cols_per_thread = auto_cols(D->nx);
-        s.rows_per_thread = s.cols_per_thread == 8 ? 3 : 2;
+        s.rows_per_thread = s.cols_per_thread == 8 ? 4 : 2;
     }
     return s;
 }
@@ -651,7 +652,8 @@ gbd_status gbd_autotune_field(const gbd_beamlet* beamlets, int32_t n_beamlets, d
     static const int kMixed[][3] = {{1, 4, GBD_SCHEME_DIRECT},   {2, 2, GBD_SCHEME_DIRECT},
                                     {2, 4, GBD_SCHEME_DIRECT},   {4, 2, GBD_SCHEME_DIRECT},
                                     {2, 2, GBD_SCHEME_ROW_PAIR}, {2, 4, GBD_SCHEME_ROW_PAIR},
-                                    {2, 8, GBD_SCHEME_ROW_PAIR}, {3, 8, GBD_SCHEME_ROW_PAIR}};
+                                    {2, 8, GBD_SCHEME_ROW_PAIR}, {3, 8, GBD_SCHEME_ROW_PAIR},
+                                    {4, 8, GBD_SCHEME_ROW_PAIR}};
     static const int kF64[][3] = {{1, 2, 0}, {2, 2, 0}, {1, 8, 0}, {2, 8, 0}, {1, 16, 0}, {1, 32, 0}};
     std::vector<std::array<int, 3>> shapes;
     if (precision == GBD_PREC_MIXED)

@@ -40,7 +40,8 @@ constexpr unsigned kFlagWide = 1u;   // some phase may exceed kWidePhase on the 
 constexpr unsigned kFlagSteep = 2u;  // the row-pair recurrence could leave FP32 range
 constexpr unsigned kFlagColSteep = 4u;  // so could an amplitude recurrence along a row
 constexpr unsigned kFlagCross = 8u;     // some beamlet has a uv term (column factor T != 1)
-constexpr unsigned kFlagSteep16 = 16u;  // the row-triple kernel's 16-row step could leave FP32 range
+constexpr unsigned kFlagSteepRows = 16u;  // a 16- or 24-row step (row triples, quadruples)
+                                          // could leave FP32 range
 
 // ----------------------------------------------------------------- PTX wrappers --
 

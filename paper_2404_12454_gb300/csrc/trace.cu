@@ -387,10 +387,11 @@ __device__ __forceinline__ unsigned write_mixed(float4* __restrict__ out, long l
         const double step = 8.0 * (fabs(q.a[2]) + fabs(q.a[4]) * (U + 96.0) +
                                     fabs(q.a[5]) * (2.0 * V + 8.0)) + 768.0 * fabs(q.a[4]);
         if (!(step <= 64.0)) flags |= gbd::kFlagSteep;
-        // the same over 16 rows (row triples: the third row is the first times R R2)
-        const double step16 = 16.0 * (fabs(q.a[2]) + fabs(q.a[4]) * (U + 96.0) +
-                                      fabs(q.a[5]) * (2.0 * V + 16.0)) + 1536.0 * fabs(q.a[4]);
-        if (!(step16 <= 64.0)) flags |= gbd::kFlagSteep16;
+        // the same over 24 rows (row triples and quadruples: the last row is the first
+        // times the product of two or three step factors)
+        const double step24 = 24.0 * (fabs(q.a[2]) + fabs(q.a[4]) * (U + 96.0) +
+                                      fabs(q.a[5]) * (2.0 * V + 24.0)) + 2304.0 * fabs(q.a[4]);
+        if (!(step24 <= 64.0)) flags |= gbd::kFlagSteepRows;
         // log2 amplitude change over one 32-column step: the narrow-phase row-pair kernels
         // carry the first row's amplitude along a thread's (up to 8) columns by a
         // recurrence, which needs the whole 224-pixel span within 2^64
