@@ -40,13 +40,14 @@ MUFU_EX2_PER_CLK_SM = 32
 MUFU_SINCOS_PER_CLK_SM = 16
 GB300_SMS = 152
 GB300_MAX_MHZ = 2070.0
-# DRAM bytes per launch of the 3 x 8 row-triple field kernel on airy_large from one ncu
-# capture (profiles/field_mixed_triple_kernel_airy_large.md) at 62 beamlet splits.  The
-# reads are the record tiles; the writes are the split partial fields, which scale with
-# the split count.
-FIELD_MIXED_NCU = {"kernel": "field_mixed_triple_kernel<8> (3x8 row triples)",
-                   "read": 3.531776e6, "write": 69.199616e6, "splits": 62, "rows": 3, "cols": 8,
-                   "scheme": 1}
+# DRAM bytes per launch of the 4 x 8 row-quadruple field kernel on airy_large from one ncu
+# capture (profiles/field_mixed_rows_kernel_airy_large.md) at 90 beamlet splits, and its
+# issued warp-instructions per 32 evaluations.  The reads are the record tiles; the writes
+# are the split partial fields, which scale with the split count.
+FIELD_MIXED_NCU = {"kernel": "field_mixed_rows_kernel<4, 8> (4x8 row quadruples)",
+                   "read": 3.682048e6, "write": 128.391424e6, "splits": 90, "rows": 4, "cols": 8,
+                   "scheme": 1, "inst_per_32_evals": 7.02}
+ISSUE_PER_CLK_SM = 4  # warp-instructions issued per clock and SM (one per sub-partition)
 
 
 def parse():
@@ -604,6 +605,16 @@ def run_ours(args, world, rank, local):
         "probe_peak_evals_per_s": probe_peak,
         "frac_of_probe_peak": achieved / probe_peak,
     }
+    # The multi-row kernels need so few MUFU operations that instruction issue binds first:
+    # the issue-slot ceiling for the captured kernel's instruction count per evaluation.
+    if traffic_bytes(tuned) is not None:
+        ipe = FIELD_MIXED_NCU["inst_per_32_evals"] / 32.0
+        issue_peak = GB300_SMS * GB300_MAX_MHZ * 1e6 * ISSUE_PER_CLK_SM / ipe
+        roofline["issue_bound"] = {
+            "warp_instructions_per_32_evals": FIELD_MIXED_NCU["inst_per_32_evals"],
+            "peak": issue_peak / 1e9, "unit": "Geval/s", "frac": achieved / issue_peak,
+            "source": ("ncu smsp__inst_executed.sum of the capture; 152 SMs x 4 issue slots "
+                       "x 2070 MHz")}
 
     # ---- error and CPU baseline (rank 0, one GPU)
     cpu = None
