@@ -210,8 +210,11 @@ gbd_status gbd_field(const gbd_beamlet* beamlets, int32_t n_beamlets, double wav
  *          amplitude can change by more than 64 over 8 rows (the row-pair scheme then falls
  *          back to direct evaluation), bit 2 if it can change by more than 64 over 8
  *          columns 32 apart (the row-pair scheme then evaluates each amplitude instead of
- *          carrying it along the row) and bit 3 if some beamlet's T is not exactly 1 (the
- *          field has a uv term; without one the row-pair kernels leave out T's update).
+ *          carrying it along the row), bit 3 if some beamlet has a uv term (auv or puv not
+ *          zero; without one T is exactly 1, the row-pair kernels leave out its update and
+ *          the row triples and quadruples run) and bit 4 if its log2 amplitude can change
+ *          by more than 64 over 24 rows (the row triples and quadruples then hand the
+ *          field to the row pairs).
  *   F64:   16 doubles per beamlet [tile][field f = 0..7][b % 64][2 doubles], same order, the
  *          phase in turns (phase / 2 pi), field 7 = S = exp of twice the uu coefficient as
  *          a complex number (re, im), the second ratio of a row recurrence; wide_flag is

@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             gbd::mixed_tile_pair<CB, WIDE>(ts.tile(k), colf, rowf, acc);
         } else {
             __syncwarp();  // every lane is done with the previous tile's row terms
-            gbd::mixed_pair_rows<gbd::kPairRowF4>(ts.tile(k), rowf, ent, lane);
+            gbd::mixed_pair_rows(ts.tile(k), rowf, ent, lane);
             __syncwarp();
             gbd::mixed_tile_pair_rows<CB, CROSS>(ts.tile(k), ent, colf, acc);
         }
@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     __shared__ int flag;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    float4* ent = dyn4 + kStages * kTileF4 + warp * (gbd::kTripleRowF4 * gbd::kTile);
+    float4* ent = dyn4 + kStages * kTileF4 + warp * (gbd::kRowsF4 * gbd::kTile);
     const int t0 = blockIdx.z * tiles_per_split;
     gbd::init_stream_barriers(full, empty, tid);
     gbd::TileStream<float4, kTileF4> ts{stage, full, empty, coef + (size_t)t0 * kTileF4,
@@ -242,9 +242,9 @@ __global__ void __launch_bounds__(kThreads, 2)
             break;
         }
         __syncwarp();  // every lane is done with the previous tile's row terms
-        gbd::mixed_pair_rows<gbd::kTripleRowF4>(ts.tile(k), rowf, ent, lane);
+        gbd::mixed_rows_terms<RB>(ts.tile(k), rowf, ent, lane);
         __syncwarp();
-        gbd::mixed_tile_rows<RB, CB>(ts.tile(k), ent, colf, acc);
+        gbd::mixed_tile_rows<RB, CB>(ent, colf, acc);
         if (!ts.release(k, lane, warp, spins)) {
             ok = false;
             ++k;
@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 
 constexpr size_t rows_smem_bytes() {
     return (size_t)kStages * gbd::kMixedTileBytes +
-           (size_t)kWarps * gbd::kTripleRowF4 * gbd::kTile * sizeof(float4);
+           (size_t)kWarps * gbd::kRowsF4 * gbd::kTile * sizeof(float4);
 }
 
 template <int CB>

@@ -240,15 +240,10 @@ __device__ __forceinline__ void mixed_tile_pair(const float4* __restrict__ st,
 //               tu-slopes (the quadratic form with tv = v - v_c substituted),
 //   ent[1][b] = (32 sa + 1024 a_uu, 32 sp, 8 (a_v + a_vv (2 tv + 8)), 8 (p_v + p_vv (2 tv + 8))),
 //   ent[2][b] = (64 a_uu, 64 p_uu, 8 a_uv, 8 p_uv),
-//   ent[3][b] = (sig = 2^(2048 a_uu), K = 2^(128 a_vv) e^(i 128 p_vv), 0)  (row triples),
-// so that the tile loops form the first-row amplitude and phase, the amplitude's first
-// ratio rho, the phase step d1 and the 8-row step factor's exponent with one or two FFMA
-// each in the thread's first column tu0.  sig is the amplitude ratio's own ratio along a
-// row; K the ratio of consecutive 8-row step factors.  NF4 (kPairRowF4 or kTripleRowF4)
-// float4 per beamlet and warp.
+// so that mixed_tile_pair_rows forms the first-row amplitude and phase, the amplitude's
+// first ratio rho, the phase step d1 and the 8-row step factor's exponent with one or two
+// FFMA each in the thread's first column tu0.  kPairRowF4 float4 per beamlet and warp.
 constexpr int kPairRowF4 = 3;
-constexpr int kTripleRowF4 = 4;
-template <int NF4>
 __device__ __forceinline__ void mixed_pair_rows(const float4* __restrict__ st, float rowf,
                                                 float4* __restrict__ ent, int lane) {
 #pragma unroll
@@ -268,14 +263,56 @@ __device__ __forceinline__ void mixed_pair_rows(const float4* __restrict__ st, f
         ent[kTile + b] = make_float4(fmaf(1024.0f, q2.x, 32.0f * sa), 32.0f * sp,
                                      8.0f * fmaf(q3.x, w, q1.z), 8.0f * fmaf(q3.y, w, q1.w));
         ent[2 * kTile + b] = make_float4(64.0f * q2.x, 64.0f * q2.y, 8.0f * q2.z, 8.0f * q2.w);
-        if (NF4 > 3) {
-            // K's phase reduced exactly (once per warp and beamlet, so the cost is small)
-            const float km = mufu_ex2(128.0f * q3.x);
-            const float kp =
-                frac_turns(128.0f * q3.y * 0.15915494309189533577f) * 6.28318530717958647692f;
-            ent[3 * kTile + b] = make_float4(mufu_ex2(2048.0f * q2.x), km * mufu_cos(kp),
-                                             km * mufu_sin(kp), 0.0f);
+    }
+}
+
+// Row terms of a tile for the row triples and quadruples, which run only on fields
+// without a uv term (a_uv = p_uv = 0 for every beamlet, the projection's cross flag
+// clear).  The 8-row step factor R = exp(8 (c_v + c_vv (2 tv + 8))) then does not depend
+// on the column, so it and its products S_2 = R (R K), S_3 = S_2 (R K^2)
+// (K = exp(128 c_vv), the ratio of consecutive step factors) are the same for all lanes
+// of the warp and are formed here, once per warp and beamlet, with their phases reduced
+// exactly.  Lane l takes beamlets l and l + 32; kRowsF4 float4 per beamlet and warp:
+//   ent[0][b] = (u_c, ra, rp, sa),  ent[1][b] = (sp, 32 sa + 1024 a_uu, 32 sp, sig),
+//   ent[2][b] = (64 a_uu, 64 p_uu, R),  ent[3][b] = (S_2, S_3),
+// with ra, rp, sa, sp as in mixed_pair_rows and sig = 2^(2048 a_uu).
+constexpr int kRowsF4 = 4;
+template <int RB>
+__device__ __forceinline__ void mixed_rows_terms(const float4* __restrict__ st, float rowf,
+                                                 float4* __restrict__ ent, int lane) {
+    const float kTwoPi = 6.28318530717958647692f, kInvTwoPi = 0.15915494309189533577f;
+#pragma unroll
+    for (int h = 0; h < kTile / 32; ++h) {
+        const int b = lane + 32 * h;
+        const float4 q0 = st[b];
+        const float4 q1 = st[kTile + b];
+        const float4 q2 = st[2 * kTile + b];
+        const float4 q3 = st[3 * kTile + b];
+        const float tv = rowf - q0.y;
+        const float ra = fmaf(tv, fmaf(q3.x, tv, q1.z), q0.z);
+        const float rp = fmaf(tv, fmaf(q3.y, tv, q1.w), q0.w);
+        const float sa = fmaf(q2.z, tv, q1.x);
+        const float sp = fmaf(q2.w, tv, q1.y);
+        const float w = fmaf(2.0f, tv, 8.0f);
+        // R = 2^(8 (a_v + a_vv w)) e^(i 8 (p_v + p_vv w)), K likewise with 128 a_vv, 128 p_vv
+        const float gp = frac_turns(8.0f * fmaf(q3.y, w, q1.w) * kInvTwoPi) * kTwoPi;
+        const float gm = mufu_ex2(8.0f * fmaf(q3.x, w, q1.z));
+        const float2 R = make_float2(gm * mufu_cos(gp), gm * mufu_sin(gp));
+        const float kp = frac_turns(128.0f * q3.y * kInvTwoPi) * kTwoPi;
+        const float km = mufu_ex2(128.0f * q3.x);
+        const float2 K = make_float2(km * mufu_cos(kp), km * mufu_sin(kp));
+        const float2 f2 = make_float2(fmaf(R.x, K.x, -R.y * K.y), fmaf(R.x, K.y, R.y * K.x));
+        const float2 S2 = make_float2(fmaf(R.x, f2.x, -R.y * f2.y), fmaf(R.x, f2.y, R.y * f2.x));
+        float2 S3 = make_float2(0.0f, 0.0f);
+        if (RB > 3) {
+            const float2 f3 = make_float2(fmaf(f2.x, K.x, -f2.y * K.y), fmaf(f2.x, K.y, f2.y * K.x));
+            S3 = make_float2(fmaf(S2.x, f3.x, -S2.y * f3.y), fmaf(S2.x, f3.y, S2.y * f3.x));
         }
+        ent[b] = make_float4(q0.x, ra, rp, sa);
+        ent[kTile + b] = make_float4(sp, fmaf(1024.0f, q2.x, 32.0f * sa), 32.0f * sp,
+                                     mufu_ex2(2048.0f * q2.x));
+        ent[2 * kTile + b] = make_float4(64.0f * q2.x, 64.0f * q2.y, R.x, R.y);
+        ent[3 * kTile + b] = make_float4(S2.x, S2.y, S3.x, S3.y);
     }
 }
 
@@ -332,51 +369,37 @@ __device__ __forceinline__ void mixed_tile_pair_rows(const float4* __restrict__ 
 }
 
 // Row triples (RB = 3: rows v, v + 8, v + 16) and quadruples (RB = 4: also v + 24) for
-// fields without a uv term (every T exactly 1): the 8-row step factor R is then constant
-// along the thread's row, the next ones are R K and R K^2 (K from mixed_pair_rows), so row
-// 8 r below the first is the first times S_r = R (R K) ... (R K^(r-1)).  Per beamlet and
-// thread the setup of mixed_tile_pair_rows plus two complex products per extra row; per
-// column the first row's value E0 = amp (cos, sin) and its products with every S_r
-// (4 FFMA each): 19 instructions for 3 pixels, 23 for 4, and no MUFU operation beyond the
-// first row's sin + cos: 22 MUFU operations per 8 RB pixels.  Requires the steep and
-// multi-row steep flags clear (every |log2 S_r| within 64).
+// fields without a uv term, on the row terms of mixed_rows_terms: row 8 r below the first
+// is the first times S_r (S_1 = R), the same for the whole row.  Per beamlet and thread
+// only the first row's amplitude and phase polynomials in the thread's first column tu0
+// are left (2 ex2 and 7 FMA-pipe instructions); per column the first row's value
+// E0 = amp (cos, sin) and 4 FFMA per later row: 19 instructions for 3 pixels, 23 for 4,
+// 16 sin/cos + 2 ex2 per 8 RB pixels.  The products a_uu tu0 and 1024 c^2 p_uu are formed
+// as (64 a_uu)(tu0 / 64) and 16 c^2 (64 p_uu), the same values exactly.  Requires the
+// steep and multi-row steep flags clear (every |log2 S_r| within 64).
 template <int RB, int CB>
-__device__ __forceinline__ void mixed_tile_rows(const float4* __restrict__ st,
-                                                const float4* __restrict__ ent,
+__device__ __forceinline__ void mixed_tile_rows(const float4* __restrict__ ent,
                                                 const float (&colf)[CB],
                                                 float2 (&acc)[RB][CB]) {
     static_assert(RB == 3 || RB == 4, "row triples or quadruples");
-    const float* stf = reinterpret_cast<const float*>(st);
 #pragma unroll 1
     for (int b = 0; b < kTile; ++b) {
-        const float uc = stf[4 * b];                                               // q0.x
-        const float2 quu = reinterpret_cast<const float2*>(st + 2 * kTile + b)[0];  // q2.xy
         const float4 e0 = ent[b];
         const float4 e1 = ent[kTile + b];
         const float4 e2 = ent[2 * kTile + b];
         const float4 e3 = ent[3 * kTile + b];
-        const float tu0 = colf[0] - uc;
-        const float ga = fmaf(e2.z, tu0, e1.z);
-        const float gp = fmaf(e2.w, tu0, e1.w);  // within 64 rad: the field is not wide
-        const float x0 = fmaf(tu0, fmaf(quu.y, tu0, e0.w), e0.y);
-        const float d1 = fmaf(e2.y, tu0, e1.y);
-        const float gm = mufu_ex2(ga);
-        // S_1 = R, then step factor f_r = f_(r-1) K and S_r = S_(r-1) f_r
-        float2 S[RB - 1];
-        S[0] = make_float2(gm * mufu_cos(gp), gm * mufu_sin(gp));
-        float2 f = S[0];
-#pragma unroll
-        for (int r = 1; r < RB - 1; ++r) {
-            f = make_float2(fmaf(f.x, e3.y, -f.y * e3.z), fmaf(f.x, e3.z, f.y * e3.y));
-            S[r] = make_float2(fmaf(S[r - 1].x, f.x, -S[r - 1].y * f.y),
-                               fmaf(S[r - 1].x, f.y, S[r - 1].y * f.x));
-        }
-        float amp = mufu_ex2(fmaf(tu0, fmaf(quu.x, tu0, e0.z), e0.x));
-        float rho = mufu_ex2(fmaf(e2.x, tu0, e1.x));
-        const float sig = e3.x;
+        const float2 S[3] = {make_float2(e2.z, e2.w), make_float2(e3.x, e3.y),
+                             make_float2(e3.z, e3.w)};
+        const float tu0 = colf[0] - e0.x;
+        const float t64 = tu0 * 0.015625f;
+        const float x0 = fmaf(tu0, fmaf(e2.y, t64, e1.x), e0.z);
+        const float d1 = fmaf(e2.y, tu0, e1.z);
+        float amp = mufu_ex2(fmaf(tu0, fmaf(e2.x, t64, e0.w), e0.y));
+        float rho = mufu_ex2(fmaf(e2.x, tu0, e1.y));
+        const float sig = e1.w;
 #pragma unroll
         for (int c = 0; c < CB; ++c) {
-            const float x = c == 0 ? x0 : fmaf((float)(1024 * c * c), quu.y, fmaf((float)c, d1, x0));
+            const float x = c == 0 ? x0 : fmaf((float)(16 * c * c), e2.y, fmaf((float)c, d1, x0));
             // the first row's value E0 once, then E0 S_r into the later rows
             const float ex = amp * mufu_cos(x), ey = amp * mufu_sin(x);
             acc[0][c].x += ex;

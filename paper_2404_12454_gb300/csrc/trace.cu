@@ -407,8 +407,11 @@ __device__ __forceinline__ unsigned write_mixed(float4* __restrict__ out, long l
         f1 = make_float4((float)q.a[1], (float)p[1], (float)q.a[2], (float)p[2]);
         f2 = make_float4((float)q.a[3], (float)p[3], (float)q.a[4], (float)p[4]);
         f3 = make_float4((float)q.a[5], (float)p[5], tm * cs, tm * sn);
-        // without a uv term T is exactly 1 and the row-pair kernels may skip its update
-        if (!(f3.z == 1.0f && f3.w == 0.0f)) flags |= gbd::kFlagCross;
+        // without a uv term (both coefficients exactly 0) T is exactly 1 and the 8-row step
+        // factor the same on every column: the row-pair kernels skip T's update and the
+        // row triples / quadruples form the factors once per warp
+        if (!(f2.z == 0.0f && f2.w == 0.0f && f3.z == 1.0f && f3.w == 0.0f))
+            flags |= gbd::kFlagCross;
     }
     float4* tile = out + (size_t)(t / gbd::kTile) * gbd::kMixedFields * gbd::kTile;
     const int l = (int)(t % gbd::kTile);
