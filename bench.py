@@ -198,14 +198,14 @@ def mufu_mix(rows: int = 1, cols: int = 0, scheme: int = 0):
     beamlet and block: cols + 1 sin/cos pairs (the first row and the exact row-step
     factor) and 4 ex2 (that factor, and the first row's amplitude, its column ratio and the
     ratio's ratio); the second row comes from multiplies on the FMA pipe.  Row triples or
-    quadruples on rows x cols pixels (no uv term): cols + 1 sin/cos pairs and 3 ex2 per
-    block, plus per beamlet and warp of 32 blocks the shared 2 ex2 and one sin/cos pair of
-    the row terms."""
+    quadruples on rows x cols pixels (no uv term): cols sin/cos pairs and 2 ex2 per block,
+    plus per beamlet and warp of 32 blocks the shared 3 ex2 and two sin/cos pairs of the
+    row terms (the step factors R and K, the amplitude ratio's ratio)."""
     if not scheme or not cols:
         return 1.0, 1.0
     if rows in (3, 4):
         px = float(rows * cols)
-        return 3.0 / px + 2.0 / (32 * px), (cols + 1) / px + 1.0 / (32 * px)
+        return 2.0 / px + 3.0 / (32 * px), cols / px + 2.0 / (32 * px)
     return 4.0 / (2 * cols), (cols + 1) / (2.0 * cols)
 
 

@@ -219,7 +219,7 @@ size_t tile_bytes(int precision) {
 
 gbd_shape default_shape(int precision) {
     gbd_shape s;
-    s.rows_per_thread = precision == GBD_PREC_MIXED ? 4 : 1;
+    s.rows_per_thread = precision == GBD_PREC_MIXED ? 3 : 1;
     s.cols_per_thread = precision == GBD_PREC_MIXED ? 8 : 16;
     s.splits = 0;
     s.ms = 0.f;
@@ -248,9 +248,8 @@ int auto_cols(int nx, int min_cols = 2) {
 }
 
 // The shape set for this device and precision, else the default (for the mixed path with
-// its columns per thread fitted to the detector's width: row quadruples on 8 columns,
-// which run the 2 x 8 row pairs themselves for the fields they cannot take, else row
-// pairs).
+// its columns per thread fitted to the detector's width: row triples on 8 columns, which
+// run the 2 x 8 row pairs themselves for the fields they cannot take, else row pairs).
 gbd_shape stored_shape(int precision, const gbd_detector* D) {
     {
         std::lock_guard<std::mutex> lk(g_mu);
@@ -260,7 +259,7 @@ gbd_shape stored_shape(int precision, const gbd_detector* D) {
     gbd_shape s = default_shape(precision);
     if (precision == GBD_PREC_MIXED && D) {
         s.cols_per_thread = auto_cols(D->nx);
-        s.rows_per_thread = s.cols_per_thread == 8 ? 4 : 2;
+        s.rows_per_thread = s.cols_per_thread == 8 ? 3 : 2;
     }
     return s;
 }
