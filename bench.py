@@ -40,13 +40,13 @@ MUFU_EX2_PER_CLK_SM = 32
 MUFU_SINCOS_PER_CLK_SM = 16
 GB300_SMS = 152
 GB300_MAX_MHZ = 2070.0
-# DRAM bytes per launch of the 4 x 8 row-quadruple field kernel on airy_large from one ncu
-# capture (profiles/field_mixed_rows_kernel_airy_large.md) at 90 beamlet splits, and its
+# DRAM bytes per launch of the 3 x 8 row-triple field kernel on airy_large from one ncu
+# capture (profiles/field_mixed_rows_kernel_airy_large.md) at 62 beamlet splits, and its
 # issued warp-instructions per 32 evaluations.  The reads are the record tiles; the writes
 # are the split partial fields, which scale with the split count.
-FIELD_MIXED_NCU = {"kernel": "field_mixed_rows_kernel<4, 8> (4x8 row quadruples)",
-                   "read": 3.682048e6, "write": 128.391424e6, "splits": 90, "rows": 4, "cols": 8,
-                   "scheme": 1, "inst_per_32_evals": 7.02}
+FIELD_MIXED_NCU = {"kernel": "field_mixed_rows_kernel<3, 8> (3x8 row triples)",
+                   "read": 3.715584e6, "write": 69.152512e6, "splits": 62, "rows": 3, "cols": 8,
+                   "scheme": 1, "inst_per_32_evals": 7.22}
 ISSUE_PER_CLK_SM = 4  # warp-instructions issued per clock and SM (one per sub-partition)
 
 
