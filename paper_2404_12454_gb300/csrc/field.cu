@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             gbd::mixed_tile_pair<CB, WIDE>(ts.tile(k), colf, rowf, acc);
         } else {
             __syncwarp();  // every lane is done with the previous tile's row terms
-            gbd::mixed_pair_rows(ts.tile(k), rowf, ent, lane);
+            gbd::mixed_pair_rows<CROSS>(ts.tile(k), rowf, ent, lane);
             __syncwarp();
             gbd::mixed_tile_pair_rows<CB, CROSS>(ts.tile(k), ent, colf, acc);
         }

@@ -242,8 +242,12 @@ __device__ __forceinline__ void mixed_tile_pair(const float4* __restrict__ st,
 //   ent[2][b] = (64 a_uu, 64 p_uu, 8 a_uv, 8 p_uv),
 // so that mixed_tile_pair_rows forms the first-row amplitude and phase, the amplitude's
 // first ratio rho, the phase step d1 and the 8-row step factor's exponent with one or two
-// FFMA each in the thread's first column tu0.  kPairRowF4 float4 per beamlet and warp.
+// FFMA each in the thread's first column tu0.  Without a uv term (CROSS = false, the
+// projection's cross flag clear) the step factor R does not depend on the column and
+// ent[1][b].zw holds R itself, formed here once per warp with its phase reduced exactly.
+// kPairRowF4 float4 per beamlet and warp.
 constexpr int kPairRowF4 = 3;
+template <bool CROSS>
 __device__ __forceinline__ void mixed_pair_rows(const float4* __restrict__ st, float rowf,
                                                 float4* __restrict__ ent, int lane) {
 #pragma unroll
@@ -260,8 +264,15 @@ __device__ __forceinline__ void mixed_pair_rows(const float4* __restrict__ st, f
         const float sp = fmaf(q2.w, tv, q1.y);
         const float w = fmaf(2.0f, tv, 8.0f);
         ent[b] = make_float4(ra, rp, sa, sp);
-        ent[kTile + b] = make_float4(fmaf(1024.0f, q2.x, 32.0f * sa), 32.0f * sp,
-                                     8.0f * fmaf(q3.x, w, q1.z), 8.0f * fmaf(q3.y, w, q1.w));
+        const float ga = 8.0f * fmaf(q3.x, w, q1.z), gp = 8.0f * fmaf(q3.y, w, q1.w);
+        if (CROSS) {
+            ent[kTile + b] = make_float4(fmaf(1024.0f, q2.x, 32.0f * sa), 32.0f * sp, ga, gp);
+        } else {
+            const float gr = frac_turns(gp * 0.15915494309189533577f) * 6.28318530717958647692f;
+            const float gm = mufu_ex2(ga);
+            ent[kTile + b] = make_float4(fmaf(1024.0f, q2.x, 32.0f * sa), 32.0f * sp,
+                                         gm * mufu_cos(gr), gm * mufu_sin(gr));
+        }
         ent[2 * kTile + b] = make_float4(64.0f * q2.x, 64.0f * q2.y, 8.0f * q2.z, 8.0f * q2.w);
     }
 }
@@ -320,7 +331,8 @@ __device__ __forceinline__ void mixed_rows_terms(const float4* __restrict__ st, 
 // terms of mixed_pair_rows: per beamlet and thread only the column-dependent setup is
 // left (about 27 instructions instead of 43 for the 2 x CB pixels).  CROSS = false is
 // for fields without a uv term (the projection's cross flag clear): there every T is
-// exactly 1, R(u + 32) = R(u) T is the identity, and its update is left out.
+// exactly 1, R(u + 32) = R(u) T is the identity, and its update is left out; R itself
+// comes from the warp's row terms (about 19 instructions of setup).
 template <int CB, bool CROSS>
 __device__ __forceinline__ void mixed_tile_pair_rows(const float4* __restrict__ st,
                                                      const float4* __restrict__ ent,
@@ -336,12 +348,19 @@ __device__ __forceinline__ void mixed_tile_pair_rows(const float4* __restrict__ 
         const float4 e1 = ent[kTile + b];
         const float4 e2 = ent[2 * kTile + b];
         const float tu0 = colf[0] - uc;
-        const float ga = fmaf(e2.z, tu0, e1.z);
-        const float gp = fmaf(e2.w, tu0, e1.w);  // within 64 rad: the field is not wide
         const float x0 = fmaf(tu0, fmaf(quu.y, tu0, e0.w), e0.y);
         const float d1 = fmaf(e2.y, tu0, e1.y);
-        const float gm = mufu_ex2(ga);
-        float rx = gm * mufu_cos(gp), ry = gm * mufu_sin(gp);
+        float rx, ry;
+        if (CROSS) {
+            const float ga = fmaf(e2.z, tu0, e1.z);
+            const float gp = fmaf(e2.w, tu0, e1.w);  // within 64 rad: the field is not wide
+            const float gm = mufu_ex2(ga);
+            rx = gm * mufu_cos(gp);
+            ry = gm * mufu_sin(gp);
+        } else {  // the same R on every column, from the warp's row terms
+            rx = e1.z;
+            ry = e1.w;
+        }
         float amp = mufu_ex2(fmaf(tu0, fmaf(quu.x, tu0, e0.z), e0.x));
         float rho = mufu_ex2(fmaf(e2.x, tu0, e1.x));
         const float sig = mufu_ex2(2048.0f * quu.x);

@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             }
             if constexpr (PAIR && SMEM && !WIDE) {
                 __syncwarp();  // every lane is done with the previous tile's row terms
-                gbd::mixed_pair_rows(ts.tile(k), rowf[0], ent, lane);
+                gbd::mixed_pair_rows<CROSS>(ts.tile(k), rowf[0], ent, lane);
                 __syncwarp();
                 gbd::mixed_tile_pair_rows<CB, CROSS>(ts.tile(k), ent, colf, acc);
             } else if constexpr (PAIR)
