@@ -192,12 +192,15 @@ def traffic_bytes(tuned):
     return n["read"] + n["write"] * tuned[2] / n["splits"]
 
 
-def mufu_mix(rows: int = 1, cols: int = 0, scheme: int = 0):
+def mufu_mix(rows: int = 1, cols: int = 0, scheme: int = 0, cross: bool = False):
     """MUFU operations per beamlet-pixel evaluation (ex2, and sin = cos) of a launch shape.
     Direct scheme: one ex2, sin and cos per evaluation.  Row pairs on 2 x cols pixels, per
     beamlet and block: cols + 1 sin/cos pairs (the first row and the exact row-step
     factor) and 4 ex2 (that factor, and the first row's amplitude, its column ratio and the
-    ratio's ratio); the second row comes from multiplies on the FMA pipe.  Row triples or
+    ratio's ratio); the second row comes from multiplies on the FMA pipe.  Without a uv term
+    (cross = False, the bench's workloads) the step factor is the same on every column and
+    is formed once per beamlet and warp of 32 blocks: 3 ex2 and cols sin/cos pairs per block,
+    plus that factor's ex2 and sin/cos pair per warp.  Row triples or
     quadruples on rows x cols pixels (no uv term): cols sin/cos pairs and 2 ex2 per block,
     plus per beamlet and warp of 32 blocks the shared 3 ex2 and two sin/cos pairs of the
     row terms (the step factors R and K, the amplitude ratio's ratio)."""
@@ -206,13 +209,16 @@ def mufu_mix(rows: int = 1, cols: int = 0, scheme: int = 0):
     if rows in (3, 4):
         px = float(rows * cols)
         return 2.0 / px + 3.0 / (32 * px), cols / px + 2.0 / (32 * px)
+    if not cross:
+        px = 2.0 * cols
+        return 3.0 / px + 1.0 / (32 * px), cols / px + 1.0 / (32 * px)
     return 4.0 / (2 * cols), (cols + 1) / (2.0 * cols)
 
 
-def peak_evals_const(cols: int = 0, rows: int = 2) -> float:
+def peak_evals_const(cols: int = 0, rows: int = 2, cross: bool = False) -> float:
     """MUFU-bound beamlet-pixel evaluations/s of a GB300 at its maximum clock: the direct
     scheme (cols = 0), or the row-pair / row-triple scheme on rows x cols pixels."""
-    n_ex2, n_sc = mufu_mix(rows, cols, 1 if cols else 0)
+    n_ex2, n_sc = mufu_mix(rows, cols, 1 if cols else 0, cross)
     return GB300_SMS * GB300_MAX_MHZ * 1e6 / (n_ex2 / MUFU_EX2_PER_CLK_SM +
                                               2.0 * n_sc / MUFU_SINCOS_PER_CLK_SM)
 
