@@ -289,8 +289,10 @@ def gbd_project_bytes(n_beamlets: int, precision: int) -> int:
 def gbd_project(beamlets, n_beamlets: int, wavelength: float, detector, precision: int, coeffs,
                 wide_flag=None, stream=None) -> None:
     """Projected records into ``coeffs``; ``wide_flag`` (int32 CUDA tensor, zeroed) gets
-    bit 0 if some beamlet's phase can exceed 256 rad on the detector and bit 1 if the
-    row-pair scheme must fall back to direct evaluation (mixed only)."""
+    the projection's flag bits (mixed only): 0 some beamlet's phase can exceed 256 rad on
+    the detector, 1 the row-pair scheme must fall back to direct evaluation, 2 the
+    amplitude may not be carried along a row, 3 the field has a uv term, 4 the row triples
+    and quadruples must hand the field to the row pairs."""
     _check(lib().gbd_project(_ptr(beamlets), int(n_beamlets), float(wavelength),
                              ctypes.byref(make_detector(detector)), int(precision), _ptr(coeffs),
                              _ptr(wide_flag), _stream(stream)))
@@ -362,7 +364,7 @@ class SweepPlan:
     def __init__(self, system, diameter, n_across, overlap_factor, waist_ratio, detector,
                  shape: Optional[Tuple[int, ...]] = None, stream=None, device="cuda",
                  zones: Optional[Sequence[Tuple[float, float]]] = None):
-        """shape: (rows, cols[, scheme]) per thread; None = the library's default (row
+        """shape: (rows, cols[, scheme]) per thread; None = the library's sweep default (row
         pairs, 8 or 4 columns per thread fitted to the detector's width)."""
         import torch
         n, a, b, c = _instance_arrays(n_across, overlap_factor, waist_ratio)
