@@ -638,9 +638,19 @@ def run_ours(args, world, rank, local):
                "sample": f"{rows.size} of {det.ny} rows x {cols.size} columns x {r['nb']} beamlets "
                          f"({r['evals']:.3g} evals, {r['seconds']:.1f} s, FP64 C + OpenMP)"}
 
-    # trace, projection, field (the instantiation the flag word selects; the others return
-    # at once: one for the direct scheme, three for row pairs), split reduction
-    launches_per_step = 3 + (4 if tuned[4] else 2)
+    # trace, projection, split reduction, and the field kernels of the shape: the
+    # instantiation the flag word selects plus the others, which return at once (direct:
+    # 2; row pairs on 2 or 4 columns: 4; on 8 columns: 5; row triples / quadruples: 6, or
+    # the 5 of the 8-column pairs when a split holds more than 16 tiles)
+    n_tiles = (nb + 63) // 64
+    tps = -(-n_tiles // max(1, tuned[2]))
+    if not tuned[4]:
+        field_launches = 2
+    elif tuned[0] >= 3:
+        field_launches = 6 if tps <= 16 else 5
+    else:
+        field_launches = 5 if tuned[1] >= 8 else 4
+    launches_per_step = 3 + field_launches
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
