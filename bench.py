@@ -640,16 +640,14 @@ def run_ours(args, world, rank, local):
 
     # trace, projection, split reduction, and the field kernels of the shape: the
     # instantiation the flag word selects plus the others, which return at once (direct:
-    # 2; row pairs on 2 or 4 columns: 4; on 8 columns: 5; row triples / quadruples: 6, or
-    # the 5 of the 8-column pairs when a split holds more than 16 tiles)
-    n_tiles = (nb + 63) // 64
-    tps = -(-n_tiles // max(1, tuned[2]))
+    # 2; row pairs on 2 or 4 columns: 3; on 8 columns: 4; row triples / quadruples: 4,
+    # also when a split holds more than 16 tiles and the 8-column pairs run alone)
     if not tuned[4]:
         field_launches = 2
-    elif tuned[0] >= 3:
-        field_launches = 6 if tps <= 16 else 5
+    elif tuned[0] >= 3 or tuned[1] >= 8:
+        field_launches = 4
     else:
-        field_launches = 5 if tuned[1] >= 8 else 4
+        field_launches = 3
     launches_per_step = 3 + field_launches
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

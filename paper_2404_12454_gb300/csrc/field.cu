@@ -34,7 +34,10 @@ __device__ __forceinline__ void record_timeout() { atomicOr(&g_field_status, gbd
 // evaluation.  Several instantiations are launched for one field; each returns at once
 // unless the projection's flag word, masked by `mask`, equals `want` and (if `anyof` is
 // not 0) shares a bit with `anyof`.
-template <int RB, int CB, bool WIDE, bool PAIR>
+// WIDE: 0 narrow phases, 1 every phase reduced exactly, kWideByFlag either, per the
+// flag word's wide bit (the direct steep fallback of the row-pair launches).
+constexpr int kWideByFlag = 2;
+template <int RB, int CB, int WIDE, bool PAIR>
 __global__ void __launch_bounds__(kThreads, 2)
     field_mixed_kernel(const float4* __restrict__ coef, int n_tiles, int tiles_per_split, int nx,
                        int ny, float2* __restrict__ partial, const unsigned* __restrict__ flags,
@@ -75,10 +78,16 @@ __global__ void __launch_bounds__(kThreads, 2)
             ok = false;
             break;
         }
-        if constexpr (PAIR)
-            gbd::mixed_tile_pair<CB, WIDE>(ts.tile(k), colf, rowf[0], acc);
-        else
-            gbd::mixed_tile<RB, CB, WIDE>(ts.tile(k), colf, rowf, acc);
+        if constexpr (PAIR) {
+            gbd::mixed_tile_pair<CB, WIDE == 1>(ts.tile(k), colf, rowf[0], acc);
+        } else if constexpr (WIDE == kWideByFlag) {  // the steep fallback: one launch for both
+            if (fw & gbd::kFlagWide)
+                gbd::mixed_tile<RB, CB, true>(ts.tile(k), colf, rowf, acc);
+            else
+                gbd::mixed_tile<RB, CB, false>(ts.tile(k), colf, rowf, acc);
+        } else {
+            gbd::mixed_tile<RB, CB, WIDE == 1>(ts.tile(k), colf, rowf, acc);
+        }
         gbd::mixed_fold<RB, CB>(acc, hi, lo);
         if (!ts.release(k, lane, warp, spins)) {
             ok = false;
@@ -611,16 +620,15 @@ cudaError_t launch_mixed_pair(const void* coeffs, int n_tiles, const gbd_project
     dim3 grid((p.nx + 32 * CB - 1) / (32 * CB), (p.ny + 15) / 16, L.splits);
     const float4* c = static_cast<const float4*>(coeffs);
     const int tps = L.tiles_per_split;
-    // exactly one runs: narrow, then wide (or column-steep), then the steep fallbacks
-    field_mixed_kernel<2, CB, false, true><<<grid, kThreads, 0, s>>>(
+    (void)kBoth;
+    // exactly one runs: narrow, then wide (or column-steep), then the steep fallback
+    field_mixed_kernel<2, CB, 0, true><<<grid, kThreads, 0, s>>>(
         c, n_tiles, tps, p.nx, p.ny, partial, flags, kAll, 0u, 0u, spins);
-    field_mixed_kernel<2, CB, true, true><<<grid, kThreads, 0, s>>>(
+    field_mixed_kernel<2, CB, 1, true><<<grid, kThreads, 0, s>>>(
         c, n_tiles, tps, p.nx, p.ny, partial, flags, kFlagSteep, 0u, kFlagWide | kFlagColSteep,
         spins);
-    field_mixed_kernel<2, CB, false, false><<<grid, kThreads, 0, s>>>(
-        c, n_tiles, tps, p.nx, p.ny, partial, flags, kBoth, kFlagSteep, 0u, spins);
-    field_mixed_kernel<2, CB, true, false><<<grid, kThreads, 0, s>>>(
-        c, n_tiles, tps, p.nx, p.ny, partial, flags, kBoth, kBoth, 0u, spins);
+    field_mixed_kernel<2, CB, kWideByFlag, false><<<grid, kThreads, 0, s>>>(
+        c, n_tiles, tps, p.nx, p.ny, partial, flags, kFlagSteep, kFlagSteep, 0u, spins);
     return cudaGetLastError();
 }
 
@@ -660,8 +668,8 @@ cudaError_t launch_f64_row(const void* coeffs, int n_tiles, const gbd_project_pa
 // Row pairs on 2 x CB pixels with shared-memory compensation; the direct 2 x 4 kernels (on
 // their own pixel grid, same splits) are the steep-beamlet fallback.
 // With `after_triple` the row-triple (or quadruple) kernel has been launched first and
-// takes the fields with neither a uv term nor multi-row steepness; the narrow no-uv-term
-// row pairs then take only the multi-row-steep ones.
+// takes the fields with neither a uv term nor multi-row steepness; the narrow row pairs
+// with the column factor's update (exact for T = 1 as well) then take the rest.
 template <int CB>
 cudaError_t launch_pair_set(const void* coeffs, int n_tiles, const gbd_project_params& p,
                             const gbd_field_launch& L, void* partial_v, const unsigned* flags,
@@ -684,20 +692,20 @@ cudaError_t launch_pair_set(const void* coeffs, int n_tiles, const gbd_project_p
     dim3 grid24((p.nx + 127) / 128, (p.ny + 15) / 16, L.splits);
     const float4* c = static_cast<const float4*>(coeffs);
     const int tps = L.tiles_per_split;
-    // exactly one runs: narrow without and with a uv term, then wide (or column-steep),
-    // then the steep fallbacks
-    field_mixed_pair_smem_kernel<CB, false, false><<<grid, kThreads, smem, s>>>(
-        c, n_tiles, tps, p.nx, p.ny, partial, flags, kAll | kFlagCross, 0u,
-        after_triple ? gbd::kFlagSteepRows : 0u, spins);
+    (void)kBoth;
+    // exactly one runs: narrow without a uv term (unless the multi-row kernel ran), narrow
+    // with one, then wide (or column-steep), then the steep fallback
+    if (!after_triple)
+        field_mixed_pair_smem_kernel<CB, false, false><<<grid, kThreads, smem, s>>>(
+            c, n_tiles, tps, p.nx, p.ny, partial, flags, kAll | kFlagCross, 0u, 0u, spins);
     field_mixed_pair_smem_kernel<CB, false, true><<<grid, kThreads, smem, s>>>(
-        c, n_tiles, tps, p.nx, p.ny, partial, flags, kAll, 0u, kFlagCross, spins);
+        c, n_tiles, tps, p.nx, p.ny, partial, flags, kAll, 0u,
+        after_triple ? (kFlagCross | gbd::kFlagSteepRows) : kFlagCross, spins);
     field_mixed_pair_smem_kernel<CB, true><<<grid, kThreads, smem, s>>>(
         c, n_tiles, tps, p.nx, p.ny, partial, flags, kFlagSteep, 0u, kFlagWide | kFlagColSteep,
         spins);
-    field_mixed_kernel<2, 4, false, false><<<grid24, kThreads, 0, s>>>(
-        c, n_tiles, tps, p.nx, p.ny, partial, flags, kBoth, kFlagSteep, 0u, spins);
-    field_mixed_kernel<2, 4, true, false><<<grid24, kThreads, 0, s>>>(
-        c, n_tiles, tps, p.nx, p.ny, partial, flags, kBoth, kBoth, 0u, spins);
+    field_mixed_kernel<2, 4, kWideByFlag, false><<<grid24, kThreads, 0, s>>>(
+        c, n_tiles, tps, p.nx, p.ny, partial, flags, kFlagSteep, kFlagSteep, 0u, spins);
     return cudaGetLastError();
 }
 
