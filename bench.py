@@ -456,8 +456,8 @@ def run_ours(args, world, rank, local):
         sweep = {"value": sv, "unit": UNIT, "ms_per_sweep": sweep_ms / args.sweep_steps,
                  "instances": plan.n, "beamlets": plan.beamlets, "evals_per_sweep": plan.evals,
                  "work_items": plan.items,
-                 "shape": "2x8 row pairs (library default)",
-                 "frac_of_mufu_peak": sv / world / peak_evals_const(8),
+                 "shape": "3x8 row triples (library default)",
+                 "frac_of_mufu_peak": sv / world / peak_evals_const(8, rows=3),
                  "frac_of_direct_scheme_mufu_peak": sv / world / peak_evals_const(),
                  "graph": True, "score_range": [float(sc.min()), float(sc.max())],
                  "workload": "1024 instances, airy_small optics, OF~U[1,3], WR~U[0.8,3], "

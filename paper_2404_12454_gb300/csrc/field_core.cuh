@@ -288,43 +288,48 @@ __device__ __forceinline__ void mixed_pair_rows(const float4* __restrict__ st, f
 //   ent[2][b] = (64 a_uu, 64 p_uu, R),  ent[3][b] = (S_2, S_3),
 // with ra, rp, sa, sp as in mixed_pair_rows and sig = 2^(2048 a_uu).
 constexpr int kRowsF4 = 4;
+// The row terms of stage beamlet b, written to ent[k * stride + i] (k = 0..3).
+template <int RB>
+__device__ __forceinline__ void mixed_rows_term(const float4* __restrict__ st, int b, float rowf,
+                                                float4* __restrict__ ent, int i, int stride) {
+    const float kTwoPi = 6.28318530717958647692f, kInvTwoPi = 0.15915494309189533577f;
+    const float4 q0 = st[b];
+    const float4 q1 = st[kTile + b];
+    const float4 q2 = st[2 * kTile + b];
+    const float4 q3 = st[3 * kTile + b];
+    const float tv = rowf - q0.y;
+    const float ra = fmaf(tv, fmaf(q3.x, tv, q1.z), q0.z);
+    const float rp = fmaf(tv, fmaf(q3.y, tv, q1.w), q0.w);
+    const float sa = fmaf(q2.z, tv, q1.x);
+    const float sp = fmaf(q2.w, tv, q1.y);
+    const float w = fmaf(2.0f, tv, 8.0f);
+    // R = 2^(8 (a_v + a_vv w)) e^(i 8 (p_v + p_vv w)), K likewise with 128 a_vv, 128 p_vv
+    const float gp = frac_turns(8.0f * fmaf(q3.y, w, q1.w) * kInvTwoPi) * kTwoPi;
+    const float gm = mufu_ex2(8.0f * fmaf(q3.x, w, q1.z));
+    const float2 R = make_float2(gm * mufu_cos(gp), gm * mufu_sin(gp));
+    const float kp = frac_turns(128.0f * q3.y * kInvTwoPi) * kTwoPi;
+    const float km = mufu_ex2(128.0f * q3.x);
+    const float2 K = make_float2(km * mufu_cos(kp), km * mufu_sin(kp));
+    const float2 f2 = make_float2(fmaf(R.x, K.x, -R.y * K.y), fmaf(R.x, K.y, R.y * K.x));
+    const float2 S2 = make_float2(fmaf(R.x, f2.x, -R.y * f2.y), fmaf(R.x, f2.y, R.y * f2.x));
+    float2 S3 = make_float2(0.0f, 0.0f);
+    if (RB > 3) {
+        const float2 f3 = make_float2(fmaf(f2.x, K.x, -f2.y * K.y), fmaf(f2.x, K.y, f2.y * K.x));
+        S3 = make_float2(fmaf(S2.x, f3.x, -S2.y * f3.y), fmaf(S2.x, f3.y, S2.y * f3.x));
+    }
+    ent[i] = make_float4(q0.x, ra, rp, sa);
+    ent[stride + i] = make_float4(sp, fmaf(1024.0f, q2.x, 32.0f * sa), 32.0f * sp,
+                                  mufu_ex2(2048.0f * q2.x));
+    ent[2 * stride + i] = make_float4(64.0f * q2.x, 64.0f * q2.y, R.x, R.y);
+    ent[3 * stride + i] = make_float4(S2.x, S2.y, S3.x, S3.y);
+}
+
+// All 64 beamlets of the tile: lane l takes beamlets l and l + 32.
 template <int RB>
 __device__ __forceinline__ void mixed_rows_terms(const float4* __restrict__ st, float rowf,
                                                  float4* __restrict__ ent, int lane) {
-    const float kTwoPi = 6.28318530717958647692f, kInvTwoPi = 0.15915494309189533577f;
 #pragma unroll
-    for (int h = 0; h < kTile / 32; ++h) {
-        const int b = lane + 32 * h;
-        const float4 q0 = st[b];
-        const float4 q1 = st[kTile + b];
-        const float4 q2 = st[2 * kTile + b];
-        const float4 q3 = st[3 * kTile + b];
-        const float tv = rowf - q0.y;
-        const float ra = fmaf(tv, fmaf(q3.x, tv, q1.z), q0.z);
-        const float rp = fmaf(tv, fmaf(q3.y, tv, q1.w), q0.w);
-        const float sa = fmaf(q2.z, tv, q1.x);
-        const float sp = fmaf(q2.w, tv, q1.y);
-        const float w = fmaf(2.0f, tv, 8.0f);
-        // R = 2^(8 (a_v + a_vv w)) e^(i 8 (p_v + p_vv w)), K likewise with 128 a_vv, 128 p_vv
-        const float gp = frac_turns(8.0f * fmaf(q3.y, w, q1.w) * kInvTwoPi) * kTwoPi;
-        const float gm = mufu_ex2(8.0f * fmaf(q3.x, w, q1.z));
-        const float2 R = make_float2(gm * mufu_cos(gp), gm * mufu_sin(gp));
-        const float kp = frac_turns(128.0f * q3.y * kInvTwoPi) * kTwoPi;
-        const float km = mufu_ex2(128.0f * q3.x);
-        const float2 K = make_float2(km * mufu_cos(kp), km * mufu_sin(kp));
-        const float2 f2 = make_float2(fmaf(R.x, K.x, -R.y * K.y), fmaf(R.x, K.y, R.y * K.x));
-        const float2 S2 = make_float2(fmaf(R.x, f2.x, -R.y * f2.y), fmaf(R.x, f2.y, R.y * f2.x));
-        float2 S3 = make_float2(0.0f, 0.0f);
-        if (RB > 3) {
-            const float2 f3 = make_float2(fmaf(f2.x, K.x, -f2.y * K.y), fmaf(f2.x, K.y, f2.y * K.x));
-            S3 = make_float2(fmaf(S2.x, f3.x, -S2.y * f3.y), fmaf(S2.x, f3.y, S2.y * f3.x));
-        }
-        ent[b] = make_float4(q0.x, ra, rp, sa);
-        ent[kTile + b] = make_float4(sp, fmaf(1024.0f, q2.x, 32.0f * sa), 32.0f * sp,
-                                     mufu_ex2(2048.0f * q2.x));
-        ent[2 * kTile + b] = make_float4(64.0f * q2.x, 64.0f * q2.y, R.x, R.y);
-        ent[3 * kTile + b] = make_float4(S2.x, S2.y, S3.x, S3.y);
-    }
+    for (int h = 0; h < kTile / 32; ++h) mixed_rows_term<RB>(st, lane + 32 * h, rowf, ent, lane + 32 * h, kTile);
 }
 
 // The narrow instantiation of mixed_tile_pair (same arithmetic, regrouped) on the row
@@ -388,7 +393,8 @@ __device__ __forceinline__ void mixed_tile_pair_rows(const float4* __restrict__ 
 }
 
 // Row triples (RB = 3: rows v, v + 8, v + 16) and quadruples (RB = 4: also v + 24) for
-// fields without a uv term, on the row terms of mixed_rows_terms: row 8 r below the first
+// fields without a uv term, on the row terms of mixed_rows_terms (NB beamlets, SoA with
+// stride NB): row 8 r below the first
 // is the first times S_r (S_1 = R), the same for the whole row.  Per beamlet and thread
 // only the first row's amplitude and phase polynomials in the thread's first column tu0
 // are left (2 ex2 and 7 FMA-pipe instructions); per column the first row's value
@@ -396,17 +402,17 @@ __device__ __forceinline__ void mixed_tile_pair_rows(const float4* __restrict__ 
 // 16 sin/cos + 2 ex2 per 8 RB pixels.  The products a_uu tu0 and 1024 c^2 p_uu are formed
 // as (64 a_uu)(tu0 / 64) and 16 c^2 (64 p_uu), the same values exactly.  Requires the
 // steep and multi-row steep flags clear (every |log2 S_r| within 64).
-template <int RB, int CB>
+template <int RB, int CB, int NB = kTile>
 __device__ __forceinline__ void mixed_tile_rows(const float4* __restrict__ ent,
                                                 const float (&colf)[CB],
                                                 float2 (&acc)[RB][CB]) {
     static_assert(RB == 3 || RB == 4, "row triples or quadruples");
 #pragma unroll 1
-    for (int b = 0; b < kTile; ++b) {
+    for (int b = 0; b < NB; ++b) {
         const float4 e0 = ent[b];
-        const float4 e1 = ent[kTile + b];
-        const float4 e2 = ent[2 * kTile + b];
-        const float4 e3 = ent[3 * kTile + b];
+        const float4 e1 = ent[NB + b];
+        const float4 e2 = ent[2 * NB + b];
+        const float4 e3 = ent[3 * NB + b];
         const float2 S[3] = {make_float2(e2.z, e2.w), make_float2(e3.x, e3.y),
                              make_float2(e3.z, e3.w)};
         const float tu0 = colf[0] - e0.x;

@@ -12,6 +12,7 @@
 // per-item slot.  The finalize kernel sums each instance's items in pixel-block order,
 // so the result does not depend on which CTA ran which item:
 //     score = sqrt((S2/e0^2 - 2 S1/e0 + S0) / n).
+#include <cuda_bf16.h>
 #include <math.h>
 
 #include <algorithm>
@@ -55,6 +56,71 @@ __global__ void __launch_bounds__(256) airy_table_kernel(int nx, int ny, double 
     for (int z = 1; z < R.n; ++z)
         if (u >= R.lo[z] && u < R.hi[z]) mask |= 1u << z;
     out[p] = make_double2(a, (double)mask);
+}
+
+// Epilogue of one work item: the moments per region of the item's pixels (|E| from
+// mag_of(r, c) for the thread's pixel (row0 + 8 r, col0 + 32 c)), reduced by warp
+// shuffles, then across warps in a fixed order into the item's slot: e0, then 4 moments
+// per region.  Every thread of the CTA calls it.
+template <int RB, int CB, class Mag>
+__device__ __forceinline__ void item_moments(Mag mag_of, int2 it, int row0, int col0, int nx,
+                                             int ny, const double2* __restrict__ airy,
+                                             int n_regions, int n_blocks,
+                                             double* __restrict__ moments,
+                                             double (*red)[kMaxRegions][4], double* red_e0) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    double e0 = -1.0;
+#pragma unroll
+    for (int r = 0; r < RB; ++r)
+#pragma unroll
+        for (int c = 0; c < CB; ++c)
+            if (row0 + 8 * r == ny / 2 && col0 + 32 * c == nx / 2) e0 = mag_of(r, c);
+    for (int o = 16; o > 0; o >>= 1) e0 = fmax(e0, __shfl_xor_sync(0xffffffffu, e0, o));
+    if (lane == 0) red_e0[warp] = e0;
+    for (int z = 0; z < n_regions; ++z) {
+        double m0 = 0.0, m1 = 0.0, m2 = 0.0, m3 = 0.0;
+#pragma unroll
+        for (int r = 0; r < RB; ++r)
+#pragma unroll
+            for (int c = 0; c < CB; ++c) {
+                const int row = row0 + 8 * r, col = col0 + 32 * c;
+                if (row >= ny || col >= nx) continue;
+                const double2 A = airy[(size_t)row * nx + col];
+                if (!((unsigned)A.y & (1u << z))) continue;
+                const double mg = mag_of(r, c);
+                m0 += mg * mg;
+                m1 += mg * A.x;
+                m2 += A.x * A.x;
+                m3 += 1.0;
+            }
+        for (int o = 16; o > 0; o >>= 1) {
+            m0 += __shfl_xor_sync(0xffffffffu, m0, o);
+            m1 += __shfl_xor_sync(0xffffffffu, m1, o);
+            m2 += __shfl_xor_sync(0xffffffffu, m2, o);
+            m3 += __shfl_xor_sync(0xffffffffu, m3, o);
+        }
+        if (lane == 0) {
+            red[warp][z][0] = m0;
+            red[warp][z][1] = m1;
+            red[warp][z][2] = m2;
+            red[warp][z][3] = m3;
+        }
+    }
+    __syncthreads();
+    // one slot per item: e0, then 4 moments per region, summed over warps in order
+    const int stride = 1 + 4 * n_regions;
+    double* dst = moments + ((size_t)it.x * n_blocks + it.y) * stride;
+    if (tid == 0) {
+        double s = -1.0;
+        for (int w = 0; w < kWarps; ++w) s = fmax(s, red_e0[w]);
+        dst[0] = s;
+    }
+    if (tid < 4 * n_regions) {
+        const int z = tid / 4, q = tid % 4;
+        double s = 0.0;
+        for (int w = 0; w < kWarps; ++w) s += red[w][z][q];
+        dst[1 + tid] = s;
+    }
 }
 
 // WIDE, PAIR: as in field_mixed_kernel (several instantiations are launched; each returns
@@ -161,59 +227,139 @@ __global__ void __launch_bounds__(kThreads, 2)
             }
             return sqrt(re * re + im * im);
         };
-        double e0 = -1.0;
-#pragma unroll
-        for (int r = 0; r < RB; ++r)
-#pragma unroll
-            for (int c = 0; c < CB; ++c)
-                if (row0 + 8 * r == ny / 2 && col0 + 32 * c == nx / 2) e0 = mag_of(r, c);
-        for (int o = 16; o > 0; o >>= 1) e0 = fmax(e0, __shfl_xor_sync(0xffffffffu, e0, o));
-        if (lane == 0) red_e0[warp] = e0;
-        for (int z = 0; z < n_regions; ++z) {
-            double m0 = 0.0, m1 = 0.0, m2 = 0.0, m3 = 0.0;
-#pragma unroll
-            for (int r = 0; r < RB; ++r)
-#pragma unroll
-                for (int c = 0; c < CB; ++c) {
-                    const int row = row0 + 8 * r, col = col0 + 32 * c;
-                    if (row >= ny || col >= nx) continue;
-                    const double2 A = airy[(size_t)row * nx + col];
-                    if (!((unsigned)A.y & (1u << z))) continue;
-                    const double mg = mag_of(r, c);
-                    m0 += mg * mg;
-                    m1 += mg * A.x;
-                    m2 += A.x * A.x;
-                    m3 += 1.0;
-                }
-            for (int o = 16; o > 0; o >>= 1) {
-                m0 += __shfl_xor_sync(0xffffffffu, m0, o);
-                m1 += __shfl_xor_sync(0xffffffffu, m1, o);
-                m2 += __shfl_xor_sync(0xffffffffu, m2, o);
-                m3 += __shfl_xor_sync(0xffffffffu, m3, o);
-            }
-            if (lane == 0) {
-                red[warp][z][0] = m0;
-                red[warp][z][1] = m1;
-                red[warp][z][2] = m2;
-                red[warp][z][3] = m3;
-            }
-        }
-        __syncthreads();
-        // one slot per item: e0, then 4 moments per region, summed over warps in order
-        const int stride = 1 + 4 * n_regions;
-        double* dst = moments + ((size_t)it.x * n_blocks + it.y) * stride;
-        if (tid == 0) {
-            double s = -1.0;
-            for (int w = 0; w < kWarps; ++w) s = fmax(s, red_e0[w]);
-            dst[0] = s;
-        }
-        if (tid < 4 * n_regions) {
-            const int z = tid / 4, q = tid % 4;
-            double s = 0.0;
-            for (int w = 0; w < kWarps; ++w) s += red[w][z][q];
-            dst[1 + tid] = s;
-        }
+        item_moments<RB, CB>(mag_of, it, row0, col0, nx, ny, airy, n_regions, n_blocks, moments,
+                             red, red_e0);
     }
+}
+
+// Row triples (3 x CB pixels per thread, rows 8 apart) on work items of 256 x 24 pixels.
+// FAST: fields without a uv term or multi-row steepness (mixed_tile_rows, the warp's row
+// terms computed per 32-beamlet half tile); otherwise every pixel is evaluated directly
+// with its phase reduced exactly (mixed_tile<3, CB, true>), which holds for any field.
+// The sums run in FP32 registers for at most kRowsChunkTiles tiles and are then folded
+// with TwoSum into a compensated pair per pixel in shared memory: hi as FP32, the much
+// smaller lo as BF16 (its rounding, 2^-9 of lo, is 2^-33 of hi), which makes 24 pixels a
+// thread fit next to two CTAs per SM.  Dynamic shared memory: the kStages record stages,
+// hi [3 CB][kThreads] float2, lo [3 CB][kThreads] bf16x2, then (FAST) each warp's row
+// terms of 32 beamlets.
+constexpr int kRowsChunkTiles = 16;
+template <int CB, bool FAST>
+__global__ void __launch_bounds__(kThreads, 2)
+    sweep_rows_kernel(const float4* __restrict__ coef, const int2* __restrict__ inst_tiles,
+                      const int2* __restrict__ items, int n_items, int tiles_x, int n_blocks,
+                      int nx, int ny, const double2* __restrict__ airy, int n_regions,
+                      double* __restrict__ moments, int* __restrict__ counter,
+                      const unsigned* __restrict__ flags, unsigned mask, unsigned want,
+                      unsigned anyof, uint32_t spins) {
+    constexpr int RB = 3;
+    const unsigned fw = *flags;
+    if ((fw & mask) != want || (anyof != 0u && (fw & anyof) == 0u)) return;
+    constexpr int kTileF4 = gbd::kMixedFields * gbd::kTile;
+    extern __shared__ __align__(128) float4 sweep_dyn[];
+    float4(*stage)[kTileF4] = reinterpret_cast<float4(*)[kTileF4]>(sweep_dyn);
+    float2* hi = reinterpret_cast<float2*>(sweep_dyn + kStages * kTileF4);  // [RB CB][kThreads]
+    uint32_t* lo = reinterpret_cast<uint32_t*>(hi + RB * CB * kThreads);     // [RB CB][kThreads]
+    float4* ent = reinterpret_cast<float4*>(lo + RB * CB * kThreads) +
+                  (threadIdx.x >> 5) * (gbd::kRowsF4 * 32);
+    __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
+    __shared__ int flag, s_item;
+    __shared__ double red[kWarps][kMaxRegions][4];
+    __shared__ double red_e0[kWarps];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    gbd::init_stream_barriers(full, empty, tid);
+    int g = 0;  // tiles this CTA has streamed so far (keeps the barrier phases in step)
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= n_items) break;
+        const int2 it = items[item];           // (instance, pixel block)
+        const int2 tt = inst_tiles[it.x];      // (first tile, tiles)
+        gbd::TileStream<float4, kTileF4> ts{stage, full, empty, coef + (size_t)tt.x * kTileF4,
+                                            tt.y, g, gbd::kMixedTileBytes, 0};
+        bool ok = ts.start(tid, spins, &flag);
+
+        const int col0 = (it.y % tiles_x) * (32 * CB) + lane;
+        const int row0 = (it.y / tiles_x) * (8 * RB) + warp;
+        float colf[CB], rowf[RB];
+#pragma unroll
+        for (int c = 0; c < CB; ++c) colf[c] = (float)(col0 + 32 * c);
+#pragma unroll
+        for (int r = 0; r < RB; ++r) rowf[r] = (float)(row0 + 8 * r);
+        float2 acc[RB][CB];
+#pragma unroll
+        for (int m = 0; m < RB * CB; ++m) {
+            acc[m / CB][m % CB] = make_float2(0.f, 0.f);
+            hi[m * kThreads + tid] = make_float2(0.f, 0.f);
+            lo[m * kThreads + tid] = 0u;
+        }
+
+        int k = 0;
+        for (; ok && k < ts.nt; ++k) {
+            if (!ts.acquire(k, spins)) {
+                ok = false;
+                break;
+            }
+            if constexpr (FAST) {
+#pragma unroll 1
+                for (int h = 0; h < gbd::kTile / 32; ++h) {
+                    __syncwarp();  // every lane is done with the previous row terms
+                    gbd::mixed_rows_term<RB>(ts.tile(k), 32 * h + lane, rowf[0], ent, lane, 32);
+                    __syncwarp();
+                    gbd::mixed_tile_rows<RB, CB, 32>(ent, colf, acc);
+                }
+            } else {
+                gbd::mixed_tile<RB, CB, true>(ts.tile(k), colf, rowf, acc);
+            }
+            if ((k + 1) % kRowsChunkTiles == 0 || k + 1 == ts.nt) {
+#pragma unroll
+                for (int m = 0; m < RB * CB; ++m) {
+                    const int q = m * kThreads + tid;
+                    const float2 h2 = hi[q];
+                    const uint32_t l2 = lo[q];
+                    float sx, ex, sy, ey;
+                    gbd::two_sum(h2.x, acc[m / CB][m % CB].x, sx, ex);
+                    gbd::two_sum(h2.y, acc[m / CB][m % CB].y, sy, ey);
+                    hi[q] = make_float2(sx, sy);
+                    const float lx = __uint_as_float(l2 << 16) + ex;
+                    const float ly = __uint_as_float(l2 & 0xffff0000u) + ey;
+                    const __nv_bfloat162 lb = __floats2bfloat162_rn(lx, ly);
+                    lo[q] = *reinterpret_cast<const uint32_t*>(&lb);
+                    acc[m / CB][m % CB] = make_float2(0.f, 0.f);
+                }
+            }
+            if (!ts.release(k, lane, warp, spins)) {
+                ok = false;
+                ++k;
+                break;
+            }
+        }
+        // every thread reaches this vote (failed waits end their loops), so the CTA
+        // leaves together when any warp gave up
+        if (!__syncthreads_and(ok)) {
+            atomicOr(&g_sweep_status, gbd::kStatusTimeout);
+            if (tid == 0) ts.drain(k, spins);
+            return;
+        }
+        g += ts.nt;
+        auto mag_of = [&](int r, int c) -> double {
+            const int q = (r * CB + c) * kThreads + tid;
+            const float2 h2 = hi[q];
+            const uint32_t l2 = lo[q];
+            const double re = (double)h2.x + (double)__uint_as_float(l2 << 16);
+            const double im = (double)h2.y + (double)__uint_as_float(l2 & 0xffff0000u);
+            return sqrt(re * re + im * im);
+        };
+        item_moments<RB, CB>(mag_of, it, row0, col0, nx, ny, airy, n_regions, n_blocks, moments,
+                             red, red_e0);
+    }
+}
+
+constexpr size_t sweep_rows_smem(int cb) {
+    return (size_t)kStages * gbd::kMixedTileBytes + (size_t)3 * cb * kThreads * (8 + 4) +
+           (size_t)kWarps * gbd::kRowsF4 * 32 * sizeof(float4);
 }
 
 // Per instance, the moments of its pixel blocks summed in block order, then one score per
@@ -329,6 +475,32 @@ cudaError_t launch_sweep_pair(dim3 grid, cudaStream_t s, const float4* coef, con
     return e;
 }
 
+// Row triples on 3 x CB pixels (work items of 256 x 24 pixels): the fast instantiation for
+// fields without a uv term or multi-row steepness, the direct one (every phase reduced)
+// for all other fields.  Exactly one runs.
+template <int CB>
+cudaError_t launch_sweep_rows(dim3 grid, cudaStream_t s, const float4* coef, const int2* it_tiles,
+                              const int2* items, int n_items, int tiles_x, int n_blocks, int nx,
+                              int ny, const double2* airy, int n_regions, double* moments,
+                              int* counter, const unsigned* flags, uint32_t spins) {
+    constexpr unsigned kAny = gbd::kFlagWide | gbd::kFlagSteep | gbd::kFlagColSteep |
+                              gbd::kFlagCross | gbd::kFlagSteepRows;
+    constexpr size_t smem = sweep_rows_smem(CB);
+    cudaError_t e = cudaFuncSetAttribute(sweep_rows_kernel<CB, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sweep_rows_kernel<CB, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    sweep_rows_kernel<CB, true><<<grid, kThreads, smem, s>>>(
+        coef, it_tiles, items, n_items, tiles_x, n_blocks, nx, ny, airy, n_regions, moments,
+        counter, flags, kAny, 0u, 0u, spins);
+    sweep_rows_kernel<CB, false><<<grid, kThreads, smem, s>>>(
+        coef, it_tiles, items, n_items, tiles_x, n_blocks, nx, ny, airy, n_regions, moments,
+        counter, flags, 0u, 0u, kAny, spins);
+    return cudaGetLastError();
+}
+
 struct SweepShape {
     int rb, cb, scheme;
     sweep_launch_fn fn;
@@ -349,6 +521,8 @@ const SweepShape kSweepShapes[] = {
      (const void*)sweep_kernel<2, 4, false, true, false>, sweep_smem(2, 4, false)},
     {2, 8, GBD_SCHEME_ROW_PAIR, launch_sweep_pair<8>,
      (const void*)sweep_kernel<2, 8, false, true, true, false>, sweep_smem(2, 8, true)},
+    {3, 8, GBD_SCHEME_ROW_PAIR, launch_sweep_rows<8>, (const void*)sweep_rows_kernel<8, true>,
+     sweep_rows_smem(8)},
 };
 
 const SweepShape* find_sweep_shape(int rb, int cb, int scheme) {
@@ -472,8 +646,9 @@ gbd_status gbd_sweep_plan_create(const gbd_system* system, double diameter, cons
         return gbd_set_error(GBD_EINVAL, "instance arrays are NULL");
     if (isinf(system->focal_length))
         return gbd_set_error(GBD_EINVAL, "the Airy score needs a lens (finite focal length)");
-    const int rb = shape ? shape->rows_per_thread : 2;
+    // default: row triples on 8 columns (or row pairs on 4, whichever fits the width)
     const int cb = shape ? shape->cols_per_thread : gbd_auto_cols(detector->nx, 4);
+    const int rb = shape ? shape->rows_per_thread : (cb == 8 ? 3 : 2);
     const int scheme = shape ? shape->scheme : GBD_SCHEME_ROW_PAIR;
     if (!find_sweep_shape(rb, cb, scheme))
         return gbd_set_error(GBD_EINVAL, "unsupported sweep shape");

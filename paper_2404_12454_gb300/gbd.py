@@ -365,7 +365,7 @@ class SweepPlan:
                  shape: Optional[Tuple[int, ...]] = None, stream=None, device="cuda",
                  zones: Optional[Sequence[Tuple[float, float]]] = None):
         """shape: (rows, cols[, scheme]) per thread; None = the library's sweep default (row
-        pairs, 8 or 4 columns per thread fitted to the detector's width)."""
+        triples on 8 columns or row pairs on 4, fitted to the detector's width)."""
         import torch
         n, a, b, c = _instance_arrays(n_across, overlap_factor, waist_ratio)
         self.n = n

@@ -73,7 +73,7 @@ def test_sweep_deterministic_graph_and_shapes():
     gbd.gbd_sync()
     assert torch.equal(a, b) and torch.equal(a, c) and torch.equal(c, d)
     for shape in ((1, 4), (2, 2), (2, 4), (4, 2), (2, 4, gbd.GBD_SCHEME_ROW_PAIR),
-                  (2, 8, gbd.GBD_SCHEME_ROW_PAIR)):
+                  (2, 8, gbd.GBD_SCHEME_ROW_PAIR), (3, 8, gbd.GBD_SCHEME_ROW_PAIR)):
         p2 = gbd.sweep_plan(sw, shape=shape)
         e = p2.run().clone()
         gbd.gbd_sync()
@@ -81,12 +81,12 @@ def test_sweep_deterministic_graph_and_shapes():
 
 
 def test_full_sweep_seeded_subset_matches_oracle():
-    """The 1024-instance sweep in one persistent launch (default shape: 2 x 8 row pairs);
+    """The 1024-instance sweep in one persistent launch (default shape: 3 x 8 row triples);
     16 seeded instances re-scored by the oracle (chosen across every beamlet count, at
     most one of 256 across)."""
     sw = W.sweep()
     plan = gbd.sweep_plan(sw)
-    assert plan.n == 1024 and plan.items == 1024 * 16  # default blocks: 256 x 16 pixels
+    assert plan.n == 1024 and plan.items == 1024 * 11  # default blocks: 256 x 24 pixels
     got = plan.run().cpu().numpy()
     gbd.gbd_sync()
     assert np.all(np.isfinite(got))
@@ -110,7 +110,7 @@ def test_sweep_autotune_picks_a_supported_shape():
                                               sw.overlap_factor, sw.waist_ratio, sw.detector,
                                               ws, scores)
     assert (r, c, scheme) in ((1, 4, 0), (2, 2, 0), (2, 4, 0), (4, 2, 0), (2, 4, 1),
-                              (2, 8, 1)) and ms > 0
+                              (2, 8, 1), (3, 8, 1)) and ms > 0
 
 
 def test_sweep_rejects_bad_instances():
@@ -163,24 +163,26 @@ def test_zone_scores_match_oracle():
     assert np.array_equal(plain, got[:, 0])
 
 
-def test_sweep_row_pairs_fall_back_on_steep_beamlets():
+@pytest.mark.parametrize("shape", [None, (2, 8, 1), (3, 8, 1)])
+def test_sweep_row_recurrences_fall_back_on_steep_beamlets(shape):
     """Beamlets 2.5 pixels wide on a coarse 96-pixel detector: the projection flags them as
-    too steep for the row-pair recurrence and the default (row-pair) plan evaluates them
+    too steep for the row recurrences and the row-pair and row-triple plans evaluate them
     directly; scores match the oracle's."""
     system, D, _ = W.sweep_optics()
     det = W.Detector(96, 96, 1e-5, 1e-5)
     sw = W.Sweep(system, D, det, (4, 6), (1.0, 1.2), (1.0, 1.5))
-    got = gbd.sweep_plan(sw).run().cpu().numpy()
+    got = gbd.sweep_plan(sw, shape=shape).run().cpu().numpy()
     gbd.gbd_sync()
     want = oracle_scores(sw, range(sw.n_instances))
     assert np.max(np.abs(got - want)) <= SCORE_TOL, (got, want)
 
 
-def test_sweep_general_row_pair_instantiation():
+@pytest.mark.parametrize("shape", [None, (2, 8, 1)])
+def test_sweep_general_row_pair_instantiation(shape):
     """A coarse detector (4 um pixels, +-25 lambda F#) where the beamlets are narrower than
     a thread's column span: the projection flags the amplitude recurrence (bit 2) but not
-    the row pairs (bit 1), so the sweep's general row-pair instantiation runs; scores
-    match the oracle's."""
+    the row pairs (bit 1), so the sweep's general row-pair instantiation (or, for the
+    default row triples, their direct instantiation) runs; scores match the oracle's."""
     import torch
     system, D, _ = W.sweep_optics()
     det = W.Detector(128, 128, 4e-6, 4e-6)
@@ -196,7 +198,7 @@ def test_sweep_general_row_pair_instantiation():
         gbd.gbd_sync()
         flags |= int(flag.item())
     assert flags & 4 and not flags & 2, flags
-    got = gbd.sweep_plan(sw).run().cpu().numpy()
+    got = gbd.sweep_plan(sw, shape=shape).run().cpu().numpy()
     gbd.gbd_sync()
     want = oracle_scores(sw, range(sw.n_instances))
     assert np.max(np.abs(got - want)) <= SCORE_TOL, (got, want)
