@@ -203,8 +203,9 @@ __device__ void trace_one(const Tracer& T, const gbd_grid& g, int N, int i, int 
     *out = r;
 }
 
-// grid: (row j, instance).  Each CTA finds its row's first record index by summing the
-// closed-form extents of the rows before it, then one thread per inside centre.
+// grid: (row j, instance, segment of the row).  Each CTA finds its row's first record
+// index by summing the closed-form extents of the rows before it, then its threads take
+// the row's inside centres in turn with the row's other segments.
 __global__ void __launch_bounds__(128) trace_kernel(gbd_trace_params P,
                                                     const gbd_instance_dev* __restrict__ inst,
                                                     gbd_beamlet* __restrict__ out) {
@@ -229,11 +230,13 @@ __global__ void __launch_bounds__(128) trace_kernel(gbd_trace_params P,
     const int a = row_extent(j, N);
     if (a < 0) return;
     const int i_lo = ((N - 1) - a) / 2;
-    for (int t = threadIdx.x; t <= a; t += blockDim.x)
+    // the row's beamlets are shared by the gridDim.z CTAs of the row (one per thread for
+    // rows of up to 128 gridDim.z beamlets), which spreads long rows over more SMs
+    for (int t = blockIdx.z * blockDim.x + threadIdx.x; t <= a; t += blockDim.x * gridDim.z)
         trace_one(LensTracer{P}, *g, N, i_lo + t, j, out + base + row_off + t);
 }
 
-// Pupil in front of a sequence of conic mirrors, one CTA per grid row (as trace_kernel).
+// Pupil in front of a sequence of conic mirrors, CTAs per grid row as in trace_kernel.
 __global__ void __launch_bounds__(128) trace_mirrors_kernel(gbd_mirror_params M,
                                                             gbd_beamlet* __restrict__ out) {
     const int N = M.n_across;
@@ -249,7 +252,7 @@ __global__ void __launch_bounds__(128) trace_mirrors_kernel(gbd_mirror_params M,
     const int a = row_extent(j, N);
     if (a < 0) return;
     const int i_lo = ((N - 1) - a) / 2;
-    for (int t = threadIdx.x; t <= a; t += blockDim.x)
+    for (int t = blockIdx.z * blockDim.x + threadIdx.x; t <= a; t += blockDim.x * gridDim.z)
         trace_one(MirrorTracer{M}, M.grid, N, i_lo + t, j, out + row_off + t);
 }
 
@@ -524,13 +527,13 @@ cudaError_t gbd_launch_trace_project(const gbd_trace_params& p, int n_instances,
 
 cudaError_t gbd_launch_trace(const gbd_trace_params& p, int n_instances, int max_n_across,
                              const gbd_instance_dev* d_inst, gbd_beamlet* out, cudaStream_t s) {
-    dim3 grid(max_n_across, n_instances);
+    dim3 grid(max_n_across, n_instances, (max_n_across + 127) / 128);
     trace_kernel<<<grid, 128, 0, s>>>(p, d_inst, out);
     return cudaGetLastError();
 }
 
 cudaError_t gbd_launch_trace_mirrors(const gbd_mirror_params& m, gbd_beamlet* out, cudaStream_t s) {
-    trace_mirrors_kernel<<<m.n_across, 128, 0, s>>>(m, out);
+    trace_mirrors_kernel<<<dim3(m.n_across, 1, (m.n_across + 127) / 128), 128, 0, s>>>(m, out);
     return cudaGetLastError();
 }
 
