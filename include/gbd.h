@@ -326,9 +326,12 @@ gbd_status gbd_timing_read(double* total_ms, int64_t* launches);
  * pixel (nx/2, ny/2).
  * gbd_sweep_plan_create: host only; validates, lays out the tables and the work list
  *   ((instance, pixel block) items, instances with the most beamlet tiles first) and the
- *   workspace.  shape = NULL picks row pairs with 8 or 4 columns per thread, whichever
- *   covers the detector's width at the lower estimated cost (8 for widths that are
- *   multiples of 256); a shape's scheme field selects direct or row-pair evaluation.
+ *   workspace.  shape = NULL picks 8 or 4 columns per thread, whichever covers the
+ *   detector's width at the lower estimated cost (8 for widths that are multiples of
+ *   256): row triples (3x8; 256 x 24-pixel items; the sums folded every 16 tiles into a
+ *   compensated pair with its low part in BF16; fields with a uv term, or too steep for
+ *   the recurrence, evaluated directly on the same items) or row pairs (2x4); a shape's
+ *   scheme field selects direct or row-recurrence evaluation.
  * gbd_sweep_bind: records the caller's device workspace (>= gbd_sweep_workspace_bytes,
  *   256-byte aligned; it must outlive the plan's runs), uploads the tables and the Airy
  *   table; synchronises `stream`.
