@@ -69,6 +69,8 @@ def parse():
                          "autotuner's pick (scheme 1 = row pairs)")
     ap.add_argument("--no-telescope", action="store_true",
                     help="skip the App. B telescope (conic-mirror trace + field) line")
+    ap.add_argument("--no-tilted", action="store_true",
+                    help="skip the tilted, aberrated system's mixed field line")
     ap.add_argument("--no-surrogate", action="store_true",
                     help="skip the surrogate-guided search versus grid and random search")
     return ap.parse_args()
@@ -535,6 +537,42 @@ def run_ours(args, world, rank, local):
                      "centre_over_airy_peak": float(abs(Er[tdet.ny // 2, tdet.nx // 2].item())
                                                     / airy_peak)}
 
+    # ---- the tilted, aberrated system (Zernike plate, detector tilted 10 deg / 5 deg):
+    # trace + mixed field at 1024^2 pixels, the default shape (a field with a uv term, so
+    # the row pairs with the column factor's update run); parity on it is a test case
+    tilted = None
+    if not args.no_tilted:
+        twl = W.tilted_zernike()
+        tsys = twl.system
+        ntb = gbd.gbd_beamlet_count(twl.pupil)
+        bt = torch.empty((ntb, gbd.BEAMLET_DOUBLES), dtype=torch.float64, device=dev)
+        wst = gbd.workspace(ntb, twl.detector, MIX, dev)
+        Et = torch.empty((twl.detector.ny, twl.detector.nx), dtype=torch.complex64, device=dev)
+
+        def tz_step():
+            gbd.gbd_trace(tsys, twl.pupil, twl.pupil.overlap_factor, twl.pupil.waist_ratio, bt,
+                          stream)
+            gbd.gbd_field(bt, ntb, tsys.wavelength, twl.detector, MIX, wst, Et, stream)
+        for _ in range(3):
+            tz_step()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b2 = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(3):
+            tz_step()
+        b2.record(stream)
+        torch.cuda.synchronize()
+        gbd.gbd_sync(stream)
+        tz_ms = a.elapsed_time(b2) / 3
+        tr, tc, ts_, tsch = gbd.gbd_field_get_shape(MIX, ntb, twl.detector)
+        tilted = {"workload": f"tilted_zernike: {ntb} beamlets x {twl.detector.nx}x"
+                              f"{twl.detector.ny} pixels, Noll 4-15 plate, detector tilted "
+                              "10 deg about x and 5 deg about y",
+                  "ms_per_field": tz_ms,
+                  "value": ntb * twl.detector.nx * twl.detector.ny / (tz_ms * 1e-3),
+                  "unit": UNIT, "shape": f"{tr}x{tc}, {ts_} splits, scheme {tsch}"}
+
     # ---- surrogate-guided search versus the reference grid and random search
     surrogate = None
     if not args.no_surrogate:
@@ -664,7 +702,7 @@ def run_ours(args, world, rank, local):
                             "scheme": "row_pair" if tuned[4] else "direct",
                             "fixed_by_flag": bool(args.shape)},
         "sweep": sweep, "surrogate": surrogate, "point_evaluation": point,
-        "telescope": telescope,
+        "telescope": telescope, "tilted": tilted,
         "error": error, "roofline": roofline, "cpu_baseline": cpu,
         "gpu_launches": launches_per_step * args.steps,
         "kernel_ms": {k: (v[0] / max(v[1], 1)) for k, v in kt.items()},

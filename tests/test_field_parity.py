@@ -267,6 +267,26 @@ def test_row_triples_and_quadruples_match_the_oracle(name, rows):
         gbd.gbd_field_reset_shape(gbd.GBD_PREC_MIXED)
 
 
+@pytest.mark.parametrize("rows", [3, 4])
+def test_row_triples_hand_uv_term_fields_to_the_row_pairs(rows):
+    """The tilted, aberrated optics on a small patch of the focal plane (beamlets ~170
+    pixels wide): the field has a uv term and no other flag, so behind the row triples /
+    quadruples the narrow row pairs with the column factor's update run; the field
+    matches the oracle for 1 and 2 splits."""
+    wl = W.scaled(W.tilted_zernike(), n_across=16, nx=128, ny=96, keep_span=False)
+    b = gpu_trace(wl)
+    f = projection_flags(b, wl)
+    assert f & 8 and not f & (1 | 2 | 4 | 16), f
+    Eo = oracle.field(oracle.trace(wl.system, wl.pupil), wl.system, wl.detector)
+    try:
+        for splits in (1, 2):
+            gbd.gbd_field_set_shape(gbd.GBD_PREC_MIXED, rows, 8, splits, gbd.GBD_SCHEME_ROW_PAIR)
+            E = gpu_field(b, wl, gbd.GBD_PREC_MIXED)
+            assert rel_l2(E, Eo) <= TOL[gbd.GBD_PREC_MIXED], splits
+    finally:
+        gbd.gbd_field_reset_shape(gbd.GBD_PREC_MIXED)
+
+
 def test_column_steep_fields_use_the_general_row_pair_instantiation():
     """Beamlets ~20 pixels wide against a thread's 224-pixel column span: the projection
     flags the amplitude recurrence along rows as unsafe (bit 2) but not the row pairs
