@@ -256,7 +256,8 @@ typedef struct {
     int32_t scheme;            /* mixed only: GBD_SCHEME_DIRECT, or           */
                                /* GBD_SCHEME_ROW_PAIR (2x2, 2x4, 2x8: the     */
                                /* second row from the first by a complex      */
-                               /* factor; 3x8, 4x8: row triples, quadruples,  */
+                               /* factor; 3x8, 4x8, 4x4: row triples and      */
+                               /* quadruples,                                 */
                                /* for fields without a uv term and splits of  */
                                /* at most 16 tiles, the 2x8 pairs otherwise)  */
 } gbd_shape;

@@ -762,6 +762,8 @@ const ShapeEntry kMixedShapes[] = {
      rows_smem_bytes()},
     {4, 8, GBD_SCHEME_ROW_PAIR, launch_mixed_rows<4, 8>, (const void*)field_mixed_rows_kernel<4, 8>,
      rows_smem_bytes()},
+    {4, 4, GBD_SCHEME_ROW_PAIR, launch_mixed_rows<4, 4>, (const void*)field_mixed_rows_kernel<4, 4>,
+     rows_smem_bytes()},
 };
 // (1,2), (2,2): every pixel evaluated directly (columns 32 apart); (1,8), (1,16), (2,8),
 // (1,32): contiguous row segments advanced by complex multiplies.

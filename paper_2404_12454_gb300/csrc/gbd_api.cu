@@ -652,7 +652,7 @@ gbd_status gbd_autotune_field(const gbd_beamlet* beamlets, int32_t n_beamlets, d
                                     {2, 4, GBD_SCHEME_DIRECT},   {4, 2, GBD_SCHEME_DIRECT},
                                     {2, 2, GBD_SCHEME_ROW_PAIR}, {2, 4, GBD_SCHEME_ROW_PAIR},
                                     {2, 8, GBD_SCHEME_ROW_PAIR}, {3, 8, GBD_SCHEME_ROW_PAIR},
-                                    {4, 8, GBD_SCHEME_ROW_PAIR}};
+                                    {4, 8, GBD_SCHEME_ROW_PAIR}, {4, 4, GBD_SCHEME_ROW_PAIR}};
     static const int kF64[][3] = {{1, 2, 0}, {2, 2, 0}, {1, 8, 0}, {2, 8, 0}, {1, 16, 0}, {1, 32, 0}};
     std::vector<std::array<int, 3>> shapes;
     if (precision == GBD_PREC_MIXED)

@@ -203,7 +203,7 @@ def test_every_shape_and_split_matches(prec):
     Eo = oracle.field(oracle.trace(wl.system, wl.pupil), wl.system, wl.detector)
     D, P = gbd.GBD_SCHEME_DIRECT, gbd.GBD_SCHEME_ROW_PAIR
     shapes = ([(1, 4, D), (2, 2, D), (2, 4, D), (4, 2, D), (2, 2, P), (2, 4, P), (2, 8, P),
-               (3, 8, P), (4, 8, P)]
+               (3, 8, P), (4, 8, P), (4, 4, P)]
               if prec == gbd.GBD_PREC_MIXED
               else [(1, 2, D), (2, 2, D), (1, 8, D), (2, 8, D), (1, 16, D), (1, 32, D)])
     try:
@@ -245,9 +245,9 @@ def test_row_pair_scheme_is_not_flagged_on_the_workloads(name):
         assert f & 8
 
 
-@pytest.mark.parametrize("rows", [3, 4])
+@pytest.mark.parametrize("rows,cols", [(3, 8), (4, 8), (4, 4)])
 @pytest.mark.parametrize("name", ["airy_small", "airy_ragged", "defocused", "airy_48"])
-def test_row_triples_and_quadruples_match_the_oracle(name, rows):
+def test_row_triples_and_quadruples_match_the_oracle(name, rows, cols):
     """Fields without a uv term: the 3 x 8 and 4 x 8 multi-row kernels (FP32 sums over
     splits of at most 16 tiles) give the oracle's field, and so does the row-pair set that
     runs in their place when a split is longer (airy_48: 1,804 beamlets, 29 tiles in one
@@ -260,7 +260,8 @@ def test_row_triples_and_quadruples_match_the_oracle(name, rows):
     Eo = oracle.field(oracle.trace(wl.system, wl.pupil), wl.system, wl.detector)
     try:
         for splits in (1, 2, 5):
-            gbd.gbd_field_set_shape(gbd.GBD_PREC_MIXED, rows, 8, splits, gbd.GBD_SCHEME_ROW_PAIR)
+            gbd.gbd_field_set_shape(gbd.GBD_PREC_MIXED, rows, cols, splits,
+                                    gbd.GBD_SCHEME_ROW_PAIR)
             E = gpu_field(b, wl, gbd.GBD_PREC_MIXED)
             assert rel_l2(E, Eo) <= TOL[gbd.GBD_PREC_MIXED], splits
     finally:
