@@ -259,7 +259,8 @@ typedef struct {
                                /* factor; 3x8, 4x8, 4x4: row triples and      */
                                /* quadruples,                                 */
                                /* for fields without a uv term and splits of  */
-                               /* at most 16 tiles, the 2x8 pairs otherwise)  */
+                               /* at most 16 tiles, the 2 x cols row pairs    */
+                               /* otherwise)                                  */
 } gbd_shape;
 
 #define GBD_SCHEME_DIRECT 0
