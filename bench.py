@@ -40,13 +40,18 @@ MUFU_EX2_PER_CLK_SM = 32
 MUFU_SINCOS_PER_CLK_SM = 16
 GB300_SMS = 152
 GB300_MAX_MHZ = 2070.0
-# DRAM bytes per launch of the 3 x 8 row-triple field kernel on airy_large from one ncu
-# capture (profiles/field_mixed_rows_kernel_airy_large.md) at 62 beamlet splits, and its
-# issued warp-instructions per 32 evaluations.  The reads are the record tiles; the writes
-# are the split partial fields, which scale with the split count.
-FIELD_MIXED_NCU = {"kernel": "field_mixed_rows_kernel<3, 8> (3x8 row triples)",
-                   "read": 3.715584e6, "write": 69.152512e6, "splits": 62, "rows": 3, "cols": 8,
-                   "scheme": 1, "inst_per_32_evals": 7.22}
+# Per-launch DRAM bytes of the multi-row field kernels on airy_large from one ncu capture
+# each (profiles/field_mixed_rows_kernel_airy_large.md), and their issued warp-
+# instructions per 32 evaluations.  The reads are the record tiles; the writes are the
+# split partial fields, which scale with the split count.
+FIELD_MIXED_NCU = [
+    {"kernel": "field_mixed_rows_kernel<4, 4> (4x4 row quadruples)", "read": 3.974656e6,
+     "write": 128.041472e6, "splits": 90, "rows": 4, "cols": 4, "scheme": 1,
+     "inst_per_32_evals": 6.77},
+    {"kernel": "field_mixed_rows_kernel<3, 8> (3x8 row triples)", "read": 3.715584e6,
+     "write": 69.152512e6, "splits": 62, "rows": 3, "cols": 8, "scheme": 1,
+     "inst_per_32_evals": 7.22},
+]
 ISSUE_PER_CLK_SM = 4  # warp-instructions issued per clock and SM (one per sub-partition)
 
 
@@ -186,10 +191,18 @@ class ClockSampler:
                 "samples_in_timed_region": len(inside)}
 
 
+def ncu_capture(tuned):
+    """The ncu record of the launch shape that ran, or None."""
+    for n in FIELD_MIXED_NCU:
+        if (tuned[0], tuned[1], tuned[4]) == (n["rows"], n["cols"], n["scheme"]):
+            return n
+    return None
+
+
 def traffic_bytes(tuned):
     """Per-launch DRAM bytes of the captured kernel, writes scaled to the split count used."""
-    n = FIELD_MIXED_NCU
-    if tuned[0] != n["rows"] or tuned[1] != n["cols"] or tuned[4] != n["scheme"]:
+    n = ncu_capture(tuned)
+    if n is None:
         return None
     return n["read"] + n["write"] * tuned[2] / n["splits"]
 
@@ -632,9 +645,10 @@ def run_ours(args, world, rank, local):
         "achieved": achieved / 1e9, "peak": peak_evals / 1e9, "unit": "Geval/s",
         "frac": achieved / peak_evals,
         "traffic": traffic_bytes(tuned),
-        "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one capture of "
-                           f"{FIELD_MIXED_NCU['kernel']} at {FIELD_MIXED_NCU['splits']} splits; "
-                           "writes scaled to this launch's split count"),
+        "traffic_source": (("ncu dram__bytes_read.sum + dram__bytes_write.sum of one capture of "
+                            f"{ncu_capture(tuned)['kernel']} at {ncu_capture(tuned)['splits']} "
+                            "splits; writes scaled to this launch's split count")
+                           if ncu_capture(tuned) else "no ncu capture of this launch shape"),
         "peak_source": (f"derived: {GB300_SMS} SMs x {GB300_MAX_MHZ:g} MHz / ({n_ex2:.4g}/"
                         f"{MUFU_EX2_PER_CLK_SM} + {2 * n_sc:.4g}/{MUFU_SINCOS_PER_CLK_SM}) clk "
                         "per evaluation"),
@@ -651,11 +665,12 @@ def run_ours(args, world, rank, local):
     }
     # The multi-row kernels need so few MUFU operations that instruction issue binds first:
     # the issue-slot ceiling for the captured kernel's instruction count per evaluation.
-    if traffic_bytes(tuned) is not None:
-        ipe = FIELD_MIXED_NCU["inst_per_32_evals"] / 32.0
+    cap = ncu_capture(tuned)
+    if cap is not None:
+        ipe = cap["inst_per_32_evals"] / 32.0
         issue_peak = GB300_SMS * GB300_MAX_MHZ * 1e6 * ISSUE_PER_CLK_SM / ipe
         roofline["issue_bound"] = {
-            "warp_instructions_per_32_evals": FIELD_MIXED_NCU["inst_per_32_evals"],
+            "warp_instructions_per_32_evals": cap["inst_per_32_evals"],
             "peak": issue_peak / 1e9, "unit": "Geval/s", "frac": achieved / issue_peak,
             "source": ("ncu smsp__inst_executed.sum of the capture; 152 SMs x 4 issue slots "
                        "x 2070 MHz")}
