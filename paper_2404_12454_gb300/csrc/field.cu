@@ -723,8 +723,14 @@ template <int RB, int CB>
 cudaError_t launch_mixed_rows(const void* coeffs, int n_tiles, const gbd_project_params& p,
                               const gbd_field_launch& L, void* partial, const unsigned* flags,
                               uint32_t spins, cudaStream_t s) {
-    if (L.tiles_per_split > kRowsMaxTiles)
-        return launch_pair_set<CB>(coeffs, n_tiles, p, L, partial, flags, spins, s, false);
+    // the row pairs behind: 8 columns per thread (the faster pairs) on detectors at least
+    // 256 pixels wide, else the multi-row shape's own column count
+    auto pairs = [&](bool after) {
+        return p.nx >= 256 || CB == 8
+                   ? launch_pair_set<8>(coeffs, n_tiles, p, L, partial, flags, spins, s, after)
+                   : launch_pair_set<CB>(coeffs, n_tiles, p, L, partial, flags, spins, s, after);
+    };
+    if (L.tiles_per_split > kRowsMaxTiles) return pairs(false);
     constexpr size_t smem = rows_smem_bytes();
     cudaError_t e = cudaFuncSetAttribute(field_mixed_rows_kernel<RB, CB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -735,7 +741,7 @@ cudaError_t launch_mixed_rows(const void* coeffs, int n_tiles, const gbd_project
     field_mixed_rows_kernel<RB, CB><<<grid, kThreads, smem, s>>>(
         static_cast<const float4*>(coeffs), n_tiles, L.tiles_per_split, p.nx, p.ny,
         static_cast<float2*>(partial), flags, kNarrow, 0u, spins);
-    return launch_pair_set<CB>(coeffs, n_tiles, p, L, partial, flags, spins, s, true);
+    return pairs(true);
 }
 
 typedef cudaError_t (*launch_fn)(const void*, int, const gbd_project_params&,
