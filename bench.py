@@ -67,6 +67,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweep-steps", type=int, default=2,
                     help="timed runs of the 1024-instance parameter sweep (0 = skip)")
+    ap.add_argument("--sweep-instances", type=int, default=1024,
+                    help="instances of the sweep (a seeded draw from the same distributions; "
+                         "fewer only for small profiling runs)")
     ap.add_argument("--no-point", action="store_true",
                     help="skip the plane- versus point-evaluation comparison")
     ap.add_argument("--shape", default="",
@@ -446,7 +449,7 @@ def run_ours(args, world, rank, local):
     # as a CUDA graph on its own stream
     sweep = None
     if args.sweep_steps > 0:
-        sw = W.sweep()
+        sw = W.sweep(n_instances=args.sweep_instances)
         sstream = torch.cuda.Stream(device=dev)
         with torch.cuda.stream(sstream):
             plan = gbd.sweep_plan(sw, stream=sstream)
@@ -475,7 +478,7 @@ def run_ours(args, world, rank, local):
                  "frac_of_mufu_peak": sv / world / peak_evals_const(8, rows=3),
                  "frac_of_direct_scheme_mufu_peak": sv / world / peak_evals_const(),
                  "graph": True, "score_range": [float(sc.min()), float(sc.max())],
-                 "workload": "1024 instances, airy_small optics, OF~U[1,3], WR~U[0.8,3], "
+                 "workload": f"{plan.n} instances, airy_small optics, OF~U[1,3], WR~U[0.8,3], "
                              "N~U{16..256}, 256x256 pixels +-5 lambda F#"}
         plan.close()
 
