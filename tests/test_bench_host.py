@@ -1,5 +1,6 @@
 """Host-side logic of bench.py without a GPU: the replica timing across ranks (gloo,
-world size 2) and the reference arm (the FP64 oracle timed on the host cores)."""
+world size 2), the reference arm (the FP64 oracle timed on the host cores) and the
+roofline arithmetic."""
 import json
 import os
 import subprocess
@@ -55,3 +56,33 @@ def test_reference_arm_prints_one_json_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
     assert d["steps"] == 2 and d["warmup"] == 1 and d["higher_is_better"] is True
+
+
+def test_roofline_arithmetic():
+    """The MUFU operations per evaluation behind the bench line's roofline: the direct
+    scheme's 3, the row pairs' (cols + 1) sin/cos pairs and 4 ex2 per 2 x cols block (3 ex2
+    and cols pairs plus the warp's share without a uv term), the multi-row kernels' cols
+    pairs and 2 ex2 per block plus the warp's share; and the peaks derived from 152 SMs at
+    2070 MHz with 32 ex2 and 16 sin/cos per clock and SM."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.mufu_mix() == (1.0, 1.0)
+    assert bench.peak_evals_const() == pytest.approx(152 * 2.07e9 / (1 / 32 + 2 / 16))
+    ex2, sc = bench.mufu_mix(2, 8, 1, cross=True)
+    assert (ex2, sc) == pytest.approx((0.25, 9 / 16))
+    ex2, sc = bench.mufu_mix(2, 8, 1)
+    assert (ex2, sc) == pytest.approx((3 / 16 + 1 / 512, 8 / 16 + 1 / 512))
+    ex2, sc = bench.mufu_mix(3, 8, 1)
+    assert (ex2, sc) == pytest.approx((2 / 24 + 3 / 768, 8 / 24 + 2 / 768))
+    ex2, sc = bench.mufu_mix(4, 4, 1)
+    assert (ex2, sc) == pytest.approx((2 / 16 + 3 / 512, 4 / 16 + 2 / 512))
+    # fewer MUFU operations per evaluation, a higher ceiling
+    assert bench.peak_evals_const(8, rows=3) > bench.peak_evals_const(8) > bench.peak_evals_const()
+    # every recorded ncu capture matches its own shape and scales its writes by splits
+    for cap in bench.FIELD_MIXED_NCU:
+        tuned = (cap["rows"], cap["cols"], cap["splits"], 0.0, cap["scheme"])
+        assert bench.ncu_capture(tuned) is cap
+        assert bench.traffic_bytes(tuned) == pytest.approx(cap["read"] + cap["write"])
+        doubled = (cap["rows"], cap["cols"], 2 * cap["splits"], 0.0, cap["scheme"])
+        assert bench.traffic_bytes(doubled) == pytest.approx(cap["read"] + 2 * cap["write"])
+    assert bench.traffic_bytes((1, 4, 10, 0.0, 0)) is None
