@@ -710,8 +710,13 @@ def run_ours(args, world, rank, local):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "precision": ("mixed: FP64 per-beamlet trace/projection, FP32 per-pixel phase with MUFU "
-                      "ex2/sin/cos" + (" (second row of each pair by an FP32 complex row-step "
-                                       "factor)" if tuned[4] else "") + ", compensated FP32 sum"),
+                      "ex2/sin/cos" + ((" (the rows 8, 16, 24 below each evaluated row by FP32 "
+                                        "complex products with exact row-step factors; FP32 "
+                                        "sums over splits of at most 1,024 beamlets)")
+                                       if tuned[4] and tuned[0] >= 3 else
+                                       (" (second row of each pair by an FP32 complex row-step "
+                                        "factor)") if tuned[4] else "")
+                      + ", splits summed with compensation (Neumaier)"),
         "data": "synthetic (ideal F/10 lens standing in for the paper's traced telescope)",
         "config": config_block(wl, nb), "clocks": clk, "e2e": e2e, "fp64_path": f64,
         "direct_scheme": direct,
