@@ -715,7 +715,8 @@ def run_ours(args, world, rank, local):
                                         "sums over splits of at most 1,024 beamlets)")
                                        if tuned[4] and tuned[0] >= 3 else
                                        (" (second row of each pair by an FP32 complex row-step "
-                                        "factor)") if tuned[4] else "")
+                                        "factor; TwoSum across 64-beamlet tiles)")
+                                       if tuned[4] else " (TwoSum across 64-beamlet tiles)")
                       + ", splits summed with compensation (Neumaier)"),
         "data": "synthetic (ideal F/10 lens standing in for the paper's traced telescope)",
         "config": config_block(wl, nb), "clocks": clk, "e2e": e2e, "fp64_path": f64,
