@@ -174,6 +174,24 @@ def test_degenerate_detectors(prec, shape):
     assert rel_l2(E, Eo) <= TOL[prec]
 
 
+@pytest.mark.parametrize("rows,cols", [(3, 8), (4, 4)])
+@pytest.mark.parametrize("shape", [(1, 1), (1, 300), (300, 1), (33, 7)])
+def test_degenerate_detectors_with_row_triples_and_quadruples(shape, rows, cols):
+    """The multi-row kernels on detectors of one row or column and on a ragged 33 x 7
+    detector (every thread's later rows or columns off the detector)."""
+    nx, ny = shape
+    wl = W.Workload("edge", W.System(1e-6, 0.024, 0.024), W.Pupil(2.4e-3, 9, 1.5, 1.5),
+                    W.Detector(nx, ny, 0.9e-6, 1.1e-6))
+    b = gpu_trace(wl)
+    Eo = oracle.field(oracle.trace(wl.system, wl.pupil), wl.system, wl.detector)
+    try:
+        gbd.gbd_field_set_shape(gbd.GBD_PREC_MIXED, rows, cols, 1, gbd.GBD_SCHEME_ROW_PAIR)
+        E = gpu_field(b, wl, gbd.GBD_PREC_MIXED)
+    finally:
+        gbd.gbd_field_reset_shape(gbd.GBD_PREC_MIXED)
+    assert rel_l2(E, Eo) <= TOL[gbd.GBD_PREC_MIXED]
+
+
 @pytest.mark.parametrize("prec", PRECS)
 def test_single_beamlet_free_space(prec):
     """One beamlet, no lens: the textbook Gaussian through the whole CUDA path."""
