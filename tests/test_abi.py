@@ -216,3 +216,41 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(gbd, "_lib", None)
     with pytest.raises(RuntimeError, match="missing"):
         gbd.lib()
+
+
+def test_sweep_plan_layout_on_the_host(lib):
+    """gbd_sweep_plan_create is host-only: the 1024-instance sweep's work list for the
+    default shape (row triples, 256 x 24-pixel items: 11 per instance on 256^2 pixels) and
+    for row pairs (256 x 16: 16 per instance) and direct 1 x 4 blocks (128 x 8: 64), the
+    same evaluation and beamlet totals (the sum over instances of beamlets x pixels), and
+    unsupported shapes rejected before anything is allocated on a device."""
+    sw = W.sweep()
+    n, a, b, c = gbd._instance_arrays(sw.n_across, sw.overlap_factor, sw.waist_ratio)
+    counts = [gbd.gbd_beamlet_count(sw.pupil(k)) for k in range(n)]
+    npix = sw.detector.nx * sw.detector.ny
+
+    def create(shape):
+        p = ctypes.c_void_p()
+        sh = gbd.gbd_shape(shape[0], shape[1], 1, 0.0, shape[2]) if shape else None
+        st = lib.gbd_sweep_plan_create(ctypes.byref(gbd.make_system(sw.system)),
+                                       float(sw.diameter), a, b, c, n,
+                                       ctypes.byref(gbd.make_detector(sw.detector)),
+                                       ctypes.byref(sh) if sh else None, ctypes.byref(p))
+        return st, p
+
+    for shape, per_instance in ((None, 11), ((3, 8, 1), 11), ((2, 8, 1), 16), ((1, 4, 0), 64)):
+        st, p = create(shape)
+        assert st == gbd.GBD_OK, shape
+        try:
+            ev, nb, items = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int32()
+            assert lib.gbd_sweep_info(p, ctypes.byref(ev), ctypes.byref(nb),
+                                      ctypes.byref(items)) == gbd.GBD_OK
+            assert items.value == n * per_instance, shape
+            assert nb.value == sum(counts)
+            assert ev.value == float(sum(counts) * npix)
+            assert lib.gbd_sweep_workspace_bytes(p) > 64 * nb.value  # the records at least
+        finally:
+            lib.gbd_sweep_plan_destroy(p)
+    for shape in ((3, 4, 1), (4, 4, 1), (2, 8, 0), (3, 3, 1)):
+        st, p = create(shape)
+        assert st == gbd.GBD_EINVAL, shape
