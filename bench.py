@@ -341,6 +341,11 @@ def run_ours(args, world, rank, local):
         tuned = gbd.gbd_autotune_field(beam, nb, sysm.wavelength, det, MIX, tune_ws, out[MIX],
                                        stream)
         del tune_ws
+    # the split count the launches use: whole tiles per split (93 requested -> 90 for
+    # 805 tiles)
+    n_tiles_mix = (nb + 63) // 64
+    tps_mix = -(-n_tiles_mix // max(1, min(tuned[2], n_tiles_mix)))
+    tuned = (tuned[0], tuned[1], -(-n_tiles_mix // tps_mix), tuned[3], tuned[4])
     ws[MIX] = torch.empty(max(256, gbd.gbd_field_workspace_bytes(nb, det, MIX)), dtype=torch.uint8,
                           device=dev)
     for _ in range(args.warmup):
