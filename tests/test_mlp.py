@@ -76,6 +76,11 @@ def test_gradient_matches_reference(B):
 
 
 def test_adam_matches_reference():
+    """The C ABI takes the hyper-parameters as float32, so the reference is given those same
+    values (0.999 as a float is 0.99900001: 1 - beta2 then differs from 0.001 by 1.3e-5
+    relative, which alone moved 6 % of the master weights by one ulp).  What remains is the
+    FP32 rounding of the update (a few ulp of a ~1e-4 step), which flips the last bit of
+    the master weight for about 0.1-0.5 % of the parameters (mostly the smallest ones)."""
     import torch
     rng = np.random.default_rng(4)
     p = rng.normal(size=M.N_PARAMS).astype(np.float32)
@@ -84,18 +89,24 @@ def test_adam_matches_reference():
     g = rng.normal(0, 0.01, size=M.N_PARAMS).astype(np.float32)
     P, Mm, V, G = (torch.tensor(a, device="cuda") for a in (p, m, v, g))
     Wb = torch.empty(M.N_PARAMS, dtype=torch.int16, device="cuda")
-    gbd.gbd_mlp_adam(P, Wb, Mm, V, G, 1e-3, 0.9, 0.999, 1e-8, 7)
+    lr, beta1, beta2, eps = (float(np.float32(h)) for h in (1e-3, 0.9, 0.999, 1e-8))
+    gbd.gbd_mlp_adam(P, Wb, Mm, V, G, lr, beta1, beta2, eps, 7)
     gbd.gbd_sync()
     p2, m2, v2 = M.adam(p.astype(np.float64), m.astype(np.float64), v.astype(np.float64),
-                        g.astype(np.float64), 1e-3, 0.9, 0.999, 1e-8, 7)
+                        g.astype(np.float64), lr, beta1, beta2, eps, 7)
     assert np.max(np.abs(P.cpu().numpy() - p2)) <= 1e-6 * np.max(np.abs(p2))
     assert np.max(np.abs(Mm.cpu().numpy() - m2)) <= 1e-6 * np.max(np.abs(m2))
     assert np.max(np.abs(V.cpu().numpy() - v2)) <= 1e-6 * np.max(np.abs(v2))
-    # the BF16 copy is the reference's rounding of the reference's FP32 master, wherever
-    # the GPU's FP32 master is that same float (over 90 %; the rest differ in the last bit)
+    # the FP32 master is the reference's value rounded to FP32 for at least 99 % of the
+    # parameters; everywhere within one ulp of the result plus 1e-6 of the step (near
+    # zero the step cancels p); the BF16 copy is the rounding of it
     p2f = p2.astype(np.float32)
-    same = P.cpu().numpy() == p2f
-    assert same.mean() > 0.9
+    got = P.cpu().numpy()
+    same = got == p2f
+    assert same.mean() >= 0.99, same.mean()
+    err = np.abs(got.astype(np.float64) - p2)
+    assert np.all(err <= np.spacing(np.abs(p2f)) + 1e-6 * np.abs(p2 - p))
+    assert np.array_equal(Wb.cpu().numpy().view(np.uint16), M.bf16_bits(got))
     assert np.array_equal(Wb.cpu().numpy().view(np.uint16)[same], M.bf16_bits(p2f)[same])
 
 
