@@ -539,7 +539,7 @@ size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
 struct gbd_sweep_plan {
     gbd_trace_params tp;
-    gbd_project_params pp;
+    gbd_project_params pp{};
     double lam_fnum, r3;
     Regions regions;
     int n_inst, max_n, rb, cb, scheme, tiles_x, tiles_y, n_blocks, n_items;
@@ -556,6 +556,8 @@ struct gbd_sweep_plan {
     cudaGraphExec_t graph = nullptr;
     double* graph_scores = nullptr;
     cudaStream_t graph_stream = nullptr;
+    uint32_t graph_spins = 0;  // wait limit baked into the captured launch
+    int graph_device = -1;     // device whose SM count and occupancy sized its grid
 };
 
 unsigned gbd_sweep_status_read_clear() {
@@ -815,7 +817,12 @@ gbd_status gbd_sweep_run_graph(gbd_sweep_plan* P, double* scores, void* stream) 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (s == nullptr || s == cudaStreamLegacy || s == cudaStreamPerThread)
         return gbd_set_error(GBD_EINVAL, "graph capture needs a created (non-default) stream");
-    if (!P->graph || P->graph_scores != scores || P->graph_stream != s) {
+    // the captured kernels hold the wait limit by value: a new limit needs a new capture
+    const uint32_t spins = gbd_wait_spins();
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (!P->graph || P->graph_scores != scores || P->graph_stream != s || P->graph_spins != spins ||
+        P->graph_device != dev) {
         if (P->graph) {
             cudaGraphExecDestroy(P->graph);
             P->graph = nullptr;
@@ -838,6 +845,8 @@ gbd_status gbd_sweep_run_graph(gbd_sweep_plan* P, double* scores, void* stream) 
         }
         P->graph_scores = scores;
         P->graph_stream = s;
+        P->graph_spins = spins;
+        P->graph_device = dev;
     }
     cudaError_t e = cudaGraphLaunch(P->graph, s);
     if (e != cudaSuccess) return gbd_set_error(GBD_ECUDA, cudaGetErrorString(e));

@@ -1,10 +1,15 @@
 """Batched parameter sweep (persistent kernel with fused Airy score) against the oracle.
 
-The oracle scores an instance by tracing it, summing its field on every pixel in FP64 and
-applying the score's definition directly.  The sweep computes the mixed-precision field and
-the score from moments.  A field error of relative L2 eps moves the score by at most about
-2 eps (the score is an RMS over fewer pixels than the field's norm), so the bound here is
-2 x the mixed-path tolerance, 4e-5.
+The oracle scores an instance by tracing it, summing its field in FP64 on the pixels the
+score reads (the disc inside the third dark ring and the centre) and applying the score's
+definition directly.  The sweep computes the mixed-precision field and the score from
+moments.  The score is an RMS of residuals r_i = |E_i|/|E_0| - A_i over n pixels; a field
+error delta_i moves it by mean(r delta)/score to first order, at most RMS(delta) (the
+triangle inequality).  The mixed field's error is about 1.5e-6 of the field's norm, i.e.
+RMS(delta) ~ 1e-7 of the peak over the disc, against scores of 1.2e-4 and up, so the
+scores are compared relatively, to SCORE_RTOL = 1e-3 of the oracle's score.  Near the
+grid optimum (256 across, OF 1.0 .. 1.2) neighbouring scores differ by 4e-5 .. 1.4e-4
+relative; the sweep must rank them as the oracle does.
 """
 import math
 
@@ -17,7 +22,14 @@ from paper_2404_12454_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-SCORE_TOL = 4e-5
+SCORE_RTOL = 1e-3
+
+
+def assert_scores(got, want, rtol=SCORE_RTOL):
+    got, want = np.asarray(got, dtype=np.float64), np.asarray(want, dtype=np.float64)
+    rel = np.abs(got - want) / want
+    assert np.all(np.isfinite(got)) and np.max(rel) <= rtol, (np.max(rel), got, want)
+    return rel
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -29,13 +41,21 @@ def _built():
 
 
 def oracle_scores(sw, idx):
+    """Oracle Airy scores; the field is evaluated on the square of pixels around the
+    centre that holds the scored disc (the score reads no other pixel)."""
+    det = sw.detector
+    lam, F = sw.system.wavelength, sw.system.focal_length / sw.diameter
+    r3 = 10.173468135062722 * lam * F / math.pi
+    hx, hy = (min(int(math.ceil(r3 / p)) + 1, n // 2 - 1) for p, n in
+              ((det.pitch_x, det.nx), (det.pitch_y, det.ny)))
+    cols = np.arange(det.nx // 2 - hx, det.nx // 2 + hx + 1)
+    rows = np.arange(det.ny // 2 - hy, det.ny // 2 + hy + 1)
     out = []
     for k in idx:
-        pupil = sw.pupil(k)
-        b = oracle.trace(sw.system, pupil)
-        E = oracle.field(b, sw.system, sw.detector)
-        out.append(oracle.airy_score(E, sw.detector, sw.system.wavelength,
-                                     sw.system.focal_length / sw.diameter))
+        b = oracle.trace(sw.system, sw.pupil(k))
+        E = np.zeros((det.ny, det.nx), dtype=np.complex128)
+        E[np.ix_(rows, cols)] = oracle.field(b, sw.system, det, cols=cols, rows=rows)
+        out.append(oracle.airy_score(E, det, lam, F))
     return np.array(out)
 
 
@@ -53,8 +73,7 @@ def test_small_sweep_scores_match_oracle():
     got = plan.run().cpu().numpy()
     gbd.gbd_sync()
     want = oracle_scores(sw, range(sw.n_instances))
-    assert np.all(np.isfinite(got))
-    assert np.max(np.abs(got - want)) <= SCORE_TOL, (got, want)
+    assert_scores(got, want)
     # the scores are distinct numbers, not a constant
     assert np.ptp(want) > 1e-3
 
@@ -82,8 +101,8 @@ def test_sweep_deterministic_graph_and_shapes():
 
 def test_full_sweep_seeded_subset_matches_oracle():
     """The 1024-instance sweep in one persistent launch (default shape: 3 x 8 row triples);
-    16 seeded instances re-scored by the oracle (chosen across every beamlet count, at
-    most one of 256 across)."""
+    18 seeded instances re-scored by the oracle: 15 across every beamlet count and the
+    three of 256 across with the smallest overlap factors (the best-scored region)."""
     sw = W.sweep()
     plan = gbd.sweep_plan(sw)
     assert plan.n == 1024 and plan.items == 1024 * 11  # default blocks: 256 x 24 pixels
@@ -93,11 +112,32 @@ def test_full_sweep_seeded_subset_matches_oracle():
     n = np.asarray(sw.n_across)
     rng = np.random.default_rng(240412455)
     idx = []
-    for N, count in ((16, 4), (32, 4), (64, 4), (128, 3), (256, 1)):
+    for N, count in ((16, 4), (32, 4), (64, 4), (128, 3)):
         cand = np.flatnonzero(n == N)
         idx += list(rng.choice(cand, size=count, replace=False))
+    c256 = np.flatnonzero(n == 256)
+    idx += list(c256[np.argsort(np.asarray(sw.overlap_factor)[c256])[:3]])
     want = oracle_scores(sw, idx)
-    assert np.max(np.abs(got[idx] - want)) <= SCORE_TOL, (got[idx], want)
+    assert_scores(got[idx], want)
+
+
+def test_sweep_ranks_the_grid_optimum_neighbourhood_like_the_oracle():
+    """The search's grid optimum is at 256 across, OF 1.0; its neighbours on the search grid
+    (OF 1.1, 1.2, and 1.3, at two waist ratios that do not act on an ideal lens) score
+    4e-5 .. 1e-3 relative above it.  The sweep's scores match the oracle's to the relative
+    bound and order the four overlap factors as the oracle does."""
+    ofs = (1.0, 1.1, 1.2, 1.3)
+    params = [(256, of, wr) for wr in (0.8, 2.0) for of in ofs] + [(128, 1.0, 0.8)]
+    sw = W.sweep_from_params(params)
+    got = gbd.sweep_plan(sw).run().cpu().numpy()
+    gbd.gbd_sync()
+    # the waist ratio does not act: the oracle scores one row and reuses it
+    want4 = oracle_scores(sw, [0, 1, 2, 3])
+    want = np.concatenate([want4, want4, oracle_scores(sw, [8])])
+    assert_scores(got, want)
+    assert np.all(np.diff(want4) > 0)
+    for row in (got[:4], got[4:8]):
+        assert np.array_equal(np.argsort(row), np.argsort(want4)), (row, want4)
 
 
 def test_sweep_autotune_picks_a_supported_shape():
@@ -124,20 +164,33 @@ def test_sweep_rejects_bad_instances():
                       sw.detector)
 
 
-def test_sweep_timeout_reported_then_recovers():
+@pytest.mark.parametrize("graph", [False, True])
+def test_sweep_timeout_reported_then_recovers(graph):
+    """A one-poll wait limit makes the sweep give up and report GBD_ETIMEOUT; with the
+    graph path a graph captured under the default limit is re-captured when the limit
+    changes (and again when it is restored)."""
+    import torch
     sw = small_sweep()
     plan = gbd.sweep_plan(sw)
-    ref = plan.run().clone()
+    s = torch.cuda.Stream()
+
+    def run():
+        with torch.cuda.stream(s):
+            out = plan.run(stream=s, graph=graph)
+        s.synchronize()
+        return out
+
+    ref = run().clone()
     gbd.gbd_sync()
     try:
         gbd.gbd_set_wait_limit(1)
-        plan.run()
+        run()
         with pytest.raises(gbd.GbdError) as ei:
             gbd.gbd_sync()
         assert ei.value.status == gbd.GBD_ETIMEOUT
     finally:
         gbd.gbd_set_wait_limit(0)
-    again = plan.run().clone()
+    again = run().clone()
     gbd.gbd_sync()
     assert bool((again == ref).all())
 
@@ -157,7 +210,7 @@ def test_zone_scores_match_oracle():
         E = oracle.field(b, sw.system, sw.detector)
         want = [oracle.airy_score(E, sw.detector, lam, F)]
         want += [oracle.zone_score(E, sw.detector, lam, F, lo, hi) for lo, hi in W.ANNULAR_ZONES]
-        assert np.max(np.abs(got[k] - np.asarray(want))) <= SCORE_TOL, (k, got[k], want)
+        assert_scores(got[k], want)
     # the plain score column equals a plan without zones
     plain = gbd.sweep_plan(sw).run().cpu().numpy()
     assert np.array_equal(plain, got[:, 0])
@@ -174,7 +227,7 @@ def test_sweep_row_recurrences_fall_back_on_steep_beamlets(shape):
     got = gbd.sweep_plan(sw, shape=shape).run().cpu().numpy()
     gbd.gbd_sync()
     want = oracle_scores(sw, range(sw.n_instances))
-    assert np.max(np.abs(got - want)) <= SCORE_TOL, (got, want)
+    assert_scores(got, want)
 
 
 @pytest.mark.parametrize("shape", [None, (2, 8, 1)])
@@ -201,4 +254,4 @@ def test_sweep_general_row_pair_instantiation(shape):
     got = gbd.sweep_plan(sw, shape=shape).run().cpu().numpy()
     gbd.gbd_sync()
     want = oracle_scores(sw, range(sw.n_instances))
-    assert np.max(np.abs(got - want)) <= SCORE_TOL, (got, want)
+    assert_scores(got, want)
