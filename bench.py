@@ -41,7 +41,7 @@ MUFU_SINCOS_PER_CLK_SM = 16
 GB300_SMS = 152
 GB300_MAX_MHZ = 2070.0
 # Per-launch DRAM bytes of the multi-row field kernels on airy_large from one ncu capture
-# each (profiles/field_mixed_rows_kernel_airy_large.md), and their issued warp-
+# each (the field_mixed_rows_kernel summary under profiles/), and their issued warp-
 # instructions per 32 evaluations.  The reads are the record tiles; the writes are the
 # split partial fields, which scale with the split count.
 FIELD_MIXED_NCU = [

@@ -108,7 +108,13 @@ int32_t gbd_beamlet_count(const gbd_pupil* pupil);
 
 /* Synchronises `stream` and returns GBD_ETIMEOUT if any kernel of this library gave up a
  * bounded wait on the current device since the last gbd_sync (the word is then cleared),
- * GBD_ECUDA on a CUDA error, else GBD_OK. */
+ * GBD_ECUDA on a CUDA error, else GBD_OK.
+ * gbd_sync is the only way to observe GBD_ETIMEOUT.  The status word is one per device,
+ * not per stream or call: a timeout of a kernel on one stream is reported by whichever
+ * gbd_sync on that device reads the word next, and a caller that synchronises by other
+ * means (cudaStreamSynchronize, torch) never sees it.  After a timeout the outputs of the
+ * calls since the previous gbd_sync are undefined; call gbd_sync after each batch of work
+ * whose results are used. */
 gbd_status gbd_sync(void* stream);
 
 /* Test hook: sets the iteration limit of every device-side bounded wait on the current
@@ -174,7 +180,7 @@ gbd_status gbd_trace_mirrors(const gbd_mirror_system* system, const gbd_pupil* p
  * precision GBD_PREC_F64: FP64 throughout, field_out is complex128 [ny][nx].
  * precision GBD_PREC_MIXED: per-beamlet projection in FP64 (constant phase reduced mod
  *   one turn), per-pixel quadratic form in FP32, exp2/sin/cos on the MUFU pipe (phases
- *   reduced exactly first when some beamlet's phase can exceed 256 rad on the detector).
+ *   reduced exactly first when some beamlet's phase can exceed 128 rad on the detector).
  *   With the row-pair scheme (see gbd_shape) only one row of each pair 8 apart is
  *   evaluated so; the row 8 below is that value times the beamlet's exact 8-row step
  *   factor (an FP32 complex multiply); with row triples (the default, for fields
@@ -195,6 +201,31 @@ gbd_status gbd_field(const gbd_beamlet* beamlets, int32_t n_beamlets, double wav
                      const gbd_detector* detector, int32_t precision, void* workspace,
                      size_t workspace_bytes, void* field_out, void* stream);
 
+/* ------------------------------------------------------------ gbd_field_rows ------
+ * The same field (Eq. sum_gaussian with the plane form of Eq. collins_factored, as
+ * gbd_field) on detector rows [row_begin, row_end) only: a slab of the detector, for
+ * spreading one field over several GPUs by pixels.  The beamlet table is the whole table
+ * (every slab sums every beamlet); the plane-evaluation method is pixel-parallel (Sec. 5),
+ * so slabs need no exchange but the final gather.
+ *   detector: the WHOLE detector (pixel (i, j) is s = ((i - nx/2) px, (j - ny/2) py) as in
+ *     gbd_field); 0 <= row_begin <= row_end <= ny.
+ *   field_out: (row_end - row_begin) x nx complex64 (MIXED) or complex128 (F64), row-major,
+ *     row 0 = detector row row_begin; device memory owned by the caller.
+ *   workspace: at least gbd_field_rows_workspace_bytes(...) bytes, 256-byte aligned (the
+ *     split partial fields cover only the slab, rounded down at its start to the launch's
+ *     row-block height of at most 48 rows).
+ * The launch (shape, splits) and the projection's kernel selection are those gbd_field
+ * takes on the whole detector, and every pixel of the slab is computed by the same thread
+ * row block, so the slab equals the same rows of gbd_field's output bit for bit, for any
+ * row range.  An empty range writes nothing.  Errors as gbd_field, plus GBD_EINVAL for a
+ * row range outside the detector. */
+size_t gbd_field_rows_workspace_bytes(int32_t n_beamlets, const gbd_detector* detector,
+                                      int32_t row_begin, int32_t row_end, int32_t precision);
+gbd_status gbd_field_rows(const gbd_beamlet* beamlets, int32_t n_beamlets, double wavelength,
+                          const gbd_detector* detector, int32_t row_begin, int32_t row_end,
+                          int32_t precision, void* workspace, size_t workspace_bytes,
+                          void* field_out, void* stream);
+
 /* Per-beamlet projection alone (the first half of gbd_field), for inspection: writes the
  * quadratic-form record of every beamlet to `coeffs` (device).
  *   MIXED: 16 floats per beamlet in the tiled layout gbd_field uses
@@ -205,7 +236,7 @@ gbd_status gbd_field(const gbd_beamlet* beamlets, int32_t n_beamlets, double wav
  *          (pixel units), excluding the common carrier exp(-ik z(s)); T = Tr + i Ti =
  *          exp(256 (auv ln 2 + i puv)), the row-pair scheme's column factor.
  *          wide_flag (device, may be NULL; zero it first) is OR-ed with bit 0 if some
- *          beamlet's phase can exceed 256 rad on the detector (gbd_field then reduces every
+ *          beamlet's phase can exceed 128 rad on the detector (gbd_field then reduces every
  *          per-pixel phase exactly before sin/cos), bit 1 if some beamlet's log2
  *          amplitude can change by more than 64 over 8 rows (the row-pair scheme then falls
  *          back to direct evaluation), bit 2 if it can change by more than 64 over 8
@@ -355,6 +386,18 @@ gbd_status gbd_sweep_plan_create(const gbd_system* system, double diameter, cons
                                  const double* overlap_factor, const double* waist_ratio,
                                  int32_t n_instances, const gbd_detector* detector,
                                  const gbd_shape* shape, gbd_sweep_plan** plan);
+/* The same sweep with every instance's beamlets traced by real rays through a sequence of
+ * conic mirrors (as gbd_trace_mirrors, App. B's telescope; Sec. 6 searches the parameters
+ * on such a traced system).  diameter: the pupil's; f_number: the system's focal ratio,
+ * which sets the Airy pattern of the score (x = pi r / (lambda f_number)); the detector is
+ * centred on the mirror sequence's image plane.  Everything else as gbd_sweep_plan_create;
+ * the plan is used with the same calls.  Errors: GBD_EINVAL for a bad mirror sequence (as
+ * gbd_trace_mirrors), f_number <= 0 or bad instances. */
+gbd_status gbd_sweep_plan_create_mirrors(const gbd_mirror_system* system, double diameter,
+                                         double f_number, const int32_t* n_across,
+                                         const double* overlap_factor, const double* waist_ratio,
+                                         int32_t n_instances, const gbd_detector* detector,
+                                         const gbd_shape* shape, gbd_sweep_plan** plan);
 size_t gbd_sweep_workspace_bytes(const gbd_sweep_plan* plan);
 gbd_status gbd_sweep_set_zones(gbd_sweep_plan* plan, int32_t n_zones, const double* lo,
                                const double* hi);

@@ -12,7 +12,7 @@
 //
 // Mixed path, per (beamlet, pixel): 4 FFMA for the quadratic form (row terms shared across
 // the thread's columns; phase coefficients in radians), ex2 / sin / cos on the MUFU pipe,
-// 2 FFMA to accumulate.  If the projection found a beamlet whose phase can exceed 256 rad
+// 2 FFMA to accumulate.  If the projection found a beamlet whose phase can exceed 128 rad
 // on the detector, the instantiation that reduces every phase exactly runs instead.  The sum runs in FP32 over each 64-beamlet tile and is folded into a
 // (hi, lo) pair with TwoSum between tiles.
 #include <math.h>
@@ -505,11 +505,14 @@ __global__ void __launch_bounds__(kThreads)
 // offset of the tilted plane), written as complex64/128.
 template <bool F64, typename P>
 __global__ void __launch_bounds__(256) field_reduce_kernel(const P* __restrict__ partial,
-                                                           int splits, int nx, int ny, double cx,
-                                                           double cy, void* __restrict__ out) {
-    const size_t npix = (size_t)nx * ny;
-    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= npix) return;
+                                                           int splits, int nx, int ny, int rows,
+                                                           int row0, int skip, int out_rows,
+                                                           double cx, double cy,
+                                                           void* __restrict__ out) {
+    const size_t npix = (size_t)nx * rows;
+    const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (size_t)nx * out_rows) return;
+    const size_t p = q + (size_t)skip * nx;
     // split order, eight loads in flight per thread (the loop is latency-bound otherwise)
     double re = 0.0, im = 0.0;
     int s = 0;
@@ -529,7 +532,7 @@ __global__ void __launch_bounds__(256) field_reduce_kernel(const P* __restrict__
         im += (double)v.y;
     }
     if (cx != 0.0 || cy != 0.0) {
-        const int i = (int)(p % nx), j = (int)(p / nx);
+        const int i = (int)(p % nx), j = (int)(p / nx) + row0;
         const double turns = cx * (i - nx / 2) + cy * (j - ny / 2);
         double sn, cs;
         sincospi(2.0 * (turns - rint(turns)), &sn, &cs);
@@ -538,9 +541,9 @@ __global__ void __launch_bounds__(256) field_reduce_kernel(const P* __restrict__
         re = r2;
     }
     if (F64)
-        static_cast<double2*>(out)[p] = make_double2(re, im);
+        static_cast<double2*>(out)[q] = make_double2(re, im);
     else
-        static_cast<float2*>(out)[p] = make_float2((float)re, (float)im);
+        static_cast<float2*>(out)[q] = make_float2((float)re, (float)im);
 }
 
 // The mixed path's reduction: GB300's FP64 pipe is too slow for an FP64 add per split and
@@ -549,11 +552,14 @@ __global__ void __launch_bounds__(256) field_reduce_kernel(const P* __restrict__
 // reduced in FP64 (one multiply-add and a rounding) and rotated in FP32.
 __global__ void __launch_bounds__(256) field_reduce_mixed_kernel(const float2* __restrict__ partial,
                                                                  int splits, int nx, int ny,
-                                                                 double cx, double cy,
+                                                                 int rows, int row0, int skip,
+                                                                 int out_rows, double cx,
+                                                                 double cy,
                                                                  float2* __restrict__ out) {
-    const size_t npix = (size_t)nx * ny;
-    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= npix) return;
+    const size_t npix = (size_t)nx * rows;
+    const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (size_t)nx * out_rows) return;
+    const size_t p = q + (size_t)skip * nx;
     float sr = 0.f, si = 0.f, cr = 0.f, ci = 0.f;
     auto add = [](float& sum, float& comp, float x) {
         const float t = __fadd_rn(sum, x);
@@ -579,7 +585,7 @@ __global__ void __launch_bounds__(256) field_reduce_mixed_kernel(const float2* _
     }
     float re = __fadd_rn(sr, cr), im = __fadd_rn(si, ci);
     if (cx != 0.0 || cy != 0.0) {
-        const int i = (int)(p % nx), j = (int)(p / nx);
+        const int i = (int)(p % nx), j = (int)(p / nx) + row0;
         const double turns = cx * (i - nx / 2) + cy * (j - ny / 2);
         float sn, cs;
         sincospif(2.0f * (float)(turns - rint(turns)), &sn, &cs);
@@ -587,7 +593,7 @@ __global__ void __launch_bounds__(256) field_reduce_mixed_kernel(const float2* _
         im = re * sn + im * cs;
         re = r2;
     }
-    out[p] = make_float2(re, im);
+    out[q] = make_float2(re, im);
 }
 
 template <int RB, int CB>
@@ -819,21 +825,39 @@ cudaError_t gbd_launch_field_kernel(int precision, const void* coeffs, int n_til
                                     cudaStream_t s) {
     const ShapeEntry* e = find_shape(precision, L.rows_per_thread, L.cols_per_thread, L.scheme);
     if (!e) return cudaErrorInvalidValue;
-    return e->fn(coeffs, n_tiles, p, L, partial, wide, wait_spins, s);
+    // the kernels see the slab as a detector of p.rows rows (the records' centre rows are
+    // relative to its first row); the partial fields are p.rows x nx
+    gbd_project_params slab = p;
+    slab.ny = p.rows;
+    return e->fn(coeffs, n_tiles, slab, L, partial, wide, wait_spins, s);
+}
+
+int gbd_field_row_block(int precision, const gbd_field_launch& L) {
+    const int rb = L.rows_per_thread, cb = L.cols_per_thread;
+    if (precision == GBD_PREC_F64) return cb >= 8 ? rb : 8 * rb;
+    if (L.scheme == GBD_SCHEME_DIRECT) return 8 * rb;
+    if (rb == 2) return 16;
+    // row triples / quadruples with the 16-row pair set behind them
+    return rb == 3 ? 48 : 32;
 }
 
 cudaError_t gbd_launch_field_reduce(int precision, const gbd_project_params& p, int splits,
-                                    const void* partial, void* out, cudaStream_t s) {
-    const size_t npix = (size_t)p.nx * p.ny;
+                                    const void* partial, void* out, int out_row0, int out_rows,
+                                    cudaStream_t s) {
+    // partial fields: rows p.row0 .. p.row0 + p.rows - 1; output: rows out_row0 .. + out_rows
+    const int skip = out_row0 - p.row0;
+    const size_t nout = (size_t)p.nx * out_rows;
+    if (nout == 0) return cudaSuccess;
     const double cx = -p.n[0] * p.px / p.wavelength, cy = -p.n[1] * p.py / p.wavelength;
-    const unsigned blocks = (unsigned)((npix + 255) / 256);
+    const unsigned blocks = (unsigned)((nout + 255) / 256);
     if (precision == GBD_PREC_F64)
         field_reduce_kernel<true, double2><<<blocks, 256, 0, s>>>(
-            static_cast<const double2*>(partial), splits, p.nx, p.ny, cx, cy, out);
+            static_cast<const double2*>(partial), splits, p.nx, p.ny, p.rows, p.row0, skip,
+            out_rows, cx, cy, out);
     else
         field_reduce_mixed_kernel<<<blocks, 256, 0, s>>>(static_cast<const float2*>(partial), splits,
-                                                         p.nx, p.ny, cx, cy,
-                                                         static_cast<float2*>(out));
+                                                         p.nx, p.ny, p.rows, p.row0, skip, out_rows,
+                                                         cx, cy, static_cast<float2*>(out));
     return cudaGetLastError();
 }
 

@@ -108,10 +108,14 @@ struct TileStream {
 };
 
 // Phase magnitude (radians) above which a beamlet's phase is range-reduced per pixel.
-// Below it the MUFU sin/cos take the radians directly: their absolute error grows about
-// linearly with |x| (3e-7 at pi, 1e-5 at 100 rad on GB300), so at <= 256 rad it stays
-// well inside the mixed path's tolerance without the four reduction instructions.
-constexpr float kWidePhase = 256.0f;
+// Below it the MUFU sin/cos take the radians directly, saving four instructions.  A phase
+// held in FP32 is off by about |x| 2^-24 however it is reduced; unreduced, the MUFU adds
+// an error that also grows with |x| (3e-7 at pi, 1e-5 at 100 rad on GB300).  Measured with
+// 3,228 beamlets 41 lambda F# wide on detectors whose phase bound runs from 100 to 250 rad,
+// the field's relative L2 error against the oracle grows from 2.1e-6 to 4.1e-6 unreduced
+// and stays 1.4-2.3e-6 reduced; at this bound it is 2.2e-6 (the benchmark workloads stay
+// under 101 rad, so none of them pays for the reduction).
+constexpr float kWidePhase = 128.0f;
 
 // One 64-beamlet tile of mixed-precision evaluation on a thread's RB x CB pixels.
 // Record fields: (i0, j0, a0, p0) (a1u, p1u, a1v, p1v) (auu, puu, auv, puv) (avv, pvv, T)

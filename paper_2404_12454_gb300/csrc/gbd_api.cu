@@ -206,6 +206,8 @@ gbd_project_params project_params(double wavelength, const gbd_detector* D) {
     p.inv_wavelength = 1.0 / wavelength;
     p.inv_px = 1.0 / D->pitch_x;
     p.inv_py = 1.0 / D->pitch_y;
+    p.row0 = 0;
+    p.rows = D->ny;
     return p;
 }
 
@@ -322,27 +324,45 @@ gbd_field_launch resolve_launch(int precision, const gbd_shape& sh, int n_tiles,
 // Workspace: [flag word | projected records | split partial fields], 256-byte aligned parts.
 constexpr size_t kFlagBytes = 256;
 
-size_t workspace_for(int precision, int n, const gbd_detector* D, const gbd_field_launch& L) {
+// First row of the slab the kernels evaluate for output rows [row_begin, row_end): row_begin
+// rounded down to the launch's row-block height, so that every pixel is computed by the
+// same thread row block (and the same recurrence chain) as on the whole detector.
+int slab_row0(int precision, const gbd_field_launch& L, int row_begin) {
+    const int h = gbd_field_row_block(precision, L);
+    return row_begin - row_begin % h;
+}
+
+size_t workspace_for(int precision, int n, const gbd_detector* D, const gbd_field_launch& L,
+                     int row_begin = 0, int row_end = -1) {
     if (n <= 0) return 0;
+    if (row_end < 0) row_end = D->ny;
+    const int rows = row_end - slab_row0(precision, L, row_begin);
     const size_t coeff = align256((size_t)n_tiles_of(n) * tile_bytes(precision));
     const size_t elem = precision == GBD_PREC_MIXED ? sizeof(float2) : sizeof(double2);
-    const size_t part = align256((size_t)L.splits * D->nx * D->ny * elem);
+    const size_t part = align256((size_t)L.splits * D->nx * rows * elem);
     return kFlagBytes + coeff + part;
 }
 
+// The field on detector rows [row_begin, row_end) (the whole detector: 0, ny).  The launch
+// (shape, splits) and the projection's flags are those of the whole detector, so a row
+// range gives the same bits as the same rows of the whole field.
 gbd_status run_field(const gbd_beamlet* beamlets, int32_t n, double wavelength,
                      const gbd_detector* D, int32_t precision, void* ws, size_t ws_bytes, void* out,
-                     cudaStream_t stream, const gbd_shape& sh) {
-    const gbd_project_params pp = project_params(wavelength, D);
-    const size_t npix = (size_t)D->nx * D->ny;
-    if (n == 0) {
+                     cudaStream_t stream, const gbd_shape& sh, int row_begin = 0,
+                     int row_end = -1) {
+    if (row_end < 0) row_end = D->ny;
+    gbd_project_params pp = project_params(wavelength, D);
+    const size_t npix = (size_t)D->nx * (row_end - row_begin);
+    if (n == 0 || npix == 0) {
         const size_t elem = precision == GBD_PREC_F64 ? 16 : 8;
-        cudaError_t e = cudaMemsetAsync(out, 0, npix * elem, stream);
+        cudaError_t e = npix ? cudaMemsetAsync(out, 0, npix * elem, stream) : cudaSuccess;
         return e == cudaSuccess ? GBD_OK : cuda_fail(e, "gbd_field memset");
     }
     const int nt = n_tiles_of(n);
     const gbd_field_launch L = resolve_launch(precision, sh, nt, D);
-    const size_t need = workspace_for(precision, n, D, L);
+    pp.row0 = slab_row0(precision, L, row_begin);
+    pp.rows = row_end - pp.row0;
+    const size_t need = workspace_for(precision, n, D, L, row_begin, row_end);
     if (ws_bytes < need)
         return fail(GBD_ENOMEM, "workspace of %zu bytes is smaller than the %zu needed", ws_bytes,
                     need);
@@ -365,7 +385,8 @@ gbd_status run_field(const gbd_beamlet* beamlets, int32_t n, double wavelength,
     if (e != cudaSuccess) return cuda_fail(e, "gbd_field launch");
     {
         TimingScope ts(kTimeReduce, stream);
-        e = gbd_launch_field_reduce(precision, pp, L.splits, partial, out, stream);
+        e = gbd_launch_field_reduce(precision, pp, L.splits, partial, out, row_begin,
+                                    row_end - row_begin, stream);
     }
     if (e != cudaSuccess) return cuda_fail(e, "gbd_field reduce launch");
     return GBD_OK;
@@ -448,6 +469,41 @@ gbd_status gbd_field_fixed_scratch(const gbd_beamlet* beamlets, int32_t n, doubl
                      stream, sh);
 }
 
+// Kernel parameters of a mirror sequence (lab-frame vertices and curvatures, the pupil
+// plane and the axial path); the pupil sampling is set by the caller.
+gbd_status gbd_make_mirror_params(const gbd_mirror_system* system, double diameter,
+                                  gbd_mirror_params* out) {
+    if (!system) return fail(GBD_EINVAL, "system is NULL");
+    if (!finite_pos(system->wavelength)) return fail(GBD_EINVAL, "wavelength must be finite and > 0");
+    if (!finite_pos(system->pupil_offset)) return fail(GBD_EINVAL, "pupil_offset must be > 0");
+    const int n = system->n_mirrors;
+    if (n < 1 || n > GBD_MAX_MIRRORS)
+        return fail(GBD_EINVAL, "n_mirrors must be in [1, %d]", GBD_MAX_MIRRORS);
+    for (int k = 0; k < n; ++k)
+        if (!isfinite(system->radius[k]) || system->radius[k] == 0.0 ||
+            !isfinite(system->spacing[k]) || system->spacing[k] == 0.0 ||
+            !isfinite(system->conic[k]))
+            return fail(GBD_EINVAL, "mirror %d: radius and spacing must be finite and non-zero", k);
+    gbd_mirror_params& m = *out;
+    memset(&m, 0, sizeof(m));
+    m.n = n;
+    double z = 0.0, dir = 1.0, axial = system->pupil_offset;
+    for (int k = 0; k < n; ++k) {
+        m.z[k] = z;
+        m.c[k] = dir / system->radius[k];
+        m.K[k] = system->conic[k];
+        z += system->spacing[k];
+        axial += fabs(system->spacing[k]);
+        dir = -dir;
+    }
+    m.z_img = z;
+    m.z_ep = -system->pupil_offset;
+    m.axial_path = axial;
+    m.wavelength = system->wavelength;
+    m.diameter = diameter;
+    return GBD_OK;
+}
+
 extern "C" {
 
 const char* gbd_last_error(void) { return g_err; }
@@ -517,40 +573,15 @@ gbd_status gbd_trace_mirrors(const gbd_mirror_system* system, const gbd_pupil* p
     if (!system) return fail(GBD_EINVAL, "system is NULL");
     gbd_status st = check_pupil(pupil);
     if (st != GBD_OK) return st;
-    if (!finite_pos(system->wavelength)) return fail(GBD_EINVAL, "wavelength must be finite and > 0");
-    if (!finite_pos(system->pupil_offset)) return fail(GBD_EINVAL, "pupil_offset must be > 0");
-    const int n = system->n_mirrors;
-    if (n < 1 || n > GBD_MAX_MIRRORS)
-        return fail(GBD_EINVAL, "n_mirrors must be in [1, %d]", GBD_MAX_MIRRORS);
-    for (int k = 0; k < n; ++k)
-        if (!isfinite(system->radius[k]) || system->radius[k] == 0.0 ||
-            !isfinite(system->spacing[k]) || system->spacing[k] == 0.0 ||
-            !isfinite(system->conic[k]))
-            return fail(GBD_EINVAL, "mirror %d: radius and spacing must be finite and non-zero", k);
+    gbd_mirror_params m;
+    if ((st = gbd_make_mirror_params(system, pupil->diameter, &m)) != GBD_OK) return st;
     if (!finite_pos(overlap_factor)) return fail(GBD_EINVAL, "overlap_factor must be > 0");
     if (!finite_pos(waist_ratio)) return fail(GBD_EINVAL, "waist_ratio must be > 0");
     const int32_t nb = gbd_beamlet_count(pupil);
     if (capacity < nb) return fail(GBD_ENOMEM, "capacity %d < %d beamlets", capacity, nb);
     if (nb > 0 && !out) return fail(GBD_EINVAL, "out is NULL");
     if (reinterpret_cast<uintptr_t>(out) & 15u) return fail(GBD_EINVAL, "out must be 16-byte aligned");
-    gbd_mirror_params m;
-    memset(&m, 0, sizeof(m));
-    m.n = n;
     m.n_across = pupil->n_across;
-    double z = 0.0, dir = 1.0, axial = system->pupil_offset;
-    for (int k = 0; k < n; ++k) {
-        m.z[k] = z;
-        m.c[k] = dir / system->radius[k];
-        m.K[k] = system->conic[k];
-        z += system->spacing[k];
-        axial += fabs(system->spacing[k]);
-        dir = -dir;
-    }
-    m.z_img = z;
-    m.z_ep = -system->pupil_offset;
-    m.axial_path = axial;
-    m.wavelength = system->wavelength;
-    m.diameter = pupil->diameter;
     m.overlap_factor = overlap_factor;
     m.waist_ratio = waist_ratio;
     m.grid = gbd_make_grid(pupil->diameter, system->wavelength, pupil->n_across, overlap_factor,
@@ -602,6 +633,35 @@ gbd_status gbd_field(const gbd_beamlet* beamlets, int32_t n_beamlets, double wav
     return run_field(beamlets, n_beamlets, wavelength, detector, precision, workspace,
                      workspace_bytes, field_out, static_cast<cudaStream_t>(stream),
                      stored_shape(precision, detector));
+}
+
+size_t gbd_field_rows_workspace_bytes(int32_t n_beamlets, const gbd_detector* detector,
+                                      int32_t row_begin, int32_t row_end, int32_t precision) {
+    if (check_detector(detector) != GBD_OK || n_beamlets <= 0) return 0;
+    if (precision != GBD_PREC_F64 && precision != GBD_PREC_MIXED) return 0;
+    if (row_begin < 0 || row_end > detector->ny || row_begin >= row_end) return 0;
+    const gbd_field_launch L =
+        resolve_launch(precision, stored_shape(precision, detector), n_tiles_of(n_beamlets),
+                       detector);
+    return workspace_for(precision, n_beamlets, detector, L, row_begin, row_end);
+}
+
+gbd_status gbd_field_rows(const gbd_beamlet* beamlets, int32_t n_beamlets, double wavelength,
+                          const gbd_detector* detector, int32_t row_begin, int32_t row_end,
+                          int32_t precision, void* workspace, size_t workspace_bytes,
+                          void* field_out, void* stream) {
+    GBD_NVTX_RANGE("gbd_field_rows");
+    // an empty range writes nothing, so its output pointer may be NULL
+    gbd_status st = check_field_args(beamlets, n_beamlets, wavelength, detector, precision,
+                                     workspace,
+                                     row_begin == row_end && !field_out ? (void*)16 : field_out);
+    if (st != GBD_OK) return st;
+    if (row_begin < 0 || row_end > detector->ny || row_begin > row_end)
+        return fail(GBD_EINVAL, "row range [%d, %d) is not inside [0, %d)", row_begin, row_end,
+                    detector->ny);
+    return run_field(beamlets, n_beamlets, wavelength, detector, precision, workspace,
+                     workspace_bytes, field_out, static_cast<cudaStream_t>(stream),
+                     stored_shape(precision, detector), row_begin, row_end);
 }
 
 gbd_status gbd_field_set_shape(int32_t precision, const gbd_shape* shape) {
@@ -835,7 +895,7 @@ gbd_status gbd_field_point(const gbd_beamlet* beamlets, int32_t n_beamlets, doub
         e = gbd_launch_point(beamlets, n_beamlets, pp, base, sp, tps, partial, wait_spins(), s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "gbd_field_point launch");
-    e = gbd_launch_field_reduce(GBD_PREC_F64, pp, sp, partial, field_out, s);
+    e = gbd_launch_field_reduce(GBD_PREC_F64, pp, sp, partial, field_out, 0, detector->ny, s);
     return e == cudaSuccess ? GBD_OK : cuda_fail(e, "gbd_field_point reduce");
 }
 

@@ -218,6 +218,11 @@ struct gbd_project_params {
     double px, py;
     int32_t nx, ny;
     double inv_wavelength, inv_px, inv_py;  // reciprocals (FP64 division is slow here)
+    // Row slab evaluated by the field kernels: detector rows row0 .. row0 + rows - 1.  The
+    // projection stores each beamlet's centre row relative to row0 (j0 - row0), so the
+    // kernels index the slab's rows from 0 with the same integer offsets tv as on the whole
+    // detector; everything else (flags, bounds) refers to the whole nx x ny detector.
+    int32_t row0, rows;
 };
 
 struct gbd_field_launch {
@@ -250,9 +255,11 @@ cudaError_t gbd_launch_trace(const gbd_trace_params& p, int n_instances, int max
 // Batched trace + mixed projection straight into the tiled records (sweep set-up).
 // One thread per record; d_rows[d_rbase[k] + j] = first beamlet index of row j of
 // instance k (inside the instance).
-cudaError_t gbd_launch_trace_project(const gbd_trace_params& p, int n_instances,
-                                     const gbd_instance_dev* d_inst, const int* d_rbase,
-                                     const int* d_rows, long long n_records,
+// Batched trace + projection of a sweep's instances: through the thin-lens system `p`,
+// or, when `m` is not null, through its mirror sequence (real rays).
+cudaError_t gbd_launch_trace_project(const gbd_trace_params& p, const gbd_mirror_params* m,
+                                     int n_instances, const gbd_instance_dev* d_inst,
+                                     const int* d_rbase, const int* d_rows, long long n_records,
                                      const gbd_project_params& g, float4* out, unsigned* wide,
                                      cudaStream_t s);
 // `wide` (mixed only, may be null): set to 1 when some beamlet's phase may exceed the
@@ -264,15 +271,24 @@ cudaError_t gbd_launch_field_kernel(int precision, const void* coeffs, int n_til
                                     const gbd_project_params& p, const gbd_field_launch& L,
                                     void* partial, const unsigned* wide, uint32_t wait_spins,
                                     cudaStream_t s);
-// partial: float2 per pixel and split for GBD_PREC_MIXED, double2 for GBD_PREC_F64
+// partial: float2 per pixel and split for GBD_PREC_MIXED, double2 for GBD_PREC_F64, over
+// the slab p.row0 .. p.row0 + p.rows - 1; writes detector rows out_row0 .. + out_rows - 1
+// (inside the slab) to `out`, row-major from out_row0
 cudaError_t gbd_launch_field_reduce(int precision, const gbd_project_params& p, int splits,
-                                    const void* partial, void* out, cudaStream_t s);
+                                    const void* partial, void* out, int out_row0, int out_rows,
+                                    cudaStream_t s);
+// Height of the pixel-row blocks of every kernel a launch runs: a slab that starts on a
+// multiple of it is split into the same thread row blocks as the whole detector.
+int gbd_field_row_block(int precision, const gbd_field_launch& L);
 int gbd_field_occupancy(int precision, int rb, int cb, int scheme);
 // Columns per thread (8, 4 or 2, at least min_cols) of the row-pair shape that covers a
 // detector nx pixels wide at the least estimated cost.
 int gbd_auto_cols(int nx, int min_cols);
 gbd_status gbd_set_error(gbd_status st, const char* msg);  // sets gbd_last_error()
 gbd_status gbd_check_system(const gbd_system* s);
+// Mirror-sequence kernel parameters (validated; GBD_EINVAL with gbd_last_error set)
+gbd_status gbd_make_mirror_params(const gbd_mirror_system* system, double diameter,
+                                  gbd_mirror_params* out);
 gbd_status gbd_check_detector(const gbd_detector* d);
 gbd_project_params gbd_make_project_params(double wavelength, const gbd_detector* d);
 gbd_trace_params gbd_make_trace_params(const gbd_system* system, double diameter);

@@ -14,6 +14,7 @@
 //     score = sqrt((S2/e0^2 - 2 S1/e0 + S0) / n).
 #include <cuda_bf16.h>
 #include <math.h>
+#include <string.h>
 
 #include <algorithm>
 #include <vector>
@@ -539,6 +540,8 @@ size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
 struct gbd_sweep_plan {
     gbd_trace_params tp;
+    bool mirrors = false;   // trace through `mp` (real rays) instead of the thin lens `tp`
+    gbd_mirror_params mp{};
     gbd_project_params pp{};
     double lam_fnum, r3;
     Regions regions;
@@ -582,7 +585,7 @@ static gbd_status sweep_enqueue(gbd_sweep_plan* P, double* scores, cudaStream_t 
     float4* coef = reinterpret_cast<float4*>(w + P->off_coef);
     cudaError_t e = cudaMemsetAsync(w + P->off_counter, 0, 256, s);
     if (e == cudaSuccess)
-        e = gbd_launch_trace_project(P->tp, P->n_inst,
+        e = gbd_launch_trace_project(P->tp, P->mirrors ? &P->mp : nullptr, P->n_inst,
                                      reinterpret_cast<const gbd_instance_dev*>(w + P->off_inst),
                                      reinterpret_cast<const int*>(w + P->off_rbase),
                                      reinterpret_cast<const int*>(w + P->off_rows),
@@ -628,26 +631,22 @@ static void sweep_layout(gbd_sweep_plan* P, int nx, int ny) {
     P->bytes = off;
 }
 
-extern "C" {
-
-gbd_status gbd_sweep_plan_create(const gbd_system* system, double diameter, const int32_t* n_across,
-                                 const double* overlap_factor, const double* waist_ratio,
-                                 int32_t n_instances, const gbd_detector* detector,
-                                 const gbd_shape* shape, gbd_sweep_plan** plan) {
-    GBD_NVTX_RANGE("gbd_sweep_plan_create");
-    if (!plan) return gbd_set_error(GBD_EINVAL, "plan is NULL");
-    *plan = nullptr;
-    gbd_status st = gbd_check_system(system);
+// Plan of a sweep through the thin-lens system `tp` or, when `mp` is not null, through
+// the mirror sequence `mp`; lam_fnum = lambda F# sets the Airy pattern's scale.
+static gbd_status sweep_create(const gbd_trace_params& tp, const gbd_mirror_params* mp,
+                               double wavelength, double diameter, double lam_fnum,
+                               const int32_t* n_across, const double* overlap_factor,
+                               const double* waist_ratio, int32_t n_instances,
+                               const gbd_detector* detector, const gbd_shape* shape,
+                               gbd_sweep_plan** plan) {
+    gbd_status st = gbd_check_detector(detector);
     if (st != GBD_OK) return st;
-    if ((st = gbd_check_detector(detector)) != GBD_OK) return st;
     if (!(isfinite(diameter) && diameter > 0.0))
         return gbd_set_error(GBD_EINVAL, "diameter must be finite and > 0");
     if (n_instances < 1 || n_instances > (1 << 20))
         return gbd_set_error(GBD_EINVAL, "n_instances must be in [1, 2^20]");
     if (!n_across || !overlap_factor || !waist_ratio)
         return gbd_set_error(GBD_EINVAL, "instance arrays are NULL");
-    if (isinf(system->focal_length))
-        return gbd_set_error(GBD_EINVAL, "the Airy score needs a lens (finite focal length)");
     // default: row triples on 8 columns (or row pairs on 4, whichever fits the width)
     const int cb = shape ? shape->cols_per_thread : gbd_auto_cols(detector->nx, 4);
     const int rb = shape ? shape->rows_per_thread : (cb == 8 ? 3 : 2);
@@ -655,9 +654,13 @@ gbd_status gbd_sweep_plan_create(const gbd_system* system, double diameter, cons
     if (!find_sweep_shape(rb, cb, scheme))
         return gbd_set_error(GBD_EINVAL, "unsupported sweep shape");
     gbd_sweep_plan* P = new gbd_sweep_plan();
-    P->tp = gbd_make_trace_params(system, diameter);
-    P->pp = gbd_make_project_params(system->wavelength, detector);
-    P->lam_fnum = system->wavelength * fabs(system->focal_length) / diameter;
+    P->tp = tp;
+    if (mp) {
+        P->mirrors = true;
+        P->mp = *mp;
+    }
+    P->pp = gbd_make_project_params(wavelength, detector);
+    P->lam_fnum = lam_fnum;
     P->r3 = 10.173468135062722 * P->lam_fnum / M_PI;  // third zero of J1
     P->regions.n = 1;
     P->regions.lo[0] = 0.0;
@@ -704,7 +707,7 @@ gbd_status gbd_sweep_plan_create(const gbd_system* system, double diameter, cons
         I.offset = tile * gbd::kTile;
         I.overlap_factor = overlap_factor[k];
         I.waist_ratio = waist_ratio[k];
-        I.grid = gbd_make_grid(diameter, system->wavelength, n_across[k], overlap_factor[k],
+        I.grid = gbd_make_grid(diameter, wavelength, n_across[k], overlap_factor[k],
                                waist_ratio[k]);
         P->inst.push_back(I);
         P->inst_tiles.push_back(make_int2((int)tile, nt));
@@ -729,6 +732,50 @@ gbd_status gbd_sweep_plan_create(const gbd_system* system, double diameter, cons
     sweep_layout(P, detector->nx, detector->ny);
     *plan = P;
     return GBD_OK;
+}
+
+extern "C" {
+
+gbd_status gbd_sweep_plan_create(const gbd_system* system, double diameter, const int32_t* n_across,
+                                 const double* overlap_factor, const double* waist_ratio,
+                                 int32_t n_instances, const gbd_detector* detector,
+                                 const gbd_shape* shape, gbd_sweep_plan** plan) {
+    GBD_NVTX_RANGE("gbd_sweep_plan_create");
+    if (!plan) return gbd_set_error(GBD_EINVAL, "plan is NULL");
+    *plan = nullptr;
+    gbd_status st = gbd_check_system(system);
+    if (st != GBD_OK) return st;
+    if (isinf(system->focal_length))
+        return gbd_set_error(GBD_EINVAL, "the Airy score needs a lens (finite focal length)");
+    if (!(isfinite(diameter) && diameter > 0.0))
+        return gbd_set_error(GBD_EINVAL, "diameter must be finite and > 0");
+    return sweep_create(gbd_make_trace_params(system, diameter), nullptr, system->wavelength,
+                        diameter, system->wavelength * fabs(system->focal_length) / diameter,
+                        n_across, overlap_factor, waist_ratio, n_instances, detector, shape, plan);
+}
+
+gbd_status gbd_sweep_plan_create_mirrors(const gbd_mirror_system* system, double diameter,
+                                         double f_number, const int32_t* n_across,
+                                         const double* overlap_factor, const double* waist_ratio,
+                                         int32_t n_instances, const gbd_detector* detector,
+                                         const gbd_shape* shape, gbd_sweep_plan** plan) {
+    GBD_NVTX_RANGE("gbd_sweep_plan_create_mirrors");
+    if (!plan) return gbd_set_error(GBD_EINVAL, "plan is NULL");
+    *plan = nullptr;
+    if (!(isfinite(diameter) && diameter > 0.0))
+        return gbd_set_error(GBD_EINVAL, "diameter must be finite and > 0");
+    if (!(isfinite(f_number) && f_number > 0.0))
+        return gbd_set_error(GBD_EINVAL, "f_number must be finite and > 0");
+    gbd_mirror_params mp;
+    gbd_status st = gbd_make_mirror_params(system, diameter, &mp);
+    if (st != GBD_OK) return st;
+    gbd_trace_params tp;
+    memset(&tp, 0, sizeof(tp));
+    tp.wavelength = system->wavelength;
+    tp.diameter = diameter;
+    tp.zdeg = -1;
+    return sweep_create(tp, &mp, system->wavelength, diameter, system->wavelength * f_number,
+                        n_across, overlap_factor, waist_ratio, n_instances, detector, shape, plan);
 }
 
 size_t gbd_sweep_workspace_bytes(const gbd_sweep_plan* plan) { return plan ? plan->bytes : 0; }

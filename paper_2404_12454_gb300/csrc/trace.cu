@@ -406,7 +406,7 @@ __device__ __forceinline__ unsigned write_mixed(float4* __restrict__ out, long l
         const double tt = 256.0 * q.p[4];
         float sn, cs;
         sincospif((float)(2.0 * (tt - rint(tt))), &sn, &cs);
-        f0 = make_float4((float)q.i0, (float)q.j0, (float)q.a[0], (float)p[0]);
+        f0 = make_float4((float)q.i0, (float)(q.j0 - G.row0), (float)q.a[0], (float)p[0]);
         f1 = make_float4((float)q.a[1], (float)p[1], (float)q.a[2], (float)p[2]);
         f2 = make_float4((float)q.a[3], (float)p[3], (float)q.a[4], (float)p[4]);
         f3 = make_float4((float)q.a[5], (float)p[5], tm * cs, tm * sn);
@@ -457,7 +457,7 @@ __global__ void __launch_bounds__(128) project_f64_kernel(const gbd_beamlet* __r
         for (int m = 0; m < gbd::kF64Fields; ++m) f[m] = make_double2(0.0, 0.0);
         f[1].x = 2.0 * gbd::kPadLog2Amp;
     } else {
-        f[0] = make_double2(q.i0, q.j0);
+        f[0] = make_double2(q.i0, q.j0 - G.row0);
         for (int m = 0; m < 6; ++m) f[1 + m] = make_double2(q.a[m], q.p[m]);
         // S = E(u+2)E(u)/E(u+1)^2 = exp of twice the uu coefficient, for row recurrences
         const double sa = exp2(2.0 * q.a[3]);
@@ -474,9 +474,13 @@ __global__ void __launch_bounds__(128) project_f64_kernel(const gbd_beamlet* __r
 // Batched trace + projection for a parameter sweep, one thread per record.  Records of
 // instance k start at inst[k].offset (a tile boundary); rows[rbase[k] + j] is the index,
 // inside the instance, of the first beamlet of grid row j.  Records between an instance's
-// last beamlet and the next tile boundary are written as padding.
+// last beamlet and the next tile boundary are written as padding.  MIRRORS: the rays go
+// through the mirror sequence M instead of the thin-lens system P (each instance keeps its
+// own pupil sampling, I.grid).
+template <bool MIRRORS>
 __global__ void __launch_bounds__(256)
-    trace_project_kernel(gbd_trace_params P, const gbd_instance_dev* __restrict__ inst, int n_inst,
+    trace_project_kernel(gbd_trace_params P, gbd_mirror_params M,
+                         const gbd_instance_dev* __restrict__ inst, int n_inst,
                          const int* __restrict__ rbase, const int* __restrict__ rows,
                          long long n_records, gbd_project_params G, float4* __restrict__ out,
                          unsigned* __restrict__ wide) {
@@ -503,7 +507,10 @@ __global__ void __launch_bounds__(256)
         }
         const int i = ((N - 1) - row_extent(a, N)) / 2 + (int)(u - R[a]);
         gbd_beamlet bm;
-        trace_one(LensTracer{P}, I.grid, N, i, a, &bm);
+        if (MIRRORS)
+            trace_one(MirrorTracer{M}, I.grid, N, i, a, &bm);
+        else
+            trace_one(LensTracer{P}, I.grid, N, i, a, &bm);
         q = project_one(bm, G);
         if (!q.pad) add_amplitude_f32(q, bm);
     }
@@ -513,15 +520,20 @@ __global__ void __launch_bounds__(256)
 
 }  // namespace
 
-cudaError_t gbd_launch_trace_project(const gbd_trace_params& p, int n_instances,
-                                     const gbd_instance_dev* d_inst, const int* d_rbase,
-                                     const int* d_rows, long long n_records,
+cudaError_t gbd_launch_trace_project(const gbd_trace_params& p, const gbd_mirror_params* m,
+                                     int n_instances, const gbd_instance_dev* d_inst,
+                                     const int* d_rbase, const int* d_rows, long long n_records,
                                      const gbd_project_params& g, float4* out, unsigned* wide,
                                      cudaStream_t s) {
     if (n_records <= 0) return cudaSuccess;
     const unsigned blocks = (unsigned)((n_records + 255) / 256);
-    trace_project_kernel<<<blocks, 256, 0, s>>>(p, d_inst, n_instances, d_rbase, d_rows, n_records, g,
-                                                out, wide);
+    if (m)
+        trace_project_kernel<true><<<blocks, 256, 0, s>>>(p, *m, d_inst, n_instances, d_rbase, d_rows,
+                                                          n_records, g, out, wide);
+    else
+        trace_project_kernel<false><<<blocks, 256, 0, s>>>(p, gbd_mirror_params{}, d_inst,
+                                                           n_instances, d_rbase, d_rows, n_records,
+                                                           g, out, wide);
     return cudaGetLastError();
 }
 

@@ -82,6 +82,14 @@ _SIGS = {
                                                     ctypes.c_int32]),
     "gbd_field": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_double, ctypes.POINTER(gbd_detector),
                                  ctypes.c_int32, _P, ctypes.c_size_t, _P, _P]),
+    "gbd_field_rows_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int32,
+                                                         ctypes.POINTER(gbd_detector),
+                                                         ctypes.c_int32, ctypes.c_int32,
+                                                         ctypes.c_int32]),
+    "gbd_field_rows": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_double,
+                                      ctypes.POINTER(gbd_detector), ctypes.c_int32,
+                                      ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_size_t, _P,
+                                      _P]),
     "gbd_project_bytes": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_int32]),
     "gbd_project": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_double,
                                    ctypes.POINTER(gbd_detector), ctypes.c_int32, _P, _P, _P]),
@@ -282,6 +290,23 @@ def gbd_field(beamlets, n_beamlets: int, wavelength: float, detector, precision:
                            _stream(stream)))
 
 
+def gbd_field_rows_workspace_bytes(n_beamlets: int, detector, row_begin: int, row_end: int,
+                                   precision: int) -> int:
+    return int(lib().gbd_field_rows_workspace_bytes(int(n_beamlets),
+                                                    ctypes.byref(make_detector(detector)),
+                                                    int(row_begin), int(row_end),
+                                                    int(precision)))
+
+
+def gbd_field_rows(beamlets, n_beamlets: int, wavelength: float, detector, row_begin: int,
+                   row_end: int, precision: int, workspace, field_out, stream=None) -> None:
+    ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check(lib().gbd_field_rows(_ptr(beamlets), int(n_beamlets), float(wavelength),
+                                ctypes.byref(make_detector(detector)), int(row_begin),
+                                int(row_end), int(precision), _ptr(workspace),
+                                ctypes.c_size_t(ws_bytes), _ptr(field_out), _stream(stream)))
+
+
 def gbd_project_bytes(n_beamlets: int, precision: int) -> int:
     return int(lib().gbd_project_bytes(int(n_beamlets), int(precision)))
 
@@ -289,7 +314,7 @@ def gbd_project_bytes(n_beamlets: int, precision: int) -> int:
 def gbd_project(beamlets, n_beamlets: int, wavelength: float, detector, precision: int, coeffs,
                 wide_flag=None, stream=None) -> None:
     """Projected records into ``coeffs``; ``wide_flag`` (int32 CUDA tensor, zeroed) gets
-    the projection's flag bits (mixed only): 0 some beamlet's phase can exceed 256 rad on
+    the projection's flag bits (mixed only): 0 some beamlet's phase can exceed 128 rad on
     the detector, 1 the row-pair scheme must fall back to direct evaluation, 2 the
     amplitude may not be carried along a row, 3 the field has a uv term, 4 the row triples
     and quadruples must hand the field to the row pairs."""
@@ -562,6 +587,23 @@ def field(beamlets, wavelength: float, detector, precision: int = GBD_PREC_MIXED
     if ws is None:
         ws = workspace(n, detector, precision, beamlets.device)
     gbd_field(beamlets, n, wavelength, detector, precision, ws, out, stream)
+    return out
+
+
+def field_rows(beamlets, wavelength: float, detector, row_begin: int, row_end: int,
+               precision: int = GBD_PREC_MIXED, ws=None, out=None, stream=None):
+    """Detector rows [row_begin, row_end) of the field, [row_end - row_begin, nx], as a
+    CUDA tensor: the same bits as those rows of ``field``."""
+    import torch
+    n = int(beamlets.shape[0])
+    dtype = torch.complex64 if precision == GBD_PREC_MIXED else torch.complex128
+    if out is None:
+        out = torch.empty((row_end - row_begin, detector.nx), dtype=dtype, device=beamlets.device)
+    if ws is None:
+        nbytes = gbd_field_rows_workspace_bytes(n, detector, row_begin, row_end, precision)
+        ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=beamlets.device)
+    gbd_field_rows(beamlets, n, wavelength, detector, row_begin, row_end, precision, ws, out,
+                   stream)
     return out
 
 
