@@ -393,6 +393,8 @@ gbd_status gbd_sweep_plan_create(const gbd_system* system, double diameter, cons
  * centred on the mirror sequence's image plane.  Everything else as gbd_sweep_plan_create;
  * the plan is used with the same calls.  Errors: GBD_EINVAL for a bad mirror sequence (as
  * gbd_trace_mirrors), f_number <= 0 or bad instances. */
+/* With shape = NULL a mirror sweep runs the row pairs (2 x 8 or 2 x 4): real-ray beamlets
+ * carry a uv term, which the row triples would evaluate directly at about half the speed. */
 gbd_status gbd_sweep_plan_create_mirrors(const gbd_mirror_system* system, double diameter,
                                          double f_number, const int32_t* n_across,
                                          const double* overlap_factor, const double* waist_ratio,

@@ -240,7 +240,10 @@ __global__ void __launch_bounds__(kThreads, 2)
 // The sums run in FP32 registers for at most kRowsChunkTiles tiles and are then folded
 // with TwoSum into a compensated pair per pixel in shared memory: hi as FP32, the much
 // smaller lo as BF16 (its rounding, 2^-9 of lo, is 2^-33 of hi), which makes 24 pixels a
-// thread fit next to two CTAs per SM.  Dynamic shared memory: the kStages record stages,
+// thread fit next to two CTAs per SM.  The direct instantiation folds after every tile: its
+// fields (uv terms, real-ray traces) near the centre add ~1,000 nearly equal in-phase terms
+// per 16 tiles onto a sum 50 times larger, whose FP32 rounding then drifts one way (scores
+// 1e-3 high at 51k beamlets; folding per tile costs under 1 % there).  Dynamic shared memory: the kStages record stages,
 // hi [3 CB][kThreads] float2, lo [3 CB][kThreads] bf16x2, then (FAST) each warp's row
 // terms of 32 beamlets.
 constexpr int kRowsChunkTiles = 16;
@@ -314,7 +317,8 @@ __global__ void __launch_bounds__(kThreads, 2)
             } else {
                 gbd::mixed_tile<RB, CB, true>(ts.tile(k), colf, rowf, acc);
             }
-            if ((k + 1) % kRowsChunkTiles == 0 || k + 1 == ts.nt) {
+            constexpr int kChunk = FAST ? kRowsChunkTiles : 1;
+            if ((k + 1) % kChunk == 0 || k + 1 == ts.nt) {
 #pragma unroll
                 for (int m = 0; m < RB * CB; ++m) {
                     const int q = m * kThreads + tid;
@@ -639,6 +643,9 @@ static gbd_status sweep_create(const gbd_trace_params& tp, const gbd_mirror_para
                                const double* waist_ratio, int32_t n_instances,
                                const gbd_detector* detector, const gbd_shape* shape,
                                gbd_sweep_plan** plan) {
+    // real-ray traced beamlets carry a uv term (the mirrors' small astigmatism), which the
+    // row triples can only evaluate directly: mirror sweeps default to the row pairs, which
+    // carry it along the row (the App. B telescope's 1024-instance sweep: 349 ms, 643 direct)
     gbd_status st = gbd_check_detector(detector);
     if (st != GBD_OK) return st;
     if (!(isfinite(diameter) && diameter > 0.0))
@@ -649,7 +656,7 @@ static gbd_status sweep_create(const gbd_trace_params& tp, const gbd_mirror_para
         return gbd_set_error(GBD_EINVAL, "instance arrays are NULL");
     // default: row triples on 8 columns (or row pairs on 4, whichever fits the width)
     const int cb = shape ? shape->cols_per_thread : gbd_auto_cols(detector->nx, 4);
-    const int rb = shape ? shape->rows_per_thread : (cb == 8 ? 3 : 2);
+    const int rb = shape ? shape->rows_per_thread : (cb == 8 && !mp ? 3 : 2);
     const int scheme = shape ? shape->scheme : GBD_SCHEME_ROW_PAIR;
     if (!find_sweep_shape(rb, cb, scheme))
         return gbd_set_error(GBD_EINVAL, "unsupported sweep shape");

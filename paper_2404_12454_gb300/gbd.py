@@ -106,6 +106,14 @@ _SIGS = {
                                              ctypes.POINTER(ctypes.c_double), ctypes.c_int32,
                                              ctypes.POINTER(gbd_detector), ctypes.POINTER(gbd_shape),
                                              ctypes.POINTER(ctypes.c_void_p)]),
+    "gbd_sweep_plan_create_mirrors": (ctypes.c_int, [ctypes.POINTER(gbd_mirror_system),
+                                                     ctypes.c_double, ctypes.c_double,
+                                                     ctypes.POINTER(ctypes.c_int32),
+                                                     ctypes.POINTER(ctypes.c_double),
+                                                     ctypes.POINTER(ctypes.c_double),
+                                                     ctypes.c_int32, ctypes.POINTER(gbd_detector),
+                                                     ctypes.POINTER(gbd_shape),
+                                                     ctypes.POINTER(ctypes.c_void_p)]),
     "gbd_sweep_workspace_bytes": (ctypes.c_size_t, [_P]),
     "gbd_sweep_set_zones": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_double)]),
@@ -388,19 +396,30 @@ class SweepPlan:
 
     def __init__(self, system, diameter, n_across, overlap_factor, waist_ratio, detector,
                  shape: Optional[Tuple[int, ...]] = None, stream=None, device="cuda",
-                 zones: Optional[Sequence[Tuple[float, float]]] = None):
+                 zones: Optional[Sequence[Tuple[float, float]]] = None,
+                 f_number: Optional[float] = None):
         """shape: (rows, cols[, scheme]) per thread; None = the library's sweep default (row
-        triples on 8 columns or row pairs on 4, fitted to the detector's width)."""
+        triples on 8 columns or row pairs on 4, fitted to the detector's width).  A mirror
+        system (workloads.MirrorSystem) traces every instance by real rays through it
+        (gbd_sweep_plan_create_mirrors) and needs the system's f_number."""
         import torch
         n, a, b, c = _instance_arrays(n_across, overlap_factor, waist_ratio)
         self.n = n
         self._plan = ctypes.c_void_p()
         sh = (gbd_shape(shape[0], shape[1], 1, 0.0, shape[2] if len(shape) > 2 else 0)
               if shape else None)
-        _check(lib().gbd_sweep_plan_create(ctypes.byref(make_system(system)), float(diameter), a, b,
-                                           c, n, ctypes.byref(make_detector(detector)),
-                                           ctypes.byref(sh) if sh else None,
-                                           ctypes.byref(self._plan)))
+        if hasattr(system, "radius"):
+            if f_number is None:
+                raise ValueError("a mirror sweep needs the system's f_number")
+            _check(lib().gbd_sweep_plan_create_mirrors(
+                ctypes.byref(make_mirror_system(system)), float(diameter), float(f_number), a, b,
+                c, n, ctypes.byref(make_detector(detector)), ctypes.byref(sh) if sh else None,
+                ctypes.byref(self._plan)))
+        else:
+            _check(lib().gbd_sweep_plan_create(ctypes.byref(make_system(system)), float(diameter),
+                                               a, b, c, n, ctypes.byref(make_detector(detector)),
+                                               ctypes.byref(sh) if sh else None,
+                                               ctypes.byref(self._plan)))
         self.n_regions = 1
         if zones:
             lo = (ctypes.c_double * len(zones))(*[float(z[0]) for z in zones])
@@ -436,9 +455,10 @@ class SweepPlan:
 
 
 def sweep_plan(sw, shape=None, stream=None, zones=None) -> SweepPlan:
-    """SweepPlan for a workloads.Sweep description."""
+    """SweepPlan for a workloads.Sweep or workloads.MirrorSweep description."""
     return SweepPlan(sw.system, sw.diameter, sw.n_across, sw.overlap_factor, sw.waist_ratio,
-                     sw.detector, shape, stream, zones=zones)
+                     sw.detector, shape, stream, zones=zones,
+                     f_number=getattr(sw, "f_number", None))
 
 
 def gbd_sweep_autotune(system, diameter, n_across, overlap_factor, waist_ratio, detector,

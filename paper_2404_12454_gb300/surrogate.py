@@ -36,9 +36,13 @@ def standardize(params: Sequence[Tuple[int, float, float]]) -> np.ndarray:
     return ((a - _CENTER) / _SCALE).astype(np.float32)
 
 
-def evaluate(params: Sequence[Tuple[int, float, float]], shape=None) -> np.ndarray:
-    """Airy scores of parameter sets (n_across, OF, WR) on the sweep optics, via the GPU."""
-    plan = gbd.sweep_plan(W.sweep_from_params(list(params)), shape=shape)
+def evaluate(params: Sequence[Tuple[int, float, float]], shape=None, optics=None) -> np.ndarray:
+    """Airy scores of parameter sets (n_across, OF, WR), via the GPU.  `optics` maps a list
+    of parameter sets to the sweep description that evaluates them (default: the thin-lens
+    sweep optics, workloads.sweep_from_params; workloads.telescope_sweep_from_params traces
+    the App. B telescope instead)."""
+    make = optics if optics is not None else W.sweep_from_params
+    plan = gbd.sweep_plan(make(list(params)), shape=shape)
     try:
         s = plan.run().cpu().numpy().copy()
         gbd.gbd_sync()
@@ -122,11 +126,11 @@ def _curve(scores: Sequence[float], steps: Sequence[int]) -> List[Tuple[int, flo
     return out
 
 
-def grid_search() -> SearchResult:
+def grid_search(optics=None) -> SearchResult:
     """The regular reference grid: 21 OF x 12 WR x 5 N, one batched sweep."""
     sw = W.grid_sweep()
     params = [(sw.n_across[k], sw.overlap_factor[k], sw.waist_ratio[k]) for k in range(sw.n_instances)]
-    s = evaluate(params)
+    s = evaluate(params, optics=optics)
     return SearchResult(params, list(s), [(len(params), float(np.min(s)))])
 
 
@@ -137,7 +141,8 @@ def random_candidates(n: int, rng: np.random.Generator) -> List[Tuple[int, float
     return [(int(a), float(b), float(c)) for a, b, c in zip(N, of, wr)]
 
 
-def random_search(budget: int, batch: int = 64, seed: int = W.SEED_SURROGATE + 1) -> SearchResult:
+def random_search(budget: int, batch: int = 64, seed: int = W.SEED_SURROGATE + 1,
+                  optics=None) -> SearchResult:
     """`budget` uniform draws over the search box, drawn and counted `batch` at a time (the
     first batch equals a surrogate search's initial sample of that size and seed)."""
     rng = np.random.default_rng(seed)
@@ -145,19 +150,21 @@ def random_search(budget: int, batch: int = 64, seed: int = W.SEED_SURROGATE + 1
     params = []
     for k in steps:
         params += random_candidates(k, rng)
-    s = evaluate(params)
+    s = evaluate(params, optics=optics)
     return SearchResult(params, list(s), _curve(s, steps))
 
 
 def surrogate_search(rounds: int = 8, per_round: int = 64, n_init: int = 128, pool: int = 16384,
                      fit_steps: int = 400, seed: int = W.SEED_SURROGATE,
                      checkpoint: Optional[str] = None, target: Optional[float] = None,
-                     min_rounds: int = 1, init_seed: Optional[int] = None) -> SearchResult:
+                     min_rounds: int = 1, init_seed: Optional[int] = None,
+                     optics=None) -> SearchResult:
     """Seeded initial sample (the first n_init instances of the 1024-instance sweep, or
     n_init random candidates drawn with `init_seed`), then rounds of fit -> rank a random
     pool -> verify the best per_round candidates.  After `min_rounds` rounds it stops early
     once the best verified score reaches `target` (if given).  With `checkpoint`, the data
-    and the network are saved after every round and a run resumes from them."""
+    and the network are saved after every round and a run resumes from them.  `optics` as
+    in `evaluate`."""
     if init_seed is None:
         sw = W.sweep()
         params = [(sw.n_across[k], sw.overlap_factor[k], sw.waist_ratio[k])
@@ -179,7 +186,7 @@ def surrogate_search(rounds: int = 8, per_round: int = 64, n_init: int = 128, po
         net.step = int(ck["step"])
         gbd.gbd_mlp_pack(net.master, net.weights)
     else:
-        scores = list(evaluate(params))
+        scores = list(evaluate(params, optics=optics))
         steps = [n_init]
     rng = np.random.default_rng(seed + 1000)
     for _ in range(start_round):  # keep the candidate stream identical on resume
@@ -194,7 +201,7 @@ def surrogate_search(rounds: int = 8, per_round: int = 64, n_init: int = 128, po
         pred = net.predict(standardize(cand))
         order = np.argsort(pred, kind="stable")
         chosen = [cand[k] for k in order[:per_round]]
-        s = evaluate(chosen)
+        s = evaluate(chosen, optics=optics)
         params += chosen
         scores += list(s)
         steps.append(len(chosen))
@@ -206,7 +213,7 @@ def surrogate_search(rounds: int = 8, per_round: int = 64, n_init: int = 128, po
 
 
 def compare_with_random(target: float, seeds: Sequence[int], n_init: int = 32,
-                        per_round: int = 32, budget: int = 1260) -> dict:
+                        per_round: int = 32, budget: int = 1260, optics=None) -> dict:
     """Evaluations each method needs to come within `target`, per seed: the surrogate
     search from n_init random draws (then rounds of per_round proposals), and random search
     drawing per_round candidates at a time, both capped at `budget` evaluations (None when
@@ -216,10 +223,10 @@ def compare_with_random(target: float, seeds: Sequence[int], n_init: int = 32,
     for sd in seeds:
         sur = surrogate_search(rounds=rounds, per_round=per_round, n_init=n_init,
                                seed=W.SEED_SURROGATE + sd, target=target, min_rounds=0,
-                               init_seed=sd)
+                               init_seed=sd, optics=optics)
         out["surrogate"].append(sur.evals_to_reach(target))
         rnd = random_search(budget=budget, batch=n_init if n_init == per_round else per_round,
-                            seed=sd)
+                            seed=sd, optics=optics)
         out["random"].append(rnd.evals_to_reach(target))
     return out
 

@@ -243,6 +243,64 @@ def hst_rc(n_across: int = 64, overlap_factor: float = 1.5, waist_ratio: float =
     return msys, Pupil(HST_DIAMETER[0], n_across, overlap_factor, waist_ratio), Detector(npix, npix, p, p)
 
 
+# The App. B prescription's image distance leaves the real system 108.1 um short of its
+# paraxial focus and 110.9 um short of its marginal focus (the RC pair's residual spherical
+# aberration).  The telescope sweep puts its detector midway, at the least-RMS-wavefront
+# focus, so that its Airy score measures the decomposition rather than that defocus.
+HST_REFOCUS = 109.5e-6
+# Detector of the telescope sweep: App. D's 2.8 mas pixels, 256^2 (+-7.6 lambda F#).
+HST_SWEEP_NPIX = 256
+
+
+@dataclasses.dataclass(frozen=True)
+class MirrorSweep:
+    """A batch of GBD instances traced through a mirror sequence (real rays), sharing the
+    optics and detector and differing in (N, OF, WR); f_number sets the Airy pattern."""
+
+    system: MirrorSystem
+    diameter: float
+    f_number: float
+    detector: Detector
+    n_across: Tuple[int, ...]
+    overlap_factor: Tuple[float, ...]
+    waist_ratio: Tuple[float, ...]
+
+    @property
+    def n_instances(self) -> int:
+        return len(self.n_across)
+
+    def pupil(self, k: int) -> Pupil:
+        return Pupil(self.diameter, self.n_across[k], self.overlap_factor[k], self.waist_ratio[k])
+
+
+def telescope_optics(refocus: float = HST_REFOCUS) -> Tuple[MirrorSystem, float, float, Detector]:
+    """The App. B telescope at 551 nm with its image plane moved `refocus` metres along the
+    axis, its pupil diameter, focal ratio (App. D's focal length) and the sweep's detector."""
+    msys, pupil, det = hst_rc(npix=HST_SWEEP_NPIX)
+    sp = tuple(HST_SPACING[:-1]) + (HST_SPACING[-1] + refocus,)
+    return (dataclasses.replace(msys, spacing=sp), pupil.diameter, HST_EFL / pupil.diameter, det)
+
+
+def telescope_sweep_from_params(params: Sequence[Tuple[int, float, float]],
+                                refocus: float = HST_REFOCUS) -> MirrorSweep:
+    msys, D, F, det = telescope_optics(refocus)
+    return MirrorSweep(msys, D, F, det, tuple(int(p[0]) for p in params),
+                       tuple(float(p[1]) for p in params), tuple(float(p[2]) for p in params))
+
+
+def telescope_sweep(n_instances: int = 1024, seed: int = SEED_SWEEP) -> MirrorSweep:
+    """The seeded 1024-instance draw of the parameter search (same draws as `sweep`) on the
+    telescope."""
+    sw = sweep(n_instances, seed)
+    return telescope_sweep_from_params(list(zip(sw.n_across, sw.overlap_factor, sw.waist_ratio)))
+
+
+def telescope_grid_sweep() -> MirrorSweep:
+    """The reference grid (21 OF x 12 WR x 5 N = 1,260) on the telescope."""
+    g = grid_sweep()
+    return telescope_sweep_from_params(list(zip(g.n_across, g.overlap_factor, g.waist_ratio)))
+
+
 def sweep_from_params(params: Sequence[Tuple[int, float, float]]) -> Sweep:
     system, D, det = sweep_optics()
     return Sweep(system, D, det, tuple(int(p[0]) for p in params),
@@ -285,6 +343,8 @@ def scaled(workload: Workload, n_across: Optional[int] = None, nx: Optional[int]
     return dataclasses.replace(workload, pupil=pupil, detector=det, oracle_stride=None)
 
 
-def sweep_subset(sw: Sweep, idx: List[int]) -> Sweep:
-    return Sweep(sw.system, sw.diameter, sw.detector, tuple(sw.n_across[i] for i in idx),
-                 tuple(sw.overlap_factor[i] for i in idx), tuple(sw.waist_ratio[i] for i in idx))
+def sweep_subset(sw, idx: List[int]):
+    """The instances idx of a Sweep or MirrorSweep."""
+    return dataclasses.replace(sw, n_across=tuple(sw.n_across[i] for i in idx),
+                               overlap_factor=tuple(sw.overlap_factor[i] for i in idx),
+                               waist_ratio=tuple(sw.waist_ratio[i] for i in idx))

@@ -70,3 +70,33 @@ def test_search_grid():
     assert set(g.n_across) == set(W.SWEEP_N_ACROSS)
     assert min(g.overlap_factor) == 1.0 and max(g.overlap_factor) == 3.0
     assert min(g.waist_ratio) == pytest.approx(0.8) and max(g.waist_ratio) == pytest.approx(3.0)
+
+
+def test_telescope_sweep_refocus_is_the_least_rms_focus():
+    """The telescope sweep's image plane sits midway between the real system's paraxial and
+    marginal foci (the least-RMS-wavefront focus of third-order spherical aberration), from
+    the oracle's real rays through the App. B prescription as printed."""
+    import oracle
+    msys, _, _ = W.hst_rc()
+
+    def crossing(h):
+        x, _, tx, _, _ = oracle.mirror_ray(msys, h, 0.0)
+        return -x / tx  # axial distance from the printed image plane to the axis crossing
+
+    paraxial, marginal = crossing(1e-3), crossing(0.5 * W.HST_DIAMETER[0])
+    assert 100e-6 < paraxial < marginal < 120e-6
+    assert W.HST_REFOCUS == pytest.approx(0.5 * (paraxial + marginal), abs=0.2e-6)
+    msys2, D, F, det = W.telescope_optics()
+    assert msys2.spacing[-1] == pytest.approx(W.HST_SPACING[-1] + W.HST_REFOCUS)
+    assert D == W.HST_DIAMETER[0] and F == pytest.approx(24.0)
+    assert (det.nx, det.ny) == (W.HST_SWEEP_NPIX, W.HST_SWEEP_NPIX)
+
+
+def test_telescope_sweep_uses_the_seeded_draws():
+    a, b = W.sweep(), W.telescope_sweep()
+    assert (a.n_across, a.overlap_factor, a.waist_ratio) == (b.n_across, b.overlap_factor,
+                                                             b.waist_ratio)
+    sub = W.sweep_subset(b, [3, 1])
+    assert isinstance(sub, W.MirrorSweep) and sub.n_across == (b.n_across[3], b.n_across[1])
+    g = W.telescope_grid_sweep()
+    assert g.n_instances == 1260 and g.system == b.system
