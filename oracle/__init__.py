@@ -5,7 +5,8 @@ and reference legs of ``bench.py`` may import this package.  It shares no code w
 the CUDA library and the library never imports it.
 
 The arithmetic lives in ``gbd_oracle.c`` (plain C, double precision, OpenMP over
-pixels); this module only marshals arguments.  Inputs are duck-typed objects with the
+pixels); this module marshals arguments, except for the truncated beamlets' edge factor
+1/2 erfc(zeta) (``truncation_factor``), written here in numpy with scipy's complex erfc.  Inputs are duck-typed objects with the
 attributes of the workload descriptions (``wavelength``, ``focal_length``, ...).
 
 Pins (tests/test_oracle_pins.py): closed-form Gaussian beam, focal-plane structure-factor
@@ -15,10 +16,12 @@ conservation, mirror symmetry, symplecticity, tilt = 0 reduction.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 from typing import Optional, Sequence, Tuple
 
 import numpy as np
+from scipy.special import erfc
 
 from . import build as _build
 
@@ -44,6 +47,9 @@ def lib():
         L.orc_threads.restype = _I
         L.orc_trace.argtypes = [_D, _D, _D, _I, _PI, _PD, _D, _D, _I, _D, _D, _PD, _I]
         L.orc_trace.restype = _I
+        L.orc_trace_truncated.argtypes = [_D, _D, _D, _I, _PI, _PD, _D, _D, _I, _D, _D, _D, _PD,
+                                          _PD, _I, _PI]
+        L.orc_trace_truncated.restype = _I
         for name in ("orc_field", "orc_field_exact"):
             fn = getattr(L, name)
             fn.argtypes = [_PD, _I, _D, _D, _D, _D, _I, _I, _D, _D, _PI, _I, _PI, _I, _PD]
@@ -127,6 +133,73 @@ def field(beamlets: np.ndarray, system, detector, cols: Optional[Sequence[int]] 
        detector.nx, detector.ny, detector.pitch_x, detector.pitch_y, _pi(c), c.size, _pi(r),
        r.size, _pd(out))
     return out[..., 0] + 1j * out[..., 1]
+
+
+def trace_truncated(system, pupil, margin: float = 3.0):
+    """Truncated decomposition (edge beamlets cut by the aperture's tangent half-plane):
+    (records, dist, n_edge), interior beamlets first, then edge beamlets; dist holds each
+    edge beamlet's signed distance d_j = R - |r_j| to the edge and +inf for interior ones."""
+    N = pupil.n_across
+    cap = (N + 2 * (int(math.ceil(0.5 * margin * pupil.overlap_factor)) + 1)) ** 2
+    out = np.zeros((cap, REC_SIZE), dtype=np.float64)
+    dist = np.zeros(cap, dtype=np.float64)
+    noll = np.ascontiguousarray(np.asarray(system.noll, dtype=np.int32).reshape(-1))
+    zc = np.ascontiguousarray(np.asarray(system.zern_coef, dtype=np.float64).reshape(-1))
+    nz = int(noll.size)
+    if nz == 0:
+        noll = np.zeros(1, dtype=np.int32)
+        zc = np.zeros(1)
+    ne = _I()
+    n = lib().orc_trace_truncated(system.wavelength, system.focal_length, system.distance, nz,
+                                  _pi(noll), _pd(zc), float(system.zern_radius),
+                                  pupil.diameter, N, pupil.overlap_factor, pupil.waist_ratio,
+                                  float(margin), _pd(out), _pd(dist), cap, ctypes.byref(ne))
+    if n < 0:
+        raise RuntimeError("oracle truncated trace: capacity too small")
+    return out[:n], dist[:n], int(ne.value)
+
+
+def truncation_factor(rec: np.ndarray, normal, d: float, wavelength: float, X, Y) -> np.ndarray:
+    """1/2 erfc(zeta) that turns beamlet `rec`'s Gaussian into the field of its input cut by
+    the half-plane n.(r - r_j) <= d (the Collins integral of Eq. collins over that half-plane
+    divided by the full one), at lab points (X, Y) of the untilted reference plane:
+        M = A + B P1,  zeta = (n^T M^-1 (rho - rho_c) - d) sqrt(i k / (2 n^T M^-1 B n)),
+    principal square root (its real part > 0 keeps the cut Gaussian integrable)."""
+    k = 2.0 * math.pi / wavelength
+    w0 = rec[REC_W0]
+    A = rec[REC_ABCD:REC_ABCD + 4].reshape(2, 2)
+    B = rec[REC_ABCD + 4:REC_ABCD + 8].reshape(2, 2)
+    M = A + B * (-1j * wavelength / (math.pi * w0 * w0))
+    Mi = np.linalg.inv(M)
+    n = np.asarray(normal, dtype=np.float64)
+    sigma = n @ Mi @ B @ n
+    root = np.sqrt(1j * k / (2.0 * sigma))
+    u = n @ Mi  # row vector n^T M^-1
+    t = u[0] * (X - rec[REC_RHO]) + u[1] * (Y - rec[REC_RHO + 1])
+    return 0.5 * erfc((t - d) * root)
+
+
+def field_truncated(records: np.ndarray, dist: np.ndarray, system, detector,
+                    cols: Optional[Sequence[int]] = None, rows: Optional[Sequence[int]] = None,
+                    normals: Optional[np.ndarray] = None) -> np.ndarray:
+    """Coherent sum of a truncated decomposition on an untilted detector: interior beamlets
+    (dist = +inf) as Gaussians (orc_field), each edge beamlet's Gaussian times its truncation
+    factor.  normals: per-beamlet edge normals (default r_j / |r_j|)."""
+    if detector.rot_x != 0.0 or detector.rot_y != 0.0:
+        raise ValueError("truncated beamlets are evaluated on untilted planes")
+    c, r = _pixels(detector, cols, rows)
+    inner = ~np.isfinite(dist)
+    E = field(records[inner], system, detector, c, r) if inner.any() else \
+        np.zeros((r.size, c.size), dtype=np.complex128)
+    X = ((c - detector.nx // 2) * detector.pitch_x)[None, :]
+    Y = ((r - detector.ny // 2) * detector.pitch_y)[:, None]
+    for q in np.flatnonzero(~inner):
+        rec = records[q]
+        nrm = normals[q] if normals is not None else rec[REC_RJ:REC_RJ + 2] / np.hypot(
+            rec[REC_RJ], rec[REC_RJ + 1])
+        g = field(rec[None, :], system, detector, c, r)
+        E = E + g * truncation_factor(rec, nrm, dist[q], system.wavelength, X, Y)
+    return E
 
 
 def zernike(j: int, radius: float, x: float, y: float) -> Tuple[float, float, float]:

@@ -226,6 +226,68 @@ void orc_sqrtdet_v(const double* m, double* out) {
 
 /* ------------------------------------------------------------------- trace -- */
 
+/* One beamlet centred at (rx, ry) in the pupil: chief ray, 4 parabasal rays, one-sided
+ * differences for ABCD (Sec. 2.2), Eq. gauss_prop with the eigenvalue sqrtdet; fills one
+ * record (zeroed first). */
+static void trace_beamlet(const orc_system* S, double rx, double ry, double a, double w0,
+                          double h, double dth, double complex p1, double* rec) {
+    memset(rec, 0, sizeof(double) * REC_SIZE);
+    /* chief ray */
+    double rc[2] = {rx, ry}, tc[2] = {0.0, 0.0}, L = 0.0;
+    trace_ray(S, rc, tc, &L);
+    /* waist rays (position offsets) -> columns of A and C */
+    double A[2][2], B[2][2], C[2][2], D[2][2];
+    for (int k = 0; k < 2; ++k) {
+        double r[2] = {rx + (k == 0 ? h : 0.0), ry + (k == 1 ? h : 0.0)};
+        double t[2] = {0.0, 0.0}, o = 0.0;
+        trace_ray(S, r, t, &o);
+        for (int q = 0; q < 2; ++q) {
+            A[q][k] = (r[q] - rc[q]) / h;
+            C[q][k] = (t[q] - tc[q]) / h;
+        }
+    }
+    /* divergence rays (slope offsets) -> columns of B and D */
+    for (int k = 0; k < 2; ++k) {
+        double r[2] = {rx, ry};
+        double t[2] = {k == 0 ? dth : 0.0, k == 1 ? dth : 0.0}, o = 0.0;
+        trace_ray(S, r, t, &o);
+        for (int q = 0; q < 2; ++q) {
+            B[q][k] = (r[q] - rc[q]) / dth;
+            D[q][k] = (t[q] - tc[q]) / dth;
+        }
+    }
+    /* Eq. gauss_prop: M = A + B P1, P2 = (C + D P1) M^-1, amplitude 1/sqrtdet(M) */
+    cmat2 M, Nn;
+    for (int q = 0; q < 2; ++q)
+        for (int k = 0; k < 2; ++k) {
+            M.m[q][k] = A[q][k] + B[q][k] * p1;
+            Nn.m[q][k] = C[q][k] + D[q][k] * p1;
+        }
+    cmat2 P = cmul(Nn, cinv(M));
+    double complex alpha = a / orc_sqrtdet(M.m[0][0], M.m[0][1], M.m[1][0], M.m[1][1]);
+
+    rec[REC_RJ] = rx;
+    rec[REC_RJ + 1] = ry;
+    rec[REC_A] = a;
+    rec[REC_W0] = w0;
+    for (int q = 0; q < 2; ++q)
+        for (int k = 0; k < 2; ++k) {
+            rec[REC_ABCD + 0 + 2 * q + k] = A[q][k];
+            rec[REC_ABCD + 4 + 2 * q + k] = B[q][k];
+            rec[REC_ABCD + 8 + 2 * q + k] = C[q][k];
+            rec[REC_ABCD + 12 + 2 * q + k] = D[q][k];
+            rec[REC_P + 2 * (2 * q + k)] = creal(P.m[q][k]);
+            rec[REC_P + 2 * (2 * q + k) + 1] = cimag(P.m[q][k]);
+        }
+    rec[REC_ALPHA] = creal(alpha);
+    rec[REC_ALPHA + 1] = cimag(alpha);
+    rec[REC_L] = L;
+    rec[REC_RHO] = rc[0];
+    rec[REC_RHO + 1] = rc[1];
+    rec[REC_THETA] = tc[0];
+    rec[REC_THETA + 1] = tc[1];
+}
+
 /* Builds the beamlet table.  Returns the number of beamlets, or -1 when capacity is
  * too small.  out: capacity x REC_SIZE doubles; beamlets in row-major grid order
  * (row j along y outer, column i along x inner). */
@@ -249,66 +311,61 @@ int orc_trace(double wavelength, double f, double d, int n_zern, const int* noll
         for (int i = 0; i < N; ++i) {
             if (!inside(i, j, N)) continue;
             if (nb >= capacity) return -1;
-            double* rec = out + (size_t)nb * REC_SIZE;
-            memset(rec, 0, sizeof(double) * REC_SIZE);
             double rx = (i - (N - 1) / 2.0) * s, ry = (j - (N - 1) / 2.0) * s;
-            /* chief ray */
-            double rc[2] = {rx, ry}, tc[2] = {0.0, 0.0}, L = 0.0;
-            trace_ray(&S, rc, tc, &L);
-            /* waist rays (position offsets) -> columns of A and C */
-            double A[2][2], B[2][2], C[2][2], D[2][2];
-            for (int k = 0; k < 2; ++k) {
-                double r[2] = {rx + (k == 0 ? h : 0.0), ry + (k == 1 ? h : 0.0)};
-                double t[2] = {0.0, 0.0}, o = 0.0;
-                trace_ray(&S, r, t, &o);
-                for (int q = 0; q < 2; ++q) {
-                    A[q][k] = (r[q] - rc[q]) / h;
-                    C[q][k] = (t[q] - tc[q]) / h;
-                }
-            }
-            /* divergence rays (slope offsets) -> columns of B and D */
-            for (int k = 0; k < 2; ++k) {
-                double r[2] = {rx, ry};
-                double t[2] = {k == 0 ? dth : 0.0, k == 1 ? dth : 0.0}, o = 0.0;
-                trace_ray(&S, r, t, &o);
-                for (int q = 0; q < 2; ++q) {
-                    B[q][k] = (r[q] - rc[q]) / dth;
-                    D[q][k] = (t[q] - tc[q]) / dth;
-                }
-            }
-            /* Eq. gauss_prop: M = A + B P1, P2 = (C + D P1) M^-1, amplitude 1/sqrtdet(M) */
-            cmat2 M, Nn;
-            for (int q = 0; q < 2; ++q)
-                for (int k = 0; k < 2; ++k) {
-                    M.m[q][k] = A[q][k] + B[q][k] * p1;
-                    Nn.m[q][k] = C[q][k] + D[q][k] * p1;
-                }
-            cmat2 P = cmul(Nn, cinv(M));
-            double complex alpha = a / orc_sqrtdet(M.m[0][0], M.m[0][1], M.m[1][0], M.m[1][1]);
-
-            rec[REC_RJ] = rx;
-            rec[REC_RJ + 1] = ry;
-            rec[REC_A] = a;
-            rec[REC_W0] = w0;
-            for (int q = 0; q < 2; ++q)
-                for (int k = 0; k < 2; ++k) {
-                    rec[REC_ABCD + 0 + 2 * q + k] = A[q][k];
-                    rec[REC_ABCD + 4 + 2 * q + k] = B[q][k];
-                    rec[REC_ABCD + 8 + 2 * q + k] = C[q][k];
-                    rec[REC_ABCD + 12 + 2 * q + k] = D[q][k];
-                    rec[REC_P + 2 * (2 * q + k)] = creal(P.m[q][k]);
-                    rec[REC_P + 2 * (2 * q + k) + 1] = cimag(P.m[q][k]);
-                }
-            rec[REC_ALPHA] = creal(alpha);
-            rec[REC_ALPHA + 1] = cimag(alpha);
-            rec[REC_L] = L;
-            rec[REC_RHO] = rc[0];
-            rec[REC_RHO + 1] = rc[1];
-            rec[REC_THETA] = tc[0];
-            rec[REC_THETA + 1] = tc[1];
+            trace_beamlet(&S, rx, ry, a, w0, h, dth, p1, out + (size_t)nb * REC_SIZE);
             ++nb;
         }
     }
+    return nb;
+}
+
+/* Truncated decomposition (Sec. 1 and the Conclusion: beamlets truncated at the aperture
+ * edge, Worku & Gross).  The same grid and weights as orc_trace, extended to every centre
+ * with |r_j| <= R + margin w0 (R = D/2).  A beamlet whose centre lies within margin w0 of the
+ * edge (| R - |r_j| | <= margin w0) is an edge beamlet: its input Gaussian is cut by the
+ * half-plane n.r <= R tangent to the aperture at the point nearest to it, n = r_j/|r_j|,
+ * i.e. by n.(r - r_j) <= d_j with d_j = R - |r_j| (negative for centres outside).  The
+ * others are interior beamlets, used untruncated.  In half-pitch units (a = 2i - (N-1),
+ * b = 2j - (N-1)) R = N and w0 = OF: interior a^2 + b^2 < (N - margin OF)^2, kept
+ * a^2 + b^2 <= (N + margin OF)^2.  out: interior beamlets first, then edge beamlets, each in
+ * row-major grid order; dist[k] = d_k (edge) or +inf (interior); *n_edge = edge count.
+ * Returns the number of beamlets, or -1 when capacity is too small. */
+int orc_trace_truncated(double wavelength, double f, double d, int n_zern, const int* noll,
+                        const double* zc, double zrad, double diameter, int n_across,
+                        double overlap_factor, double waist_ratio, double margin, double* out,
+                        double* dist, int capacity, int* n_edge) {
+    orc_system S = {wavelength, f, d, n_zern, noll, zc, zrad};
+    const int N = n_across;
+    const double s = diameter / N, R = 0.5 * diameter;
+    const double w0 = overlap_factor * diameter / (2.0 * N);
+    const double a = s * s / (M_PI * w0 * w0);
+    const double h = waist_ratio * w0;
+    const double dth = waist_ratio * wavelength / (M_PI * w0);
+    const double complex p1 = -I * wavelength / (M_PI * w0 * w0);
+    const double outer = (N + margin * overlap_factor) * (N + margin * overlap_factor);
+    const double inner_r = N - margin * overlap_factor;
+    const double inner = inner_r > 0.0 ? inner_r * inner_r : -1.0;
+    /* grid indices whose centre can lie within R + margin w0 */
+    const int ext = (int)ceil(0.5 * margin * overlap_factor) + 1;
+    int nb = 0, ne = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int j = -ext; j < N + ext; ++j) {
+            for (int i = -ext; i < N + ext; ++i) {
+                const double aa = 2.0 * i - (N - 1), bb = 2.0 * j - (N - 1);
+                const double q = aa * aa + bb * bb;
+                if (q > outer) continue;
+                const int edge = !(q < inner);
+                if (edge != pass) continue;
+                if (nb >= capacity) return -1;
+                double rx = (i - (N - 1) / 2.0) * s, ry = (j - (N - 1) / 2.0) * s;
+                trace_beamlet(&S, rx, ry, a, w0, h, dth, p1, out + (size_t)nb * REC_SIZE);
+                dist[nb] = edge ? R - sqrt(rx * rx + ry * ry) : INFINITY;
+                ne += edge;
+                ++nb;
+            }
+        }
+    }
+    *n_edge = ne;
     return nb;
 }
 
