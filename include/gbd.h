@@ -93,7 +93,8 @@ typedef struct {
     double center[2];   /* beamlet centre r_j in the pupil, m                           */
     double weight;      /* a_j = s^2 / (pi w0^2)                                        */
     double waist;       /* w0 = OF D / (2N), m                                          */
-    double reserved;    /* 0                                                            */
+    double edge_distance; /* 0; for an edge beamlet of gbd_trace_truncated, the signed
+                             distance d_j = R - |r_j| from its centre to the aperture edge */
 } gbd_beamlet;
 
 /* Message describing the last failure on this thread ("" when none). */
@@ -200,6 +201,44 @@ size_t gbd_field_workspace_bytes(int32_t n_beamlets, const gbd_detector* detecto
 gbd_status gbd_field(const gbd_beamlet* beamlets, int32_t n_beamlets, double wavelength,
                      const gbd_detector* detector, int32_t precision, void* workspace,
                      size_t workspace_bytes, void* field_out, void* stream);
+
+/* ------------------------------------------------------- truncated beamlets ------
+ * Beamlets truncated at the aperture edge (Sec. 1 and the Conclusion: Worku & Gross's
+ * truncated Gaussian beamlets represent hard edges better; the plane method applies to any
+ * closed-form solution of the Collins integral, Eq. collins).
+ * Decomposition (gbd_trace_truncated): the gbd_trace grid (same spacing s, waist w0, weights)
+ *   extended to every centre with |r_j| <= R + margin w0 (R = D/2).  Centres more than
+ *   margin w0 inside the edge give whole beamlets; the others are edge beamlets, whose input
+ *   Gaussian is cut by the aperture's tangent half-plane n.(r - r_j) <= d_j, n = r_j/|r_j|,
+ *   d_j = R - |r_j| (negative outside).  In half-pitch units (a = 2i - (N-1), b = 2j - (N-1))
+ *   a centre is kept when a^2 + b^2 <= (N + margin OF)^2 and whole when a^2 + b^2 <
+ *   (N - margin OF)^2.  out: the whole beamlets first, then the edge beamlets, each in
+ *   row-major grid order (the grid's row j along y outer); an edge beamlet's edge_distance
+ *   is d_j.  *n_edge (host, may be NULL) receives the edge count.
+ * gbd_truncated_count: the number of beamlets (and in *n_edge the edge ones), or -1 for bad
+ *   arguments (host only).
+ * gbd_field_truncated: the field of such a table on an UNTILTED detector: the first
+ *   n_beamlets - n_edge records as gbd_field, plus for each edge beamlet its Gaussian times
+ *       1/2 erfc(zeta),  zeta = (n^T M^-1 (rho - rho_c) - d) sqrt(i k / (2 n^T M^-1 B n)),
+ *   M = A + B P1 (the Collins integral of the cut Gaussian over its half-plane; principal
+ *   root), evaluated through the Faddeeva function (Weideman's rational approximation:
+ *   36 terms in FP64, 16 in the mixed path's FP32).  workspace: at least
+ *   gbd_field_truncated_workspace_bytes(...) bytes, 256-byte aligned.
+ * Errors: GBD_EINVAL (bad arguments, margin outside [0, 10], n_edge outside
+ *   [0, n_beamlets]), GBD_ENOMEM (capacity or workspace too small), GBD_EUNSUPPORTED (a
+ *   tilted detector). */
+int32_t gbd_truncated_count(const gbd_pupil* pupil, double overlap_factor, double margin,
+                            int32_t* n_edge);
+gbd_status gbd_trace_truncated(const gbd_system* system, const gbd_pupil* pupil,
+                               double overlap_factor, double waist_ratio, double margin,
+                               gbd_beamlet* out, int32_t capacity, int32_t* n_edge,
+                               void* stream);
+size_t gbd_field_truncated_workspace_bytes(int32_t n_beamlets, int32_t n_edge,
+                                           const gbd_detector* detector, int32_t precision);
+gbd_status gbd_field_truncated(const gbd_beamlet* beamlets, int32_t n_beamlets, int32_t n_edge,
+                               double wavelength, const gbd_detector* detector, int32_t precision,
+                               void* workspace, size_t workspace_bytes, void* field_out,
+                               void* stream);
 
 /* ------------------------------------------------------------ gbd_field_rows ------
  * The same field (Eq. sum_gaussian with the plane form of Eq. collins_factored, as

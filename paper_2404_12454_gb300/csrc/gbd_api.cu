@@ -469,6 +469,42 @@ gbd_status gbd_field_fixed_scratch(const gbd_beamlet* beamlets, int32_t n, doubl
                      stream, sh);
 }
 
+// The truncated decomposition's grid classes in half-pitch units (a = 2i - (N-1),
+// b = 2j - (N-1); R = N, w0 = OF): kept when a^2 + b^2 <= outer = (N + margin OF)^2,
+// interior when a^2 + b^2 < inner = (N - margin OF)^2.
+struct TruncatedGrid {
+    int ext;
+    double inner, outer;
+    int32_t total, edge;
+};
+
+gbd_status truncated_grid(const gbd_pupil* pupil, double overlap_factor, double margin,
+                          TruncatedGrid* g) {
+    gbd_status st = check_pupil(pupil);
+    if (st != GBD_OK) return st;
+    if (!finite_pos(overlap_factor)) return fail(GBD_EINVAL, "overlap_factor must be > 0");
+    if (!(margin >= 0.0 && margin <= 10.0)) return fail(GBD_EINVAL, "margin must be in [0, 10]");
+    const int N = pupil->n_across;
+    const double mo = margin * overlap_factor;
+    const double ro = N + mo, ri = N - mo;
+    g->outer = ro * ro;
+    g->inner = ri > 0.0 ? ri * ri : -1.0;
+    g->ext = (int)ceil(0.5 * mo) + 1;
+    long long total = 0, edge = 0;
+    for (int j = -g->ext; j < N + g->ext; ++j)
+        for (int i = -g->ext; i < N + g->ext; ++i) {
+            const double a = 2.0 * i - (N - 1), b = 2.0 * j - (N - 1);
+            const double q = a * a + b * b;
+            if (q > g->outer) continue;
+            ++total;
+            edge += !(q < g->inner);
+        }
+    if (total > INT32_MAX) return fail(GBD_EINVAL, "too many beamlets");
+    g->total = (int32_t)total;
+    g->edge = (int32_t)edge;
+    return GBD_OK;
+}
+
 // Kernel parameters of a mirror sequence (lab-frame vertices and curvatures, the pupil
 // plane and the axial path); the pupil sampling is set by the caller.
 gbd_status gbd_make_mirror_params(const gbd_mirror_system* system, double diameter,
@@ -662,6 +698,79 @@ gbd_status gbd_field_rows(const gbd_beamlet* beamlets, int32_t n_beamlets, doubl
     return run_field(beamlets, n_beamlets, wavelength, detector, precision, workspace,
                      workspace_bytes, field_out, static_cast<cudaStream_t>(stream),
                      stored_shape(precision, detector), row_begin, row_end);
+}
+
+int32_t gbd_truncated_count(const gbd_pupil* pupil, double overlap_factor, double margin,
+                            int32_t* n_edge) {
+    TruncatedGrid g;
+    if (truncated_grid(pupil, overlap_factor, margin, &g) != GBD_OK) return -1;
+    if (n_edge) *n_edge = g.edge;
+    return g.total;
+}
+
+gbd_status gbd_trace_truncated(const gbd_system* system, const gbd_pupil* pupil,
+                               double overlap_factor, double waist_ratio, double margin,
+                               gbd_beamlet* out, int32_t capacity, int32_t* n_edge,
+                               void* stream) {
+    GBD_NVTX_RANGE("gbd_trace_truncated");
+    gbd_status st = check_system(system);
+    if (st != GBD_OK) return st;
+    TruncatedGrid g;
+    if ((st = truncated_grid(pupil, overlap_factor, margin, &g)) != GBD_OK) return st;
+    if (!finite_pos(waist_ratio)) return fail(GBD_EINVAL, "waist_ratio must be > 0");
+    if (capacity < g.total) return fail(GBD_ENOMEM, "capacity %d < %d beamlets", capacity, g.total);
+    if (g.total > 0 && !out) return fail(GBD_EINVAL, "out is NULL");
+    if (reinterpret_cast<uintptr_t>(out) & 15u) return fail(GBD_EINVAL, "out must be 16-byte aligned");
+    if (n_edge) *n_edge = g.edge;
+    gbd_trace_params p = gbd_make_trace_params(system, pupil->diameter);
+    p.overlap_factor = overlap_factor;
+    p.waist_ratio = waist_ratio;
+    p.n_across = pupil->n_across;
+    p.grid = gbd_make_grid(pupil->diameter, system->wavelength, pupil->n_across, overlap_factor,
+                           waist_ratio);
+    cudaError_t e;
+    {
+        TimingScope ts(kTimeTrace, static_cast<cudaStream_t>(stream));
+        e = gbd_launch_trace_truncated(p, g.ext, g.inner, g.outer, g.total - g.edge, out,
+                                       static_cast<cudaStream_t>(stream));
+    }
+    return e == cudaSuccess ? GBD_OK : cuda_fail(e, "gbd_trace_truncated launch");
+}
+
+size_t gbd_field_truncated_workspace_bytes(int32_t n_beamlets, int32_t n_edge,
+                                           const gbd_detector* detector, int32_t precision) {
+    if (check_detector(detector) != GBD_OK || n_beamlets < 0 || n_edge < 0 || n_edge > n_beamlets)
+        return 0;
+    if (precision != GBD_PREC_F64 && precision != GBD_PREC_MIXED) return 0;
+    const size_t edge = align256((size_t)n_edge * gbd::kEdgeFields * sizeof(double2));
+    return edge + gbd_field_workspace_bytes(n_beamlets - n_edge, detector, precision);
+}
+
+gbd_status gbd_field_truncated(const gbd_beamlet* beamlets, int32_t n_beamlets, int32_t n_edge,
+                               double wavelength, const gbd_detector* detector, int32_t precision,
+                               void* workspace, size_t workspace_bytes, void* field_out,
+                               void* stream) {
+    GBD_NVTX_RANGE("gbd_field_truncated");
+    gbd_status st = check_field_args(beamlets, n_beamlets, wavelength, detector, precision,
+                                     workspace, field_out);
+    if (st != GBD_OK) return st;
+    if (n_edge < 0 || n_edge > n_beamlets)
+        return fail(GBD_EINVAL, "n_edge must be in [0, n_beamlets]");
+    if (detector->rot_x != 0.0 || detector->rot_y != 0.0)
+        return fail(GBD_EUNSUPPORTED, "truncated beamlets are evaluated on untilted planes");
+    const size_t edge = align256((size_t)n_edge * gbd::kEdgeFields * sizeof(double2));
+    if (workspace_bytes < edge) return fail(GBD_ENOMEM, "workspace too small for the edge records");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    char* base = static_cast<char*>(workspace);
+    st = run_field(beamlets, n_beamlets - n_edge, wavelength, detector, precision, base + edge,
+                   workspace_bytes - edge, field_out, s, stored_shape(precision, detector));
+    if (st != GBD_OK || n_edge == 0) return st;
+    const gbd_project_params pp = project_params(wavelength, detector);
+    double2* rec = reinterpret_cast<double2*>(base);
+    cudaError_t e = gbd_launch_project_edge(beamlets + (n_beamlets - n_edge), n_edge, pp, rec, s);
+    if (e == cudaSuccess)
+        e = gbd_launch_field_edge(precision, rec, n_edge, detector->nx, detector->ny, field_out, s);
+    return e == cudaSuccess ? GBD_OK : cuda_fail(e, "gbd_field_truncated launch");
 }
 
 gbd_status gbd_field_set_shape(int32_t precision, const gbd_shape* shape) {

@@ -26,6 +26,7 @@ struct NvtxRange {
 constexpr int kTile = 64;
 constexpr int kMixedFields = 4;   // float4 fields per beamlet
 constexpr int kF64Fields = 8;     // double2 fields per beamlet
+constexpr int kEdgeFields = 16;   // double2 fields per edge record (truncated beamlets)
 constexpr uint32_t kMixedTileBytes = kTile * kMixedFields * 16;
 constexpr uint32_t kF64TileBytes = kTile * kF64Fields * 16;
 constexpr float kPadLog2Amp = -1000.0f;  // exp2 of this is 0: padding beamlets vanish
@@ -277,6 +278,16 @@ cudaError_t gbd_launch_field_kernel(int precision, const void* coeffs, int n_til
 cudaError_t gbd_launch_field_reduce(int precision, const gbd_project_params& p, int splits,
                                     const void* partial, void* out, int out_row0, int out_rows,
                                     cudaStream_t s);
+// Truncated decomposition: trace of the extended grid (interior beamlets first), and the
+// edge records of its last n beamlets (see project_edge_kernel).
+cudaError_t gbd_launch_trace_truncated(const gbd_trace_params& p, int ext, double inner,
+                                       double outer, long long n_interior, gbd_beamlet* out,
+                                       cudaStream_t s);
+cudaError_t gbd_launch_project_edge(const gbd_beamlet* b, int n, const gbd_project_params& p,
+                                    double2* out, cudaStream_t s);
+// Adds the edge beamlets' sum onto a field of nx x ny pixels (complex64 / complex128).
+cudaError_t gbd_launch_field_edge(int precision, const double2* edge_records, int n_edge, int nx,
+                                  int ny, void* out, cudaStream_t s);
 // Height of the pixel-row blocks of every kernel a launch runs: a slab that starts on a
 // multiple of it is split into the same thread row blocks as the whole detector.
 int gbd_field_row_block(int precision, const gbd_field_launch& L);

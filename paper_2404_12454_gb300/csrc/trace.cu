@@ -199,7 +199,7 @@ __device__ void trace_one(const Tracer& T, const gbd_grid& g, int N, int i, int 
     r.center[1] = cy;
     r.weight = weight;
     r.waist = w0;
-    r.reserved = 0.0;
+    r.edge_distance = 0.0;
     *out = r;
 }
 
@@ -254,6 +254,56 @@ __global__ void __launch_bounds__(128) trace_mirrors_kernel(gbd_mirror_params M,
     const int i_lo = ((N - 1) - a) / 2;
     for (int t = blockIdx.z * blockDim.x + threadIdx.x; t <= a; t += blockDim.x * gridDim.z)
         trace_one(MirrorTracer{M}, M.grid, N, i_lo + t, j, out + row_off + t);
+}
+
+// Truncated decomposition (gbd_trace_truncated): the grid extended to every centre within
+// R + margin w0, interior beamlets (q < inner) first, then edge beamlets, each in row-major
+// grid order; q = a^2 + b^2 in half-pitch units (a = 2i - (N-1), b = 2j - (N-1)), kept when
+// q <= outer.  grid: (row of the extended grid, pass 0 interior / 1 edge); 128 threads.
+// Each CTA sums the counts of the rows before its own (O(rows^2) per CTA, tiny), then its
+// threads rank the row's members by a block-wide ballot scan.
+__device__ __forceinline__ int truncated_class(int i, int j, int N, double inner, double outer) {
+    const double a = 2.0 * i - (N - 1), b = 2.0 * j - (N - 1);
+    const double q = a * a + b * b;  // exact: integers below 2^26
+    if (q > outer) return -1;
+    return q < inner ? 0 : 1;
+}
+
+__global__ void __launch_bounds__(128) trace_truncated_kernel(gbd_trace_params P, int ext,
+                                                              double inner, double outer,
+                                                              long long n_interior,
+                                                              gbd_beamlet* __restrict__ out) {
+    const int N = P.n_across, W = N + 2 * ext;
+    const int j = (int)blockIdx.x - ext, pass = blockIdx.y;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __shared__ long long warp_sum[4];
+    __shared__ int warp_cnt[4];
+    long long acc = 0;
+    for (long long q = tid; q < (long long)(j + ext) * W; q += blockDim.x)
+        acc += truncated_class((int)(q % W) - ext, (int)(q / W) - ext, N, inner, outer) == pass;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) warp_sum[warp] = acc;
+    __syncthreads();
+    long long base = warp_sum[0] + warp_sum[1] + warp_sum[2] + warp_sum[3] +
+                     (pass ? n_interior : 0);
+    const double R = 0.5 * P.diameter;
+    for (int c0 = 0; c0 < W; c0 += blockDim.x) {
+        const int i = c0 + tid - ext;
+        const bool mine = c0 + tid < W && truncated_class(i, j, N, inner, outer) == pass;
+        const unsigned bal = __ballot_sync(0xffffffffu, mine);
+        __syncthreads();  // warp_cnt of the previous chunk has been read
+        if (lane == 0) warp_cnt[warp] = __popc(bal);
+        __syncthreads();
+        int before = __popc(bal & ((1u << lane) - 1u));
+        for (int w = 0; w < warp; ++w) before += warp_cnt[w];
+        if (mine) {
+            gbd_beamlet* o = out + base + before;
+            trace_one(LensTracer{P}, P.grid, N, i, j, o);
+            if (pass) o->edge_distance = R - sqrt(o->center[0] * o->center[0] +
+                                                  o->center[1] * o->center[1]);
+        }
+        base += warp_cnt[0] + warp_cnt[1] + warp_cnt[2] + warp_cnt[3];
+    }
 }
 
 // ---------------------------------------------------------------- projection --
@@ -518,7 +568,82 @@ __global__ void __launch_bounds__(256)
     if (f && wide) atomicOr(wide, f);
 }
 
+// Edge records of a truncated decomposition (FP64, gbd::kEdgeFields double2 per beamlet,
+// beamlet after beamlet), for an untilted detector:
+//   [0] (i0, j0)  [1..6] the beamlet's Gaussian, (log2 |E|, phase in turns) coefficients of
+//   1, tu, tv, tu^2, tu tv, tv^2 (as the FP64 records)  [7..9] zeta = z0 + zu tu + zv tv
+//   [10..15] Psi = ln E - zeta^2 + ln(1/2) in the same form.
+// The cut beamlet's field is E 1/2 erfc(zeta) = e^Psi w(i zeta) (Re zeta >= 0) or
+// E - e^Psi w(-i zeta) (Re zeta < 0), w the Faddeeva function; with n = r_j / |r_j|,
+// M = A + B P1, zeta = (n^T M^-1 (rho - rho_c) - d) sqrt(i k / (2 n^T M^-1 B n)) (the
+// Collins integral over the half-plane n.(r - r_j) <= d of the input, principal root).
+__global__ void __launch_bounds__(128) project_edge_kernel(const gbd_beamlet* __restrict__ b,
+                                                           int n, gbd_project_params G,
+                                                           double2* __restrict__ out) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const gbd_beamlet bm = b[t];
+    double2* o = out + (size_t)t * gbd::kEdgeFields;
+    Quad q = project_one(bm, G);
+    if (q.pad) {
+        for (int m = 0; m < gbd::kEdgeFields; ++m) o[m] = make_double2(0.0, 0.0);
+        o[1].x = o[10].x = 2.0 * gbd::kPadLog2Amp;
+        return;
+    }
+    add_amplitude_f64(q, bm);
+    const double k = 2.0 * M_PI * G.inv_wavelength;
+    const double w0 = bm.waist, p1 = -G.wavelength / (M_PI * w0 * w0);  // P1 = i p1 I
+    // M = A + B P1 and its inverse; sigma = n^T M^-1 B n; u = n^T M^-1
+    const double* A = bm.abcd;
+    const double* B = bm.abcd + 4;
+    const cd M00{A[0], B[0] * p1}, M01{A[1], B[1] * p1}, M10{A[2], B[2] * p1}, M11{A[3], B[3] * p1};
+    const cd idet = gbd::cdiv(gbd::mk(1.0), M00 * M11 - M01 * M10);
+    const cd Mi00 = M11 * idet, Mi01 = gbd::mk(0.0) - M01 * idet, Mi10 = gbd::mk(0.0) - M10 * idet,
+             Mi11 = M00 * idet;
+    const double rr = sqrt(bm.center[0] * bm.center[0] + bm.center[1] * bm.center[1]);
+    const double nx = rr > 0.0 ? bm.center[0] / rr : 1.0, ny = rr > 0.0 ? bm.center[1] / rr : 0.0;
+    const cd u0 = nx * Mi00 + ny * Mi10, u1 = nx * Mi01 + ny * Mi11;  // n^T M^-1
+    const double Bn0 = B[0] * nx + B[1] * ny, Bn1 = B[2] * nx + B[3] * ny;
+    const cd sigma = Bn0 * u0 + Bn1 * u1;
+    const cd root = gbd::csqrt_p(gbd::cdiv(cd{0.0, 0.5 * k}, sigma));
+    const int hx = G.nx / 2, hy = G.ny / 2;
+    const double d0x = (q.i0 - hx) * G.px - bm.rho[0], d0y = (q.j0 - hy) * G.py - bm.rho[1];
+    const cd z0 = (u0 * gbd::mk(d0x) + u1 * gbd::mk(d0y) - gbd::mk(bm.edge_distance)) * root;
+    const cd zu = G.px * (u0 * root), zv = G.py * (u1 * root);
+    const cd zz[6] = {z0 * z0, 2.0 * (z0 * zu), 2.0 * (z0 * zv), zu * zu, 2.0 * (zu * zv),
+                      zv * zv};
+    const double log2e = 1.4426950408889634, inv_two_pi = 0.15915494309189533577;
+    o[0] = make_double2(q.i0, q.j0);
+    for (int m = 0; m < 6; ++m) {
+        o[1 + m] = make_double2(q.a[m], q.p[m]);
+        double pa = q.a[m] - zz[m].re * log2e, pp = q.p[m] - zz[m].im * inv_two_pi;
+        if (m == 0) {
+            pa -= 1.0;  // the factor 1/2
+            pp -= rint(pp);
+        }
+        o[10 + m] = make_double2(pa, pp);
+    }
+    o[7] = make_double2(z0.re, z0.im);
+    o[8] = make_double2(zu.re, zu.im);
+    o[9] = make_double2(zv.re, zv.im);
+}
+
 }  // namespace
+
+cudaError_t gbd_launch_trace_truncated(const gbd_trace_params& p, int ext, double inner,
+                                       double outer, long long n_interior, gbd_beamlet* out,
+                                       cudaStream_t s) {
+    const int W = p.n_across + 2 * ext;
+    trace_truncated_kernel<<<dim3(W, 2), 128, 0, s>>>(p, ext, inner, outer, n_interior, out);
+    return cudaGetLastError();
+}
+
+cudaError_t gbd_launch_project_edge(const gbd_beamlet* b, int n, const gbd_project_params& p,
+                                    double2* out, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    project_edge_kernel<<<(n + 127) / 128, 128, 0, s>>>(b, n, p, out);
+    return cudaGetLastError();
+}
 
 cudaError_t gbd_launch_trace_project(const gbd_trace_params& p, const gbd_mirror_params* m,
                                      int n_instances, const gbd_instance_dev* d_inst,

@@ -90,6 +90,17 @@ _SIGS = {
                                       ctypes.POINTER(gbd_detector), ctypes.c_int32,
                                       ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_size_t, _P,
                                       _P]),
+    "gbd_truncated_count": (ctypes.c_int32, [ctypes.POINTER(gbd_pupil), ctypes.c_double,
+                                             ctypes.c_double, ctypes.POINTER(ctypes.c_int32)]),
+    "gbd_trace_truncated": (ctypes.c_int, [ctypes.POINTER(gbd_system), ctypes.POINTER(gbd_pupil),
+                                           ctypes.c_double, ctypes.c_double, ctypes.c_double, _P,
+                                           ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), _P]),
+    "gbd_field_truncated_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_int32,
+                                                              ctypes.POINTER(gbd_detector),
+                                                              ctypes.c_int32]),
+    "gbd_field_truncated": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                           ctypes.POINTER(gbd_detector), ctypes.c_int32, _P,
+                                           ctypes.c_size_t, _P, _P]),
     "gbd_project_bytes": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_int32]),
     "gbd_project": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_double,
                                    ctypes.POINTER(gbd_detector), ctypes.c_int32, _P, _P, _P]),
@@ -313,6 +324,40 @@ def gbd_field_rows(beamlets, n_beamlets: int, wavelength: float, detector, row_b
                                 ctypes.byref(make_detector(detector)), int(row_begin),
                                 int(row_end), int(precision), _ptr(workspace),
                                 ctypes.c_size_t(ws_bytes), _ptr(field_out), _stream(stream)))
+
+
+def gbd_truncated_count(pupil, overlap_factor: float, margin: float = 3.0) -> Tuple[int, int]:
+    """(beamlets, edge beamlets) of the truncated decomposition; (-1, 0) for bad input."""
+    ne = ctypes.c_int32(0)
+    n = int(lib().gbd_truncated_count(ctypes.byref(make_pupil(pupil)), float(overlap_factor),
+                                      float(margin), ctypes.byref(ne)))
+    return n, int(ne.value)
+
+
+def gbd_trace_truncated(system, pupil, overlap_factor: float, waist_ratio: float, margin: float,
+                        out, stream=None) -> int:
+    """Fills `out` (float64 CUDA tensor [>= n, 36]); returns the edge count."""
+    ne = ctypes.c_int32(0)
+    _check(lib().gbd_trace_truncated(ctypes.byref(make_system(system)), ctypes.byref(make_pupil(pupil)),
+                                     float(overlap_factor), float(waist_ratio), float(margin),
+                                     _ptr(out), int(out.shape[0]), ctypes.byref(ne), _stream(stream)))
+    return int(ne.value)
+
+
+def gbd_field_truncated_workspace_bytes(n_beamlets: int, n_edge: int, detector,
+                                        precision: int) -> int:
+    return int(lib().gbd_field_truncated_workspace_bytes(int(n_beamlets), int(n_edge),
+                                                         ctypes.byref(make_detector(detector)),
+                                                         int(precision)))
+
+
+def gbd_field_truncated(beamlets, n_beamlets: int, n_edge: int, wavelength: float, detector,
+                        precision: int, workspace, field_out, stream=None) -> None:
+    ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check(lib().gbd_field_truncated(_ptr(beamlets), int(n_beamlets), int(n_edge),
+                                     float(wavelength), ctypes.byref(make_detector(detector)),
+                                     int(precision), _ptr(workspace), ctypes.c_size_t(ws_bytes),
+                                     _ptr(field_out), _stream(stream)))
 
 
 def gbd_project_bytes(n_beamlets: int, precision: int) -> int:
@@ -627,6 +672,29 @@ def field_rows(beamlets, wavelength: float, detector, row_begin: int, row_end: i
     return out
 
 
+def trace_truncated(system, pupil, margin: float = 3.0, device="cuda", stream=None):
+    """(beamlet table of the truncated decomposition, edge count): whole beamlets first."""
+    import torch
+    n, _ = gbd_truncated_count(pupil, pupil.overlap_factor, margin)
+    out = torch.empty((max(n, 1), BEAMLET_DOUBLES), dtype=torch.float64, device=device)
+    ne = gbd_trace_truncated(system, pupil, pupil.overlap_factor, pupil.waist_ratio, margin, out,
+                             stream)
+    return out[:n], ne
+
+
+def field_truncated(beamlets, n_edge: int, wavelength: float, detector,
+                    precision: int = GBD_PREC_MIXED, stream=None):
+    """Field [ny, nx] of a truncated decomposition (untilted detector) as a CUDA tensor."""
+    import torch
+    n = int(beamlets.shape[0])
+    dtype = torch.complex64 if precision == GBD_PREC_MIXED else torch.complex128
+    out = torch.empty((detector.ny, detector.nx), dtype=dtype, device=beamlets.device)
+    nbytes = gbd_field_truncated_workspace_bytes(n, n_edge, detector, precision)
+    ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=beamlets.device)
+    gbd_field_truncated(beamlets, n, n_edge, wavelength, detector, precision, ws, out, stream)
+    return out
+
+
 def psf(system, pupil, detector, precision: int = GBD_PREC_MIXED, stream=None):
     """Trace + field in one call; returns the complex field as a CUDA tensor."""
     b = trace(system, pupil, stream=stream)
@@ -639,4 +707,4 @@ def unpack(rec: np.ndarray) -> dict:
     return dict(rho=r[0:2], theta=r[2:4], path=r[4], amp=complex(r[5], r[6]),
                 P=(r[7:15:2] + 1j * r[8:15:2]).reshape(2, 2), A=r[15:19].reshape(2, 2),
                 B=r[19:23].reshape(2, 2), C=r[23:27].reshape(2, 2), D=r[27:31].reshape(2, 2),
-                center=r[31:33], weight=r[33], waist=r[34])
+                center=r[31:33], weight=r[33], waist=r[34], edge_distance=r[35])

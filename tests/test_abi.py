@@ -254,3 +254,17 @@ def test_sweep_plan_layout_on_the_host(lib):
     for shape in ((3, 4, 1), (4, 4, 1), (2, 8, 0), (3, 3, 1)):
         st, p = create(shape)
         assert st == gbd.GBD_EINVAL, shape
+
+
+@pytest.mark.parametrize("N,OF,margin", [(32, 1.5, 3.0), (17, 2.2, 2.0), (4, 1.5, 3.0),
+                                         (64, 1.0, 0.0), (9, 1.2, 1.0)])
+def test_truncated_count_matches_oracle(lib, N, OF, margin):
+    """Host-side count of the truncated decomposition (whole + edge beamlets) against the
+    oracle's enumeration (N = 4 with margin 3: every beamlet is an edge beamlet)."""
+    import oracle
+    pupil = W.Pupil(2.4e-3, N, OF, 1.0)
+    sysm = W.System(1e-6, 0.024, 0.024)
+    recs, dist, ne = oracle.trace_truncated(sysm, pupil, margin=margin)
+    assert gbd.gbd_truncated_count(pupil, OF, margin) == (recs.shape[0], ne)
+    assert gbd.gbd_truncated_count(pupil, OF, -1.0)[0] == -1
+    assert gbd.gbd_truncated_count(pupil, -1.0, 3.0)[0] == -1
