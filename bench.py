@@ -40,17 +40,15 @@ MUFU_EX2_PER_CLK_SM = 32
 MUFU_SINCOS_PER_CLK_SM = 16
 GB300_SMS = 152
 GB300_MAX_MHZ = 2070.0
-# Per-launch DRAM bytes of the multi-row field kernels on airy_large from one ncu capture
-# each (the field_mixed_rows_kernel summary under profiles/), and their issued warp-
-# instructions per 32 evaluations.  The reads are the record tiles; the writes are the
-# split partial fields, which scale with the split count.
+# Per-launch DRAM bytes of the multi-row field kernel on airy_large from one ncu capture
+# (the field_mixed_rows_kernel summary under profiles/), and its issued warp-instructions
+# per 32 evaluations.  The reads are the record tiles; the writes are the summed field:
+# the kernel sums its split partials itself in L2 and drops their lines, so its DRAM
+# traffic does not grow with the split count.
 FIELD_MIXED_NCU = [
-    {"kernel": "field_mixed_rows_kernel<4, 4> (4x4 row quadruples)", "read": 3.974656e6,
-     "write": 128.041472e6, "splits": 90, "rows": 4, "cols": 4, "scheme": 1,
-     "inst_per_32_evals": 6.77},
-    {"kernel": "field_mixed_rows_kernel<3, 8> (3x8 row triples)", "read": 3.715584e6,
-     "write": 69.152512e6, "splits": 62, "rows": 3, "cols": 8, "scheme": 1,
-     "inst_per_32_evals": 7.22},
+    {"kernel": "field_mixed_rows_kernel<4, 4> (4x4 row quadruples)", "read": 3.3344e6,
+     "write": 2.884352e6, "splits": 90, "rows": 4, "cols": 4, "scheme": 1,
+     "inst_per_32_evals": 6.81},
 ]
 ISSUE_PER_CLK_SM = 4  # warp-instructions issued per clock and SM (one per sub-partition)
 
@@ -83,6 +81,8 @@ def parse():
                     help="skip the 1024-instance sweep and the search on the App. B telescope")
     ap.add_argument("--no-sharding", action="store_true",
                     help="skip the pixel-sharded field (row slabs + gather)")
+    ap.add_argument("--no-truncated", action="store_true",
+                    help="skip the truncated-beamlet fields")
     ap.add_argument("--no-surrogate", action="store_true",
                     help="skip the surrogate-guided search versus grid and random search")
     return ap.parse_args()
@@ -207,11 +207,12 @@ def ncu_capture(tuned):
 
 
 def traffic_bytes(tuned):
-    """Per-launch DRAM bytes of the captured kernel, writes scaled to the split count used."""
+    """Per-launch DRAM bytes of the captured kernel (records read, field written; neither
+    depends on the split count)."""
     n = ncu_capture(tuned)
     if n is None:
         return None
-    return n["read"] + n["write"] * tuned[2] / n["splits"]
+    return n["read"] + n["write"]
 
 
 def mufu_mix(rows: int = 1, cols: int = 0, scheme: int = 0, cross: bool = False):
@@ -679,6 +680,60 @@ def run_ours(args, world, rank, local):
                   "value": ntb * twl.detector.nx * twl.detector.ny / (tz_ms * 1e-3),
                   "unit": UNIT, "shape": f"{tr}x{tc}, {ts_} splits, scheme {tsch}"}
 
+    # ---- truncated beamlets (edge beamlets cut by the aperture's tangent half-plane): the
+    # distance to the exact hard-aperture focal field on the small Airy workload, and the
+    # cost of the cut field next to the plain one on both Airy workloads
+    truncated = None
+    if not args.no_truncated:
+        from scipy.special import j1 as bessel_j1
+
+        def timed_ms(fn, reps=5):
+            fn()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            return a.elapsed_time(b) / reps
+
+        truncated = {}
+        for name in ("airy_small", "airy_large"):
+            tw = W.by_name(name)
+            bp = gbd.trace(tw.system, tw.pupil, stream=stream)
+            bc, ne = gbd.trace_truncated(tw.system, tw.pupil, stream=stream)
+            out_p = torch.empty((tw.detector.ny, tw.detector.nx), dtype=torch.complex64, device=dev)
+            out_c = torch.empty_like(out_p)
+            wsp = gbd.workspace(bp.shape[0], tw.detector, MIX)
+            wsc = torch.empty(gbd.gbd_field_truncated_workspace_bytes(bc.shape[0], ne, tw.detector,
+                                                                      MIX),
+                              dtype=torch.uint8, device=dev)
+            t_plain = timed_ms(lambda: gbd.gbd_field(bp, bp.shape[0], tw.system.wavelength,
+                                                     tw.detector, MIX, wsp, out_p, stream))
+            t_cut = timed_ms(lambda: gbd.gbd_field_truncated(bc, bc.shape[0], ne,
+                                                             tw.system.wavelength, tw.detector,
+                                                             MIX, wsc, out_c, stream))
+            gbd.gbd_sync(stream)
+            ent = {"beamlets": int(bc.shape[0]), "edge_beamlets": ne,
+                   "plain_beamlets": int(bp.shape[0]), "plain_ms": t_plain, "truncated_ms": t_cut}
+            if name == "airy_small":
+                det_s = tw.detector
+                lam_s, f_s, R_s = tw.system.wavelength, tw.system.focal_length, tw.pupil.diameter / 2
+                k_s = 2 * math.pi / lam_s
+                xs = (np.arange(det_s.nx) - det_s.nx // 2) * det_s.pitch_x
+                Xs, Ys = np.meshgrid(xs, xs)
+                rs = np.hypot(Xs, Ys)
+                us = k_s * R_s * rs / f_s
+                safe = np.where(us == 0, 1.0, us)
+                exact = ((1j / (lam_s * f_s)) * np.exp(-1j * k_s * rs * rs / (2 * f_s)) * math.pi
+                         * R_s * R_s * np.where(us == 0, 1.0, 2 * bessel_j1(safe) / safe))
+                for key, o in (("plain_vs_hard_aperture_rel_l2", out_p),
+                               ("truncated_vs_hard_aperture_rel_l2", out_c)):
+                    e = o.cpu().numpy().astype(np.complex128)
+                    ent[key] = float(np.linalg.norm(e - exact) / np.linalg.norm(exact))
+            truncated[name] = ent
+
     # ---- surrogate-guided search versus the reference grid and random search
     surrogate = None
     if not args.no_surrogate:
@@ -754,7 +809,7 @@ def run_ours(args, world, rank, local):
         "traffic": traffic_bytes(tuned),
         "traffic_source": (("ncu dram__bytes_read.sum + dram__bytes_write.sum of one capture of "
                             f"{ncu_capture(tuned)['kernel']} at {ncu_capture(tuned)['splits']} "
-                            "splits; writes scaled to this launch's split count")
+                            "splits (the kernel sums its split partials in L2)")
                            if ncu_capture(tuned) else "no ncu capture of this launch shape"),
         "peak_source": (f"derived: {GB300_SMS} SMs x {GB300_MAX_MHZ:g} MHz / ({n_ex2:.4g}/"
                         f"{MUFU_EX2_PER_CLK_SM} + {2 * n_sc:.4g}/{MUFU_SINCOS_PER_CLK_SM}) clk "
@@ -831,7 +886,7 @@ def run_ours(args, world, rank, local):
                             "fixed_by_flag": bool(args.shape)},
         "sweep": sweep, "sweep_telescope": sweep_tel, "surrogate": surrogate,
         "point_evaluation": point, "telescope": telescope, "tilted": tilted,
-        "pixel_sharding": sharding,
+        "pixel_sharding": sharding, "truncated": truncated,
         "error": error, "roofline": roofline, "cpu_baseline": cpu,
         "gpu_launches": launches_per_step * args.steps,
         "kernel_ms": {k: (v[0] / max(v[1], 1)) for k, v in kt.items()},
@@ -878,6 +933,11 @@ def summary(line: dict) -> dict:
             g("surrogate", "telescope", "within_0.1pct", "random_mean_capped_at_1260")],
         "mlp_step_us": g("surrogate", "mlp_train_step_us_batch1024"),
         "sharding_8_slab_efficiency_bound": g("pixel_sharding", "slabs_8_efficiency_bound"),
+        "truncated_small_err_plain_vs_cut": [
+            g("truncated", "airy_small", "plain_vs_hard_aperture_rel_l2", digits=3),
+            g("truncated", "airy_small", "truncated_vs_hard_aperture_rel_l2", digits=3)],
+        "truncated_large_ms_plain_vs_cut": [g("truncated", "airy_large", "plain_ms"),
+                                            g("truncated", "airy_large", "truncated_ms")],
         "gpu_launches": line.get("gpu_launches"),
     }
 

@@ -202,18 +202,118 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
 }
 
+// Split partials of pixel p summed in split order with Neumaier's compensation in FP32 (the
+// partials were written by other CTAs: read through L2).
+__device__ __forceinline__ void neumaier_add(float& sum, float& comp, float x) {
+    const float t = __fadd_rn(sum, x);
+    comp = __fadd_rn(comp, fabsf(sum) >= fabsf(x) ? __fadd_rn(__fsub_rn(sum, t), x)
+                                                   : __fadd_rn(__fsub_rn(x, t), sum));
+    sum = t;
+}
+
+}  // namespace
+
+namespace gbd {
+__device__ __forceinline__ float2 sum_partials(const float2* __restrict__ partial, size_t npix,
+                                               size_t p, int splits) {
+    float sr = 0.f, si = 0.f, cr = 0.f, ci = 0.f;
+    int s = 0;
+    for (; s + 8 <= splits; s += 8) {
+        float2 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = __ldcg(partial + (size_t)(s + u) * npix + p);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            neumaier_add(sr, cr, v[u].x);
+            neumaier_add(si, ci, v[u].y);
+        }
+    }
+    for (; s < splits; ++s) {
+        const float2 v = __ldcg(partial + (size_t)s * npix + p);
+        neumaier_add(sr, cr, v.x);
+        neumaier_add(si, ci, v.y);
+    }
+    return make_float2(__fadd_rn(sr, cr), __fadd_rn(si, ci));
+}
+
+// The same sum for NP pixels at once (NP x 8 loads in flight instead of 8: the sum of a
+// whole pixel block by one CTA is latency-bound otherwise); each pixel's additions are in
+// the same order as sum_partials', so the results are the same bits.
+template <int NP>
+__device__ __forceinline__ void sum_partials_n(const float2* __restrict__ partial, size_t npix,
+                                               const size_t (&p)[NP], int splits,
+                                               float2 (&res)[NP]) {
+    float sr[NP], si[NP], cr[NP], ci[NP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) sr[q] = si[q] = cr[q] = ci[q] = 0.f;
+    int s = 0;
+    for (; s + 8 <= splits; s += 8) {
+        float2 v[NP][8];
+#pragma unroll
+        for (int q = 0; q < NP; ++q)
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[q][u] = __ldcg(partial + (size_t)(s + u) * npix + p[q]);
+#pragma unroll
+        for (int q = 0; q < NP; ++q)
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                neumaier_add(sr[q], cr[q], v[q][u].x);
+                neumaier_add(si[q], ci[q], v[q][u].y);
+            }
+    }
+    for (; s < splits; ++s)
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            const float2 v = __ldcg(partial + (size_t)s * npix + p[q]);
+            neumaier_add(sr[q], cr[q], v.x);
+            neumaier_add(si[q], ci[q], v.y);
+        }
+#pragma unroll
+    for (int q = 0; q < NP; ++q) res[q] = make_float2(__fadd_rn(sr[q], cr[q]), __fadd_rn(si[q], ci[q]));
+}
+
+// Slab pixel (row, col) of the summed field into the output window, carrier applied (its
+// phase in turns reduced in FP64, the rotation in FP32).
+__device__ __forceinline__ void reduce_store(const ReduceOut& ro, int nx, int row, int col,
+                                             float2 v) {
+    const int orow = row - ro.skip;
+    if (orow < 0 || orow >= ro.out_rows) return;
+    float re = v.x, im = v.y;
+    if (ro.cx != 0.0 || ro.cy != 0.0) {
+        const int j = row + ro.row0;
+        const double turns = ro.cx * (col - nx / 2) + ro.cy * (j - ro.ny / 2);
+        float sn, cs;
+        sincospif(2.0f * (float)(turns - rint(turns)), &sn, &cs);
+        const float r2 = re * cs - im * sn;
+        im = re * sn + im * cs;
+        re = r2;
+    }
+    static_cast<float2*>(ro.out)[(size_t)orow * nx + col] = make_float2(re, im);
+}
+}  // namespace gbd
+
+namespace {
+
 // Row triples or quadruples on RB x CB pixels per thread (rows 8 apart, columns 32
 // apart) for fields without a uv term (mixed_tile_rows).  The sums stay in FP32 registers
 // over the whole split, so the launch requires short splits (at most kRowsMaxTiles tiles
 // = 1,024 beamlets); the reduction sums the splits with compensation.  Dynamic shared
 // memory: the kStages record stages, then each warp's row terms of the current tile.
+//
+// The grid runs the splits of a pixel block next to each other (blockIdx.x = split, y and z
+// = the pixel block), so a block's split partials are written close together in time and
+// stay in L2.  Each CTA writes its partial, then bumps the block's counter; the CTA that
+// completes the block sums the block's partials in split order with Neumaier's compensation
+// (the reduction kernel's arithmetic, so the bits are the same), applies the tilted plane's
+// carrier and writes the field rows of the output window.  No CTA waits for another.
 constexpr int kRowsMaxTiles = 16;
 template <int RB, int CB>
 __global__ void __launch_bounds__(kThreads, 2)
     field_mixed_rows_kernel(const float4* __restrict__ coef, int n_tiles, int tiles_per_split,
                             int nx, int ny, float2* __restrict__ partial,
                             const unsigned* __restrict__ flags, unsigned mask, unsigned want,
-                            uint32_t spins) {
+                            uint32_t spins, unsigned* __restrict__ done,
+                            gbd::ReduceOut ro) {
     const unsigned fw = *flags;
     if ((fw & mask) != want) return;
     constexpr int kTileF4 = gbd::kMixedFields * gbd::kTile;
@@ -224,15 +324,16 @@ __global__ void __launch_bounds__(kThreads, 2)
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     float4* ent = dyn4 + kStages * kTileF4 + warp * (gbd::kRowsF4 * gbd::kTile);
-    const int t0 = blockIdx.z * tiles_per_split;
+    const int split = blockIdx.x, bx = blockIdx.y, by = blockIdx.z;
+    const int t0 = split * tiles_per_split;
     gbd::init_stream_barriers(full, empty, tid);
     gbd::TileStream<float4, kTileF4> ts{stage, full, empty, coef + (size_t)t0 * kTileF4,
-                                        min(n_tiles - t0, tiles_per_split), 0,
+                                        max(0, min(n_tiles - t0, tiles_per_split)), 0,
                                         gbd::kMixedTileBytes, 0};
     bool ok = ts.start(tid, spins, &flag);
 
-    const int col0 = blockIdx.x * (32 * CB) + lane;
-    const int row0 = blockIdx.y * (8 * RB) + warp;
+    const int col0 = bx * (32 * CB) + lane;
+    const int row0 = by * (8 * RB) + warp;
     float colf[CB];
 #pragma unroll
     for (int c = 0; c < CB; ++c) colf[c] = (float)(col0 + 32 * c);
@@ -261,12 +362,12 @@ __global__ void __launch_bounds__(kThreads, 2)
         }
     }
     if (!ok) {
+        // the partial is still written (garbage) and counted, so the block completes
         record_timeout();
         if (tid == 0) ts.drain(k, spins);
-        return;
     }
     const size_t npix = (size_t)nx * ny;
-    float2* out = partial + (size_t)blockIdx.z * npix;
+    float2* out = partial + (size_t)split * npix;
 #pragma unroll
     for (int r = 0; r < RB; ++r) {
         const int row = row0 + 8 * r;
@@ -278,7 +379,59 @@ __global__ void __launch_bounds__(kThreads, 2)
             out[(size_t)row * nx + col] = acc[r][c];
         }
     }
+    // the last CTA of this pixel block to finish sums the block's partials
+    __shared__ int last;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+        const unsigned blk = (unsigned)(by * gridDim.y + bx);
+        last = atomicAdd(&done[blk], 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int splits = gridDim.x;
+    // the thread's pixels 2 at a time, 16 loads in flight (off-detector ones read pixel 0
+    // and are not stored; 4 at a time would cost the 4 x 4 shape its third CTA per SM)
+    constexpr int kNP = 2;
+    static_assert((RB * CB) % kNP == 0, "pixel groups");
+#pragma unroll 1
+    for (int m0 = 0; m0 < RB * CB; m0 += kNP) {
+        size_t pq[kNP];
+        float2 v[kNP];
+#pragma unroll
+        for (int q = 0; q < kNP; ++q) {
+            const int row = row0 + 8 * ((m0 + q) / CB), col = col0 + 32 * ((m0 + q) % CB);
+            pq[q] = row < ny && col < nx ? (size_t)row * nx + col : 0;
+        }
+        gbd::sum_partials_n<kNP>(partial, npix, pq, splits, v);
+#pragma unroll
+        for (int q = 0; q < kNP; ++q) {
+            const int row = row0 + 8 * ((m0 + q) / CB), col = col0 + 32 * ((m0 + q) % CB);
+            if (row < ny && col < nx) gbd::reduce_store(ro, nx, row, col, v[q]);
+        }
+    }
+    // The block's partials are consumed: drop their L2 lines instead of letting them be
+    // written back to HBM.  Only when every 128-byte line of the block's rows belongs to
+    // this block (rows of a multiple of 16 pixels; the block spans 32 CB pixels = 2 CB lines).
+    if ((nx & 15) == 0) {
+        __syncthreads();  // every thread has read its pixels' partials
+        const int rows_here = min(8 * RB, ny - by * (8 * RB));
+        const int lines_per_row = (min(32 * CB, nx - bx * (32 * CB)) * 8 + 127) / 128;
+        const int per_split = rows_here * lines_per_row;
+        const long long total = (long long)splits * per_split;
+        for (long long q = tid; q < total; q += kThreads) {
+            const int s = (int)(q / per_split), rem = (int)(q % per_split);
+            const int row = by * (8 * RB) + rem / lines_per_row, line = rem % lines_per_row;
+            const float2* a = partial + (size_t)s * npix + (size_t)row * nx + bx * (32 * CB);
+            gbd::discard_l2_line(reinterpret_cast<const char*>(a) + 128 * line);
+        }
+    }
 }
+
+// The flag bits that hand a field from the multi-row kernels to the row pairs.
+constexpr unsigned kRowsNarrow = gbd::kFlagWide | gbd::kFlagSteep | gbd::kFlagColSteep |
+                                 gbd::kFlagCross | gbd::kFlagSteepRows;
 
 constexpr size_t rows_smem_bytes() {
     return (size_t)kStages * gbd::kMixedTileBytes +
@@ -549,57 +702,26 @@ __global__ void __launch_bounds__(256) field_reduce_kernel(const P* __restrict__
 // The mixed path's reduction: GB300's FP64 pipe is too slow for an FP64 add per split and
 // pixel (it made this kernel FP64-bound at ~1 TB/s), so the float2 partials are summed in
 // FP32 with Neumaier's compensation, in split order; the carrier's phase in turns is
-// reduced in FP64 (one multiply-add and a rounding) and rotated in FP32.
+// reduced in FP64 (one multiply-add and a rounding) and rotated in FP32.  When the flag
+// word shows that the multi-row kernel took the field (rows_mask: its hand-over bits all
+// clear), that kernel has already summed and stored every pixel and this one returns.
 __global__ void __launch_bounds__(256) field_reduce_mixed_kernel(const float2* __restrict__ partial,
-                                                                 int splits, int nx, int ny,
-                                                                 int rows, int row0, int skip,
-                                                                 int out_rows, double cx,
-                                                                 double cy,
-                                                                 float2* __restrict__ out) {
-    const size_t npix = (size_t)nx * rows;
+                                                                 int splits,
+                                                                 const unsigned* __restrict__ flags,
+                                                                 unsigned rows_mask, int nx,
+                                                                 int rows, gbd::ReduceOut ro) {
+    if (rows_mask != 0u && flags && (*flags & rows_mask) == 0u) return;
     const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= (size_t)nx * out_rows) return;
-    const size_t p = q + (size_t)skip * nx;
-    float sr = 0.f, si = 0.f, cr = 0.f, ci = 0.f;
-    auto add = [](float& sum, float& comp, float x) {
-        const float t = __fadd_rn(sum, x);
-        comp = __fadd_rn(comp, fabsf(sum) >= fabsf(x) ? __fadd_rn(__fsub_rn(sum, t), x)
-                                                       : __fadd_rn(__fsub_rn(x, t), sum));
-        sum = t;
-    };
-    int s = 0;
-    for (; s + 8 <= splits; s += 8) {
-        float2 v[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = __ldg(partial + (size_t)(s + u) * npix + p);
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            add(sr, cr, v[u].x);
-            add(si, ci, v[u].y);
-        }
-    }
-    for (; s < splits; ++s) {
-        const float2 v = __ldg(partial + (size_t)s * npix + p);
-        add(sr, cr, v.x);
-        add(si, ci, v.y);
-    }
-    float re = __fadd_rn(sr, cr), im = __fadd_rn(si, ci);
-    if (cx != 0.0 || cy != 0.0) {
-        const int i = (int)(p % nx), j = (int)(p / nx) + row0;
-        const double turns = cx * (i - nx / 2) + cy * (j - ny / 2);
-        float sn, cs;
-        sincospif(2.0f * (float)(turns - rint(turns)), &sn, &cs);
-        const float r2 = re * cs - im * sn;
-        im = re * sn + im * cs;
-        re = r2;
-    }
-    out[q] = make_float2(re, im);
+    if (q >= (size_t)nx * ro.out_rows) return;
+    const size_t p = q + (size_t)ro.skip * nx;
+    gbd::reduce_store(ro, nx, (int)(p / nx), (int)(p % nx),
+                      gbd::sum_partials(partial, (size_t)nx * rows, p, splits));
 }
 
 template <int RB, int CB>
 cudaError_t launch_mixed(const void* coeffs, int n_tiles, const gbd_project_params& p,
                          const gbd_field_launch& L, void* partial_v, const unsigned* flags,
-                         uint32_t spins, cudaStream_t s) {
+                         uint32_t spins, const gbd::ReduceOut&, cudaStream_t s) {
     using gbd::kFlagWide;
     float2* partial = static_cast<float2*>(partial_v);
     dim3 grid((p.nx + 32 * CB - 1) / (32 * CB), (p.ny + 8 * RB - 1) / (8 * RB), L.splits);
@@ -617,7 +739,7 @@ cudaError_t launch_mixed(const void* coeffs, int n_tiles, const gbd_project_para
 template <int CB>
 cudaError_t launch_mixed_pair(const void* coeffs, int n_tiles, const gbd_project_params& p,
                               const gbd_field_launch& L, void* partial_v, const unsigned* flags,
-                              uint32_t spins, cudaStream_t s) {
+                              uint32_t spins, const gbd::ReduceOut&, cudaStream_t s) {
     float2* partial = static_cast<float2*>(partial_v);
     using gbd::kFlagColSteep;
     using gbd::kFlagSteep;
@@ -641,7 +763,7 @@ cudaError_t launch_mixed_pair(const void* coeffs, int n_tiles, const gbd_project
 template <int RB, int CB>
 cudaError_t launch_f64(const void* coeffs, int n_tiles, const gbd_project_params& p,
                        const gbd_field_launch& L, void* partial_v, const unsigned* /*wide*/,
-                       uint32_t spins, cudaStream_t s) {
+                       uint32_t spins, const gbd::ReduceOut&, cudaStream_t s) {
     double2* partial = static_cast<double2*>(partial_v);
     const size_t smem = (size_t)kStages * gbd::kF64TileBytes;
     cudaError_t e = cudaFuncSetAttribute(field_f64_kernel<RB, CB>,
@@ -657,7 +779,7 @@ cudaError_t launch_f64(const void* coeffs, int n_tiles, const gbd_project_params
 template <int RB, int CB>
 cudaError_t launch_f64_row(const void* coeffs, int n_tiles, const gbd_project_params& p,
                            const gbd_field_launch& L, void* partial_v, const unsigned* /*wide*/,
-                           uint32_t spins, cudaStream_t s) {
+                           uint32_t spins, const gbd::ReduceOut&, cudaStream_t s) {
     double2* partial = static_cast<double2*>(partial_v);
     const size_t smem = (size_t)kStages * gbd::kF64TileBytes;
     cudaError_t e = cudaFuncSetAttribute(field_f64_row_kernel<RB, CB>,
@@ -718,7 +840,7 @@ cudaError_t launch_pair_set(const void* coeffs, int n_tiles, const gbd_project_p
 template <int CB>
 cudaError_t launch_mixed_pair_smem(const void* coeffs, int n_tiles, const gbd_project_params& p,
                                    const gbd_field_launch& L, void* partial, const unsigned* flags,
-                                   uint32_t spins, cudaStream_t s) {
+                                   uint32_t spins, const gbd::ReduceOut&, cudaStream_t s) {
     return launch_pair_set<CB>(coeffs, n_tiles, p, L, partial, flags, spins, s, false);
 }
 
@@ -728,7 +850,7 @@ cudaError_t launch_mixed_pair_smem(const void* coeffs, int n_tiles, const gbd_pr
 template <int RB, int CB>
 cudaError_t launch_mixed_rows(const void* coeffs, int n_tiles, const gbd_project_params& p,
                               const gbd_field_launch& L, void* partial, const unsigned* flags,
-                              uint32_t spins, cudaStream_t s) {
+                              uint32_t spins, const gbd::ReduceOut& ro, cudaStream_t s) {
     // the row pairs behind: 8 columns per thread (the faster pairs) on detectors at least
     // 256 pixels wide, else the multi-row shape's own column count
     auto pairs = [&](bool after) {
@@ -741,18 +863,17 @@ cudaError_t launch_mixed_rows(const void* coeffs, int n_tiles, const gbd_project
     cudaError_t e = cudaFuncSetAttribute(field_mixed_rows_kernel<RB, CB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    constexpr unsigned kNarrow = gbd::kFlagWide | gbd::kFlagSteep | gbd::kFlagColSteep |
-                                 gbd::kFlagCross | gbd::kFlagSteepRows;
-    dim3 grid((p.nx + 32 * CB - 1) / (32 * CB), (p.ny + 8 * RB - 1) / (8 * RB), L.splits);
+    // splits fastest: a pixel block's splits run together
+    dim3 grid(L.splits, (p.nx + 32 * CB - 1) / (32 * CB), (p.ny + 8 * RB - 1) / (8 * RB));
     field_mixed_rows_kernel<RB, CB><<<grid, kThreads, smem, s>>>(
         static_cast<const float4*>(coeffs), n_tiles, L.tiles_per_split, p.nx, p.ny,
-        static_cast<float2*>(partial), flags, kNarrow, 0u, spins);
+        static_cast<float2*>(partial), flags, kRowsNarrow, 0u, spins, ro.done, ro);
     return pairs(true);
 }
 
 typedef cudaError_t (*launch_fn)(const void*, int, const gbd_project_params&,
                                  const gbd_field_launch&, void*, const unsigned*, uint32_t,
-                                 cudaStream_t);
+                                 const gbd::ReduceOut&, cudaStream_t);
 
 struct ShapeEntry {
     int rb, cb, scheme;
@@ -770,11 +891,14 @@ const ShapeEntry kMixedShapes[] = {
     {2, 4, GBD_SCHEME_ROW_PAIR, launch_mixed_pair<4>, (const void*)field_mixed_kernel<2, 4, false, true>},
     {2, 8, GBD_SCHEME_ROW_PAIR, launch_mixed_pair_smem<8>,
      (const void*)field_mixed_pair_smem_kernel<8, false, false>, pair_smem_bytes<8>()},
-    {3, 8, GBD_SCHEME_ROW_PAIR, launch_mixed_rows<3, 8>, (const void*)field_mixed_rows_kernel<3, 8>,
+    {3, 8, GBD_SCHEME_ROW_PAIR, launch_mixed_rows<3, 8>,
+     (const void*)field_mixed_rows_kernel<3, 8>,
      rows_smem_bytes()},
-    {4, 8, GBD_SCHEME_ROW_PAIR, launch_mixed_rows<4, 8>, (const void*)field_mixed_rows_kernel<4, 8>,
+    {4, 8, GBD_SCHEME_ROW_PAIR, launch_mixed_rows<4, 8>,
+     (const void*)field_mixed_rows_kernel<4, 8>,
      rows_smem_bytes()},
-    {4, 4, GBD_SCHEME_ROW_PAIR, launch_mixed_rows<4, 4>, (const void*)field_mixed_rows_kernel<4, 4>,
+    {4, 4, GBD_SCHEME_ROW_PAIR, launch_mixed_rows<4, 4>,
+     (const void*)field_mixed_rows_kernel<4, 4>,
      rows_smem_bytes()},
 };
 // (1,2), (2,2): every pixel evaluated directly (columns 32 apart); (1,8), (1,16), (2,8),
@@ -822,14 +946,14 @@ int gbd_field_occupancy(int precision, int rb, int cb, int scheme) {
 cudaError_t gbd_launch_field_kernel(int precision, const void* coeffs, int n_tiles,
                                     const gbd_project_params& p, const gbd_field_launch& L,
                                     void* partial, const unsigned* wide, uint32_t wait_spins,
-                                    cudaStream_t s) {
+                                    const gbd::ReduceOut& ro, cudaStream_t s) {
     const ShapeEntry* e = find_shape(precision, L.rows_per_thread, L.cols_per_thread, L.scheme);
     if (!e) return cudaErrorInvalidValue;
     // the kernels see the slab as a detector of p.rows rows (the records' centre rows are
     // relative to its first row); the partial fields are p.rows x nx
     gbd_project_params slab = p;
     slab.ny = p.rows;
-    return e->fn(coeffs, n_tiles, slab, L, partial, wide, wait_spins, s);
+    return e->fn(coeffs, n_tiles, slab, L, partial, wide, wait_spins, ro, s);
 }
 
 int gbd_field_row_block(int precision, const gbd_field_launch& L) {
@@ -841,23 +965,41 @@ int gbd_field_row_block(int precision, const gbd_field_launch& L) {
     return rb == 3 ? 48 : 32;
 }
 
-cudaError_t gbd_launch_field_reduce(int precision, const gbd_project_params& p, int splits,
-                                    const void* partial, void* out, int out_row0, int out_rows,
+gbd::ReduceOut gbd_reduce_out(const gbd_project_params& p, void* out, unsigned* done,
+                              int out_row0, int out_rows) {
+    gbd::ReduceOut ro;
+    ro.out = out;
+    ro.done = done;
+    ro.ny = p.ny;
+    ro.row0 = p.row0;
+    ro.skip = out_row0 - p.row0;
+    ro.out_rows = out_rows;
+    ro.cx = -p.n[0] * p.px / p.wavelength;
+    ro.cy = -p.n[1] * p.py / p.wavelength;
+    return ro;
+}
+
+cudaError_t gbd_launch_field_reduce(int precision, const gbd_project_params& p,
+                                    const gbd_field_launch& L, const unsigned* flags,
+                                    const void* partial, const gbd::ReduceOut& ro,
                                     cudaStream_t s) {
-    // partial fields: rows p.row0 .. p.row0 + p.rows - 1; output: rows out_row0 .. + out_rows
-    const int skip = out_row0 - p.row0;
-    const size_t nout = (size_t)p.nx * out_rows;
+    // partial fields: rows p.row0 .. p.row0 + p.rows - 1; output: the window of ro
+    const size_t nout = (size_t)p.nx * ro.out_rows;
     if (nout == 0) return cudaSuccess;
-    const double cx = -p.n[0] * p.px / p.wavelength, cy = -p.n[1] * p.py / p.wavelength;
     const unsigned blocks = (unsigned)((nout + 255) / 256);
-    if (precision == GBD_PREC_F64)
+    if (precision == GBD_PREC_F64) {
         field_reduce_kernel<true, double2><<<blocks, 256, 0, s>>>(
-            static_cast<const double2*>(partial), splits, p.nx, p.ny, p.rows, p.row0, skip,
-            out_rows, cx, cy, out);
-    else
-        field_reduce_mixed_kernel<<<blocks, 256, 0, s>>>(static_cast<const float2*>(partial), splits,
-                                                         p.nx, p.ny, p.rows, p.row0, skip, out_rows,
-                                                         cx, cy, static_cast<float2*>(out));
+            static_cast<const double2*>(partial), L.splits, p.nx, p.ny, p.rows, p.row0, ro.skip,
+            ro.out_rows, ro.cx, ro.cy, ro.out);
+    } else {
+        // a multi-row launch whose kernel took the field has stored it already
+        const bool rows = L.scheme == GBD_SCHEME_ROW_PAIR && L.rows_per_thread >= 3 &&
+                          L.tiles_per_split <= kRowsMaxTiles;
+        field_reduce_mixed_kernel<<<blocks, 256, 0, s>>>(static_cast<const float2*>(partial),
+                                                         L.splits, flags,
+                                                         rows ? kRowsNarrow : 0u, p.nx, p.rows,
+                                                         ro);
+    }
     return cudaGetLastError();
 }
 

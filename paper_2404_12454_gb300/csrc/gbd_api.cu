@@ -332,6 +332,12 @@ int slab_row0(int precision, const gbd_field_launch& L, int row_begin) {
     return row_begin - row_begin % h;
 }
 
+// Completion counters of the multi-row kernel's pixel blocks (32 CB x 8 RB pixels; sized
+// for the smallest block, 32 x 8).
+size_t counter_bytes(int nx, int rows) {
+    return align256((size_t)((nx + 31) / 32) * ((rows + 7) / 8) * sizeof(unsigned));
+}
+
 size_t workspace_for(int precision, int n, const gbd_detector* D, const gbd_field_launch& L,
                      int row_begin = 0, int row_end = -1) {
     if (n <= 0) return 0;
@@ -340,7 +346,7 @@ size_t workspace_for(int precision, int n, const gbd_detector* D, const gbd_fiel
     const size_t coeff = align256((size_t)n_tiles_of(n) * tile_bytes(precision));
     const size_t elem = precision == GBD_PREC_MIXED ? sizeof(float2) : sizeof(double2);
     const size_t part = align256((size_t)L.splits * D->nx * rows * elem);
-    return kFlagBytes + coeff + part;
+    return kFlagBytes + counter_bytes(D->nx, rows) + coeff + part;
 }
 
 // The field on detector rows [row_begin, row_end) (the whole detector: 0, ny).  The launch
@@ -366,12 +372,16 @@ gbd_status run_field(const gbd_beamlet* beamlets, int32_t n, double wavelength,
     if (ws_bytes < need)
         return fail(GBD_ENOMEM, "workspace of %zu bytes is smaller than the %zu needed", ws_bytes,
                     need);
+    // [flag word | pixel-block counters | projected records | split partials]
     char* base = static_cast<char*>(ws);
     unsigned* wide = reinterpret_cast<unsigned*>(base);
-    void* coeffs = base + kFlagBytes;
-    void* partial = base + kFlagBytes + align256((size_t)nt * tile_bytes(precision));
-    cudaError_t e = cudaMemsetAsync(wide, 0, sizeof(unsigned), stream);
+    const size_t cnt = counter_bytes(D->nx, pp.rows);
+    unsigned* done = reinterpret_cast<unsigned*>(base + kFlagBytes);
+    void* coeffs = base + kFlagBytes + cnt;
+    void* partial = base + kFlagBytes + cnt + align256((size_t)nt * tile_bytes(precision));
+    cudaError_t e = cudaMemsetAsync(wide, 0, kFlagBytes + cnt, stream);
     if (e != cudaSuccess) return cuda_fail(e, "gbd_field flag reset");
+    const gbd::ReduceOut ro = gbd_reduce_out(pp, out, done, row_begin, row_end - row_begin);
     {
         TimingScope ts(kTimeProject, stream);
         e = gbd_launch_project(beamlets, n, pp, precision, coeffs, wide, stream);
@@ -380,13 +390,12 @@ gbd_status run_field(const gbd_beamlet* beamlets, int32_t n, double wavelength,
     {
         TimingScope ts(precision == GBD_PREC_MIXED ? kTimeMixed : kTimeF64, stream);
         e = gbd_launch_field_kernel(precision, coeffs, nt, pp, L, partial, wide, wait_spins(),
-                                    stream);
+                                    ro, stream);
     }
     if (e != cudaSuccess) return cuda_fail(e, "gbd_field launch");
     {
         TimingScope ts(kTimeReduce, stream);
-        e = gbd_launch_field_reduce(precision, pp, L.splits, partial, out, row_begin,
-                                    row_end - row_begin, stream);
+        e = gbd_launch_field_reduce(precision, pp, L, wide, partial, ro, stream);
     }
     if (e != cudaSuccess) return cuda_fail(e, "gbd_field reduce launch");
     return GBD_OK;
@@ -1004,7 +1013,14 @@ gbd_status gbd_field_point(const gbd_beamlet* beamlets, int32_t n_beamlets, doub
         e = gbd_launch_point(beamlets, n_beamlets, pp, base, sp, tps, partial, wait_spins(), s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "gbd_field_point launch");
-    e = gbd_launch_field_reduce(GBD_PREC_F64, pp, sp, partial, field_out, 0, detector->ny, s);
+    gbd_field_launch PL;
+    PL.rows_per_thread = 1;
+    PL.cols_per_thread = 1;
+    PL.splits = sp;
+    PL.tiles_per_split = tps;
+    PL.scheme = GBD_SCHEME_DIRECT;
+    e = gbd_launch_field_reduce(GBD_PREC_F64, pp, PL, nullptr, partial,
+                                gbd_reduce_out(pp, field_out, nullptr, 0, detector->ny), s);
     return e == cudaSuccess ? GBD_OK : cuda_fail(e, "gbd_field_point reduce");
 }
 

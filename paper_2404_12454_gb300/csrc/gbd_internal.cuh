@@ -81,6 +81,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
+// Drops the 128-byte L2 line at `p` (128-byte aligned) without writing it back: its
+// contents become undefined.  For scratch data that has been consumed.
+__device__ __forceinline__ void discard_l2_line(const void* p) {
+    asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
+}
+
 // Bounded wait on an mbarrier phase: false after `spins` unsuccessful polls.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t spins) {
     for (uint32_t it = 0; it < spins; ++it)
@@ -231,6 +237,19 @@ struct gbd_field_launch {
 };
 
 namespace gbd {
+// Where the summed split partials go: the output window (rows skip .. skip + out_rows - 1 of
+// the evaluated slab, the slab starting at detector row row0 of ny) with the tilted plane's
+// carrier exp(2 pi i (cx (i - nx/2) + cy (j - ny/2))) applied, and the per-pixel-block
+// completion counters of the multi-row kernel (zeroed before each field).
+struct ReduceOut {
+    void* out;
+    unsigned* done;
+    int ny, row0, skip, out_rows;
+    double cx, cy;
+};
+}  // namespace gbd
+
+namespace gbd {
 // Index of the monomial xi^a eta^b in a degree-ordered table: degree g = a + b occupies
 // entries g(g+1)/2 .. g(g+1)/2 + g.  Degree <= 10 needs 66 entries.
 __host__ __device__ __forceinline__ int plate_index(int a, int b) {
@@ -268,15 +287,24 @@ cudaError_t gbd_launch_trace_project(const gbd_trace_params& p, const gbd_mirror
 cudaError_t gbd_launch_project(const gbd_beamlet* b, int n, const gbd_project_params& p,
                                int precision, void* coeffs, unsigned* wide, cudaStream_t s);
 cudaError_t gbd_launch_trace_mirrors(const gbd_mirror_params& m, gbd_beamlet* out, cudaStream_t s);
+// ro: where a kernel that sums the splits itself (the multi-row kernels) stores the field.
 cudaError_t gbd_launch_field_kernel(int precision, const void* coeffs, int n_tiles,
                                     const gbd_project_params& p, const gbd_field_launch& L,
                                     void* partial, const unsigned* wide, uint32_t wait_spins,
-                                    cudaStream_t s);
+                                    const gbd::ReduceOut& ro, cudaStream_t s);
 // partial: float2 per pixel and split for GBD_PREC_MIXED, double2 for GBD_PREC_F64, over
 // the slab p.row0 .. p.row0 + p.rows - 1; writes detector rows out_row0 .. + out_rows - 1
 // (inside the slab) to `out`, row-major from out_row0
-cudaError_t gbd_launch_field_reduce(int precision, const gbd_project_params& p, int splits,
-                                    const void* partial, void* out, int out_row0, int out_rows,
+// Output window of a field: detector rows out_row0 .. out_row0 + out_rows - 1 (inside the
+// evaluated slab p.row0 .. p.row0 + p.rows - 1) into `out`; `done`: the multi-row kernel's
+// per-pixel-block counters (zeroed before the launch; at least ceil(nx/32) ceil(rows/8)).
+gbd::ReduceOut gbd_reduce_out(const gbd_project_params& p, void* out, unsigned* done,
+                              int out_row0, int out_rows);
+// Sums the split partials into the output window, unless the flag word (may be null) shows
+// that the launch's multi-row kernel took the field and stored it itself.
+cudaError_t gbd_launch_field_reduce(int precision, const gbd_project_params& p,
+                                    const gbd_field_launch& L, const unsigned* flags,
+                                    const void* partial, const gbd::ReduceOut& ro,
                                     cudaStream_t s);
 // Truncated decomposition: trace of the extended grid (interior beamlets first), and the
 // edge records of its last n beamlets (see project_edge_kernel).

@@ -76,10 +76,13 @@ const FaddeevaT<T, NW>& faddeeva_table() {
 }
 
 // w(z) for Im z >= 0 (z = zr + i zi): q = 1/(L - iz), Z = (L + iz) q, w = (2 p(Z) q + 1/sqrt(pi)) q.
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+
 template <typename T, int NW>
 __device__ __forceinline__ void faddeeva(T zr, T zi, const FaddeevaT<T, NW>& F, T& wr, T& wi) {
     const T dr = F.L + zi, di = -zr;  // L - iz
-    const T inv = (T)1 / (dr * dr + di * di);
+    const T inv = recip(dr * dr + di * di);
     const T qr = dr * inv, qi = -di * inv;  // 1 / (L - iz)
     const T nr = F.L - zi, ni = zr;         // L + iz
     const T Zr = nr * qr - ni * qi, Zi = nr * qi + ni * qr;
@@ -96,8 +99,11 @@ __device__ __forceinline__ void faddeeva(T zr, T zi, const FaddeevaT<T, NW>& F, 
     wi = sr * qi + si * qr;
 }
 
+// cos and sin of 2 pi p: the turns reduced exactly to [-1/2, 1/2], then (FP32) the MUFU
+// sin/cos of the radians in [-pi, pi] (absolute error ~1e-6, well inside the mixed path's
+// tolerance for these edge terms).
 __device__ __forceinline__ void cis_turns(float p, float& c, float& s) {
-    sincospif(2.0f * (p - rintf(p)), &s, &c);
+    __sincosf(6.28318530717958647692f * (p - rintf(p)), &s, &c);
 }
 __device__ __forceinline__ void cis_turns(double p, double& c, double& s) {
     sincospi(2.0 * (p - rint(p)), &s, &c);
@@ -110,19 +116,28 @@ struct Cplx {
     T x, y;
 };
 
-// The edge beamlets' sum added onto the field, one pixel per thread; edge records staged
-// through shared memory (converted to T) 32 beamlets at a time.
-constexpr int kEdgeChunk = 32;
+// The edge beamlets' sum added onto the field, kEdgePix consecutive pixels (row-major
+// order) per thread; the edge records are staged through shared memory (converted to T) 32
+// beamlets at a time, and each thread loads a record once for its pixels.  Per pixel the
+// Faddeeva argument (i zeta or -i zeta) is selected without a branch; the Gaussian term
+// is evaluated only where Re zeta < 0 (neighbouring pixels mostly agree on the sign).
+constexpr int kEdgeChunk = 32, kEdgePix = 4;
 template <typename T, int NW>
 __global__ void __launch_bounds__(256) field_edge_kernel(const double2* __restrict__ rec,
                                                          int n_edge, int nx, int ny,
                                                          FaddeevaT<T, NW> F,
                                                          Cplx<T>* __restrict__ out) {
-    __shared__ T s[kEdgeChunk][2 * gbd::kEdgeFields];
-    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool live = p < (long long)nx * ny;
-    const T pi_ = (T)(live ? p % nx : 0), pj = (T)(live ? p / nx : 0);
-    T accr = 0, acci = 0;
+    __shared__ __align__(16) T s[kEdgeChunk][2 * gbd::kEdgeFields];
+    const long long npix = (long long)nx * ny;
+    const long long p0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * kEdgePix;
+    T pu[kEdgePix], pv[kEdgePix], accr[kEdgePix], acci[kEdgePix];
+#pragma unroll
+    for (int c = 0; c < kEdgePix; ++c) {
+        const long long p = min(p0 + c, npix - 1);
+        pu[c] = (T)(p % nx);
+        pv[c] = (T)(p / nx);
+        accr[c] = acci[c] = (T)0;
+    }
     for (int b0 = 0; b0 < n_edge; b0 += kEdgeChunk) {
         __syncthreads();
         for (int q = threadIdx.x; q < kEdgeChunk * gbd::kEdgeFields; q += blockDim.x) {
@@ -135,43 +150,49 @@ __global__ void __launch_bounds__(256) field_edge_kernel(const double2* __restri
         __syncthreads();
         const int nb = min(kEdgeChunk, n_edge - b0);
         for (int b = 0; b < nb; ++b) {
-            const T* r = s[b];
-            const T tu = pi_ - r[0], tv = pj - r[1];
-            const T tuu = tu * tu, tuv = tu * tv, tvv = tv * tv;
-            // zeta
-            const T zr = r[14] + r[16] * tu + r[18] * tv;
-            const T zi = r[15] + r[17] * tu + r[19] * tv;
-            const bool neg = zr < (T)0;
-            T wr, wi;
-            if (neg)
-                faddeeva<T, NW>(zi, -zr, F, wr, wi);  // -i zeta
-            else
-                faddeeva<T, NW>(-zi, zr, F, wr, wi);  // i zeta
-            // e^Psi
-            const T ga = r[20] + r[22] * tu + r[24] * tv + r[26] * tuu + r[28] * tuv + r[30] * tvv;
-            const T gp = r[21] + r[23] * tu + r[25] * tv + r[27] * tuu + r[29] * tuv + r[31] * tvv;
-            T c, sn;
-            cis_turns(gp, c, sn);
-            const T gm = pow2(ga);
-            T tr = gm * (c * wr - sn * wi), ti = gm * (c * wi + sn * wr);
-            if (neg) {
-                const T ea = r[2] + r[4] * tu + r[6] * tv + r[8] * tuu + r[10] * tuv + r[12] * tvv;
-                const T ep = r[3] + r[5] * tu + r[7] * tv + r[9] * tuu + r[11] * tuv + r[13] * tvv;
-                T ec, es;
-                cis_turns(ep, ec, es);
-                const T em = pow2(ea);
-                tr = em * ec - tr;
-                ti = em * es - ti;
+            T r[2 * gbd::kEdgeFields];
+#pragma unroll
+            for (int m = 0; m < 2 * gbd::kEdgeFields; ++m) r[m] = s[b][m];
+#pragma unroll
+            for (int c = 0; c < kEdgePix; ++c) {
+                const T tu = pu[c] - r[0], tv = pv[c] - r[1];
+                const T tuu = tu * tu, tuv = tu * tv, tvv = tv * tv;
+                const T zr = r[14] + r[16] * tu + r[18] * tv;
+                const T zi = r[15] + r[17] * tu + r[19] * tv;
+                const bool neg = zr < (T)0;
+                // i zeta = (-zi, zr); -i zeta = (zi, -zr): the one in the upper half-plane
+                T wr, wi;
+                faddeeva<T, NW>(neg ? zi : -zi, neg ? -zr : zr, F, wr, wi);
+                const T ga = r[20] + r[22] * tu + r[24] * tv + r[26] * tuu + r[28] * tuv + r[30] * tvv;
+                const T gp = r[21] + r[23] * tu + r[25] * tv + r[27] * tuu + r[29] * tuv + r[31] * tvv;
+                T gc, gs;
+                cis_turns(gp, gc, gs);
+                const T gm = pow2(ga);
+                T tr = gm * (gc * wr - gs * wi), ti = gm * (gc * wi + gs * wr);
+                if (neg) {
+                    // where Re zeta < 0 the cut field is E - e^Psi w(-i zeta)
+                    const T ea = r[2] + r[4] * tu + r[6] * tv + r[8] * tuu + r[10] * tuv +
+                                 r[12] * tvv;
+                    const T ep = r[3] + r[5] * tu + r[7] * tv + r[9] * tuu + r[11] * tuv +
+                                 r[13] * tvv;
+                    T ec, es;
+                    cis_turns(ep, ec, es);
+                    const T em = pow2(ea);
+                    tr = em * ec - tr;
+                    ti = em * es - ti;
+                }
+                accr[c] += tr;
+                acci[c] += ti;
             }
-            accr += tr;
-            acci += ti;
         }
     }
-    if (live) {
-        Cplx<T> o = out[p];
-        o.x += accr;
-        o.y += acci;
-        out[p] = o;
+#pragma unroll
+    for (int c = 0; c < kEdgePix; ++c) {
+        if (p0 + c >= npix) break;
+        Cplx<T> o = out[p0 + c];
+        o.x += accr[c];
+        o.y += acci[c];
+        out[p0 + c] = o;
     }
 }
 
@@ -181,7 +202,7 @@ cudaError_t gbd_launch_field_edge(int precision, const double2* edge_records, in
                                   int ny, void* out, cudaStream_t s) {
     if (n_edge <= 0) return cudaSuccess;
     const long long npix = (long long)nx * ny;
-    const unsigned blocks = (unsigned)((npix + 255) / 256);
+    const unsigned blocks = (unsigned)((npix + 256LL * kEdgePix - 1) / (256LL * kEdgePix));
     if (precision == GBD_PREC_F64)
         field_edge_kernel<double, 36><<<blocks, 256, 0, s>>>(
             edge_records, n_edge, nx, ny, faddeeva_table<double, 36>(),

@@ -78,11 +78,12 @@ def test_roofline_arithmetic():
     assert (ex2, sc) == pytest.approx((2 / 16 + 3 / 512, 4 / 16 + 2 / 512))
     # fewer MUFU operations per evaluation, a higher ceiling
     assert bench.peak_evals_const(8, rows=3) > bench.peak_evals_const(8) > bench.peak_evals_const()
-    # every recorded ncu capture matches its own shape and scales its writes by splits
+    # every recorded ncu capture matches its own shape; the multi-row kernel sums its split
+    # partials in L2, so its traffic does not depend on the split count
     for cap in bench.FIELD_MIXED_NCU:
         tuned = (cap["rows"], cap["cols"], cap["splits"], 0.0, cap["scheme"])
         assert bench.ncu_capture(tuned) is cap
         assert bench.traffic_bytes(tuned) == pytest.approx(cap["read"] + cap["write"])
         doubled = (cap["rows"], cap["cols"], 2 * cap["splits"], 0.0, cap["scheme"])
-        assert bench.traffic_bytes(doubled) == pytest.approx(cap["read"] + 2 * cap["write"])
+        assert bench.traffic_bytes(doubled) == pytest.approx(cap["read"] + cap["write"])
     assert bench.traffic_bytes((1, 4, 10, 0.0, 0)) is None
