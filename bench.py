@@ -49,6 +49,9 @@ FIELD_MIXED_NCU = [
     {"kernel": "field_mixed_rows_kernel<4, 4> (4x4 row quadruples)", "read": 3.3344e6,
      "write": 2.884352e6, "splits": 90, "rows": 4, "cols": 4, "scheme": 1,
      "inst_per_32_evals": 6.81},
+    {"kernel": "field_mixed_rows_kernel<4, 8> (4x8 row quadruples, packed FP32x2)",
+     "read": 3.353088e6, "write": 4.194816e6, "splits": 90, "rows": 4, "cols": 8, "scheme": 1,
+     "inst_per_32_evals": 4.74},
 ]
 ISSUE_PER_CLK_SM = 4  # warp-instructions issued per clock and SM (one per sub-partition)
 

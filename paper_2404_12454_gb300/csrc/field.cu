@@ -354,7 +354,13 @@ __global__ void __launch_bounds__(kThreads, 2)
         __syncwarp();  // every lane is done with the previous tile's row terms
         gbd::mixed_rows_terms<RB>(ts.tile(k), rowf, ent, lane);
         __syncwarp();
-        gbd::mixed_tile_rows<RB, CB>(ent, colf, acc);
+        // packed FP32x2 arithmetic where it pays: on airy_large the 4 x 8 shape (2 CTAs per
+        // SM) ran 2.85 ms with it against 3.02 without; 4 x 4 (2.92 -> 3.00 ms) and 3 x 8
+        // (2.99 -> 3.30 ms) are faster with scalar instructions
+        if constexpr (RB == 4 && CB == 8)
+            gbd::mixed_tile_rows_x2<RB, CB>(ent, colf, acc);
+        else
+            gbd::mixed_tile_rows<RB, CB>(ent, colf, acc);
         if (!ts.release(k, lane, warp, spins)) {
             ok = false;
             ++k;

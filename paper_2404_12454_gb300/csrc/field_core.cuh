@@ -446,6 +446,55 @@ __device__ __forceinline__ void mixed_tile_rows(const float4* __restrict__ ent,
     }
 }
 
+// mixed_tile_rows with the complex arithmetic in packed FP32x2 instructions (FFMA2, FMUL2,
+// FADD2 on (re, im) pairs): E0 = amp (cos, sin) one FMUL2, the first row one FADD2, each
+// later row two FFMA2 (E0.re (S.re, S.im) and E0.im (-S.im, S.re) onto (re, im)) and the
+// amplitude recurrence one FMUL2 ((amp, rho) *= (rho, sig)): 15 instructions per column
+// of 4 pixels instead of 24.  Every lane rounds as the scalar FMA / FMUL / FADD, in the same
+// order, so the sums are the same bits as mixed_tile_rows' (up to the compiler's choice of
+// contracting the first row's add into an FMA there).  The packed operations all run on
+// the FMA-heavy pipe, which then binds (ncu: math-pipe throttle the largest stall, 61 % of
+// issue slots on the 4 x 8 shape); moving a row back to scalar FFMA did not help (3.04
+// and 2.89 ms for one and two scalar rows against 2.85 ms).
+template <int RB, int CB, int NB = kTile>
+__device__ __forceinline__ void mixed_tile_rows_x2(const float4* __restrict__ ent,
+                                                   const float (&colf)[CB],
+                                                   float2 (&acc)[RB][CB]) {
+    static_assert(RB == 3 || RB == 4, "row triples or quadruples");
+#pragma unroll 1
+    for (int b = 0; b < NB; ++b) {
+        const float4 e0 = ent[b];
+        const float4 e1 = ent[NB + b];
+        const float4 e2 = ent[2 * NB + b];
+        const float4 e3 = ent[3 * NB + b];
+        const float2 S[3] = {make_float2(e2.z, e2.w), make_float2(e3.x, e3.y),
+                             make_float2(e3.z, e3.w)};
+        float2 Sr[3];  // (-S.im, S.re): multiplies E0.im
+#pragma unroll
+        for (int r = 0; r < 3; ++r) Sr[r] = make_float2(-S[r].y, S[r].x);
+        const float tu0 = colf[0] - e0.x;
+        const float t64 = tu0 * 0.015625f;
+        const float x0 = fmaf(tu0, fmaf(e2.y, t64, e1.x), e0.z);
+        const float d1 = fmaf(e2.y, tu0, e1.z);
+        // (amp, rho): the first row's amplitude at the thread's column and its ratio
+        float2 ar = make_float2(mufu_ex2(fmaf(tu0, fmaf(e2.x, t64, e0.w), e0.y)),
+                                mufu_ex2(fmaf(e2.x, tu0, e1.y)));
+        const float sig = e1.w;
+#pragma unroll
+        for (int c = 0; c < CB; ++c) {
+            const float x = c == 0 ? x0 : fmaf((float)(16 * c * c), e2.y, fmaf((float)c, d1, x0));
+            const float2 E0 = __fmul2_rn(make_float2(ar.x, ar.x), make_float2(mufu_cos(x), mufu_sin(x)));
+            acc[0][c] = __fadd2_rn(acc[0][c], E0);
+#pragma unroll
+            for (int r = 1; r < RB; ++r) {
+                acc[r][c] = __ffma2_rn(make_float2(E0.y, E0.y), Sr[r - 1], acc[r][c]);
+                acc[r][c] = __ffma2_rn(make_float2(E0.x, E0.x), S[r - 1], acc[r][c]);
+            }
+            if (c + 1 < CB) ar = __fmul2_rn(ar, make_float2(ar.y, sig));
+        }
+    }
+}
+
 // A compensated (hi, lo) sum rounded once to FP32 (the split partial written to memory).
 __device__ __forceinline__ float2 round_pair(float2 hi, float2 lo) {
     return make_float2((float)((double)hi.x + (double)lo.x), (float)((double)hi.y + (double)lo.y));
