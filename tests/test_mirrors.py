@@ -3,9 +3,12 @@
 The two tracers share nothing: the oracle finds each surface by Newton iteration on the
 sag and reflects about the sag gradient; the library solves the implicit quadric in
 closed form.  Records agree to rounding.  The path L is the difference of two ~16 m
-optical paths, so two correct FP64 traces differ in L by a few ulp of 16 m (~1e-14 m),
-i.e. ~1e-7 rad of phase at 551 nm: the end-to-end FP64 field bound is therefore 1e-6 (the
-evaluation itself is held to 1e-11 by the thin-lens parity tests, same kernels).
+optical paths, so two correct FP64 traces differ in L by a few ulp of 16 m (measured
+1e-14 to 3e-14 m, 4e-16 m on the 1 m paraboloid), ~1e-7 rad of phase at 551 nm; and the
+ABCD blocks are one-sided differences of real rays whose offsets are microns to
+millimetres on ~1 m positions (~1e-10 relative).  Measured end-to-end FP64 field errors:
+3.4e-9 (paraboloid) to 9.0e-8 (the three-mirror relay); the bound is 3e-7.  The
+evaluation kernels themselves are held to 1e-11 by the thin-lens parity tests.
 """
 import numpy as np
 import pytest
@@ -16,7 +19,7 @@ from paper_2404_12454_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-E2E_TOL = {gbd.GBD_PREC_F64: 1e-6, gbd.GBD_PREC_MIXED: 2e-5}
+E2E_TOL = {gbd.GBD_PREC_F64: 3e-7, gbd.GBD_PREC_MIXED: 2e-5}
 PRECS = (gbd.GBD_PREC_F64, gbd.GBD_PREC_MIXED)
 
 
