@@ -573,7 +573,7 @@ gbd_status gbd_sync(void* stream) {
     cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "gbd_sync");
     unsigned st = gbd_field_status_read_clear() | gbd_sweep_status_read_clear() |
-                  gbd_point_status_read_clear();
+                  gbd_point_status_read_clear() | gbd_mlp_status_read_clear();
     if (st & gbd::kStatusTimeout) return fail(GBD_ETIMEOUT, "a device wait gave up (timeout)");
     return GBD_OK;
 }

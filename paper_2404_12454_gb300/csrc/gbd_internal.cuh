@@ -335,6 +335,7 @@ int gbd_sm_count();
 uint32_t gbd_wait_spins();
 unsigned gbd_sweep_status_read_clear();
 unsigned gbd_point_status_read_clear();
+unsigned gbd_mlp_status_read_clear();
 long gbd_point_pixel_ctas(int nx, int ny);
 int gbd_point_occupancy();
 // Point evaluation: packs the beamlets into `coeffs` (FP64 tiles) and launches the

@@ -177,7 +177,8 @@ def test_mlp_rejects_bad_arguments(lib):
 
     B = 64
     need = gbd.gbd_mlp_workspace_bytes(B)
-    assert need >= 3 * 4 * B * 128 * 4 + 2 * B * 4
+    # six transposed operands in two BF16 parts, a_4 and d_1 in FP32, y and dL/dy
+    assert need >= 12 * 128 * B * 2 + 2 * 128 * B * 4 + 2 * B * 4
     assert gbd.gbd_mlp_workspace_bytes(0) == 0
     base = dict(master=T(), weights=T(), m=T(), v=T(), x=T(), target=T(), lr=1e-3, b1=0.9,
                 b2=0.999, eps=1e-8, first=1, steps=3, loss=T(), ws=T(n=need))

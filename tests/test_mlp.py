@@ -1,7 +1,9 @@
 """MLP surrogate kernels (through the C ABI) against the FP64 reference in oracle/mlp.py.
 
-The GPU keeps BF16 weights and FP32 activations; the reference uses the same BF16 weights
-and float64 arithmetic, so forward values agree to FP32 rounding (1e-5 relative) and the
+The GPU keeps BF16 weights and FP32 activations and runs the hidden layers on the tensor
+cores with the FP32 operands split into BF16 parts (three for the forward activations, two
+for the errors and the weight gradients); the reference uses the same BF16 weights and
+float64 arithmetic, so forward values agree to FP32 rounding (1e-5 relative) and the
 gradient, an FP32 sum over the batch, to 1e-4 relative L2.  BF16 rounding decides bits, so
 it is compared bit for bit.
 """
@@ -151,3 +153,45 @@ def test_training_learns_and_is_deterministic():
     assert la == lb
     assert np.array_equal(a.master.cpu().numpy(), b.master.cpu().numpy())
     assert la < 0.05 * first, (first, la)
+
+
+@pytest.mark.parametrize("B", [16, 1024, 3000])
+def test_gradient_is_deterministic(B):
+    """Every sum has a fixed order: two evaluations give the same bits (3000 samples: phase A
+    loops over items, the weight-gradient tiles over 12 staged blocks with a ragged last)."""
+    import torch
+    p, x, t, P, Wb, X, T = _setup(7, B)
+    ws = torch.empty(gbd.gbd_mlp_workspace_bytes(B), dtype=torch.uint8, device="cuda")
+    out = []
+    for _ in range(2):
+        grad = torch.empty(M.N_PARAMS, dtype=torch.float32, device="cuda")
+        loss = torch.empty(1, dtype=torch.float32, device="cuda")
+        gbd.gbd_mlp_grad(Wb, X, T, grad, loss, ws)
+        gbd.gbd_sync()
+        out.append((grad.cpu(), loss.item()))
+    assert torch.equal(out[0][0], out[1][0]) and out[0][1] == out[1][1]
+    L, g = M.loss_grad(p, x, t)
+    assert np.linalg.norm(out[0][0].numpy() - g) <= 1e-4 * np.linalg.norm(g)
+
+
+def test_grid_barrier_timeout_is_reported_and_context_survives():
+    """A wait limit of one poll makes the training kernel's grid barrier give up: the
+    kernel records GBD_ETIMEOUT and returns, and the next call works normally."""
+    import torch
+    B = 512
+    p, x, t, P, Wb, X, T = _setup(8, B)
+    ws = torch.empty(gbd.gbd_mlp_workspace_bytes(B), dtype=torch.uint8, device="cuda")
+    grad = torch.empty(M.N_PARAMS, dtype=torch.float32, device="cuda")
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    try:
+        gbd.gbd_set_wait_limit(1)
+        gbd.gbd_mlp_grad(Wb, X, T, grad, loss, ws)
+        with pytest.raises(gbd.GbdError) as ei:
+            gbd.gbd_sync()
+        assert ei.value.status == gbd.GBD_ETIMEOUT
+    finally:
+        gbd.gbd_set_wait_limit(0)
+    gbd.gbd_mlp_grad(Wb, X, T, grad, loss, ws)
+    gbd.gbd_sync()
+    L, g = M.loss_grad(p, x, t)
+    assert np.linalg.norm(grad.cpu().numpy() - g) <= 1e-4 * np.linalg.norm(g)
