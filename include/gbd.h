@@ -457,12 +457,15 @@ void gbd_sweep_plan_destroy(gbd_sweep_plan* plan);
  * Not in the paper: a small network that learns log10 of the sweep's Airy score from
  * (overlap factor, waist ratio, log2 beamlets across), standardised by the caller, so
  * that a search verifies only the parameter sets it predicts to be best.
- * Architecture: 3 -> 128 -> 128 -> 128 -> 128 -> 1, exact GELU 0.5 x (1 + erf(x / sqrt 2))
- * after each hidden layer, linear output.  GBD_MLP_PARAMS floats in the order
+ * Architecture: 3 -> 128 -> 128 -> 128 -> 128 -> 1, GELU x Phi(x) after each hidden layer
+ * (Phi, the normal CDF, by Abramowitz & Stegun 7.1.26: absolute error <= 1.5e-7), linear
+ * output.  GBD_MLP_PARAMS floats in the order
  * W1[128][3] b1[128] W2[128][128] b2[128] W3 b3 W4 b4 W5[1][128] b5[1] (W[out][in]).
  * Compute: BF16 weights (round to nearest even from the FP32 master copy), FP32
- * activations and accumulation; loss = mean over the batch of (y - target)^2; Adam with
- * bias correction on the FP32 master weights.  All reductions have a fixed order, so
+ * activations and accumulation; the 128 x 128 layers on the tensor cores with the FP32
+ * operands split into BF16 parts (forward pass: three, FP32-accurate; training: two,
+ * 2^-18 relative); loss = mean over the batch of (y - target)^2; Adam with bias correction
+ * on the FP32 master weights.  All reductions have an order fixed by the batch size, so
  * results are deterministic.  x is float[batch][3], target/y float[batch], all device;
  * weights 16-byte aligned, workspaces 256-byte aligned (EINVAL otherwise); batch 1 .. 2^20
  * for training, 1 .. 2^24 for the forward pass.
@@ -470,14 +473,16 @@ void gbd_sweep_plan_destroy(gbd_sweep_plan* plan);
  * gbd_mlp_forward:    y = MLP(x); no workspace.
  * gbd_mlp_grad:       grad = dLoss/dparams (float[GBD_MLP_PARAMS]) and *loss (device float,
  *                     may be NULL) at the BF16 weights; workspace >= gbd_mlp_workspace_bytes
- *                     (the four hidden layers' activations, GELU derivatives and errors,
- *                     3 x 4 x batch x 128 floats, and per-chunk gradient partials).
+ *                     (about 4 KB per sample: the layers' activations and errors in BF16
+ *                     parts, a_4 and dL/dz_1 in FP32, y and dL/dy; a 106 KB weight image).
  * gbd_mlp_adam:       one Adam step (step counts from 1) on master/m/v, then repacks.
  * gbd_mlp_train:      `steps` full-batch steps (gradient, then Adam), step numbers
  *                     first_step, first_step + 1, ...; *loss (may be NULL) = the loss of
- *                     the last step, at the weights before its update.  The launches are
- *                     queued on `stream` from this call, without returning to the caller
- *                     between steps; nothing is synchronised.
+ *                     the last step, at the weights before its update.  One cooperative
+ *                     launch runs all steps (every CTA resident; grid barriers between the
+ *                     sample-parallel and the parameter-parallel phase of each step, bounded
+ *                     waits: GBD_ETIMEOUT from gbd_sync); nothing is synchronised.
+ *                     gbd_mlp_grad is the same launch with one step and no update.
  * gbd_mlp_train_step: gbd_mlp_train with steps = 1. */
 #define GBD_MLP_PARAMS 50177
 size_t gbd_mlp_workspace_bytes(int32_t batch);

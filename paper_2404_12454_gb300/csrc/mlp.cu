@@ -11,11 +11,13 @@
 // operand v (activation or error) is split into BF16 parts v = hi + mid + lo (each the
 // rounding of what the previous parts leave; |v - hi - mid - lo| <= 2^-27 |v|) or
 // v ~ hi + lo (2^-18 |v|), and W v is the sum of one product per part:
-//   forward   z_l = W_l a_{l-1}:     a in three parts (FP32-accurate activations);
+//   forward   z_l = W_l a_{l-1}:     a in three parts (inference: FP32-accurate
+//                                    activations) or two (training);
 //   backward  e = W_l^T d_l:         d in two parts;
 //   gradient  dW_l = sum_n d_l a_{l-1}^T: d and a in two parts each, the products
 //             hi.hi + (hi.lo + lo.hi) (the dropped lo.lo is below 2^-17 relative).
-// The first layer (3 inputs), the output unit and the biases stay on the FP32 pipe.
+// The first layer (3 inputs), the output unit and the biases stay on the FP32 pipe.  GELU's
+// normal CDF is Abramowitz & Stegun's 7.1.26 (absolute error <= 1.5e-7).
 //
 // A training call is one persistent cooperative kernel over all its steps; each step is
 //   phase A (sample-parallel): CTAs take items of 8 samples (the mma's n); the CTA stages
@@ -52,7 +54,8 @@ __host__ __device__ constexpr int off_b(int l) {
 constexpr int NPARAM = 50177;
 
 constexpr int NS = 8;          // samples per phase-A item (the mma's n)
-constexpr int THREADS = 256;   // 8 warps, one 16-unit m-tile each
+constexpr int THREADS = 512;   // 16 warps: a pair per 16-unit m-tile, splitting K
+constexpr int NWARP = THREADS / 32;
 constexpr int WP = H + 8;      // padded BF16 row of staged weights and operand planes
 constexpr int GP = H + 4;      // padded FP32 row of GELU derivatives and the last activations
 constexpr int KI = 32;         // items (of NS samples) per staged block of a gradient tile
@@ -71,7 +74,8 @@ constexpr size_t kOffW1 = kOffA4 + sizeof(float) * NS * GP;     // [H][3] f32
 constexpr size_t kOffBias = kOffW1 + sizeof(float) * H * 3;     // [4][H] f32
 constexpr size_t kOffW5 = kOffBias + sizeof(float) * 4 * H;     // [H] f32
 constexpr size_t kOffMisc = kOffW5 + sizeof(float) * H;  // b5, dy[NS], x[NS][3], target[NS]
-constexpr size_t kSmemA = kOffMisc + 256;
+constexpr size_t kOffXch = kOffMisc + 256;  // [2 K-halves][8 m-tiles][32 lanes] float2
+constexpr size_t kSmemA = kOffXch + sizeof(float2) * 2 * 8 * 32;
 // The weight image in the workspace: the small parameters as FP32 in the shared-memory
 // order from kOffW1 (W1, b1..b4, W5, b5, padding: one bulk copy), then W2..W4 as BF16 rows
 // padded to WP (the kOffWs bytes: one bulk copy).
@@ -87,12 +91,17 @@ constexpr int NBUF = 4;
 constexpr size_t kDBytes = sizeof(uint16_t) * KI * TO * NS;
 constexpr size_t kABytes = sizeof(uint16_t) * KI * TI * NS;
 constexpr size_t kStageBytes = 2 * kDBytes + 2 * kABytes;
-constexpr size_t kOffRed = NBUF * kStageBytes;                      // [8][TO][TI] f32
-constexpr size_t kOffBsum = kOffRed + sizeof(float) * 8 * TO * TI;  // 1024 f32 scratch
-constexpr size_t kSmemB = kOffBsum + sizeof(float) * 16 * 16 * 4;
-// mbarriers (weights: small, big; ring: NBUF) after both phases' bytes
+constexpr int RP = TI + 8;  // padded row of the warps' partial tiles (conflict-free float2)
+// after a task's blocks are consumed, the ring's first bytes hold the warps' partial tiles
+// and the small tasks' scratch
+constexpr size_t kOffRed = 0;                                           // [NWARP][TO][RP] f32
+constexpr size_t kOffBsum = kOffRed + sizeof(float) * NWARP * TO * RP;  // 2048 f32 scratch
+constexpr size_t kSmemB = NBUF * kStageBytes;
+static_assert(kOffBsum + sizeof(float) * 2048 <= kSmemB, "phase-B scratch");
+// mbarriers (weights: small parameters, W2, W3, W4; ring: NBUF) after both phases' bytes
+constexpr int kWBars = 4;
 constexpr size_t kOffBars = kSmemA > kSmemB ? kSmemA : kSmemB;
-constexpr size_t kSmemStep = kOffBars + 8 * (2 + NBUF);
+constexpr size_t kSmemStep = kOffBars + 8 * (kWBars + NBUF);
 static_assert(kSmemStep <= 227 * 1024, "shared memory");
 static_assert(kOffBars % 8 == 0 && kSmemA % 8 == 0, "mbarrier alignment");
 
@@ -100,10 +109,26 @@ __device__ __forceinline__ float bf2f(uint16_t w) { return __uint_as_float((uint
 __device__ __forceinline__ uint16_t f2bf(float v) {
     return __bfloat16_as_ushort(__float2bfloat16_rn(v));
 }
-// gelu(x) and gelu'(x) = Phi(x) + x phi(x) from one erf
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+// gelu(x) = x Phi(x) and gelu'(x) = Phi(x) + x phi(x).  Phi(-|x|) = erfc(u) / 2, u = |x| / sqrt 2,
+// by Abramowitz & Stegun 7.1.26 (Hastings' rational approximation, |error| <= 1.5e-7):
+//   erfc(u) = t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) e^(-u^2),  t = 1 / (1 + p u),
+// where e^(-u^2) = e^(-x^2/2) is also the normal density's exponential (one ex2, one rcp).
 __device__ __forceinline__ float gelu_and_grad(float x, float& grad) {
-    const float cdf = 0.5f * (1.0f + erff(x * 0.70710678118654752f));
-    grad = cdf + x * 0.39894228040143268f * expf(-0.5f * x * x);
+    const float u = fabsf(x) * 0.70710678118654752f;
+    const float t = rcp_approx(fmaf(0.3275911f, u, 1.0f));
+    const float poly =
+        t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f),
+                         -0.284496736f),
+                 0.254829592f);
+    const float e = gbd::mufu_ex2(-0.72134752044448170f * x * x);  // e^(-x^2/2)
+    const float tail = 0.5f * poly * e;                               // Phi(-|x|)
+    const float cdf = x >= 0.f ? 1.0f - tail : tail;
+    grad = fmaf(x * 0.39894228040143268f, e, cdf);
     return x * cdf;
 }
 // v = hi + mid + lo (each a BF16 rounding of the remainder; the subtractions are exact)
@@ -265,6 +290,7 @@ struct SmemA {
     float* bias;    // b1..b4 [4][H]
     float* w5;      // [H]
     float* misc;    // [0] b5, [8..15] dL/dy, [16..39] x, [40..47] targets of the item
+    float2* xch;    // K-half partial sums exchanged by the two warps of an m-tile
     __device__ explicit SmemA(unsigned char* s)
         : ws(reinterpret_cast<uint16_t*>(s + kOffWs)),
           pl(reinterpret_cast<uint16_t*>(s + kOffPl)),
@@ -273,21 +299,35 @@ struct SmemA {
           w1(reinterpret_cast<float*>(s + kOffW1)),
           bias(reinterpret_cast<float*>(s + kOffBias)),
           w5(reinterpret_cast<float*>(s + kOffW5)),
-          misc(reinterpret_cast<float*>(s + kOffMisc)) {}
+          misc(reinterpret_cast<float*>(s + kOffMisc)),
+          xch(reinterpret_cast<float2*>(s + kOffXch)) {}
     __device__ uint16_t* plane(int buf, int part) const { return pl + (buf * 3 + part) * NS * WP; }
 };
 
 // Start copying the weight image into shared memory (thread 0, bulk copies): bars[0]
-// signals the small parameters, bars[1] W2..W4.  The caller has ordered the image's latest
-// writes before this (kernel start or a grid barrier).
+// signals the small parameters, bars[1 + l] the rows of W_{l+2}, so that each layer waits
+// only for its own matrix.  The caller has ordered the image's latest writes before this
+// (kernel start or a grid barrier).
 __device__ void stage_weights(const Planes& pl, const SmemA& S, uint64_t* bars) {
     if (threadIdx.x == 0) {
         proxy_fence();
         gbd::mbar_arrive_expect_tx(bars, kImgSmallBytes);
         gbd::bulk_copy_g2s(S.w1, pl.img_small, kImgSmallBytes, bars);
-        gbd::mbar_arrive_expect_tx(bars + 1, kImgBigBytes);
-        gbd::bulk_copy_g2s(S.ws, pl.img_big, kImgBigBytes, bars + 1);
+        constexpr uint32_t mat = kImgBigBytes / 3;
+#pragma unroll
+        for (int l = 0; l < 3; ++l) {
+            gbd::mbar_arrive_expect_tx(bars + 1 + l, mat);
+            gbd::bulk_copy_g2s(S.ws + (size_t)l * H * WP, pl.img_big + (size_t)l * H * WP, mat,
+                               bars + 1 + l);
+        }
     }
+}
+
+// Gives up waiting for the weight copies from bars[from] on: drains them all (default
+// limit) so that no copy is left writing into shared memory.
+__device__ void drain_weights(uint64_t* bars, int from, uint32_t parity) {
+    for (int b = from; b < kWBars; ++b)
+        gbd::mbar_wait_bounded(bars + b, parity, gbd::kDefaultWaitSpins);
 }
 
 // Inference: the weights straight from the BF16 vector (16-byte loads), once per CTA.
@@ -305,42 +345,45 @@ __device__ void load_weights(const uint16_t* __restrict__ W, const SmemA& S) {
     if (threadIdx.x == 0) S.misc[0] = bf2f(__ldg(W + off_b(4)));
 }
 
-// z = W_l a for the warp's 16 units (rows 16 warp ..) and the item's 8 samples:
-// acc[p] = W_l (part p of a); in = the three input planes [NS][WP].
+// Half (kh) of z = W_l a for the 16 units of m-tile mt and the item's 8 samples:
+// acc[p] = W_l (part p of a) over inputs 64 kh .. 64 kh + 63, p < NP; in = the input
+// planes [NS][WP].
+template <int NP>
 __device__ __forceinline__ void fwd_mma(const uint16_t* Wl, const uint16_t* in0,
-                                        const uint16_t* in1, const uint16_t* in2, int warp,
-                                        int lane, float (&acc)[3][4]) {
+                                        const uint16_t* in1, const uint16_t* in2, int mt,
+                                        int kh, int lane, float (&acc)[3][4]) {
     const int g = lane >> 2, q = lane & 3;
-    const uint16_t* arow = Wl + (size_t)(16 * warp + (lane & 15)) * WP + (lane >> 4) * 8;
+    const uint16_t* arow = Wl + (size_t)(16 * mt + (lane & 15)) * WP + (lane >> 4) * 8;
 #pragma unroll
     for (int p = 0; p < 3; ++p)
 #pragma unroll
         for (int e = 0; e < 4; ++e) acc[p][e] = 0.f;
 #pragma unroll
-    for (int kk = 0; kk < H / 16; ++kk) {
+    for (int kk = 4 * kh; kk < 4 * kh + 4; ++kk) {
         uint32_t a[4];
         ldsm_x4(a, arow + 16 * kk);
         const int o = g * WP + 16 * kk + 2 * q;
         mma(acc[0], a, lds32(in0 + o), lds32(in0 + o + 8));
         mma(acc[1], a, lds32(in1 + o), lds32(in1 + o + 8));
-        mma(acc[2], a, lds32(in2 + o), lds32(in2 + o + 8));
+        if (NP == 3) mma(acc[2], a, lds32(in2 + o), lds32(in2 + o + 8));
     }
 }
 
-// e = W_l^T d for the warp's 16 input units and the item's 8 samples (d in two parts).
+// Half (kh: outputs 64 kh ..) of e = W_l^T d for the 16 input units of m-tile mt and the
+// item's 8 samples (d in two parts).
 __device__ __forceinline__ void bwd_mma(const uint16_t* Wl, const uint16_t* in0,
-                                        const uint16_t* in1, int warp, int lane,
+                                        const uint16_t* in1, int mt, int kh, int lane,
                                         float (&acc)[2][4]) {
     const int g = lane >> 2, q = lane & 3;
     // ldmatrix.trans of W rows o (the k index) and 8 consecutive input units (the m index)
     const uint16_t* arow =
-        Wl + (size_t)(((lane >> 4) << 3) + (lane & 7)) * WP + 16 * warp + ((lane >> 3) & 1) * 8;
+        Wl + (size_t)(((lane >> 4) << 3) + (lane & 7)) * WP + 16 * mt + ((lane >> 3) & 1) * 8;
 #pragma unroll
     for (int p = 0; p < 2; ++p)
 #pragma unroll
         for (int e = 0; e < 4; ++e) acc[p][e] = 0.f;
 #pragma unroll
-    for (int kk = 0; kk < H / 16; ++kk) {
+    for (int kk = 4 * kh; kk < 4 * kh + 4; ++kk) {
         uint32_t a[4];
         ldsm_x4_t(a, arow + (size_t)16 * kk * WP);
         const int o = g * WP + 16 * kk + 2 * q;
@@ -349,8 +392,23 @@ __device__ __forceinline__ void bwd_mma(const uint16_t* Wl, const uint16_t* in0,
     }
 }
 
-// Forward pass of one item (samples n0 .. n0 + 7 of the padded batch).  TRAIN: also stage
-// a_1..a_3 (two parts) and a_4 for the workspace.  Leaves gelu(z_4) in S.a4, gelu'(z_l) in
+// The two K-halves of an m-tile's 16 x 8 result: warp kh keeps rows 8 kh .. 8 kh + 7 (its
+// lane's samples 2q, 2q + 1) and receives the other warp's partial sums of them; the
+// result is (half 0) + (half 1) in both warps.  Ends with the block synchronised.
+__device__ __forceinline__ float2 join_halves(const SmemA& S, const float (&part)[4], int mt,
+                                              int kh, int lane) {
+    S.xch[(kh * 8 + mt) * 32 + lane] =
+        kh == 0 ? make_float2(part[2], part[3]) : make_float2(part[0], part[1]);
+    __syncthreads();
+    const float2 o = S.xch[((kh ^ 1) * 8 + mt) * 32 + lane];
+    return kh == 0 ? make_float2(part[0] + o.x, part[1] + o.y)
+                   : make_float2(o.x + part[2], o.y + part[3]);
+}
+
+// Forward pass of one item (samples n0 .. n0 + 7 of the padded batch).  Inference splits
+// the activations into three BF16 parts (FP32-accurate outputs); training into two
+// (2^-18 relative, far inside the gradient's error budget) and also stores a_1..a_3 (two
+// parts) and a_4 in the workspace.  Leaves gelu(z_4) in S.a4, gelu'(z_l) in
 // S.g, and returns with the block synchronised.  `first`: the step's first item, which
 // waits for the staged parameters (bars[0] before layer 1, bars[1] after it); false if a
 // wait gave up.
@@ -369,61 +427,75 @@ __device__ bool forward_item(const SmemA& S, const float* __restrict__ x,
         S.misc[40 + n] = n0 + n < B ? __ldg(target + n0 + n) : 0.f;
     }
     if (first && !wait_copies(bars, parity, spins)) {
-        gbd::mbar_wait_bounded(bars + 1, parity, gbd::kDefaultWaitSpins);
+        drain_weights(bars, 1, parity);
         return false;
     }
     __syncthreads();
-    {  // layer 1 (3 inputs): unit u, samples ns .. ns + 3
-        const int u = t & (H - 1), ns = (t >> 7) * 4;
+    {  // layer 1 (3 inputs): unit u, samples ns, ns + 1
+        const int u = t & (H - 1), ns = (t >> 7) * 2;
         const float w0 = S.w1[u * 3], w1 = S.w1[u * 3 + 1], w2 = S.w1[u * 3 + 2], b = S.bias[u];
-        uint16_t hi[4], mid[4], lo[4];
+        uint16_t hi[2], mid[2], lo[2];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < 2; ++k) {
             const int n = ns + k;
             const float* xn = S.misc + 16 + 3 * n;
             const float z = fmaf(w2, xn[2], fmaf(w1, xn[1], fmaf(w0, xn[0], b)));
             float gd;
             const float a = gelu_and_grad(z, gd);
             S.g[n * GP + u] = gd;
-            split3(a, hi[k], mid[k], lo[k]);
+            if (TRAIN) {
+                split2(a, hi[k], mid[k]);
+            } else {
+                split3(a, hi[k], mid[k], lo[k]);
+                S.plane(0, 2)[n * WP + u] = lo[k];
+            }
             S.plane(0, 0)[n * WP + u] = hi[k];
             S.plane(0, 1)[n * WP + u] = mid[k];
-            S.plane(0, 2)[n * WP + u] = lo[k];
         }
         if (TRAIN) {
             const size_t off = a_index(u, n0 + ns, items);
-            *reinterpret_cast<uint2*>(pl.a[0][0] + off) =
-                make_uint2(pack2(hi[0], hi[1]), pack2(hi[2], hi[3]));
-            *reinterpret_cast<uint2*>(pl.a[0][1] + off) =
-                make_uint2(pack2(mid[0], mid[1]), pack2(mid[2], mid[3]));
+            *reinterpret_cast<uint32_t*>(pl.a[0][0] + off) = pack2(hi[0], hi[1]);
+            *reinterpret_cast<uint32_t*>(pl.a[0][1] + off) = pack2(mid[0], mid[1]);
         }
     }
-    if (first && !wait_copies(bars + 1, parity, spins)) return false;
     __syncthreads();
-    const int g = lane >> 2, q = lane & 3;
+    const int g = lane >> 2, q = lane & 3, mt = warp & 7, kh = warp >> 3;
+    constexpr int NP = TRAIN ? 2 : 3;
     for (int l = 2; l <= 4; ++l) {
         const int cur = l & 1, nxt = cur ^ 1;  // layer 2 reads buffer 0
+        if (first && !wait_copies(bars + l - 1, parity, spins)) {
+            drain_weights(bars, l, parity);
+            return false;
+        }
         float acc[3][4];
-        fwd_mma(S.ws + (size_t)(l - 2) * H * WP, S.plane(cur, 0), S.plane(cur, 1),
-                S.plane(cur, 2), warp, lane, acc);
+        fwd_mma<NP>(S.ws + (size_t)(l - 2) * H * WP, S.plane(cur, 0), S.plane(cur, 1),
+                    S.plane(cur, 2), mt, kh, lane, acc);
+        float part[4];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int u = 16 * warp + g + 8 * h;
+        for (int c = 0; c < 4; ++c)
+            part[c] = (NP == 3 ? acc[2][c] + acc[1][c] : acc[1][c]) + acc[0][c];
+        const float2 zz = join_halves(S, part, mt, kh, lane);
+        {
+            const int u = 16 * mt + g + 8 * kh;
             const float b = S.bias[(l - 1) * H + u];
             float av[2];
             uint16_t hi[2], mid[2], lo[2];
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
-                const int n = 2 * q + e, c = 2 * h + e;
-                const float z = (acc[2][c] + acc[1][c]) + acc[0][c] + b;
+                const int n = 2 * q + e;
+                const float z = (e ? zz.y : zz.x) + b;
                 float gd;
                 av[e] = gelu_and_grad(z, gd);
                 S.g[((l - 1) * NS + n) * GP + u] = gd;
                 if (l < 4) {
-                    split3(av[e], hi[e], mid[e], lo[e]);
+                    if (TRAIN) {
+                        split2(av[e], hi[e], mid[e]);
+                    } else {
+                        split3(av[e], hi[e], mid[e], lo[e]);
+                        S.plane(nxt, 2)[n * WP + u] = lo[e];
+                    }
                     S.plane(nxt, 0)[n * WP + u] = hi[e];
                     S.plane(nxt, 1)[n * WP + u] = mid[e];
-                    S.plane(nxt, 2)[n * WP + u] = lo[e];
                 } else {
                     S.a4[n * GP + u] = av[e];
                 }
@@ -458,7 +530,7 @@ __device__ __forceinline__ float output_unit(const SmemA& S, int n, int lane) {
 __device__ void backward_item(const SmemA& S, int B, int n0, const Planes& pl, int Bp) {
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const int items = Bp / NS;
-    {
+    if (warp < NS) {
         const int n = warp;
         const float y = output_unit(S, n, lane);
         if (lane == 0) {
@@ -469,12 +541,12 @@ __device__ void backward_item(const SmemA& S, int B, int n0, const Planes& pl, i
         }
     }
     __syncthreads();
-    {  // d_4 = dL/dy w5 gelu'(z_4): unit u, samples ns .. ns + 3
-        const int u = t & (H - 1), ns = (t >> 7) * 4;
+    {  // d_4 = dL/dy w5 gelu'(z_4): unit u, samples ns, ns + 1
+        const int u = t & (H - 1), ns = (t >> 7) * 2;
         const float w = S.w5[u];
-        uint16_t hi[4], lo[4];
+        uint16_t hi[2], lo[2];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < 2; ++k) {
             const int n = ns + k;
             const float d = S.misc[8 + n] * w * S.g[(3 * NS + n) * GP + u];
             split2(d, hi[k], lo[k]);
@@ -482,27 +554,28 @@ __device__ void backward_item(const SmemA& S, int B, int n0, const Planes& pl, i
             S.plane(0, 1)[n * WP + u] = lo[k];
         }
         const size_t off = d_index(u, n0 + ns, items);
-        *reinterpret_cast<uint2*>(pl.d[2][0] + off) =
-            make_uint2(pack2(hi[0], hi[1]), pack2(hi[2], hi[3]));
-        *reinterpret_cast<uint2*>(pl.d[2][1] + off) =
-            make_uint2(pack2(lo[0], lo[1]), pack2(lo[2], lo[3]));
+        *reinterpret_cast<uint32_t*>(pl.d[2][0] + off) = pack2(hi[0], hi[1]);
+        *reinterpret_cast<uint32_t*>(pl.d[2][1] + off) = pack2(lo[0], lo[1]);
     }
     __syncthreads();
-    const int g = lane >> 2, q = lane & 3;
+    const int g = lane >> 2, q = lane & 3, mt = warp & 7, kh = warp >> 3;
     for (int l = 4; l >= 2; --l) {  // W_l: d_l -> d_{l-1}
         const int cur = l & 1, nxt = cur ^ 1;  // d_4 sits in buffer 0
         float acc[2][4];
-        bwd_mma(S.ws + (size_t)(l - 2) * H * WP, S.plane(cur, 0), S.plane(cur, 1), warp, lane,
+        bwd_mma(S.ws + (size_t)(l - 2) * H * WP, S.plane(cur, 0), S.plane(cur, 1), mt, kh, lane,
                 acc);
+        float part[4];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int i = 16 * warp + g + 8 * h;
+        for (int c = 0; c < 4; ++c) part[c] = acc[1][c] + acc[0][c];
+        const float2 ee = join_halves(S, part, mt, kh, lane);
+        {
+            const int i = 16 * mt + g + 8 * kh;
             float dv[2];
             uint16_t hi[2], lo[2];
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
-                const int n = 2 * q + e, c = 2 * h + e;
-                dv[e] = (acc[1][c] + acc[0][c]) * S.g[((l - 2) * NS + n) * GP + i];
+                const int n = 2 * q + e;
+                dv[e] = (e ? ee.y : ee.x) * S.g[((l - 2) * NS + n) * GP + i];
                 if (l > 2) {
                     split2(dv[e], hi[e], lo[e]);
                     S.plane(nxt, 0)[n * WP + i] = hi[e];
@@ -590,7 +663,7 @@ __device__ __forceinline__ void emit(const StepArgs& A, int k, const AdamState& 
 // Gradient of a 16 x 32 tile of W_{L+2} (L = 0..2) over the whole batch:
 // dW[o][i] = sum_n d[o][n] a[i][n].  The tile's operands arrive KI items at a time (four
 // bulk copies per block) through a ring of NBUF buffers, each with its mbarrier (phase
-// parities in *ring); warp w takes k-steps (item pairs) w, w + 8 of each block and the
+// parities in *ring); warp w takes k-step (item pair) w of each block and the
 // warps' sums are added in warp order.  The tile with ib == 0 also sums the bias gradient
 // of its 16 units.  False if a wait gave up.
 template <bool TRAIN>
@@ -601,11 +674,11 @@ __device__ bool hidden_task(const StepArgs& A, unsigned char* smem, uint64_t* ri
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const int items = A.Bp / NS;
     const int wbase = off_w(L + 1), bbase = off_b(L + 1);
-    // this thread's parameters: tile entries t and t + 256 (row-major 16 x 32), bias t < 16
+    // this thread's parameters: tile entry t (row-major 16 x 32), bias t < 16
+    static_assert(THREADS == TO * TI, "one tile entry per thread");
     const int k0 = wbase + (TO * ob + t / TI) * H + TI * ib + t % TI;
-    const int k1 = k0 + (THREADS / TI) * H;
     const bool has_bias = ib == 0 && t < TO;
-    const AdamState st0 = prefetch<TRAIN>(A, k0), st1 = prefetch<TRAIN>(A, k1);
+    const AdamState st0 = prefetch<TRAIN>(A, k0);
     const AdamState stb = has_bias ? prefetch<TRAIN>(A, bbase + TO * ob + t) : AdamState{};
     const uint16_t* dsrc0 = A.pl.d[L][0] + (size_t)ob * items * TO * NS;
     const uint16_t* dsrc1 = A.pl.d[L][1] + (size_t)ob * items * TO * NS;
@@ -653,7 +726,7 @@ __device__ bool hidden_task(const StepArgs& A, unsigned char* smem, uint64_t* ri
         const uint16_t* dl = reinterpret_cast<const uint16_t*>(b + kDBytes);
         const uint16_t* ah = reinterpret_cast<const uint16_t*>(b + 2 * kDBytes);
         const uint16_t* al = reinterpret_cast<const uint16_t*>(b + 2 * kDBytes + kABytes);
-        for (int kk = warp; kk < ks; kk += 8) {
+        for (int kk = warp; kk < ks; kk += NWARP) {
             uint32_t Ah[4], Al[4];
             const int ao = ((2 * kk + (lane >> 4)) * TO + (lane & 15)) * NS;
             ldsm_x4(Ah, dh + ao);
@@ -693,32 +766,29 @@ __device__ bool hidden_task(const StepArgs& A, unsigned char* smem, uint64_t* ri
         }
         __syncthreads();  // the buffer is refilled NBUF - 1 blocks on
     }
-    float* red = reinterpret_cast<float*>(smem + kOffRed);  // [8][TO][TI]
+    float* red = reinterpret_cast<float*>(smem + kOffRed);  // [NWARP][TO][RP]
     float* bs = reinterpret_cast<float*>(smem + kOffBsum);  // [16 item pairs][TO]
     {
         const int g = lane >> 2, q = lane & 3;
-        float* rw = red + warp * TO * TI;
+        float* rw = red + warp * TO * RP;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            rw[g * TI + 8 * j + 2 * q] = crs[j][0] + acc[j][0];
-            rw[g * TI + 8 * j + 2 * q + 1] = crs[j][1] + acc[j][1];
-            rw[(g + 8) * TI + 8 * j + 2 * q] = crs[j][2] + acc[j][2];
-            rw[(g + 8) * TI + 8 * j + 2 * q + 1] = crs[j][3] + acc[j][3];
+            *reinterpret_cast<float2*>(rw + g * RP + 8 * j + 2 * q) =
+                make_float2(crs[j][0] + acc[j][0], crs[j][1] + acc[j][1]);
+            *reinterpret_cast<float2*>(rw + (g + 8) * RP + 8 * j + 2 * q) =
+                make_float2(crs[j][2] + acc[j][2], crs[j][3] + acc[j][3]);
         }
         if (ib == 0) bs[t] = bsum;
     }
     __syncthreads();
-    float s0 = red[t], s1 = red[t + THREADS];
+    const int r0 = (t / TI) * RP + t % TI;
+    float s0 = red[r0];
 #pragma unroll
-    for (int w = 1; w < 8; ++w) {
-        s0 += red[w * TO * TI + t];
-        s1 += red[w * TO * TI + t + THREADS];
-    }
+    for (int w = 1; w < NWARP; ++w) s0 += red[w * TO * RP + r0];
     emit<TRAIN>(A, k0, st0, s0, c1, c2);
-    emit<TRAIN>(A, k1, st1, s1, c1, c2);
     if (has_bias) {
         float s = bs[t];
-        for (int k = 1; k < 16; ++k) s += bs[k * TO + t];
+        for (int k = 1; k < THREADS / TO; ++k) s += bs[k * TO + t];
         emit<TRAIN>(A, bbase + TO * ob + t, stb, s, c1, c2);
     }
     __syncthreads();  // shared memory is reused by the next task
@@ -726,17 +796,17 @@ __device__ bool hidden_task(const StepArgs& A, unsigned char* smem, uint64_t* ri
 }
 
 // First layer: dW1[u][c] = sum_n d_1[u][n] x[n][c], db1[u] = sum_n d_1[u][n] for 16 units;
-// thread (o, q) takes samples q, q + 16, ...; the 16 partial sums are added in q order.
+// thread (o, q) takes samples q, q + 32, ...; the 32 partial sums are added in q order.
 template <bool TRAIN>
 __device__ void first_task(const StepArgs& A, unsigned char* smem, int f, float c1, float c2) {
-    const int t = threadIdx.x, o = t >> 4, q = t & 15, u = 16 * f + o;
+    const int t = threadIdx.x, o = t >> 5, q = t & 31, u = 16 * f + o;
     // thread t < 64 owns parameter (unit 16 f + t / 4, column t % 4; column 3 = bias)
     const int pu = 16 * f + (t >> 2), pc = t & 3;
     const int pk = pc < 3 ? off_w(0) + pu * 3 + pc : off_b(0) + pu;
     const AdamState st = t < 64 ? prefetch<TRAIN>(A, pk) : AdamState{};
     float g0 = 0.f, g1 = 0.f, g2 = 0.f, gb = 0.f;
 #pragma unroll 4
-    for (int n = q; n < A.B; n += 16) {
+    for (int n = q; n < A.B; n += 32) {
         const float dn = __ldcg(A.pl.d1 + f_index(u, n));
         const float* xn = A.x + (size_t)n * 3;
         g0 = fmaf(dn, __ldg(xn), g0);
@@ -744,14 +814,14 @@ __device__ void first_task(const StepArgs& A, unsigned char* smem, int f, float 
         g2 = fmaf(dn, __ldg(xn + 2), g2);
         gb += dn;
     }
-    float* bs = reinterpret_cast<float*>(smem + kOffBsum);  // [16 units][16 q][4]
+    float* bs = reinterpret_cast<float*>(smem + kOffBsum);  // [16 units][32 q][4]
     float4* b4 = reinterpret_cast<float4*>(bs);
     b4[t] = make_float4(g0, g1, g2, gb);
     __syncthreads();
     if (t < 64) {
         const int uo = t >> 2;
-        float s = bs[(uo * 16) * 4 + pc];
-        for (int k = 1; k < 16; ++k) s += bs[(uo * 16 + k) * 4 + pc];
+        float s = bs[(uo * 32) * 4 + pc];
+        for (int k = 1; k < 32; ++k) s += bs[(uo * 32 + k) * 4 + pc];
         emit<TRAIN>(A, pk, st, s, c1, c2);
     }
     __syncthreads();
@@ -773,19 +843,19 @@ __device__ float block_sum(float v, float* red) {
 template <bool TRAIN>
 __device__ void out_task(const StepArgs& A, unsigned char* smem, int f, float c1, float c2,
                          bool last) {
-    const int t = threadIdx.x, o = t >> 4, q = t & 15, u = 16 * f + o;
+    const int t = threadIdx.x, o = t >> 5, q = t & 31, u = 16 * f + o;
     const AdamState st = t < 16 ? prefetch<TRAIN>(A, off_w(4) + 16 * f + t) : AdamState{};
     const AdamState stb = f == 0 && t == 0 ? prefetch<TRAIN>(A, off_b(4)) : AdamState{};
     float g = 0.f;
 #pragma unroll 4
-    for (int n = q; n < A.B; n += 16)
+    for (int n = q; n < A.B; n += 32)
         g = fmaf(__ldcg(A.pl.dout + n), __ldcg(A.pl.a4 + f_index(u, n)), g);
     float* bs = reinterpret_cast<float*>(smem + kOffBsum);
     bs[t] = g;
     __syncthreads();
     if (t < 16) {
-        float s = bs[t * 16];
-        for (int k = 1; k < 16; ++k) s += bs[t * 16 + k];
+        float s = bs[t * 32];
+        for (int k = 1; k < 32; ++k) s += bs[t * 32 + k];
         emit<TRAIN>(A, off_w(4) + 16 * f + t, st, s, c1, c2);
     }
     if (f == 0) {
@@ -819,8 +889,8 @@ template <bool TRAIN>
 __global__ void __launch_bounds__(THREADS, 1) mlp_step_kernel(const StepArgs A) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ float corr[2];
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kOffBars);  // weights: 2, ring: NBUF
-    init_bars(bars, 2 + NBUF);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kOffBars);  // weights, then the ring
+    init_bars(bars, kWBars + NBUF);
     const int items = A.Bp / NS;
     unsigned epoch = 0;
     uint32_t wpar = 0, ringpar = 0;
@@ -848,7 +918,8 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_step_kernel(const StepArgs A) 
         bool fenced = false;
         for (int task = blockIdx.x; task < kTasks; task += gridDim.x) {
             if (task < kHiddenTasks) {
-                if (!hidden_task<TRAIN>(A, smem, bars + 2, ringpar, fenced, task, c1, c2)) return;
+                if (!hidden_task<TRAIN>(A, smem, bars + kWBars, ringpar, fenced, task, c1, c2))
+                    return;
             } else if (task < kHiddenTasks + kFirstTasks) {
                 first_task<TRAIN>(A, smem, task - kHiddenTasks, c1, c2);
             } else {
@@ -872,8 +943,10 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_kernel(const uint16_t*
     const Planes none{};
     for (int it = blockIdx.x; it < items; it += gridDim.x) {
         forward_item<false>(S, x, nullptr, B, it * NS, none, 0, false, nullptr, 0u, 0u);
-        const float v = output_unit(S, warp, lane);
-        if (lane == 0 && it * NS + warp < B) y[it * NS + warp] = v;
+        if (warp < NS) {
+            const float v = output_unit(S, warp, lane);
+            if (lane == 0 && it * NS + warp < B) y[it * NS + warp] = v;
+        }
         __syncthreads();  // S.a4 and the input samples are rewritten by the next item
     }
 }
