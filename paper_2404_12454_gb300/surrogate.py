@@ -233,7 +233,8 @@ def compare_with_random(target: float, seeds: Sequence[int], n_init: int = 32,
 
 def time_training(batch: int = 1024, steps: int = 100, seed: int = 0) -> float:
     """Microseconds per full-batch training step of a fresh network on `batch` synthetic
-    samples (inputs ~ N(0, 1), target = first input), after 5 untimed steps."""
+    samples (inputs ~ N(0, 1), target = first input), after 5 untimed steps: wall time of
+    one MLP.fit call (host copies of the data, workspace allocation, the loss read back)."""
     import time
 
     import torch
@@ -247,6 +248,29 @@ def time_training(batch: int = 1024, steps: int = 100, seed: int = 0) -> float:
     return (time.perf_counter() - t0) / steps * 1e6
 
 
+def time_training_device(batch: int = 1024, steps: int = 100, seed: int = 0) -> float:
+    """Microseconds per training step on the device: CUDA events on the current stream
+    around one gbd_mlp_train call of `steps` steps (data and workspace resident), after a
+    5-step warm-up call."""
+    import torch
+    net = MLP()
+    rng = np.random.default_rng(seed)
+    xt = torch.tensor(rng.normal(size=(batch, 3)).astype(np.float32), device=net.device)
+    yt = xt[:, 0].contiguous()
+    ws = torch.empty(gbd.gbd_mlp_workspace_bytes(batch), dtype=torch.uint8, device=net.device)
+    loss = torch.zeros(1, dtype=torch.float32, device=net.device)
+    gbd.gbd_mlp_train(net.master, net.weights, net.m, net.v, xt, yt, 2e-3, 0.9, 0.999, 1e-8, 1,
+                      5, loss, ws)
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    start.record()
+    gbd.gbd_mlp_train(net.master, net.weights, net.m, net.v, xt, yt, 2e-3, 0.9, 0.999, 1e-8, 6,
+                      steps, loss, ws)
+    stop.record()
+    gbd.gbd_sync()
+    return start.elapsed_time(stop) / steps * 1e3
+
+
 if __name__ == "__main__":
     import argparse
     import json
@@ -258,4 +282,5 @@ if __name__ == "__main__":
     from . import build
     build.build()
     print(json.dumps({"batch": a.batch, "steps": a.steps,
-                      "us_per_step": time_training(a.batch, a.steps)}))
+                      "us_per_step": time_training(a.batch, a.steps),
+                      "device_us_per_step": time_training_device(a.batch, a.steps)}))
