@@ -48,10 +48,10 @@ GB300_MAX_MHZ = 2070.0
 FIELD_MIXED_NCU = [
     {"kernel": "field_mixed_rows_kernel<4, 4> (4x4 row quadruples)", "read": 3.3344e6,
      "write": 2.884352e6, "splits": 90, "rows": 4, "cols": 4, "scheme": 1,
-     "inst_per_32_evals": 6.81},
+     "inst_per_32_evals": 6.81, "fma_pipe_active": 0.675},
     {"kernel": "field_mixed_rows_kernel<4, 8> (4x8 row quadruples, packed FP32x2)",
      "read": 3.353088e6, "write": 4.194816e6, "splits": 90, "rows": 4, "cols": 8, "scheme": 1,
-     "inst_per_32_evals": 4.74},
+     "inst_per_32_evals": 4.74, "fma_pipe_active": 0.721},
 ]
 ISSUE_PER_CLK_SM = 4  # warp-instructions issued per clock and SM (one per sub-partition)
 
@@ -841,6 +841,11 @@ def run_ours(args, world, rank, local):
             "peak": issue_peak / 1e9, "unit": "Geval/s", "frac": achieved / issue_peak,
             "source": ("ncu smsp__inst_executed.sum of the capture; 152 SMs x 4 issue slots "
                        "x 2070 MHz")}
+        # what binds the packed kernels: the FMA-heavy pipe (the packed FP32x2 operations
+        # and the phase FMAs); its busy fraction over the captured launch
+        roofline["fma_pipe"] = {
+            "active_frac": cap["fma_pipe_active"],
+            "source": "ncu sm__pipe_fma_cycles_active.avg.pct_of_peak_sustained_active of the capture"}
 
     # ---- error and CPU baseline (rank 0, one GPU)
     cpu = None
