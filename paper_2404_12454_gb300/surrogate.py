@@ -4,9 +4,10 @@ overlap factor and number of beamlets reproduce the Airy pattern best).
 Every candidate (N beamlets across, overlap factor, waist ratio) is judged by a real GBD
 evaluation: a batched sweep on the GPU (gbd_sweep_*), which returns the RMS error of the
 PSF against the analytic Airy amplitude.  The surrogate is the library's MLP (gbd_mlp_*,
-trained on the GPU by its own forward/backward/Adam kernels) fitted to log10 of those
-scores; each round it ranks a random candidate pool, the best `per_round` candidates are
-verified by a sweep and appended to the data, and the network is refitted.  Plain grid
+trained on the GPU by its own training kernel: forward, backward and Adam in one launch
+per fit) fitted to log10 of those scores; each round it ranks a random candidate pool, the
+best `per_round` candidates are verified by a sweep and appended to the data, and the
+network is refitted.  Plain grid
 search (21 OF x 12 WR x 5 N = 1,260 evaluations) is the reference and the fallback, and
 random search at an equal budget is the ablation without the network.
 
