@@ -1,7 +1,7 @@
 // MLP surrogate of the parameter search: (OF, WR, log2 N) standardised -> 128 -> 128 ->
-// 128 -> 128 -> 1 (predicted log10 Airy score), exact GELU, BF16 weights with FP32
-// activations and accumulation, FP32 master weights updated by Adam.  Not in the paper:
-// it learns the sweep's scores so that the search verifies only promising parameter sets.
+// 128 -> 128 -> 1 (predicted log10 Airy score), GELU, BF16 weights with FP32 activations
+// and accumulation, FP32 master weights updated by Adam.  Not in the paper: it learns the
+// sweep's scores so that the search verifies only promising parameter sets.
 //
 // Parameter layout (floats, GBD_MLP_PARAMS = 50,177): W1[128][3] b1[128] W2[128][128] b2
 // W3 b3 W4 b4 W5[1][128] b5[1]; the BF16 copy has the same layout.
@@ -19,21 +19,23 @@
 // The first layer (3 inputs), the output unit and the biases stay on the FP32 pipe.  GELU's
 // normal CDF is Abramowitz & Stegun's 7.1.26 (absolute error <= 1.5e-7).
 //
-// A training call is one persistent cooperative kernel over all its steps; each step is
-//   phase A (sample-parallel): CTAs take items of 8 samples (the mma's n); the CTA stages
-//     W2..W4 in shared memory once per step, runs the forward pass (storing gelu'(z) in
-//     shared memory) and the backward pass of each item, and writes the activations and
-//     errors the weight gradients need to the workspace, transposed to [unit][sample];
+// A training call is one persistent cooperative kernel over all its steps (512 threads,
+// one CTA per SM); each step is
+//   phase A (sample-parallel): the CTA stages the weight image (bulk copies; the image in
+//     the workspace is kept current by Adam) and takes items of 8 samples (the mma's n):
+//     forward pass (gelu'(z) kept in shared memory), output, backward pass, each 128 x 128
+//     layer split over K between the two warps of a 16-unit m-tile; the activations and
+//     errors the weight gradients need go to the workspace, blocked per gradient tile;
 //   grid barrier;
 //   phase B (parameter-parallel): 112 tasks, each owning a set of parameters and summing
 //     its gradient over the whole batch in a fixed order: 96 tiles of 16 x 32 hidden
-//     weights (mma over the samples, staged 256 samples at a time), 8 first-layer and 8
-//     output-unit tasks of 16 units (FP32 sums); each task applies Adam to its parameters
-//     at once (or writes the gradient, for gbd_mlp_grad);
+//     weights (mma over the samples, streamed 256 samples at a time by bulk copies), 8
+//     first-layer and 8 output-unit tasks of 16 units (FP32 sums); each task applies Adam
+//     to its parameters at once (or writes the gradient, for gbd_mlp_grad);
 //   grid barrier (before the next step stages the updated weights).
 // Every sum runs in an order fixed by the batch size alone (not by the grid), so training
-// is deterministic.  Data written inside the kernel is read through L2 only (cp.async.cg,
-// ld.global.cg): L1 is not coherent across CTAs.
+// is deterministic.  Data written inside the kernel by other CTAs is read through L2 only
+// (bulk copies after a proxy fence, ld.global.cg): L1 is not coherent across CTAs.
 #include <cuda_bf16.h>
 #include <math.h>
 
