@@ -409,7 +409,7 @@ def run_ours(args, world, rank, local):
         # the FP64 path's row-segment shape, picked by one timed run each (the library's
         # autotuner would spend tens of seconds on this 0.4 s kernel)
         best64 = None
-        for shp in ((1, 16), (1, 32), (2, 8)):
+        for shp in ((1, 32), (4, 8), (8, 4)):
             gbd.gbd_field_set_shape(F64, shp[0], shp[1], 0)
             ws[F64] = torch.empty(max(256, gbd.gbd_field_workspace_bytes(nb, det, F64)),
                                   dtype=torch.uint8, device=dev)

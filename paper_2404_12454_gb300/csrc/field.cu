@@ -546,6 +546,21 @@ __global__ void __launch_bounds__(kThreads)
 // keep FP64 relative precision; a beamlet whose amplitude at the segment's first pixel
 // is below 2^-1000 contributes zero to that segment (it cannot rise by 2^900 within the
 // CB pixels of a segment sampled by the detector).
+// A beamlet without a uv term (c_uv = 0, a block-uniform test) factorises on the segment:
+// E(u, v) = X(u) Y(v) with X = exp(c_u t_u + c_uu t_u^2) advanced along the row as above
+// and Y = exp(c_0 + c_v t_v + c_vv t_v^2) the same for every thread of a row band.  With
+// RB > 1 rows per thread each warp evaluates Y once per tile for the (at most two) bands
+// its lanes cover, into a shared-memory table (exp2 + sincospi per beamlet, band and row,
+// shared by the band's lanes), and a lane then spends 4 + 4 + 4 RB FP64 operations per
+// column of RB pixels and two exact evaluations (X, R) per beamlet and segment, instead of
+// 10 RB operations and 2 RB evaluations.  Warps covering more bands (narrow detectors) and
+// beamlets with a uv term take the per-row recurrence.
+constexpr int kYBands = 2;  // row bands per warp table
+template <int RB>
+constexpr size_t f64_row_smem() {
+    return (size_t)kStages * gbd::kF64TileBytes +
+           (RB > 1 ? (size_t)(kThreads / 32) * kYBands * RB * gbd::kTile * sizeof(double2) : 0);
+}
 template <int RB, int CB>
 __global__ void __launch_bounds__(kThreads)
     field_f64_row_kernel(const double2* __restrict__ coef, int n_tiles, int tiles_per_split,
@@ -569,6 +584,13 @@ __global__ void __launch_bounds__(kThreads)
     const long long seg = (long long)blockIdx.x * kThreads + tid;
     const int col0 = (int)(seg % segs_x) * CB;
     const int row0 = (int)(seg / segs_x) * RB;  // rows row0 .. row0 + RB - 1
+    // the warp's row bands and its table of Y (beamlets without a uv term)
+    const long long wseg0 = (long long)blockIdx.x * kThreads + (tid & ~31);
+    const int wband0 = (int)(wseg0 / segs_x);
+    const int wbands = (int)((wseg0 + 31) / segs_x) - wband0 + 1;
+    const bool wtable = RB > 1 && wbands <= kYBands;
+    const int yband = (int)(seg / segs_x) - wband0;  // this lane's band in the table
+    double2* ytab = dyn + kStages * kTileD2 + warp * (kYBands * RB * gbd::kTile);
     double acc_re[RB][CB], acc_im[RB][CB];
 #pragma unroll
     for (int r = 0; r < RB; ++r)
@@ -582,6 +604,29 @@ __global__ void __launch_bounds__(kThreads)
             break;
         }
         const double2* st = ts.tile(k);
+        if (wtable) {
+            __syncwarp();  // every lane is done with the previous tile's table
+            for (int e = lane; e < wbands * RB * gbd::kTile; e += 32) {
+                const int b = e % gbd::kTile, r = (e / gbd::kTile) % RB, q = e / (gbd::kTile * RB);
+                const double2 cuv = st[5 * gbd::kTile + b];
+                double2 y = make_double2(0.0, 0.0);
+                if (cuv.x == 0.0 && cuv.y == 0.0) {
+                    const double2 ij = st[b];
+                    const double2 c0 = st[gbd::kTile + b];
+                    const double2 cv = st[3 * gbd::kTile + b];
+                    const double2 cvv = st[6 * gbd::kTile + b];
+                    const double tv = (double)((wband0 + q) * RB + r) - ij.y;
+                    const double ya = fma(tv, fma(cvv.x, tv, cv.x), c0.x);
+                    const double yp = fma(tv, fma(cvv.y, tv, cv.y), c0.y);
+                    const double amp = exp2(ya);
+                    double sn, cs;
+                    sincospi(2.0 * (yp - rint(yp)), &sn, &cs);
+                    y = make_double2(amp * cs, amp * sn);
+                }
+                ytab[(q * RB + r) * gbd::kTile + b] = y;
+            }
+            __syncwarp();
+        }
 #pragma unroll 1
         for (int b = 0; b < gbd::kTile; ++b) {
             const double2 ij = st[b];
@@ -593,6 +638,46 @@ __global__ void __launch_bounds__(kThreads)
             const double2 cvv = st[6 * gbd::kTile + b];
             const double2 S = st[7 * gbd::kTile + b];
             const double tu = (double)col0 - ij.x;
+            if (wtable && cuv.x == 0.0 && cuv.y == 0.0) {
+                const double xa = tu * fma(cuu.x, tu, cu.x);
+                if (!(xa > -1000.0)) continue;  // X below 2^-1000 on the whole segment
+                const double xp = tu * fma(cuu.y, tu, cu.y);
+                const double da = fma(cuu.x, 2.0 * tu + 1.0, cu.x);
+                const double dp = fma(cuu.y, 2.0 * tu + 1.0, cu.y);
+                double er, ei, rr, ri;
+                {
+                    const double amp = exp2(xa);
+                    double sn, cs;
+                    sincospi(2.0 * (xp - rint(xp)), &sn, &cs);
+                    er = amp * cs;
+                    ei = amp * sn;
+                }
+                {
+                    const double amp = exp2(da);
+                    double sn, cs;
+                    sincospi(2.0 * (dp - rint(dp)), &sn, &cs);
+                    rr = amp * cs;
+                    ri = amp * sn;
+                }
+                double2 y[RB];
+#pragma unroll
+                for (int r = 0; r < RB; ++r) y[r] = ytab[(yband * RB + r) * gbd::kTile + b];
+#pragma unroll
+                for (int c = 0; c < CB; ++c) {
+#pragma unroll
+                    for (int r = 0; r < RB; ++r) {
+                        acc_re[r][c] = fma(er, y[r].x, fma(-ei, y[r].y, acc_re[r][c]));
+                        acc_im[r][c] = fma(er, y[r].y, fma(ei, y[r].x, acc_im[r][c]));
+                    }
+                    const double nr = fma(er, rr, -ei * ri), ni = fma(er, ri, ei * rr);
+                    er = nr;
+                    ei = ni;
+                    const double mr = fma(rr, S.x, -ri * S.y), mi = fma(rr, S.y, ri * S.x);
+                    rr = mr;
+                    ri = mi;
+                }
+                continue;
+            }
 #pragma unroll
             for (int r = 0; r < RB; ++r) {
                 const double tv = (double)(row0 + r) - ij.y;
@@ -787,7 +872,7 @@ cudaError_t launch_f64_row(const void* coeffs, int n_tiles, const gbd_project_pa
                            const gbd_field_launch& L, void* partial_v, const unsigned* /*wide*/,
                            uint32_t spins, const gbd::ReduceOut&, cudaStream_t s) {
     double2* partial = static_cast<double2*>(partial_v);
-    const size_t smem = (size_t)kStages * gbd::kF64TileBytes;
+    const size_t smem = f64_row_smem<RB>();
     cudaError_t e = cudaFuncSetAttribute(field_f64_row_kernel<RB, CB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -908,15 +993,20 @@ const ShapeEntry kMixedShapes[] = {
      rows_smem_bytes()},
 };
 // (1,2), (2,2): every pixel evaluated directly (columns 32 apart); (1,8), (1,16), (2,8),
-// (1,32): contiguous row segments advanced by complex multiplies.
+// (1,32), (4,8), (2,16), (8,4): contiguous row segments advanced by complex multiplies
+// (with RB > 1 rows, the row factors of beamlets without a uv term from a warp table).
 constexpr size_t kF64Smem = (size_t)kStages * gbd::kF64TileBytes;
 const ShapeEntry kF64Shapes[] = {
     {1, 2, 0, launch_f64<1, 2>, (const void*)field_f64_kernel<1, 2>, kF64Smem},
     {2, 2, 0, launch_f64<2, 2>, (const void*)field_f64_kernel<2, 2>, kF64Smem},
     {1, 8, 0, launch_f64_row<1, 8>, (const void*)field_f64_row_kernel<1, 8>, kF64Smem},
-    {2, 8, 0, launch_f64_row<2, 8>, (const void*)field_f64_row_kernel<2, 8>, kF64Smem},
+    {2, 8, 0, launch_f64_row<2, 8>, (const void*)field_f64_row_kernel<2, 8>, f64_row_smem<2>()},
     {1, 16, 0, launch_f64_row<1, 16>, (const void*)field_f64_row_kernel<1, 16>, kF64Smem},
     {1, 32, 0, launch_f64_row<1, 32>, (const void*)field_f64_row_kernel<1, 32>, kF64Smem},
+    {4, 8, 0, launch_f64_row<4, 8>, (const void*)field_f64_row_kernel<4, 8>, f64_row_smem<4>()},
+    {2, 16, 0, launch_f64_row<2, 16>, (const void*)field_f64_row_kernel<2, 16>,
+     f64_row_smem<2>()},
+    {8, 4, 0, launch_f64_row<8, 4>, (const void*)field_f64_row_kernel<8, 4>, f64_row_smem<8>()},
 };
 
 const ShapeEntry* find_shape(int precision, int rb, int cb, int scheme) {

@@ -831,7 +831,8 @@ gbd_status gbd_autotune_field(const gbd_beamlet* beamlets, int32_t n_beamlets, d
                                     {2, 2, GBD_SCHEME_ROW_PAIR}, {2, 4, GBD_SCHEME_ROW_PAIR},
                                     {2, 8, GBD_SCHEME_ROW_PAIR}, {3, 8, GBD_SCHEME_ROW_PAIR},
                                     {4, 8, GBD_SCHEME_ROW_PAIR}, {4, 4, GBD_SCHEME_ROW_PAIR}};
-    static const int kF64[][3] = {{1, 2, 0}, {2, 2, 0}, {1, 8, 0}, {2, 8, 0}, {1, 16, 0}, {1, 32, 0}};
+    static const int kF64[][3] = {{1, 2, 0}, {2, 2, 0}, {1, 8, 0},  {2, 8, 0},
+                                  {1, 16, 0}, {1, 32, 0}, {4, 8, 0}, {2, 16, 0}, {8, 4, 0}};
     std::vector<std::array<int, 3>> shapes;
     if (precision == GBD_PREC_MIXED)
         for (auto& v : kMixed) shapes.push_back({v[0], v[1], v[2]});

@@ -174,6 +174,26 @@ def test_degenerate_detectors(prec, shape):
     assert rel_l2(E, Eo) <= TOL[prec]
 
 
+@pytest.mark.parametrize("rows,cols", [(4, 8), (2, 16), (8, 4)])
+@pytest.mark.parametrize("shape", [(1, 1), (1, 300), (300, 1), (33, 7), (128, 96), (300, 40)])
+def test_fp64_shared_row_recurrence(shape, rows, cols):
+    """The FP64 row segments whose row factors come from a warp table (beamlets without a
+    uv term: the untilted thin-lens system) on one-row, one-column (narrow: the per-row
+    fallback), ragged and wide detectors, against the oracle at the FP64 tolerance."""
+    nx, ny = shape
+    wl = W.Workload("edge", W.System(1e-6, 0.024, 0.024), W.Pupil(2.4e-3, 9, 1.5, 1.5),
+                    W.Detector(nx, ny, 0.9e-6, 1.1e-6))
+    b = gpu_trace(wl)
+    Eo = oracle.field(oracle.trace(wl.system, wl.pupil), wl.system, wl.detector)
+    try:
+        for splits in (1, 3):
+            gbd.gbd_field_set_shape(gbd.GBD_PREC_F64, rows, cols, splits, gbd.GBD_SCHEME_DIRECT)
+            E = gpu_field(b, wl, gbd.GBD_PREC_F64)
+            assert rel_l2(E, Eo) <= TOL[gbd.GBD_PREC_F64], (rows, cols, splits)
+    finally:
+        gbd.gbd_field_reset_shape(gbd.GBD_PREC_F64)
+
+
 @pytest.mark.parametrize("rows,cols", [(3, 8), (4, 4)])
 @pytest.mark.parametrize("shape", [(1, 1), (1, 300), (300, 1), (33, 7)])
 def test_degenerate_detectors_with_row_triples_and_quadruples(shape, rows, cols):
@@ -223,7 +243,8 @@ def test_every_shape_and_split_matches(prec):
     shapes = ([(1, 4, D), (2, 2, D), (2, 4, D), (4, 2, D), (2, 2, P), (2, 4, P), (2, 8, P),
                (3, 8, P), (4, 8, P), (4, 4, P)]
               if prec == gbd.GBD_PREC_MIXED
-              else [(1, 2, D), (2, 2, D), (1, 8, D), (2, 8, D), (1, 16, D), (1, 32, D)])
+              else [(1, 2, D), (2, 2, D), (1, 8, D), (2, 8, D), (1, 16, D), (1, 32, D),
+                    (4, 8, D), (2, 16, D), (8, 4, D)])
     try:
         for rows, cols, scheme in shapes:
             for splits in (1, 2, 5):

@@ -68,7 +68,7 @@ def shapes(prec):
     D, P = gbd.GBD_SCHEME_DIRECT, gbd.GBD_SCHEME_ROW_PAIR
     if prec == gbd.GBD_PREC_MIXED:
         return [None, (2, 4, D), (1, 4, D), (2, 4, P), (2, 8, P), (3, 8, P), (4, 4, P), (4, 8, P)]
-    return [None, (1, 2, D), (2, 2, D), (1, 8, D), (2, 8, D), (1, 32, D)]
+    return [None, (1, 2, D), (2, 2, D), (1, 8, D), (2, 8, D), (1, 32, D), (4, 8, D), (2, 16, D), (8, 4, D)]
 
 
 @pytest.mark.parametrize("prec", PRECS)
