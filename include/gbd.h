@@ -222,8 +222,11 @@ gbd_status gbd_field(const gbd_beamlet* beamlets, int32_t n_beamlets, double wav
  *       1/2 erfc(zeta),  zeta = (n^T M^-1 (rho - rho_c) - d) sqrt(i k / (2 n^T M^-1 B n)),
  *   M = A + B P1 (the Collins integral of the cut Gaussian over its half-plane; principal
  *   root), evaluated through the Faddeeva function (Weideman's rational approximation:
- *   36 terms in FP64, 16 in the mixed path's FP32).  workspace: at least
- *   gbd_field_truncated_workspace_bytes(...) bytes, 256-byte aligned.
+ *   36 terms in FP64, 16 in the mixed path's FP32, where along a row it is Taylor-stepped
+ *   to 4th order from pixel to pixel while the step is short).  The edge beamlets are split
+ *   over CTAs into partial fields added in split order (deterministic).  workspace: at
+ *   least gbd_field_truncated_workspace_bytes(...) bytes, 256-byte aligned (the edge
+ *   records, then the larger of gbd_field's workspace and the edge partial fields).
  * Errors: GBD_EINVAL (bad arguments, margin outside [0, 10], n_edge outside
  *   [0, n_beamlets]), GBD_ENOMEM (capacity or workspace too small), GBD_EUNSUPPORTED (a
  *   tilted detector). */

@@ -752,7 +752,10 @@ size_t gbd_field_truncated_workspace_bytes(int32_t n_beamlets, int32_t n_edge,
         return 0;
     if (precision != GBD_PREC_F64 && precision != GBD_PREC_MIXED) return 0;
     const size_t edge = align256((size_t)n_edge * gbd::kEdgeFields * sizeof(double2));
-    return edge + gbd_field_workspace_bytes(n_beamlets - n_edge, detector, precision);
+    // after the whole beamlets' field, its scratch holds the edge splits' partial fields
+    return edge + std::max(gbd_field_workspace_bytes(n_beamlets - n_edge, detector, precision),
+                           gbd_field_edge_partial_bytes(precision, n_edge, detector->nx,
+                                                        detector->ny));
 }
 
 gbd_status gbd_field_truncated(const gbd_beamlet* beamlets, int32_t n_beamlets, int32_t n_edge,
@@ -768,7 +771,9 @@ gbd_status gbd_field_truncated(const gbd_beamlet* beamlets, int32_t n_beamlets, 
     if (detector->rot_x != 0.0 || detector->rot_y != 0.0)
         return fail(GBD_EUNSUPPORTED, "truncated beamlets are evaluated on untilted planes");
     const size_t edge = align256((size_t)n_edge * gbd::kEdgeFields * sizeof(double2));
-    if (workspace_bytes < edge) return fail(GBD_ENOMEM, "workspace too small for the edge records");
+    if (workspace_bytes < edge + gbd_field_edge_partial_bytes(precision, n_edge, detector->nx,
+                                                             detector->ny))
+        return fail(GBD_ENOMEM, "workspace too small for the edge records and partial fields");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     char* base = static_cast<char*>(workspace);
     st = run_field(beamlets, n_beamlets - n_edge, wavelength, detector, precision, base + edge,
@@ -778,7 +783,8 @@ gbd_status gbd_field_truncated(const gbd_beamlet* beamlets, int32_t n_beamlets, 
     double2* rec = reinterpret_cast<double2*>(base);
     cudaError_t e = gbd_launch_project_edge(beamlets + (n_beamlets - n_edge), n_edge, pp, rec, s);
     if (e == cudaSuccess)
-        e = gbd_launch_field_edge(precision, rec, n_edge, detector->nx, detector->ny, field_out, s);
+        e = gbd_launch_field_edge(precision, rec, n_edge, detector->nx, detector->ny, field_out,
+                                  base + edge, s);
     return e == cudaSuccess ? GBD_OK : cuda_fail(e, "gbd_field_truncated launch");
 }
 

@@ -313,9 +313,12 @@ cudaError_t gbd_launch_trace_truncated(const gbd_trace_params& p, int ext, doubl
                                        cudaStream_t s);
 cudaError_t gbd_launch_project_edge(const gbd_beamlet* b, int n, const gbd_project_params& p,
                                     double2* out, cudaStream_t s);
-// Adds the edge beamlets' sum onto a field of nx x ny pixels (complex64 / complex128).
+// Partial fields of the edge kernel's beamlet splits (bytes, reusable scratch).
+size_t gbd_field_edge_partial_bytes(int precision, int n_edge, int nx, int ny);
+// Adds the edge beamlets' sum onto a field of nx x ny pixels (complex64 / complex128),
+// through per-split partial fields in `partial` (gbd_field_edge_partial_bytes).
 cudaError_t gbd_launch_field_edge(int precision, const double2* edge_records, int n_edge, int nx,
-                                  int ny, void* out, cudaStream_t s);
+                                  int ny, void* out, void* partial, cudaStream_t s);
 // Height of the pixel-row blocks of every kernel a launch runs: a slab that starts on a
 // multiple of it is split into the same thread row blocks as the whole detector.
 int gbd_field_row_block(int precision, const gbd_field_launch& L);

@@ -116,65 +116,119 @@ struct Cplx {
     T x, y;
 };
 
-// The edge beamlets' sum added onto the field, kEdgePix consecutive pixels (row-major
-// order) per thread; the edge records are staged through shared memory (converted to T) 32
-// beamlets at a time, and each thread loads a record once for its pixels.  Per pixel the
-// Faddeeva argument (i zeta or -i zeta) is selected without a branch; the Gaussian term
-// is evaluated only where Re zeta < 0 (neighbouring pixels mostly agree on the sign).
-constexpr int kEdgeChunk = 32, kEdgePix = 4;
-template <typename T, int NW>
+// One Taylor step of w from z to z + h (FP32 path): the derivatives at z follow from
+// w' = -2 z w + 2 i / sqrt(pi) by w^(n+1) = -2 z w^(n) - 2 n w^(n-1); to 4th order the step
+// keeps 4e-7 relative over a segment of 8 steps while |h| (2 |z|_1 + 3) <= 0.2 (checked
+// against a reference Faddeeva function off the device).
+__device__ __forceinline__ void faddeeva_step(float zr, float zi, float hr, float hi, float& wr,
+                                              float& wi) {
+    const float c = 1.12837916709551257390f;  // 2 / sqrt(pi)
+    const float d1r = -2.0f * fmaf(zr, wr, -zi * wi), d1i = fmaf(-2.0f, fmaf(zr, wi, zi * wr), c);
+    const float d2r = fmaf(-2.0f, wr, -2.0f * fmaf(zr, d1r, -zi * d1i));
+    const float d2i = fmaf(-2.0f, wi, -2.0f * fmaf(zr, d1i, zi * d1r));
+    const float d3r = fmaf(-4.0f, d1r, -2.0f * fmaf(zr, d2r, -zi * d2i));
+    const float d3i = fmaf(-4.0f, d1i, -2.0f * fmaf(zr, d2i, zi * d2r));
+    const float d4r = fmaf(-6.0f, d2r, -2.0f * fmaf(zr, d3r, -zi * d3i));
+    const float d4i = fmaf(-6.0f, d2i, -2.0f * fmaf(zr, d3i, zi * d3r));
+    // Horner in h: w + h (d1 + h/2 (d2 + h/3 (d3 + h/4 d4)))
+    float ar = d4r, ai = d4i, tr;
+    tr = fmaf(0.25f * hr, ar, fmaf(-0.25f * hi, ai, d3r));
+    ai = fmaf(0.25f * hr, ai, fmaf(0.25f * hi, ar, d3i));
+    ar = tr;
+    const float third = 0.333333343f;
+    tr = fmaf(third * hr, ar, fmaf(-third * hi, ai, d2r));
+    ai = fmaf(third * hr, ai, fmaf(third * hi, ar, d2i));
+    ar = tr;
+    tr = fmaf(0.5f * hr, ar, fmaf(-0.5f * hi, ai, d1r));
+    ai = fmaf(0.5f * hr, ai, fmaf(0.5f * hi, ar, d1i));
+    ar = tr;
+    tr = fmaf(hr, ar, fmaf(-hi, ai, wr));
+    wi = fmaf(hr, ai, fmaf(hi, ar, wi));
+    wr = tr;
+}
+
+// The edge beamlets' sum over split blockIdx.y (beamlets [y per_split, (y + 1) per_split))
+// into that split's partial field.  A thread takes kEdgePix consecutive pixels of one row;
+// the edge records are staged through shared memory (converted to T) 32 beamlets at a time.  Per beamlet the quadratic forms' row terms are formed once for
+// the thread's row (then 2 FMA per form and pixel, zeta 1 FMA).  The Faddeeva argument
+// (i zeta or -i zeta, whichever lies in the upper half-plane) is selected without a
+// branch; STEP (the FP32 path): w is evaluated exactly at the segment's first pixel,
+// where the sign of Re zeta changes, and where the step is too long for the Taylor step,
+// and Taylor-stepped from the previous pixel otherwise.  The Gaussian term is evaluated
+// only where Re zeta < 0 (neighbouring pixels mostly agree on the sign).
+constexpr int kEdgeChunk = 32, kEdgePix = 8;
+template <typename T, int NW, bool STEP>
 __global__ void __launch_bounds__(256) field_edge_kernel(const double2* __restrict__ rec,
-                                                         int n_edge, int nx, int ny,
-                                                         FaddeevaT<T, NW> F,
-                                                         Cplx<T>* __restrict__ out) {
+                                                         int n_edge, int per_split, int nx,
+                                                         int ny, FaddeevaT<T, NW> F,
+                                                         Cplx<T>* __restrict__ partial) {
     __shared__ __align__(16) T s[kEdgeChunk][2 * gbd::kEdgeFields];
-    const long long npix = (long long)nx * ny;
-    const long long p0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * kEdgePix;
-    T pu[kEdgePix], pv[kEdgePix], accr[kEdgePix], acci[kEdgePix];
+    const int segs_x = (nx + kEdgePix - 1) / kEdgePix;
+    const long long seg = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = seg < (long long)segs_x * ny;
+    const int row = live ? (int)(seg / segs_x) : 0;
+    const int col0 = live ? (int)(seg % segs_x) * kEdgePix : 0;
+    T accr[kEdgePix], acci[kEdgePix];
 #pragma unroll
-    for (int c = 0; c < kEdgePix; ++c) {
-        const long long p = min(p0 + c, npix - 1);
-        pu[c] = (T)(p % nx);
-        pv[c] = (T)(p / nx);
-        accr[c] = acci[c] = (T)0;
-    }
-    for (int b0 = 0; b0 < n_edge; b0 += kEdgeChunk) {
+    for (int c = 0; c < kEdgePix; ++c) accr[c] = acci[c] = (T)0;
+    const int b_lo = blockIdx.y * per_split, b_hi = min(n_edge, b_lo + per_split);
+    for (int b0 = b_lo; b0 < b_hi; b0 += kEdgeChunk) {
         __syncthreads();
         for (int q = threadIdx.x; q < kEdgeChunk * gbd::kEdgeFields; q += blockDim.x) {
             const int bb = b0 + q / gbd::kEdgeFields, f = q % gbd::kEdgeFields;
-            const double2 v = bb < n_edge ? rec[(size_t)bb * gbd::kEdgeFields + f]
-                                          : make_double2(0.0, 0.0);
+            const double2 v = bb < b_hi ? rec[(size_t)bb * gbd::kEdgeFields + f]
+                                        : make_double2(0.0, 0.0);
             s[q / gbd::kEdgeFields][2 * f] = (T)v.x;
             s[q / gbd::kEdgeFields][2 * f + 1] = (T)v.y;
         }
         __syncthreads();
-        const int nb = min(kEdgeChunk, n_edge - b0);
+        const int nb = min(kEdgeChunk, b_hi - b0);
         for (int b = 0; b < nb; ++b) {
-            T r[2 * gbd::kEdgeFields];
-#pragma unroll
-            for (int m = 0; m < 2 * gbd::kEdgeFields; ++m) r[m] = s[b][m];
+            const T* r = s[b];
+            const T tu0 = (T)col0 - r[0], tv = (T)row - r[1];
+            // row terms: form(tu) = A + tu (B + C tu)
+            const T eA = fma(tv, fma(r[12], tv, r[6]), r[2]), eB = fma(r[10], tv, r[4]);
+            const T pA = fma(tv, fma(r[13], tv, r[7]), r[3]), pB = fma(r[11], tv, r[5]);
+            const T gA = fma(tv, fma(r[30], tv, r[24]), r[20]), gB = fma(r[28], tv, r[22]);
+            const T qA = fma(tv, fma(r[31], tv, r[25]), r[21]), qB = fma(r[29], tv, r[23]);
+            const T zr0 = fma(r[18], tv, r[14]), zi0 = fma(r[19], tv, r[15]);
+            T wr = (T)0, wi = (T)0, xpr = (T)0, xpi = (T)0;
+            bool pneg = false;
 #pragma unroll
             for (int c = 0; c < kEdgePix; ++c) {
-                const T tu = pu[c] - r[0], tv = pv[c] - r[1];
-                const T tuu = tu * tu, tuv = tu * tv, tvv = tv * tv;
-                const T zr = r[14] + r[16] * tu + r[18] * tv;
-                const T zi = r[15] + r[17] * tu + r[19] * tv;
+                const T tu = tu0 + (T)c;
+                const T zr = fma(r[16], tu, zr0), zi = fma(r[17], tu, zi0);
                 const bool neg = zr < (T)0;
                 // i zeta = (-zi, zr); -i zeta = (zi, -zr): the one in the upper half-plane
-                T wr, wi;
-                faddeeva<T, NW>(neg ? zi : -zi, neg ? -zr : zr, F, wr, wi);
-                const T ga = r[20] + r[22] * tu + r[24] * tv + r[26] * tuu + r[28] * tuv + r[30] * tvv;
-                const T gp = r[21] + r[23] * tu + r[25] * tv + r[27] * tuu + r[29] * tuv + r[31] * tvv;
+                const T xr = neg ? zi : -zi, xi = neg ? -zr : zr;
+                bool exact = true;
+                T hr = (T)0, hi = (T)0;
+                if constexpr (STEP) {
+                    if (c > 0 && neg == pneg) {
+                        hr = xr - xpr;
+                        hi = xi - xpi;
+                        const T m = fabs(hr) + fabs(hi), zz = fabs(xpr) + fabs(xpi);
+                        exact = !(m * fma((T)2, zz, (T)3) <= (T)0.2);
+                    }
+                }
+                if (exact) {
+                    faddeeva<T, NW>(xr, xi, F, wr, wi);
+                } else {
+                    if constexpr (STEP) faddeeva_step(xpr, xpi, hr, hi, wr, wi);
+                }
+                xpr = xr;
+                xpi = xi;
+                pneg = neg;
+                const T ga = fma(tu, fma(r[26], tu, gB), gA);
+                const T gp = fma(tu, fma(r[27], tu, qB), qA);
                 T gc, gs;
                 cis_turns(gp, gc, gs);
                 const T gm = pow2(ga);
                 T tr = gm * (gc * wr - gs * wi), ti = gm * (gc * wi + gs * wr);
                 if (neg) {
                     // where Re zeta < 0 the cut field is E - e^Psi w(-i zeta)
-                    const T ea = r[2] + r[4] * tu + r[6] * tv + r[8] * tuu + r[10] * tuv +
-                                 r[12] * tvv;
-                    const T ep = r[3] + r[5] * tu + r[7] * tv + r[9] * tuu + r[11] * tuv +
-                                 r[13] * tvv;
+                    const T ea = fma(tu, fma(r[8], tu, eB), eA);
+                    const T ep = fma(tu, fma(r[9], tu, pB), pA);
                     T ec, es;
                     cis_turns(ep, ec, es);
                     const T em = pow2(ea);
@@ -186,30 +240,72 @@ __global__ void __launch_bounds__(256) field_edge_kernel(const double2* __restri
             }
         }
     }
+    if (!live) return;
+    Cplx<T>* part = partial + (size_t)blockIdx.y * nx * ny + (size_t)row * nx + col0;
 #pragma unroll
     for (int c = 0; c < kEdgePix; ++c) {
-        if (p0 + c >= npix) break;
-        Cplx<T> o = out[p0 + c];
-        o.x += accr[c];
-        o.y += acci[c];
-        out[p0 + c] = o;
+        if (col0 + c >= nx) break;
+        part[c] = Cplx<T>{accr[c], acci[c]};
     }
+}
+
+// out += the splits' partial fields, added in split order.
+template <typename T>
+__global__ void __launch_bounds__(256) field_edge_reduce_kernel(const Cplx<T>* __restrict__ partial,
+                                                                int splits, long long npix,
+                                                                Cplx<T>* __restrict__ out) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npix) return;
+    T sx = partial[p].x, sy = partial[p].y;
+    for (int k = 1; k < splits; ++k) {
+        sx += partial[(size_t)k * npix + p].x;
+        sy += partial[(size_t)k * npix + p].y;
+    }
+    out[p].x += sx;
+    out[p].y += sy;
+}
+
+// Beamlet splits of the edge kernel: about 8 CTAs per SM in all (each thread walks its
+// split's beamlets serially), at least 64 beamlets per split.
+int edge_splits(int n_edge, int nx, int ny) {
+    const long long segs = (long long)((nx + kEdgePix - 1) / kEdgePix) * ny;
+    const long long pix_ctas = (segs + 255) / 256;
+    long long want = (8LL * 152 + pix_ctas - 1) / pix_ctas;
+    const long long cap = (n_edge + 63) / 64;
+    if (want > cap) want = cap;
+    return want < 1 ? 1 : (int)want;
 }
 
 }  // namespace
 
+size_t gbd_field_edge_partial_bytes(int precision, int n_edge, int nx, int ny) {
+    if (n_edge <= 0) return 0;
+    const size_t elem = precision == GBD_PREC_F64 ? sizeof(Cplx<double>) : sizeof(Cplx<float>);
+    return (size_t)edge_splits(n_edge, nx, ny) * nx * ny * elem;
+}
+
 cudaError_t gbd_launch_field_edge(int precision, const double2* edge_records, int n_edge, int nx,
-                                  int ny, void* out, cudaStream_t s) {
+                                  int ny, void* out, void* partial, cudaStream_t s) {
     if (n_edge <= 0) return cudaSuccess;
+    const int splits = edge_splits(n_edge, nx, ny);
+    const int per = (n_edge + splits - 1) / splits;
+    const int per_split = (per + kEdgeChunk - 1) / kEdgeChunk * kEdgeChunk;
+    const long long segs = (long long)((nx + kEdgePix - 1) / kEdgePix) * ny;
+    const dim3 grid((unsigned)((segs + 255) / 256), (unsigned)splits);
     const long long npix = (long long)nx * ny;
-    const unsigned blocks = (unsigned)((npix + 256LL * kEdgePix - 1) / (256LL * kEdgePix));
-    if (precision == GBD_PREC_F64)
-        field_edge_kernel<double, 36><<<blocks, 256, 0, s>>>(
-            edge_records, n_edge, nx, ny, faddeeva_table<double, 36>(),
-            static_cast<Cplx<double>*>(out));
-    else
-        field_edge_kernel<float, 16><<<blocks, 256, 0, s>>>(
-            edge_records, n_edge, nx, ny, faddeeva_table<float, 16>(),
-            static_cast<Cplx<float>*>(out));
+    const unsigned rblocks = (unsigned)((npix + 255) / 256);
+    if (precision == GBD_PREC_F64) {
+        field_edge_kernel<double, 36, false><<<grid, 256, 0, s>>>(
+            edge_records, n_edge, per_split, nx, ny, faddeeva_table<double, 36>(),
+            static_cast<Cplx<double>*>(partial));
+        field_edge_reduce_kernel<double><<<rblocks, 256, 0, s>>>(
+            static_cast<const Cplx<double>*>(partial), splits, npix, static_cast<Cplx<double>*>(out));
+    } else {
+        field_edge_kernel<float, 16, true><<<grid, 256, 0, s>>>(
+            edge_records, n_edge, per_split, nx, ny, faddeeva_table<float, 16>(),
+            static_cast<Cplx<float>*>(partial));
+        field_edge_reduce_kernel<float><<<rblocks, 256, 0, s>>>(
+            static_cast<const Cplx<float>*>(partial), splits, npix, static_cast<Cplx<float>*>(out));
+    }
     return cudaGetLastError();
 }
