@@ -143,3 +143,20 @@ def test_truncated_edge_cases():
         gbd.gbd_trace_truncated(wl.system, pupil, pupil.overlap_factor, pupil.waist_ratio, 3.0,
                                 small)
     assert ei.value.status == gbd.GBD_ENOMEM
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_truncated_field_is_deterministic_and_split_sized(prec):
+    """The edge beamlets are split over CTAs into partial fields added in split order: two
+    evaluations give the same bits; a detector of 333 x 7 pixels (ragged 8-pixel row
+    segments, many splits per pixel block) still matches the oracle."""
+    wl = W.scaled(W.airy_small(), nx=333, ny=7)
+    b, ne = gbd.trace_truncated(wl.system, wl.pupil)
+    E1 = gbd.field_truncated(b, ne, wl.system.wavelength, wl.detector, prec)
+    E2 = gbd.field_truncated(b, ne, wl.system.wavelength, wl.detector, prec)
+    gbd.gbd_sync()
+    assert np.array_equal(E1.cpu().numpy(), E2.cpu().numpy())
+    o, dist, _ = oracle.trace_truncated(wl.system, wl.pupil)
+    Eo = oracle.field_truncated(o, dist, wl.system, wl.detector)
+    err = rel_l2(E1.cpu().numpy().astype(np.complex128), Eo)
+    assert err <= TOL[prec], err
