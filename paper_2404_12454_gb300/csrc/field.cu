@@ -1099,9 +1099,13 @@ cudaError_t gbd_launch_field_reduce(int precision, const gbd_project_params& p,
     return cudaGetLastError();
 }
 
-unsigned gbd_field_status_read_clear() {
-    unsigned v = 0, zero = 0;
-    if (cudaMemcpyFromSymbol(&v, g_field_status, sizeof(v)) != cudaSuccess) return 0;
-    if (v) cudaMemcpyToSymbol(g_field_status, &zero, sizeof(zero));
-    return v;
+// The status word: copied into pinned host memory on the caller's stream (gbd_sync), and
+// cleared once it has been reported.
+cudaError_t gbd_field_status_fetch(unsigned* host, cudaStream_t s) {
+    return cudaMemcpyFromSymbolAsync(host, g_field_status, sizeof(unsigned), 0,
+                                     cudaMemcpyDeviceToHost, s);
+}
+void gbd_field_status_clear() {
+    const unsigned zero = 0;
+    cudaMemcpyToSymbol(g_field_status, &zero, sizeof(zero));
 }

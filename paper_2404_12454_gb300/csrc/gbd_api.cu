@@ -562,19 +562,40 @@ int32_t gbd_beamlet_count(const gbd_pupil* pupil) {
     for (long long j = 0; j < N; ++j) {
         const long long b = 2 * j - (N - 1);
         const long long r2 = N * N - b * b;
-        // odd/even values a = 2i - (N-1) with a^2 <= r2
-        for (long long a = -(N - 1); a <= N - 1; a += 2)
-            if (a * a <= r2) ++count;
+        // the values a = 2i - (N-1), i = 0 .. N-1, with a^2 <= r2, i.e. |a| <= m = isqrt(r2):
+        // i from ceil((N-1-m)/2) to floor((N-1+m)/2), within [0, N-1]
+        long long m = (long long)sqrt((double)r2);
+        while (m * m > r2) --m;
+        while ((m + 1) * (m + 1) <= r2) ++m;
+        const long long lo = N - 1 - m <= 0 ? 0 : (N - m) / 2;
+        const long long hi = std::min(N - 1, (N - 1 + m) / 2);
+        if (hi >= lo) count += hi - lo + 1;
     }
     return (int32_t)count;
 }
 
 gbd_status gbd_sync(void* stream) {
-    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    // the four translation units' status words are copied into pinned host memory behind
+    // the stream's work, so one synchronisation covers the work and the status
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    thread_local unsigned* h = nullptr;
+    if (!h && cudaMallocHost(reinterpret_cast<void**>(&h), 4 * sizeof(unsigned)) != cudaSuccess) {
+        h = nullptr;
+        return cuda_fail(cudaGetLastError(), "gbd_sync status buffer");
+    }
+    cudaError_t e = gbd_field_status_fetch(h, s);
+    if (e == cudaSuccess) e = gbd_sweep_status_fetch(h + 1, s);
+    if (e == cudaSuccess) e = gbd_point_status_fetch(h + 2, s);
+    if (e == cudaSuccess) e = gbd_mlp_status_fetch(h + 3, s);
+    const cudaError_t es = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = es;
     if (e != cudaSuccess) return cuda_fail(e, "gbd_sync");
-    unsigned st = gbd_field_status_read_clear() | gbd_sweep_status_read_clear() |
-                  gbd_point_status_read_clear() | gbd_mlp_status_read_clear();
-    if (st & gbd::kStatusTimeout) return fail(GBD_ETIMEOUT, "a device wait gave up (timeout)");
+    if (h[0]) gbd_field_status_clear();
+    if (h[1]) gbd_sweep_status_clear();
+    if (h[2]) gbd_point_status_clear();
+    if (h[3]) gbd_mlp_status_clear();
+    if ((h[0] | h[1] | h[2] | h[3]) & gbd::kStatusTimeout)
+        return fail(GBD_ETIMEOUT, "a device wait gave up (timeout)");
     return GBD_OK;
 }
 

@@ -336,9 +336,12 @@ gbd_project_params gbd_make_project_params(double wavelength, const gbd_detector
 gbd_trace_params gbd_make_trace_params(const gbd_system* system, double diameter);
 int gbd_sm_count();
 uint32_t gbd_wait_spins();
-unsigned gbd_sweep_status_read_clear();
-unsigned gbd_point_status_read_clear();
-unsigned gbd_mlp_status_read_clear();
+cudaError_t gbd_sweep_status_fetch(unsigned* host, cudaStream_t s);
+void gbd_sweep_status_clear();
+cudaError_t gbd_point_status_fetch(unsigned* host, cudaStream_t s);
+void gbd_point_status_clear();
+cudaError_t gbd_mlp_status_fetch(unsigned* host, cudaStream_t s);
+void gbd_mlp_status_clear();
 long gbd_point_pixel_ctas(int nx, int ny);
 int gbd_point_occupancy();
 // Point evaluation: packs the beamlets into `coeffs` (FP64 tiles) and launches the
@@ -351,5 +354,6 @@ gbd_status gbd_field_fixed_scratch(const gbd_beamlet* beamlets, int32_t n, doubl
                                    void* scratch, size_t scratch_bytes, void* out,
                                    cudaStream_t stream);
 bool gbd_field_shape_supported(int precision, int rb, int cb, int scheme);
-unsigned gbd_field_status_read_clear();
+cudaError_t gbd_field_status_fetch(unsigned* host, cudaStream_t s);
+void gbd_field_status_clear();
 cudaError_t gbd_run_probes(double* out);

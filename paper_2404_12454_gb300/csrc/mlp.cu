@@ -1110,11 +1110,15 @@ gbd_status launch_steps(StepArgs& a, int resident, cudaStream_t s) {
 
 }  // namespace
 
-unsigned gbd_mlp_status_read_clear() {
-    unsigned v = 0, zero = 0;
-    if (cudaMemcpyFromSymbol(&v, g_mlp_status, sizeof(v)) != cudaSuccess) return 0;
-    if (v) cudaMemcpyToSymbol(g_mlp_status, &zero, sizeof(zero));
-    return v;
+// The status word: copied into pinned host memory on the caller's stream (gbd_sync), and
+// cleared once it has been reported.
+cudaError_t gbd_mlp_status_fetch(unsigned* host, cudaStream_t s) {
+    return cudaMemcpyFromSymbolAsync(host, g_mlp_status, sizeof(unsigned), 0,
+                                     cudaMemcpyDeviceToHost, s);
+}
+void gbd_mlp_status_clear() {
+    const unsigned zero = 0;
+    cudaMemcpyToSymbol(g_mlp_status, &zero, sizeof(zero));
 }
 
 extern "C" {

@@ -185,9 +185,13 @@ cudaError_t gbd_launch_point(const gbd_beamlet* b, int n, const gbd_project_para
     return cudaGetLastError();
 }
 
-unsigned gbd_point_status_read_clear() {
-    unsigned v = 0, zero = 0;
-    if (cudaMemcpyFromSymbol(&v, g_point_status, sizeof(v)) != cudaSuccess) return 0;
-    if (v) cudaMemcpyToSymbol(g_point_status, &zero, sizeof(zero));
-    return v;
+// The status word: copied into pinned host memory on the caller's stream (gbd_sync), and
+// cleared once it has been reported.
+cudaError_t gbd_point_status_fetch(unsigned* host, cudaStream_t s) {
+    return cudaMemcpyFromSymbolAsync(host, g_point_status, sizeof(unsigned), 0,
+                                     cudaMemcpyDeviceToHost, s);
+}
+void gbd_point_status_clear() {
+    const unsigned zero = 0;
+    cudaMemcpyToSymbol(g_point_status, &zero, sizeof(zero));
 }

@@ -567,11 +567,15 @@ struct gbd_sweep_plan {
     int graph_device = -1;     // device whose SM count and occupancy sized its grid
 };
 
-unsigned gbd_sweep_status_read_clear() {
-    unsigned v = 0, zero = 0;
-    if (cudaMemcpyFromSymbol(&v, g_sweep_status, sizeof(v)) != cudaSuccess) return 0;
-    if (v) cudaMemcpyToSymbol(g_sweep_status, &zero, sizeof(zero));
-    return v;
+// The status word: copied into pinned host memory on the caller's stream (gbd_sync), and
+// cleared once it has been reported.
+cudaError_t gbd_sweep_status_fetch(unsigned* host, cudaStream_t s) {
+    return cudaMemcpyFromSymbolAsync(host, g_sweep_status, sizeof(unsigned), 0,
+                                     cudaMemcpyDeviceToHost, s);
+}
+void gbd_sweep_status_clear() {
+    const unsigned zero = 0;
+    cudaMemcpyToSymbol(g_sweep_status, &zero, sizeof(zero));
 }
 
 static gbd_status sweep_enqueue(gbd_sweep_plan* P, double* scores, cudaStream_t s) {

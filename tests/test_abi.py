@@ -50,6 +50,18 @@ def test_version_and_beamlet_count(lib):
     assert gbd.gbd_beamlet_count(W.Pupil(2.4e-3, 0, 1.5, 1.5)) == -1
 
 
+def test_beamlet_count_equals_brute_force(lib):
+    """The per-row closed count (integer square roots) against the plain double loop over
+    the grid's inside-test (2i-(N-1))^2 + (2j-(N-1))^2 <= N^2, for every N up to 600."""
+    for n in range(1, 601):
+        want = 0
+        for j in range(n):
+            b = 2 * j - (n - 1)
+            a = [2 * i - (n - 1) for i in range(n)]
+            want += sum(1 for x in a if x * x + b * b <= n * n)
+        assert gbd.gbd_beamlet_count(W.Pupil(2.4e-3, n, 1.5, 1.5)) == want, n
+
+
 def _einval(call):
     with pytest.raises(gbd.GbdError) as ei:
         call()
