@@ -263,6 +263,11 @@ gbd_shape stored_shape(int precision, const gbd_detector* D) {
         s.cols_per_thread = auto_cols(D->nx);
         s.rows_per_thread = s.cols_per_thread == 8 ? 3 : 2;
     }
+    // FP64: 1 x 32 row segments on detectors 256 pixels wide or more (airy_large 335 ms
+    // against 405 ms for 1 x 16; on fields with a uv term the fastest shape too); the
+    // row-band shapes (8 x 4: 202 ms without a uv term, 2.6x slower with one) are left to
+    // the autotuner, which sees the beamlets
+    if (precision == GBD_PREC_F64 && D && D->nx >= 256) s.cols_per_thread = 32;
     return s;
 }
 
