@@ -184,8 +184,8 @@ gbd_status gbd_trace_mirrors(const gbd_mirror_system* system, const gbd_pupil* p
  *   reduced exactly first when some beamlet's phase can exceed 128 rad on the detector).
  *   With the row-pair scheme (see gbd_shape) only one row of each pair 8 apart is
  *   evaluated so; the row 8 below is that value times the beamlet's exact 8-row step
- *   factor (an FP32 complex multiply); with row triples (the default, for fields
- *   without a uv term) or quadruples also the rows 16 (and 24) below, by the next step
+ *   factor (an FP32 complex multiply); with row quadruples (the default, for fields
+ *   without a uv term) or triples also the rows 16 and 24 (16) below, by the next step
  *   factors.  The sum runs in FP32 64-beamlet chunks combined with compensated (TwoSum)
  *   accumulation (row triples and quadruples: in FP32 over the whole beamlet split, which
  *   then holds at most 1,024 beamlets); beamlet
@@ -316,14 +316,16 @@ gbd_status gbd_field_point(const gbd_beamlet* beamlets, int32_t n_beamlets, doub
  * (mixed) evaluation scheme.  Unless a shape was set for the current device with
  * gbd_field_set_shape (NULL restores this default), gbd_field uses 8, 4 or 2 columns per
  * thread, whichever covers the detector's width at the least estimated cost (8 for widths
- * that are multiples of 256), as row triples (3x8) or row pairs (2x4, 2x2), or 1x16 row
- * segments (F64), with splits from a built-in heuristic; gbd_autotune_field times the
+ * that are multiples of 256), as row quadruples (4x8) or row pairs (2x4, 2x2), or row
+ * segments (F64: 1x32 on detectors 256 or more pixels wide, else 1x16), with splits from a built-in heuristic; gbd_autotune_field times the
  * candidate shapes on the given problem (synchronously, with CUDA events) and keeps the
  * fastest. */
 typedef struct {
     int32_t rows_per_thread;   /* mixed: 1x4, 2x2, 2x4, 4x2 (columns 32 apart);   */
     int32_t cols_per_thread;   /* F64: 1x2, 2x2 (direct), 1x8, 2x8, 1x16, 1x32   */
-                               /* (contiguous row segments, complex recurrence)   */
+                               /* (contiguous row segments, complex recurrence),  */
+                               /* 2x16, 4x8, 8x4 (row bands: no-uv beamlets as    */
+                               /* X(u) Y(v), Y from a per-warp table)             */
     int32_t splits;            /* beamlet splits (0 = heuristic)             */
     float   ms;                /* measured time of the shape (autotune)      */
     int32_t scheme;            /* mixed only: GBD_SCHEME_DIRECT, or           */

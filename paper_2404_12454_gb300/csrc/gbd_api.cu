@@ -221,7 +221,7 @@ size_t tile_bytes(int precision) {
 
 gbd_shape default_shape(int precision) {
     gbd_shape s;
-    s.rows_per_thread = precision == GBD_PREC_MIXED ? 3 : 1;
+    s.rows_per_thread = precision == GBD_PREC_MIXED ? 4 : 1;
     s.cols_per_thread = precision == GBD_PREC_MIXED ? 8 : 16;
     s.splits = 0;
     s.ms = 0.f;
@@ -250,7 +250,7 @@ int auto_cols(int nx, int min_cols = 2) {
 }
 
 // The shape set for this device and precision, else the default (for the mixed path with
-// its columns per thread fitted to the detector's width: row triples on 8 columns, which
+// its columns per thread fitted to the detector's width: row quadruples on 8 columns, which
 // run the 2 x 8 row pairs themselves for the fields they cannot take, else row pairs).
 gbd_shape stored_shape(int precision, const gbd_detector* D) {
     {
@@ -260,8 +260,10 @@ gbd_shape stored_shape(int precision, const gbd_detector* D) {
     }
     gbd_shape s = default_shape(precision);
     if (precision == GBD_PREC_MIXED && D) {
+        // 8 columns: the row quadruples in packed FP32x2 (airy_large 2.85 ms against 2.99
+        // for the row triples); fields with a uv term fall back to the row pairs either way
         s.cols_per_thread = auto_cols(D->nx);
-        s.rows_per_thread = s.cols_per_thread == 8 ? 3 : 2;
+        s.rows_per_thread = s.cols_per_thread == 8 ? 4 : 2;
     }
     // FP64: 1 x 32 row segments on detectors 256 pixels wide or more (airy_large 335 ms
     // against 405 ms for 1 x 16; on fields with a uv term the fastest shape too); the
