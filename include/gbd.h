@@ -184,9 +184,10 @@ gbd_status gbd_trace_mirrors(const gbd_mirror_system* system, const gbd_pupil* p
  *   reduced exactly first when some beamlet's phase can exceed 128 rad on the detector).
  *   With the row-pair scheme (see gbd_shape) only one row of each pair 8 apart is
  *   evaluated so; the row 8 below is that value times the beamlet's exact 8-row step
- *   factor (an FP32 complex multiply); with row quadruples (the default, for fields
- *   without a uv term) or triples also the rows 16 and 24 (16) below, by the next step
- *   factors.  The sum runs in FP32 64-beamlet chunks combined with compensated (TwoSum)
+ *   factor (an FP32 complex multiply); with row quadruples (the default) or triples also
+ *   the rows 16 and 24 (16) below, by the next step factors (with a uv term: times the
+ *   column's power W^r of the uv factor, stepped along the row; on row triples behind
+ *   a 4x8 pick).  The sum runs in FP32 64-beamlet chunks combined with compensated (TwoSum)
  *   accumulation (row triples and quadruples: in FP32 over the whole beamlet split, which
  *   then holds at most 1,024 beamlets); beamlet
  *   splits are rounded once to FP32 and summed in split order with Neumaier's
@@ -255,7 +256,7 @@ gbd_status gbd_field_truncated(const gbd_beamlet* beamlets, int32_t n_beamlets, 
  *     row 0 = detector row row_begin; device memory owned by the caller.
  *   workspace: at least gbd_field_rows_workspace_bytes(...) bytes, 256-byte aligned (the
  *     split partial fields cover only the slab, rounded down at its start to the launch's
- *     row-block height of at most 48 rows).
+ *     row-block height of at most 96 rows).
  * The launch (shape, splits) and the projection's kernel selection are those gbd_field
  * takes on the whole detector, and every pixel of the slab is computed by the same thread
  * row block, so the slab equals the same rows of gbd_field's output bit for bit, for any
@@ -332,9 +333,9 @@ typedef struct {
                                /* GBD_SCHEME_ROW_PAIR (2x2, 2x4, 2x8: the     */
                                /* second row from the first by a complex      */
                                /* factor; 3x8, 4x8, 4x4: row triples and      */
-                               /* quadruples,                                 */
-                               /* for fields without a uv term and splits of  */
-                               /* at most 16 tiles, the 2 x cols row pairs    */
+                               /* quadruples, for splits of at most 16 tiles  */
+                               /* and fields whose 24-row amplitude step      */
+                               /* stays within 2^64, the 2 x cols row pairs   */
                                /* otherwise)                                  */
 } gbd_shape;
 

@@ -295,7 +295,8 @@ __device__ __forceinline__ void reduce_store(const ReduceOut& ro, int nx, int ro
 namespace {
 
 // Row triples or quadruples on RB x CB pixels per thread (rows 8 apart, columns 32
-// apart) for fields without a uv term (mixed_tile_rows).  The sums stay in FP32 registers
+// apart): without a uv term mixed_tile_rows (or its packed form), with one (CROSS)
+// mixed_tile_rows_cross with the per-column row factors.  The sums stay in FP32 registers
 // over the whole split, so the launch requires short splits (at most kRowsMaxTiles tiles
 // = 1,024 beamlets); the reduction sums the splits with compensation.  Dynamic shared
 // memory: the kStages record stages, then each warp's row terms of the current tile.
@@ -307,7 +308,7 @@ namespace {
 // (the reduction kernel's arithmetic, so the bits are the same), applies the tilted plane's
 // carrier and writes the field rows of the output window.  No CTA waits for another.
 constexpr int kRowsMaxTiles = 16;
-template <int RB, int CB>
+template <int RB, int CB, bool CROSS = false>
 __global__ void __launch_bounds__(kThreads, 2)
     field_mixed_rows_kernel(const float4* __restrict__ coef, int n_tiles, int tiles_per_split,
                             int nx, int ny, float2* __restrict__ partial,
@@ -323,7 +324,8 @@ __global__ void __launch_bounds__(kThreads, 2)
     __shared__ int flag;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    float4* ent = dyn4 + kStages * kTileF4 + warp * (gbd::kRowsF4 * gbd::kTile);
+    constexpr int kEntF4 = CROSS ? gbd::kRowsCrossF4 : gbd::kRowsF4;
+    float4* ent = dyn4 + kStages * kTileF4 + warp * (kEntF4 * gbd::kTile);
     const int split = blockIdx.x, bx = blockIdx.y, by = blockIdx.z;
     const int t0 = split * tiles_per_split;
     gbd::init_stream_barriers(full, empty, tid);
@@ -352,12 +354,17 @@ __global__ void __launch_bounds__(kThreads, 2)
             break;
         }
         __syncwarp();  // every lane is done with the previous tile's row terms
-        gbd::mixed_rows_terms<RB>(ts.tile(k), rowf, ent, lane);
+        if constexpr (CROSS)
+            gbd::mixed_rows_cross_terms<RB>(ts.tile(k), rowf, ent, lane);
+        else
+            gbd::mixed_rows_terms<RB>(ts.tile(k), rowf, ent, lane);
         __syncwarp();
         // packed FP32x2 arithmetic where it pays: on airy_large the 4 x 8 shape (2 CTAs per
         // SM) ran 2.85 ms with it against 3.02 without; 4 x 4 (2.92 -> 3.00 ms) and 3 x 8
         // (2.99 -> 3.30 ms) are faster with scalar instructions
-        if constexpr (RB == 4 && CB == 8)
+        if constexpr (CROSS)
+            gbd::mixed_tile_rows_cross<RB, CB>(ent, colf, acc);
+        else if constexpr (RB == 4 && CB == 8)
             gbd::mixed_tile_rows_x2<RB, CB>(ent, colf, acc);
         else
             gbd::mixed_tile_rows<RB, CB>(ent, colf, acc);
@@ -438,10 +445,15 @@ __global__ void __launch_bounds__(kThreads, 2)
 // The flag bits that hand a field from the multi-row kernels to the row pairs.
 constexpr unsigned kRowsNarrow = gbd::kFlagWide | gbd::kFlagSteep | gbd::kFlagColSteep |
                                  gbd::kFlagCross | gbd::kFlagSteepRows;
+// The bits that hand it to the row pairs whether or not it has a uv term (the multi-row
+// kernels store the field themselves when these are all clear).
+constexpr unsigned kRowsTaken = kRowsNarrow & ~gbd::kFlagCross;
 
+template <bool CROSS = false>
 constexpr size_t rows_smem_bytes() {
     return (size_t)kStages * gbd::kMixedTileBytes +
-           (size_t)kWarps * gbd::kRowsF4 * gbd::kTile * sizeof(float4);
+           (size_t)kWarps * (CROSS ? gbd::kRowsCrossF4 : gbd::kRowsF4) * gbd::kTile *
+               sizeof(float4);
 }
 
 template <int CB>
@@ -886,9 +898,9 @@ cudaError_t launch_f64_row(const void* coeffs, int n_tiles, const gbd_project_pa
 
 // Row pairs on 2 x CB pixels with shared-memory compensation; the direct 2 x 4 kernels (on
 // their own pixel grid, same splits) are the steep-beamlet fallback.
-// With `after_triple` the row-triple (or quadruple) kernel has been launched first and
-// takes the fields with neither a uv term nor multi-row steepness; the narrow row pairs
-// with the column factor's update (exact for T = 1 as well) then take the rest.
+// With `after_triple` the row-triple (or quadruple) kernels have been launched first and
+// take the fields without multi-row steepness, with or without a uv term; the narrow row
+// pairs with the column factor's update (exact for T = 1 as well) then take the rest.
 template <int CB>
 cudaError_t launch_pair_set(const void* coeffs, int n_tiles, const gbd_project_params& p,
                             const gbd_field_launch& L, void* partial_v, const unsigned* flags,
@@ -912,14 +924,15 @@ cudaError_t launch_pair_set(const void* coeffs, int n_tiles, const gbd_project_p
     const float4* c = static_cast<const float4*>(coeffs);
     const int tps = L.tiles_per_split;
     (void)kBoth;
-    // exactly one runs: narrow without a uv term (unless the multi-row kernel ran), narrow
-    // with one, then wide (or column-steep), then the steep fallback
+    // exactly one runs: narrow without a uv term (unless the multi-row kernels ran), narrow
+    // with one (after them: narrow and multi-row steep), then wide (or column-steep), then
+    // the steep fallback
     if (!after_triple)
         field_mixed_pair_smem_kernel<CB, false, false><<<grid, kThreads, smem, s>>>(
             c, n_tiles, tps, p.nx, p.ny, partial, flags, kAll | kFlagCross, 0u, 0u, spins);
     field_mixed_pair_smem_kernel<CB, false, true><<<grid, kThreads, smem, s>>>(
         c, n_tiles, tps, p.nx, p.ny, partial, flags, kAll, 0u,
-        after_triple ? (kFlagCross | gbd::kFlagSteepRows) : kFlagCross, spins);
+        after_triple ? gbd::kFlagSteepRows : kFlagCross, spins);
     field_mixed_pair_smem_kernel<CB, true><<<grid, kThreads, smem, s>>>(
         c, n_tiles, tps, p.nx, p.ny, partial, flags, kFlagSteep, 0u, kFlagWide | kFlagColSteep,
         spins);
@@ -950,15 +963,27 @@ cudaError_t launch_mixed_rows(const void* coeffs, int n_tiles, const gbd_project
                    : launch_pair_set<CB>(coeffs, n_tiles, p, L, partial, flags, spins, s, after);
     };
     if (L.tiles_per_split > kRowsMaxTiles) return pairs(false);
-    constexpr size_t smem = rows_smem_bytes();
-    cudaError_t e = cudaFuncSetAttribute(field_mixed_rows_kernel<RB, CB>,
+    // fields with a uv term on row triples behind the 4 x 8 quadruples (tilted Zernike
+    // 1024^2: 4.60 ms against 4.70 ms on 4 x 8; the telescope's PSF 4.68 against 4.89)
+    constexpr int RX = RB == 4 && CB == 8 ? 3 : RB;
+    constexpr size_t smem = rows_smem_bytes<false>(), smem_x = rows_smem_bytes<true>();
+    cudaError_t e = cudaFuncSetAttribute(field_mixed_rows_kernel<RB, CB, false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(field_mixed_rows_kernel<RX, CB, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_x);
     if (e != cudaSuccess) return e;
     // splits fastest: a pixel block's splits run together
-    dim3 grid(L.splits, (p.nx + 32 * CB - 1) / (32 * CB), (p.ny + 8 * RB - 1) / (8 * RB));
-    field_mixed_rows_kernel<RB, CB><<<grid, kThreads, smem, s>>>(
+    const int gx = (p.nx + 32 * CB - 1) / (32 * CB);
+    dim3 grid(L.splits, gx, (p.ny + 8 * RB - 1) / (8 * RB));
+    dim3 grid_x(L.splits, gx, (p.ny + 8 * RX - 1) / (8 * RX));
+    // exactly one of the two runs (or neither): without a uv term, then with one
+    field_mixed_rows_kernel<RB, CB, false><<<grid, kThreads, smem, s>>>(
         static_cast<const float4*>(coeffs), n_tiles, L.tiles_per_split, p.nx, p.ny,
         static_cast<float2*>(partial), flags, kRowsNarrow, 0u, spins, ro.done, ro);
+    field_mixed_rows_kernel<RX, CB, true><<<grid_x, kThreads, smem_x, s>>>(
+        static_cast<const float4*>(coeffs), n_tiles, L.tiles_per_split, p.nx, p.ny,
+        static_cast<float2*>(partial), flags, kRowsNarrow, gbd::kFlagCross, spins, ro.done, ro);
     return pairs(true);
 }
 
@@ -1057,7 +1082,9 @@ int gbd_field_row_block(int precision, const gbd_field_launch& L) {
     if (precision == GBD_PREC_F64) return cb >= 8 ? rb : 8 * rb;
     if (L.scheme == GBD_SCHEME_DIRECT) return 8 * rb;
     if (rb == 2) return 16;
-    // row triples / quadruples with the 16-row pair set behind them
+    // row triples / quadruples with the 16-row pair set behind them (4 x 8: and the
+    // 24-row blocks of the row triples that take fields with a uv term)
+    if (rb == 4 && cb == 8) return 96;
     return rb == 3 ? 48 : 32;
 }
 
@@ -1088,12 +1115,12 @@ cudaError_t gbd_launch_field_reduce(int precision, const gbd_project_params& p,
             static_cast<const double2*>(partial), L.splits, p.nx, p.ny, p.rows, p.row0, ro.skip,
             ro.out_rows, ro.cx, ro.cy, ro.out);
     } else {
-        // a multi-row launch whose kernel took the field has stored it already
+        // a multi-row launch whose kernels took the field has stored it already
         const bool rows = L.scheme == GBD_SCHEME_ROW_PAIR && L.rows_per_thread >= 3 &&
                           L.tiles_per_split <= kRowsMaxTiles;
         field_reduce_mixed_kernel<<<blocks, 256, 0, s>>>(static_cast<const float2*>(partial),
                                                          L.splits, flags,
-                                                         rows ? kRowsNarrow : 0u, p.nx, p.rows,
+                                                         rows ? kRowsTaken : 0u, p.nx, p.rows,
                                                          ro);
     }
     return cudaGetLastError();

@@ -281,9 +281,10 @@ __device__ __forceinline__ void mixed_pair_rows(const float4* __restrict__ st, f
     }
 }
 
-// Row terms of a tile for the row triples and quadruples, which run only on fields
-// without a uv term (a_uv = p_uv = 0 for every beamlet, the projection's cross flag
-// clear).  The 8-row step factor R = exp(8 (c_v + c_vv (2 tv + 8))) then does not depend
+// Row terms of a tile for the row triples and quadruples on fields without a uv term
+// (a_uv = p_uv = 0 for every beamlet, the projection's cross flag clear; with one,
+// mixed_rows_cross_terms adds the column factors to these).  The 8-row step factor
+// R = exp(8 (c_v + c_vv (2 tv + 8))) then does not depend
 // on the column, so it and its products S_2 = R (R K), S_3 = S_2 (R K^2)
 // (K = exp(128 c_vv), the ratio of consecutive step factors) are the same for all lanes
 // of the warp and are formed here, once per warp and beamlet, with their phases reduced
@@ -491,6 +492,109 @@ __device__ __forceinline__ void mixed_tile_rows_x2(const float4* __restrict__ en
                 acc[r][c] = __ffma2_rn(make_float2(E0.x, E0.x), S[r - 1], acc[r][c]);
             }
             if (c + 1 < CB) ar = __fmul2_rn(ar, make_float2(ar.y, sig));
+        }
+    }
+}
+
+// Row terms of a tile for the row triples and quadruples on fields with a uv term.  The
+// 8-row step factor at column offset tu from the beamlet's centre is then R W(tu) with
+// W(tu) = exp(8 c_uv tu), so row 8 r below the first is the first times
+// P_r(tu) = S_r W(tu)^r, S_r the column-free products of mixed_rows_term; along a thread's
+// columns (32 apart) P_r steps by T^r, T = W(32) = exp(256 c_uv) (stored in the record).
+// kRowsCrossF4 float4 per beamlet and warp: the kRowsF4 of mixed_rows_term, then
+//   ent[4][b] = (T.re, T^2.re, T.im, T^2.im)   (rows 1 and 2 step as one FP32x2 pair),
+//   ent[5][b] = (T^3, 8 a_uv, 8 p_uv).
+constexpr int kRowsCrossF4 = 6;
+template <int RB>
+__device__ __forceinline__ void mixed_rows_cross_terms(const float4* __restrict__ st, float rowf,
+                                                       float4* __restrict__ ent, int lane) {
+#pragma unroll
+    for (int h = 0; h < kTile / 32; ++h) {
+        const int b = lane + 32 * h;
+        mixed_rows_term<RB>(st, b, rowf, ent, b, kTile);
+        const float4 q2 = st[2 * kTile + b];
+        const float4 q3 = st[3 * kTile + b];
+        const float2 T = make_float2(q3.z, q3.w);
+        const float2 T2 = make_float2(fmaf(T.x, T.x, -T.y * T.y), 2.0f * T.x * T.y);
+        const float2 T3 = make_float2(fmaf(T2.x, T.x, -T2.y * T.y), fmaf(T2.x, T.y, T2.y * T.x));
+        ent[4 * kTile + b] = make_float4(T.x, T2.x, T.y, T2.y);
+        ent[5 * kTile + b] = make_float4(T3.x, T3.y, 8.0f * q2.z, 8.0f * q2.w);
+    }
+}
+
+// mixed_tile_rows for fields with a uv term, on the row terms of mixed_rows_cross_terms.
+// Per beamlet and thread, besides the first row's polynomials: W0 = W(tu0) at the thread's
+// first column (one ex2 and a sin/cos of a phase within 64 rad, reduced exactly first) and
+// P_r = S_r W0^r by complex multiplies.  Per column: the first row's value E0 as in
+// mixed_tile_rows, 4 FFMA per later row (E0 P_r), and the step P_r <- P_r T^r: rows 1 and 2
+// as the FP32x2 pairs X = (P_1.re, P_2.re), Y = (P_1.im, P_2.im), X <- X (T.re, T^2.re) -
+// Y (T.im, T^2.im), Y <- X (T.im, T^2.im) + Y (T.re, T^2.re) (4 packed instructions, no
+// operand moves), row 3 (quadruples) in scalar.  Requires the same flags clear as
+// mixed_tile_rows except the cross flag: the steep-rows bound covers |log2 P_r| with the
+// uv term over the detector, the wide bound the step phase 8 (p_v + p_uv tu + ...).
+template <int RB, int CB>
+__device__ __forceinline__ void mixed_tile_rows_cross(const float4* __restrict__ ent,
+                                                      const float (&colf)[CB],
+                                                      float2 (&acc)[RB][CB]) {
+    static_assert(RB == 3 || RB == 4, "row triples or quadruples");
+    const float kTwoPi = 6.28318530717958647692f, kInvTwoPi = 0.15915494309189533577f;
+#pragma unroll 1
+    for (int b = 0; b < kTile; ++b) {
+        const float4 e0 = ent[b];
+        const float4 e1 = ent[kTile + b];
+        const float4 e2 = ent[2 * kTile + b];
+        const float4 e3 = ent[3 * kTile + b];
+        const float4 e4 = ent[4 * kTile + b];
+        const float4 e5 = ent[5 * kTile + b];
+        const float tu0 = colf[0] - e0.x;
+        const float t64 = tu0 * 0.015625f;
+        const float x0 = fmaf(tu0, fmaf(e2.y, t64, e1.x), e0.z);
+        const float d1 = fmaf(e2.y, tu0, e1.z);
+        float amp = mufu_ex2(fmaf(tu0, fmaf(e2.x, t64, e0.w), e0.y));
+        float rho = mufu_ex2(fmaf(e2.x, tu0, e1.y));
+        const float sig = e1.w;
+        // W0 = 2^(8 a_uv tu0) e^(i 8 p_uv tu0) and P_r = S_r W0^r at the first column
+        const float wp = frac_turns(e5.w * tu0 * kInvTwoPi) * kTwoPi;
+        const float wm = mufu_ex2(e5.z * tu0);
+        const float2 W = make_float2(wm * mufu_cos(wp), wm * mufu_sin(wp));
+        const float2 W2 = make_float2(fmaf(W.x, W.x, -W.y * W.y), 2.0f * W.x * W.y);
+        const float2 S1 = make_float2(e2.z, e2.w), S2 = make_float2(e3.x, e3.y);
+        float2 X = make_float2(fmaf(S1.x, W.x, -S1.y * W.y), fmaf(S2.x, W2.x, -S2.y * W2.y));
+        float2 Y = make_float2(fmaf(S1.x, W.y, S1.y * W.x), fmaf(S2.x, W2.y, S2.y * W2.x));
+        float2 P3 = make_float2(0.0f, 0.0f);
+        if (RB > 3) {
+            const float2 W3 = make_float2(fmaf(W2.x, W.x, -W2.y * W.y), fmaf(W2.x, W.y, W2.y * W.x));
+            P3 = make_float2(fmaf(e3.z, W3.x, -e3.w * W3.y), fmaf(e3.z, W3.y, e3.w * W3.x));
+        }
+        const float2 Tx = make_float2(e4.x, e4.y), Ty = make_float2(e4.z, e4.w);
+        const float2 Tyn = make_float2(-e4.z, -e4.w);
+        const float2 T3 = make_float2(e5.x, e5.y);
+#pragma unroll
+        for (int c = 0; c < CB; ++c) {
+            const float x = c == 0 ? x0 : fmaf((float)(16 * c * c), e2.y, fmaf((float)c, d1, x0));
+            const float ex = amp * mufu_cos(x), ey = amp * mufu_sin(x);
+            acc[0][c].x += ex;
+            acc[0][c].y += ey;
+            acc[1][c].x = fmaf(ex, X.x, fmaf(-ey, Y.x, acc[1][c].x));
+            acc[1][c].y = fmaf(ex, Y.x, fmaf(ey, X.x, acc[1][c].y));
+            acc[2][c].x = fmaf(ex, X.y, fmaf(-ey, Y.y, acc[2][c].x));
+            acc[2][c].y = fmaf(ex, Y.y, fmaf(ey, X.y, acc[2][c].y));
+            if (RB > 3) {
+                acc[RB - 1][c].x = fmaf(ex, P3.x, fmaf(-ey, P3.y, acc[RB - 1][c].x));
+                acc[RB - 1][c].y = fmaf(ex, P3.y, fmaf(ey, P3.x, acc[RB - 1][c].y));
+            }
+            if (c + 1 < CB) {
+                const float2 Xn = __ffma2_rn(Y, Tyn, __fmul2_rn(X, Tx));
+                Y = __ffma2_rn(Y, Tx, __fmul2_rn(X, Ty));
+                X = Xn;
+                if (RB > 3) {
+                    const float p3x = fmaf(P3.x, T3.x, -P3.y * T3.y);
+                    P3.y = fmaf(P3.x, T3.y, P3.y * T3.x);
+                    P3.x = p3x;
+                }
+                amp *= rho;
+                rho *= sig;
+            }
         }
     }
 }

@@ -360,20 +360,24 @@ def test_row_triples_and_quadruples_match_the_oracle(name, rows, cols):
         gbd.gbd_field_reset_shape(gbd.GBD_PREC_MIXED)
 
 
-@pytest.mark.parametrize("rows", [3, 4])
-def test_row_triples_hand_uv_term_fields_to_the_row_pairs(rows):
+@pytest.mark.parametrize("rows,cols", [(3, 8), (4, 8), (4, 4)])
+@pytest.mark.parametrize("nx,ny", [(128, 96), (120, 77)])
+def test_row_triples_and_quadruples_take_uv_term_fields(rows, cols, nx, ny):
     """The tilted, aberrated optics on a small patch of the focal plane (beamlets ~170
-    pixels wide): the field has a uv term and no other flag, so behind the row triples /
-    quadruples the narrow row pairs with the column factor's update run; the field
-    matches the oracle for 1 and 2 splits."""
-    wl = W.scaled(W.tilted_zernike(), n_across=16, nx=128, ny=96, keep_span=False)
+    pixels wide): the field has a uv term and no other flag, so the multi-row kernels'
+    instantiation with the per-column row factors P_r = S_r W^r runs (rows 8 r below the
+    first as E0 S_r W(tu)^r, W stepped along the row by T^r); the field matches the oracle
+    for 1, 2 and 5 splits, on a detector that fills whole thread blocks in neither
+    direction as well."""
+    wl = W.scaled(W.tilted_zernike(), n_across=16, nx=nx, ny=ny, keep_span=False)
     b = gpu_trace(wl)
     f = projection_flags(b, wl)
     assert f & 8 and not f & (1 | 2 | 4 | 16), f
     Eo = oracle.field(oracle.trace(wl.system, wl.pupil), wl.system, wl.detector)
     try:
-        for splits in (1, 2):
-            gbd.gbd_field_set_shape(gbd.GBD_PREC_MIXED, rows, 8, splits, gbd.GBD_SCHEME_ROW_PAIR)
+        for splits in (1, 2, 5):
+            gbd.gbd_field_set_shape(gbd.GBD_PREC_MIXED, rows, cols, splits,
+                                    gbd.GBD_SCHEME_ROW_PAIR)
             E = gpu_field(b, wl, gbd.GBD_PREC_MIXED)
             assert rel_l2(E, Eo) <= TOL[gbd.GBD_PREC_MIXED], splits
     finally:
