@@ -665,7 +665,8 @@ def run_ours(args, world, rank, local):
 
     # ---- the tilted, aberrated system (Zernike plate, detector tilted 10 deg / 5 deg):
     # trace + mixed field at 1024^2 pixels, the default shape (a field with a uv term, so
-    # the row pairs with the column factor's update run); parity on it is a test case
+    # the row triples with per-column row factors run behind the 4 x 8 pick); parity on it
+    # is a test case
     tilted = None
     if not args.no_tilted:
         twl = W.tilted_zernike()

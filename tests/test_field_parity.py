@@ -384,6 +384,31 @@ def test_row_triples_and_quadruples_take_uv_term_fields(rows, cols, nx, ny):
         gbd.gbd_field_reset_shape(gbd.GBD_PREC_MIXED)
 
 
+@pytest.mark.parametrize("rows,cols", [(3, 8), (4, 8), (4, 4)])
+def test_multi_row_steep_fields_go_to_the_row_pairs(rows, cols):
+    """Pixels 40 times taller than wide on the tilted optics' small patch (beamlets ~170
+    pixels wide and ~4 rows tall): a 24-row step's log2 amplitude change exceeds 64 while
+    an 8-row step's and the 224-column span's stay within it, so the projection sets the
+    cross and multi-row steep bits only; behind the multi-row kernels the row pairs with
+    the column factor's update then take the field, and it matches the oracle."""
+    import dataclasses
+    base = W.scaled(W.tilted_zernike(), n_across=16, nx=128, ny=96, keep_span=False)
+    d = base.detector
+    wl = dataclasses.replace(base, oracle_stride=None,
+                             detector=dataclasses.replace(d, ny=32, pitch_y=40 * d.pitch_x))
+    b = gpu_trace(wl)
+    assert projection_flags(b, wl) == 8 | 16
+    Eo = oracle.field(oracle.trace(wl.system, wl.pupil), wl.system, wl.detector)
+    try:
+        for splits in (1, 3):
+            gbd.gbd_field_set_shape(gbd.GBD_PREC_MIXED, rows, cols, splits,
+                                    gbd.GBD_SCHEME_ROW_PAIR)
+            E = gpu_field(b, wl, gbd.GBD_PREC_MIXED)
+            assert rel_l2(E, Eo) <= TOL[gbd.GBD_PREC_MIXED], splits
+    finally:
+        gbd.gbd_field_reset_shape(gbd.GBD_PREC_MIXED)
+
+
 def test_column_steep_fields_use_the_general_row_pair_instantiation():
     """Beamlets ~20 pixels wide against a thread's 224-pixel column span: the projection
     flags the amplitude recurrence along rows as unsafe (bit 2) but not the row pairs
