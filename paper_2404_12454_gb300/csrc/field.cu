@@ -324,7 +324,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     __shared__ int flag;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    constexpr int kEntF4 = CROSS ? gbd::kRowsCrossF4 : gbd::kRowsF4;
+    constexpr int kEntF4 = CROSS ? gbd::kRowsCrossF4<RB> : gbd::kRowsF4;
     float4* ent = dyn4 + kStages * kTileF4 + warp * (kEntF4 * gbd::kTile);
     const int split = blockIdx.x, bx = blockIdx.y, by = blockIdx.z;
     const int t0 = split * tiles_per_split;
@@ -449,10 +449,10 @@ constexpr unsigned kRowsNarrow = gbd::kFlagWide | gbd::kFlagSteep | gbd::kFlagCo
 // kernels store the field themselves when these are all clear).
 constexpr unsigned kRowsTaken = kRowsNarrow & ~gbd::kFlagCross;
 
-template <bool CROSS = false>
+template <bool CROSS = false, int RB = 4>
 constexpr size_t rows_smem_bytes() {
     return (size_t)kStages * gbd::kMixedTileBytes +
-           (size_t)kWarps * (CROSS ? gbd::kRowsCrossF4 : gbd::kRowsF4) * gbd::kTile *
+           (size_t)kWarps * (CROSS ? gbd::kRowsCrossF4<RB> : gbd::kRowsF4) * gbd::kTile *
                sizeof(float4);
 }
 
@@ -966,7 +966,7 @@ cudaError_t launch_mixed_rows(const void* coeffs, int n_tiles, const gbd_project
     // fields with a uv term on row triples behind the 4 x 8 quadruples (tilted Zernike
     // 1024^2: 4.60 ms against 4.70 ms on 4 x 8; the telescope's PSF 4.68 against 4.89)
     constexpr int RX = RB == 4 && CB == 8 ? 3 : RB;
-    constexpr size_t smem = rows_smem_bytes<false>(), smem_x = rows_smem_bytes<true>();
+    constexpr size_t smem = rows_smem_bytes<false>(), smem_x = rows_smem_bytes<true, RX>();
     cudaError_t e = cudaFuncSetAttribute(field_mixed_rows_kernel<RB, CB, false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)

@@ -501,28 +501,44 @@ __device__ __forceinline__ void mixed_tile_rows_x2(const float4* __restrict__ en
 // W(tu) = exp(8 c_uv tu), so row 8 r below the first is the first times
 // P_r(tu) = S_r W(tu)^r, S_r the column-free products of mixed_rows_term; along a thread's
 // columns (32 apart) P_r steps by T^r, T = W(32) = exp(256 c_uv) (stored in the record).
-// kRowsCrossF4 float4 per beamlet and warp: the kRowsF4 of mixed_rows_term, then
+// kRowsCrossF4<RB> float4 per beamlet and warp: the kRowsF4 of mixed_rows_term, with
 //   ent[4][b] = (T.re, T^2.re, T.im, T^2.im)   (rows 1 and 2 step as one FP32x2 pair),
-//   ent[5][b] = (T^3, 8 a_uv, 8 p_uv).
-constexpr int kRowsCrossF4 = 6;
+// and (8 a_uv, 8 p_uv) in the unused S_3 slot of ent[3][b] for the triples; the
+// quadruples add ent[5][b] = (T^3, 8 a_uv, 8 p_uv).
+template <int RB>
+constexpr int kRowsCrossF4 = RB > 3 ? 6 : 5;
+// The cross row terms of stage beamlet b, written to ent[k * stride + i].
+template <int RB>
+__device__ __forceinline__ void mixed_rows_cross_term(const float4* __restrict__ st, int b,
+                                                      float rowf, float4* __restrict__ ent,
+                                                      int i, int stride) {
+    mixed_rows_term<RB>(st, b, rowf, ent, i, stride);
+    const float4 q2 = st[2 * kTile + b];
+    const float4 q3 = st[3 * kTile + b];
+    const float2 T = make_float2(q3.z, q3.w);
+    const float2 T2 = make_float2(fmaf(T.x, T.x, -T.y * T.y), 2.0f * T.x * T.y);
+    ent[4 * stride + i] = make_float4(T.x, T2.x, T.y, T2.y);
+    if (RB > 3) {
+        const float2 T3 =
+            make_float2(fmaf(T2.x, T.x, -T2.y * T.y), fmaf(T2.x, T.y, T2.y * T.x));
+        ent[5 * stride + i] = make_float4(T3.x, T3.y, 8.0f * q2.z, 8.0f * q2.w);
+    } else {
+        const float4 e3 = ent[3 * stride + i];  // written above by this thread
+        ent[3 * stride + i] = make_float4(e3.x, e3.y, 8.0f * q2.z, 8.0f * q2.w);
+    }
+}
+
+// All 64 beamlets of the tile: lane l takes beamlets l and l + 32.
 template <int RB>
 __device__ __forceinline__ void mixed_rows_cross_terms(const float4* __restrict__ st, float rowf,
                                                        float4* __restrict__ ent, int lane) {
 #pragma unroll
-    for (int h = 0; h < kTile / 32; ++h) {
-        const int b = lane + 32 * h;
-        mixed_rows_term<RB>(st, b, rowf, ent, b, kTile);
-        const float4 q2 = st[2 * kTile + b];
-        const float4 q3 = st[3 * kTile + b];
-        const float2 T = make_float2(q3.z, q3.w);
-        const float2 T2 = make_float2(fmaf(T.x, T.x, -T.y * T.y), 2.0f * T.x * T.y);
-        const float2 T3 = make_float2(fmaf(T2.x, T.x, -T2.y * T.y), fmaf(T2.x, T.y, T2.y * T.x));
-        ent[4 * kTile + b] = make_float4(T.x, T2.x, T.y, T2.y);
-        ent[5 * kTile + b] = make_float4(T3.x, T3.y, 8.0f * q2.z, 8.0f * q2.w);
-    }
+    for (int h = 0; h < kTile / 32; ++h)
+        mixed_rows_cross_term<RB>(st, lane + 32 * h, rowf, ent, lane + 32 * h, kTile);
 }
 
-// mixed_tile_rows for fields with a uv term, on the row terms of mixed_rows_cross_terms.
+// mixed_tile_rows for fields with a uv term, on the cross row terms (NB beamlets, SoA with
+// stride NB).
 // Per beamlet and thread, besides the first row's polynomials: W0 = W(tu0) at the thread's
 // first column (one ex2 and a sin/cos of a phase within 64 rad, reduced exactly first) and
 // P_r = S_r W0^r by complex multiplies.  Per column: the first row's value E0 as in
@@ -532,20 +548,21 @@ __device__ __forceinline__ void mixed_rows_cross_terms(const float4* __restrict_
 // operand moves), row 3 (quadruples) in scalar.  Requires the same flags clear as
 // mixed_tile_rows except the cross flag: the steep-rows bound covers |log2 P_r| with the
 // uv term over the detector, the wide bound the step phase 8 (p_v + p_uv tu + ...).
-template <int RB, int CB>
+template <int RB, int CB, int NB = kTile>
 __device__ __forceinline__ void mixed_tile_rows_cross(const float4* __restrict__ ent,
                                                       const float (&colf)[CB],
                                                       float2 (&acc)[RB][CB]) {
     static_assert(RB == 3 || RB == 4, "row triples or quadruples");
     const float kTwoPi = 6.28318530717958647692f, kInvTwoPi = 0.15915494309189533577f;
 #pragma unroll 1
-    for (int b = 0; b < kTile; ++b) {
+    for (int b = 0; b < NB; ++b) {
         const float4 e0 = ent[b];
-        const float4 e1 = ent[kTile + b];
-        const float4 e2 = ent[2 * kTile + b];
-        const float4 e3 = ent[3 * kTile + b];
-        const float4 e4 = ent[4 * kTile + b];
-        const float4 e5 = ent[5 * kTile + b];
+        const float4 e1 = ent[NB + b];
+        const float4 e2 = ent[2 * NB + b];
+        const float4 e3 = ent[3 * NB + b];
+        const float4 e4 = ent[4 * NB + b];
+        // (T^3, 8 a_uv, 8 p_uv); the triples keep the last two in e3.zw
+        const float4 e5 = RB > 3 ? ent[5 * NB + b] : make_float4(0.0f, 0.0f, e3.z, e3.w);
         const float tu0 = colf[0] - e0.x;
         const float t64 = tu0 * 0.015625f;
         const float x0 = fmaf(tu0, fmaf(e2.y, t64, e1.x), e0.z);

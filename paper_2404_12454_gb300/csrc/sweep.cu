@@ -234,9 +234,11 @@ __global__ void __launch_bounds__(kThreads, 2)
 }
 
 // Row triples (3 x CB pixels per thread, rows 8 apart) on work items of 256 x 24 pixels.
-// FAST: fields without a uv term or multi-row steepness (mixed_tile_rows, the warp's row
-// terms computed per 32-beamlet half tile); otherwise every pixel is evaluated directly
-// with its phase reduced exactly (mixed_tile<3, CB, true>), which holds for any field.
+// FAST: fields without multi-row steepness (the warp's row terms computed per 32-beamlet
+// half tile): without a uv term mixed_tile_rows, with one (CROSS) mixed_tile_rows_cross
+// with the per-column row factors, folded after every tile like the direct instantiation
+// (real-ray traced fields); otherwise every pixel is evaluated directly with its phase
+// reduced exactly (mixed_tile<3, CB, true>), which holds for any field.
 // The sums run in FP32 registers for at most kRowsChunkTiles tiles and are then folded
 // with TwoSum into a compensated pair per pixel in shared memory: hi as FP32, the much
 // smaller lo as BF16 (its rounding, 2^-9 of lo, is 2^-33 of hi), which makes 24 pixels a
@@ -247,7 +249,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 // hi [3 CB][kThreads] float2, lo [3 CB][kThreads] bf16x2, then (FAST) each warp's row
 // terms of 32 beamlets.
 constexpr int kRowsChunkTiles = 16;
-template <int CB, bool FAST>
+template <int CB, bool FAST, bool CROSS = false>
 __global__ void __launch_bounds__(kThreads, 2)
     sweep_rows_kernel(const float4* __restrict__ coef, const int2* __restrict__ inst_tiles,
                       const int2* __restrict__ items, int n_items, int tiles_x, int n_blocks,
@@ -263,8 +265,9 @@ __global__ void __launch_bounds__(kThreads, 2)
     float4(*stage)[kTileF4] = reinterpret_cast<float4(*)[kTileF4]>(sweep_dyn);
     float2* hi = reinterpret_cast<float2*>(sweep_dyn + kStages * kTileF4);  // [RB CB][kThreads]
     uint32_t* lo = reinterpret_cast<uint32_t*>(hi + RB * CB * kThreads);     // [RB CB][kThreads]
+    constexpr int kEntF4 = CROSS ? gbd::kRowsCrossF4<RB> : gbd::kRowsF4;
     float4* ent = reinterpret_cast<float4*>(lo + RB * CB * kThreads) +
-                  (threadIdx.x >> 5) * (gbd::kRowsF4 * 32);
+                  (threadIdx.x >> 5) * (kEntF4 * 32);
     __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
     __shared__ int flag, s_item;
     __shared__ double red[kWarps][kMaxRegions][4];
@@ -310,14 +313,22 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll 1
                 for (int h = 0; h < gbd::kTile / 32; ++h) {
                     __syncwarp();  // every lane is done with the previous row terms
-                    gbd::mixed_rows_term<RB>(ts.tile(k), 32 * h + lane, rowf[0], ent, lane, 32);
-                    __syncwarp();
-                    gbd::mixed_tile_rows<RB, CB, 32>(ent, colf, acc);
+                    if constexpr (CROSS) {
+                        gbd::mixed_rows_cross_term<RB>(ts.tile(k), 32 * h + lane, rowf[0], ent,
+                                                       lane, 32);
+                        __syncwarp();
+                        gbd::mixed_tile_rows_cross<RB, CB, 32>(ent, colf, acc);
+                    } else {
+                        gbd::mixed_rows_term<RB>(ts.tile(k), 32 * h + lane, rowf[0], ent, lane,
+                                                 32);
+                        __syncwarp();
+                        gbd::mixed_tile_rows<RB, CB, 32>(ent, colf, acc);
+                    }
                 }
             } else {
                 gbd::mixed_tile<RB, CB, true>(ts.tile(k), colf, rowf, acc);
             }
-            constexpr int kChunk = FAST ? kRowsChunkTiles : 1;
+            constexpr int kChunk = FAST && !CROSS ? kRowsChunkTiles : 1;
             if ((k + 1) % kChunk == 0 || k + 1 == ts.nt) {
 #pragma unroll
                 for (int m = 0; m < RB * CB; ++m) {
@@ -362,9 +373,9 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
 }
 
-constexpr size_t sweep_rows_smem(int cb) {
+constexpr size_t sweep_rows_smem(int cb, bool cross = false) {
     return (size_t)kStages * gbd::kMixedTileBytes + (size_t)3 * cb * kThreads * (8 + 4) +
-           (size_t)kWarps * gbd::kRowsF4 * 32 * sizeof(float4);
+           (size_t)kWarps * (cross ? gbd::kRowsCrossF4<3> : gbd::kRowsF4) * 32 * sizeof(float4);
 }
 
 // Per instance, the moments of its pixel blocks summed in block order, then one score per
@@ -480,9 +491,9 @@ cudaError_t launch_sweep_pair(dim3 grid, cudaStream_t s, const float4* coef, con
     return e;
 }
 
-// Row triples on 3 x CB pixels (work items of 256 x 24 pixels): the fast instantiation for
-// fields without a uv term or multi-row steepness, the direct one (every phase reduced)
-// for all other fields.  Exactly one runs.
+// Row triples on 3 x CB pixels (work items of 256 x 24 pixels): the fast instantiations
+// for fields without multi-row steepness (without a uv term, then with one), the direct
+// one (every phase reduced) for all other fields.  Exactly one runs.
 template <int CB>
 cudaError_t launch_sweep_rows(dim3 grid, cudaStream_t s, const float4* coef, const int2* it_tiles,
                               const int2* items, int n_items, int tiles_x, int n_blocks, int nx,
@@ -490,9 +501,12 @@ cudaError_t launch_sweep_rows(dim3 grid, cudaStream_t s, const float4* coef, con
                               int* counter, const unsigned* flags, uint32_t spins) {
     constexpr unsigned kAny = gbd::kFlagWide | gbd::kFlagSteep | gbd::kFlagColSteep |
                               gbd::kFlagCross | gbd::kFlagSteepRows;
-    constexpr size_t smem = sweep_rows_smem(CB);
+    constexpr size_t smem = sweep_rows_smem(CB), smem_x = sweep_rows_smem(CB, true);
     cudaError_t e = cudaFuncSetAttribute(sweep_rows_kernel<CB, true>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sweep_rows_kernel<CB, true, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_x);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(sweep_rows_kernel<CB, false>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -500,9 +514,12 @@ cudaError_t launch_sweep_rows(dim3 grid, cudaStream_t s, const float4* coef, con
     sweep_rows_kernel<CB, true><<<grid, kThreads, smem, s>>>(
         coef, it_tiles, items, n_items, tiles_x, n_blocks, nx, ny, airy, n_regions, moments,
         counter, flags, kAny, 0u, 0u, spins);
+    sweep_rows_kernel<CB, true, true><<<grid, kThreads, smem_x, s>>>(
+        coef, it_tiles, items, n_items, tiles_x, n_blocks, nx, ny, airy, n_regions, moments,
+        counter, flags, kAny, gbd::kFlagCross, 0u, spins);
     sweep_rows_kernel<CB, false><<<grid, kThreads, smem, s>>>(
         coef, it_tiles, items, n_items, tiles_x, n_blocks, nx, ny, airy, n_regions, moments,
-        counter, flags, 0u, 0u, kAny, spins);
+        counter, flags, 0u, 0u, kAny & ~gbd::kFlagCross, spins);
     return cudaGetLastError();
 }
 
@@ -647,9 +664,11 @@ static gbd_status sweep_create(const gbd_trace_params& tp, const gbd_mirror_para
                                const double* waist_ratio, int32_t n_instances,
                                const gbd_detector* detector, const gbd_shape* shape,
                                gbd_sweep_plan** plan) {
-    // real-ray traced beamlets carry a uv term (the mirrors' small astigmatism), which the
-    // row triples can only evaluate directly: mirror sweeps default to the row pairs, which
-    // carry it along the row (the App. B telescope's 1024-instance sweep: 349 ms, 643 direct)
+    // real-ray traced beamlets carry a uv term (the mirrors' small astigmatism): mirror
+    // sweeps default to the row pairs, which carry it along the row (the App. B telescope's
+    // 1024-instance sweep: 349 ms; scores within 9e-5 of the oracle's where the two paths
+    // differ most); the row triples with per-column row factors take 340 ms but sit up to
+    // 2.2e-4 from the oracle there (643 ms when they evaluated these fields directly)
     gbd_status st = gbd_check_detector(detector);
     if (st != GBD_OK) return st;
     if (!(isfinite(diameter) && diameter > 0.0))
