@@ -256,7 +256,7 @@ gbd_status gbd_field_truncated(const gbd_beamlet* beamlets, int32_t n_beamlets, 
  *     row 0 = detector row row_begin; device memory owned by the caller.
  *   workspace: at least gbd_field_rows_workspace_bytes(...) bytes, 256-byte aligned (the
  *     split partial fields cover only the slab, rounded down at its start to the launch's
- *     row-block height of at most 96 rows).
+ *     row-block height of at most 48 rows).
  * The launch (shape, splits) and the projection's kernel selection are those gbd_field
  * takes on the whole detector, and every pixel of the slab is computed by the same thread
  * row block, so the slab equals the same rows of gbd_field's output bit for bit, for any

@@ -335,7 +335,15 @@ __global__ void __launch_bounds__(kThreads, 2)
     bool ok = ts.start(tid, spins, &flag);
 
     const int col0 = bx * (32 * CB) + lane;
-    const int row0 = by * (8 * RB) + warp;
+    // the block's first row in slab coordinates: blocks sit at detector rows that are
+    // multiples of 8 RB, so every pixel is computed by the same thread row as in the whole
+    // field.  Slabs start at multiples of the launch's row-block height, which the blocks
+    // without a uv term divide; the uv-term triples behind a 4 x 8 pick (24 rows against
+    // a 32-row alignment) may start inside their first block and evaluate the rows before
+    // the slab without storing them (kAnchor)
+    constexpr bool kAnchor = CROSS;
+    const int rb0 = by * (8 * RB) - (kAnchor ? ro.row0 % (8 * RB) : 0);
+    const int row0 = rb0 + warp;
     float colf[CB];
 #pragma unroll
     for (int c = 0; c < CB; ++c) colf[c] = (float)(col0 + 32 * c);
@@ -384,7 +392,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
     for (int r = 0; r < RB; ++r) {
         const int row = row0 + 8 * r;
-        if (row >= ny) continue;
+        if ((kAnchor && row < 0) || row >= ny) continue;
 #pragma unroll
         for (int c = 0; c < CB; ++c) {
             const int col = col0 + 32 * c;
@@ -415,13 +423,14 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
         for (int q = 0; q < kNP; ++q) {
             const int row = row0 + 8 * ((m0 + q) / CB), col = col0 + 32 * ((m0 + q) % CB);
-            pq[q] = row < ny && col < nx ? (size_t)row * nx + col : 0;
+            pq[q] = (!kAnchor || row >= 0) && row < ny && col < nx ? (size_t)row * nx + col : 0;
         }
         gbd::sum_partials_n<kNP>(partial, npix, pq, splits, v);
 #pragma unroll
         for (int q = 0; q < kNP; ++q) {
             const int row = row0 + 8 * ((m0 + q) / CB), col = col0 + 32 * ((m0 + q) % CB);
-            if (row < ny && col < nx) gbd::reduce_store(ro, nx, row, col, v[q]);
+            if ((!kAnchor || row >= 0) && row < ny && col < nx)
+                gbd::reduce_store(ro, nx, row, col, v[q]);
         }
     }
     // The block's partials are consumed: drop their L2 lines instead of letting them be
@@ -429,13 +438,14 @@ __global__ void __launch_bounds__(kThreads, 2)
     // this block (rows of a multiple of 16 pixels; the block spans 32 CB pixels = 2 CB lines).
     if ((nx & 15) == 0) {
         __syncthreads();  // every thread has read its pixels' partials
-        const int rows_here = min(8 * RB, ny - by * (8 * RB));
+        const int r_lo = kAnchor ? max(rb0, 0) : rb0;
+        const int rows_here = min(rb0 + 8 * RB, ny) - r_lo;
         const int lines_per_row = (min(32 * CB, nx - bx * (32 * CB)) * 8 + 127) / 128;
         const int per_split = rows_here * lines_per_row;
         const long long total = (long long)splits * per_split;
         for (long long q = tid; q < total; q += kThreads) {
             const int s = (int)(q / per_split), rem = (int)(q % per_split);
-            const int row = by * (8 * RB) + rem / lines_per_row, line = rem % lines_per_row;
+            const int row = r_lo + rem / lines_per_row, line = rem % lines_per_row;
             const float2* a = partial + (size_t)s * npix + (size_t)row * nx + bx * (32 * CB);
             gbd::discard_l2_line(reinterpret_cast<const char*>(a) + 128 * line);
         }
@@ -974,9 +984,13 @@ cudaError_t launch_mixed_rows(const void* coeffs, int n_tiles, const gbd_project
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_x);
     if (e != cudaSuccess) return e;
     // splits fastest: a pixel block's splits run together
+    // pixel blocks at detector rows that are multiples of 8 RB (p.ny: the slab's rows, its
+    // first detector row ro.row0, a multiple of 8 RB for the kernel without a uv term; the
+    // one with a uv term may start inside its first block)
     const int gx = (p.nx + 32 * CB - 1) / (32 * CB);
+    const int off_x = ro.row0 % (8 * RX);
     dim3 grid(L.splits, gx, (p.ny + 8 * RB - 1) / (8 * RB));
-    dim3 grid_x(L.splits, gx, (p.ny + 8 * RX - 1) / (8 * RX));
+    dim3 grid_x(L.splits, gx, (p.ny + off_x + 8 * RX - 1) / (8 * RX));
     // exactly one of the two runs (or neither): without a uv term, then with one
     field_mixed_rows_kernel<RB, CB, false><<<grid, kThreads, smem, s>>>(
         static_cast<const float4*>(coeffs), n_tiles, L.tiles_per_split, p.nx, p.ny,
@@ -1082,9 +1096,9 @@ int gbd_field_row_block(int precision, const gbd_field_launch& L) {
     if (precision == GBD_PREC_F64) return cb >= 8 ? rb : 8 * rb;
     if (L.scheme == GBD_SCHEME_DIRECT) return 8 * rb;
     if (rb == 2) return 16;
-    // row triples / quadruples with the 16-row pair set behind them (4 x 8: and the
-    // 24-row blocks of the row triples that take fields with a uv term)
-    if (rb == 4 && cb == 8) return 96;
+    // row triples / quadruples with the 16-row pair set behind them (behind 4 x 8 the row
+    // triples that take fields with a uv term place their 24-row blocks at detector rows,
+    // whatever the slab's first row)
     return rb == 3 ? 48 : 32;
 }
 

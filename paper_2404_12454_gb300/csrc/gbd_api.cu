@@ -340,9 +340,10 @@ int slab_row0(int precision, const gbd_field_launch& L, int row_begin) {
 }
 
 // Completion counters of the multi-row kernel's pixel blocks (32 CB x 8 RB pixels; sized
-// for the smallest block, 32 x 8).
+// for the smallest block, 32 x 8, and one more block row: a slab may start inside its
+// first block).
 size_t counter_bytes(int nx, int rows) {
-    return align256((size_t)((nx + 31) / 32) * ((rows + 7) / 8) * sizeof(unsigned));
+    return align256((size_t)((nx + 31) / 32) * ((rows + 7) / 8 + 1) * sizeof(unsigned));
 }
 
 size_t workspace_for(int precision, int n, const gbd_detector* D, const gbd_field_launch& L,
