@@ -50,7 +50,7 @@ FIELD_MIXED_NCU = [
      "write": 2.884352e6, "splits": 90, "rows": 4, "cols": 4, "scheme": 1,
      "inst_per_32_evals": 6.81, "fma_pipe_active": 0.675},
     {"kernel": "field_mixed_rows_kernel<4, 8> (4x8 row quadruples, packed FP32x2)",
-     "read": 3.353088e6, "write": 4.194816e6, "splits": 90, "rows": 4, "cols": 8, "scheme": 1,
+     "read": 3.3472e6, "write": 3.54176e6, "splits": 90, "rows": 4, "cols": 8, "scheme": 1,
      "inst_per_32_evals": 4.74, "fma_pipe_active": 0.721},
 ]
 ISSUE_PER_CLK_SM = 4  # warp-instructions issued per clock and SM (one per sub-partition)
@@ -882,11 +882,16 @@ def run_ours(args, world, rank, local):
 
     # trace, projection, split reduction, and the field kernels of the shape: the
     # instantiation the flag word selects plus the others, which return at once (direct:
-    # 2; row pairs on 2 or 4 columns: 3; on 8 columns: 4; row triples / quadruples: 4,
-    # also when a split holds more than 16 tiles and the 8-column pairs run alone)
+    # 2; row pairs on 2 or 4 columns: 3; on 8 columns: 4; row triples / quadruples: their
+    # two instantiations, without and with a uv term, and 3 row-pair launches behind them,
+    # or the 8-column pairs alone (4) when a split holds more than 16 tiles)
+    tiles = -(-nb // 64)
+    tiles_per_split = -(-tiles // max(1, tuned[2]))
     if not tuned[4]:
         field_launches = 2
-    elif tuned[0] >= 3 or tuned[1] >= 8:
+    elif tuned[0] >= 3:
+        field_launches = 5 if tiles_per_split <= 16 else 4
+    elif tuned[1] >= 8:
         field_launches = 4
     else:
         field_launches = 3
