@@ -41,6 +41,10 @@ def cases():
                                        W.Pupil(2.4e-3, 20, 2.0, 1.2),
                                        W.Detector(64, 131, 0.4e-6, 0.5e-6, math.radians(-12),
                                                   math.radians(7))),
+        # a uv term and no other flag: the multi-row kernels' uv-term instantiation runs,
+        # behind a 4 x 8 pick on 24-row blocks placed at detector rows, so slabs starting at
+        # rows 32 or 64 begin 8 or 16 rows into their first block
+        "tilted_patch": W.scaled(tz, n_across=16, nx=128, ny=96, keep_span=False),
     }
 
 
@@ -69,6 +73,21 @@ def shapes(prec):
     if prec == gbd.GBD_PREC_MIXED:
         return [None, (2, 4, D), (1, 4, D), (2, 4, P), (2, 8, P), (3, 8, P), (4, 4, P), (4, 8, P)]
     return [None, (1, 2, D), (2, 2, D), (1, 8, D), (2, 8, D), (1, 32, D), (4, 8, D), (2, 16, D), (8, 4, D)]
+
+
+def test_tilted_patch_takes_the_uv_term_row_kernels():
+    """The tilted patch's flag word is the cross bit alone (its fields go to the multi-row
+    kernels' uv-term instantiation, which the slab test below then covers)."""
+    import torch
+    wl = cases()["tilted_patch"]
+    b = gbd.trace(wl.system, wl.pupil)
+    n = b.shape[0]
+    coef = torch.empty(gbd.gbd_project_bytes(n, gbd.GBD_PREC_MIXED), dtype=torch.uint8,
+                       device="cuda")
+    flag = torch.zeros(1, dtype=torch.int32, device="cuda")
+    gbd.gbd_project(b, n, wl.system.wavelength, wl.detector, gbd.GBD_PREC_MIXED, coef, flag)
+    gbd.gbd_sync()
+    assert int(flag.item()) == 8
 
 
 @pytest.mark.parametrize("prec", PRECS)
