@@ -807,7 +807,7 @@ __device__ void first_task(const StepArgs& A, unsigned char* smem, int f, float 
     const int pk = pc < 3 ? off_w(0) + pu * 3 + pc : off_b(0) + pu;
     const AdamState st = t < 64 ? prefetch<TRAIN>(A, pk) : AdamState{};
     float g0 = 0.f, g1 = 0.f, g2 = 0.f, gb = 0.f;
-#pragma unroll 4
+#pragma unroll 8
     for (int n = q; n < A.B; n += 32) {
         const float dn = __ldcg(A.pl.d1 + f_index(u, n));
         const float* xn = A.x + (size_t)n * 3;
@@ -849,7 +849,7 @@ __device__ void out_task(const StepArgs& A, unsigned char* smem, int f, float c1
     const AdamState st = t < 16 ? prefetch<TRAIN>(A, off_w(4) + 16 * f + t) : AdamState{};
     const AdamState stb = f == 0 && t == 0 ? prefetch<TRAIN>(A, off_b(4)) : AdamState{};
     float g = 0.f;
-#pragma unroll 4
+#pragma unroll 8
     for (int n = q; n < A.B; n += 32)
         g = fmaf(__ldcg(A.pl.dout + n), __ldcg(A.pl.a4 + f_index(u, n)), g);
     float* bs = reinterpret_cast<float*>(smem + kOffBsum);
