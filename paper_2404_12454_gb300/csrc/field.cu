@@ -37,7 +37,7 @@ __device__ __forceinline__ void record_timeout() { atomicOr(&g_field_status, gbd
 // WIDE: 0 narrow phases, 1 every phase reduced exactly, kWideByFlag either, per the
 // flag word's wide bit (the direct steep fallback of the row-pair launches).
 constexpr int kWideByFlag = 2;
-template <int RB, int CB, int WIDE, bool PAIR>
+template <int RB, int CB, int WIDE, bool PAIR, bool LOOP = false>
 __global__ void __launch_bounds__(kThreads, 2)
     field_mixed_kernel(const float4* __restrict__ coef, int n_tiles, int tiles_per_split, int nx,
                        int ny, float2* __restrict__ partial, const unsigned* __restrict__ flags,
@@ -51,67 +51,83 @@ __global__ void __launch_bounds__(kThreads, 2)
     __shared__ int flag;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int t0 = blockIdx.z * tiles_per_split;
     gbd::init_stream_barriers(full, empty, tid);
-    gbd::TileStream<float4, kTileF4> ts{stage, full, empty, coef + (size_t)t0 * kTileF4,
-                                        min(n_tiles - t0, tiles_per_split), 0,
-                                        gbd::kMixedTileBytes, 0};
-    bool ok = ts.start(tid, spins, &flag);
+    // split `split` of the beamlets into its partial field, the CTA's stream starting at its
+    // g-th tile; false after a failed wait (the CTA then leaves)
+    auto run = [&](int split, int g) -> bool {
+        const int t0 = split * tiles_per_split;
+        gbd::TileStream<float4, kTileF4> ts{stage, full, empty, coef + (size_t)t0 * kTileF4,
+                                            min(n_tiles - t0, tiles_per_split), g,
+                                            gbd::kMixedTileBytes, 0};
+        bool ok = ts.start(tid, spins, &flag);
 
-    const int col0 = blockIdx.x * (32 * CB) + lane;
-    const int row0 = blockIdx.y * (8 * RB) + warp;
-    float colf[CB], rowf[RB];
+        const int col0 = blockIdx.x * (32 * CB) + lane;
+        const int row0 = blockIdx.y * (8 * RB) + warp;
+        float colf[CB], rowf[RB];
 #pragma unroll
-    for (int c = 0; c < CB; ++c) colf[c] = (float)(col0 + 32 * c);
+        for (int c = 0; c < CB; ++c) colf[c] = (float)(col0 + 32 * c);
 #pragma unroll
-    for (int r = 0; r < RB; ++r) rowf[r] = (float)(row0 + 8 * r);
+        for (int r = 0; r < RB; ++r) rowf[r] = (float)(row0 + 8 * r);
 
-    float2 acc[RB][CB], hi[RB][CB], lo[RB][CB];
+        float2 acc[RB][CB], hi[RB][CB], lo[RB][CB];
 #pragma unroll
-    for (int r = 0; r < RB; ++r)
+        for (int r = 0; r < RB; ++r)
 #pragma unroll
-        for (int c = 0; c < CB; ++c) acc[r][c] = hi[r][c] = lo[r][c] = make_float2(0.f, 0.f);
+            for (int c = 0; c < CB; ++c) acc[r][c] = hi[r][c] = lo[r][c] = make_float2(0.f, 0.f);
 
-    int k = 0;
-    for (; ok && k < ts.nt; ++k) {
-        if (!ts.acquire(k, spins)) {
-            ok = false;
-            break;
+        int k = 0;
+        for (; ok && k < ts.nt; ++k) {
+            if (!ts.acquire(k, spins)) {
+                ok = false;
+                break;
+            }
+            if constexpr (PAIR) {
+                gbd::mixed_tile_pair<CB, WIDE == 1>(ts.tile(k), colf, rowf[0], acc);
+            } else if constexpr (WIDE == kWideByFlag) {  // the steep fallback: both in one
+                if (fw & gbd::kFlagWide)
+                    gbd::mixed_tile<RB, CB, true>(ts.tile(k), colf, rowf, acc);
+                else
+                    gbd::mixed_tile<RB, CB, false>(ts.tile(k), colf, rowf, acc);
+            } else {
+                gbd::mixed_tile<RB, CB, WIDE == 1>(ts.tile(k), colf, rowf, acc);
+            }
+            gbd::mixed_fold<RB, CB>(acc, hi, lo);
+            if (!ts.release(k, lane, warp, spins)) {
+                ok = false;
+                ++k;
+                break;
+            }
         }
-        if constexpr (PAIR) {
-            gbd::mixed_tile_pair<CB, WIDE == 1>(ts.tile(k), colf, rowf[0], acc);
-        } else if constexpr (WIDE == kWideByFlag) {  // the steep fallback: one launch for both
-            if (fw & gbd::kFlagWide)
-                gbd::mixed_tile<RB, CB, true>(ts.tile(k), colf, rowf, acc);
-            else
-                gbd::mixed_tile<RB, CB, false>(ts.tile(k), colf, rowf, acc);
-        } else {
-            gbd::mixed_tile<RB, CB, WIDE == 1>(ts.tile(k), colf, rowf, acc);
+        if (!ok) {
+            record_timeout();
+            if (tid == 0) ts.drain(k, spins);
+            return false;
         }
-        gbd::mixed_fold<RB, CB>(acc, hi, lo);
-        if (!ts.release(k, lane, warp, spins)) {
-            ok = false;
-            ++k;
-            break;
-        }
-    }
-    if (!ok) {
-        record_timeout();
-        if (tid == 0) ts.drain(k, spins);
-        return;
-    }
-    const size_t npix = (size_t)nx * ny;
-    float2* out = partial + (size_t)blockIdx.z * npix;
+        const size_t npix = (size_t)nx * ny;
+        float2* out = partial + (size_t)split * npix;
 #pragma unroll
-    for (int r = 0; r < RB; ++r) {
-        const int row = row0 + 8 * r;
-        if (row >= ny) continue;
+        for (int r = 0; r < RB; ++r) {
+            const int row = row0 + 8 * r;
+            if (row >= ny) continue;
 #pragma unroll
-        for (int c = 0; c < CB; ++c) {
-            const int col = col0 + 32 * c;
-            if (col >= nx) continue;
-            out[(size_t)row * nx + col] = gbd::round_pair(hi[r][c], lo[r][c]);
+            for (int c = 0; c < CB; ++c) {
+                const int col = col0 + 32 * c;
+                if (col >= nx) continue;
+                out[(size_t)row * nx + col] = gbd::round_pair(hi[r][c], lo[r][c]);
+            }
         }
+        return true;
+    };
+    if constexpr (LOOP) {
+        // a fallback launch (fallback_z): splits blockIdx.z, blockIdx.z + gridDim.z, ...
+        const int nsplit = (n_tiles + tiles_per_split - 1) / tiles_per_split;
+        int g = 0;  // tiles this CTA has streamed (keeps the barrier phases in step)
+        for (int split = blockIdx.z; split < nsplit; split += gridDim.z) {
+            if (!run(split, g)) return;
+            g += min(n_tiles - split * tiles_per_split, tiles_per_split);
+        }
+    } else {
+        run(blockIdx.z, 0);
     }
 }
 
@@ -120,7 +136,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 // memory: the kStages record stages, then 2 CB x kThreads float4 (hi, lo) slots, then
 // (narrow instantiation) each warp's row terms of the current tile, kPairRowF4 x kTile
 // float4 per warp.
-template <int CB, bool WIDE, bool CROSS = true>
+template <int CB, bool WIDE, bool CROSS = true, bool LOOP = false>
 __global__ void __launch_bounds__(kThreads, 2)
     field_mixed_pair_smem_kernel(const float4* __restrict__ coef, int n_tiles, int tiles_per_split,
                                  int nx, int ny, float2* __restrict__ partial,
@@ -137,68 +153,85 @@ __global__ void __launch_bounds__(kThreads, 2)
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     float4* ent = comp + 2 * CB * kThreads + warp * (gbd::kPairRowF4 * gbd::kTile);
-#pragma unroll
-    for (int m = 0; m < 2 * CB; ++m) comp[m * kThreads + tid] = make_float4(0.f, 0.f, 0.f, 0.f);
-    const int t0 = blockIdx.z * tiles_per_split;
     gbd::init_stream_barriers(full, empty, tid);
-    gbd::TileStream<float4, kTileF4> ts{stage, full, empty, coef + (size_t)t0 * kTileF4,
-                                        min(n_tiles - t0, tiles_per_split), 0,
-                                        gbd::kMixedTileBytes, 0};
-    bool ok = ts.start(tid, spins, &flag);
+    // split `split` into its partial field (as field_mixed_kernel's)
+    auto run = [&](int split, int g) -> bool {
+        // each thread clears and later reads only its own compensation slots
+#pragma unroll
+        for (int m = 0; m < 2 * CB; ++m)
+            comp[m * kThreads + tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int t0 = split * tiles_per_split;
+        gbd::TileStream<float4, kTileF4> ts{stage, full, empty, coef + (size_t)t0 * kTileF4,
+                                            min(n_tiles - t0, tiles_per_split), g,
+                                            gbd::kMixedTileBytes, 0};
+        bool ok = ts.start(tid, spins, &flag);
 
-    const int col0 = blockIdx.x * (32 * CB) + lane;
-    const int row0 = blockIdx.y * 16 + warp;
-    float colf[CB];
+        const int col0 = blockIdx.x * (32 * CB) + lane;
+        const int row0 = blockIdx.y * 16 + warp;
+        float colf[CB];
 #pragma unroll
-    for (int c = 0; c < CB; ++c) colf[c] = (float)(col0 + 32 * c);
-    const float rowf = (float)row0;
+        for (int c = 0; c < CB; ++c) colf[c] = (float)(col0 + 32 * c);
+        const float rowf = (float)row0;
 
-    float2 acc[2][CB];
+        float2 acc[2][CB];
 #pragma unroll
-    for (int r = 0; r < 2; ++r)
+        for (int r = 0; r < 2; ++r)
 #pragma unroll
-        for (int c = 0; c < CB; ++c) acc[r][c] = make_float2(0.f, 0.f);
+            for (int c = 0; c < CB; ++c) acc[r][c] = make_float2(0.f, 0.f);
 
-    int k = 0;
-    for (; ok && k < ts.nt; ++k) {
-        if (!ts.acquire(k, spins)) {
-            ok = false;
-            break;
+        int k = 0;
+        for (; ok && k < ts.nt; ++k) {
+            if (!ts.acquire(k, spins)) {
+                ok = false;
+                break;
+            }
+            if constexpr (WIDE) {
+                gbd::mixed_tile_pair<CB, WIDE>(ts.tile(k), colf, rowf, acc);
+            } else {
+                __syncwarp();  // every lane is done with the previous tile's row terms
+                gbd::mixed_pair_rows<CROSS>(ts.tile(k), rowf, ent, lane);
+                __syncwarp();
+                gbd::mixed_tile_pair_rows<CB, CROSS>(ts.tile(k), ent, colf, acc);
+            }
+            gbd::mixed_fold_smem<2, CB>(acc, comp, tid);
+            if (!ts.release(k, lane, warp, spins)) {
+                ok = false;
+                ++k;
+                break;
+            }
         }
-        if constexpr (WIDE) {
-            gbd::mixed_tile_pair<CB, WIDE>(ts.tile(k), colf, rowf, acc);
-        } else {
-            __syncwarp();  // every lane is done with the previous tile's row terms
-            gbd::mixed_pair_rows<CROSS>(ts.tile(k), rowf, ent, lane);
-            __syncwarp();
-            gbd::mixed_tile_pair_rows<CB, CROSS>(ts.tile(k), ent, colf, acc);
+        if (!ok) {
+            record_timeout();
+            if (tid == 0) ts.drain(k, spins);
+            return false;
         }
-        gbd::mixed_fold_smem<2, CB>(acc, comp, tid);
-        if (!ts.release(k, lane, warp, spins)) {
-            ok = false;
-            ++k;
-            break;
-        }
-    }
-    if (!ok) {
-        record_timeout();
-        if (tid == 0) ts.drain(k, spins);
-        return;
-    }
-    const size_t npix = (size_t)nx * ny;
-    float2* out = partial + (size_t)blockIdx.z * npix;
+        const size_t npix = (size_t)nx * ny;
+        float2* out = partial + (size_t)split * npix;
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        const int row = row0 + 8 * r;
-        if (row >= ny) continue;
+        for (int r = 0; r < 2; ++r) {
+            const int row = row0 + 8 * r;
+            if (row >= ny) continue;
 #pragma unroll
-        for (int c = 0; c < CB; ++c) {
-            const int col = col0 + 32 * c;
-            if (col >= nx) continue;
-            const float4 v = comp[(r * CB + c) * kThreads + tid];
-            out[(size_t)row * nx + col] =
-                gbd::round_pair(make_float2(v.x, v.y), make_float2(v.z, v.w));
+            for (int c = 0; c < CB; ++c) {
+                const int col = col0 + 32 * c;
+                if (col >= nx) continue;
+                const float4 v = comp[(r * CB + c) * kThreads + tid];
+                out[(size_t)row * nx + col] =
+                    gbd::round_pair(make_float2(v.x, v.y), make_float2(v.z, v.w));
+            }
         }
+        return true;
+    };
+    if constexpr (LOOP) {
+        // a fallback launch (fallback_z): splits blockIdx.z, blockIdx.z + gridDim.z, ...
+        const int nsplit = (n_tiles + tiles_per_split - 1) / tiles_per_split;
+        int g = 0;  // tiles this CTA has streamed (keeps the barrier phases in step)
+        for (int split = blockIdx.z; split < nsplit; split += gridDim.z) {
+            if (!run(split, g)) return;
+            g += min(n_tiles - split * tiles_per_split, tiles_per_split);
+        }
+    } else {
+        run(blockIdx.z, 0);
     }
 }
 
@@ -847,6 +880,17 @@ cudaError_t launch_mixed(const void* coeffs, int n_tiles, const gbd_project_para
     return cudaGetLastError();
 }
 
+// Grid depth of a fallback launch, which the flag word selects only for some fields and
+// which otherwise returns at once: its CTAs take the splits in equal shares (the LOOP
+// instantiations of field_mixed_kernel and field_mixed_pair_smem_kernel), about 8 CTAs per
+// SM in all, so that an idle launch schedules far fewer CTAs.
+unsigned fallback_z(int splits, unsigned blocks_xy) {
+    const long want = (8L * gbd_sm_count() + blocks_xy - 1) / blocks_xy;
+    const int z = (int)(want < 1 ? 1 : want < splits ? want : splits);
+    const int per = (splits + z - 1) / z;
+    return (unsigned)((splits + per - 1) / per);
+}
+
 // Row pairs, with the direct 2 x CB kernels as the fallback when the projection flags a
 // beamlet too steep for the recurrence.
 template <int CB>
@@ -859,16 +903,17 @@ cudaError_t launch_mixed_pair(const void* coeffs, int n_tiles, const gbd_project
     using gbd::kFlagWide;
     constexpr unsigned kBoth = kFlagWide | kFlagSteep, kAll = kBoth | kFlagColSteep;
     dim3 grid((p.nx + 32 * CB - 1) / (32 * CB), (p.ny + 15) / 16, L.splits);
+    const dim3 grid_fb(grid.x, grid.y, fallback_z(L.splits, grid.x * grid.y));
     const float4* c = static_cast<const float4*>(coeffs);
     const int tps = L.tiles_per_split;
     (void)kBoth;
     // exactly one runs: narrow, then wide (or column-steep), then the steep fallback
     field_mixed_kernel<2, CB, 0, true><<<grid, kThreads, 0, s>>>(
         c, n_tiles, tps, p.nx, p.ny, partial, flags, kAll, 0u, 0u, spins);
-    field_mixed_kernel<2, CB, 1, true><<<grid, kThreads, 0, s>>>(
+    field_mixed_kernel<2, CB, 1, true, true><<<grid_fb, kThreads, 0, s>>>(
         c, n_tiles, tps, p.nx, p.ny, partial, flags, kFlagSteep, 0u, kFlagWide | kFlagColSteep,
         spins);
-    field_mixed_kernel<2, CB, kWideByFlag, false><<<grid, kThreads, 0, s>>>(
+    field_mixed_kernel<2, CB, kWideByFlag, false, true><<<grid_fb, kThreads, 0, s>>>(
         c, n_tiles, tps, p.nx, p.ny, partial, flags, kFlagSteep, kFlagSteep, 0u, spins);
     return cudaGetLastError();
 }
@@ -925,28 +970,34 @@ cudaError_t launch_pair_set(const void* coeffs, int n_tiles, const gbd_project_p
     cudaError_t e = cudaSuccess;
     for (const void* fn : {(const void*)field_mixed_pair_smem_kernel<CB, false, false>,
                            (const void*)field_mixed_pair_smem_kernel<CB, false, true>,
-                           (const void*)field_mixed_pair_smem_kernel<CB, true, true>})
+                           (const void*)field_mixed_pair_smem_kernel<CB, false, true, true>,
+                           (const void*)field_mixed_pair_smem_kernel<CB, true, true, true>})
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((p.nx + 32 * CB - 1) / (32 * CB), (p.ny + 15) / 16, L.splits);
-    dim3 grid24((p.nx + 127) / 128, (p.ny + 15) / 16, L.splits);
+    const dim3 grid_fb(grid.x, grid.y, fallback_z(L.splits, grid.x * grid.y));
+    dim3 grid24((p.nx + 127) / 128, (p.ny + 15) / 16, 1);
+    grid24.z = fallback_z(L.splits, grid24.x * grid24.y);
     const float4* c = static_cast<const float4*>(coeffs);
     const int tps = L.tiles_per_split;
     (void)kBoth;
     // exactly one runs: narrow without a uv term (unless the multi-row kernels ran), narrow
-    // with one (after them: narrow and multi-row steep), then wide (or column-steep), then
-    // the steep fallback
-    if (!after_triple)
+    // with one (behind the multi-row kernels a fallback: narrow and multi-row steep), then
+    // wide (or column-steep), then the steep fallback
+    if (!after_triple) {
         field_mixed_pair_smem_kernel<CB, false, false><<<grid, kThreads, smem, s>>>(
             c, n_tiles, tps, p.nx, p.ny, partial, flags, kAll | kFlagCross, 0u, 0u, spins);
-    field_mixed_pair_smem_kernel<CB, false, true><<<grid, kThreads, smem, s>>>(
-        c, n_tiles, tps, p.nx, p.ny, partial, flags, kAll, 0u,
-        after_triple ? gbd::kFlagSteepRows : kFlagCross, spins);
-    field_mixed_pair_smem_kernel<CB, true><<<grid, kThreads, smem, s>>>(
+        field_mixed_pair_smem_kernel<CB, false, true><<<grid, kThreads, smem, s>>>(
+            c, n_tiles, tps, p.nx, p.ny, partial, flags, kAll, 0u, kFlagCross, spins);
+    } else {
+        field_mixed_pair_smem_kernel<CB, false, true, true><<<grid_fb, kThreads, smem, s>>>(
+            c, n_tiles, tps, p.nx, p.ny, partial, flags, kAll, 0u, gbd::kFlagSteepRows, spins);
+    }
+    field_mixed_pair_smem_kernel<CB, true, true, true><<<grid_fb, kThreads, smem, s>>>(
         c, n_tiles, tps, p.nx, p.ny, partial, flags, kFlagSteep, 0u, kFlagWide | kFlagColSteep,
         spins);
-    field_mixed_kernel<2, 4, kWideByFlag, false><<<grid24, kThreads, 0, s>>>(
+    field_mixed_kernel<2, 4, kWideByFlag, false, true><<<grid24, kThreads, 0, s>>>(
         c, n_tiles, tps, p.nx, p.ny, partial, flags, kFlagSteep, kFlagSteep, 0u, spins);
     return cudaGetLastError();
 }
