@@ -448,6 +448,55 @@ def test_row_pair_scheme_falls_back_on_steep_beamlets(splits):
         gbd.gbd_field_reset_shape(prec)
 
 
+def fallback_cases():
+    """Fields that only the fallback launches take, with 51 record tiles: beamlets 64 across
+    focused to ~8 pixels on a 512^2 detector of 50 um pixels (steep, wide, column-steep and
+    multi-row steep: the direct fallback, every phase reduced) and the 41 lambda F# beamlets
+    of near_wide_case on a 704^2 detector (the wide bit alone: the general row pairs)."""
+    big = W.airy_large()
+    p = big.detector.pitch_x
+    return {
+        "steep": (W.Workload("steep64", W.System(1e-6, 0.024, 0.024), W.Pupil(2.4e-3, 64, 1.0, 1.0),
+                             W.Detector(512, 512, 5e-5, 5e-5)), 2),
+        "wide": (W.Workload("wide704", big.system, W.Pupil(2.4e-3, 64, 1.0, 1.0),
+                            W.Detector(704, 704, p, p)), 1),
+    }
+
+
+@pytest.mark.parametrize("shape", [(2, 8), (4, 8), (2, 4)])
+@pytest.mark.parametrize("name", ["steep", "wide"])
+def test_fallbacks_take_several_splits_per_cta(name, shape):
+    """The fallback launches spread their splits in equal shares over about 8 CTAs per SM,
+    so with one split per record tile (51) each CTA streams up to six splits in turn, its
+    tile barriers' phases carried from one to the next.  The field matches the oracle (on a
+    strided sample; the steep field, which lives near the centre, on the central window),
+    agrees with 9 splits (one per CTA) to FP32 rounding, and repeats bit for bit."""
+    wl, bit = fallback_cases()[name]
+    b = gpu_trace(wl)
+    f = projection_flags(b, wl)
+    assert f & bit and (name == "steep" or f == 1), f
+    nx, ny = wl.detector.nx, wl.detector.ny
+    # the steep field lives within a few pixels of the centre (5 of a 16-pixel-stride sample
+    # above 1e-3 of its peak): its sample is the central 112^2 window
+    if name == "steep":
+        cols = rows = np.arange(nx // 2 - 56, nx // 2 + 56)
+    else:
+        cols, rows = np.arange(5, nx, 16), np.arange(3, ny, 16)
+    Eo = oracle.field(oracle.trace(wl.system, wl.pupil), wl.system, wl.detector, cols, rows)
+    prec = gbd.GBD_PREC_MIXED
+    try:
+        gbd.gbd_field_set_shape(prec, shape[0], shape[1], 51, gbd.GBD_SCHEME_ROW_PAIR)
+        E = gpu_field(b, wl, prec)
+        E2 = gpu_field(b, wl, prec)
+        gbd.gbd_field_set_shape(prec, shape[0], shape[1], 9, gbd.GBD_SCHEME_ROW_PAIR)
+        E9 = gpu_field(b, wl, prec)
+    finally:
+        gbd.gbd_field_reset_shape(prec)
+    assert np.array_equal(E, E2)
+    assert rel_l2(E[np.ix_(rows, cols)], Eo) <= TOL[prec]
+    assert rel_l2(E, E9) <= 1e-6
+
+
 def test_autotune_then_parity():
     import torch
     wl = W.airy_small()
