@@ -357,7 +357,8 @@ __global__ void __launch_bounds__(kThreads, 2)
     __shared__ int flag;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    constexpr int kEntF4 = CROSS ? gbd::kRowsCrossF4<RB> : gbd::kRowsF4;
+    constexpr bool kX2 = !CROSS && RB == 4 && CB == 8;  // the packed quadruples
+    constexpr int kEntF4 = CROSS ? gbd::kRowsCrossF4<RB> : kX2 ? gbd::kRowsX2F4 : gbd::kRowsF4;
     float4* ent = dyn4 + kStages * kTileF4 + warp * (kEntF4 * gbd::kTile);
     const int split = blockIdx.x, bx = blockIdx.y, by = blockIdx.z;
     const int t0 = split * tiles_per_split;
@@ -398,7 +399,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         if constexpr (CROSS)
             gbd::mixed_rows_cross_terms<RB>(ts.tile(k), rowf, ent, lane);
         else
-            gbd::mixed_rows_terms<RB>(ts.tile(k), rowf, ent, lane);
+            gbd::mixed_rows_terms<RB, kX2>(ts.tile(k), rowf, ent, lane);
         __syncwarp();
         // packed FP32x2 arithmetic where it pays: on airy_large the 4 x 8 shape (2 CTAs per
         // SM) ran 2.85 ms with it against 3.02 without; 4 x 4 (2.92 -> 3.00 ms) and 3 x 8
@@ -492,11 +493,13 @@ constexpr unsigned kRowsNarrow = gbd::kFlagWide | gbd::kFlagSteep | gbd::kFlagCo
 // kernels store the field themselves when these are all clear).
 constexpr unsigned kRowsTaken = kRowsNarrow & ~gbd::kFlagCross;
 
-template <bool CROSS = false, int RB = 4>
+template <bool CROSS = false, int RB = 4, int CB = 4>
 constexpr size_t rows_smem_bytes() {
     return (size_t)kStages * gbd::kMixedTileBytes +
-           (size_t)kWarps * (CROSS ? gbd::kRowsCrossF4<RB> : gbd::kRowsF4) * gbd::kTile *
-               sizeof(float4);
+           (size_t)kWarps *
+               (CROSS ? gbd::kRowsCrossF4<RB>
+                      : RB == 4 && CB == 8 ? gbd::kRowsX2F4 : gbd::kRowsF4) *
+               gbd::kTile * sizeof(float4);
 }
 
 template <int CB>
@@ -1027,7 +1030,8 @@ cudaError_t launch_mixed_rows(const void* coeffs, int n_tiles, const gbd_project
     // fields with a uv term on row triples behind the 4 x 8 quadruples (tilted Zernike
     // 1024^2: 4.60 ms against 4.70 ms on 4 x 8; the telescope's PSF 4.68 against 4.89)
     constexpr int RX = RB == 4 && CB == 8 ? 3 : RB;
-    constexpr size_t smem = rows_smem_bytes<false>(), smem_x = rows_smem_bytes<true, RX>();
+    constexpr size_t smem = rows_smem_bytes<false, RB, CB>(),
+                     smem_x = rows_smem_bytes<true, RX>();
     cudaError_t e = cudaFuncSetAttribute(field_mixed_rows_kernel<RB, CB, false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
@@ -1077,7 +1081,7 @@ const ShapeEntry kMixedShapes[] = {
      rows_smem_bytes()},
     {4, 8, GBD_SCHEME_ROW_PAIR, launch_mixed_rows<4, 8>,
      (const void*)field_mixed_rows_kernel<4, 8>,
-     rows_smem_bytes()},
+     rows_smem_bytes<false, 4, 8>()},
     {4, 4, GBD_SCHEME_ROW_PAIR, launch_mixed_rows<4, 4>,
      (const void*)field_mixed_rows_kernel<4, 4>,
      rows_smem_bytes()},

@@ -293,8 +293,13 @@ __device__ __forceinline__ void mixed_pair_rows(const float4* __restrict__ st, f
 //   ent[2][b] = (64 a_uu, 64 p_uu, R),  ent[3][b] = (S_2, S_3),
 // with ra, rp, sa, sp as in mixed_pair_rows and sig = 2^(2048 a_uu).
 constexpr int kRowsF4 = 4;
-// The row terms of stage beamlet b, written to ent[k * stride + i] (k = 0..3).
-template <int RB>
+// The packed quadruples (mixed_tile_rows_x2) also take the pairs (-S_r.im, S_r.re) from
+// the row terms: ent[4][b] = (-S_1.im, S_1.re, -S_2.im, S_2.re), ent[5][b] = (-S_3.im,
+// S_3.re, 0, 0), formed once per warp instead of by every thread.
+constexpr int kRowsX2F4 = 6;
+// The row terms of stage beamlet b, written to ent[k * stride + i] (k = 0..3, and 4, 5
+// with SWAP).
+template <int RB, bool SWAP = false>
 __device__ __forceinline__ void mixed_rows_term(const float4* __restrict__ st, int b, float rowf,
                                                 float4* __restrict__ ent, int i, int stride) {
     const float kTwoPi = 6.28318530717958647692f, kInvTwoPi = 0.15915494309189533577f;
@@ -327,14 +332,19 @@ __device__ __forceinline__ void mixed_rows_term(const float4* __restrict__ st, i
                                   mufu_ex2(2048.0f * q2.x));
     ent[2 * stride + i] = make_float4(64.0f * q2.x, 64.0f * q2.y, R.x, R.y);
     ent[3 * stride + i] = make_float4(S2.x, S2.y, S3.x, S3.y);
+    if (SWAP) {
+        ent[4 * stride + i] = make_float4(-R.y, R.x, -S2.y, S2.x);
+        ent[5 * stride + i] = make_float4(-S3.y, S3.x, 0.0f, 0.0f);
+    }
 }
 
 // All 64 beamlets of the tile: lane l takes beamlets l and l + 32.
-template <int RB>
+template <int RB, bool SWAP = false>
 __device__ __forceinline__ void mixed_rows_terms(const float4* __restrict__ st, float rowf,
                                                  float4* __restrict__ ent, int lane) {
 #pragma unroll
-    for (int h = 0; h < kTile / 32; ++h) mixed_rows_term<RB>(st, lane + 32 * h, rowf, ent, lane + 32 * h, kTile);
+    for (int h = 0; h < kTile / 32; ++h)
+        mixed_rows_term<RB, SWAP>(st, lane + 32 * h, rowf, ent, lane + 32 * h, kTile);
 }
 
 // The narrow instantiation of mixed_tile_pair (same arithmetic, regrouped) on the row
@@ -468,11 +478,13 @@ __device__ __forceinline__ void mixed_tile_rows_x2(const float4* __restrict__ en
         const float4 e1 = ent[NB + b];
         const float4 e2 = ent[2 * NB + b];
         const float4 e3 = ent[3 * NB + b];
+        const float4 e4 = ent[4 * NB + b];
+        const float4 e5 = ent[5 * NB + b];
         const float2 S[3] = {make_float2(e2.z, e2.w), make_float2(e3.x, e3.y),
                              make_float2(e3.z, e3.w)};
-        float2 Sr[3];  // (-S.im, S.re): multiplies E0.im
-#pragma unroll
-        for (int r = 0; r < 3; ++r) Sr[r] = make_float2(-S[r].y, S[r].x);
+        // (-S.im, S.re): multiplies E0.im (from the row terms)
+        const float2 Sr[3] = {make_float2(e4.x, e4.y), make_float2(e4.z, e4.w),
+                              make_float2(e5.x, e5.y)};
         const float tu0 = colf[0] - e0.x;
         const float t64 = tu0 * 0.015625f;
         const float x0 = fmaf(tu0, fmaf(e2.y, t64, e1.x), e0.z);
