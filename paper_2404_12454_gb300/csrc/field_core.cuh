@@ -489,21 +489,25 @@ __device__ __forceinline__ void mixed_tile_rows_x2(const float4* __restrict__ en
         const float t64 = tu0 * 0.015625f;
         const float x0 = fmaf(tu0, fmaf(e2.y, t64, e1.x), e0.z);
         const float d1 = fmaf(e2.y, tu0, e1.z);
-        // (amp, rho): the first row's amplitude at the thread's column and its ratio
-        float2 ar = make_float2(mufu_ex2(fmaf(tu0, fmaf(e2.x, t64, e0.w), e0.y)),
-                                mufu_ex2(fmaf(e2.x, tu0, e1.y)));
+        // the first row's amplitude at the thread's column and its ratio, advanced in scalar
+        // FMULs (the FMA-lite pipe can take them; the packed form sits on the heavy pipe)
+        float amp = mufu_ex2(fmaf(tu0, fmaf(e2.x, t64, e0.w), e0.y));
+        float rho = mufu_ex2(fmaf(e2.x, tu0, e1.y));
         const float sig = e1.w;
 #pragma unroll
         for (int c = 0; c < CB; ++c) {
             const float x = c == 0 ? x0 : fmaf((float)(16 * c * c), e2.y, fmaf((float)c, d1, x0));
-            const float2 E0 = __fmul2_rn(make_float2(ar.x, ar.x), make_float2(mufu_cos(x), mufu_sin(x)));
+            const float2 E0 = __fmul2_rn(make_float2(amp, amp), make_float2(mufu_cos(x), mufu_sin(x)));
             acc[0][c] = __fadd2_rn(acc[0][c], E0);
 #pragma unroll
             for (int r = 1; r < RB; ++r) {
                 acc[r][c] = __ffma2_rn(make_float2(E0.y, E0.y), Sr[r - 1], acc[r][c]);
                 acc[r][c] = __ffma2_rn(make_float2(E0.x, E0.x), S[r - 1], acc[r][c]);
             }
-            if (c + 1 < CB) ar = __fmul2_rn(ar, make_float2(ar.y, sig));
+            if (c + 1 < CB) {
+                amp *= rho;
+                rho *= sig;
+            }
         }
     }
 }
