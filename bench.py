@@ -50,8 +50,8 @@ FIELD_MIXED_NCU = [
      "write": 2.884352e6, "splits": 90, "rows": 4, "cols": 4, "scheme": 1,
      "inst_per_32_evals": 6.81, "fma_pipe_active": 0.675},
     {"kernel": "field_mixed_rows_kernel<4, 8> (4x8 row quadruples, packed FP32x2)",
-     "read": 3.3472e6, "write": 3.54176e6, "splits": 90, "rows": 4, "cols": 8, "scheme": 1,
-     "inst_per_32_evals": 4.74, "fma_pipe_active": 0.721},
+     "read": 3.364864e6, "write": 4.082944e6, "splits": 90, "rows": 4, "cols": 8, "scheme": 1,
+     "inst_per_32_evals": 4.38, "fma_pipe_active": 0.730},
 ]
 ISSUE_PER_CLK_SM = 4  # warp-instructions issued per clock and SM (one per sub-partition)
 
