@@ -459,14 +459,16 @@ __device__ __forceinline__ void mixed_tile_rows(const float4* __restrict__ ent,
 
 // mixed_tile_rows with the complex arithmetic in packed FP32x2 instructions (FFMA2, FMUL2,
 // FADD2 on (re, im) pairs): E0 = amp (cos, sin) one FMUL2, the first row one FADD2, each
-// later row two FFMA2 (E0.re (S.re, S.im) and E0.im (-S.im, S.re) onto (re, im)) and the
-// amplitude recurrence one FMUL2 ((amp, rho) *= (rho, sig)): 15 instructions per column
-// of 4 pixels instead of 24.  Every lane rounds as the scalar FMA / FMUL / FADD, in the same
-// order, so the sums are the same bits as mixed_tile_rows' (up to the compiler's choice of
-// contracting the first row's add into an FMA there).  The packed operations all run on
-// the FMA-heavy pipe, which then binds (ncu: math-pipe throttle the largest stall, 61 % of
-// issue slots on the 4 x 8 shape); moving a row back to scalar FFMA did not help (3.04
-// and 2.89 ms for one and two scalar rows against 2.85 ms).
+// later row two FFMA2 (E0.re (S.re, S.im) and E0.im (-S.im, S.re) onto (re, im)); the
+// amplitude recurrence in two scalar FMULs (the FMA-lite pipe takes them).  The pairs
+// (-S.im, S.re) come from the row terms (mixed_rows_term<RB, true>: ent[4], ent[5]), formed
+// once per warp instead of by every thread (a negation and a move each).  Every lane rounds
+// as the scalar FMA / FMUL / FADD, in the same order, so the sums are the same bits as
+// mixed_tile_rows' (up to the compiler's choice of contracting the first row's add into an
+// FMA there).  The packed operations all run on the FMA-heavy pipe, which then binds (ncu:
+// math-pipe throttle the largest stall); moving a row back to scalar FFMA did not help
+// (3.04 and 2.89 ms for one and two scalar rows against 2.85 ms), nor did forming E0 by
+// scalar FMULs (2.78 ms against 2.74 ms).
 template <int RB, int CB, int NB = kTile>
 __device__ __forceinline__ void mixed_tile_rows_x2(const float4* __restrict__ ent,
                                                    const float (&colf)[CB],
