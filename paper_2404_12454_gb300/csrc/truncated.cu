@@ -119,8 +119,16 @@ struct Cplx {
 // One Taylor step of w from z to z + h (FP32 path): the derivatives at z follow from
 // w' = -2 z w + 2 i / sqrt(pi) by w^(n+1) = -2 z w^(n) - 2 n w^(n-1); to 4th order the step
 // keeps 4e-7 relative over a segment of 8 steps while |h| (2 |z|_1 + 3) <= 0.2 (checked
-// against a reference Faddeeva function off the device).
-__device__ __forceinline__ void faddeeva_step(float zr, float zi, float hr, float hi, float& wr,
+// against a reference Faddeeva function off the device).  The step and its scaled copies
+// for the Horner evaluation, h/4, h/3, h/2, h, are formed once per run of steps.
+struct TaylorStep {
+    float r[4], i[4];
+};
+__device__ __forceinline__ TaylorStep taylor_step(float hr, float hi) {
+    const float third = 0.333333343f;
+    return {{0.25f * hr, third * hr, 0.5f * hr, hr}, {0.25f * hi, third * hi, 0.5f * hi, hi}};
+}
+__device__ __forceinline__ void faddeeva_step(float zr, float zi, const TaylorStep& h, float& wr,
                                               float& wi) {
     const float c = 1.12837916709551257390f;  // 2 / sqrt(pi)
     const float d1r = -2.0f * fmaf(zr, wr, -zi * wi), d1i = fmaf(-2.0f, fmaf(zr, wi, zi * wr), c);
@@ -132,18 +140,17 @@ __device__ __forceinline__ void faddeeva_step(float zr, float zi, float hr, floa
     const float d4i = fmaf(-6.0f, d2i, -2.0f * fmaf(zr, d3i, zi * d3r));
     // Horner in h: w + h (d1 + h/2 (d2 + h/3 (d3 + h/4 d4)))
     float ar = d4r, ai = d4i, tr;
-    tr = fmaf(0.25f * hr, ar, fmaf(-0.25f * hi, ai, d3r));
-    ai = fmaf(0.25f * hr, ai, fmaf(0.25f * hi, ar, d3i));
+    tr = fmaf(h.r[0], ar, fmaf(-h.i[0], ai, d3r));
+    ai = fmaf(h.r[0], ai, fmaf(h.i[0], ar, d3i));
     ar = tr;
-    const float third = 0.333333343f;
-    tr = fmaf(third * hr, ar, fmaf(-third * hi, ai, d2r));
-    ai = fmaf(third * hr, ai, fmaf(third * hi, ar, d2i));
+    tr = fmaf(h.r[1], ar, fmaf(-h.i[1], ai, d2r));
+    ai = fmaf(h.r[1], ai, fmaf(h.i[1], ar, d2i));
     ar = tr;
-    tr = fmaf(0.5f * hr, ar, fmaf(-0.5f * hi, ai, d1r));
-    ai = fmaf(0.5f * hr, ai, fmaf(0.5f * hi, ar, d1i));
+    tr = fmaf(h.r[2], ar, fmaf(-h.i[2], ai, d1r));
+    ai = fmaf(h.r[2], ai, fmaf(h.i[2], ar, d1i));
     ar = tr;
-    tr = fmaf(hr, ar, fmaf(-hi, ai, wr));
-    wi = fmaf(hr, ai, fmaf(hi, ar, wi));
+    tr = fmaf(h.r[3], ar, fmaf(-h.i[3], ai, wr));
+    wi = fmaf(h.r[3], ai, fmaf(h.i[3], ar, wi));
     wr = tr;
 }
 
@@ -194,6 +201,11 @@ __global__ void __launch_bounds__(256) field_edge_kernel(const double2* __restri
             const T zr0 = fma(r[18], tv, r[14]), zi0 = fma(r[19], tv, r[15]);
             T wr = (T)0, wi = (T)0, xpr = (T)0, xpi = (T)0;
             bool pneg = false;
+            // zeta steps by (r16, r17) from pixel to pixel, so its image x = -i zeta
+            // (Re zeta < 0) or i zeta steps by +-(r17, -r16): the Taylor step is fixed by
+            // the sign, which only changes at an exact evaluation
+            TaylorStep hs{};
+            const T mh = fabs(r[16]) + fabs(r[17]);  // |h|_1
 #pragma unroll
             for (int c = 0; c < kEdgePix; ++c) {
                 const T tu = tu0 + (T)c;
@@ -202,19 +214,18 @@ __global__ void __launch_bounds__(256) field_edge_kernel(const double2* __restri
                 // i zeta = (-zi, zr); -i zeta = (zi, -zr): the one in the upper half-plane
                 const T xr = neg ? zi : -zi, xi = neg ? -zr : zr;
                 bool exact = true;
-                T hr = (T)0, hi = (T)0;
                 if constexpr (STEP) {
                     if (c > 0 && neg == pneg) {
-                        hr = xr - xpr;
-                        hi = xi - xpi;
-                        const T m = fabs(hr) + fabs(hi), zz = fabs(xpr) + fabs(xpi);
-                        exact = !(m * fma((T)2, zz, (T)3) <= (T)0.2);
+                        const T zz = fabs(xpr) + fabs(xpi);
+                        exact = !(mh * fma((T)2, zz, (T)3) <= (T)0.2);
                     }
                 }
                 if (exact) {
                     faddeeva<T, NW>(xr, xi, F, wr, wi);
+                    if constexpr (STEP)
+                        hs = taylor_step(neg ? r[17] : -r[17], neg ? -r[16] : r[16]);
                 } else {
-                    if constexpr (STEP) faddeeva_step(xpr, xpi, hr, hi, wr, wi);
+                    if constexpr (STEP) faddeeva_step(xpr, xpi, hs, wr, wi);
                 }
                 xpr = xr;
                 xpi = xi;
