@@ -456,7 +456,10 @@ def run_ours(args, world, rank, local):
     e2e = {"value": world * evals * args.steps / e2e_total, "unit": UNIT,
            "h2d_bytes_per_step": gbd_system_bytes + 16 + 40,
            "d2h_bytes_per_step": npix * 8,
-           "api": "gbd_psf (host parameters -> pinned host complex64 field)"}
+           "api": "gbd_psf (host parameters -> pinned host complex64 field)",
+           # host-clock spread of the steps (the value is their sum: a host stall counts)
+           "step_ms_median": float(np.median(e2e_t)) * 1e3,
+           "step_ms_max": float(np.max(e2e_t)) * 1e3}
 
     # ---- batched parameter sweep: 1024 uneven instances in one persistent launch, replayed
     # as a CUDA graph on its own stream
